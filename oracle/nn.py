@@ -1,0 +1,74 @@
+"""ctypes front end of the oracle's brute-force nearest-neighbour scan (nn.c).
+
+Exact P_D of Eq. (7): for each mapped query the data point with the smallest
+squared Euclidean distance in the map of Sec. 3.2 (which equals d_e^2 / 2 of
+Eq. 3).  TEST INFRASTRUCTURE ONLY.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_build", "liboracle_nn.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile nn.c with gcc (OpenMP, no FP contraction) into oracle/_build."""
+    src = os.path.join(_HERE, "nn.c")
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+        os.makedirs(os.path.dirname(_SO), exist_ok=True)
+        tmp = _SO + f".{os.getpid()}.tmp"
+        subprocess.run(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+                        src, "-o", tmp, "-lm"], check=True)
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            dp = ctypes.POINTER(ctypes.c_double)
+            ip = ctypes.POINTER(ctypes.c_int64)
+            lib.oracle_nn_top2.argtypes = [dp, ctypes.c_int64, dp, ctypes.c_int64, ctypes.c_int,
+                                           ip, dp, ip, dp]
+            lib.oracle_nn_top2.restype = None
+            lib.oracle_nn_threads.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def threads() -> int:
+    return int(_load().oracle_nn_threads())
+
+
+def nn_top2(zd: np.ndarray, zq: np.ndarray):
+    """Exact nearest and second-nearest data rows for every query row.
+
+    Returns (i1, d1, i2, d2): int64 indices and float64 squared distances
+    |z_j - q|^2 in the mapped coordinates.
+    """
+    lib = _load()
+    zd = np.ascontiguousarray(zd, dtype=np.float64)
+    zq = np.ascontiguousarray(zq, dtype=np.float64)
+    n, dim = zd.shape
+    m = zq.shape[0]
+    assert zq.shape[1] == dim
+    i1 = np.empty(m, np.int64)
+    i2 = np.empty(m, np.int64)
+    d1 = np.empty(m, np.float64)
+    d2 = np.empty(m, np.float64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int64)
+    lib.oracle_nn_top2(zd.ctypes.data_as(dp), n, zq.ctypes.data_as(dp), m, dim,
+                       i1.ctypes.data_as(ip), d1.ctypes.data_as(dp),
+                       i2.ctypes.data_as(ip), d2.ctypes.data_as(dp))
+    return i1, d1, i2, d2

@@ -1,0 +1,85 @@
+"""Pins of the oracle's DD fixed-point iteration (Eq. 4-8)."""
+import numpy as np
+import pytest
+
+import dd_inputs as I
+from oracle import dd, fem, metric
+
+
+def small_problem(n_el=2, N=2000, seed=0, law=I.LINEAR, load=("tension", 1e-3)):
+    C = I.isotropic_C()
+    data = I.make_dataset(N, law, seed=seed)
+    return dd.DDProblem(data, C, n_el, I.load_case(*load)), C, data
+
+
+def test_monotone_and_terminates():
+    P, C, data = small_problem()
+    m = P.fe.m
+    r = P.solve(I.initial_association(m, len(data), seed=0))
+    assert r.converged and r.iters > 2
+    pc, pd = np.array(r.d2_after_pc), np.array(r.d2_after_pd)
+    tol = 1e-12 * pc[0]
+    assert np.all(pd <= pc + tol)                  # P_D minimises over the data
+    assert np.all(pc[1:] <= pd[:-1] + tol)         # P_C minimises over the constraint set
+    assert r.changed[-1] == 0
+
+
+@pytest.mark.parametrize("load", [("tension", 1e-3), ("torsion", 1e-3)])
+def test_pc_lands_in_constraint_set(load):
+    """Equilibrium A_e{w B^T sig} = f on the free dofs, compatibility eps = B u."""
+    P, C, data = small_problem(load=load)
+    idx = I.initial_association(P.fe.m, len(data), seed=4)
+    u, eta, eps, sig = P.project_C(idx)
+    free = P.solver.free
+    r = P.fe.assemble_BT(sig) - P.f
+    assert np.abs(r[free]).max() < 1e-10 * np.abs(P.f).max()
+    assert np.allclose(eps, P.fe.strains(u), rtol=0, atol=1e-18)
+
+
+def test_planted_linear_fem_solution_is_a_fixed_point():
+    """Add to D the states (eps_FEM, C eps_FEM) of the linear FE solution:
+    from that association Eq. (5a) returns u_FEM, Eq. (5b) gives S = 0, so
+    eta = 0 and the state is reproduced with zero distance."""
+    C = I.isotropic_C()
+    n_el = 2
+    b = fem.HexBox(n_el, n_el, n_el, C)
+    solver = fem.DirectSolver(b.K(), b.clamped_bottom())
+    L = I.load_case("torsion", 1e-3)
+    u_fem = solver.solve(b.top_traction_force(L.t0, L.tx, L.ty))
+    eps_fem = b.strains(u_fem)
+    planted = np.concatenate([eps_fem, eps_fem @ C.T], axis=1)
+    noise = I.make_dataset(500, I.LINEAR, seed=1).astype(np.float64)
+    data = np.concatenate([noise, planted])          # float64: planted exactly
+    P = dd.DDProblem(data, C, n_el, L)
+    init = np.arange(len(noise), len(data), dtype=np.int32)
+    r = P.solve(init, max_iter=10)
+    # symmetric meshes give several material points the same FE state, so
+    # the association may move between equal planted points: compare states
+    assert r.converged
+    assert np.allclose(data[r.idx], planted, rtol=0, atol=1e-15)
+    assert np.allclose(r.u, u_fem, rtol=0, atol=1e-9 * np.abs(u_fem).max())
+    assert max(r.d2_after_pc[0], r.d2_after_pd[-1]) <= 1e-28
+
+
+def test_dense_noise_free_data_approaches_linear_fem():
+    """Noise-free data on sigma = C eps, metric = C: the DD displacement tends
+    to the linear FE displacement as the data set is refined."""
+    C = I.isotropic_C()
+    law = I.DataLaw("linear", -2e-3, 2e-3, 0.0)
+    n_el = 2
+    L = I.load_case("tension", 1e-3)
+    b = fem.HexBox(n_el, n_el, n_el, C)
+    u_fem = fem.DirectSolver(b.K(), b.clamped_bottom()).solve(b.top_traction_force(L.t0))
+    errs = []
+    for N in (300, 3000, 30000):
+        P = dd.DDProblem(I.make_dataset(N, law, seed=2), C, n_el, L)
+        r = P.solve(I.initial_association(P.fe.m, N, seed=2))
+        errs.append(np.linalg.norm(r.u - u_fem) / np.linalg.norm(u_fem))
+    assert errs[2] < errs[0] and errs[2] < 0.5 * errs[0]
+
+
+def test_distance_history_consistent_with_eq2():
+    P, C, data = small_problem(N=500)
+    r = P.solve(I.initial_association(P.fe.m, len(data), seed=9))
+    # after P_D the recorded distance is sum w |dq|^2 = sum 1/2 w d_e^2 of the new association
+    assert np.isclose(P.global_d2(r.eps, r.sig, r.idx), r.d2_after_pd[-1], rtol=1e-12)
