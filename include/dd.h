@@ -1,0 +1,258 @@
+/*
+ * dd.h - C ABI of a GB300 (sm_103a) library for the hot path of model-free
+ * data-driven (DD) computational mechanics: per-iteration projection of every
+ * material point's (strain, stress) state onto its nearest point of a material
+ * data set, alternating with the projection onto the constraint set.
+ *
+ * Method: Eggersmann, Stainier, Ortiz & Reese, "Efficient Data Structures for
+ * Model-free Data-Driven Computational Mechanics" (arXiv:2012.00357).
+ *   Sec. 2, Eq. (1)-(3): DD problem, global distance, C-weighted local metric.
+ *   Sec. 2, Eq. (4)-(6): constraint projection P_C (two solves with K).
+ *   Sec. 2, Eq. (7)-(8): data projection P_D and the fixed-point iteration.
+ *   Sec. 3.2:            Euclidean map q = (C^{1/2} eps, C^{-1/2} sig).
+ *   Sec. 4.2-4.5, Eq. (11), (13), (14): approximate k-means search, accuracy
+ *                        ramp of f_d, warm start and moving-query radius.
+ *
+ * Conventions shared by every call
+ *   - States are rows of 12 values (eps[6], sig[6]) in Voigt order
+ *     (xx, yy, zz, yz, xz, xy), engineering shear strains, row-major.
+ *   - The metric C is a symmetric positive definite 6x6 Voigt matrix, given
+ *     as 36 row-major doubles in host memory.
+ *   - Pointers documented "host or device" may point to either; the library
+ *     detects the kind with cudaPointerGetAttributes.  Device pointers must
+ *     belong to the context's device.  Host-pointer calls are synchronous;
+ *     device-pointer calls are ordered on the given stream and the caller
+ *     synchronises before reading the results.
+ *   - Every call returns a dd_status; no call aborts or throws.  After an
+ *     error dd_last_error(ctx) returns a message.  A DD_ERR_CUDA or
+ *     DD_ERR_TIMEOUT status leaves the context usable unless the CUDA
+ *     context itself was lost (then every later call returns DD_ERR_CUDA).
+ *   - Objects are owned by the caller once returned and are released with
+ *     the matching *_free / dd_destroy call.  Calls on one context are not
+ *     thread-safe; use one context per host thread.
+ */
+#ifndef DD_H
+#define DD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#pragma GCC visibility push(default)
+#endif
+
+typedef enum dd_status {
+    DD_OK = 0,
+    DD_ERR_ARG = 1,            /* invalid argument: null, size, range, NaN */
+    DD_ERR_NOT_SPD = 2,        /* metric not symmetric positive definite */
+    DD_ERR_OOM = 3,            /* device allocation failed or HBM budget exceeded */
+    DD_ERR_CUDA = 4,           /* CUDA runtime error */
+    DD_ERR_TIMEOUT = 5,        /* a bounded device-side wait expired */
+    DD_ERR_NOT_CONVERGED = 6,  /* iteration limit reached; outputs are filled */
+    DD_ERR_STATE = 7           /* call not valid for this object */
+} dd_status;
+
+typedef struct dd_ctx dd_ctx;
+typedef struct dd_dataset dd_dataset;
+
+/* Search modes of the data projection P_D (Eq. 7). */
+enum {
+    DD_SEARCH_EXACT_FP32 = 0,  /* exact: FP32 streaming scan + FP64 rescoring */
+    DD_SEARCH_EXACT_TC = 1,    /* exact: FP16 tensor-core contraction, FP32
+                                  accumulation, candidates rescored in FP64 */
+    DD_SEARCH_ANN = 2          /* approximate k-means partition search (Eq. 13),
+                                  warm-started from the previous neighbour */
+};
+
+/* ------------------------------------------------------------------------ */
+/* Context                                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`.  `hbm_budget` caps the device
+ * bytes the context may hold (0 = no cap beyond the device's free memory).
+ * Allocates a stream and small bookkeeping buffers.  *out is set on DD_OK. */
+dd_status dd_create(int device, size_t hbm_budget, dd_ctx **out);
+
+/* Release the context.  Every dataset created from it must be freed first. */
+void dd_destroy(dd_ctx *ctx);
+
+/* Message of the last failed call on ctx ("" if none).  Valid until the next
+ * call on ctx.  ctx may be NULL (then: the last dd_create failure). */
+const char *dd_last_error(const dd_ctx *ctx);
+
+/* Device bytes currently held by the context (datasets, workspaces). */
+size_t dd_bytes_in_use(const dd_ctx *ctx);
+
+/* ------------------------------------------------------------------------ */
+/* Material data set                                                         */
+/* ------------------------------------------------------------------------ */
+
+typedef struct dd_dataset_opts {
+    int build_fp16;     /* 1: also build the FP16 operand copy used by
+                           DD_SEARCH_EXACT_TC (32 bytes per point) */
+    int ann_nlist;      /* >0: build the k-means partition used by DD_SEARCH_ANN
+                           with this many clusters; 0: none */
+    int ann_train_iters;/* Lloyd iterations of the partition build (default 8) */
+    int64_t ann_sample; /* training sample size (0: min(N, 64 * ann_nlist)) */
+    uint64_t seed;      /* seed of the partition build's initial centroids */
+    int borrow;         /* 1 and eps_sig is a device pointer: keep using the
+                           caller's buffer instead of copying it; it must stay
+                           valid and unchanged until dd_free_dataset */
+} dd_dataset_opts;
+
+/* Load a material data set D = {(eps_j, sig_j)}, j = 0..N-1 (Sec. 2) and
+ * pre-transform it to the Euclidean map of Sec. 3.2,
+ *     z_j = (C^{1/2} eps_j, C^{-1/2} sig_j) / sqrt(2),
+ * so that |z_j - z(y)|^2 = d_e^2(y, (eps_j, sig_j)) / 2 with d_e of Eq. (3).
+ *   eps_sig  host or device, float32 [N x 12] row-major (eps[6], sig[6]).
+ *            These values are the data set; FP64 rescoring reads them.
+ *   N        1 .. 2^31 - 1.
+ *   C        host, 36 doubles, the SPD metric of Eq. (3).
+ *   opts     may be NULL (all zero).
+ * Errors: DD_ERR_ARG (N out of range, null pointers, non-finite data),
+ * DD_ERR_NOT_SPD, DD_ERR_OOM, DD_ERR_CUDA.  Synchronous. */
+dd_status dd_load_dataset(dd_ctx *ctx, const float *eps_sig, int64_t N,
+                          const double *C, const dd_dataset_opts *opts,
+                          dd_dataset **out);
+
+void dd_free_dataset(dd_dataset *ds);
+
+/* Number of points and the byte size of the device-resident copies. */
+int64_t dd_dataset_size(const dd_dataset *ds);
+size_t dd_dataset_bytes(const dd_dataset *ds);
+
+/* Write points start .. start+N-1 of the seeded synthetic data set into the
+ * device buffer out_dev (float32 [N x 12]).  This is the device copy of the
+ * input generator of the Python module dd_inputs (SplitMix64 counter stream,
+ * uniform strains in [eps_lo, eps_hi], stress from the law `law` = 0:
+ * sig = C eps, 1: sig = C eps (1 + beta |eps|), plus Irwin-Hall noise of std
+ * noise_std), bit-identical to it.  It is not part of the DD method; it
+ * exists so that data sets of 10^8-10^9 points can be made in place.
+ * Asynchronous on `stream` (a cudaStream_t, NULL = the context's stream). */
+dd_status dd_synth_dataset(dd_ctx *ctx, int law, double eps_lo, double eps_hi,
+                           double noise_std, double beta, const double *C,
+                           uint64_t seed, int64_t start, int64_t N,
+                           float *out_dev, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Data projection P_D                                                       */
+/* ------------------------------------------------------------------------ */
+
+typedef struct dd_search_opts {
+    int mode;                 /* DD_SEARCH_* */
+    int certify;              /* exact modes: 1 (default when opts is NULL)
+                                 = queries whose low-precision candidate window
+                                 overflowed are re-searched exactly in FP64,
+                                 so the result is the exact argmin; 0 = keep
+                                 the best rescored candidate (reported) */
+    double f_d;               /* DD_SEARCH_ANN: accuracy parameter of Eq. (13),
+                                 0 = no backtracking .. 1 = exact */
+    const int32_t *prev_idx;  /* DD_SEARCH_ANN: previous neighbour of each
+                                 query (warm start), host or device, or NULL */
+    void *stream;             /* cudaStream_t for device pointers, NULL = ctx */
+} dd_search_opts;
+
+typedef struct dd_search_stats {
+    int64_t uncertified;      /* queries re-searched in FP64 (exact modes) */
+    int64_t distances;        /* point distances evaluated (the paper's
+                                 "comparisons", Sec. 3.1) */
+    int64_t skipped;          /* queries answered by the moving-query radius */
+    double ms;                /* device time of the call (CUDA events) */
+} dd_search_stats;
+
+/* Nearest data point of each state y_i (Eq. 7):
+ *     idx[i] = argmin_j d_e^2(y_i, (eps_j, sig_j)),  d2[i] = that d_e^2 (Eq. 3,
+ *     without the 1/2 of Eq. 2), evaluated in FP64 from the stored data.
+ * Ties between data points with equal FP64 distance go to the lowest index.
+ *   y       host or device, float64 [m x 12] states (eps, sig).
+ *   m       >= 0 (0 is a no-op).
+ *   idx     host or device, int32 [m] (output).
+ *   d2      host or device, float64 [m] (output), may be NULL.
+ *   stats   host, may be NULL.
+ * All of y, idx, d2 must be of the same kind (all host or all device). */
+dd_status dd_project_nearest(dd_dataset *ds, const double *y, int64_t m,
+                             const dd_search_opts *opts, int32_t *idx,
+                             double *d2, dd_search_stats *stats);
+
+/* ------------------------------------------------------------------------ */
+/* DD solve: z_{i+1} = P_D(P_C(z_i)), Eq. (8)                               */
+/* ------------------------------------------------------------------------ */
+
+/* Box [0,lx]x[0,ly]x[0,lz] of nx*ny*nz trilinear hexahedra, 2x2x2 Gauss
+ * points.  Node (i,j,k) = i + (nx+1)(j + (ny+1)k), dof = 3 node + component;
+ * element (i,j,k) = i + nx(j + ny k); Gauss point g = gx + 2gy + 4gz at
+ * (2g* - 1)/sqrt(3); material point = 8 element + g. */
+typedef struct dd_mesh {
+    int nx, ny, nz;
+    double lx, ly, lz;
+} dd_mesh;
+
+/* Boundary conditions: every dof on z = 0 is clamped; the face z = lz carries
+ * the traction t(x,y) = t0 + tx (x - lx/2) + ty (y - ly/2), integrated into
+ * consistent nodal forces f (2x2 Gauss per face). */
+typedef struct dd_load {
+    double t0[3], tx[3], ty[3];
+} dd_load;
+
+typedef struct dd_solve_opts {
+    int mode;                 /* DD_SEARCH_* used for P_D */
+    int certify;              /* as in dd_search_opts (exact modes) */
+    double f_d0, f_d_final;   /* DD_SEARCH_ANN: f_d ramps linearly from f_d0
+                                 to f_d_final over ramp_iters iterations
+                                 (Sec. 4.5), then stays at f_d_final */
+    int ramp_iters;
+    int max_iter;             /* DD iterations (default 100) */
+    double cg_rtol;           /* CG relative residual (default 1e-12) */
+    int cg_max_iter;          /* CG iterations per solve (default 20000) */
+    uint64_t seed;            /* initial association when init_idx is NULL:
+                                 idx_e = SplitMix64(key(seed, 3), e) mod N */
+    const int32_t *init_idx;  /* host, int32 [n_gp], or NULL */
+    int stall_iters;          /* DD_SEARCH_ANN: stop when the global distance
+                                 has not decreased by more than 1e-12 relative
+                                 for this many iterations (default 3) */
+} dd_solve_opts;
+
+/* Result of a solve: the constraint-set state y = (u, eps, sig) of the last
+ * P_C and the data association idx it was computed from (Sec. 2).  All
+ * arrays are host memory allocated by the library; release with
+ * dd_result_free. */
+typedef struct dd_result {
+    int64_t n_nodes, n_gp;
+    int iters;                /* P_C solves performed */
+    int converged;            /* association unchanged in the last P_D */
+    double *u;                /* [n_nodes x 3] displacement */
+    double *eta;              /* [n_nodes x 3] Lagrange multiplier of Eq. 5b */
+    double *eps;              /* [n_gp x 6] */
+    double *sig;              /* [n_gp x 6] */
+    int32_t *idx;             /* [n_gp] association of the last P_C */
+    double *d2_pc;            /* [iters] global distance Eq. 2 after P_C */
+    double *d2_pd;            /* [iters] global distance Eq. 2 after P_D */
+    int64_t *changed;         /* [iters] associations changed by P_D */
+    int *cg_iters;            /* [iters] CG iterations (max of the two solves) */
+    double search_ms, cg_ms, other_ms;  /* device time per phase, summed */
+    int64_t uncertified;      /* exact modes: FP64 re-searches, summed */
+    int64_t distances;        /* point distances evaluated, summed */
+} dd_result;
+
+/* Solve one DD problem on the data set.  Returns DD_OK when the association
+ * stopped changing (exact modes) or the distance stalled (ANN),
+ * DD_ERR_NOT_CONVERGED when max_iter was reached (result filled), or an
+ * error.  Synchronous. */
+dd_status dd_solve(dd_dataset *ds, const dd_mesh *mesh, const dd_load *load,
+                   const dd_solve_opts *opts, dd_result *out);
+
+void dd_result_free(dd_result *r);
+
+#if defined(__GNUC__)
+#pragma GCC visibility pop
+#endif
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DD_H */

@@ -1,0 +1,244 @@
+"""Thin ctypes binding of libdd (include/dd.h).
+
+Argument marshalling only: every step of the DD path runs in the CUDA
+library.  Functions keep the C names; arrays may be numpy arrays (host memory)
+or torch CUDA tensors (device memory), passed as raw pointers.  There is no
+fallback: if libdd.so is missing or a call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_int, c_int32, c_int64, c_size_t, c_uint64, c_void_p
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdd.so")
+
+DD_OK, DD_ERR_ARG, DD_ERR_NOT_SPD, DD_ERR_OOM, DD_ERR_CUDA, DD_ERR_TIMEOUT, DD_ERR_NOT_CONVERGED, DD_ERR_STATE = range(8)
+STATUS_NAMES = ["DD_OK", "DD_ERR_ARG", "DD_ERR_NOT_SPD", "DD_ERR_OOM", "DD_ERR_CUDA", "DD_ERR_TIMEOUT",
+                "DD_ERR_NOT_CONVERGED", "DD_ERR_STATE"]
+DD_SEARCH_EXACT_FP32, DD_SEARCH_EXACT_TC, DD_SEARCH_ANN = 0, 1, 2
+
+# Entry points declared in include/dd.h (checked by the tests).
+EXPORTS = [
+    "dd_create", "dd_destroy", "dd_last_error", "dd_bytes_in_use", "dd_load_dataset", "dd_free_dataset",
+    "dd_dataset_size", "dd_dataset_bytes", "dd_synth_dataset", "dd_project_nearest", "dd_solve",
+    "dd_result_free",
+]
+
+
+class DDError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+class dd_dataset_opts(ctypes.Structure):
+    _fields_ = [("build_fp16", c_int), ("ann_nlist", c_int), ("ann_train_iters", c_int),
+                ("ann_sample", c_int64), ("seed", c_uint64), ("borrow", c_int)]
+
+
+class dd_search_opts(ctypes.Structure):
+    _fields_ = [("mode", c_int), ("certify", c_int), ("f_d", c_double), ("prev_idx", c_void_p),
+                ("stream", c_void_p)]
+
+
+class dd_search_stats(ctypes.Structure):
+    _fields_ = [("uncertified", c_int64), ("distances", c_int64), ("skipped", c_int64), ("ms", c_double)]
+
+
+class dd_mesh(ctypes.Structure):
+    _fields_ = [("nx", c_int), ("ny", c_int), ("nz", c_int), ("lx", c_double), ("ly", c_double),
+                ("lz", c_double)]
+
+
+class dd_load(ctypes.Structure):
+    _fields_ = [("t0", c_double * 3), ("tx", c_double * 3), ("ty", c_double * 3)]
+
+
+class dd_solve_opts(ctypes.Structure):
+    _fields_ = [("mode", c_int), ("certify", c_int), ("f_d0", c_double), ("f_d_final", c_double),
+                ("ramp_iters", c_int), ("max_iter", c_int), ("cg_rtol", c_double), ("cg_max_iter", c_int),
+                ("seed", c_uint64), ("init_idx", c_void_p), ("stall_iters", c_int)]
+
+
+class dd_result(ctypes.Structure):
+    _fields_ = [("n_nodes", c_int64), ("n_gp", c_int64), ("iters", c_int), ("converged", c_int),
+                ("u", POINTER(c_double)), ("eta", POINTER(c_double)), ("eps", POINTER(c_double)),
+                ("sig", POINTER(c_double)), ("idx", POINTER(c_int32)), ("d2_pc", POINTER(c_double)),
+                ("d2_pd", POINTER(c_double)), ("changed", POINTER(c_int64)), ("cg_iters", POINTER(c_int)),
+                ("search_ms", c_double), ("cg_ms", c_double), ("other_ms", c_double),
+                ("uncertified", c_int64), ("distances", c_int64)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libdd (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libdd.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp = c_void_p
+        L.dd_create.argtypes = [c_int, c_size_t, POINTER(vp)]
+        L.dd_destroy.argtypes = [vp]
+        L.dd_destroy.restype = None
+        L.dd_last_error.argtypes = [vp]
+        L.dd_last_error.restype = c_char_p
+        L.dd_bytes_in_use.argtypes = [vp]
+        L.dd_bytes_in_use.restype = c_size_t
+        L.dd_load_dataset.argtypes = [vp, vp, c_int64, POINTER(c_double), POINTER(dd_dataset_opts), POINTER(vp)]
+        L.dd_free_dataset.argtypes = [vp]
+        L.dd_free_dataset.restype = None
+        L.dd_dataset_size.argtypes = [vp]
+        L.dd_dataset_size.restype = c_int64
+        L.dd_dataset_bytes.argtypes = [vp]
+        L.dd_dataset_bytes.restype = c_size_t
+        L.dd_synth_dataset.argtypes = [vp, c_int, c_double, c_double, c_double, c_double, POINTER(c_double),
+                                       c_uint64, c_int64, c_int64, vp, vp]
+        L.dd_project_nearest.argtypes = [vp, vp, c_int64, POINTER(dd_search_opts), vp, vp,
+                                         POINTER(dd_search_stats)]
+        L.dd_solve.argtypes = [vp, POINTER(dd_mesh), POINTER(dd_load), POINTER(dd_solve_opts), POINTER(dd_result)]
+        L.dd_result_free.argtypes = [POINTER(dd_result)]
+        L.dd_result_free.restype = None
+        for name in EXPORTS:
+            getattr(L, name)
+        _lib = L
+    return _lib
+
+
+def _ptr(a) -> int | None:
+    """Raw pointer of a numpy array or torch tensor (None passes NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"], "array must be C-contiguous"
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous(), "tensor must be contiguous"
+        return a.data_ptr()
+    raise TypeError(type(a))
+
+
+def _check(ctx, st: int):
+    if st != DD_OK:
+        msg = lib().dd_last_error(ctx)
+        raise DDError(st, msg.decode() if msg else "")
+
+
+def _Cmat(C) -> ctypes.Array:
+    C = np.ascontiguousarray(C, dtype=np.float64).reshape(36)
+    return (c_double * 36)(*C.tolist())
+
+
+# ---------------------------------------------------------------------------
+# Same names as the C ABI
+# ---------------------------------------------------------------------------
+def dd_create(device: int = 0, hbm_budget: int = 0):
+    ctx = c_void_p()
+    _check(None, lib().dd_create(device, hbm_budget, ctypes.byref(ctx)))
+    return ctx
+
+
+def dd_destroy(ctx) -> None:
+    lib().dd_destroy(ctx)
+
+
+def dd_last_error(ctx) -> str:
+    m = lib().dd_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def dd_bytes_in_use(ctx) -> int:
+    return int(lib().dd_bytes_in_use(ctx))
+
+
+def dd_load_dataset(ctx, eps_sig, C, build_fp16: bool = False, ann_nlist: int = 0, ann_train_iters: int = 0,
+                    ann_sample: int = 0, seed: int = 0, borrow: bool = False):
+    N = int(eps_sig.shape[0])
+    assert tuple(eps_sig.shape[1:]) == (12,)
+    opts = dd_dataset_opts(int(build_fp16), int(ann_nlist), int(ann_train_iters), int(ann_sample), int(seed),
+                           int(borrow))
+    ds = c_void_p()
+    _check(ctx, lib().dd_load_dataset(ctx, _ptr(eps_sig), N, _Cmat(C), ctypes.byref(opts), ctypes.byref(ds)))
+    return ds
+
+
+def dd_free_dataset(ds) -> None:
+    lib().dd_free_dataset(ds)
+
+
+def dd_dataset_size(ds) -> int:
+    return int(lib().dd_dataset_size(ds))
+
+
+def dd_dataset_bytes(ds) -> int:
+    return int(lib().dd_dataset_bytes(ds))
+
+
+def dd_synth_dataset(ctx, out_dev, law, C, seed: int = 0, start: int = 0, stream=None) -> None:
+    """law: a dd_inputs.DataLaw; out_dev: torch float32 CUDA tensor [N, 12]."""
+    N = int(out_dev.shape[0])
+    _check(ctx, lib().dd_synth_dataset(ctx, law.code, law.eps_lo, law.eps_hi, law.noise_std, law.beta, _Cmat(C),
+                                       int(seed), int(start), N, _ptr(out_dev), stream))
+
+
+def dd_project_nearest(ds, ctx, y, idx, d2=None, mode: int = DD_SEARCH_EXACT_FP32, certify: bool = True,
+                       f_d: float = 0.0, prev_idx=None, stream=None, want_stats: bool = True):
+    m = int(y.shape[0])
+    opts = dd_search_opts(int(mode), int(certify), float(f_d), _ptr(prev_idx), stream)
+    st = dd_search_stats()
+    _check(ctx, lib().dd_project_nearest(ds, _ptr(y), m, ctypes.byref(opts), _ptr(idx), _ptr(d2),
+                                         ctypes.byref(st) if want_stats else None))
+    return st
+
+
+class Result:
+    """Host copy of a dd_result."""
+
+    def __init__(self, r: dd_result):
+        nn, ng, it = r.n_nodes, r.n_gp, r.iters
+        arr = np.ctypeslib.as_array
+        self.n_nodes, self.n_gp, self.iters, self.converged = nn, ng, it, bool(r.converged)
+        self.u = arr(r.u, shape=(nn * 3,)).copy()
+        self.eta = arr(r.eta, shape=(nn * 3,)).copy()
+        self.eps = arr(r.eps, shape=(ng, 6)).copy()
+        self.sig = arr(r.sig, shape=(ng, 6)).copy()
+        self.idx = arr(r.idx, shape=(ng,)).copy()
+        self.d2_pc = arr(r.d2_pc, shape=(max(it, 1),))[:it].copy()
+        self.d2_pd = arr(r.d2_pd, shape=(max(it, 1),))[:it].copy()
+        self.changed = arr(r.changed, shape=(max(it, 1),))[:it].copy()
+        self.cg_iters = arr(r.cg_iters, shape=(max(it, 1),))[:it].copy()
+        self.search_ms, self.cg_ms, self.other_ms = r.search_ms, r.cg_ms, r.other_ms
+        self.uncertified, self.distances = r.uncertified, r.distances
+
+
+def dd_solve(ds, ctx, n_el, load, mode: int = DD_SEARCH_EXACT_FP32, init_idx=None, max_iter: int = 100,
+             cg_rtol: float = 1e-12, cg_max_iter: int = 20000, certify: bool = True, f_d0: float = 0.0,
+             f_d_final: float = 0.0, ramp_iters: int = 20, seed: int = 0, stall_iters: int = 3,
+             lengths=(1.0, 1.0, 1.0), allow_not_converged: bool = True):
+    """Solve one cube problem; `load` is a dd_inputs.Load.  Returns a Result."""
+    nx, ny, nz = (n_el, n_el, n_el) if np.isscalar(n_el) else n_el
+    mesh = dd_mesh(nx, ny, nz, *lengths)
+    L = dd_load((c_double * 3)(*load.t0), (c_double * 3)(*load.tx), (c_double * 3)(*load.ty))
+    ii = None if init_idx is None else np.ascontiguousarray(init_idx, dtype=np.int32)
+    opts = dd_solve_opts(int(mode), int(certify), float(f_d0), float(f_d_final), int(ramp_iters), int(max_iter),
+                         float(cg_rtol), int(cg_max_iter), int(seed), _ptr(ii), int(stall_iters))
+    r = dd_result()
+    st = lib().dd_solve(ds, ctypes.byref(mesh), ctypes.byref(L), ctypes.byref(opts), ctypes.byref(r))
+    try:
+        if st != DD_OK and not (allow_not_converged and st == DD_ERR_NOT_CONVERGED):
+            _check(ctx, st)
+        return Result(r)
+    finally:
+        lib().dd_result_free(ctypes.byref(r))
+
+
+def dd_result_free(r: dd_result) -> None:
+    """Release the library-allocated arrays of a raw dd_result (dd_solve's
+    wrapper above already copies and frees them)."""
+    lib().dd_result_free(ctypes.byref(r))

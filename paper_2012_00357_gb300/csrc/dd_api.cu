@@ -1,0 +1,534 @@
+// C ABI of libdd: context, data set, data projection P_D and the DD solve.
+//
+// The DD iteration z_{i+1} = P_D(P_C(z_i)) (Sec. 2, Eq. 8) runs device
+// resident: per iteration the host issues the kernels of P_C (fem.cu) and
+// P_D (search_*.cu, ann.cu) on one stream and reads back three scalars (the
+// number of changed associations and the global distance Eq. 2 after P_C and
+// after P_D) for the stop test of Sec. 2.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "dd_internal.cuh"
+#include "fem.cuh"
+
+static thread_local std::string g_create_err;
+
+dd_status dd_fail(dd_ctx *ctx, dd_status st, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    else g_create_err = msg;
+    return st;
+}
+
+dd_status dd_alloc(dd_ctx *ctx, void **p, size_t bytes, const char *what) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 256;
+    if (ctx->budget && ctx->in_use + bytes > ctx->budget)
+        return dd_fail(ctx, DD_ERR_OOM, std::string("HBM budget exceeded allocating ") + what);
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return dd_fail(ctx, DD_ERR_OOM, std::string("cudaMalloc failed for ") + what + ": " + cudaGetErrorString(e));
+    }
+    ctx->in_use += bytes;
+    return DD_OK;
+}
+
+void dd_free(dd_ctx *ctx, void *p, size_t bytes) {
+    if (!p) return;
+    cudaFree(p);
+    if (bytes == 0) bytes = 256;
+    ctx->in_use -= std::min(ctx->in_use, bytes);
+}
+
+dd_status dd_workspace(dd_ctx *ctx, int slot, size_t bytes, void **out) {
+    Workspace &w = ctx->ws[slot];
+    if (w.bytes >= bytes && w.ptr) {
+        *out = w.ptr;
+        return DD_OK;
+    }
+    if (w.ptr) {
+        DD_TRY_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        DD_TRY_CUDA(ctx, cudaDeviceSynchronize());
+        dd_free(ctx, w.ptr, w.bytes);
+        w.ptr = nullptr;
+        w.bytes = 0;
+    }
+    size_t nb = std::max<size_t>(bytes + bytes / 4, 4096);
+    DD_TRY(dd_alloc(ctx, &w.ptr, nb, "workspace"));
+    w.bytes = nb;
+    *out = w.ptr;
+    return DD_OK;
+}
+
+dd_status dd_check_device_error(dd_ctx *ctx, cudaStream_t s, const char *where) {
+    unsigned h = 0;
+    DD_TRY_CUDA(ctx, cudaMemcpyAsync(&h, ctx->dev_err, sizeof(h), cudaMemcpyDeviceToHost, s));
+    DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+    if (h == 0) return DD_OK;
+    DD_TRY_CUDA(ctx, cudaMemsetAsync(ctx->dev_err, 0, sizeof(unsigned), s));
+    DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+    if (h & DEV_ERR_TIMEOUT) return dd_fail(ctx, DD_ERR_TIMEOUT, std::string(where) + ": device wait timed out");
+    return dd_fail(ctx, DD_ERR_ARG, std::string(where) + ": index out of range");
+}
+
+bool dd_is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+dd_status dd_transform_dataset(dd_dataset *ds);
+dd_status dd_init_association(dd_ctx *ctx, uint64_t seed, int64_t n, int64_t N, int32_t *idx, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+extern "C" dd_status dd_create(int device, size_t hbm_budget, dd_ctx **out) {
+    if (!out) return dd_fail(nullptr, DD_ERR_ARG, "dd_create: out is NULL");
+    *out = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        return dd_fail(nullptr, DD_ERR_CUDA, "no CUDA device available");
+    }
+    if (device < 0 || device >= n) return dd_fail(nullptr, DD_ERR_ARG, "dd_create: device out of range");
+    dd_ctx *ctx = new dd_ctx();
+    ctx->device = device;
+    ctx->budget = hbm_budget;
+    auto bail = [&](const char *what, cudaError_t err) {
+        g_create_err = std::string(what) + ": " + cudaGetErrorString(err);
+        cudaGetLastError();
+        if (ctx->dev_err) cudaFree(ctx->dev_err);
+        if (ctx->stream) cudaStreamDestroy(ctx->stream);
+        delete ctx;
+        return DD_ERR_CUDA;
+    };
+    if ((e = cudaSetDevice(device)) != cudaSuccess) return bail("cudaSetDevice", e);
+    if ((e = cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess)
+        return bail("cudaDeviceGetAttribute", e);
+    if ((e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail("cudaStreamCreate", e);
+    if ((e = cudaMalloc((void **)&ctx->dev_err, 256)) != cudaSuccess) return bail("cudaMalloc", e);
+    if ((e = cudaMemset(ctx->dev_err, 0, 256)) != cudaSuccess) return bail("cudaMemset", e);
+    ctx->in_use = 256;
+    *out = ctx;
+    return DD_OK;
+}
+
+extern "C" void dd_destroy(dd_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto &w : ctx->ws)
+        if (w.ptr) cudaFree(w.ptr);
+    cudaFree(ctx->dev_err);
+    cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+extern "C" const char *dd_last_error(const dd_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
+
+extern "C" size_t dd_bytes_in_use(const dd_ctx *ctx) { return ctx ? ctx->in_use : 0; }
+
+// ---------------------------------------------------------------------------
+// Data set
+// ---------------------------------------------------------------------------
+extern "C" dd_status dd_load_dataset(dd_ctx *ctx, const float *eps_sig, int64_t N, const double *C,
+                                     const dd_dataset_opts *opts, dd_dataset **out) {
+    if (!ctx) return DD_ERR_ARG;
+    if (!out || !eps_sig || !C) return dd_fail(ctx, DD_ERR_ARG, "dd_load_dataset: NULL argument");
+    *out = nullptr;
+    if (N < 1 || N > INT32_MAX) return dd_fail(ctx, DD_ERR_ARG, "dd_load_dataset: N out of range");
+    dd_dataset_opts o;
+    std::memset(&o, 0, sizeof(o));
+    if (opts) o = *opts;
+    if (o.ann_nlist < 0 || o.ann_nlist > N) return dd_fail(ctx, DD_ERR_ARG, "dd_load_dataset: ann_nlist out of range");
+    DD_TRY_CUDA(ctx, cudaSetDevice(ctx->device));
+    dd_dataset *ds = new dd_dataset();
+    ds->ctx = ctx;
+    if (!dd_metric_maps(C, &ds->M)) {
+        delete ds;
+        return dd_fail(ctx, DD_ERR_NOT_SPD, "metric C is not symmetric positive definite");
+    }
+    ds->N = N;
+    ds->N_pad = (N + kDataTile - 1) / kDataTile * kDataTile;
+    const bool dev = dd_is_device_ptr(eps_sig);
+    dd_status st = DD_OK;
+    auto fail = [&](dd_status s2) {
+        dd_free_dataset(ds);
+        return s2;
+    };
+    if (dev && o.borrow) {
+        ds->raw = eps_sig;
+        ds->owns_raw = false;
+    } else {
+        void *p = nullptr;
+        if ((st = dd_alloc(ctx, &p, (size_t)N * 48, "data set")) != DD_OK) return fail(st);
+        ds->raw = (const float *)p;
+        ds->bytes += (size_t)N * 48;
+        cudaError_t e = cudaMemcpyAsync(p, eps_sig, (size_t)N * 48, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                        ctx->stream);
+        if (e != cudaSuccess) return fail(dd_fail(ctx, DD_ERR_CUDA, std::string("copy data set: ") + cudaGetErrorString(e)));
+    }
+    void *p = nullptr;
+    if ((st = dd_alloc(ctx, &p, (size_t)ds->N_pad * 48, "mapped data")) != DD_OK) return fail(st);
+    ds->z32 = (float *)p;
+    if ((st = dd_alloc(ctx, &p, (size_t)ds->N_pad * 4, "norms")) != DD_OK) return fail(st);
+    ds->zn = (float *)p;
+    ds->bytes += (size_t)ds->N_pad * 52;
+    if ((st = dd_transform_dataset(ds)) != DD_OK) return fail(st);
+    if (o.build_fp16 && (st = dd_build_fp16(ds)) != DD_OK) return fail(st);
+    if (o.ann_nlist > 0 && (st = dd_build_ann(ds, o)) != DD_OK) return fail(st);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return fail(dd_fail(ctx, DD_ERR_CUDA, cudaGetErrorString(e)));
+    *out = ds;
+    return DD_OK;
+}
+
+extern "C" void dd_free_dataset(dd_dataset *ds) {
+    if (!ds) return;
+    dd_ctx *ctx = ds->ctx;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    if (ds->owns_raw) dd_free(ctx, (void *)ds->raw, (size_t)ds->N * 48);
+    dd_free(ctx, ds->z32, (size_t)ds->N_pad * 48);
+    dd_free(ctx, ds->zn, (size_t)ds->N_pad * 4);
+    if (ds->z16) dd_free(ctx, ds->z16, (size_t)ds->N_pad * 32);
+    dd_free_ann(ds);
+    delete ds;
+}
+
+extern "C" int64_t dd_dataset_size(const dd_dataset *ds) { return ds ? ds->N : 0; }
+
+extern "C" size_t dd_dataset_bytes(const dd_dataset *ds) { return ds ? ds->bytes : 0; }
+
+// ---------------------------------------------------------------------------
+// P_D
+// ---------------------------------------------------------------------------
+static dd_status run_search(dd_dataset *ds, int mode, int certify, double f_d, const int32_t *prev_dev,
+                            const double *y_dev, int64_t m, SearchOut out, dd_search_stats *st, cudaStream_t s) {
+    switch (mode) {
+    case DD_SEARCH_EXACT_FP32:
+        return dd_search_exact_fp32(ds, y_dev, m, certify, out, st, s);
+    case DD_SEARCH_EXACT_TC:
+        if (!ds->z16) return dd_fail(ds->ctx, DD_ERR_STATE, "tensor-core search needs the FP16 copy (build_fp16)");
+        return dd_search_exact_tc(ds, y_dev, m, certify, out, st, s);
+    case DD_SEARCH_ANN:
+        if (!ds->ann.nlist) return dd_fail(ds->ctx, DD_ERR_STATE, "ANN search needs the partition (ann_nlist)");
+        return dd_search_ann(ds, y_dev, m, f_d, prev_dev, out, st, s);
+    default:
+        return dd_fail(ds->ctx, DD_ERR_ARG, "unknown search mode");
+    }
+}
+
+extern "C" dd_status dd_project_nearest(dd_dataset *ds, const double *y, int64_t m, const dd_search_opts *opts,
+                                        int32_t *idx, double *d2, dd_search_stats *stats) {
+    if (!ds) return DD_ERR_ARG;
+    dd_ctx *ctx = ds->ctx;
+    if (m < 0) return dd_fail(ctx, DD_ERR_ARG, "dd_project_nearest: m < 0");
+    if (m == 0) return DD_OK;
+    if (!y || !idx) return dd_fail(ctx, DD_ERR_ARG, "dd_project_nearest: NULL argument");
+    dd_search_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.certify = 1;
+    if (opts) o = *opts;
+    if (o.mode == DD_SEARCH_ANN && !(o.f_d >= 0.0 && o.f_d <= 1.0))
+        return dd_fail(ctx, DD_ERR_ARG, "dd_project_nearest: f_d outside [0, 1]");
+    DD_TRY_CUDA(ctx, cudaSetDevice(ctx->device));
+    const bool dev = dd_is_device_ptr(y);
+    if (dd_is_device_ptr(idx) != dev || (d2 && dd_is_device_ptr(d2) != dev))
+        return dd_fail(ctx, DD_ERR_ARG, "dd_project_nearest: y, idx and d2 must all be host or all device memory");
+    cudaStream_t s = o.stream ? (cudaStream_t)o.stream : ctx->stream;
+    const double *y_dev = y;
+    int32_t *idx_dev = idx;
+    double *d2_dev = d2;
+    const int32_t *prev_dev = o.prev_idx;
+    if (!dev) {
+        size_t by = (size_t)m * 96, bi = ((size_t)m * 4 + 255) / 256 * 256, bd = (size_t)m * 8;
+        void *w = nullptr;
+        DD_TRY(dd_workspace(ctx, WS_QUERY, by + 2 * bi + bd, &w));
+        char *c = (char *)w;
+        y_dev = (const double *)c;
+        idx_dev = (int32_t *)(c + by);
+        d2_dev = (double *)(c + by + bi);
+        int32_t *prev_tmp = (int32_t *)(c + by + bi + bd);
+        DD_TRY_CUDA(ctx, cudaMemcpyAsync((void *)y_dev, y, by, cudaMemcpyHostToDevice, s));
+        if (o.prev_idx) {
+            DD_TRY_CUDA(ctx, cudaMemcpyAsync(prev_tmp, o.prev_idx, (size_t)m * 4, cudaMemcpyHostToDevice, s));
+            prev_dev = prev_tmp;
+        }
+    } else if (o.prev_idx && !dd_is_device_ptr(o.prev_idx)) {
+        return dd_fail(ctx, DD_ERR_ARG, "dd_project_nearest: prev_idx must be device memory with device y");
+    }
+    dd_search_stats local;
+    std::memset(&local, 0, sizeof(local));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (stats) {
+        DD_TRY_CUDA(ctx, cudaEventCreate(&e0));
+        DD_TRY_CUDA(ctx, cudaEventCreate(&e1));
+        DD_TRY_CUDA(ctx, cudaEventRecord(e0, s));
+    }
+    SearchOut out{idx_dev, d2_dev, nullptr};
+    dd_status st = run_search(ds, o.mode, o.certify, o.f_d, prev_dev, y_dev, m, out, stats ? &local : nullptr, s);
+    if (st != DD_OK) return st;
+    if (stats) {
+        DD_TRY_CUDA(ctx, cudaEventRecord(e1, s));
+        DD_TRY_CUDA(ctx, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        local.ms = ms;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        *stats = local;
+    }
+    if (!dev) {
+        DD_TRY_CUDA(ctx, cudaMemcpyAsync(idx, idx_dev, (size_t)m * 4, cudaMemcpyDeviceToHost, s));
+        if (d2) DD_TRY_CUDA(ctx, cudaMemcpyAsync(d2, d2_dev, (size_t)m * 8, cudaMemcpyDeviceToHost, s));
+        DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+    }
+    if (!dev || stats) DD_TRY(dd_check_device_error(ctx, s, "dd_project_nearest"));
+    return DD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// DD solve
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Bump {
+    char *base;
+    size_t off = 0;
+    template <class T>
+    T *take(size_t n) {
+        T *p = (T *)(base + off);
+        off += (n * sizeof(T) + 255) / 256 * 256;
+        return p;
+    }
+};
+
+size_t solve_bytes(const MeshDev &g, int n_sm) {
+    size_t nn = (size_t)g.n_nodes, ng = (size_t)g.n_gp;
+    auto r = [](size_t b) { return (b + 255) / 256 * 256; };
+    return r(576 * 8) + r(nn * 3 * 8) + 7 * r(nn * 6 * 8) + r(nn * 9 * 8) + r((size_t)2 * n_sm * 32 * 8 * 8) + r(64) +
+           r(64) + r(64) + r(ng * 12 * 8) + r(ng * 6 * 8) + r(ng * 12 * 8) + 3 * r(ng * 8) + 2 * r(ng * 4) + r(64);
+}
+
+}  // namespace
+
+static void dd_solve_defaults(dd_solve_opts *o) {
+    std::memset(o, 0, sizeof(*o));
+    o->mode = DD_SEARCH_EXACT_FP32;
+    o->certify = 1;
+    o->ramp_iters = 20;
+    o->max_iter = 100;
+    o->cg_rtol = 1e-12;
+    o->cg_max_iter = 20000;
+    o->stall_iters = 3;
+}
+
+extern "C" dd_status dd_solve(dd_dataset *ds, const dd_mesh *mesh, const dd_load *load, const dd_solve_opts *opts,
+                              dd_result *out) {
+    if (!ds) return DD_ERR_ARG;
+    dd_ctx *ctx = ds->ctx;
+    if (!mesh || !load || !out) return dd_fail(ctx, DD_ERR_ARG, "dd_solve: NULL argument");
+    std::memset(out, 0, sizeof(*out));
+    if (mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1 || !(mesh->lx > 0) || !(mesh->ly > 0) || !(mesh->lz > 0))
+        return dd_fail(ctx, DD_ERR_ARG, "dd_solve: bad mesh");
+    if ((int64_t)mesh->nx * mesh->ny * mesh->nz * 8 > INT32_MAX) return dd_fail(ctx, DD_ERR_ARG, "dd_solve: mesh too large");
+    dd_solve_opts o;
+    dd_solve_defaults(&o);
+    if (opts) {
+        o = *opts;
+        if (o.max_iter <= 0) o.max_iter = 100;
+        if (!(o.cg_rtol > 0)) o.cg_rtol = 1e-12;
+        if (o.cg_max_iter <= 0) o.cg_max_iter = 20000;
+        if (o.ramp_iters < 0) o.ramp_iters = 0;
+        if (o.stall_iters <= 0) o.stall_iters = 3;
+    }
+    if (o.mode < 0 || o.mode > 2) return dd_fail(ctx, DD_ERR_ARG, "dd_solve: unknown mode");
+    for (int c = 0; c < 3; ++c)
+        if (!std::isfinite(load->t0[c]) || !std::isfinite(load->tx[c]) || !std::isfinite(load->ty[c]))
+            return dd_fail(ctx, DD_ERR_ARG, "dd_solve: non-finite load");
+    DD_TRY_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t s = ctx->stream;
+    const MeshDev g = fem_mesh(*mesh);
+    ElemOps ops;
+    fem_elem_ops(g, &ops);
+    std::vector<double> Ke(576), f((size_t)g.n_nodes * 3);
+    fem_element_stiffness(g, ops, ds->M.C, Ke.data());
+    fem_traction_force(g, *load, mesh->lx, mesh->ly, f.data());
+
+    void *w = nullptr;
+    DD_TRY(dd_workspace(ctx, WS_SOLVE, solve_bytes(g, ctx->n_sm), &w));
+    Bump bp{(char *)w};
+    const size_t nn = g.n_nodes, ng = g.n_gp;
+    double *dKe = bp.take<double>(576), *df = bp.take<double>(nn * 3);
+    CGBuffers cb;
+    double *b = bp.take<double>(nn * 6), *x = bp.take<double>(nn * 6);
+    cb.b = b;
+    cb.x = x;
+    cb.r = bp.take<double>(nn * 6);
+    cb.z = bp.take<double>(nn * 6);
+    cb.p0 = bp.take<double>(nn * 6);
+    cb.p1 = bp.take<double>(nn * 6);
+    cb.q = bp.take<double>(nn * 6);
+    double *Minv = bp.take<double>(nn * 9);
+    cb.Minv = Minv;
+    cb.Ke = dKe;
+    cb.part = bp.take<double>((size_t)2 * ctx->n_sm * 32 * 8);
+    cb.bar = bp.take<unsigned>(16);
+    cb.it_out = bp.take<int>(16);
+    cb.res_out = bp.take<double>(8);
+    double *star = bp.take<double>(ng * 12), *ce = bp.take<double>(ng * 6), *y = bp.take<double>(ng * 12);
+    double *dpc = bp.take<double>(ng), *d2 = bp.take<double>(ng), *d2nd = bp.take<double>(ng);
+    int32_t *idx_a = bp.take<int32_t>(ng), *idx_b = bp.take<int32_t>(ng);
+    double *stats = bp.take<double>(8);
+
+    DD_TRY_CUDA(ctx, cudaMemcpyAsync(dKe, Ke.data(), 576 * 8, cudaMemcpyHostToDevice, s));
+    DD_TRY_CUDA(ctx, cudaMemcpyAsync(df, f.data(), nn * 3 * 8, cudaMemcpyHostToDevice, s));
+    DD_TRY_CUDA(ctx, cudaMemsetAsync(x, 0, nn * 6 * 8, s));
+    DD_TRY(fem_block_jacobi(ctx, g, dKe, Minv, s));
+    if (o.init_idx) {
+        DD_TRY_CUDA(ctx, cudaMemcpyAsync(idx_a, o.init_idx, ng * 4, dd_is_device_ptr(o.init_idx) ? cudaMemcpyDeviceToDevice
+                                                                                                   : cudaMemcpyHostToDevice,
+                                         s));
+    } else {
+        DD_TRY(dd_init_association(ctx, o.seed, ng, ds->N, idx_a, s));
+    }
+
+    std::vector<double> h_pc, h_pd;
+    std::vector<int64_t> h_ch;
+    std::vector<int> h_cg;
+    cudaEvent_t ev[4];
+    for (auto &e : ev) DD_TRY_CUDA(ctx, cudaEventCreate(&e));
+    int32_t *cur = idx_a, *nxt = idx_b;
+    bool converged = false;
+    int stall = 0;
+    double best_pd = INFINITY;
+    dd_search_stats sst;
+    std::memset(&sst, 0, sizeof(sst));
+    dd_status result = DD_OK;
+    int it = 0;
+    for (it = 1; it <= o.max_iter; ++it) {
+        DD_TRY_CUDA(ctx, cudaEventRecord(ev[0], s));
+        DD_TRY(fem_gather_star(ds, cur, ng, star, ce, s));
+        DD_TRY(fem_assemble_rhs(ctx, g, ops, star, ce, df, b, s));
+        DD_TRY(fem_cg(ctx, g, cb, o.cg_rtol, o.cg_max_iter, s));
+        DD_TRY_CUDA(ctx, cudaEventRecord(ev[1], s));
+        DD_TRY(fem_recover(ds, g, ops, x, star, y, dpc, s));
+        DD_TRY_CUDA(ctx, cudaEventRecord(ev[2], s));
+        double f_d = o.f_d_final;
+        if (o.mode == DD_SEARCH_ANN && o.ramp_iters > 0)
+            f_d = o.f_d0 + (o.f_d_final - o.f_d0) * std::min(1.0, (double)(it - 1) / (double)o.ramp_iters);
+        SearchOut so{nxt, d2, d2nd};
+        DD_TRY(run_search(ds, o.mode, o.certify, f_d, cur, y, ng, so, &sst, s));
+        DD_TRY_CUDA(ctx, cudaEventRecord(ev[3], s));
+        DD_TRY(fem_iter_stats(ctx, nxt, cur, d2, dpc, ng, g.w, stats, s));
+        double hs[3];
+        int cg_it = 0;
+        DD_TRY_CUDA(ctx, cudaMemcpyAsync(hs, stats, sizeof(hs), cudaMemcpyDeviceToHost, s));
+        DD_TRY_CUDA(ctx, cudaMemcpyAsync(&cg_it, cb.it_out, sizeof(int), cudaMemcpyDeviceToHost, s));
+        DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+        DD_TRY(dd_check_device_error(ctx, s, "dd_solve"));
+        float t01 = 0, t12 = 0, t23 = 0;
+        cudaEventElapsedTime(&t01, ev[0], ev[1]);
+        cudaEventElapsedTime(&t12, ev[1], ev[2]);
+        cudaEventElapsedTime(&t23, ev[2], ev[3]);
+        out->cg_ms += t01;
+        out->other_ms += t12;
+        out->search_ms += t23;
+        h_pc.push_back(hs[2]);
+        h_pd.push_back(hs[1]);
+        h_ch.push_back((int64_t)hs[0]);
+        h_cg.push_back(cg_it);
+        if (hs[0] == 0.0) {
+            converged = true;
+            break;
+        }
+        if (o.mode == DD_SEARCH_ANN) {
+            if (hs[1] < best_pd * (1.0 - 1e-12)) {
+                best_pd = hs[1];
+                stall = 0;
+            } else if (++stall >= o.stall_iters) {
+                converged = true;
+                // keep the association the constraint state was computed from
+                break;
+            }
+        }
+        std::swap(cur, nxt);
+    }
+    if (it > o.max_iter) {
+        it = o.max_iter;
+        result = DD_ERR_NOT_CONVERGED;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+
+    // results
+    out->n_nodes = g.n_nodes;
+    out->n_gp = g.n_gp;
+    out->iters = (int)h_pc.size();
+    out->converged = converged ? 1 : 0;
+    out->u = (double *)std::malloc(nn * 3 * 8);
+    out->eta = (double *)std::malloc(nn * 3 * 8);
+    out->eps = (double *)std::malloc(ng * 6 * 8);
+    out->sig = (double *)std::malloc(ng * 6 * 8);
+    out->idx = (int32_t *)std::malloc(ng * 4);
+    size_t ni = h_pc.size() ? h_pc.size() : 1;
+    out->d2_pc = (double *)std::malloc(ni * 8);
+    out->d2_pd = (double *)std::malloc(ni * 8);
+    out->changed = (int64_t *)std::malloc(ni * 8);
+    out->cg_iters = (int *)std::malloc(ni * sizeof(int));
+    if (!out->u || !out->eta || !out->eps || !out->sig || !out->idx || !out->d2_pc || !out->d2_pd || !out->changed ||
+        !out->cg_iters) {
+        dd_result_free(out);
+        return dd_fail(ctx, DD_ERR_OOM, "dd_solve: host allocation failed");
+    }
+    std::vector<double> hx(nn * 6), hy(ng * 12);
+    DD_TRY_CUDA(ctx, cudaMemcpyAsync(hx.data(), x, nn * 6 * 8, cudaMemcpyDeviceToHost, s));
+    DD_TRY_CUDA(ctx, cudaMemcpyAsync(hy.data(), y, ng * 12 * 8, cudaMemcpyDeviceToHost, s));
+    DD_TRY_CUDA(ctx, cudaMemcpyAsync(out->idx, cur, ng * 4, cudaMemcpyDeviceToHost, s));
+    DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+    for (size_t a = 0; a < nn; ++a)
+        for (int c = 0; c < 3; ++c) {
+            out->u[a * 3 + c] = hx[a * 6 + c];
+            out->eta[a * 3 + c] = hx[a * 6 + 3 + c];
+        }
+    for (size_t e = 0; e < ng; ++e)
+        for (int c = 0; c < 6; ++c) {
+            out->eps[e * 6 + c] = hy[e * 12 + c];
+            out->sig[e * 6 + c] = hy[e * 12 + 6 + c];
+        }
+    for (size_t i = 0; i < h_pc.size(); ++i) {
+        out->d2_pc[i] = h_pc[i];
+        out->d2_pd[i] = h_pd[i];
+        out->changed[i] = h_ch[i];
+        out->cg_iters[i] = h_cg[i];
+    }
+    out->uncertified = sst.uncertified;
+    out->distances = sst.distances;
+    return result;
+}
+
+extern "C" void dd_result_free(dd_result *r) {
+    if (!r) return;
+    std::free(r->u);
+    std::free(r->eta);
+    std::free(r->eps);
+    std::free(r->sig);
+    std::free(r->idx);
+    std::free(r->d2_pc);
+    std::free(r->d2_pd);
+    std::free(r->changed);
+    std::free(r->cg_iters);
+    std::memset(r, 0, sizeof(*r));
+}

@@ -1,0 +1,241 @@
+// Internal declarations shared by the translation units of libdd.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/dd.h"
+
+// ---------------------------------------------------------------------------
+// Error plumbing
+// ---------------------------------------------------------------------------
+struct DDError {
+    dd_status st;
+    std::string msg;
+};
+
+#define DD_TRY_CUDA(ctx, call)                                                      \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess) {                                                    \
+            return dd_fail((ctx), DD_ERR_CUDA, std::string(#call) + ": " +          \
+                                                   cudaGetErrorString(e_));         \
+        }                                                                           \
+    } while (0)
+
+#define DD_TRY(x)                                                                   \
+    do {                                                                            \
+        dd_status s_ = (x);                                                         \
+        if (s_ != DD_OK) return s_;                                                 \
+    } while (0)
+
+// Device error word bits (written by kernels, read by the host after a call).
+enum : unsigned {
+    DEV_ERR_TIMEOUT = 1u,      // a bounded wait expired
+    DEV_ERR_BOUNDS = 2u,       // an index failed its bounds check
+};
+
+// Wall-clock limit of every device-side spin wait.
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // 2 s
+
+__device__ __forceinline__ unsigned long long dd_globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ---------------------------------------------------------------------------
+// Metric maps of a data set: C, C^{-1}, C^{1/2}, C^{-1/2}, the centre of the
+// stored coordinates.  Passed to kernels by value.
+// ---------------------------------------------------------------------------
+struct MetricMaps {
+    double C[36];
+    double Cinv[36];
+    double Ch[36];
+    double Cmh[36];
+    double mu[12];
+};
+
+// ---------------------------------------------------------------------------
+// Context and data set
+// ---------------------------------------------------------------------------
+struct Workspace {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+struct dd_ctx {
+    int device = 0;
+    int n_sm = 0;
+    size_t budget = 0;
+    size_t in_use = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    unsigned *dev_err = nullptr;        // device error word
+    // grow-only scratch buffers keyed by purpose
+    Workspace ws[8];
+};
+
+enum WsSlot { WS_SEARCH = 0, WS_QUERY = 1, WS_MISC = 2, WS_SOLVE = 3, WS_TC = 4, WS_ANN = 5 };
+
+struct AnnIndex {
+    int nlist = 0;
+    float *cent = nullptr;      // [nlist x 12] centroids (centred mapped coordinates)
+    float *radius = nullptr;    // [nlist] max distance centroid -> member
+    int64_t *offs = nullptr;    // [nlist + 1] cluster ranges in the sorted order
+    int32_t *perm = nullptr;    // [N] original index of sorted position
+    int32_t *cluster_of = nullptr; // [N] cluster of each original point
+    float *zs = nullptr;        // [N x 12] mapped coordinates in sorted order
+};
+
+struct dd_dataset {
+    dd_ctx *ctx = nullptr;
+    int64_t N = 0, N_pad = 0;
+    const float *raw = nullptr;  // [N x 12] (eps, sig) as loaded
+    bool owns_raw = true;
+    float *z32 = nullptr;        // [N_pad x 12] centred mapped coordinates, FP32
+    float *zn = nullptr;         // [N_pad] |z32|^2 (padding: huge)
+    double R = 0.0;              // max_j |z32_j|
+    double maxabs = 0.0;         // max_j,k |z32_jk|
+    MetricMaps M;
+    // tensor-core operand copy
+    __half *z16 = nullptr;       // UMMA canonical layout, see search_tc.cu
+    double scale16 = 0.0;        // power-of-two scale of the FP16 copy
+    double R16 = 0.0;            // max_j |z16_j| (scaled units)
+    AnnIndex ann;
+    size_t bytes = 0;
+};
+
+dd_status dd_fail(dd_ctx *ctx, dd_status st, const std::string &msg);
+dd_status dd_alloc(dd_ctx *ctx, void **p, size_t bytes, const char *what);
+void dd_free(dd_ctx *ctx, void *p, size_t bytes);
+dd_status dd_workspace(dd_ctx *ctx, int slot, size_t bytes, void **out);
+dd_status dd_check_device_error(dd_ctx *ctx, cudaStream_t s, const char *where);
+bool dd_is_device_ptr(const void *p);
+
+// Host linear algebra (host_linalg.cu)
+bool dd_metric_maps(const double *C, MetricMaps *M);   // false: not SPD
+
+// Padding granule of the data arrays (points).
+constexpr int64_t kDataTile = 256;
+
+// ---------------------------------------------------------------------------
+// Search (search_fp32.cu / search_tc.cu / ann.cu)
+// ---------------------------------------------------------------------------
+// Per-query record consumed by the low-precision scans.
+struct QueryRec {
+    float q[12];      // centred mapped coordinates, FP32
+    float w2;         // candidate window (twice the score error bound)
+    float qn;         // |q|^2
+    float pad[2];
+};
+
+struct SearchOut {
+    int32_t *idx;     // [m]
+    double *d2;       // [m] Eq. (3) distance, may be null
+    double *d2nd;     // [m] second-best distance lower bound, may be null
+};
+
+dd_status dd_map_queries(dd_dataset *ds, const double *y_dev, int64_t m, double *zq64,
+                         QueryRec *rec, cudaStream_t s);
+dd_status dd_search_exact_fp32(dd_dataset *ds, const double *y_dev, int64_t m, int certify,
+                               SearchOut out, dd_search_stats *st, cudaStream_t s);
+dd_status dd_search_exact_tc(dd_dataset *ds, const double *y_dev, int64_t m, int certify,
+                             SearchOut out, dd_search_stats *st, cudaStream_t s);
+dd_status dd_build_fp16(dd_dataset *ds);
+dd_status dd_search_ann(dd_dataset *ds, const double *y_dev, int64_t m, double f_d,
+                        const int32_t *prev_idx_dev, SearchOut out, dd_search_stats *st,
+                        cudaStream_t s);
+dd_status dd_build_ann(dd_dataset *ds, const dd_dataset_opts &o);
+void dd_free_ann(dd_dataset *ds);
+
+// Shared by the exact scans: merge split candidates, rescore in FP64 and
+// re-search uncertified queries.  Candidate layout described in search_fp32.cu.
+struct CandHeader {
+    float mrun;       // smallest score seen in the split
+    float dropped;    // smallest score that did not fit in the buffer (+inf: none)
+    int cnt;          // valid entries
+    int pad;
+};
+dd_status dd_merge_rescore(dd_dataset *ds, const double *y_dev, int64_t m, int splits, int cap,
+                           const CandHeader *hdr, const float2 *cand, const QueryRec *rec,
+                           int certify, SearchOut out, dd_search_stats *st, cudaStream_t s);
+
+// Eq. (3) in FP64 between a state y (eps, sig) and data point j (raw FP32).
+__device__ __forceinline__ double dd_eq3(const MetricMaps &M, const double *y, const float *row) {
+    double de[6], ds[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        de[k] = y[k] - (double)row[k];
+        ds[k] = y[6 + k] - (double)row[6 + k];
+    }
+    double a = 0.0, b = 0.0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        double ce = 0.0, cs = 0.0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            ce += M.C[6 * i + k] * de[k];
+            cs += M.Cinv[6 * i + k] * ds[k];
+        }
+        a += ce * de[i];
+        b += cs * ds[i];
+    }
+    return a + b;
+}
+
+// Bounded mbarrier wait.  Returns false on timeout.
+__device__ __forceinline__ bool dd_mbar_wait(uint32_t bar, uint32_t parity) {
+    uint32_t done = 0;
+    unsigned long long t0 = 0;
+    for (int spin = 0;; ++spin) {
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((spin & 63) == 0) {
+            unsigned long long t = dd_globaltimer();
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > kWaitLimitNs) return false;
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t dd_smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void dd_mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void dd_fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void dd_mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void dd_mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// 1-D bulk copy global -> shared (TMA engine), completion on an mbarrier.
+// dst, src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void dd_bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}

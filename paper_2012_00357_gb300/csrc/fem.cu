@@ -1,0 +1,638 @@
+// Constraint-set projection P_C of the DD iteration (Sec. 2, Eq. 4-6) on the
+// GPU, for a box of trilinear hexahedra with 2x2x2 Gauss points, clamped at
+// z = 0 and loaded by a traction on z = lz.
+//
+//   E = A_e{ w B^T C eps* }                       k_assemble_rhs   (Eq. 5a)
+//   S = f - A_e{ w B^T sig* }                     k_assemble_rhs   (Eq. 5b)
+//   K u = E,  K eta = S                           k_cg             (Eq. 5)
+//   eps = B u,  sig = sig* + C B eta              k_recover        (Eq. 6)
+//
+// The two systems share K, so every vector stores both per node, interleaved
+// as (u_x, u_y, u_z, eta_x, eta_y, eta_z): one gather of a neighbour serves
+// both right-hand sides.  K is never assembled: all elements of the box have
+// the same 24x24 stiffness Ke, and the node-based matrix-free product gathers
+// Ke blocks over the (up to) eight elements around a node, so no atomics are
+// needed and the result does not depend on scheduling.  The preconditioned CG
+// runs as one cooperative persistent kernel with bounded grid barriers and
+// fixed-order reductions (deterministic), warm-started from the previous DD
+// iteration's (u, eta).
+#include <cmath>
+
+#include "dd_internal.cuh"
+#include "fem.cuh"
+
+namespace {
+
+__device__ __forceinline__ void node_ijk(const MeshDev &g, int64_t a, int &i, int &j, int &k) {
+    const int64_t nx1 = g.nx + 1, ny1 = g.ny + 1;
+    i = (int)(a % nx1);
+    j = (int)((a / nx1) % ny1);
+    k = (int)(a / (nx1 * ny1));
+}
+
+__device__ __forceinline__ int64_t node_id(const MeshDev &g, int i, int j, int k) {
+    return i + (int64_t)(g.nx + 1) * (j + (int64_t)(g.ny + 1) * k);
+}
+
+__device__ __forceinline__ void bt_times(const double *dN, const double *v, double out[3]) {
+    // B_a^T v for the Voigt vector v = (xx, yy, zz, yz, xz, xy)
+    out[0] = dN[0] * v[0] + dN[2] * v[4] + dN[1] * v[5];
+    out[1] = dN[1] * v[1] + dN[2] * v[3] + dN[0] * v[5];
+    out[2] = dN[2] * v[2] + dN[1] * v[3] + dN[0] * v[4];
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_gather_star(const int32_t *__restrict__ idx, const float *__restrict__ raw,
+                              int64_t N, MetricMaps M, int64_t n_gp, double *__restrict__ star,
+                              double *__restrict__ ce, unsigned *__restrict__ err) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n_gp) return;
+    int64_t j = idx[e];
+    if (j < 0 || j >= N) {
+        atomicOr(err, DEV_ERR_BOUNDS);
+        j = 0;
+    }
+    double s[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        s[k] = (double)raw[j * 12 + k];
+        star[e * 12 + k] = s[k];
+    }
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+        double acc = 0.0;
+#pragma unroll
+        for (int b = 0; b < 6; ++b) acc += M.C[6 * a + b] * s[b];
+        ce[e * 6 + a] = acc;
+    }
+}
+
+__global__ void k_assemble_rhs(MeshDev g, ElemOps ops, const double *__restrict__ star,
+                               const double *__restrict__ ce, const double *__restrict__ f,
+                               double *__restrict__ b) {
+    int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (a >= g.n_nodes) return;
+    int i, j, k;
+    node_ijk(g, a, i, j, k);
+    double out[6] = {0, 0, 0, 0, 0, 0};
+    if (k > 0) {
+        out[3] = f[a * 3 + 0];
+        out[4] = f[a * 3 + 1];
+        out[5] = f[a * 3 + 2];
+        for (int oz = -1; oz <= 0; ++oz)
+            for (int oy = -1; oy <= 0; ++oy)
+                for (int ox = -1; ox <= 0; ++ox) {
+                    int ei = i + ox, ej = j + oy, ek = k + oz;
+                    if (ei < 0 || ej < 0 || ek < 0 || ei >= g.nx || ej >= g.ny || ek >= g.nz) continue;
+                    int la = (-ox) + 2 * (-oy) + 4 * (-oz);
+                    int64_t el = ei + (int64_t)g.nx * (ej + (int64_t)g.ny * ek);
+                    for (int gp = 0; gp < 8; ++gp) {
+                        int64_t e = el * 8 + gp;
+                        const double *dN = ops.dN[gp][la];
+                        double t[3], v[6];
+#pragma unroll
+                        for (int c = 0; c < 6; ++c) v[c] = ce[e * 6 + c];
+                        bt_times(dN, v, t);
+                        out[0] += g.w * t[0];
+                        out[1] += g.w * t[1];
+                        out[2] += g.w * t[2];
+#pragma unroll
+                        for (int c = 0; c < 6; ++c) v[c] = star[e * 12 + 6 + c];
+                        bt_times(dN, v, t);
+                        out[3] -= g.w * t[0];
+                        out[4] -= g.w * t[1];
+                        out[5] -= g.w * t[2];
+                    }
+                }
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) b[a * 6 + c] = out[c];
+}
+
+// 3x3 block-Jacobi preconditioner: inverse of the node's diagonal block of K.
+__global__ void k_block_jacobi(MeshDev g, const double *__restrict__ Ke, double *__restrict__ Minv) {
+    int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (a >= g.n_nodes) return;
+    int i, j, k;
+    node_ijk(g, a, i, j, k);
+    double D[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    if (k > 0) {
+        for (int oz = -1; oz <= 0; ++oz)
+            for (int oy = -1; oy <= 0; ++oy)
+                for (int ox = -1; ox <= 0; ++ox) {
+                    int ei = i + ox, ej = j + oy, ek = k + oz;
+                    if (ei < 0 || ej < 0 || ek < 0 || ei >= g.nx || ej >= g.ny || ek >= g.nz) continue;
+                    int la = (-ox) + 2 * (-oy) + 4 * (-oz);
+                    for (int r = 0; r < 3; ++r)
+                        for (int c = 0; c < 3; ++c) D[3 * r + c] += Ke[(3 * la + r) * 24 + 3 * la + c];
+                }
+        double det = D[0] * (D[4] * D[8] - D[5] * D[7]) - D[1] * (D[3] * D[8] - D[5] * D[6]) +
+                     D[2] * (D[3] * D[7] - D[4] * D[6]);
+        double id = 1.0 / det;
+        double I[9];
+        I[0] = (D[4] * D[8] - D[5] * D[7]) * id;
+        I[1] = (D[2] * D[7] - D[1] * D[8]) * id;
+        I[2] = (D[1] * D[5] - D[2] * D[4]) * id;
+        I[3] = (D[5] * D[6] - D[3] * D[8]) * id;
+        I[4] = (D[0] * D[8] - D[2] * D[6]) * id;
+        I[5] = (D[2] * D[3] - D[0] * D[5]) * id;
+        I[6] = (D[3] * D[7] - D[4] * D[6]) * id;
+        I[7] = (D[1] * D[6] - D[0] * D[7]) * id;
+        I[8] = (D[0] * D[4] - D[1] * D[3]) * id;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) Minv[a * 9 + c] = I[c];
+    } else {
+#pragma unroll
+        for (int c = 0; c < 9; ++c) Minv[a * 9 + c] = 0.0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Cooperative preconditioned CG for both systems
+// ---------------------------------------------------------------------------
+constexpr int kCgThreads = 256;
+
+struct CGArgs {
+    MeshDev g;
+    const double *Ke;      // [24 x 24]
+    const double *Minv;    // [n_nodes x 9]
+    const double *b;       // [n_nodes x 6]
+    double *x, *r, *z, *p0, *p1, *q;
+    double *part;          // [2 x grid x 8]: alternating reduction partials
+    unsigned *bar;         // [2]: count, generation
+    unsigned *err;
+    double rtol2;
+    int max_it;
+    int *it_out;           // [1]
+    double *res_out;       // [2] final relative residuals
+};
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Bounded grid barrier for a cooperative launch.  Returns false if any block
+// reported a timeout.
+__device__ bool grid_barrier(unsigned *bar, unsigned nblocks, unsigned *err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        unsigned g0 = ld_acquire(bar + 1);
+        __threadfence();
+        unsigned old = atomicAdd(bar, 1u);
+        if (old == nblocks - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            unsigned long long t0 = dd_globaltimer();
+            int spin = 0;
+            while (ld_acquire(bar + 1) == g0) {
+                if ((++spin & 31) == 0 && dd_globaltimer() - t0 > kWaitLimitNs) {
+                    atomicOr(err, DEV_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        if (ok && (ld_acquire(err) & DEV_ERR_TIMEOUT)) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Sum NV per-thread values over the block; thread 0 gets the totals.
+template <int NV>
+__device__ void block_sum(double (&v)[NV], double *sh /* [NV * 32] */) {
+#pragma unroll
+    for (int c = 0; c < NV; ++c)
+        for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < NV; ++c) sh[c * 32 + wid] = v[c];
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int c = 0; c < NV; ++c) {
+            double t = lane < nw ? sh[c * 32 + lane] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            v[c] = t;
+        }
+    }
+    __syncthreads();
+}
+
+// After a barrier: every block sums the grid partials in the same order.
+template <int NV>
+__device__ void grid_total(const double *part, int nblk, double (&tot)[NV], double *sh) {
+    double v[NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) v[c] = 0.0;
+    for (int t = threadIdx.x; t < nblk; t += blockDim.x)
+#pragma unroll
+        for (int c = 0; c < NV; ++c) v[c] += __ldcg(part + (size_t)t * 8 + c);
+    block_sum<NV>(v, sh);
+    __shared__ double s_tot[8];
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int c = 0; c < NV; ++c) s_tot[c] = v[c];
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < NV; ++c) tot[c] = s_tot[c];
+    __syncthreads();
+}
+
+// y_a = (K v)_a for both systems, v = vz + beta .* vp (vp may be null).
+__device__ __forceinline__ void spmv_node(const MeshDev &g, const double *sKe, int64_t a,
+                                          const double *vz, const double *vp, const double beta[2],
+                                          double y[6]) {
+    int i, j, k;
+    node_ijk(g, a, i, j, k);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) y[c] = 0.0;
+    if (k == 0) return;
+    for (int oz = -1; oz <= 0; ++oz)
+        for (int oy = -1; oy <= 0; ++oy)
+            for (int ox = -1; ox <= 0; ++ox) {
+                int ei = i + ox, ej = j + oy, ek = k + oz;
+                if (ei < 0 || ej < 0 || ek < 0 || ei >= g.nx || ej >= g.ny || ek >= g.nz) continue;
+                int la = (-ox) + 2 * (-oy) + 4 * (-oz);
+#pragma unroll
+                for (int lb = 0; lb < 8; ++lb) {
+                    int64_t nb = node_id(g, ei + (lb & 1), ej + ((lb >> 1) & 1), ek + ((lb >> 2) & 1));
+                    double xv[6];
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) {
+                        double t = __ldcg(vz + nb * 6 + c);
+                        if (vp) t += beta[c / 3] * __ldcg(vp + nb * 6 + c);
+                        xv[c] = t;
+                    }
+                    const double *kb = sKe + (3 * la) * 24 + 3 * lb;
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) {
+                        double k0 = kb[r * 24 + 0], k1 = kb[r * 24 + 1], k2 = kb[r * 24 + 2];
+                        y[r] += k0 * xv[0] + k1 * xv[1] + k2 * xv[2];
+                        y[3 + r] += k0 * xv[3] + k1 * xv[4] + k2 * xv[5];
+                    }
+                }
+            }
+}
+
+__device__ __forceinline__ void apply_minv(const double *Mi, const double *r, double *z) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            z[3 * s + a] = Mi[3 * a] * r[3 * s] + Mi[3 * a + 1] * r[3 * s + 1] + Mi[3 * a + 2] * r[3 * s + 2];
+}
+
+__global__ void __launch_bounds__(kCgThreads) k_cg(CGArgs A) {
+    __shared__ double sKe[576];
+    __shared__ double sh[8 * 32];
+    const MeshDev &g = A.g;
+    for (int t = threadIdx.x; t < 576; t += blockDim.x) sKe[t] = A.Ke[t];
+    __syncthreads();
+    const unsigned G = gridDim.x;
+    const int64_t stride = (int64_t)G * blockDim.x;
+    const int64_t a0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const double zero_beta[2] = {0.0, 0.0};
+    // Phase A reduces into partA, phase B (and the set-up) into partB: a block
+    // can only overwrite a buffer after every block passed the barrier that
+    // follows the other buffer's reduction, i.e. after all reads of it.
+    double *partA = A.part, *partB = A.part + (size_t)G * 8;
+
+    // r = b - K x, z = M^-1 r, p0 = z; partials rz, rr, bb
+    {
+        double v[6] = {0, 0, 0, 0, 0, 0};
+        for (int64_t a = a0; a < g.n_nodes; a += stride) {
+            double kx[6], rr[6], zz[6];
+            spmv_node(g, sKe, a, A.x, nullptr, zero_beta, kx);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) rr[c] = A.b[a * 6 + c] - kx[c];
+            apply_minv(A.Minv + a * 9, rr, zz);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                A.r[a * 6 + c] = rr[c];
+                A.z[a * 6 + c] = zz[c];
+                A.p0[a * 6 + c] = zz[c];
+                double bc = A.b[a * 6 + c];
+                v[c / 3] += rr[c] * zz[c];
+                v[2 + c / 3] += rr[c] * rr[c];
+                v[4 + c / 3] += bc * bc;
+            }
+        }
+        block_sum<6>(v, sh);
+        if (threadIdx.x == 0)
+            for (int c = 0; c < 6; ++c) partB[blockIdx.x * 8 + c] = v[c];
+    }
+    if (!grid_barrier(A.bar, G, A.err)) return;
+    double tot[6];
+    grid_total<6>(partB, G, tot, sh);
+    double rz[2] = {tot[0], tot[1]}, rr[2] = {tot[2], tot[3]}, bb[2] = {tot[4], tot[5]};
+    bool conv[2];
+    for (int s = 0; s < 2; ++s) conv[s] = !(rr[s] > A.rtol2 * bb[s]);
+
+    double beta[2] = {0.0, 0.0};
+    double *pold = A.p0, *pnew = A.p1;
+    int it = 0;
+    for (; it < A.max_it && !(conv[0] && conv[1]); ++it) {
+        // phase A: p_new = z + beta p_old, q = K p_new, partial p.q
+        double v[2] = {0, 0};
+        for (int64_t a = a0; a < g.n_nodes; a += stride) {
+            double kq[6];
+            spmv_node(g, sKe, a, A.z, pold, beta, kq);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                double pn = A.z[a * 6 + c] + beta[c / 3] * pold[a * 6 + c];
+                pnew[a * 6 + c] = pn;
+                A.q[a * 6 + c] = kq[c];
+                v[c / 3] += pn * kq[c];
+            }
+        }
+        block_sum<2>(v, sh);
+        if (threadIdx.x == 0) {
+            partA[blockIdx.x * 8 + 0] = v[0];
+            partA[blockIdx.x * 8 + 1] = v[1];
+        }
+        if (!grid_barrier(A.bar, G, A.err)) return;
+        double pq[2];
+        grid_total<2>(partA, G, pq, sh);
+        double alpha[2];
+        for (int s = 0; s < 2; ++s) alpha[s] = (conv[s] || !(pq[s] > 0.0)) ? 0.0 : rz[s] / pq[s];
+        // phase B: x += alpha p, r -= alpha q, z = M^-1 r, partial r.z, r.r
+        double w[4] = {0, 0, 0, 0};
+        for (int64_t a = a0; a < g.n_nodes; a += stride) {
+            double rv[6], zv[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                double al = alpha[c / 3];
+                A.x[a * 6 + c] += al * pnew[a * 6 + c];
+                rv[c] = A.r[a * 6 + c] - al * A.q[a * 6 + c];
+                A.r[a * 6 + c] = rv[c];
+            }
+            apply_minv(A.Minv + a * 9, rv, zv);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                A.z[a * 6 + c] = zv[c];
+                w[c / 3] += rv[c] * zv[c];
+                w[2 + c / 3] += rv[c] * rv[c];
+            }
+        }
+        block_sum<4>(w, sh);
+        if (threadIdx.x == 0)
+            for (int c = 0; c < 4; ++c) partB[blockIdx.x * 8 + c] = w[c];
+        if (!grid_barrier(A.bar, G, A.err)) return;
+        double t4[4];
+        grid_total<4>(partB, G, t4, sh);
+        for (int s = 0; s < 2; ++s) {
+            if (!conv[s]) {
+                beta[s] = (rz[s] != 0.0) ? t4[s] / rz[s] : 0.0;
+                rz[s] = t4[s];
+                rr[s] = t4[2 + s];
+                conv[s] = !(rr[s] > A.rtol2 * bb[s]) || !(pq[s] > 0.0);
+            } else {
+                beta[s] = 0.0;
+            }
+        }
+        double *t = pold;
+        pold = pnew;
+        pnew = t;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *A.it_out = it;
+        A.res_out[0] = bb[0] > 0 ? sqrt(rr[0] / bb[0]) : 0.0;
+        A.res_out[1] = bb[1] > 0 ? sqrt(rr[1] / bb[1]) : 0.0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_recover(MeshDev g, ElemOps ops, MetricMaps M, const double *__restrict__ x,
+                          const double *__restrict__ star, double *__restrict__ y,
+                          double *__restrict__ dpc) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= g.n_gp) return;
+    const int64_t el = e / 8;
+    const int gp = (int)(e % 8);
+    const int ei = (int)(el % g.nx), ej = (int)((el / g.nx) % g.ny), ek = (int)(el / ((int64_t)g.nx * g.ny));
+    double eu[6] = {0, 0, 0, 0, 0, 0}, en[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        int64_t nb = node_id(g, ei + (a & 1), ej + ((a >> 1) & 1), ek + ((a >> 2) & 1));
+        const double *dN = ops.dN[gp][a];
+        const double *xv = x + nb * 6;
+        // B_a u_a for u and for eta
+        eu[0] += dN[0] * xv[0];
+        eu[1] += dN[1] * xv[1];
+        eu[2] += dN[2] * xv[2];
+        eu[3] += dN[2] * xv[1] + dN[1] * xv[2];
+        eu[4] += dN[2] * xv[0] + dN[0] * xv[2];
+        eu[5] += dN[1] * xv[0] + dN[0] * xv[1];
+        en[0] += dN[0] * xv[3];
+        en[1] += dN[1] * xv[4];
+        en[2] += dN[2] * xv[5];
+        en[3] += dN[2] * xv[4] + dN[1] * xv[5];
+        en[4] += dN[2] * xv[3] + dN[0] * xv[5];
+        en[5] += dN[1] * xv[3] + dN[0] * xv[4];
+    }
+    double yy[12];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) yy[c] = eu[c];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        double s = star[e * 12 + 6 + c];
+#pragma unroll
+        for (int b = 0; b < 6; ++b) s += M.C[6 * c + b] * en[b];
+        yy[6 + c] = s;
+    }
+#pragma unroll
+    for (int c = 0; c < 12; ++c) y[e * 12 + c] = yy[c];
+    // distance to the current association (Eq. 3), weighted as in Eq. 2
+    double de[6], ds[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        de[c] = yy[c] - star[e * 12 + c];
+        ds[c] = yy[6 + c] - star[e * 12 + 6 + c];
+    }
+    double d = 0.0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        double ce = 0.0, cs = 0.0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            ce += M.C[6 * i + k] * de[k];
+            cs += M.Cinv[6 * i + k] * ds[k];
+        }
+        d += ce * de[i] + cs * ds[i];
+    }
+    dpc[e] = 0.5 * g.w * d;
+}
+
+// Iteration statistics in one block, fixed order: changed associations,
+// sum_e 1/2 w d_e^2 after P_D, sum after P_C.
+__global__ void __launch_bounds__(1024) k_iter_stats(const int32_t *__restrict__ idx_new,
+                                                     const int32_t *__restrict__ idx_old,
+                                                     const double *__restrict__ d2,
+                                                     const double *__restrict__ dpc, int64_t n,
+                                                     double w, double *__restrict__ out) {
+    __shared__ double sh[3 * 32];
+    double v[3] = {0, 0, 0};
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+        v[0] += (idx_new[e] != idx_old[e]) ? 1.0 : 0.0;
+        v[1] += 0.5 * w * d2[e];
+        v[2] += dpc[e];
+    }
+    block_sum<3>(v, sh);
+    if (threadIdx.x == 0) {
+        out[0] = v[0];
+        out[1] = v[1];
+        out[2] = v[2];
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+static const double kGP = 0.57735026918962576451;   // 1/sqrt(3)
+
+void fem_elem_ops(const MeshDev &g, ElemOps *ops) {
+    const double h[3] = {g.hx, g.hy, g.hz};
+    for (int gp = 0; gp < 8; ++gp) {
+        double xi[3] = {(2 * (gp & 1) - 1) * kGP, (2 * ((gp >> 1) & 1) - 1) * kGP,
+                        (2 * ((gp >> 2) & 1) - 1) * kGP};
+        for (int a = 0; a < 8; ++a) {
+            double s[3] = {2.0 * (a & 1) - 1.0, 2.0 * ((a >> 1) & 1) - 1.0, 2.0 * ((a >> 2) & 1) - 1.0};
+            double f[3] = {1 + s[0] * xi[0], 1 + s[1] * xi[1], 1 + s[2] * xi[2]};
+            double d[3] = {s[0] * f[1] * f[2] / 8.0, f[0] * s[1] * f[2] / 8.0, f[0] * f[1] * s[2] / 8.0};
+            for (int c = 0; c < 3; ++c) ops->dN[gp][a][c] = d[c] * 2.0 / h[c];
+        }
+    }
+}
+
+void fem_element_stiffness(const MeshDev &g, const ElemOps &ops, const double *C, double *Ke) {
+    for (int i = 0; i < 576; ++i) Ke[i] = 0.0;
+    for (int gp = 0; gp < 8; ++gp) {
+        double B[6][24] = {};
+        for (int a = 0; a < 8; ++a) {
+            const double *d = ops.dN[gp][a];
+            int c = 3 * a;
+            B[0][c] = d[0];
+            B[1][c + 1] = d[1];
+            B[2][c + 2] = d[2];
+            B[3][c + 1] = d[2];
+            B[3][c + 2] = d[1];
+            B[4][c] = d[2];
+            B[4][c + 2] = d[0];
+            B[5][c] = d[1];
+            B[5][c + 1] = d[0];
+        }
+        double CB[6][24];
+        for (int r = 0; r < 6; ++r)
+            for (int c = 0; c < 24; ++c) {
+                double s = 0.0;
+                for (int k = 0; k < 6; ++k) s += C[6 * r + k] * B[k][c];
+                CB[r][c] = s;
+            }
+        for (int r = 0; r < 24; ++r)
+            for (int c = 0; c < 24; ++c) {
+                double s = 0.0;
+                for (int k = 0; k < 6; ++k) s += B[k][r] * CB[k][c];
+                Ke[r * 24 + c] += g.w * s;
+            }
+    }
+}
+
+void fem_traction_force(const MeshDev &g, const dd_load &L, double lx, double ly, double *f) {
+    for (int64_t i = 0; i < g.n_nodes * 3; ++i) f[i] = 0.0;
+    const double hx = g.hx, hy = g.hy, wq = hx * hy / 4.0;
+    for (int i = 0; i < g.nx; ++i)
+        for (int j = 0; j < g.ny; ++j)
+            for (int qx = 0; qx < 2; ++qx)
+                for (int qy = 0; qy < 2; ++qy) {
+                    double gx = (2 * qx - 1) * kGP, gy = (2 * qy - 1) * kGP;
+                    double x = (i + 0.5 * (1 + gx)) * hx, y = (j + 0.5 * (1 + gy)) * hy;
+                    double t[3];
+                    for (int c = 0; c < 3; ++c) t[c] = L.t0[c] + L.tx[c] * (x - lx / 2) + L.ty[c] * (y - ly / 2);
+                    for (int ax = 0; ax < 2; ++ax)
+                        for (int ay = 0; ay < 2; ++ay) {
+                            double N = 0.25 * (1 + (2 * ax - 1) * gx) * (1 + (2 * ay - 1) * gy);
+                            int64_t n = (i + ax) + (int64_t)(g.nx + 1) * ((j + ay) + (int64_t)(g.ny + 1) * g.nz);
+                            for (int c = 0; c < 3; ++c) f[n * 3 + c] += N * t[c] * wq;
+                        }
+                }
+}
+
+dd_status fem_gather_star(dd_dataset *ds, const int32_t *idx, int64_t n_gp, double *star, double *ce,
+                          cudaStream_t s) {
+    k_gather_star<<<(unsigned)((n_gp + 255) / 256), 256, 0, s>>>(idx, ds->raw, ds->N, ds->M, n_gp, star,
+                                                                ce, ds->ctx->dev_err);
+    DD_TRY_CUDA(ds->ctx, cudaGetLastError());
+    return DD_OK;
+}
+
+dd_status fem_assemble_rhs(dd_ctx *ctx, const MeshDev &g, const ElemOps &ops, const double *star,
+                           const double *ce, const double *f, double *b, cudaStream_t s) {
+    k_assemble_rhs<<<(unsigned)((g.n_nodes + 127) / 128), 128, 0, s>>>(g, ops, star, ce, f, b);
+    DD_TRY_CUDA(ctx, cudaGetLastError());
+    return DD_OK;
+}
+
+dd_status fem_block_jacobi(dd_ctx *ctx, const MeshDev &g, const double *Ke, double *Minv, cudaStream_t s) {
+    k_block_jacobi<<<(unsigned)((g.n_nodes + 127) / 128), 128, 0, s>>>(g, Ke, Minv);
+    DD_TRY_CUDA(ctx, cudaGetLastError());
+    return DD_OK;
+}
+
+dd_status fem_cg(dd_ctx *ctx, const MeshDev &g, const CGBuffers &B, double rtol, int max_it,
+                 cudaStream_t s) {
+    int occ = 0;
+    DD_TRY_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg, kCgThreads, 0));
+    if (occ < 1) return dd_fail(ctx, DD_ERR_CUDA, "CG kernel cannot be resident");
+    int64_t want = (g.n_nodes + kCgThreads - 1) / kCgThreads;
+    int grid = (int)std::min<int64_t>(want, (int64_t)occ * ctx->n_sm);
+    grid = std::max(grid, 1);
+    CGArgs A;
+    A.g = g;
+    A.Ke = B.Ke;
+    A.Minv = B.Minv;
+    A.b = B.b;
+    A.x = B.x;
+    A.r = B.r;
+    A.z = B.z;
+    A.p0 = B.p0;
+    A.p1 = B.p1;
+    A.q = B.q;
+    A.part = B.part;
+    A.bar = B.bar;
+    A.err = ctx->dev_err;
+    A.rtol2 = rtol * rtol;
+    A.max_it = max_it;
+    A.it_out = B.it_out;
+    A.res_out = B.res_out;
+    DD_TRY_CUDA(ctx, cudaMemsetAsync(B.bar, 0, 2 * sizeof(unsigned), s));
+    void *args[] = {&A};
+    DD_TRY_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)k_cg, dim3(grid), dim3(kCgThreads), args, 0, s));
+    return DD_OK;
+}
+
+dd_status fem_recover(dd_dataset *ds, const MeshDev &g, const ElemOps &ops, const double *x,
+                      const double *star, double *y, double *dpc, cudaStream_t s) {
+    k_recover<<<(unsigned)((g.n_gp + 127) / 128), 128, 0, s>>>(g, ops, ds->M, x, star, y, dpc);
+    DD_TRY_CUDA(ds->ctx, cudaGetLastError());
+    return DD_OK;
+}
+
+dd_status fem_iter_stats(dd_ctx *ctx, const int32_t *idx_new, const int32_t *idx_old, const double *d2,
+                         const double *dpc, int64_t n, double w, double *out, cudaStream_t s) {
+    k_iter_stats<<<1, 1024, 0, s>>>(idx_new, idx_old, d2, dpc, n, w, out);
+    DD_TRY_CUDA(ctx, cudaGetLastError());
+    return DD_OK;
+}

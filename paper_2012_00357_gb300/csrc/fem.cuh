@@ -1,0 +1,56 @@
+// Finite-element operators of the constraint projection P_C (fem.cu).
+#pragma once
+
+#include "dd_internal.cuh"
+
+struct MeshDev {
+    int nx, ny, nz;
+    int64_t n_nodes, n_el, n_gp;
+    double hx, hy, hz;
+    double w;            // Gauss weight * det J = hx hy hz / 8
+};
+
+// Physical shape-function gradients dN[gauss point][local node][x,y,z] of
+// the (identical) elements of the box.
+struct ElemOps {
+    double dN[8][8][3];
+};
+
+struct CGBuffers {
+    const double *Ke, *Minv, *b;
+    double *x, *r, *z, *p0, *p1, *q, *part;
+    unsigned *bar;
+    int *it_out;
+    double *res_out;
+};
+
+inline MeshDev fem_mesh(const dd_mesh &m) {
+    MeshDev g;
+    g.nx = m.nx;
+    g.ny = m.ny;
+    g.nz = m.nz;
+    g.n_nodes = (int64_t)(m.nx + 1) * (m.ny + 1) * (m.nz + 1);
+    g.n_el = (int64_t)m.nx * m.ny * m.nz;
+    g.n_gp = 8 * g.n_el;
+    g.hx = m.lx / m.nx;
+    g.hy = m.ly / m.ny;
+    g.hz = m.lz / m.nz;
+    g.w = g.hx * g.hy * g.hz / 8.0;
+    return g;
+}
+
+void fem_elem_ops(const MeshDev &g, ElemOps *ops);
+void fem_element_stiffness(const MeshDev &g, const ElemOps &ops, const double *C, double *Ke);
+void fem_traction_force(const MeshDev &g, const dd_load &L, double lx, double ly, double *f);
+
+dd_status fem_gather_star(dd_dataset *ds, const int32_t *idx, int64_t n_gp, double *star, double *ce,
+                          cudaStream_t s);
+dd_status fem_assemble_rhs(dd_ctx *ctx, const MeshDev &g, const ElemOps &ops, const double *star,
+                           const double *ce, const double *f, double *b, cudaStream_t s);
+dd_status fem_block_jacobi(dd_ctx *ctx, const MeshDev &g, const double *Ke, double *Minv, cudaStream_t s);
+dd_status fem_cg(dd_ctx *ctx, const MeshDev &g, const CGBuffers &B, double rtol, int max_it,
+                 cudaStream_t s);
+dd_status fem_recover(dd_dataset *ds, const MeshDev &g, const ElemOps &ops, const double *x,
+                      const double *star, double *y, double *dpc, cudaStream_t s);
+dd_status fem_iter_stats(dd_ctx *ctx, const int32_t *idx_new, const int32_t *idx_old, const double *d2,
+                         const double *dpc, int64_t n, double w, double *out, cudaStream_t s);

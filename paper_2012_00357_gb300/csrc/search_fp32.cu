@@ -1,0 +1,431 @@
+// Exact data projection P_D (Eq. 7) on CUDA cores.
+//
+// The linear search of the paper (every query against every data point) is
+// restated for the GPU as a certified two-stage scan:
+//
+//  1. k_scan_fp32 streams the centred mapped coordinates z_j (FP32, 48 B per
+//     point) through shared memory with the TMA bulk-copy engine and scores
+//     every (query, point) pair with the expanded form
+//         s_j = |z_j|^2 - 2 z_j . q   ( = |z_j - q|^2 - |q|^2 ),
+//     12 FFMA per pair.  Each query keeps every point whose score lies within
+//     a window w of its running minimum; w is twice a bound on the score
+//     error (FP32 storage of z and q plus FP32 arithmetic), so the exact
+//     nearest point is always inside the final window.
+//  2. dd_merge_rescore merges the windows of the data splits, rescores the
+//     survivors with Eq. (3) in FP64 from the stored (eps, sig) values and
+//     picks the minimum (lowest index on ties).  A query whose window
+//     overflowed the candidate buffer is re-searched by an FP64 scan over all
+//     points, so the returned neighbour is the exact one.
+//
+// Candidate layout, per (query q, split s): header hdr[q * S + s] and
+// entries cand[(q * S + s) * CAP + c] = (score, index bits).
+#include <cfloat>
+#include <cmath>
+
+#include "dd_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kRQ = 4;                       // queries per thread
+constexpr int kCap = 8;                      // candidate buffer per query
+constexpr int kT = 128;                      // data points per stage
+constexpr int kStages = 4;
+constexpr int kQT = kThreads * kRQ;          // queries per CTA
+
+constexpr size_t kScanSmem =
+    size_t(kStages) * kT * 12 * 4 + size_t(kStages) * kT * 4 + size_t(kRQ) * kCap * kThreads * 8;
+
+// ---------------------------------------------------------------------------
+// Query map: y = (eps, sig) -> centred q = (C^{1/2} eps, C^{-1/2} sig)/sqrt(2) - mu
+// ---------------------------------------------------------------------------
+__global__ void k_map_queries(const double *__restrict__ y, int64_t m, MetricMaps M, double R,
+                              double *__restrict__ zq64, QueryRec *__restrict__ rec) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    double s[12], z[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) s[k] = y[i * 12 + k];
+    const double r2 = 0.70710678118654752440;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+        double e = 0.0, g = 0.0;
+#pragma unroll
+        for (int b = 0; b < 6; ++b) {
+            e += M.Ch[6 * a + b] * s[b];
+            g += M.Cmh[6 * a + b] * s[6 + b];
+        }
+        z[a] = e * r2 - M.mu[a];
+        z[6 + a] = g * r2 - M.mu[6 + a];
+    }
+    QueryRec r;
+    double qn = 0.0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        if (zq64) zq64[i * 12 + k] = z[k];
+        r.q[k] = (float)z[k];
+        qn += (double)r.q[k] * (double)r.q[k];
+    }
+    // score error bound: storage rounding of z and q (2^-24 relative each),
+    // 12-term FFMA chain and the rounded |z|^2, bounded by 2^-18 (R + |q|)^2.
+    double b = R + sqrt(qn);
+    double E = ldexp(b * b, -18);
+    r.w2 = (float)(2.0 * E * 1.0001);
+    r.qn = (float)qn;
+    r.pad[0] = r.pad[1] = 0.f;
+    bool finite = isfinite(qn);
+    if (!finite) r.w2 = INFINITY;
+    rec[i] = r;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 streaming scan with candidate windows
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads, 2)
+    k_scan_fp32(const float *__restrict__ z32, const float *__restrict__ zn, int64_t N,
+                int64_t n_tiles, const QueryRec *__restrict__ rec, int64_t m, int splits,
+                int64_t tiles_per_split, CandHeader *__restrict__ hdr, float2 *__restrict__ cand,
+                unsigned *__restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    float *sz = reinterpret_cast<float *>(smem);
+    float *sn = sz + kStages * kT * 12;
+    float2 *buf = reinterpret_cast<float2 *>(sn + kStages * kT);
+    __shared__ __align__(8) uint64_t full[kStages];
+
+    const int tid = threadIdx.x;
+    const int split = blockIdx.y;
+    const int64_t qbase = (int64_t)blockIdx.x * kQT;
+    const int64_t t_begin = split * tiles_per_split;
+    const int64_t t_end = min(n_tiles, t_begin + tiles_per_split);
+    const int64_t ntl = t_end > t_begin ? t_end - t_begin : 0;
+
+    float q[kRQ][12], lim[kRQ], w2[kRQ], mrun[kRQ], dropped[kRQ];
+    int cnt[kRQ];
+#pragma unroll
+    for (int r = 0; r < kRQ; ++r) {
+        int64_t qi = qbase + r * kThreads + tid;
+        mrun[r] = INFINITY;
+        dropped[r] = INFINITY;
+        cnt[r] = 0;
+        if (qi < m) {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) q[r][k] = -2.0f * rec[qi].q[k];
+            w2[r] = rec[qi].w2;
+            lim[r] = INFINITY;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) q[r][k] = 0.f;
+            w2[r] = 0.f;
+            lim[r] = -INFINITY;
+        }
+    }
+
+    const uint32_t zbytes = kT * 12 * 4, nbytes = kT * 4;
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) dd_mbar_init(dd_smem_addr(&full[s]), 1);
+        dd_fence_mbar_init();
+        for (int s = 0; s < kStages && s < ntl; ++s) {
+            int64_t j0 = (t_begin + s) * kT;
+            uint32_t bar = dd_smem_addr(&full[s]);
+            dd_mbar_expect_tx(bar, zbytes + nbytes);
+            dd_bulk_g2s(dd_smem_addr(sz + s * kT * 12), z32 + j0 * 12, zbytes, bar);
+            dd_bulk_g2s(dd_smem_addr(sn + s * kT), zn + j0, nbytes, bar);
+        }
+    }
+    __syncthreads();
+
+    bool ok = true;
+    for (int64_t it = 0; it < ntl; ++it) {
+        const int s = (int)(it % kStages);
+        const uint32_t parity = (uint32_t)((it / kStages) & 1);
+        if (ok && !dd_mbar_wait(dd_smem_addr(&full[s]), parity)) {
+            ok = false;
+            atomicOr(err, DEV_ERR_TIMEOUT);
+        }
+        const float4 *tz = reinterpret_cast<const float4 *>(sz + s * kT * 12);
+        const float *tn = sn + s * kT;
+        const int64_t j0 = (t_begin + it) * kT;
+#pragma unroll 2
+        for (int p = 0; p < kT; ++p) {
+            const float4 a = tz[3 * p + 0], b = tz[3 * p + 1], c = tz[3 * p + 2];
+            const float n = tn[p];
+            float sc[kRQ];
+            bool any = false;
+#pragma unroll
+            for (int r = 0; r < kRQ; ++r) {
+                float v = fmaf(q[r][0], a.x, n);
+                v = fmaf(q[r][1], a.y, v);
+                v = fmaf(q[r][2], a.z, v);
+                v = fmaf(q[r][3], a.w, v);
+                v = fmaf(q[r][4], b.x, v);
+                v = fmaf(q[r][5], b.y, v);
+                v = fmaf(q[r][6], b.z, v);
+                v = fmaf(q[r][7], b.w, v);
+                v = fmaf(q[r][8], c.x, v);
+                v = fmaf(q[r][9], c.y, v);
+                v = fmaf(q[r][10], c.z, v);
+                v = fmaf(q[r][11], c.w, v);
+                sc[r] = v;
+                any |= (v <= lim[r]);
+            }
+            if (any) {
+                const int64_t j = j0 + p;
+                if (j < N) {
+#pragma unroll
+                    for (int r = 0; r < kRQ; ++r) {
+                        if (sc[r] <= lim[r]) {
+                            if (sc[r] < mrun[r]) {
+                                mrun[r] = sc[r];
+                                lim[r] = sc[r] + w2[r];
+                            }
+                            float2 *bq = buf + (size_t)r * kCap * kThreads + tid;
+                            if (cnt[r] == kCap) {
+                                int c2 = 0;
+                                for (int e = 0; e < kCap; ++e) {
+                                    float2 v = bq[e * kThreads];
+                                    if (v.x <= lim[r]) bq[(c2++) * kThreads] = v;
+                                }
+                                cnt[r] = c2;
+                            }
+                            if (cnt[r] < kCap) {
+                                bq[cnt[r] * kThreads] = make_float2(sc[r], __int_as_float((int)j));
+                                cnt[r]++;
+                            } else {
+                                dropped[r] = fminf(dropped[r], sc[r]);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (tid == 0 && it + kStages < ntl) {
+            int64_t j0n = (t_begin + it + kStages) * kT;
+            uint32_t bar = dd_smem_addr(&full[s]);
+            dd_mbar_expect_tx(bar, zbytes + nbytes);
+            dd_bulk_g2s(dd_smem_addr(sz + s * kT * 12), z32 + j0n * 12, zbytes, bar);
+            dd_bulk_g2s(dd_smem_addr(sn + s * kT), zn + j0n, nbytes, bar);
+        }
+    }
+
+#pragma unroll
+    for (int r = 0; r < kRQ; ++r) {
+        int64_t qi = qbase + r * kThreads + tid;
+        if (qi >= m) continue;
+        const size_t slot = (size_t)qi * splits + split;
+        const float2 *bq = buf + (size_t)r * kCap * kThreads + tid;
+        int c2 = 0;
+        for (int e = 0; e < cnt[r]; ++e) {
+            float2 v = bq[e * kThreads];
+            if (v.x <= lim[r]) cand[slot * kCap + (c2++)] = v;
+        }
+        CandHeader h;
+        h.mrun = mrun[r];
+        h.dropped = dropped[r];
+        h.cnt = c2;
+        h.pad = 0;
+        hdr[slot] = h;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Merge + FP64 rescoring (thread per query)
+// ---------------------------------------------------------------------------
+__global__ void k_merge_rescore(const float *__restrict__ raw, MetricMaps M,
+                                const double *__restrict__ y, int64_t m, int splits, int cap,
+                                const CandHeader *__restrict__ hdr, const float2 *__restrict__ cand,
+                                const QueryRec *__restrict__ rec, int certify,
+                                int32_t *__restrict__ idx, double *__restrict__ d2,
+                                double *__restrict__ d2nd, int64_t *__restrict__ fb_list,
+                                unsigned long long *__restrict__ fb_count) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const CandHeader *h = hdr + (size_t)i * splits;
+    float gmin = INFINITY;
+    for (int s = 0; s < splits; ++s) gmin = fminf(gmin, h[s].mrun);
+    const float w2 = rec[i].w2;
+    const float lim = gmin + w2;
+    bool uncert = !(w2 < INFINITY);
+    for (int s = 0; s < splits; ++s) uncert |= (h[s].dropped <= lim);
+    double yy[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) yy[k] = y[i * 12 + k];
+    double best = INFINITY, second = INFINITY;
+    int32_t bj = -1;
+    for (int s = 0; s < splits; ++s) {
+        const float2 *c = cand + ((size_t)i * splits + s) * cap;
+        for (int e = 0; e < h[s].cnt; ++e) {
+            float2 v = c[e];
+            if (!(v.x <= lim)) continue;
+            int32_t j = __float_as_int(v.y);
+            double d = dd_eq3(M, yy, raw + (size_t)j * 12);
+            if (d < best || (d == best && j < bj)) {
+                second = best;
+                best = d;
+                bj = j;
+            } else if (d < second) {
+                second = d;
+            }
+        }
+    }
+    if (bj < 0) uncert = true;
+    // every point outside the window has |z - q|^2 >= gmin + qn + w2/2
+    double lb = 2.0 * ((double)gmin + (double)rec[i].qn + 0.5 * (double)w2);
+    if (uncert && certify) {
+        unsigned long long k = atomicAdd(fb_count, 1ull);
+        fb_list[k] = i;
+        return;
+    }
+    idx[i] = bj;
+    if (d2) d2[i] = best;
+    if (d2nd) d2nd[i] = fmin(second, lb);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 exhaustive re-search of uncertified queries (block per query)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_fallback_fp64(const float *__restrict__ raw, int64_t N,
+                                                       MetricMaps M, const double *__restrict__ y,
+                                                       const int64_t *__restrict__ list,
+                                                       const unsigned long long *__restrict__ count,
+                                                       int32_t *__restrict__ idx,
+                                                       double *__restrict__ d2,
+                                                       double *__restrict__ d2nd) {
+    __shared__ double sb[256], ss[256];
+    __shared__ int32_t sj[256];
+    const unsigned long long n = *count;
+    for (unsigned long long t = blockIdx.x; t < n; t += gridDim.x) {
+        const int64_t i = list[t];
+        double yy[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) yy[k] = y[i * 12 + k];
+        double b1 = INFINITY, b2 = INFINITY;
+        int32_t j1 = -1;
+        for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+            double d = dd_eq3(M, yy, raw + (size_t)j * 12);
+            if (d < b1) {
+                b2 = b1;
+                b1 = d;
+                j1 = (int32_t)j;
+            } else if (d < b2) {
+                b2 = d;
+            }
+        }
+        sb[threadIdx.x] = b1;
+        ss[threadIdx.x] = b2;
+        sj[threadIdx.x] = j1;
+        __syncthreads();
+        for (int w = 128; w > 0; w >>= 1) {
+            if (threadIdx.x < w) {
+                double a1 = sb[threadIdx.x], a2 = ss[threadIdx.x];
+                double c1 = sb[threadIdx.x + w], c2 = ss[threadIdx.x + w];
+                int32_t ja = sj[threadIdx.x], jc = sj[threadIdx.x + w];
+                bool take_c = (c1 < a1) || (c1 == a1 && jc >= 0 && (ja < 0 || jc < ja));
+                double n1 = take_c ? c1 : a1;
+                double n2 = take_c ? fmin(a1, c2) : fmin(a2, c1);
+                sb[threadIdx.x] = n1;
+                ss[threadIdx.x] = n2;
+                sj[threadIdx.x] = take_c ? jc : ja;
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            idx[i] = sj[0];
+            if (d2) d2[i] = sb[0];
+            if (d2nd) d2nd[i] = ss[0];
+        }
+        __syncthreads();
+    }
+}
+
+int pick_splits(int64_t qtiles, int64_t n_tiles, int n_sm, int per_sm) {
+    const int64_t slots = (int64_t)n_sm * per_sm;
+    if (qtiles >= slots) return 1;
+    int64_t best_s = 1;
+    double best_eff = 0.0;
+    for (int64_t s = 1; s <= slots && s <= n_tiles; ++s) {
+        int64_t ctas = qtiles * s;
+        int64_t waves = (ctas + slots - 1) / slots;
+        double eff = (double)ctas / (double)(waves * slots);
+        // prefer full waves, then fewer splits
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best_s = s;
+        }
+        if (ctas >= slots && eff > 0.94) break;
+    }
+    return (int)best_s;
+}
+
+}  // namespace
+
+dd_status dd_map_queries(dd_dataset *ds, const double *y_dev, int64_t m, double *zq64,
+                         QueryRec *rec, cudaStream_t s) {
+    if (m == 0) return DD_OK;
+    k_map_queries<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(y_dev, m, ds->M, ds->R, zq64, rec);
+    DD_TRY_CUDA(ds->ctx, cudaGetLastError());
+    return DD_OK;
+}
+
+dd_status dd_merge_rescore(dd_dataset *ds, const double *y_dev, int64_t m, int splits, int cap,
+                           const CandHeader *hdr, const float2 *cand, const QueryRec *rec,
+                           int certify, SearchOut out, dd_search_stats *st, cudaStream_t s) {
+    dd_ctx *ctx = ds->ctx;
+    void *w = nullptr;
+    size_t need = (size_t)m * sizeof(int64_t) + 256;
+    DD_TRY(dd_workspace(ctx, WS_MISC, need, &w));
+    unsigned long long *fb_count = reinterpret_cast<unsigned long long *>(w);
+    int64_t *fb_list = reinterpret_cast<int64_t *>(reinterpret_cast<char *>(w) + 256);
+    DD_TRY_CUDA(ctx, cudaMemsetAsync(fb_count, 0, sizeof(unsigned long long), s));
+    k_merge_rescore<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(
+        ds->raw, ds->M, y_dev, m, splits, cap, hdr, cand, rec, certify, out.idx, out.d2, out.d2nd,
+        fb_list, fb_count);
+    DD_TRY_CUDA(ctx, cudaGetLastError());
+    if (certify) {
+        int grid = (int)std::min<int64_t>(m, (int64_t)ctx->n_sm * 4);
+        k_fallback_fp64<<<grid, 256, 0, s>>>(ds->raw, ds->N, ds->M, y_dev, fb_list, fb_count,
+                                             out.idx, out.d2, out.d2nd);
+        DD_TRY_CUDA(ctx, cudaGetLastError());
+    }
+    if (st) {
+        unsigned long long n = 0;
+        DD_TRY_CUDA(ctx, cudaMemcpyAsync(&n, fb_count, sizeof(n), cudaMemcpyDeviceToHost, s));
+        DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+        st->uncertified += (int64_t)n;
+        st->distances += (int64_t)n * ds->N;
+    }
+    return DD_OK;
+}
+
+dd_status dd_search_exact_fp32(dd_dataset *ds, const double *y_dev, int64_t m, int certify,
+                               SearchOut out, dd_search_stats *st, cudaStream_t s) {
+    dd_ctx *ctx = ds->ctx;
+    if (m == 0) return DD_OK;
+    const int64_t n_tiles = (ds->N + kT - 1) / kT;
+    const int64_t qtiles = (m + kQT - 1) / kQT;
+    const int splits = pick_splits(qtiles, n_tiles, ctx->n_sm, 2);
+    const int64_t tps = (n_tiles + splits - 1) / splits;
+
+    size_t rec_bytes = ((size_t)m * sizeof(QueryRec) + 255) / 256 * 256;
+    size_t hdr_bytes = ((size_t)m * splits * sizeof(CandHeader) + 255) / 256 * 256;
+    size_t cand_bytes = (size_t)m * splits * kCap * sizeof(float2);
+    void *w = nullptr;
+    DD_TRY(dd_workspace(ctx, WS_SEARCH, rec_bytes + hdr_bytes + cand_bytes, &w));
+    QueryRec *rec = reinterpret_cast<QueryRec *>(w);
+    CandHeader *hdr = reinterpret_cast<CandHeader *>(reinterpret_cast<char *>(w) + rec_bytes);
+    float2 *cand = reinterpret_cast<float2 *>(reinterpret_cast<char *>(w) + rec_bytes + hdr_bytes);
+
+    DD_TRY(dd_map_queries(ds, y_dev, m, nullptr, rec, s));
+    static bool attr_set = false;
+    if (!attr_set) {
+        DD_TRY_CUDA(ctx, cudaFuncSetAttribute(k_scan_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)kScanSmem));
+        attr_set = true;
+    }
+    dim3 grid((unsigned)qtiles, (unsigned)splits);
+    k_scan_fp32<<<grid, kThreads, kScanSmem, s>>>(ds->z32, ds->zn, ds->N, n_tiles, rec, m, splits, tps,
+                                                  hdr, cand, ctx->dev_err);
+    DD_TRY_CUDA(ctx, cudaGetLastError());
+    if (st) st->distances += m * ds->N;
+    return dd_merge_rescore(ds, y_dev, m, splits, kCap, hdr, cand, rec, certify, out, st, s);
+}

@@ -1,0 +1,81 @@
+"""GPU DD solve (Eq. 8) against the FP64 oracle's direct-solve iteration."""
+import numpy as np
+import pytest
+
+import dd_inputs as I
+from oracle import dd as odd
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2012_00357_gb300 as P  # noqa: E402
+
+C = I.isotropic_C()
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    P.build()
+    c = P.dd_create(0)
+    yield c
+    P.dd_destroy(c)
+
+
+def compare(r, o, rtol_u=1e-6):
+    assert r.converged == o.converged
+    assert r.iters == o.iters
+    assert np.array_equal(r.idx, o.idx)
+    scale = np.abs(o.u).max()
+    assert np.allclose(r.u, o.u, rtol=0, atol=rtol_u * scale)
+    assert np.allclose(r.eps, o.eps, rtol=0, atol=rtol_u * np.abs(o.eps).max())
+    assert np.allclose(r.sig, o.sig, rtol=0, atol=rtol_u * np.abs(o.sig).max())
+    assert np.allclose(r.d2_pd, o.d2_after_pd, rtol=1e-6)
+    assert np.allclose(r.d2_pc, o.d2_after_pc, rtol=1e-6)
+
+
+def test_cube4_N1e4_exact_matches_oracle(ctx):
+    """4^3 cube, N = 10^4 linear data, tension 1e-3, seed 0: iterate until the
+    association stops changing."""
+    W = I.WORKLOADS["cube4_N1e4_exact_fp64"]
+    data = I.make_dataset(W.N, W.law, seed=W.seed)
+    load = I.load_case(*W.loads[0])
+    init = I.initial_association(W.m, W.N, seed=W.seed)
+    ds = P.dd_load_dataset(ctx, data, C)
+    try:
+        r = P.dd_solve(ds, ctx, W.n_el, load, init_idx=init)
+    finally:
+        P.dd_free_dataset(ds)
+    o = odd.DDProblem(data, C, W.n_el, load).solve(init)
+    compare(r, o)
+    assert r.converged
+
+
+@pytest.mark.parametrize("case", ["shear", "bending", "torsion"])
+def test_load_cases_match_oracle(ctx, case):
+    data = I.make_dataset(4000, I.NONLINEAR, seed=2)
+    load = I.load_case(case, 1e-3)
+    init = I.initial_association(8 * 27, len(data), seed=4)
+    ds = P.dd_load_dataset(ctx, data, C)
+    try:
+        r = P.dd_solve(ds, ctx, 3, load, init_idx=init)
+    finally:
+        P.dd_free_dataset(ds)
+    o = odd.DDProblem(data, C, 3, load).solve(init)
+    compare(r, o)
+
+
+def test_monotone_distance_and_library_init(ctx):
+    data = I.make_dataset(6000, I.LINEAR, seed=9)
+    ds = P.dd_load_dataset(ctx, data, C)
+    try:
+        r = P.dd_solve(ds, ctx, 3, I.load_case("tension", 1e-3), seed=0)
+    finally:
+        P.dd_free_dataset(ds)
+    # the library's own initial association is the same SplitMix64 draw
+    o = odd.DDProblem(data, C, 3, I.load_case("tension", 1e-3)).solve(I.initial_association(216, 6000, seed=0))
+    compare(r, o)
+    tol = 1e-12 * r.d2_pc[0]
+    assert np.all(r.d2_pd <= r.d2_pc + tol) and np.all(r.d2_pc[1:] <= r.d2_pd[:-1] + tol)
