@@ -203,7 +203,8 @@ extern "C" void dd_free_dataset(dd_dataset *ds) {
     if (ds->owns_raw) dd_free(ctx, (void *)ds->raw, (size_t)ds->N * 48);
     dd_free(ctx, ds->z32, (size_t)ds->N_pad * 48);
     dd_free(ctx, ds->zn, (size_t)ds->N_pad * 4);
-    if (ds->z16) dd_free(ctx, ds->z16, (size_t)ds->N_pad * 32);
+    if (ds->z16hi) dd_free(ctx, ds->z16hi, (size_t)ds->N_pad * 32);
+    if (ds->z16lo) dd_free(ctx, ds->z16lo, (size_t)ds->N_pad * 32);
     dd_free_ann(ds);
     delete ds;
 }
@@ -221,7 +222,7 @@ static dd_status run_search(dd_dataset *ds, int mode, int certify, double f_d, c
     case DD_SEARCH_EXACT_FP32:
         return dd_search_exact_fp32(ds, y_dev, m, certify, out, st, s);
     case DD_SEARCH_EXACT_TC:
-        if (!ds->z16) return dd_fail(ds->ctx, DD_ERR_STATE, "tensor-core search needs the FP16 copy (build_fp16)");
+        if (!ds->z16hi) return dd_fail(ds->ctx, DD_ERR_STATE, "tensor-core search needs the FP16 copy (build_fp16)");
         return dd_search_exact_tc(ds, y_dev, m, certify, out, st, s);
     case DD_SEARCH_ANN:
         if (!ds->ann.nlist) return dd_fail(ds->ctx, DD_ERR_STATE, "ANN search needs the partition (ann_nlist)");

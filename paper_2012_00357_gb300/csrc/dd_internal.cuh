@@ -103,10 +103,11 @@ struct dd_dataset {
     double R = 0.0;              // max_j |z32_j|
     double maxabs = 0.0;         // max_j,k |z32_jk|
     MetricMaps M;
-    // tensor-core operand copy
-    __half *z16 = nullptr;       // UMMA canonical layout, see search_tc.cu
-    double scale16 = 0.0;        // power-of-two scale of the FP16 copy
-    double R16 = 0.0;            // max_j |z16_j| (scaled units)
+    // tensor-core operands (search_tc.cu): split FP16 copies of s*z32 in the
+    // UMMA canonical K-major layout, hi = fp16(s z), lo = fp16(s z - hi)
+    __half *z16hi = nullptr;     // [N_pad x 16]
+    __half *z16lo = nullptr;     // [N_pad x 16]
+    double scale16 = 0.0;        // power-of-two scale s
     AnnIndex ann;
     size_t bytes = 0;
 };
@@ -164,7 +165,7 @@ struct CandHeader {
 };
 dd_status dd_merge_rescore(dd_dataset *ds, const double *y_dev, int64_t m, int splits, int cap,
                            const CandHeader *hdr, const float2 *cand, const QueryRec *rec,
-                           int certify, SearchOut out, dd_search_stats *st, cudaStream_t s);
+                           int certify, double inv_s2, SearchOut out, dd_search_stats *st, cudaStream_t s);
 
 // Eq. (3) in FP64 between a state y (eps, sig) and data point j (raw FP32).
 __device__ __forceinline__ double dd_eq3(const MetricMaps &M, const double *y, const float *row) {
@@ -238,4 +239,89 @@ __device__ __forceinline__ void dd_bulk_g2s(uint32_t dst, const void *src, uint3
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
         "l"(src), "r"(bytes), "r"(bar)
         : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Candidate window of one query inside a low-precision scan.
+//
+// Every point whose score s lies within w2 of the running minimum mrun is
+// kept (w2 = twice the score error bound, so the exact nearest point is
+// always inside the final window).  The buffer holds `cap` entries; when it
+// is full of in-window entries the worst one is evicted and the smallest
+// evicted score is remembered in `dropped`: the result is certified exact
+// iff dropped > final mrun + w2.  In top-k mode (no certification wanted)
+// the entry threshold `lim` also falls to the buffer's worst score once it
+// is full, so the buffer ends as the best `cap` scores.
+// ---------------------------------------------------------------------------
+struct CandState {
+    float mrun, wl, lim, dropped;
+    int cnt;
+};
+
+__device__ __forceinline__ void cand_init(CandState &c, bool active) {
+    c.mrun = INFINITY;
+    c.wl = INFINITY;
+    c.lim = active ? INFINITY : -INFINITY;
+    c.dropped = INFINITY;
+    c.cnt = 0;
+}
+
+// buf: this query's entry 0; consecutive entries are `st` float2 apart.
+__device__ __forceinline__ void cand_insert(CandState &c, float s, int j, float w2, float2 *buf, int st, int cap,
+                                            bool topk) {
+    if (s < c.mrun) {
+        c.mrun = s;
+        c.wl = s + w2;
+    }
+    if (!(s <= c.wl)) return;
+    if (c.cnt == cap) {
+        int c2 = 0;
+        for (int e = 0; e < cap; ++e) {
+            float2 v = buf[e * st];
+            if (v.x <= c.wl) buf[(c2++) * st] = v;
+        }
+        c.cnt = c2;
+    }
+    if (c.cnt < cap) {
+        buf[c.cnt * st] = make_float2(s, __int_as_float(j));
+        c.cnt++;
+    } else {
+        int pm = 0;
+        float mx = buf[0].x;
+        for (int e = 1; e < cap; ++e) {
+            float v = buf[e * st].x;
+            if (v > mx) {
+                mx = v;
+                pm = e;
+            }
+        }
+        if (s < mx) {
+            c.dropped = fminf(c.dropped, mx);
+            buf[pm * st] = make_float2(s, __int_as_float(j));
+        } else {
+            c.dropped = fminf(c.dropped, s);
+        }
+    }
+    c.lim = c.wl;
+    if (topk && c.cnt == cap) {
+        float mx = buf[0].x;
+        for (int e = 1; e < cap; ++e) mx = fmaxf(mx, buf[e * st].x);
+        c.lim = fminf(c.wl, mx);
+    }
+}
+
+// Write the window's surviving entries and header for (query slot).
+__device__ __forceinline__ void cand_store(const CandState &c, const float2 *buf, int st, int cap, size_t slot,
+                                           CandHeader *hdr, float2 *cand) {
+    int c2 = 0;
+    for (int e = 0; e < c.cnt; ++e) {
+        float2 v = buf[e * st];
+        if (v.x <= c.wl) cand[slot * cap + (c2++)] = v;
+    }
+    CandHeader h;
+    h.mrun = c.mrun;
+    h.dropped = c.dropped;
+    h.cnt = c2;
+    h.pad = 0;
+    hdr[slot] = h;
 }

@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     k_scan_fp32(const float *__restrict__ z32, const float *__restrict__ zn, int64_t N,
                 int64_t n_tiles, const QueryRec *__restrict__ rec, int64_t m, int splits,
                 int64_t tiles_per_split, CandHeader *__restrict__ hdr, float2 *__restrict__ cand,
-                unsigned *__restrict__ err) {
+                bool topk, unsigned *__restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem[];
     float *sz = reinterpret_cast<float *>(smem);
     float *sn = sz + kStages * kT * 12;
@@ -99,24 +99,20 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int64_t t_end = min(n_tiles, t_begin + tiles_per_split);
     const int64_t ntl = t_end > t_begin ? t_end - t_begin : 0;
 
-    float q[kRQ][12], lim[kRQ], w2[kRQ], mrun[kRQ], dropped[kRQ];
-    int cnt[kRQ];
+    float q[kRQ][12], w2[kRQ];
+    CandState cs[kRQ];
 #pragma unroll
     for (int r = 0; r < kRQ; ++r) {
         int64_t qi = qbase + r * kThreads + tid;
-        mrun[r] = INFINITY;
-        dropped[r] = INFINITY;
-        cnt[r] = 0;
+        cand_init(cs[r], qi < m);
         if (qi < m) {
 #pragma unroll
             for (int k = 0; k < 12; ++k) q[r][k] = -2.0f * rec[qi].q[k];
             w2[r] = rec[qi].w2;
-            lim[r] = INFINITY;
         } else {
 #pragma unroll
             for (int k = 0; k < 12; ++k) q[r][k] = 0.f;
             w2[r] = 0.f;
-            lim[r] = -INFINITY;
         }
     }
 
@@ -166,35 +162,16 @@ __global__ void __launch_bounds__(kThreads, 2)
                 v = fmaf(q[r][10], c.z, v);
                 v = fmaf(q[r][11], c.w, v);
                 sc[r] = v;
-                any |= (v <= lim[r]);
+                any |= (v <= cs[r].lim);
             }
             if (any) {
                 const int64_t j = j0 + p;
                 if (j < N) {
 #pragma unroll
-                    for (int r = 0; r < kRQ; ++r) {
-                        if (sc[r] <= lim[r]) {
-                            if (sc[r] < mrun[r]) {
-                                mrun[r] = sc[r];
-                                lim[r] = sc[r] + w2[r];
-                            }
-                            float2 *bq = buf + (size_t)r * kCap * kThreads + tid;
-                            if (cnt[r] == kCap) {
-                                int c2 = 0;
-                                for (int e = 0; e < kCap; ++e) {
-                                    float2 v = bq[e * kThreads];
-                                    if (v.x <= lim[r]) bq[(c2++) * kThreads] = v;
-                                }
-                                cnt[r] = c2;
-                            }
-                            if (cnt[r] < kCap) {
-                                bq[cnt[r] * kThreads] = make_float2(sc[r], __int_as_float((int)j));
-                                cnt[r]++;
-                            } else {
-                                dropped[r] = fminf(dropped[r], sc[r]);
-                            }
-                        }
-                    }
+                    for (int r = 0; r < kRQ; ++r)
+                        if (sc[r] <= cs[r].lim)
+                            cand_insert(cs[r], sc[r], (int)j, w2[r], buf + (size_t)r * kCap * kThreads + tid,
+                                        kThreads, kCap, topk);
                 }
             }
         }
@@ -212,19 +189,8 @@ __global__ void __launch_bounds__(kThreads, 2)
     for (int r = 0; r < kRQ; ++r) {
         int64_t qi = qbase + r * kThreads + tid;
         if (qi >= m) continue;
-        const size_t slot = (size_t)qi * splits + split;
-        const float2 *bq = buf + (size_t)r * kCap * kThreads + tid;
-        int c2 = 0;
-        for (int e = 0; e < cnt[r]; ++e) {
-            float2 v = bq[e * kThreads];
-            if (v.x <= lim[r]) cand[slot * kCap + (c2++)] = v;
-        }
-        CandHeader h;
-        h.mrun = mrun[r];
-        h.dropped = dropped[r];
-        h.cnt = c2;
-        h.pad = 0;
-        hdr[slot] = h;
+        cand_store(cs[r], buf + (size_t)r * kCap * kThreads + tid, kThreads, kCap, (size_t)qi * splits + split, hdr,
+                   cand);
     }
 }
 
@@ -234,7 +200,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 __global__ void k_merge_rescore(const float *__restrict__ raw, MetricMaps M,
                                 const double *__restrict__ y, int64_t m, int splits, int cap,
                                 const CandHeader *__restrict__ hdr, const float2 *__restrict__ cand,
-                                const QueryRec *__restrict__ rec, int certify,
+                                const QueryRec *__restrict__ rec, int certify, double inv_s2,
                                 int32_t *__restrict__ idx, double *__restrict__ d2,
                                 double *__restrict__ d2nd, int64_t *__restrict__ fb_list,
                                 unsigned long long *__restrict__ fb_count) {
@@ -269,8 +235,9 @@ __global__ void k_merge_rescore(const float *__restrict__ raw, MetricMaps M,
         }
     }
     if (bj < 0) uncert = true;
-    // every point outside the window has |z - q|^2 >= gmin + qn + w2/2
-    double lb = 2.0 * ((double)gmin + (double)rec[i].qn + 0.5 * (double)w2);
+    // every point outside the window has |z - q|^2 >= gmin + qn + w2/2 (in
+    // score units; inv_s2 converts to the mapped coordinates)
+    double lb = 2.0 * inv_s2 * ((double)gmin + (double)rec[i].qn + 0.5 * (double)w2);
     if (uncert && certify) {
         unsigned long long k = atomicAdd(fb_count, 1ull);
         fb_list[k] = i;
@@ -369,7 +336,7 @@ dd_status dd_map_queries(dd_dataset *ds, const double *y_dev, int64_t m, double 
 
 dd_status dd_merge_rescore(dd_dataset *ds, const double *y_dev, int64_t m, int splits, int cap,
                            const CandHeader *hdr, const float2 *cand, const QueryRec *rec,
-                           int certify, SearchOut out, dd_search_stats *st, cudaStream_t s) {
+                           int certify, double inv_s2, SearchOut out, dd_search_stats *st, cudaStream_t s) {
     dd_ctx *ctx = ds->ctx;
     void *w = nullptr;
     size_t need = (size_t)m * sizeof(int64_t) + 256;
@@ -378,7 +345,7 @@ dd_status dd_merge_rescore(dd_dataset *ds, const double *y_dev, int64_t m, int s
     int64_t *fb_list = reinterpret_cast<int64_t *>(reinterpret_cast<char *>(w) + 256);
     DD_TRY_CUDA(ctx, cudaMemsetAsync(fb_count, 0, sizeof(unsigned long long), s));
     k_merge_rescore<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(
-        ds->raw, ds->M, y_dev, m, splits, cap, hdr, cand, rec, certify, out.idx, out.d2, out.d2nd,
+        ds->raw, ds->M, y_dev, m, splits, cap, hdr, cand, rec, certify, inv_s2, out.idx, out.d2, out.d2nd,
         fb_list, fb_count);
     DD_TRY_CUDA(ctx, cudaGetLastError());
     if (certify) {
@@ -416,16 +383,11 @@ dd_status dd_search_exact_fp32(dd_dataset *ds, const double *y_dev, int64_t m, i
     float2 *cand = reinterpret_cast<float2 *>(reinterpret_cast<char *>(w) + rec_bytes + hdr_bytes);
 
     DD_TRY(dd_map_queries(ds, y_dev, m, nullptr, rec, s));
-    static bool attr_set = false;
-    if (!attr_set) {
-        DD_TRY_CUDA(ctx, cudaFuncSetAttribute(k_scan_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)kScanSmem));
-        attr_set = true;
-    }
+    DD_TRY_CUDA(ctx, cudaFuncSetAttribute(k_scan_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScanSmem));
     dim3 grid((unsigned)qtiles, (unsigned)splits);
     k_scan_fp32<<<grid, kThreads, kScanSmem, s>>>(ds->z32, ds->zn, ds->N, n_tiles, rec, m, splits, tps,
-                                                  hdr, cand, ctx->dev_err);
+                                                  hdr, cand, certify == 0, ctx->dev_err);
     DD_TRY_CUDA(ctx, cudaGetLastError());
     if (st) st->distances += m * ds->N;
-    return dd_merge_rescore(ds, y_dev, m, splits, kCap, hdr, cand, rec, certify, out, st, s);
+    return dd_merge_rescore(ds, y_dev, m, splits, kCap, hdr, cand, rec, certify, 1.0, out, st, s);
 }

@@ -1,11 +1,492 @@
-// Tensor-core exact search: placeholder until the tcgen05 kernel lands.
+// Exact data projection P_D (Eq. 7) as a dense contraction on the 5th-gen
+// tensor cores (tcgen05, accumulators in TMEM).
+//
+// The squared distance |z_j - q|^2 = |q|^2 + (|z_j|^2 - 2 z_j . q) is a
+// rank-16 contraction: with the query row A = (q, 1, 1, 0, 0) and the data
+// row B_j = (-2 z_j, |z_j|^2 split in two FP16 terms, 0, 0), D = A B^T holds
+// the score |z_j|^2 - 2 z_j . q of every (query, point) pair.  Inputs are
+// FP16 (coordinates centred and scaled by a power of two s so that
+// |s z| <= 32), products are exact and accumulate in FP32.
+//
+// Two precisions:
+//  * KC = 1: one MMA (K = 16) per tile; FP16 quantisation limits the score
+//    error to about 2^-10 (R + |q|)^2, so the candidate window is wide and
+//    the kernel keeps the best `cap` scores (top-k) for FP64 rescoring.
+//  * KC = 3: split FP16 (x = hi + lo for data and query): three MMAs
+//    (q_hi.x_hi + q_lo.x_hi + q_hi.x_lo) give ~22-bit operands, the window
+//    is narrow and the result is certified exact like the FP32 scan.
+//
+// Pipeline per CTA (one 128-query tile x one range of 128-point data tiles):
+//   warp 0        TMA producer: 1-D bulk copies of the pre-laid-out FP16
+//                 operand tiles into a ring of shared-memory stages
+//   warp 1        TMEM allocator and single-thread MMA issuer; accumulators
+//                 double-buffered in TMEM (2 x 128 columns)
+//   warps 2..5    epilogue: tcgen05.ld of one query row per thread, a
+//                 3-input-min gate and the candidate window (dd_internal.cuh)
+// Every mbarrier wait is bounded; on a timeout the kernel flags the error,
+// stops issuing work, drains what is in flight and frees TMEM.
+//
+// Operand layout (UMMA canonical K-major, no swizzle): each group of 8 rows
+// is 256 bytes = two 8x16-byte core matrices (K elements 0..7, then 8..15);
+// groups are contiguous, so LBO = 128 B and SBO = 256 B, and a 128-row tile
+// is one contiguous 4 KB block that a single bulk copy moves.
+#include <cmath>
+
 #include "dd_internal.cuh"
 
-dd_status dd_build_fp16(dd_dataset *ds) {
-    return dd_fail(ds->ctx, DD_ERR_STATE, "tensor-core search not built yet");
+namespace {
+
+constexpr int kTN = 128;            // data points per tile (MMA N)
+constexpr int kTM = 128;            // queries per CTA (MMA M)
+constexpr int kStages = 6;
+constexpr int kCap = 8;
+constexpr int kThreadsTC = 192;
+constexpr uint32_t kTileBytes = 4096;   // 128 rows x 16 fp16
+constexpr uint32_t kTmemCols = 256;
+
+// ---- PTX wrappers --------------------------------------------------------
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);          // start address
+    d |= (uint64_t)(128u >> 4) << 16;                  // LBO: next core matrix along K
+    d |= (uint64_t)(256u >> 4) << 32;                  // SBO: next 8-row group
+    d |= (uint64_t)1 << 46;                            // descriptor version
+    return d;                                          // base offset 0, no swizzle
 }
 
-dd_status dd_search_exact_tc(dd_dataset *ds, const double *, int64_t, int, SearchOut, dd_search_stats *,
-                             cudaStream_t) {
-    return dd_fail(ds->ctx, DD_ERR_STATE, "tensor-core search not built yet");
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+    return (1u << 4)                       // D format F32
+           | (0u << 7) | (0u << 10)        // A, B format F16
+           | ((uint32_t)(N >> 3) << 17)    // N
+           | ((uint32_t)(M >> 4) << 24);   // M
+}
+
+__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%"
+        "28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+__device__ __forceinline__ float min32(const float (&v)[32]) {
+    float a[11];
+#pragma unroll
+    for (int i = 0; i < 10; ++i) a[i] = min3f(v[3 * i], v[3 * i + 1], v[3 * i + 2]);
+    a[10] = fminf(v[30], v[31]);
+    float b0 = min3f(a[0], a[1], a[2]), b1 = min3f(a[3], a[4], a[5]), b2 = min3f(a[6], a[7], a[8]);
+    float b3 = fminf(a[9], a[10]);
+    return fminf(min3f(b0, b1, b2), b3);
+}
+
+// Offset of (row, k) inside a tile in the canonical layout (bytes).
+__host__ __device__ __forceinline__ uint32_t canon_off(int row, int k) {
+    return (uint32_t)((row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+// ---- data operands ---------------------------------------------------------
+// hi tile row j: (-2 x_hi, split |x_hi|^2, 0, 0); lo tile row j: (-2 x_lo,
+// split (|x_hi + x_lo|^2 - |x_hi|^2), 0, 0), x = s * z32_j.
+__global__ void k_build_fp16(const float *__restrict__ z32, int64_t N, int64_t N_pad, float s,
+                             __half *__restrict__ zhi, __half *__restrict__ zlo) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= N_pad) return;
+    __half h[16], l[16];
+    if (j < N) {
+        double nh = 0.0, nt = 0.0;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            float x = z32[j * 12 + k] * s;
+            __half xh = __float2half_rn(x);
+            float r = x - __half2float(xh);
+            __half xl = __float2half_rn(r);
+            double a = (double)__half2float(xh), b = (double)__half2float(xl);
+            nh += a * a;
+            nt += (a + b) * (a + b);
+            h[k] = __float2half_rn(-2.0f * __half2float(xh));
+            l[k] = __float2half_rn(-2.0f * __half2float(xl));
+        }
+        double c = nt - nh;
+        __half nh0 = __double2half(nh);
+        __half nh1 = __double2half(nh - (double)__half2float(nh0));
+        __half c0 = __double2half(c);
+        __half c1 = __double2half(c - (double)__half2float(c0));
+        h[12] = nh0;
+        h[13] = nh1;
+        l[12] = c0;
+        l[13] = c1;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) h[k] = l[k] = __float2half_rn(0.f);
+        h[12] = h[13] = __float2half_rn(30000.f);   // padding rows never win
+        l[12] = l[13] = __float2half_rn(0.f);
+    }
+    h[14] = h[15] = l[14] = l[15] = __float2half_rn(0.f);
+    const int64_t tile = j / kTN;
+    const int row = (int)(j % kTN);
+    char *ph = reinterpret_cast<char *>(zhi) + tile * kTileBytes;
+    char *pl = reinterpret_cast<char *>(zlo) + tile * kTileBytes;
+#pragma unroll
+    for (int half8 = 0; half8 < 2; ++half8) {
+        uint4 vh, vl;
+        __half *th = reinterpret_cast<__half *>(&vh), *tl = reinterpret_cast<__half *>(&vl);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            th[k] = h[8 * half8 + k];
+            tl[k] = l[8 * half8 + k];
+        }
+        *reinterpret_cast<uint4 *>(ph + canon_off(row, 8 * half8)) = vh;
+        *reinterpret_cast<uint4 *>(pl + canon_off(row, 8 * half8)) = vl;
+    }
+}
+
+// ---- query operands ----------------------------------------------------------
+// A chunks per 128-query tile (each 4 KB): A0 = (q_hi, 1, 1), A1 = (q_lo, 0, 0),
+// A2 = (q_hi, 1, 1).  KC = 1 uses A0 only.  rec: window and |q~|^2 (scaled).
+__global__ void k_prep_tc(const double *__restrict__ y, int64_t m, int64_t m_pad, MetricMaps M, double s, double Rs,
+                          int kc, __half *__restrict__ qa, QueryRec *__restrict__ rec) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= m_pad) return;
+    __half hq[16], lq[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) hq[k] = lq[k] = __float2half_rn(0.f);
+    if (i < m) {
+        double z[12], sy[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) sy[k] = y[i * 12 + k];
+        const double r2 = 0.70710678118654752440;
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+            double e = 0.0, g = 0.0;
+#pragma unroll
+            for (int b = 0; b < 6; ++b) {
+                e += M.Ch[6 * a + b] * sy[b];
+                g += M.Cmh[6 * a + b] * sy[6 + b];
+            }
+            z[a] = (e * r2 - M.mu[a]) * s;
+            z[6 + a] = (g * r2 - M.mu[6 + a]) * s;
+        }
+        bool in_range = true;
+        double qn = 0.0, qs = 0.0;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            in_range &= fabs(z[k]) < 30000.0;
+            qs += z[k] * z[k];
+        }
+        if (in_range) {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                hq[k] = __double2half(z[k]);
+                double h = (double)__half2float(hq[k]);
+                lq[k] = __double2half(z[k] - h);
+                double t = (kc == 3) ? h + (double)__half2float(lq[k]) : h;
+                qn += t * t;
+            }
+            hq[12] = hq[13] = __float2half_rn(1.f);
+        }
+        QueryRec r;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) r.q[k] = 0.f;
+        double B = Rs + sqrt(qs);
+        double E = (kc == 3) ? ldexp(B * B, -15) : 1.05 * ldexp(B * B, -10);
+        E += ldexp(1.0, -18);
+        r.w2 = in_range ? (float)(2.0 * E) : INFINITY;
+        r.qn = (float)qn;
+        r.pad[0] = r.pad[1] = 0.f;
+        rec[i] = r;
+    }
+    const int64_t tile = i / kTM;
+    const int row = (int)(i % kTM);
+    char *base = reinterpret_cast<char *>(qa) + tile * (int64_t)kc * kTileBytes;
+#pragma unroll
+    for (int half8 = 0; half8 < 2; ++half8) {
+        uint4 v0, v1;
+        __half *t0 = reinterpret_cast<__half *>(&v0), *t1 = reinterpret_cast<__half *>(&v1);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            t0[k] = hq[8 * half8 + k];
+            t1[k] = (8 * half8 + k < 12) ? lq[8 * half8 + k] : __float2half_rn(0.f);
+        }
+        *reinterpret_cast<uint4 *>(base + canon_off(row, 8 * half8)) = v0;
+        if (kc == 3) {
+            *reinterpret_cast<uint4 *>(base + kTileBytes + canon_off(row, 8 * half8)) = v1;
+            *reinterpret_cast<uint4 *>(base + 2 * kTileBytes + canon_off(row, 8 * half8)) = v0;
+        }
+    }
+}
+
+// ---- the contraction kernel ------------------------------------------------------
+template <int KC>
+__global__ void __launch_bounds__(kThreadsTC, 2)
+    k_scan_tc(const __half *__restrict__ zhi, const __half *__restrict__ zlo, int64_t N, int64_t n_tiles,
+              const __half *__restrict__ qa, const QueryRec *__restrict__ rec, int64_t m, int splits, int64_t tps,
+              CandHeader *__restrict__ hdr, float2 *__restrict__ cand, bool topk, unsigned *__restrict__ err) {
+    constexpr uint32_t kStageBytes = (KC == 1 ? 1 : 2) * kTileBytes;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *sA = smem;                                   // KC * 4 KB
+    unsigned char *sB = smem + KC * kTileBytes;                 // kStages * stage
+    float2 *sCand = reinterpret_cast<float2 *>(sB + kStages * kStageBytes);   // kCap x 128
+    __shared__ __align__(8) uint64_t bar_full[kStages], bar_empty[kStages], bar_tfull[2], bar_tempty[2], bar_a,
+        bar_done;
+    __shared__ uint32_t tmem_slot;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int split = blockIdx.y;
+    const int64_t t_begin = split * tps;
+    const int64_t t_end = min(n_tiles, t_begin + tps);
+    const int64_t ntl = t_end > t_begin ? t_end - t_begin : 0;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            dd_mbar_init(dd_smem_addr(&bar_full[s]), 1);
+            dd_mbar_init(dd_smem_addr(&bar_empty[s]), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            dd_mbar_init(dd_smem_addr(&bar_tfull[a]), 1);
+            dd_mbar_init(dd_smem_addr(&bar_tempty[a]), 4);
+        }
+        dd_mbar_init(dd_smem_addr(&bar_a), 1);
+        dd_mbar_init(dd_smem_addr(&bar_done), 1);
+        dd_fence_mbar_init();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         dd_smem_addr(&tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- producer ----------------
+            bool ok = true;
+            const char *ga = reinterpret_cast<const char *>(qa) + (int64_t)blockIdx.x * KC * kTileBytes;
+            dd_mbar_expect_tx(dd_smem_addr(&bar_a), KC * kTileBytes);
+            dd_bulk_g2s(dd_smem_addr(sA), ga, KC * kTileBytes, dd_smem_addr(&bar_a));
+            int64_t issued = 0;
+            for (int64_t t = 0; t < ntl; ++t) {
+                const int s = (int)(t % kStages);
+                if (t >= kStages && !dd_mbar_wait(dd_smem_addr(&bar_empty[s]), (uint32_t)(((t / kStages) - 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t bf = dd_smem_addr(&bar_full[s]);
+                const int64_t tile = t_begin + t;
+                dd_mbar_expect_tx(bf, kStageBytes);
+                dd_bulk_g2s(dd_smem_addr(sB + s * kStageBytes), reinterpret_cast<const char *>(zhi) + tile * kTileBytes,
+                            kTileBytes, bf);
+                if (KC == 3)
+                    dd_bulk_g2s(dd_smem_addr(sB + s * kStageBytes + kTileBytes),
+                                reinterpret_cast<const char *>(zlo) + tile * kTileBytes, kTileBytes, bf);
+                issued = t + 1;
+            }
+            if (!ok) {
+                atomicOr(err, DEV_ERR_TIMEOUT);
+                // drain: wait (bounded) for every issued copy that nobody consumed
+                for (int64_t t = (issued > kStages ? issued - kStages : 0); t < issued; ++t)
+                    dd_mbar_wait(dd_smem_addr(&bar_full[t % kStages]), (uint32_t)((t / kStages) & 1));
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            bool ok = dd_mbar_wait(dd_smem_addr(&bar_a), 0);
+            constexpr uint32_t idesc = idesc_f16(kTM, kTN);
+            const uint32_t a0 = dd_smem_addr(sA);
+            for (int64_t t = 0; ok && t < ntl; ++t) {
+                const int s = (int)(t % kStages);
+                const int ab = (int)(t & 1);
+                if (!dd_mbar_wait(dd_smem_addr(&bar_full[s]), (uint32_t)((t / kStages) & 1))) {
+                    ok = false;
+                    break;
+                }
+                if (t >= 2 && !dd_mbar_wait(dd_smem_addr(&bar_tempty[ab]), (uint32_t)(((t >> 1) - 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)ab * kTN;
+                const uint32_t bh = dd_smem_addr(sB + s * kStageBytes);
+                umma_f16(d, umma_desc(a0), umma_desc(bh), idesc, 0u);
+                if (KC == 3) {
+                    umma_f16(d, umma_desc(a0 + kTileBytes), umma_desc(bh), idesc, 1u);
+                    umma_f16(d, umma_desc(a0 + 2 * kTileBytes), umma_desc(bh + kTileBytes), idesc, 1u);
+                }
+                umma_commit(dd_smem_addr(&bar_empty[s]));
+                umma_commit(dd_smem_addr(&bar_tfull[ab]));
+            }
+            if (!ok) atomicOr(err, DEV_ERR_TIMEOUT);
+            // all issued MMAs complete before TMEM is released
+            umma_commit(dd_smem_addr(&bar_done));
+            if (!dd_mbar_wait(dd_smem_addr(&bar_done), 0)) atomicOr(err, DEV_ERR_TIMEOUT);
+        }
+    } else {
+        // ---------------- epilogue: one query row per thread ----------------
+        const int quarter = warp & 3;
+        const int row = quarter * 32 + lane;
+        const int64_t qi = (int64_t)blockIdx.x * kTM + row;
+        const bool active = qi < m;
+        const float w2 = active ? rec[qi].w2 : 0.f;
+        CandState cs;
+        cand_init(cs, active);
+        float2 *buf = sCand + row;
+        bool ok = true;
+        for (int64_t t = 0; t < ntl; ++t) {
+            const int ab = (int)(t & 1);
+            // warp-uniform outcome: tcgen05.ld below is .sync.aligned
+            ok = __all_sync(0xffffffffu, dd_mbar_wait(dd_smem_addr(&bar_tfull[ab]), (uint32_t)((t >> 1) & 1)));
+            if (!ok) {
+                if (lane == 0) atomicOr(err, DEV_ERR_TIMEOUT);
+                break;
+            }
+            tc_fence_after();
+            const int64_t jb = (t_begin + t) * kTN;
+#pragma unroll 1
+            for (int c = 0; c < kTN / 32; ++c) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)ab * kTN + (uint32_t)c * 32, v);
+                if (c == kTN / 32 - 1) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) dd_mbar_arrive(dd_smem_addr(&bar_tempty[ab]));
+                }
+                const float mn = min32(v);
+                if (mn <= cs.lim) {
+                    const int64_t j0 = jb + c * 32;
+#pragma unroll
+                    for (int k = 0; k < 32; ++k)
+                        if (v[k] <= cs.lim && j0 + k < N)
+                            cand_insert(cs, v[k], (int)(j0 + k), w2, buf, kTM, kCap, topk);
+                }
+            }
+        }
+        if (active) cand_store(cs, buf, kTM, kCap, (size_t)qi * splits + split, hdr, cand);
+    }
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+template <int KC>
+size_t tc_smem_bytes() {
+    size_t s = KC * kTileBytes + kStages * (KC == 1 ? 1 : 2) * kTileBytes + kCap * kTM * 8 + 1024;
+    return s < 100 * 1024 ? 100 * 1024 : s;   // at most two CTAs (2 x 256 TMEM columns) per SM
+}
+
+int pick_splits_tc(int64_t qtiles, int64_t n_tiles, int n_sm) {
+    const int64_t slots = (int64_t)n_sm * 2;
+    if (qtiles >= slots) return 1;
+    int64_t best_s = 1;
+    double best_eff = 0.0;
+    for (int64_t s = 1; s <= slots && s <= n_tiles; ++s) {
+        int64_t ctas = qtiles * s;
+        int64_t waves = (ctas + slots - 1) / slots;
+        double eff = (double)ctas / (double)(waves * slots);
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best_s = s;
+        }
+        if (ctas >= slots && eff > 0.94) break;
+    }
+    return (int)best_s;
+}
+
+}  // namespace
+
+dd_status dd_build_fp16(dd_dataset *ds) {
+    dd_ctx *ctx = ds->ctx;
+    if (ds->z16hi) return DD_OK;
+    // power-of-two scale with max |s z| <= 32
+    double mx = ds->maxabs > 0 ? ds->maxabs : 1.0;
+    ds->scale16 = std::ldexp(1.0, (int)std::floor(std::log2(32.0 / mx)));
+    void *p = nullptr;
+    DD_TRY(dd_alloc(ctx, &p, (size_t)ds->N_pad * 32, "fp16 operands"));
+    ds->z16hi = (__half *)p;
+    DD_TRY(dd_alloc(ctx, &p, (size_t)ds->N_pad * 32, "fp16 operands"));
+    ds->z16lo = (__half *)p;
+    ds->bytes += (size_t)ds->N_pad * 64;
+    k_build_fp16<<<(unsigned)((ds->N_pad + 255) / 256), 256, 0, ctx->stream>>>(ds->z32, ds->N, ds->N_pad,
+                                                                               (float)ds->scale16, ds->z16hi, ds->z16lo);
+    DD_TRY_CUDA(ctx, cudaGetLastError());
+    return DD_OK;
+}
+
+dd_status dd_search_exact_tc(dd_dataset *ds, const double *y_dev, int64_t m, int certify, SearchOut out,
+                             dd_search_stats *st, cudaStream_t s) {
+    dd_ctx *ctx = ds->ctx;
+    if (m == 0) return DD_OK;
+    const int kc = certify ? 3 : 1;
+    const int64_t n_tiles = (ds->N + kTN - 1) / kTN;
+    const int64_t qtiles = (m + kTM - 1) / kTM;
+    const int64_t m_pad = qtiles * kTM;
+    const int splits = pick_splits_tc(qtiles, n_tiles, ctx->n_sm);
+    const int64_t tps = (n_tiles + splits - 1) / splits;
+    auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
+    size_t qa_bytes = r256((size_t)qtiles * kc * kTileBytes);
+    size_t rec_bytes = r256((size_t)m * sizeof(QueryRec));
+    size_t hdr_bytes = r256((size_t)m * splits * sizeof(CandHeader));
+    size_t cand_bytes = (size_t)m * splits * kCap * sizeof(float2);
+    void *w = nullptr;
+    DD_TRY(dd_workspace(ctx, WS_TC, qa_bytes + rec_bytes + hdr_bytes + cand_bytes, &w));
+    char *c = (char *)w;
+    __half *qa = (__half *)c;
+    QueryRec *rec = (QueryRec *)(c + qa_bytes);
+    CandHeader *hdr = (CandHeader *)(c + qa_bytes + rec_bytes);
+    float2 *cand = (float2 *)(c + qa_bytes + rec_bytes + hdr_bytes);
+
+    const double Rs = ds->R * ds->scale16 * (1.0 + 1e-6);
+    k_prep_tc<<<(unsigned)((m_pad + 127) / 128), 128, 0, s>>>(y_dev, m, m_pad, ds->M, ds->scale16, Rs, kc, qa, rec);
+    DD_TRY_CUDA(ctx, cudaGetLastError());
+    dim3 grid((unsigned)qtiles, (unsigned)splits);
+    if (kc == 3) {
+        size_t sm = tc_smem_bytes<3>();
+        DD_TRY_CUDA(ctx, cudaFuncSetAttribute(k_scan_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_scan_tc<3><<<grid, kThreadsTC, sm, s>>>(ds->z16hi, ds->z16lo, ds->N, n_tiles, qa, rec, m, splits, tps, hdr,
+                                                  cand, false, ctx->dev_err);
+    } else {
+        size_t sm = tc_smem_bytes<1>();
+        DD_TRY_CUDA(ctx, cudaFuncSetAttribute(k_scan_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_scan_tc<1><<<grid, kThreadsTC, sm, s>>>(ds->z16hi, ds->z16lo, ds->N, n_tiles, qa, rec, m, splits, tps, hdr,
+                                                  cand, true, ctx->dev_err);
+    }
+    DD_TRY_CUDA(ctx, cudaGetLastError());
+    if (st) st->distances += m * ds->N;
+    return dd_merge_rescore(ds, y_dev, m, splits, kCap, hdr, cand, rec, certify, 1.0 / (ds->scale16 * ds->scale16), out, st, s);
 }
