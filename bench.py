@@ -1,0 +1,332 @@
+"""Benchmark of the data-driven (DD) hot path on GB300.
+
+A step is one DD iteration z_{i+1} = P_D(P_C(z_i)) of a running solve
+(assembly of E and S, FP64 CG for both systems, recovery, nearest-data
+projection of every material point, convergence statistics) through the
+library's C ABI.  `value` = material-point searches per second over the
+timed steps (whole job, all ranks).  Under torchrun every rank runs an
+independent replica (the search does not shard).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload NAME] [--mode tc|fp32|tc_topk]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import dd_inputs as I  # noqa: E402
+
+METRIC = "DD searches/s & solve time at N=1e9 (ANN vs exact); p50/p99 serve latency"
+UNIT = "searches/s"
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+L2_BYTES = 129 * 2 ** 20
+
+
+def load_peaks():
+    try:
+        with open(PEAKS) as f:
+            p = json.load(f)
+        return {"hbm_gbs": p["hbm_gbs"], "bf16_tflops": p["bf16_tflops"],
+                "bf16_tflops_sustained": p.get("bf16_tflops_sustained"), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 5 + i and r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo", init_method="env://")
+    return world, rank, local
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ----------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle's brute-force P_D on a bounded query sample
+# ----------------------------------------------------------------------------
+def oracle_searches_per_s(W: I.Workload, C, target_s: float = 12.0, max_queries: int = 4096):
+    from oracle import metric, nn
+    t0 = time.time()
+    data = I.make_dataset(W.N, W.law, seed=W.seed)
+    Z = metric.to_z(data, C)
+    gen_s = time.time() - t0
+    y = I.make_states(max_queries, W.law, seed=99, spread=0.05)
+    zq = metric.to_z(y, C)
+    t = time.perf_counter()
+    nn.nn_top2(Z, zq[:16])
+    dt = time.perf_counter() - t
+    rate = 16 / max(dt, 1e-9)
+    n = int(min(max_queries, max(16, rate * target_s)))
+    t = time.perf_counter()
+    nn.nn_top2(Z, zq[:n])
+    dt = time.perf_counter() - t
+    return {"value": n / dt, "unit": UNIT, "cores": nn.threads(), "kind": "oracle",
+            "sample": f"{n} query states x all {W.N} data points, brute-force FP64 scan (oracle/nn.c); "
+                      f"data generation {gen_s:.1f}s not timed"}
+
+
+# ----------------------------------------------------------------------------
+def make_workload(name: str):
+    W = I.WORKLOADS[name]
+    return W
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    import paper_2012_00357_gb300 as P
+
+    P.build()
+    torch.cuda.set_device(local)
+    W = make_workload(args.workload)
+    C = I.isotropic_C(W.law.E, W.law.nu)
+    mode = {"tc": P.DD_SEARCH_EXACT_TC, "tc_topk": P.DD_SEARCH_EXACT_TC, "fp32": P.DD_SEARCH_EXACT_FP32}[args.mode]
+    certify = args.mode != "tc_topk"
+    ctx = P.dd_create(local)
+    raw = torch.empty((W.N, 12), dtype=torch.float32, device="cuda")
+    P.dd_synth_dataset(ctx, raw, W.law, C, seed=W.seed)
+    ds = P.dd_load_dataset(ctx, raw, C, borrow=True, build_fp16=(mode == P.DD_SEARCH_EXACT_TC))
+    load = I.load_case(*W.loads[0])
+    init = I.initial_association(W.m, W.N, seed=W.seed)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    data_bytes = W.N * (64 if mode == P.DD_SEARCH_EXACT_TC else 52)
+    flush_l2 = data_bytes < 2 * L2_BYTES
+
+    def new_solver():
+        return P.dd_solver_create(ds, ctx, W.n_el, load, mode=mode, certify=certify, init_idx=init,
+                                  max_iter=100000)
+
+    sv = new_solver()
+    for _ in range(args.warmup):
+        if P.dd_solver_done(sv):
+            P.dd_solver_free(sv)
+            sv = new_solver()
+        P.dd_solver_step(sv, ctx)
+
+    barrier(world)
+    torch.cuda.synchronize()
+    step_ms, scan_ms, infos = [], [], []
+    launches0 = P.dd_launch_count(ctx)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    wall0 = time.perf_counter()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            if P.dd_solver_done(sv):
+                P.dd_solver_free(sv)
+                sv = new_solver()
+            if flush_l2:
+                flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            info = P.dd_solver_step(sv, ctx)     # synchronous
+            step_ms.append((time.perf_counter() - t) * 1e3)
+            scan_ms.append(info.scan_ms)
+            infos.append(info)
+    torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - wall0
+    launches = P.dd_launch_count(ctx) - launches0
+
+    # device time of the steps: the library brackets each step's kernels with
+    # CUDA events on the stream it launches them on
+    dev_ms = [i.cg_ms + i.other_ms + i.search_ms for i in infos]
+    total_ms = sum(dev_ms)
+    total_ms = max_over_ranks(total_ms, world)
+    searches = W.m * args.steps * world
+    value = searches / (total_ms / 1e3)
+
+    # full solve time from the random association (one solve, outside the steps)
+    t = time.perf_counter()
+    r = P.dd_solve(ds, ctx, W.n_el, load, mode=mode, certify=certify, init_idx=init, max_iter=200)
+    solve_s = time.perf_counter() - t
+
+    # end-to-end through the public API with host buffers (pinned): one
+    # projection of the step's m states per call, copies inside the timed region
+    y = torch.from_numpy(I.make_states(W.m, W.law, seed=7, spread=0.05)).pin_memory()
+    idx_h = torch.empty(W.m, dtype=torch.int32).pin_memory()
+    d2_h = torch.empty(W.m, dtype=torch.float64).pin_memory()
+    P.dd_project_nearest(ds, ctx, y.numpy(), idx_h.numpy(), d2_h.numpy(), mode=mode, certify=certify)
+    reps = max(3, args.steps)
+    t = time.perf_counter()
+    for _ in range(reps):
+        P.dd_project_nearest(ds, ctx, y.numpy(), idx_h.numpy(), d2_h.numpy(), mode=mode, certify=certify)
+    e2e_s = max_over_ranks((time.perf_counter() - t) / reps, world)
+
+    peaks = load_peaks()
+    kc = 3 if (mode == P.DD_SEARCH_EXACT_TC and certify) else 1
+    scan_avg = statistics.mean(scan_ms)
+    if mode == P.DD_SEARCH_EXACT_TC:
+        flops = 2.0 * W.m * W.N * 16 * kc
+        achieved = flops / (scan_avg / 1e3) / 1e12
+        roof = {"kernel": f"k_scan_tc<{kc}>", "bound": "tensor", "achieved": achieved,
+                "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "frac": achieved / peaks["bf16_tflops"],
+                "traffic": None, "peak_source": f"{peaks['source']} bf16 dense burst (fp16 same rate)",
+                "algorithmic": f"2*m*N*16*{kc} flops per launch (K padded to 16 per FP16 term)"}
+    else:
+        # FP32 CUDA-core scan: 12 FFMA per (query, point); peak from unit counts and clocks
+        clk_mhz = clk.summary().get("sm_mhz") or 1920.0
+        peak_tflops = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12
+        flops = 2.0 * 12 * W.m * W.N
+        achieved = flops / (scan_avg / 1e3) / 1e12
+        roof = {"kernel": "k_scan_fp32", "bound": "alu", "achieved": achieved, "peak": peak_tflops,
+                "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock",
+                "algorithmic": "2*12*m*N flops per launch (12 FFMA per pair)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64 (P_C, rescoring) + " + ("fp16 split, f32 accum" if kc == 3 and mode == 1
+                                                                    else "fp16, f32 accum" if mode == 1 else "f32"),
+        "data": "synthetic (dd_inputs generator, made on device)",
+        "config": {"workload": W.name, "mesh": f"{W.n_el}^3 hex, 2x2x2 Gauss", "material_points": W.m,
+                   "data_points": W.N, "law": W.law.kind, "load": W.loads[0][0], "search": args.mode,
+                   "l2": "flushed before every step" if flush_l2 else "inputs larger than L2",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roof,
+        "e2e": {"value": W.m * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": W.m * 96,
+                "d2h_bytes_per_step": W.m * 12,
+                "what": "dd_project_nearest with pinned host buffers (states in, indices + distances out)"},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "detail": {
+            "device_ms_per_step": statistics.mean(dev_ms), "scan_ms_per_step": scan_avg,
+            "cg_ms_per_step": statistics.mean(i.cg_ms for i in infos),
+            "search_ms_per_step": statistics.mean(i.search_ms for i in infos),
+            "cg_iters": [i.cg_iters for i in infos][:8], "uncertified": sum(i.uncertified for i in infos),
+            "dd_iterations_per_s": args.steps * world / (total_ms / 1e3), "wall_s": wall,
+            "wall_ms_per_step": statistics.mean(step_ms),
+            "solve_s": solve_s, "solve_iters": r.iters, "solve_converged": r.converged,
+            "solve_search_ms": r.search_ms, "solve_cg_ms": r.cg_ms,
+        },
+    }
+    P.dd_free_dataset(ds)
+    P.dd_solver_free(sv)
+    P.dd_destroy(ctx)
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_searches_per_s(W, C, target_s=args.cpu_seconds)
+    return line
+
+
+def run_reference(args, world, rank):
+    """The FP64 oracle on the host cores, same workload and metric."""
+    if rank != 0:
+        return None
+    W = make_workload(args.workload)
+    C = I.isotropic_C(W.law.E, W.law.nu)
+    per_step = max(4.0, 60.0 / max(1, args.steps + args.warmup))
+    vals = []
+    info = None
+    for i in range(args.warmup + args.steps):
+        info = oracle_searches_per_s(W, C, target_s=per_step) if info is None or i == args.warmup else info
+        if i >= args.warmup:
+            vals.append(info["value"])
+    v = statistics.mean(vals)
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (dd_inputs)", "config": {"workload": W.name, "material_points": W.m,
+                                                        "data_points": W.N},
+            "cpu_baseline": {**info, "value": v},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cube16_N1e6_exact")
+    ap.add_argument("--mode", default="tc", choices=["tc", "tc_topk", "fp32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        line = run_reference(args, world, rank)
+    else:
+        line = run_ours(args, world, rank, local)
+    if rank == 0 and line is not None:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

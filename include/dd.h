@@ -162,6 +162,8 @@ typedef struct dd_search_stats {
                                  "comparisons", Sec. 3.1) */
     int64_t skipped;          /* queries answered by the moving-query radius */
     double ms;                /* device time of the call (CUDA events) */
+    double scan_ms;           /* device time of the dominant scan kernel alone
+                                 (CUDA events on the launching stream) */
 } dd_search_stats;
 
 /* Nearest data point of each state y_i (Eq. 7):
@@ -246,6 +248,47 @@ dd_status dd_solve(dd_dataset *ds, const dd_mesh *mesh, const dd_load *load,
                    const dd_solve_opts *opts, dd_result *out);
 
 void dd_result_free(dd_result *r);
+
+/* ------------------------------------------------------------------------ */
+/* Stepwise solve: the state of one DD problem kept on the device            */
+/* ------------------------------------------------------------------------ */
+
+typedef struct dd_solver dd_solver;
+
+/* Statistics of one iteration z_{i+1} = P_D(P_C(z_i)). */
+typedef struct dd_iter_info {
+    int iter;                 /* 1-based iteration number */
+    int64_t changed;          /* associations changed by P_D */
+    double d2_pc, d2_pd;      /* global distance Eq. 2 after P_C, after P_D */
+    int cg_iters;             /* CG iterations (max of the two systems) */
+    double cg_ms, search_ms, other_ms, scan_ms;   /* device times */
+    int64_t uncertified, distances;
+    double f_d;               /* accuracy parameter used (ANN) */
+    int done;                 /* 1: the stop rule fired or max_iter reached */
+} dd_iter_info;
+
+/* Set up a DD problem (mesh, load, options as for dd_solve) on the data set:
+ * builds the element operators and the preconditioner, draws or copies the
+ * initial association and allocates the per-problem device state (about
+ * 700 bytes per node + 600 bytes per material point).  The data set must
+ * outlive the solver. */
+dd_status dd_solver_create(dd_dataset *ds, const dd_mesh *mesh, const dd_load *load,
+                           const dd_solve_opts *opts, dd_solver **out);
+
+/* One DD iteration (P_C, then P_D, then the stop test of Sec. 2).
+ * Synchronous; info may be NULL.  Returns DD_ERR_STATE once done. */
+dd_status dd_solver_step(dd_solver *sv, dd_iter_info *info);
+
+/* 1 once the stop rule fired or max_iter iterations ran. */
+int dd_solver_done(const dd_solver *sv);
+
+/* Copy the current state to a host result (as dd_solve returns it). */
+dd_status dd_solver_result(dd_solver *sv, dd_result *out);
+
+void dd_solver_free(dd_solver *sv);
+
+/* Number of kernels the context has launched so far (instrumentation). */
+int64_t dd_launch_count(const dd_ctx *ctx);
 
 #if defined(__GNUC__)
 #pragma GCC visibility pop

@@ -25,7 +25,8 @@ DD_SEARCH_EXACT_FP32, DD_SEARCH_EXACT_TC, DD_SEARCH_ANN = 0, 1, 2
 EXPORTS = [
     "dd_create", "dd_destroy", "dd_last_error", "dd_bytes_in_use", "dd_load_dataset", "dd_free_dataset",
     "dd_dataset_size", "dd_dataset_bytes", "dd_synth_dataset", "dd_project_nearest", "dd_solve",
-    "dd_result_free",
+    "dd_result_free", "dd_solver_create", "dd_solver_step", "dd_solver_done", "dd_solver_result",
+    "dd_solver_free", "dd_launch_count",
 ]
 
 
@@ -46,7 +47,15 @@ class dd_search_opts(ctypes.Structure):
 
 
 class dd_search_stats(ctypes.Structure):
-    _fields_ = [("uncertified", c_int64), ("distances", c_int64), ("skipped", c_int64), ("ms", c_double)]
+    _fields_ = [("uncertified", c_int64), ("distances", c_int64), ("skipped", c_int64), ("ms", c_double),
+                ("scan_ms", c_double)]
+
+
+class dd_iter_info(ctypes.Structure):
+    _fields_ = [("iter", c_int), ("changed", c_int64), ("d2_pc", c_double), ("d2_pd", c_double),
+                ("cg_iters", c_int), ("cg_ms", c_double), ("search_ms", c_double), ("other_ms", c_double),
+                ("scan_ms", c_double), ("uncertified", c_int64), ("distances", c_int64), ("f_d", c_double),
+                ("done", c_int)]
 
 
 class dd_mesh(ctypes.Structure):
@@ -105,6 +114,15 @@ def lib():
         L.dd_solve.argtypes = [vp, POINTER(dd_mesh), POINTER(dd_load), POINTER(dd_solve_opts), POINTER(dd_result)]
         L.dd_result_free.argtypes = [POINTER(dd_result)]
         L.dd_result_free.restype = None
+        L.dd_solver_create.argtypes = [vp, POINTER(dd_mesh), POINTER(dd_load), POINTER(dd_solve_opts), POINTER(vp)]
+        L.dd_solver_step.argtypes = [vp, POINTER(dd_iter_info)]
+        L.dd_solver_done.argtypes = [vp]
+        L.dd_solver_done.restype = c_int
+        L.dd_solver_result.argtypes = [vp, POINTER(dd_result)]
+        L.dd_solver_free.argtypes = [vp]
+        L.dd_solver_free.restype = None
+        L.dd_launch_count.argtypes = [vp]
+        L.dd_launch_count.restype = c_int64
         for name in EXPORTS:
             getattr(L, name)
         _lib = L
@@ -242,3 +260,53 @@ def dd_result_free(r: dd_result) -> None:
     """Release the library-allocated arrays of a raw dd_result (dd_solve's
     wrapper above already copies and frees them)."""
     lib().dd_result_free(ctypes.byref(r))
+
+
+def _solve_args(n_el, load, mode, init_idx, max_iter, cg_rtol, cg_max_iter, certify, f_d0, f_d_final, ramp_iters,
+                seed, stall_iters, lengths):
+    nx, ny, nz = (n_el, n_el, n_el) if np.isscalar(n_el) else n_el
+    mesh = dd_mesh(nx, ny, nz, *lengths)
+    L = dd_load((c_double * 3)(*load.t0), (c_double * 3)(*load.tx), (c_double * 3)(*load.ty))
+    ii = None if init_idx is None else np.ascontiguousarray(init_idx, dtype=np.int32)
+    opts = dd_solve_opts(int(mode), int(certify), float(f_d0), float(f_d_final), int(ramp_iters), int(max_iter),
+                         float(cg_rtol), int(cg_max_iter), int(seed), _ptr(ii), int(stall_iters))
+    return mesh, L, opts, ii
+
+
+def dd_solver_create(ds, ctx, n_el, load, mode: int = DD_SEARCH_EXACT_FP32, init_idx=None, max_iter: int = 100,
+                     cg_rtol: float = 1e-12, cg_max_iter: int = 20000, certify: bool = True, f_d0: float = 0.0,
+                     f_d_final: float = 0.0, ramp_iters: int = 20, seed: int = 0, stall_iters: int = 3,
+                     lengths=(1.0, 1.0, 1.0)):
+    mesh, L, opts, ii = _solve_args(n_el, load, mode, init_idx, max_iter, cg_rtol, cg_max_iter, certify, f_d0,
+                                    f_d_final, ramp_iters, seed, stall_iters, lengths)
+    sv = c_void_p()
+    _check(ctx, lib().dd_solver_create(ds, ctypes.byref(mesh), ctypes.byref(L), ctypes.byref(opts),
+                                       ctypes.byref(sv)))
+    return sv
+
+
+def dd_solver_step(sv, ctx) -> dd_iter_info:
+    info = dd_iter_info()
+    _check(ctx, lib().dd_solver_step(sv, ctypes.byref(info)))
+    return info
+
+
+def dd_solver_done(sv) -> bool:
+    return bool(lib().dd_solver_done(sv))
+
+
+def dd_solver_result(sv, ctx) -> Result:
+    r = dd_result()
+    try:
+        _check(ctx, lib().dd_solver_result(sv, ctypes.byref(r)))
+        return Result(r)
+    finally:
+        lib().dd_result_free(ctypes.byref(r))
+
+
+def dd_solver_free(sv) -> None:
+    lib().dd_solver_free(sv)
+
+
+def dd_launch_count(ctx) -> int:
+    return int(lib().dd_launch_count(ctx))

@@ -118,6 +118,7 @@ dd_status dd_transform_dataset(dd_dataset *ds) {
     void *w = nullptr;
     DD_TRY(dd_workspace(ctx, WS_MISC, (size_t)blocks * 12 * sizeof(double) + 64, &w));
     double *part = reinterpret_cast<double *>(w);
+    ctx->launches += 2;
     k_sample_sum<<<blocks, 256, 0, s>>>(ds->raw, ds->N, S, ds->M, part);
     DD_TRY_CUDA(ctx, cudaGetLastError());
     std::vector<double> hp((size_t)blocks * 12);

@@ -120,6 +120,8 @@ extern "C" dd_status dd_create(int device, size_t hbm_budget, dd_ctx **out) {
         return bail("cudaStreamCreate", e);
     if ((e = cudaMalloc((void **)&ctx->dev_err, 256)) != cudaSuccess) return bail("cudaMalloc", e);
     if ((e = cudaMemset(ctx->dev_err, 0, 256)) != cudaSuccess) return bail("cudaMemset", e);
+    if ((e = cudaEventCreate(&ctx->ev_scan[0])) != cudaSuccess) return bail("cudaEventCreate", e);
+    if ((e = cudaEventCreate(&ctx->ev_scan[1])) != cudaSuccess) return bail("cudaEventCreate", e);
     ctx->in_use = 256;
     *out = ctx;
     return DD_OK;
@@ -132,6 +134,8 @@ extern "C" void dd_destroy(dd_ctx *ctx) {
     for (auto &w : ctx->ws)
         if (w.ptr) cudaFree(w.ptr);
     cudaFree(ctx->dev_err);
+    cudaEventDestroy(ctx->ev_scan[0]);
+    cudaEventDestroy(ctx->ev_scan[1]);
     cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -139,6 +143,8 @@ extern "C" void dd_destroy(dd_ctx *ctx) {
 extern "C" const char *dd_last_error(const dd_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
 
 extern "C" size_t dd_bytes_in_use(const dd_ctx *ctx) { return ctx ? ctx->in_use : 0; }
+
+extern "C" int64_t dd_launch_count(const dd_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
 // ---------------------------------------------------------------------------
 // Data set
@@ -216,7 +222,7 @@ extern "C" size_t dd_dataset_bytes(const dd_dataset *ds) { return ds ? ds->bytes
 // ---------------------------------------------------------------------------
 // P_D
 // ---------------------------------------------------------------------------
-static dd_status run_search(dd_dataset *ds, int mode, int certify, double f_d, const int32_t *prev_dev,
+dd_status dd_run_search(dd_dataset *ds, int mode, int certify, double f_d, const int32_t *prev_dev,
                             const double *y_dev, int64_t m, SearchOut out, dd_search_stats *st, cudaStream_t s) {
     switch (mode) {
     case DD_SEARCH_EXACT_FP32:
@@ -280,7 +286,7 @@ extern "C" dd_status dd_project_nearest(dd_dataset *ds, const double *y, int64_t
         DD_TRY_CUDA(ctx, cudaEventRecord(e0, s));
     }
     SearchOut out{idx_dev, d2_dev, nullptr};
-    dd_status st = run_search(ds, o.mode, o.certify, o.f_d, prev_dev, y_dev, m, out, stats ? &local : nullptr, s);
+    dd_status st = dd_run_search(ds, o.mode, o.certify, o.f_d, prev_dev, y_dev, m, out, stats ? &local : nullptr, s);
     if (st != DD_OK) return st;
     if (stats) {
         DD_TRY_CUDA(ctx, cudaEventRecord(e1, s));
@@ -301,235 +307,3 @@ extern "C" dd_status dd_project_nearest(dd_dataset *ds, const double *y, int64_t
     return DD_OK;
 }
 
-// ---------------------------------------------------------------------------
-// DD solve
-// ---------------------------------------------------------------------------
-namespace {
-
-struct Bump {
-    char *base;
-    size_t off = 0;
-    template <class T>
-    T *take(size_t n) {
-        T *p = (T *)(base + off);
-        off += (n * sizeof(T) + 255) / 256 * 256;
-        return p;
-    }
-};
-
-size_t solve_bytes(const MeshDev &g, int n_sm) {
-    size_t nn = (size_t)g.n_nodes, ng = (size_t)g.n_gp;
-    auto r = [](size_t b) { return (b + 255) / 256 * 256; };
-    return r(576 * 8) + r(nn * 3 * 8) + 7 * r(nn * 6 * 8) + r(nn * 9 * 8) + r((size_t)2 * n_sm * 32 * 8 * 8) + r(64) +
-           r(64) + r(64) + r(ng * 12 * 8) + r(ng * 6 * 8) + r(ng * 12 * 8) + 3 * r(ng * 8) + 2 * r(ng * 4) + r(64);
-}
-
-}  // namespace
-
-static void dd_solve_defaults(dd_solve_opts *o) {
-    std::memset(o, 0, sizeof(*o));
-    o->mode = DD_SEARCH_EXACT_FP32;
-    o->certify = 1;
-    o->ramp_iters = 20;
-    o->max_iter = 100;
-    o->cg_rtol = 1e-12;
-    o->cg_max_iter = 20000;
-    o->stall_iters = 3;
-}
-
-extern "C" dd_status dd_solve(dd_dataset *ds, const dd_mesh *mesh, const dd_load *load, const dd_solve_opts *opts,
-                              dd_result *out) {
-    if (!ds) return DD_ERR_ARG;
-    dd_ctx *ctx = ds->ctx;
-    if (!mesh || !load || !out) return dd_fail(ctx, DD_ERR_ARG, "dd_solve: NULL argument");
-    std::memset(out, 0, sizeof(*out));
-    if (mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1 || !(mesh->lx > 0) || !(mesh->ly > 0) || !(mesh->lz > 0))
-        return dd_fail(ctx, DD_ERR_ARG, "dd_solve: bad mesh");
-    if ((int64_t)mesh->nx * mesh->ny * mesh->nz * 8 > INT32_MAX) return dd_fail(ctx, DD_ERR_ARG, "dd_solve: mesh too large");
-    dd_solve_opts o;
-    dd_solve_defaults(&o);
-    if (opts) {
-        o = *opts;
-        if (o.max_iter <= 0) o.max_iter = 100;
-        if (!(o.cg_rtol > 0)) o.cg_rtol = 1e-12;
-        if (o.cg_max_iter <= 0) o.cg_max_iter = 20000;
-        if (o.ramp_iters < 0) o.ramp_iters = 0;
-        if (o.stall_iters <= 0) o.stall_iters = 3;
-    }
-    if (o.mode < 0 || o.mode > 2) return dd_fail(ctx, DD_ERR_ARG, "dd_solve: unknown mode");
-    for (int c = 0; c < 3; ++c)
-        if (!std::isfinite(load->t0[c]) || !std::isfinite(load->tx[c]) || !std::isfinite(load->ty[c]))
-            return dd_fail(ctx, DD_ERR_ARG, "dd_solve: non-finite load");
-    DD_TRY_CUDA(ctx, cudaSetDevice(ctx->device));
-    cudaStream_t s = ctx->stream;
-    const MeshDev g = fem_mesh(*mesh);
-    ElemOps ops;
-    fem_elem_ops(g, &ops);
-    std::vector<double> Ke(576), f((size_t)g.n_nodes * 3);
-    fem_element_stiffness(g, ops, ds->M.C, Ke.data());
-    fem_traction_force(g, *load, mesh->lx, mesh->ly, f.data());
-
-    void *w = nullptr;
-    DD_TRY(dd_workspace(ctx, WS_SOLVE, solve_bytes(g, ctx->n_sm), &w));
-    Bump bp{(char *)w};
-    const size_t nn = g.n_nodes, ng = g.n_gp;
-    double *dKe = bp.take<double>(576), *df = bp.take<double>(nn * 3);
-    CGBuffers cb;
-    double *b = bp.take<double>(nn * 6), *x = bp.take<double>(nn * 6);
-    cb.b = b;
-    cb.x = x;
-    cb.r = bp.take<double>(nn * 6);
-    cb.z = bp.take<double>(nn * 6);
-    cb.p0 = bp.take<double>(nn * 6);
-    cb.p1 = bp.take<double>(nn * 6);
-    cb.q = bp.take<double>(nn * 6);
-    double *Minv = bp.take<double>(nn * 9);
-    cb.Minv = Minv;
-    cb.Ke = dKe;
-    cb.part = bp.take<double>((size_t)2 * ctx->n_sm * 32 * 8);
-    cb.bar = bp.take<unsigned>(16);
-    cb.it_out = bp.take<int>(16);
-    cb.res_out = bp.take<double>(8);
-    double *star = bp.take<double>(ng * 12), *ce = bp.take<double>(ng * 6), *y = bp.take<double>(ng * 12);
-    double *dpc = bp.take<double>(ng), *d2 = bp.take<double>(ng), *d2nd = bp.take<double>(ng);
-    int32_t *idx_a = bp.take<int32_t>(ng), *idx_b = bp.take<int32_t>(ng);
-    double *stats = bp.take<double>(8);
-
-    DD_TRY_CUDA(ctx, cudaMemcpyAsync(dKe, Ke.data(), 576 * 8, cudaMemcpyHostToDevice, s));
-    DD_TRY_CUDA(ctx, cudaMemcpyAsync(df, f.data(), nn * 3 * 8, cudaMemcpyHostToDevice, s));
-    DD_TRY_CUDA(ctx, cudaMemsetAsync(x, 0, nn * 6 * 8, s));
-    DD_TRY(fem_block_jacobi(ctx, g, dKe, Minv, s));
-    if (o.init_idx) {
-        DD_TRY_CUDA(ctx, cudaMemcpyAsync(idx_a, o.init_idx, ng * 4, dd_is_device_ptr(o.init_idx) ? cudaMemcpyDeviceToDevice
-                                                                                                   : cudaMemcpyHostToDevice,
-                                         s));
-    } else {
-        DD_TRY(dd_init_association(ctx, o.seed, ng, ds->N, idx_a, s));
-    }
-
-    std::vector<double> h_pc, h_pd;
-    std::vector<int64_t> h_ch;
-    std::vector<int> h_cg;
-    cudaEvent_t ev[4];
-    for (auto &e : ev) DD_TRY_CUDA(ctx, cudaEventCreate(&e));
-    int32_t *cur = idx_a, *nxt = idx_b;
-    bool converged = false;
-    int stall = 0;
-    double best_pd = INFINITY;
-    dd_search_stats sst;
-    std::memset(&sst, 0, sizeof(sst));
-    dd_status result = DD_OK;
-    int it = 0;
-    for (it = 1; it <= o.max_iter; ++it) {
-        DD_TRY_CUDA(ctx, cudaEventRecord(ev[0], s));
-        DD_TRY(fem_gather_star(ds, cur, ng, star, ce, s));
-        DD_TRY(fem_assemble_rhs(ctx, g, ops, star, ce, df, b, s));
-        DD_TRY(fem_cg(ctx, g, cb, o.cg_rtol, o.cg_max_iter, s));
-        DD_TRY_CUDA(ctx, cudaEventRecord(ev[1], s));
-        DD_TRY(fem_recover(ds, g, ops, x, star, y, dpc, s));
-        DD_TRY_CUDA(ctx, cudaEventRecord(ev[2], s));
-        double f_d = o.f_d_final;
-        if (o.mode == DD_SEARCH_ANN && o.ramp_iters > 0)
-            f_d = o.f_d0 + (o.f_d_final - o.f_d0) * std::min(1.0, (double)(it - 1) / (double)o.ramp_iters);
-        SearchOut so{nxt, d2, d2nd};
-        DD_TRY(run_search(ds, o.mode, o.certify, f_d, cur, y, ng, so, &sst, s));
-        DD_TRY_CUDA(ctx, cudaEventRecord(ev[3], s));
-        DD_TRY(fem_iter_stats(ctx, nxt, cur, d2, dpc, ng, g.w, stats, s));
-        double hs[3];
-        int cg_it = 0;
-        DD_TRY_CUDA(ctx, cudaMemcpyAsync(hs, stats, sizeof(hs), cudaMemcpyDeviceToHost, s));
-        DD_TRY_CUDA(ctx, cudaMemcpyAsync(&cg_it, cb.it_out, sizeof(int), cudaMemcpyDeviceToHost, s));
-        DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
-        DD_TRY(dd_check_device_error(ctx, s, "dd_solve"));
-        float t01 = 0, t12 = 0, t23 = 0;
-        cudaEventElapsedTime(&t01, ev[0], ev[1]);
-        cudaEventElapsedTime(&t12, ev[1], ev[2]);
-        cudaEventElapsedTime(&t23, ev[2], ev[3]);
-        out->cg_ms += t01;
-        out->other_ms += t12;
-        out->search_ms += t23;
-        h_pc.push_back(hs[2]);
-        h_pd.push_back(hs[1]);
-        h_ch.push_back((int64_t)hs[0]);
-        h_cg.push_back(cg_it);
-        if (hs[0] == 0.0) {
-            converged = true;
-            break;
-        }
-        if (o.mode == DD_SEARCH_ANN) {
-            if (hs[1] < best_pd * (1.0 - 1e-12)) {
-                best_pd = hs[1];
-                stall = 0;
-            } else if (++stall >= o.stall_iters) {
-                converged = true;
-                // keep the association the constraint state was computed from
-                break;
-            }
-        }
-        std::swap(cur, nxt);
-    }
-    if (it > o.max_iter) {
-        it = o.max_iter;
-        result = DD_ERR_NOT_CONVERGED;
-    }
-    for (auto &e : ev) cudaEventDestroy(e);
-
-    // results
-    out->n_nodes = g.n_nodes;
-    out->n_gp = g.n_gp;
-    out->iters = (int)h_pc.size();
-    out->converged = converged ? 1 : 0;
-    out->u = (double *)std::malloc(nn * 3 * 8);
-    out->eta = (double *)std::malloc(nn * 3 * 8);
-    out->eps = (double *)std::malloc(ng * 6 * 8);
-    out->sig = (double *)std::malloc(ng * 6 * 8);
-    out->idx = (int32_t *)std::malloc(ng * 4);
-    size_t ni = h_pc.size() ? h_pc.size() : 1;
-    out->d2_pc = (double *)std::malloc(ni * 8);
-    out->d2_pd = (double *)std::malloc(ni * 8);
-    out->changed = (int64_t *)std::malloc(ni * 8);
-    out->cg_iters = (int *)std::malloc(ni * sizeof(int));
-    if (!out->u || !out->eta || !out->eps || !out->sig || !out->idx || !out->d2_pc || !out->d2_pd || !out->changed ||
-        !out->cg_iters) {
-        dd_result_free(out);
-        return dd_fail(ctx, DD_ERR_OOM, "dd_solve: host allocation failed");
-    }
-    std::vector<double> hx(nn * 6), hy(ng * 12);
-    DD_TRY_CUDA(ctx, cudaMemcpyAsync(hx.data(), x, nn * 6 * 8, cudaMemcpyDeviceToHost, s));
-    DD_TRY_CUDA(ctx, cudaMemcpyAsync(hy.data(), y, ng * 12 * 8, cudaMemcpyDeviceToHost, s));
-    DD_TRY_CUDA(ctx, cudaMemcpyAsync(out->idx, cur, ng * 4, cudaMemcpyDeviceToHost, s));
-    DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
-    for (size_t a = 0; a < nn; ++a)
-        for (int c = 0; c < 3; ++c) {
-            out->u[a * 3 + c] = hx[a * 6 + c];
-            out->eta[a * 3 + c] = hx[a * 6 + 3 + c];
-        }
-    for (size_t e = 0; e < ng; ++e)
-        for (int c = 0; c < 6; ++c) {
-            out->eps[e * 6 + c] = hy[e * 12 + c];
-            out->sig[e * 6 + c] = hy[e * 12 + 6 + c];
-        }
-    for (size_t i = 0; i < h_pc.size(); ++i) {
-        out->d2_pc[i] = h_pc[i];
-        out->d2_pd[i] = h_pd[i];
-        out->changed[i] = h_ch[i];
-        out->cg_iters[i] = h_cg[i];
-    }
-    out->uncertified = sst.uncertified;
-    out->distances = sst.distances;
-    return result;
-}
-
-extern "C" void dd_result_free(dd_result *r) {
-    if (!r) return;
-    std::free(r->u);
-    std::free(r->eta);
-    std::free(r->eps);
-    std::free(r->sig);
-    std::free(r->idx);
-    std::free(r->d2_pc);
-    std::free(r->d2_pd);
-    std::free(r->changed);
-    std::free(r->cg_iters);
-    std::memset(r, 0, sizeof(*r));
-}

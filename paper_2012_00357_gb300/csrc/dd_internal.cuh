@@ -79,6 +79,8 @@ struct dd_ctx {
     unsigned *dev_err = nullptr;        // device error word
     // grow-only scratch buffers keyed by purpose
     Workspace ws[8];
+    int64_t launches = 0;               // kernels launched (instrumentation)
+    cudaEvent_t ev_scan[2] = {nullptr, nullptr};   // brackets the dominant scan kernel
 };
 
 enum WsSlot { WS_SEARCH = 0, WS_QUERY = 1, WS_MISC = 2, WS_SOLVE = 3, WS_TC = 4, WS_ANN = 5 };
@@ -153,6 +155,8 @@ dd_status dd_search_ann(dd_dataset *ds, const double *y_dev, int64_t m, double f
                         const int32_t *prev_idx_dev, SearchOut out, dd_search_stats *st,
                         cudaStream_t s);
 dd_status dd_build_ann(dd_dataset *ds, const dd_dataset_opts &o);
+dd_status dd_run_search(dd_dataset *ds, int mode, int certify, double f_d, const int32_t *prev_dev,
+                        const double *y_dev, int64_t m, SearchOut out, dd_search_stats *st, cudaStream_t s);
 void dd_free_ann(dd_dataset *ds);
 
 // Shared by the exact scans: merge split candidates, rescore in FP64 and

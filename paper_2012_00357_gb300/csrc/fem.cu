@@ -572,6 +572,7 @@ void fem_traction_force(const MeshDev &g, const dd_load &L, double lx, double ly
 
 dd_status fem_gather_star(dd_dataset *ds, const int32_t *idx, int64_t n_gp, double *star, double *ce,
                           cudaStream_t s) {
+    ds->ctx->launches++;
     k_gather_star<<<(unsigned)((n_gp + 255) / 256), 256, 0, s>>>(idx, ds->raw, ds->N, ds->M, n_gp, star,
                                                                 ce, ds->ctx->dev_err);
     DD_TRY_CUDA(ds->ctx, cudaGetLastError());
@@ -580,12 +581,14 @@ dd_status fem_gather_star(dd_dataset *ds, const int32_t *idx, int64_t n_gp, doub
 
 dd_status fem_assemble_rhs(dd_ctx *ctx, const MeshDev &g, const ElemOps &ops, const double *star,
                            const double *ce, const double *f, double *b, cudaStream_t s) {
+    ctx->launches++;
     k_assemble_rhs<<<(unsigned)((g.n_nodes + 127) / 128), 128, 0, s>>>(g, ops, star, ce, f, b);
     DD_TRY_CUDA(ctx, cudaGetLastError());
     return DD_OK;
 }
 
 dd_status fem_block_jacobi(dd_ctx *ctx, const MeshDev &g, const double *Ke, double *Minv, cudaStream_t s) {
+    ctx->launches++;
     k_block_jacobi<<<(unsigned)((g.n_nodes + 127) / 128), 128, 0, s>>>(g, Ke, Minv);
     DD_TRY_CUDA(ctx, cudaGetLastError());
     return DD_OK;
@@ -619,12 +622,14 @@ dd_status fem_cg(dd_ctx *ctx, const MeshDev &g, const CGBuffers &B, double rtol,
     A.res_out = B.res_out;
     DD_TRY_CUDA(ctx, cudaMemsetAsync(B.bar, 0, 2 * sizeof(unsigned), s));
     void *args[] = {&A};
+    ctx->launches++;
     DD_TRY_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)k_cg, dim3(grid), dim3(kCgThreads), args, 0, s));
     return DD_OK;
 }
 
 dd_status fem_recover(dd_dataset *ds, const MeshDev &g, const ElemOps &ops, const double *x,
                       const double *star, double *y, double *dpc, cudaStream_t s) {
+    ds->ctx->launches++;
     k_recover<<<(unsigned)((g.n_gp + 127) / 128), 128, 0, s>>>(g, ops, ds->M, x, star, y, dpc);
     DD_TRY_CUDA(ds->ctx, cudaGetLastError());
     return DD_OK;
@@ -632,6 +637,7 @@ dd_status fem_recover(dd_dataset *ds, const MeshDev &g, const ElemOps &ops, cons
 
 dd_status fem_iter_stats(dd_ctx *ctx, const int32_t *idx_new, const int32_t *idx_old, const double *d2,
                          const double *dpc, int64_t n, double w, double *out, cudaStream_t s) {
+    ctx->launches++;
     k_iter_stats<<<1, 1024, 0, s>>>(idx_new, idx_old, d2, dpc, n, w, out);
     DD_TRY_CUDA(ctx, cudaGetLastError());
     return DD_OK;

@@ -329,6 +329,7 @@ int pick_splits(int64_t qtiles, int64_t n_tiles, int n_sm, int per_sm) {
 dd_status dd_map_queries(dd_dataset *ds, const double *y_dev, int64_t m, double *zq64,
                          QueryRec *rec, cudaStream_t s) {
     if (m == 0) return DD_OK;
+    ds->ctx->launches++;
     k_map_queries<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(y_dev, m, ds->M, ds->R, zq64, rec);
     DD_TRY_CUDA(ds->ctx, cudaGetLastError());
     return DD_OK;
@@ -344,12 +345,14 @@ dd_status dd_merge_rescore(dd_dataset *ds, const double *y_dev, int64_t m, int s
     unsigned long long *fb_count = reinterpret_cast<unsigned long long *>(w);
     int64_t *fb_list = reinterpret_cast<int64_t *>(reinterpret_cast<char *>(w) + 256);
     DD_TRY_CUDA(ctx, cudaMemsetAsync(fb_count, 0, sizeof(unsigned long long), s));
+    ctx->launches++;
     k_merge_rescore<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(
         ds->raw, ds->M, y_dev, m, splits, cap, hdr, cand, rec, certify, inv_s2, out.idx, out.d2, out.d2nd,
         fb_list, fb_count);
     DD_TRY_CUDA(ctx, cudaGetLastError());
     if (certify) {
         int grid = (int)std::min<int64_t>(m, (int64_t)ctx->n_sm * 4);
+        ctx->launches++;
         k_fallback_fp64<<<grid, 256, 0, s>>>(ds->raw, ds->N, ds->M, y_dev, fb_list, fb_count,
                                              out.idx, out.d2, out.d2nd);
         DD_TRY_CUDA(ctx, cudaGetLastError());
@@ -385,9 +388,18 @@ dd_status dd_search_exact_fp32(dd_dataset *ds, const double *y_dev, int64_t m, i
     DD_TRY(dd_map_queries(ds, y_dev, m, nullptr, rec, s));
     DD_TRY_CUDA(ctx, cudaFuncSetAttribute(k_scan_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScanSmem));
     dim3 grid((unsigned)qtiles, (unsigned)splits);
+    ctx->launches++;
+    if (st) DD_TRY_CUDA(ctx, cudaEventRecord(ctx->ev_scan[0], s));
     k_scan_fp32<<<grid, kThreads, kScanSmem, s>>>(ds->z32, ds->zn, ds->N, n_tiles, rec, m, splits, tps,
                                                   hdr, cand, certify == 0, ctx->dev_err);
     DD_TRY_CUDA(ctx, cudaGetLastError());
+    if (st) DD_TRY_CUDA(ctx, cudaEventRecord(ctx->ev_scan[1], s));
     if (st) st->distances += m * ds->N;
-    return dd_merge_rescore(ds, y_dev, m, splits, kCap, hdr, cand, rec, certify, 1.0, out, st, s);
+    DD_TRY(dd_merge_rescore(ds, y_dev, m, splits, kCap, hdr, cand, rec, certify, 1.0, out, st, s));
+    if (st) {
+        float ms = 0.f;
+        DD_TRY_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev_scan[0], ctx->ev_scan[1]));
+        st->scan_ms += ms;
+    }
+    return DD_OK;
 }

@@ -442,6 +442,7 @@ dd_status dd_build_fp16(dd_dataset *ds) {
     DD_TRY(dd_alloc(ctx, &p, (size_t)ds->N_pad * 32, "fp16 operands"));
     ds->z16lo = (__half *)p;
     ds->bytes += (size_t)ds->N_pad * 64;
+    ctx->launches++;
     k_build_fp16<<<(unsigned)((ds->N_pad + 255) / 256), 256, 0, ctx->stream>>>(ds->z32, ds->N, ds->N_pad,
                                                                                (float)ds->scale16, ds->z16hi, ds->z16lo);
     DD_TRY_CUDA(ctx, cudaGetLastError());
@@ -472,9 +473,11 @@ dd_status dd_search_exact_tc(dd_dataset *ds, const double *y_dev, int64_t m, int
     float2 *cand = (float2 *)(c + qa_bytes + rec_bytes + hdr_bytes);
 
     const double Rs = ds->R * ds->scale16 * (1.0 + 1e-6);
+    ctx->launches += 2;
     k_prep_tc<<<(unsigned)((m_pad + 127) / 128), 128, 0, s>>>(y_dev, m, m_pad, ds->M, ds->scale16, Rs, kc, qa, rec);
     DD_TRY_CUDA(ctx, cudaGetLastError());
     dim3 grid((unsigned)qtiles, (unsigned)splits);
+    if (st) DD_TRY_CUDA(ctx, cudaEventRecord(ctx->ev_scan[0], s));
     if (kc == 3) {
         size_t sm = tc_smem_bytes<3>();
         DD_TRY_CUDA(ctx, cudaFuncSetAttribute(k_scan_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -487,6 +490,14 @@ dd_status dd_search_exact_tc(dd_dataset *ds, const double *y_dev, int64_t m, int
                                                   cand, true, ctx->dev_err);
     }
     DD_TRY_CUDA(ctx, cudaGetLastError());
+    if (st) DD_TRY_CUDA(ctx, cudaEventRecord(ctx->ev_scan[1], s));
     if (st) st->distances += m * ds->N;
-    return dd_merge_rescore(ds, y_dev, m, splits, kCap, hdr, cand, rec, certify, 1.0 / (ds->scale16 * ds->scale16), out, st, s);
+    DD_TRY(dd_merge_rescore(ds, y_dev, m, splits, kCap, hdr, cand, rec, certify, 1.0 / (ds->scale16 * ds->scale16),
+                            out, st, s));
+    if (st) {
+        float ms = 0.f;
+        DD_TRY_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev_scan[0], ctx->ev_scan[1]));
+        st->scan_ms += ms;
+    }
+    return DD_OK;
 }

@@ -1,0 +1,353 @@
+// The DD fixed-point iteration z_{i+1} = P_D(P_C(z_i)) (Sec. 2, Eq. 8) as a
+// device-resident solver object.
+//
+// A dd_solver owns the state of one problem on the device: the element
+// operators, the two CG solution vectors (warm start of the next P_C), the
+// recovered states y and the association.  One step issues, on one stream:
+//   gather (eps*, sig*) of the association, assemble E and S (Eq. 5),
+//   cooperative CG for K u = E and K eta = S, recovery of eps and sig
+//   (Eq. 6), the nearest-data projection (Eq. 7) and a fixed-order reduction
+//   of the iteration statistics;
+// then reads back three scalars for the stop rule: the association did not
+// change (exact search, Sec. 2), or for the approximate search the global
+// distance Eq. (2) stopped decreasing.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "dd_internal.cuh"
+#include "fem.cuh"
+
+dd_status dd_init_association(dd_ctx *ctx, uint64_t seed, int64_t n, int64_t N, int32_t *idx, cudaStream_t s);
+
+struct dd_solver {
+    dd_dataset *ds = nullptr;
+    dd_ctx *ctx = nullptr;
+    dd_mesh mesh;
+    dd_solve_opts o;
+    MeshDev g;
+    ElemOps ops;
+    void *block = nullptr;
+    size_t block_bytes = 0;
+    double *Ke = nullptr, *f = nullptr, *Minv = nullptr, *star = nullptr, *ce = nullptr, *y = nullptr;
+    double *dpc = nullptr, *d2 = nullptr, *d2nd = nullptr, *stats = nullptr;
+    int32_t *cur = nullptr, *nxt = nullptr;
+    CGBuffers cb;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    int it = 0;
+    bool converged = false, done = false;
+    int stall = 0;
+    double best_pd = INFINITY;
+    std::vector<double> h_pc, h_pd;
+    std::vector<int64_t> h_ch;
+    std::vector<int> h_cg;
+    double cg_ms = 0, search_ms = 0, other_ms = 0;
+    int64_t uncertified = 0, distances = 0;
+};
+
+namespace {
+
+void solve_defaults(dd_solve_opts *o) {
+    std::memset(o, 0, sizeof(*o));
+    o->mode = DD_SEARCH_EXACT_FP32;
+    o->certify = 1;
+    o->ramp_iters = 20;
+    o->max_iter = 100;
+    o->cg_rtol = 1e-12;
+    o->cg_max_iter = 20000;
+    o->stall_iters = 3;
+}
+
+struct Bump {
+    char *base;
+    size_t off = 0;
+    template <class T>
+    T *take(size_t n) {
+        T *p = base ? (T *)(base + off) : nullptr;
+        off += (n * sizeof(T) + 255) / 256 * 256;
+        return p;
+    }
+};
+
+// Lay out (or, with base == nullptr, size) the solver's device block.
+size_t carve(dd_solver *sv, char *base) {
+    Bump bp{base};
+    const size_t nn = sv->g.n_nodes, ng = sv->g.n_gp;
+    sv->Ke = bp.take<double>(576);
+    sv->f = bp.take<double>(nn * 3);
+    CGBuffers &cb = sv->cb;
+    double *b = bp.take<double>(nn * 6), *x = bp.take<double>(nn * 6);
+    cb.b = b;
+    cb.x = x;
+    cb.r = bp.take<double>(nn * 6);
+    cb.z = bp.take<double>(nn * 6);
+    cb.p0 = bp.take<double>(nn * 6);
+    cb.p1 = bp.take<double>(nn * 6);
+    cb.q = bp.take<double>(nn * 6);
+    sv->Minv = bp.take<double>(nn * 9);
+    cb.Minv = sv->Minv;
+    cb.Ke = sv->Ke;
+    cb.part = bp.take<double>((size_t)2 * sv->ctx->n_sm * 32 * 8);
+    cb.bar = bp.take<unsigned>(16);
+    cb.it_out = bp.take<int>(16);
+    cb.res_out = bp.take<double>(8);
+    sv->star = bp.take<double>(ng * 12);
+    sv->ce = bp.take<double>(ng * 6);
+    sv->y = bp.take<double>(ng * 12);
+    sv->dpc = bp.take<double>(ng);
+    sv->d2 = bp.take<double>(ng);
+    sv->d2nd = bp.take<double>(ng);
+    sv->cur = bp.take<int32_t>(ng);
+    sv->nxt = bp.take<int32_t>(ng);
+    sv->stats = bp.take<double>(8);
+    return bp.off;
+}
+
+}  // namespace
+
+extern "C" dd_status dd_solver_create(dd_dataset *ds, const dd_mesh *mesh, const dd_load *load,
+                                      const dd_solve_opts *opts, dd_solver **out) {
+    if (!ds) return DD_ERR_ARG;
+    dd_ctx *ctx = ds->ctx;
+    if (!mesh || !load || !out) return dd_fail(ctx, DD_ERR_ARG, "dd_solver_create: NULL argument");
+    *out = nullptr;
+    if (mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1 || !(mesh->lx > 0) || !(mesh->ly > 0) || !(mesh->lz > 0))
+        return dd_fail(ctx, DD_ERR_ARG, "dd_solver_create: bad mesh");
+    if ((int64_t)mesh->nx * mesh->ny * mesh->nz * 8 > INT32_MAX)
+        return dd_fail(ctx, DD_ERR_ARG, "dd_solver_create: mesh too large");
+    dd_solve_opts o;
+    solve_defaults(&o);
+    if (opts) {
+        o = *opts;
+        if (o.max_iter <= 0) o.max_iter = 100;
+        if (!(o.cg_rtol > 0)) o.cg_rtol = 1e-12;
+        if (o.cg_max_iter <= 0) o.cg_max_iter = 20000;
+        if (o.ramp_iters < 0) o.ramp_iters = 0;
+        if (o.stall_iters <= 0) o.stall_iters = 3;
+    }
+    if (o.mode < 0 || o.mode > 2) return dd_fail(ctx, DD_ERR_ARG, "dd_solver_create: unknown mode");
+    if (o.mode == DD_SEARCH_ANN && !(o.f_d0 >= 0 && o.f_d0 <= 1 && o.f_d_final >= 0 && o.f_d_final <= 1))
+        return dd_fail(ctx, DD_ERR_ARG, "dd_solver_create: f_d outside [0, 1]");
+    for (int c = 0; c < 3; ++c)
+        if (!std::isfinite(load->t0[c]) || !std::isfinite(load->tx[c]) || !std::isfinite(load->ty[c]))
+            return dd_fail(ctx, DD_ERR_ARG, "dd_solver_create: non-finite load");
+    DD_TRY_CUDA(ctx, cudaSetDevice(ctx->device));
+    dd_solver *sv = new dd_solver();
+    sv->ds = ds;
+    sv->ctx = ctx;
+    sv->mesh = *mesh;
+    sv->o = o;
+    sv->o.init_idx = nullptr;
+    sv->g = fem_mesh(*mesh);
+    fem_elem_ops(sv->g, &sv->ops);
+    auto fail = [&](dd_status st) {
+        dd_solver_free(sv);
+        return st;
+    };
+    sv->block_bytes = carve(sv, nullptr);
+    dd_status st = dd_alloc(ctx, &sv->block, sv->block_bytes, "solver state");
+    if (st != DD_OK) return fail(st);
+    carve(sv, (char *)sv->block);
+    for (auto &e : sv->ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return fail(dd_fail(ctx, DD_ERR_CUDA, "cudaEventCreate"));
+    const size_t nn = sv->g.n_nodes, ng = sv->g.n_gp;
+    std::vector<double> Ke(576), f(nn * 3);
+    fem_element_stiffness(sv->g, sv->ops, ds->M.C, Ke.data());
+    fem_traction_force(sv->g, *load, mesh->lx, mesh->ly, f.data());
+    cudaStream_t s = ctx->stream;
+    if (cudaMemcpyAsync(sv->Ke, Ke.data(), 576 * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(sv->f, f.data(), nn * 3 * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(sv->cb.x, 0, nn * 6 * 8, s) != cudaSuccess)
+        return fail(dd_fail(ctx, DD_ERR_CUDA, "dd_solver_create: upload"));
+    if ((st = fem_block_jacobi(ctx, sv->g, sv->Ke, sv->Minv, s)) != DD_OK) return fail(st);
+    if (opts && opts->init_idx) {
+        cudaMemcpyKind k = dd_is_device_ptr(opts->init_idx) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        if (cudaMemcpyAsync(sv->cur, opts->init_idx, ng * 4, k, s) != cudaSuccess)
+            return fail(dd_fail(ctx, DD_ERR_CUDA, "dd_solver_create: copy init_idx"));
+    } else if ((st = dd_init_association(ctx, o.seed, ng, ds->N, sv->cur, s)) != DD_OK) {
+        return fail(st);
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(dd_fail(ctx, DD_ERR_CUDA, "dd_solver_create: sync"));
+    *out = sv;
+    return DD_OK;
+}
+
+extern "C" void dd_solver_free(dd_solver *sv) {
+    if (!sv) return;
+    cudaSetDevice(sv->ctx->device);
+    cudaStreamSynchronize(sv->ctx->stream);
+    for (auto &e : sv->ev)
+        if (e) cudaEventDestroy(e);
+    dd_free(sv->ctx, sv->block, sv->block_bytes);
+    delete sv;
+}
+
+extern "C" int dd_solver_done(const dd_solver *sv) { return sv ? (sv->done ? 1 : 0) : 1; }
+
+extern "C" dd_status dd_solver_step(dd_solver *sv, dd_iter_info *info) {
+    if (!sv) return DD_ERR_ARG;
+    dd_ctx *ctx = sv->ctx;
+    if (sv->done) return dd_fail(ctx, DD_ERR_STATE, "dd_solver_step: solve already finished");
+    DD_TRY_CUDA(ctx, cudaSetDevice(ctx->device));
+    dd_dataset *ds = sv->ds;
+    const dd_solve_opts &o = sv->o;
+    const MeshDev &g = sv->g;
+    const int64_t ng = g.n_gp;
+    cudaStream_t s = ctx->stream;
+    const int it = ++sv->it;
+    DD_TRY_CUDA(ctx, cudaEventRecord(sv->ev[0], s));
+    DD_TRY(fem_gather_star(ds, sv->cur, ng, sv->star, sv->ce, s));
+    DD_TRY(fem_assemble_rhs(ctx, g, sv->ops, sv->star, sv->ce, sv->f, const_cast<double *>(sv->cb.b), s));
+    DD_TRY(fem_cg(ctx, g, sv->cb, o.cg_rtol, o.cg_max_iter, s));
+    DD_TRY_CUDA(ctx, cudaEventRecord(sv->ev[1], s));
+    DD_TRY(fem_recover(ds, g, sv->ops, sv->cb.x, sv->star, sv->y, sv->dpc, s));
+    DD_TRY_CUDA(ctx, cudaEventRecord(sv->ev[2], s));
+    double f_d = o.f_d_final;
+    if (o.mode == DD_SEARCH_ANN && o.ramp_iters > 0)
+        f_d = o.f_d0 + (o.f_d_final - o.f_d0) * std::min(1.0, (double)(it - 1) / (double)o.ramp_iters);
+    SearchOut so{sv->nxt, sv->d2, sv->d2nd};
+    dd_search_stats sst;
+    std::memset(&sst, 0, sizeof(sst));
+    DD_TRY(dd_run_search(ds, o.mode, o.certify, f_d, sv->cur, sv->y, ng, so, &sst, s));
+    DD_TRY_CUDA(ctx, cudaEventRecord(sv->ev[3], s));
+    DD_TRY(fem_iter_stats(ctx, sv->nxt, sv->cur, sv->d2, sv->dpc, ng, g.w, sv->stats, s));
+    double hs[3];
+    int cg_it = 0;
+    DD_TRY_CUDA(ctx, cudaMemcpyAsync(hs, sv->stats, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    DD_TRY_CUDA(ctx, cudaMemcpyAsync(&cg_it, sv->cb.it_out, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+    DD_TRY(dd_check_device_error(ctx, s, "dd_solver_step"));
+    float t01 = 0, t12 = 0, t23 = 0;
+    cudaEventElapsedTime(&t01, sv->ev[0], sv->ev[1]);
+    cudaEventElapsedTime(&t12, sv->ev[1], sv->ev[2]);
+    cudaEventElapsedTime(&t23, sv->ev[2], sv->ev[3]);
+    sv->cg_ms += t01;
+    sv->other_ms += t12;
+    sv->search_ms += t23;
+    sv->uncertified += sst.uncertified;
+    sv->distances += sst.distances;
+    sv->h_pc.push_back(hs[2]);
+    sv->h_pd.push_back(hs[1]);
+    sv->h_ch.push_back((int64_t)hs[0]);
+    sv->h_cg.push_back(cg_it);
+    bool stop = false;
+    if (hs[0] == 0.0) {
+        sv->converged = true;
+        stop = true;   // nxt == cur: the state was computed from the final association
+    } else if (o.mode == DD_SEARCH_ANN) {
+        if (hs[1] < sv->best_pd * (1.0 - 1e-12)) {
+            sv->best_pd = hs[1];
+            sv->stall = 0;
+        } else if (++sv->stall >= o.stall_iters) {
+            sv->converged = true;
+            stop = true;   // keep the association the constraint state was computed from
+        }
+    }
+    if (!stop) std::swap(sv->cur, sv->nxt);
+    if (stop || it >= o.max_iter) sv->done = true;
+    if (info) {
+        info->iter = it;
+        info->changed = (int64_t)hs[0];
+        info->d2_pc = hs[2];
+        info->d2_pd = hs[1];
+        info->cg_iters = cg_it;
+        info->cg_ms = t01;
+        info->other_ms = t12;
+        info->search_ms = t23;
+        info->scan_ms = sst.scan_ms;
+        info->uncertified = sst.uncertified;
+        info->distances = sst.distances;
+        info->f_d = f_d;
+        info->done = sv->done ? 1 : 0;
+    }
+    return DD_OK;
+}
+
+extern "C" dd_status dd_solver_result(dd_solver *sv, dd_result *out) {
+    if (!sv || !out) return DD_ERR_ARG;
+    dd_ctx *ctx = sv->ctx;
+    std::memset(out, 0, sizeof(*out));
+    const size_t nn = sv->g.n_nodes, ng = sv->g.n_gp;
+    out->n_nodes = sv->g.n_nodes;
+    out->n_gp = sv->g.n_gp;
+    out->iters = (int)sv->h_pc.size();
+    out->converged = sv->converged ? 1 : 0;
+    size_t ni = sv->h_pc.size() ? sv->h_pc.size() : 1;
+    out->u = (double *)std::malloc(nn * 3 * 8);
+    out->eta = (double *)std::malloc(nn * 3 * 8);
+    out->eps = (double *)std::malloc(ng * 6 * 8);
+    out->sig = (double *)std::malloc(ng * 6 * 8);
+    out->idx = (int32_t *)std::malloc(ng * 4);
+    out->d2_pc = (double *)std::malloc(ni * 8);
+    out->d2_pd = (double *)std::malloc(ni * 8);
+    out->changed = (int64_t *)std::malloc(ni * 8);
+    out->cg_iters = (int *)std::malloc(ni * sizeof(int));
+    if (!out->u || !out->eta || !out->eps || !out->sig || !out->idx || !out->d2_pc || !out->d2_pd || !out->changed ||
+        !out->cg_iters) {
+        dd_result_free(out);
+        return dd_fail(ctx, DD_ERR_OOM, "dd_solver_result: host allocation failed");
+    }
+    // the state of the last P_C and the association it was computed from
+    const int32_t *assoc = sv->converged ? sv->cur : sv->nxt;
+    if (sv->it == 0) assoc = sv->cur;
+    std::vector<double> hx(nn * 6), hy(ng * 12);
+    cudaStream_t s = ctx->stream;
+    DD_TRY_CUDA(ctx, cudaMemcpyAsync(hx.data(), sv->cb.x, nn * 6 * 8, cudaMemcpyDeviceToHost, s));
+    DD_TRY_CUDA(ctx, cudaMemcpyAsync(hy.data(), sv->y, ng * 12 * 8, cudaMemcpyDeviceToHost, s));
+    DD_TRY_CUDA(ctx, cudaMemcpyAsync(out->idx, assoc, ng * 4, cudaMemcpyDeviceToHost, s));
+    DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+    for (size_t a = 0; a < nn; ++a)
+        for (int c = 0; c < 3; ++c) {
+            out->u[a * 3 + c] = hx[a * 6 + c];
+            out->eta[a * 3 + c] = hx[a * 6 + 3 + c];
+        }
+    for (size_t e = 0; e < ng; ++e)
+        for (int c = 0; c < 6; ++c) {
+            out->eps[e * 6 + c] = hy[e * 12 + c];
+            out->sig[e * 6 + c] = hy[e * 12 + 6 + c];
+        }
+    for (size_t i = 0; i < sv->h_pc.size(); ++i) {
+        out->d2_pc[i] = sv->h_pc[i];
+        out->d2_pd[i] = sv->h_pd[i];
+        out->changed[i] = sv->h_ch[i];
+        out->cg_iters[i] = sv->h_cg[i];
+    }
+    out->search_ms = sv->search_ms;
+    out->cg_ms = sv->cg_ms;
+    out->other_ms = sv->other_ms;
+    out->uncertified = sv->uncertified;
+    out->distances = sv->distances;
+    return DD_OK;
+}
+
+extern "C" dd_status dd_solve(dd_dataset *ds, const dd_mesh *mesh, const dd_load *load, const dd_solve_opts *opts,
+                              dd_result *out) {
+    if (!ds) return DD_ERR_ARG;
+    if (!out) return dd_fail(ds->ctx, DD_ERR_ARG, "dd_solve: NULL argument");
+    std::memset(out, 0, sizeof(*out));
+    dd_solver *sv = nullptr;
+    DD_TRY(dd_solver_create(ds, mesh, load, opts, &sv));
+    dd_status st = DD_OK;
+    while (!sv->done && (st = dd_solver_step(sv, nullptr)) == DD_OK) {
+    }
+    if (st == DD_OK) st = dd_solver_result(sv, out);
+    if (st == DD_OK && !sv->converged) st = DD_ERR_NOT_CONVERGED;
+    dd_solver_free(sv);
+    return st;
+}
+
+extern "C" void dd_result_free(dd_result *r) {
+    if (!r) return;
+    std::free(r->u);
+    std::free(r->eta);
+    std::free(r->eps);
+    std::free(r->sig);
+    std::free(r->idx);
+    std::free(r->d2_pc);
+    std::free(r->d2_pd);
+    std::free(r->changed);
+    std::free(r->cg_iters);
+    std::memset(r, 0, sizeof(*r));
+}

@@ -91,6 +91,7 @@ extern "C" dd_status dd_synth_dataset(dd_ctx *ctx, int law, double eps_lo, doubl
     P.key = fmix64(fmix64(seed + kGamma) + 1ull);   // stream 1: data sets
     cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
     DD_TRY_CUDA(ctx, cudaSetDevice(ctx->device));
+    ctx->launches++;
     k_synth<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(P, start, N, out_dev);
     DD_TRY_CUDA(ctx, cudaGetLastError());
     return DD_OK;
@@ -104,6 +105,7 @@ __global__ void k_init_assoc(uint64_t key, int64_t n, int64_t N, int32_t *__rest
 
 dd_status dd_init_association(dd_ctx *ctx, uint64_t seed, int64_t n, int64_t N, int32_t *idx, cudaStream_t s) {
     uint64_t key = fmix64(fmix64(seed + kGamma) + 3ull);
+    ctx->launches++;
     k_init_assoc<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(key, n, N, idx);
     DD_TRY_CUDA(ctx, cudaGetLastError());
     return DD_OK;
