@@ -125,6 +125,17 @@ void dd_free_dataset(dd_dataset *ds);
 int64_t dd_dataset_size(const dd_dataset *ds);
 size_t dd_dataset_bytes(const dd_dataset *ds);
 
+/* The k-means partition of DD_SEARCH_ANN (built when ann_nlist > 0):
+ * number of clusters L (0 if none), and a host copy of the index.
+ *   cluster_of  host int32 [N]: cluster of every data point, or NULL
+ *   centroids   host float64 [L x 12]: centroids in the mapped coordinates
+ *               z = (C^{1/2} eps, C^{-1/2} sig)/sqrt(2), or NULL
+ *   radii       host float64 [L]: radius d_r of every cluster (largest
+ *               centroid-member distance, rounded up), or NULL
+ * Errors: DD_ERR_STATE if no partition was built.  Synchronous. */
+int dd_dataset_ann_nlist(const dd_dataset *ds);
+dd_status dd_dataset_ann_index(dd_dataset *ds, int32_t *cluster_of, double *centroids, double *radii);
+
 /* Write points start .. start+N-1 of the seeded synthetic data set into the
  * device buffer out_dev (float32 [N x 12]).  This is the device copy of the
  * input generator of the Python module dd_inputs (SplitMix64 counter stream,

