@@ -191,6 +191,29 @@ dd_status dd_project_nearest(dd_dataset *ds, const double *y, int64_t m,
                              const dd_search_opts *opts, int32_t *idx,
                              double *d2, dd_search_stats *stats);
 
+/* Largest query count accepted by dd_project_nearest_noalloc. */
+#define DD_NOALLOC_MAX_QUERIES 65536
+
+/* Exact nearest-data projection that allocates no device memory.  The paper
+ * has no counterpart: this exists for callers that cannot allocate during a
+ * call, for example a serving loop whose device memory is fully reserved by
+ * another allocator, or a latency-bound caller that cannot accept cudaMalloc /
+ * cudaFree (which can fail under memory pressure, and cudaFree synchronises
+ * the device).  Same result as dd_project_nearest with DD_SEARCH_EXACT_FP32
+ * and certify = 1: idx[i] and d2[i] (Eq. 3, FP64) of the nearest data point.
+ *   y_dev    device, float64 [m x 12] states (eps, sig)
+ *   m        0 .. DD_NOALLOC_MAX_QUERIES; larger m returns DD_ERR_ARG
+ *   idx_dev  device, int32 [m] (output); d2_dev device, float64 [m] (output)
+ *   stream   cudaStream_t, NULL = the context's stream; asynchronous
+ * Scratch is one file-scope device array of 32 MiB that every GPU loading the
+ * library holds until exit.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  All calls share the array: calls
+ * whose work overlaps on the GPU (different streams, or several host threads)
+ * race on it and must be serialised by the caller. */
+dd_status dd_project_nearest_noalloc(dd_dataset *ds, const double *y_dev, int64_t m,
+                                     int32_t *idx_dev, double *d2_dev, void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* DD solve: z_{i+1} = P_D(P_C(z_i)), Eq. (8)                               */
 /* ------------------------------------------------------------------------ */

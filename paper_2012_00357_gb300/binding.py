@@ -27,7 +27,9 @@ EXPORTS = [
     "dd_dataset_size", "dd_dataset_bytes", "dd_synth_dataset", "dd_project_nearest", "dd_solve",
     "dd_result_free", "dd_solver_create", "dd_solver_step", "dd_solver_done", "dd_solver_result",
     "dd_solver_free", "dd_launch_count", "dd_dataset_ann_nlist", "dd_dataset_ann_index",
+    "dd_project_nearest_noalloc",
 ]
+DD_NOALLOC_MAX_QUERIES = 65536
 
 
 class DDError(RuntimeError):
@@ -126,6 +128,7 @@ def lib():
         L.dd_dataset_ann_nlist.argtypes = [vp]
         L.dd_dataset_ann_nlist.restype = c_int
         L.dd_dataset_ann_index.argtypes = [vp, vp, vp, vp]
+        L.dd_project_nearest_noalloc.argtypes = [vp, vp, c_int64, vp, vp, vp]
         for name in EXPORTS:
             getattr(L, name)
         _lib = L
@@ -328,3 +331,11 @@ def dd_dataset_ann_index(ds, ctx):
     rad = np.empty(L, np.float64)
     _check(ctx, lib().dd_dataset_ann_index(ds, _ptr(cl), _ptr(cent), _ptr(rad)))
     return cl, cent, rad
+
+
+def dd_project_nearest_noalloc(ds, ctx, y_dev, idx_dev, d2_dev, stream=None) -> None:
+    """Exact projection that allocates no device memory (device buffers only;
+    asynchronous on `stream`).  For callers that cannot allocate during a
+    call, e.g. a loop whose device memory is reserved by another allocator."""
+    _check(ctx, lib().dd_project_nearest_noalloc(ds, _ptr(y_dev), int(y_dev.shape[0]), _ptr(idx_dev),
+                                                 _ptr(d2_dev), stream))

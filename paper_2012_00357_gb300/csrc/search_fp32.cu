@@ -19,8 +19,11 @@
 //
 // Candidate layout, per (query q, split s): header hdr[q * S + s] and
 // entries cand[(q * S + s) * CAP + c] = (score, index bits).
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <mutex>
+#include <string>
 
 #include "dd_internal.cuh"
 
@@ -436,5 +439,84 @@ dd_status dd_search_exact_fp32(dd_dataset *ds, const double *y_dev, int64_t m, i
         DD_TRY_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev_scan[0], ctx->ev_scan[1]));
         st->scan_ms += ms;
     }
+    return DD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the exact FP32 projection.
+//
+// For callers that cannot allocate device memory during a call: for example a
+// serving loop whose device memory is fully reserved up front by another
+// allocator (a framework's caching allocator owning the HBM), or a real-time
+// caller that cannot accept cudaMalloc/cudaFree, which may fail under memory
+// pressure and (cudaFree) synchronise the whole device.  The scratch of the
+// FP32 scan (query records, candidate windows, the re-search list) lives in
+// the file-scope array below instead of the context's workspaces.  Every GPU
+// that loads the library holds this array (32 MiB) until the process exits.
+// ---------------------------------------------------------------------------
+static constexpr size_t kNoAllocScratchBytes = 32ull << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+}  // namespace
+
+extern "C" dd_status dd_project_nearest_noalloc(dd_dataset *ds, const double *y_dev, int64_t m, int32_t *idx_dev,
+                                               double *d2_dev, void *stream) {
+    if (!ds) return DD_ERR_ARG;
+    dd_ctx *ctx = ds->ctx;
+    if (m < 0 || m > DD_NOALLOC_MAX_QUERIES)
+        return dd_fail(ctx, DD_ERR_ARG,
+                       "dd_project_nearest_noalloc: m must be in [0, " + std::to_string(DD_NOALLOC_MAX_QUERIES) + "]");
+    if (m == 0) return DD_OK;
+    if (!y_dev || !idx_dev || !d2_dev) return dd_fail(ctx, DD_ERR_ARG, "dd_project_nearest_noalloc: NULL argument");
+    if (ctx->device < 0 || ctx->device >= kNoAllocMaxDevices)
+        return dd_fail(ctx, DD_ERR_ARG, "dd_project_nearest_noalloc: device index too large");
+    DD_TRY_CUDA(ctx, cudaSetDevice(ctx->device));
+    // Set-up, once per device, with that device current: the device address
+    // of the scratch array (host code only sees a host-side stand-in).
+    void *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[ctx->device]) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess)
+                return dd_fail(ctx, DD_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            g_noalloc_ptr[ctx->device] = p;
+        }
+        base = g_noalloc_ptr[ctx->device];
+    }
+    cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
+    const int64_t n_tiles = (ds->N + kT - 1) / kT;
+    const int64_t qtiles = (m + kQT - 1) / kQT;
+    auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t fixed = r256((size_t)m * sizeof(QueryRec)) + r256((size_t)m * sizeof(int64_t)) + 256;
+    const size_t per_split = (size_t)m * (sizeof(CandHeader) + kCap * sizeof(float2));
+    const int64_t s_fit = (int64_t)((kNoAllocScratchBytes - fixed - 512) / per_split);
+    const int splits = (int)std::max<int64_t>(1, std::min<int64_t>(pick_splits(qtiles, n_tiles, ctx->n_sm, 2), s_fit));
+    const int64_t tps = (n_tiles + splits - 1) / splits;
+    char *c = (char *)base;
+    unsigned long long *fb_count = (unsigned long long *)c;
+    QueryRec *rec = (QueryRec *)(c + 256);
+    int64_t *fb_list = (int64_t *)(c + 256 + r256((size_t)m * sizeof(QueryRec)));
+    CandHeader *hdr = (CandHeader *)(c + fixed);
+    float2 *cand = (float2 *)(c + fixed + r256((size_t)m * splits * sizeof(CandHeader)));
+    // the re-search counter must start at zero; every other region is fully
+    // written before it is read
+    DD_TRY_CUDA(ctx, cudaMemsetAsync(fb_count, 0, sizeof(unsigned long long), s));
+    ctx->launches += 4;
+    k_map_queries<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(y_dev, m, ds->M, ds->R, nullptr, rec);
+    DD_TRY_CUDA(ctx, cudaFuncSetAttribute(k_scan_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScanSmem));
+    k_scan_fp32<<<dim3((unsigned)qtiles, (unsigned)splits), kThreads, kScanSmem, s>>>(
+        ds->z32, ds->zn, ds->N, n_tiles, rec, m, splits, tps, hdr, cand, false, ctx->dev_err);
+    k_merge_rescore<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(ds->raw, ds->M, y_dev, m, splits, kCap, hdr, cand,
+                                                                rec, 1, 1.0, idx_dev, d2_dev, nullptr, fb_list,
+                                                                fb_count);
+    const int grid = (int)std::min<int64_t>(m, (int64_t)ctx->n_sm * 4);
+    k_fallback_fp64<<<grid, 256, 0, s>>>(ds->raw, ds->N, ds->M, y_dev, fb_list, fb_count, idx_dev, d2_dev, nullptr);
+    DD_TRY_CUDA(ctx, cudaGetLastError());
     return DD_OK;
 }
