@@ -250,6 +250,11 @@ typedef struct dd_solve_opts {
     int stall_iters;          /* DD_SEARCH_ANN: stop when the global distance
                                  has not decreased by more than 1e-12 relative
                                  for this many iterations (default 3) */
+    int cg_mode;              /* P_C solves: 0 (default) = FP32 Krylov
+                                 iterations inside FP64 iterative refinement
+                                 (residual b - K x and x in FP64, stop test
+                                 |b - K x| <= cg_rtol |b| in FP64); 1 = FP64
+                                 preconditioned CG throughout */
 } dd_solve_opts;
 
 /* Result of a solve: the constraint-set state y = (u, eps, sig) of the last
@@ -299,6 +304,8 @@ typedef struct dd_iter_info {
     int64_t uncertified, distances;
     double f_d;               /* accuracy parameter used (ANN) */
     int done;                 /* 1: the stop rule fired or max_iter reached */
+    int64_t skipped;          /* ANN: queries kept by the moving-query radius
+                                 (Eq. 14) without a search */
 } dd_iter_info;
 
 /* Set up a DD problem (mesh, load, options as for dd_solve) on the data set:

@@ -57,7 +57,7 @@ class dd_iter_info(ctypes.Structure):
     _fields_ = [("iter", c_int), ("changed", c_int64), ("d2_pc", c_double), ("d2_pd", c_double),
                 ("cg_iters", c_int), ("cg_ms", c_double), ("search_ms", c_double), ("other_ms", c_double),
                 ("scan_ms", c_double), ("uncertified", c_int64), ("distances", c_int64), ("f_d", c_double),
-                ("done", c_int)]
+                ("done", c_int), ("skipped", c_int64)]
 
 
 class dd_mesh(ctypes.Structure):
@@ -72,7 +72,7 @@ class dd_load(ctypes.Structure):
 class dd_solve_opts(ctypes.Structure):
     _fields_ = [("mode", c_int), ("certify", c_int), ("f_d0", c_double), ("f_d_final", c_double),
                 ("ramp_iters", c_int), ("max_iter", c_int), ("cg_rtol", c_double), ("cg_max_iter", c_int),
-                ("seed", c_uint64), ("init_idx", c_void_p), ("stall_iters", c_int)]
+                ("seed", c_uint64), ("init_idx", c_void_p), ("stall_iters", c_int), ("cg_mode", c_int)]
 
 
 class dd_result(ctypes.Structure):
@@ -244,14 +244,14 @@ class Result:
 def dd_solve(ds, ctx, n_el, load, mode: int = DD_SEARCH_EXACT_FP32, init_idx=None, max_iter: int = 100,
              cg_rtol: float = 1e-12, cg_max_iter: int = 20000, certify: bool = True, f_d0: float = 0.0,
              f_d_final: float = 0.0, ramp_iters: int = 20, seed: int = 0, stall_iters: int = 3,
-             lengths=(1.0, 1.0, 1.0), allow_not_converged: bool = True):
+             lengths=(1.0, 1.0, 1.0), allow_not_converged: bool = True, cg_mode: int = 0):
     """Solve one cube problem; `load` is a dd_inputs.Load.  Returns a Result."""
     nx, ny, nz = (n_el, n_el, n_el) if np.isscalar(n_el) else n_el
     mesh = dd_mesh(nx, ny, nz, *lengths)
     L = dd_load((c_double * 3)(*load.t0), (c_double * 3)(*load.tx), (c_double * 3)(*load.ty))
     ii = None if init_idx is None else np.ascontiguousarray(init_idx, dtype=np.int32)
     opts = dd_solve_opts(int(mode), int(certify), float(f_d0), float(f_d_final), int(ramp_iters), int(max_iter),
-                         float(cg_rtol), int(cg_max_iter), int(seed), _ptr(ii), int(stall_iters))
+                         float(cg_rtol), int(cg_max_iter), int(seed), _ptr(ii), int(stall_iters), int(cg_mode))
     r = dd_result()
     st = lib().dd_solve(ds, ctypes.byref(mesh), ctypes.byref(L), ctypes.byref(opts), ctypes.byref(r))
     try:
@@ -269,22 +269,22 @@ def dd_result_free(r: dd_result) -> None:
 
 
 def _solve_args(n_el, load, mode, init_idx, max_iter, cg_rtol, cg_max_iter, certify, f_d0, f_d_final, ramp_iters,
-                seed, stall_iters, lengths):
+                seed, stall_iters, lengths, cg_mode=0):
     nx, ny, nz = (n_el, n_el, n_el) if np.isscalar(n_el) else n_el
     mesh = dd_mesh(nx, ny, nz, *lengths)
     L = dd_load((c_double * 3)(*load.t0), (c_double * 3)(*load.tx), (c_double * 3)(*load.ty))
     ii = None if init_idx is None else np.ascontiguousarray(init_idx, dtype=np.int32)
     opts = dd_solve_opts(int(mode), int(certify), float(f_d0), float(f_d_final), int(ramp_iters), int(max_iter),
-                         float(cg_rtol), int(cg_max_iter), int(seed), _ptr(ii), int(stall_iters))
+                         float(cg_rtol), int(cg_max_iter), int(seed), _ptr(ii), int(stall_iters), int(cg_mode))
     return mesh, L, opts, ii
 
 
 def dd_solver_create(ds, ctx, n_el, load, mode: int = DD_SEARCH_EXACT_FP32, init_idx=None, max_iter: int = 100,
                      cg_rtol: float = 1e-12, cg_max_iter: int = 20000, certify: bool = True, f_d0: float = 0.0,
                      f_d_final: float = 0.0, ramp_iters: int = 20, seed: int = 0, stall_iters: int = 3,
-                     lengths=(1.0, 1.0, 1.0)):
+                     lengths=(1.0, 1.0, 1.0), cg_mode: int = 0):
     mesh, L, opts, ii = _solve_args(n_el, load, mode, init_idx, max_iter, cg_rtol, cg_max_iter, certify, f_d0,
-                                    f_d_final, ramp_iters, seed, stall_iters, lengths)
+                                    f_d_final, ramp_iters, seed, stall_iters, lengths, cg_mode)
     sv = c_void_p()
     _check(ctx, lib().dd_solver_create(ds, ctypes.byref(mesh), ctypes.byref(L), ctypes.byref(opts),
                                        ctypes.byref(sv)))

@@ -50,6 +50,8 @@ dd_status fem_assemble_rhs(dd_ctx *ctx, const MeshDev &g, const ElemOps &ops, co
 dd_status fem_block_jacobi(dd_ctx *ctx, const MeshDev &g, const double *Ke, double *Minv, cudaStream_t s);
 dd_status fem_cg(dd_ctx *ctx, const MeshDev &g, const CGBuffers &B, double rtol, int max_it,
                  cudaStream_t s);
+dd_status fem_cg_mixed(dd_ctx *ctx, const MeshDev &g, const CGBuffers &B, double rtol, int max_it,
+                       cudaStream_t s);
 dd_status fem_recover(dd_dataset *ds, const MeshDev &g, const ElemOps &ops, const double *x,
                       const double *star, double *y, double *dpc, cudaStream_t s);
 dd_status fem_iter_stats(dd_ctx *ctx, const int32_t *idx_new, const int32_t *idx_old, const double *d2,

@@ -21,8 +21,11 @@
 //                 operand tiles into a ring of shared-memory stages
 //   warp 1        TMEM allocator and single-thread MMA issuer; accumulators
 //                 double-buffered in TMEM (2 x 128 columns)
-//   warps 2..5    epilogue: tcgen05.ld of one query row per thread, a
-//                 3-input-min gate and the candidate window (dd_internal.cuh)
+//   warps 2..9    epilogue: two warps per TMEM lane quarter, each taking 64
+//                 of the tile's 128 columns (one query row per thread): two
+//                 tcgen05.ld before one wait, a 3-input-min gate and the
+//                 candidate window (dd_internal.cuh); each column half keeps
+//                 its own window and is merged later like a data split
 // Every mbarrier wait is bounded; on a timeout the kernel flags the error,
 // stops issuing work, drains what is in flight and frees TMEM.
 //
@@ -40,7 +43,8 @@ constexpr int kTN = 128;            // data points per tile (MMA N)
 constexpr int kTM = 128;            // queries per CTA (MMA M)
 constexpr int kStages = 6;
 constexpr int kCap = 8;
-constexpr int kThreadsTC = 192;
+constexpr int kThreadsTC = 320;     // producer, MMA issuer, 8 epilogue warps
+constexpr int kEpiWarps = 8;
 constexpr uint32_t kTileBytes = 4096;   // 128 rows x 16 fp16
 constexpr uint32_t kTmemCols = 256;
 
@@ -90,6 +94,26 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
+    uint32_t r[64];
+#define DD_LD32(OFF, R)                                                                                            \
+    asm volatile(                                                                                                  \
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "                                                                  \
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%" \
+        "28,%29,%30,%31}, [%32];"                                                                                 \
+        : "=r"(R[0]), "=r"(R[1]), "=r"(R[2]), "=r"(R[3]), "=r"(R[4]), "=r"(R[5]), "=r"(R[6]), "=r"(R[7]),         \
+          "=r"(R[8]), "=r"(R[9]), "=r"(R[10]), "=r"(R[11]), "=r"(R[12]), "=r"(R[13]), "=r"(R[14]), "=r"(R[15]),   \
+          "=r"(R[16]), "=r"(R[17]), "=r"(R[18]), "=r"(R[19]), "=r"(R[20]), "=r"(R[21]), "=r"(R[22]), "=r"(R[23]), \
+          "=r"(R[24]), "=r"(R[25]), "=r"(R[26]), "=r"(R[27]), "=r"(R[28]), "=r"(R[29]), "=r"(R[30]), "=r"(R[31]) \
+        : "r"(taddr + (OFF)))
+    DD_LD32(0, r);
+    DD_LD32(32, (r + 32));
+#undef DD_LD32
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ float min3f(float a, float b, float c) {
@@ -254,7 +278,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2)
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *sA = smem;                                   // KC * 4 KB
     unsigned char *sB = smem + KC * kTileBytes;                 // kStages * stage
-    float2 *sCand = reinterpret_cast<float2 *>(sB + kStages * kStageBytes);   // kCap x 128
+    float2 *sCand = reinterpret_cast<float2 *>(sB + kStages * kStageBytes);   // kCap x 256
     __shared__ __align__(8) uint64_t bar_full[kStages], bar_empty[kStages], bar_tfull[2], bar_tempty[2], bar_a,
         bar_done;
     __shared__ uint32_t tmem_slot;
@@ -272,7 +296,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2)
         }
         for (int a = 0; a < 2; ++a) {
             dd_mbar_init(dd_smem_addr(&bar_tfull[a]), 1);
-            dd_mbar_init(dd_smem_addr(&bar_tempty[a]), 4);
+            dd_mbar_init(dd_smem_addr(&bar_tempty[a]), kEpiWarps);
         }
         dd_mbar_init(dd_smem_addr(&bar_a), 1);
         dd_mbar_init(dd_smem_addr(&bar_done), 1);
@@ -355,15 +379,16 @@ __global__ void __launch_bounds__(kThreadsTC, 2)
             if (!dd_mbar_wait(dd_smem_addr(&bar_done), 0)) atomicOr(err, DEV_ERR_TIMEOUT);
         }
     } else {
-        // ---------------- epilogue: one query row per thread ----------------
+        // ---------------- epilogue: one query row and one column half per thread ----------------
         const int quarter = warp & 3;
+        const int half = (warp - 2) >> 2;
         const int row = quarter * 32 + lane;
         const int64_t qi = (int64_t)blockIdx.x * kTM + row;
         const bool active = qi < m;
         const float w2 = active ? rec[qi].w2 : 0.f;
         CandState cs;
         cand_init(cs, active);
-        float2 *buf = sCand + row;
+        float2 *buf = sCand + half * kTM + row;
         bool ok = true;
         for (int64_t t = 0; t < ntl; ++t) {
             const int ab = (int)(t & 1);
@@ -374,27 +399,27 @@ __global__ void __launch_bounds__(kThreadsTC, 2)
                 break;
             }
             tc_fence_after();
-            const int64_t jb = (t_begin + t) * kTN;
-#pragma unroll 1
-            for (int c = 0; c < kTN / 32; ++c) {
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)ab * kTN + (uint32_t)c * 32, v);
-                if (c == kTN / 32 - 1) {
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) dd_mbar_arrive(dd_smem_addr(&bar_tempty[ab]));
-                }
-                const float mn = min32(v);
+            float v[64];
+            tmem_ld64(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)ab * kTN + (uint32_t)half * 64, v);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) dd_mbar_arrive(dd_smem_addr(&bar_tempty[ab]));
+            const int64_t jb = (t_begin + t) * kTN + half * 64;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                float u[32];
+#pragma unroll
+                for (int k = 0; k < 32; ++k) u[k] = v[32 * c + k];
+                const float mn = min32(u);
                 if (mn <= cs.lim) {
-                    const int64_t j0 = jb + c * 32;
+                    const int64_t j0 = jb + 32 * c;
 #pragma unroll
                     for (int k = 0; k < 32; ++k)
-                        if (v[k] <= cs.lim && j0 + k < N)
-                            cand_insert(cs, v[k], (int)(j0 + k), w2, buf, kTM, kCap, topk);
+                        if (u[k] <= cs.lim && j0 + k < N) cand_insert(cs, u[k], (int)(j0 + k), w2, buf, 2 * kTM, kCap, topk);
                 }
             }
         }
-        if (active) cand_store(cs, buf, kTM, kCap, (size_t)qi * splits + split, hdr, cand);
+        if (active) cand_store(cs, buf, 2 * kTM, kCap, ((size_t)qi * splits + split) * 2 + half, hdr, cand);
     }
     __syncthreads();
     if (warp == 1) {
@@ -406,7 +431,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2)
 
 template <int KC>
 size_t tc_smem_bytes() {
-    size_t s = KC * kTileBytes + kStages * (KC == 1 ? 1 : 2) * kTileBytes + kCap * kTM * 8 + 1024;
+    size_t s = KC * kTileBytes + kStages * (KC == 1 ? 1 : 2) * kTileBytes + kCap * 2 * kTM * 8 + 1024;
     return s < 100 * 1024 ? 100 * 1024 : s;   // at most two CTAs (2 x 256 TMEM columns) per SM
 }
 
@@ -462,8 +487,8 @@ dd_status dd_search_exact_tc(dd_dataset *ds, const double *y_dev, int64_t m, int
     auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
     size_t qa_bytes = r256((size_t)qtiles * kc * kTileBytes);
     size_t rec_bytes = r256((size_t)m * sizeof(QueryRec));
-    size_t hdr_bytes = r256((size_t)m * splits * sizeof(CandHeader));
-    size_t cand_bytes = (size_t)m * splits * kCap * sizeof(float2);
+    size_t hdr_bytes = r256((size_t)m * splits * 2 * sizeof(CandHeader));
+    size_t cand_bytes = (size_t)m * splits * 2 * kCap * sizeof(float2);
     void *w = nullptr;
     DD_TRY(dd_workspace(ctx, WS_TC, qa_bytes + rec_bytes + hdr_bytes + cand_bytes, &w));
     char *c = (char *)w;
@@ -492,7 +517,7 @@ dd_status dd_search_exact_tc(dd_dataset *ds, const double *y_dev, int64_t m, int
     DD_TRY_CUDA(ctx, cudaGetLastError());
     if (st) DD_TRY_CUDA(ctx, cudaEventRecord(ctx->ev_scan[1], s));
     if (st) st->distances += m * ds->N;
-    DD_TRY(dd_merge_rescore(ds, y_dev, m, splits, kCap, hdr, cand, rec, certify, 1.0 / (ds->scale16 * ds->scale16),
+    DD_TRY(dd_merge_rescore(ds, y_dev, m, 2 * splits, kCap, hdr, cand, rec, certify, 1.0 / (ds->scale16 * ds->scale16),
                             out, st, s));
     if (st) {
         float ms = 0.f;

@@ -131,6 +131,7 @@ extern "C" dd_status dd_solver_create(dd_dataset *ds, const dd_mesh *mesh, const
         if (o.stall_iters <= 0) o.stall_iters = 3;
     }
     if (o.mode < 0 || o.mode > 2) return dd_fail(ctx, DD_ERR_ARG, "dd_solver_create: unknown mode");
+    if (o.cg_mode < 0 || o.cg_mode > 1) return dd_fail(ctx, DD_ERR_ARG, "dd_solver_create: unknown cg_mode");
     if (o.mode == DD_SEARCH_ANN && !(o.f_d0 >= 0 && o.f_d0 <= 1 && o.f_d_final >= 0 && o.f_d_final <= 1))
         return dd_fail(ctx, DD_ERR_ARG, "dd_solver_create: f_d outside [0, 1]");
     for (int c = 0; c < 3; ++c)
@@ -204,7 +205,8 @@ extern "C" dd_status dd_solver_step(dd_solver *sv, dd_iter_info *info) {
     DD_TRY_CUDA(ctx, cudaEventRecord(sv->ev[0], s));
     DD_TRY(fem_gather_star(ds, sv->cur, ng, sv->star, sv->ce, s));
     DD_TRY(fem_assemble_rhs(ctx, g, sv->ops, sv->star, sv->ce, sv->f, const_cast<double *>(sv->cb.b), s));
-    DD_TRY(fem_cg(ctx, g, sv->cb, o.cg_rtol, o.cg_max_iter, s));
+    if (o.cg_mode == 1) DD_TRY(fem_cg(ctx, g, sv->cb, o.cg_rtol, o.cg_max_iter, s));
+    else DD_TRY(fem_cg_mixed(ctx, g, sv->cb, o.cg_rtol, o.cg_max_iter, s));
     DD_TRY_CUDA(ctx, cudaEventRecord(sv->ev[1], s));
     DD_TRY(fem_recover(ds, g, sv->ops, sv->cb.x, sv->star, sv->y, sv->dpc, s));
     DD_TRY_CUDA(ctx, cudaEventRecord(sv->ev[2], s));
@@ -270,6 +272,7 @@ extern "C" dd_status dd_solver_step(dd_solver *sv, dd_iter_info *info) {
         info->distances = sst.distances;
         info->f_d = f_d;
         info->done = sv->done ? 1 : 0;
+        info->skipped = sst.skipped;
     }
     return DD_OK;
 }

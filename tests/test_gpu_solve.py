@@ -79,3 +79,20 @@ def test_monotone_distance_and_library_init(ctx):
     compare(r, o)
     tol = 1e-12 * r.d2_pc[0]
     assert np.all(r.d2_pd <= r.d2_pc + tol) and np.all(r.d2_pc[1:] <= r.d2_pd[:-1] + tol)
+
+
+def test_mixed_precision_cg_matches_fp64_cg(ctx):
+    """FP32 Krylov steps inside FP64 refinement meet the same FP64 residual
+    test as the FP64 CG: same associations, displacements within 1e-9."""
+    data = I.make_dataset(6000, I.NONLINEAR, seed=5)
+    load = I.load_case("torsion", 1e-3)
+    init = I.initial_association(8 * 64, len(data), seed=5)
+    ds = P.dd_load_dataset(ctx, data, C)
+    try:
+        r64 = P.dd_solve(ds, ctx, 4, load, init_idx=init, cg_mode=1)
+        rmx = P.dd_solve(ds, ctx, 4, load, init_idx=init, cg_mode=0)
+    finally:
+        P.dd_free_dataset(ds)
+    assert r64.iters == rmx.iters and np.array_equal(r64.idx, rmx.idx)
+    assert np.allclose(rmx.u, r64.u, rtol=0, atol=1e-9 * np.abs(r64.u).max())
+    assert np.allclose(rmx.eta, r64.eta, rtol=0, atol=1e-9 * np.abs(r64.eta).max() + 1e-300)
