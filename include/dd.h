@@ -328,6 +328,24 @@ dd_status dd_solver_result(dd_solver *sv, dd_result *out);
 
 void dd_solver_free(dd_solver *sv);
 
+/* One DD iteration of n solves on the same data set at once: the P_C solves
+ * of all of them run in ONE cooperative CG launch (each solve on its own range
+ * of thread blocks, meshes of any size) and the P_D searches of all material
+ * points in ONE search over the concatenated states.  Every solver must be
+ * unfinished, appear once, and share the search mode, certify and cg_mode;
+ * the approximate search uses each solve's own f_d ramp position.  infos
+ * (host, n entries) may be NULL.  Synchronous.  Results are those of stepping
+ * each solver alone. */
+dd_status dd_solvers_step(dd_solver **svs, int n, dd_iter_info *infos);
+
+/* Solve nsolves problems (meshes[i], loads[i], the same options) on one data
+ * set together, stepping all unfinished solves with dd_solvers_step until
+ * every one has stopped.  outs: host array of nsolves results (free each
+ * with dd_result_free).  Returns DD_ERR_NOT_CONVERGED if any solve reached
+ * max_iter.  init_idx in opts, if given, is used for every solve. */
+dd_status dd_solve_batch(dd_dataset *ds, int nsolves, const dd_mesh *meshes, const dd_load *loads,
+                         const dd_solve_opts *opts, dd_result *outs);
+
 /* Number of kernels the context has launched so far (instrumentation). */
 int64_t dd_launch_count(const dd_ctx *ctx);
 

@@ -10,9 +10,10 @@ rules of the paper's k-means search with the warm start of Sec. 4.3:
   * backtracking (Eq. 13): a further cluster, taken in order of increasing
     centroid distance d(x, q), is searched when d(x, q) - f_d d_r < d_c;
     f_d = 1 gives the exact search by the triangle inequality;
-  * only the `n_cand` nearest centroids are candidates; when a cluster
-    beyond them could still pass Eq. (13) (tested with the largest radius),
-    the query is answered by the exhaustive search instead.
+  * only the `n_cand` nearest centroids are candidates for backtracking; for
+    an exact request (f_d = 1), when a cluster beyond them could still pass
+    Eq. (13) (tested with the largest radius), the query is answered by the
+    exhaustive search instead, so f_d = 1 stays exact.
 
 Distances are plain Euclidean distances in the mapped coordinates of
 Sec. 3.2 (|dq|^2 = d_e^2 / 2).  Ties go to the lowest data index.
@@ -61,7 +62,7 @@ def ann_search(Z, zq, cent, rad, cluster_of, f_d, prev_idx=None, n_cand=8):
             if k == 0 or dcent[l] - f_d * rad[l] < dc:
                 scan(l)
                 dc = np.sqrt(best_d)
-        if L > n_cand and dcent[order[-1]] - f_d * rmax < dc:
+        if f_d >= 1.0 and L > n_cand and dcent[order[-1]] - f_d * rmax < dc:
             d = ((Z - q) ** 2).sum(1)
             best_j = int(np.argmin(d))
             best_d = float(d[best_j])

@@ -27,7 +27,7 @@ EXPORTS = [
     "dd_dataset_size", "dd_dataset_bytes", "dd_synth_dataset", "dd_project_nearest", "dd_solve",
     "dd_result_free", "dd_solver_create", "dd_solver_step", "dd_solver_done", "dd_solver_result",
     "dd_solver_free", "dd_launch_count", "dd_dataset_ann_nlist", "dd_dataset_ann_index",
-    "dd_project_nearest_noalloc",
+    "dd_project_nearest_noalloc", "dd_solvers_step", "dd_solve_batch",
 ]
 DD_NOALLOC_MAX_QUERIES = 65536
 
@@ -129,6 +129,9 @@ def lib():
         L.dd_dataset_ann_nlist.restype = c_int
         L.dd_dataset_ann_index.argtypes = [vp, vp, vp, vp]
         L.dd_project_nearest_noalloc.argtypes = [vp, vp, c_int64, vp, vp, vp]
+        L.dd_solvers_step.argtypes = [POINTER(vp), c_int, POINTER(dd_iter_info)]
+        L.dd_solve_batch.argtypes = [vp, c_int, POINTER(dd_mesh), POINTER(dd_load), POINTER(dd_solve_opts),
+                                     POINTER(dd_result)]
         for name in EXPORTS:
             getattr(L, name)
         _lib = L
@@ -339,3 +342,34 @@ def dd_project_nearest_noalloc(ds, ctx, y_dev, idx_dev, d2_dev, stream=None) -> 
     call, e.g. a loop whose device memory is reserved by another allocator."""
     _check(ctx, lib().dd_project_nearest_noalloc(ds, _ptr(y_dev), int(y_dev.shape[0]), _ptr(idx_dev),
                                                  _ptr(d2_dev), stream))
+
+
+def dd_solvers_step(svs, ctx):
+    """One iteration of several solvers at once; returns their dd_iter_info."""
+    n = len(svs)
+    arr = (c_void_p * n)(*[sv.value for sv in svs])
+    infos = (dd_iter_info * n)()
+    _check(ctx, lib().dd_solvers_step(arr, n, infos))
+    return list(infos)
+
+
+def dd_solve_batch(ds, ctx, n_els, loads, mode: int = DD_SEARCH_EXACT_FP32, init_idx=None, max_iter: int = 100,
+                   cg_rtol: float = 1e-12, cg_max_iter: int = 20000, certify: bool = True, f_d0: float = 0.0,
+                   f_d_final: float = 0.0, ramp_iters: int = 20, seed: int = 0, stall_iters: int = 3,
+                   cg_mode: int = 0, allow_not_converged: bool = True):
+    """Solve several cube problems together; n_els[i] edge elements, loads[i]."""
+    n = len(n_els)
+    meshes = (dd_mesh * n)(*[dd_mesh(k, k, k, 1.0, 1.0, 1.0) for k in n_els])
+    Ls = (dd_load * n)(*[dd_load((c_double * 3)(*L.t0), (c_double * 3)(*L.tx), (c_double * 3)(*L.ty))
+                         for L in loads])
+    _, _, opts, ii = _solve_args(n_els[0], loads[0], mode, init_idx, max_iter, cg_rtol, cg_max_iter, certify, f_d0,
+                                 f_d_final, ramp_iters, seed, stall_iters, (1.0, 1.0, 1.0), cg_mode)
+    outs = (dd_result * n)()
+    st = lib().dd_solve_batch(ds, n, meshes, Ls, ctypes.byref(opts), outs)
+    try:
+        if st != DD_OK and not (allow_not_converged and st == DD_ERR_NOT_CONVERGED):
+            _check(ctx, st)
+        return [Result(r) for r in outs]
+    finally:
+        for r in outs:
+            lib().dd_result_free(ctypes.byref(r))

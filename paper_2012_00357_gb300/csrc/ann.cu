@@ -18,9 +18,11 @@
 //      in order of centroid distance, d_c shrinking as better points appear;
 //      f_d = 1 is exact by the triangle inequality, f_d = 0 scans only
 //      clusters whose centroid is nearer than the best point so far;
-//   4. a query whose candidate list might miss a cluster allowed by Eq. 13
-//      (the kCand-th centroid still passes the test with the largest radius)
-//      is re-searched exhaustively, so f_d = 1 always returns the exact point;
+//   4. backtracking is bounded to the kCand nearest centroids; for f_d = 1 a
+//      query whose candidate list might miss a cluster allowed by Eq. 13 (the
+//      kCand-th centroid still passes the test with the largest radius) is
+//      re-searched by the certified exact scan, so f_d = 1 always returns the
+//      exact point;
 //   5. the answer is rescored with Eq. (3) in FP64.
 // Moving-query radius (Eq. 14): with a motion record (previous query, its
 // nearest and second-nearest distances) a query that moved less than
@@ -260,6 +262,7 @@ struct ProbeArgs {
     int64_t m, N;
     int L;
     float f_d;
+    const float *fd_q;          // per-query f_d (may be null: f_d for all)
     float rmax;
     const int32_t *prev;        // may be null
     const float *mot_q;         // motion record (may be null): previous query [m x 12]
@@ -319,21 +322,24 @@ __global__ void __launch_bounds__(256) k_ann_probe(ProbeArgs A) {
     };
     if (cl0 >= 0) scan(cl0);
     float dc = sqrtf(b.d);
+    const float f_d = A.fd_q ? A.fd_q[i] : A.f_d;
     for (int k = 0; k < kCand; ++k) {
         const int l = A.cand_cl[i * kCand + k];
         if (l < 0) break;
         if (l == cl0) continue;
         const float dl = A.cand_d[i * kCand + k];
-        if (k == 0 || dl - A.f_d * A.radius[l] < dc) {
+        if (k == 0 || dl - f_d * A.radius[l] < dc) {
             scan(l);
             dc = sqrtf(b.d);
         }
     }
-    // completeness of the candidate list under Eq. (13)
+    // completeness of the candidate list under Eq. (13), for exact requests
+    // (f_d = 1) only; below that, backtracking is bounded to the kCand
+    // nearest centroids
     bool incomplete = false;
-    if (A.L > kCand) {
+    if (A.L > kCand && f_d >= 1.0f) {
         const float dP = A.cand_d[i * kCand + kCand - 1];
-        incomplete = (dP - A.f_d * A.rmax < dc);
+        incomplete = (dP - f_d * A.rmax < dc);
     }
     if (lane == 0) {
         atomicAdd(A.counters, scanned);
@@ -380,7 +386,48 @@ __global__ void k_export_index(const float *__restrict__ cent, const float *__re
     r_out[l] = radius[l];
 }
 
+__global__ void k_gather_queries(const double *__restrict__ y, const int64_t *__restrict__ list, int64_t n,
+                                 double *__restrict__ ys) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int64_t i = list[t];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) ys[t * 12 + k] = y[i * 12 + k];
+}
+
+__global__ void k_scatter_results(const int64_t *__restrict__ list, int64_t n, const int32_t *__restrict__ si,
+                                  const double *__restrict__ sd, const double *__restrict__ sd2,
+                                  int32_t *__restrict__ idx, double *__restrict__ d2, double *__restrict__ d2nd) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int64_t i = list[t];
+    idx[i] = si[t];
+    if (d2) d2[i] = sd[t];
+    if (d2nd) d2nd[i] = sd2[t];
+}
+
 }  // namespace
+
+// Certified exact search (FP32 scan + FP64 rescoring) of the listed queries.
+static dd_status ann_exact_subset(dd_dataset *ds, const double *y_dev, const int64_t *list, int64_t n, SearchOut out,
+                                  cudaStream_t s) {
+    dd_ctx *ctx = ds->ctx;
+    auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
+    void *w = nullptr;
+    DD_TRY(dd_workspace(ctx, WS_ANN_BUILD, r256((size_t)n * 96) + r256((size_t)n * 4) + 2 * r256((size_t)n * 8), &w));
+    char *c = (char *)w;
+    double *ys = (double *)c;
+    int32_t *si = (int32_t *)(c + r256((size_t)n * 96));
+    double *sd = (double *)(c + r256((size_t)n * 96) + r256((size_t)n * 4));
+    double *sd2 = (double *)(c + r256((size_t)n * 96) + r256((size_t)n * 4) + r256((size_t)n * 8));
+    ctx->launches += 2;
+    k_gather_queries<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(y_dev, list, n, ys);
+    DD_TRY_CUDA(ctx, cudaGetLastError());
+    DD_TRY(dd_search_exact_fp32(ds, ys, n, 1, SearchOut{si, sd, sd2}, nullptr, s));
+    k_scatter_results<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(list, n, si, sd, sd2, out.idx, out.d2, out.d2nd);
+    DD_TRY_CUDA(ctx, cudaGetLastError());
+    return DD_OK;
+}
 
 dd_status dd_ann_motion_update(dd_ctx *ctx, const QueryRec *rec, int64_t m, const double *d2, const double *d2nd,
                                AnnMotion *mot, cudaStream_t s) {
@@ -529,10 +576,10 @@ dd_status dd_build_ann(dd_dataset *ds, const dd_dataset_opts &o) {
 
 dd_status dd_search_ann(dd_dataset *ds, const double *y_dev, int64_t m, double f_d, const int32_t *prev_idx_dev,
                         SearchOut out, dd_search_stats *st, cudaStream_t s) {
-    return dd_search_ann_motion(ds, y_dev, m, f_d, prev_idx_dev, nullptr, out, st, s);
+    return dd_search_ann_motion(ds, y_dev, m, f_d, nullptr, prev_idx_dev, nullptr, out, st, s);
 }
 
-dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, double f_d,
+dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, double f_d, const float *fd_q,
                                const int32_t *prev_idx_dev, AnnMotion *mot, SearchOut out, dd_search_stats *st,
                                cudaStream_t s) {
     dd_ctx *ctx = ds->ctx;
@@ -575,6 +622,7 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
     A.N = ds->N;
     A.L = a.nlist;
     A.f_d = (float)f_d;
+    A.fd_q = fd_q;
     A.rmax = a.rmax;
     A.prev = prev_idx_dev;
     A.mot_q = mot ? mot->q : nullptr;
@@ -591,9 +639,13 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
     k_ann_finish<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(ds->raw, ds->M, y_dev, m, out.idx, d2f, out.d2,
                                                              out.d2nd);
     DD_TRY_CUDA(ctx, cudaGetLastError());
-    // exhaustive re-search where the candidate list may be incomplete
-    dd_status fs = dd_fallback_exact(ds, y_dev, fb_list, counters + 2, m, out, s);
-    if (fs != DD_OK) return fs;
+    // exact re-search where the candidate list may be incomplete (f_d = 1)
+    unsigned long long n_fb = 0;
+    if (f_d >= 1.0 || fd_q) {
+        DD_TRY_CUDA(ctx, cudaMemcpyAsync(&n_fb, counters + 2, sizeof(n_fb), cudaMemcpyDeviceToHost, s));
+        DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+        if (n_fb) DD_TRY(ann_exact_subset(ds, y_dev, fb_list, (int64_t)n_fb, out, s));
+    }
     if (mot && out.d2 && out.d2nd) DD_TRY(dd_ann_motion_update(ctx, rec, m, out.d2, out.d2nd, mot, s));
     if (st) {
         unsigned long long h[3];
@@ -602,9 +654,9 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
         float ms = 0.f;
         DD_TRY_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev_scan[0], ctx->ev_scan[1]));
         st->scan_ms += ms;
-        st->distances += (int64_t)h[0] + m * (int64_t)a.nlist + (int64_t)h[2] * ds->N;
+        st->distances += (int64_t)h[0] + m * (int64_t)a.nlist + (int64_t)n_fb * ds->N;
         st->skipped += (int64_t)h[1];
-        st->uncertified += (int64_t)h[2];
+        st->uncertified += (int64_t)n_fb;
     }
     return DD_OK;
 }

@@ -78,12 +78,15 @@ struct dd_ctx {
     std::string err;
     unsigned *dev_err = nullptr;        // device error word
     // grow-only scratch buffers keyed by purpose
-    Workspace ws[8];
+    Workspace ws[12];
     int64_t launches = 0;               // kernels launched (instrumentation)
     cudaEvent_t ev_scan[2] = {nullptr, nullptr};   // brackets the dominant scan kernel
 };
 
-enum WsSlot { WS_SEARCH = 0, WS_QUERY = 1, WS_MISC = 2, WS_SOLVE = 3, WS_TC = 4, WS_ANN = 5, WS_ANN_SCAN = 6, WS_ANN_BUILD = 7 };
+enum WsSlot {
+    WS_SEARCH = 0, WS_QUERY = 1, WS_MISC = 2, WS_SOLVE = 3, WS_TC = 4, WS_ANN = 5, WS_ANN_SCAN = 6, WS_ANN_BUILD = 7,
+    WS_BATCH = 8, WS_BATCH_CG = 9
+};
 
 struct AnnIndex {
     int nlist = 0;
@@ -166,7 +169,7 @@ dd_status dd_search_ann(dd_dataset *ds, const double *y_dev, int64_t m, double f
                         const int32_t *prev_idx_dev, SearchOut out, dd_search_stats *st,
                         cudaStream_t s);
 dd_status dd_build_ann(dd_dataset *ds, const dd_dataset_opts &o);
-dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, double f_d,
+dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, double f_d, const float *fd_q,
                                const int32_t *prev_idx_dev, AnnMotion *mot, SearchOut out, dd_search_stats *st,
                                cudaStream_t s);
 // FP64 exhaustive re-search of the queries listed in fb_list (count on device).

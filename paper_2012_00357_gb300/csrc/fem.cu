@@ -20,26 +20,9 @@
 
 #include "dd_internal.cuh"
 #include "fem.cuh"
+#include "fem_dev.cuh"
 
 namespace {
-
-__device__ __forceinline__ void node_ijk(const MeshDev &g, int64_t a, int &i, int &j, int &k) {
-    const int64_t nx1 = g.nx + 1, ny1 = g.ny + 1;
-    i = (int)(a % nx1);
-    j = (int)((a / nx1) % ny1);
-    k = (int)(a / (nx1 * ny1));
-}
-
-__device__ __forceinline__ int64_t node_id(const MeshDev &g, int i, int j, int k) {
-    return i + (int64_t)(g.nx + 1) * (j + (int64_t)(g.ny + 1) * k);
-}
-
-__device__ __forceinline__ void bt_times(const double *dN, const double *v, double out[3]) {
-    // B_a^T v for the Voigt vector v = (xx, yy, zz, yz, xz, xy)
-    out[0] = dN[0] * v[0] + dN[2] * v[4] + dN[1] * v[5];
-    out[1] = dN[1] * v[1] + dN[2] * v[3] + dN[0] * v[5];
-    out[2] = dN[2] * v[2] + dN[1] * v[3] + dN[0] * v[4];
-}
 
 // ---------------------------------------------------------------------------
 __global__ void k_gather_star(const int32_t *__restrict__ idx, const float *__restrict__ raw,
@@ -166,88 +149,6 @@ struct CGArgs {
     int *it_out;           // [1]
     double *res_out;       // [2] final relative residuals
 };
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Bounded grid barrier for a cooperative launch.  Returns false if any block
-// reported a timeout.
-__device__ bool grid_barrier(unsigned *bar, unsigned nblocks, unsigned *err) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        unsigned g0 = ld_acquire(bar + 1);
-        __threadfence();
-        unsigned old = atomicAdd(bar, 1u);
-        if (old == nblocks - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            unsigned long long t0 = dd_globaltimer();
-            int spin = 0;
-            while (ld_acquire(bar + 1) == g0) {
-                if ((++spin & 31) == 0 && dd_globaltimer() - t0 > kWaitLimitNs) {
-                    atomicOr(err, DEV_ERR_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-            }
-        }
-        __threadfence();
-        if (ok && (ld_acquire(err) & DEV_ERR_TIMEOUT)) ok = 0;
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
-// Sum NV per-thread values over the block; thread 0 gets the totals.
-template <int NV>
-__device__ void block_sum(double (&v)[NV], double *sh /* [NV * 32] */) {
-#pragma unroll
-    for (int c = 0; c < NV; ++c)
-        for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0)
-#pragma unroll
-        for (int c = 0; c < NV; ++c) sh[c * 32 + wid] = v[c];
-    __syncthreads();
-    if (wid == 0) {
-        const int nw = blockDim.x >> 5;
-#pragma unroll
-        for (int c = 0; c < NV; ++c) {
-            double t = lane < nw ? sh[c * 32 + lane] : 0.0;
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-            v[c] = t;
-        }
-    }
-    __syncthreads();
-}
-
-// After a barrier: every block sums the grid partials in the same order.
-template <int NV>
-__device__ void grid_total(const double *part, int nblk, double (&tot)[NV], double *sh) {
-    double v[NV];
-#pragma unroll
-    for (int c = 0; c < NV; ++c) v[c] = 0.0;
-    for (int t = threadIdx.x; t < nblk; t += blockDim.x)
-#pragma unroll
-        for (int c = 0; c < NV; ++c) v[c] += __ldcg(part + (size_t)t * 8 + c);
-    block_sum<NV>(v, sh);
-    __shared__ double s_tot[8];
-    if (threadIdx.x == 0)
-#pragma unroll
-        for (int c = 0; c < NV; ++c) s_tot[c] = v[c];
-    __syncthreads();
-#pragma unroll
-    for (int c = 0; c < NV; ++c) tot[c] = s_tot[c];
-    __syncthreads();
-}
 
 // y_a = (K v)_a for both systems, v = vz + beta .* vp (vp may be null).
 __device__ __forceinline__ void spmv_node(const MeshDev &g, const double *sKe, int64_t a,
@@ -441,52 +342,6 @@ struct CGMArgs {
     int *it_out;
     double *res_out;
 };
-
-template <typename T>
-__device__ __forceinline__ void spmv_node_t(const MeshDev &g, const T *sKe, int64_t a, const T *vz, const T *vp,
-                                            const T beta[2], T y[6]) {
-    int i, j, k;
-    node_ijk(g, a, i, j, k);
-#pragma unroll
-    for (int c = 0; c < 6; ++c) y[c] = T(0);
-    if (k == 0) return;
-    for (int oz = -1; oz <= 0; ++oz)
-        for (int oy = -1; oy <= 0; ++oy)
-            for (int ox = -1; ox <= 0; ++ox) {
-                int ei = i + ox, ej = j + oy, ek = k + oz;
-                if (ei < 0 || ej < 0 || ek < 0 || ei >= g.nx || ej >= g.ny || ek >= g.nz) continue;
-                int la = (-ox) + 2 * (-oy) + 4 * (-oz);
-#pragma unroll
-                for (int lb = 0; lb < 8; ++lb) {
-                    int64_t nb = node_id(g, ei + (lb & 1), ej + ((lb >> 1) & 1), ek + ((lb >> 2) & 1));
-                    T xv[6];
-#pragma unroll
-                    for (int c = 0; c < 6; ++c) {
-                        T t = __ldcg(vz + nb * 6 + c);
-                        if (vp) t += beta[c / 3] * __ldcg(vp + nb * 6 + c);
-                        xv[c] = t;
-                    }
-                    const T *kb = sKe + (3 * la) * 24 + 3 * lb;
-#pragma unroll
-                    for (int r = 0; r < 3; ++r) {
-                        T k0 = kb[r * 24 + 0], k1 = kb[r * 24 + 1], k2 = kb[r * 24 + 2];
-                        y[r] += k0 * xv[0] + k1 * xv[1] + k2 * xv[2];
-                        y[3 + r] += k0 * xv[3] + k1 * xv[4] + k2 * xv[5];
-                    }
-                }
-            }
-}
-
-__device__ __forceinline__ void apply_minv_f(const double *Mi, const float *r, float *z) {
-    float m[9];
-#pragma unroll
-    for (int c = 0; c < 9; ++c) m[c] = (float)Mi[c];
-#pragma unroll
-    for (int s = 0; s < 2; ++s)
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-            z[3 * s + a] = m[3 * a] * r[3 * s] + m[3 * a + 1] * r[3 * s + 1] + m[3 * a + 2] * r[3 * s + 2];
-}
 
 __global__ void __launch_bounds__(kCgmThreads) k_cg_mixed(CGMArgs A) {
     __shared__ double sKe[576];

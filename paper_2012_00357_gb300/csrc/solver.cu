@@ -19,34 +19,10 @@
 
 #include "dd_internal.cuh"
 #include "fem.cuh"
+#include "solver.cuh"
 
 dd_status dd_init_association(dd_ctx *ctx, uint64_t seed, int64_t n, int64_t N, int32_t *idx, cudaStream_t s);
 
-struct dd_solver {
-    dd_dataset *ds = nullptr;
-    dd_ctx *ctx = nullptr;
-    dd_mesh mesh;
-    dd_solve_opts o;
-    MeshDev g;
-    ElemOps ops;
-    void *block = nullptr;
-    size_t block_bytes = 0;
-    double *Ke = nullptr, *f = nullptr, *Minv = nullptr, *star = nullptr, *ce = nullptr, *y = nullptr;
-    double *dpc = nullptr, *d2 = nullptr, *d2nd = nullptr, *stats = nullptr;
-    int32_t *cur = nullptr, *nxt = nullptr;
-    AnnMotion mot{nullptr, nullptr};    // Eq. 14 record of the approximate search
-    CGBuffers cb;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    int it = 0;
-    bool converged = false, done = false;
-    int stall = 0;
-    double best_pd = INFINITY;
-    std::vector<double> h_pc, h_pd;
-    std::vector<int64_t> h_ch;
-    std::vector<int> h_cg;
-    double cg_ms = 0, search_ms = 0, other_ms = 0;
-    int64_t uncertified = 0, distances = 0;
-};
 
 namespace {
 
@@ -109,6 +85,60 @@ size_t carve(dd_solver *sv, char *base) {
 }
 
 }  // namespace
+
+double dd_solver_fd(const dd_solver *sv, int it) {
+    const dd_solve_opts &o = sv->o;
+    if (o.mode == DD_SEARCH_ANN && o.ramp_iters > 0)
+        return o.f_d0 + (o.f_d_final - o.f_d0) * std::min(1.0, (double)(it - 1) / (double)o.ramp_iters);
+    return o.f_d_final;
+}
+
+bool dd_solver_account(dd_solver *sv, const double hs[3], int cg_it, float cg_ms, float other_ms, float search_ms,
+                       const dd_search_stats &sst, double f_d, dd_iter_info *info) {
+    const dd_solve_opts &o = sv->o;
+    const int it = sv->it;
+    sv->cg_ms += cg_ms;
+    sv->other_ms += other_ms;
+    sv->search_ms += search_ms;
+    sv->uncertified += sst.uncertified;
+    sv->distances += sst.distances;
+    sv->h_pc.push_back(hs[2]);
+    sv->h_pd.push_back(hs[1]);
+    sv->h_ch.push_back((int64_t)hs[0]);
+    sv->h_cg.push_back(cg_it);
+    bool stop = false;
+    if (hs[0] == 0.0) {
+        sv->converged = true;
+        stop = true;   // nxt == cur: the state was computed from the final association
+    } else if (o.mode == DD_SEARCH_ANN) {
+        if (hs[1] < sv->best_pd * (1.0 - 1e-12)) {
+            sv->best_pd = hs[1];
+            sv->stall = 0;
+        } else if (++sv->stall >= o.stall_iters) {
+            sv->converged = true;
+            stop = true;   // keep the association the constraint state was computed from
+        }
+    }
+    if (!stop) std::swap(sv->cur, sv->nxt);
+    if (stop || it >= o.max_iter) sv->done = true;
+    if (info) {
+        info->iter = it;
+        info->changed = (int64_t)hs[0];
+        info->d2_pc = hs[2];
+        info->d2_pd = hs[1];
+        info->cg_iters = cg_it;
+        info->cg_ms = cg_ms;
+        info->other_ms = other_ms;
+        info->search_ms = search_ms;
+        info->scan_ms = sst.scan_ms;
+        info->uncertified = sst.uncertified;
+        info->distances = sst.distances;
+        info->f_d = f_d;
+        info->done = sv->done ? 1 : 0;
+        info->skipped = sst.skipped;
+    }
+    return sv->done;
+}
 
 extern "C" dd_status dd_solver_create(dd_dataset *ds, const dd_mesh *mesh, const dd_load *load,
                                       const dd_solve_opts *opts, dd_solver **out) {
@@ -210,15 +240,13 @@ extern "C" dd_status dd_solver_step(dd_solver *sv, dd_iter_info *info) {
     DD_TRY_CUDA(ctx, cudaEventRecord(sv->ev[1], s));
     DD_TRY(fem_recover(ds, g, sv->ops, sv->cb.x, sv->star, sv->y, sv->dpc, s));
     DD_TRY_CUDA(ctx, cudaEventRecord(sv->ev[2], s));
-    double f_d = o.f_d_final;
-    if (o.mode == DD_SEARCH_ANN && o.ramp_iters > 0)
-        f_d = o.f_d0 + (o.f_d_final - o.f_d0) * std::min(1.0, (double)(it - 1) / (double)o.ramp_iters);
+    const double f_d = dd_solver_fd(sv, it);
     SearchOut so{sv->nxt, sv->d2, sv->d2nd};
     dd_search_stats sst;
     std::memset(&sst, 0, sizeof(sst));
     if (o.mode == DD_SEARCH_ANN) {
         if (!ds->ann.nlist) return dd_fail(ctx, DD_ERR_STATE, "ANN search needs the partition (ann_nlist)");
-        DD_TRY(dd_search_ann_motion(ds, sv->y, ng, f_d, sv->cur, &sv->mot, so, &sst, s));
+        DD_TRY(dd_search_ann_motion(ds, sv->y, ng, f_d, nullptr, sv->cur, &sv->mot, so, &sst, s));
     } else {
         DD_TRY(dd_run_search(ds, o.mode, o.certify, f_d, sv->cur, sv->y, ng, so, &sst, s));
     }
@@ -234,46 +262,7 @@ extern "C" dd_status dd_solver_step(dd_solver *sv, dd_iter_info *info) {
     cudaEventElapsedTime(&t01, sv->ev[0], sv->ev[1]);
     cudaEventElapsedTime(&t12, sv->ev[1], sv->ev[2]);
     cudaEventElapsedTime(&t23, sv->ev[2], sv->ev[3]);
-    sv->cg_ms += t01;
-    sv->other_ms += t12;
-    sv->search_ms += t23;
-    sv->uncertified += sst.uncertified;
-    sv->distances += sst.distances;
-    sv->h_pc.push_back(hs[2]);
-    sv->h_pd.push_back(hs[1]);
-    sv->h_ch.push_back((int64_t)hs[0]);
-    sv->h_cg.push_back(cg_it);
-    bool stop = false;
-    if (hs[0] == 0.0) {
-        sv->converged = true;
-        stop = true;   // nxt == cur: the state was computed from the final association
-    } else if (o.mode == DD_SEARCH_ANN) {
-        if (hs[1] < sv->best_pd * (1.0 - 1e-12)) {
-            sv->best_pd = hs[1];
-            sv->stall = 0;
-        } else if (++sv->stall >= o.stall_iters) {
-            sv->converged = true;
-            stop = true;   // keep the association the constraint state was computed from
-        }
-    }
-    if (!stop) std::swap(sv->cur, sv->nxt);
-    if (stop || it >= o.max_iter) sv->done = true;
-    if (info) {
-        info->iter = it;
-        info->changed = (int64_t)hs[0];
-        info->d2_pc = hs[2];
-        info->d2_pd = hs[1];
-        info->cg_iters = cg_it;
-        info->cg_ms = t01;
-        info->other_ms = t12;
-        info->search_ms = t23;
-        info->scan_ms = sst.scan_ms;
-        info->uncertified = sst.uncertified;
-        info->distances = sst.distances;
-        info->f_d = f_d;
-        info->done = sv->done ? 1 : 0;
-        info->skipped = sst.skipped;
-    }
+    dd_solver_account(sv, hs, cg_it, t01, t12, t23, sst, f_d, info);
     return DD_OK;
 }
 

@@ -1,0 +1,39 @@
+// State of one DD problem on the device (solver.cu, batch.cu).
+#pragma once
+
+#include <vector>
+
+#include "dd_internal.cuh"
+#include "fem.cuh"
+
+struct dd_solver {
+    dd_dataset *ds = nullptr;
+    dd_ctx *ctx = nullptr;
+    dd_mesh mesh;
+    dd_solve_opts o;
+    MeshDev g;
+    ElemOps ops;
+    void *block = nullptr;
+    size_t block_bytes = 0;
+    double *Ke = nullptr, *f = nullptr, *Minv = nullptr, *star = nullptr, *ce = nullptr, *y = nullptr;
+    double *dpc = nullptr, *d2 = nullptr, *d2nd = nullptr, *stats = nullptr;
+    int32_t *cur = nullptr, *nxt = nullptr;
+    AnnMotion mot{nullptr, nullptr};    // Eq. 14 record of the approximate search
+    CGBuffers cb;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    int it = 0;
+    bool converged = false, done = false;
+    int stall = 0;
+    double best_pd = INFINITY;
+    std::vector<double> h_pc, h_pd;
+    std::vector<int64_t> h_ch;
+    std::vector<int> h_cg;
+    double cg_ms = 0, search_ms = 0, other_ms = 0;
+    int64_t uncertified = 0, distances = 0;
+};
+
+// Host-side bookkeeping after one iteration's statistics are on the host:
+// history, stop rule, association swap.  Returns true when the solve stops.
+bool dd_solver_account(dd_solver *sv, const double hs[3], int cg_it, float cg_ms, float other_ms, float search_ms,
+                       const dd_search_stats &sst, double f_d, dd_iter_info *info);
+double dd_solver_fd(const dd_solver *sv, int it);
