@@ -346,6 +346,52 @@ dd_status dd_solvers_step(dd_solver **svs, int n, dd_iter_info *infos);
 dd_status dd_solve_batch(dd_dataset *ds, int nsolves, const dd_mesh *meshes, const dd_load *loads,
                          const dd_solve_opts *opts, dd_result *outs);
 
+/* ------------------------------------------------------------------------ */
+/* Serving: one resident data set, requests admitted by memory and batched   */
+/* ------------------------------------------------------------------------ */
+
+typedef struct dd_server dd_server;
+
+typedef struct dd_server_opts {
+    dd_solve_opts solve;      /* options of every solve; init_idx is ignored and
+                                 each request's seed draws its association */
+    size_t state_budget;      /* device bytes the active solves' states may
+                                 hold; a request waits while it does not fit
+                                 (0 = no cap).  Search workspaces are extra. */
+    int max_batch;            /* most solves stepped together (0 = 64) */
+} dd_server_opts;
+
+typedef struct dd_server_stats {
+    int64_t submitted, completed, active, pending, steps, max_active;
+    double busy_ms;           /* host time spent in batched steps */
+} dd_server_stats;
+
+/* Start a worker thread that serves DD solves on ds.  From then on the worker
+ * owns the context: other calls on it (and on ds) must wait until
+ * dd_server_stop.  Each tick the worker admits pending requests in arrival
+ * order while their states fit in state_budget, runs one iteration of every
+ * active solve with dd_solvers_step (requests that arrived meanwhile join
+ * the next tick) and retires finished solves. */
+dd_status dd_server_start(dd_dataset *ds, const dd_server_opts *opts, dd_server **out);
+
+/* Queue a solve (mesh, load, seed of its initial association).  Thread-safe.
+ * *ticket identifies the request. */
+dd_status dd_server_submit(dd_server *sv, const dd_mesh *mesh, const dd_load *load, uint64_t seed,
+                           int64_t *ticket);
+
+/* Wait up to timeout_s seconds (0 = do not wait) for a request.  On
+ * completion returns the solve's status (DD_OK or DD_ERR_NOT_CONVERGED with
+ * *out filled; free with dd_result_free) and *latency_ms = time from submit
+ * to result; DD_ERR_TIMEOUT if not finished yet.  A ticket can be collected
+ * once.  Thread-safe. */
+dd_status dd_server_poll(dd_server *sv, int64_t ticket, double timeout_s, dd_result *out, double *latency_ms);
+
+dd_status dd_server_get_stats(dd_server *sv, dd_server_stats *out);
+
+/* Finish every queued and active request, stop the worker and release the
+ * server (results not collected are freed). */
+dd_status dd_server_stop(dd_server *sv);
+
 /* Number of kernels the context has launched so far (instrumentation). */
 int64_t dd_launch_count(const dd_ctx *ctx);
 

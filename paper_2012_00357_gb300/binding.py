@@ -27,7 +27,8 @@ EXPORTS = [
     "dd_dataset_size", "dd_dataset_bytes", "dd_synth_dataset", "dd_project_nearest", "dd_solve",
     "dd_result_free", "dd_solver_create", "dd_solver_step", "dd_solver_done", "dd_solver_result",
     "dd_solver_free", "dd_launch_count", "dd_dataset_ann_nlist", "dd_dataset_ann_index",
-    "dd_project_nearest_noalloc", "dd_solvers_step", "dd_solve_batch",
+    "dd_project_nearest_noalloc", "dd_solvers_step", "dd_solve_batch", "dd_server_start", "dd_server_submit",
+    "dd_server_poll", "dd_server_get_stats", "dd_server_stop",
 ]
 DD_NOALLOC_MAX_QUERIES = 65536
 
@@ -73,6 +74,15 @@ class dd_solve_opts(ctypes.Structure):
     _fields_ = [("mode", c_int), ("certify", c_int), ("f_d0", c_double), ("f_d_final", c_double),
                 ("ramp_iters", c_int), ("max_iter", c_int), ("cg_rtol", c_double), ("cg_max_iter", c_int),
                 ("seed", c_uint64), ("init_idx", c_void_p), ("stall_iters", c_int), ("cg_mode", c_int)]
+
+
+class dd_server_opts(ctypes.Structure):
+    _fields_ = [("solve", dd_solve_opts), ("state_budget", c_size_t), ("max_batch", c_int)]
+
+
+class dd_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", c_int64), ("completed", c_int64), ("active", c_int64), ("pending", c_int64),
+                ("steps", c_int64), ("max_active", c_int64), ("busy_ms", c_double)]
 
 
 class dd_result(ctypes.Structure):
@@ -130,6 +140,11 @@ def lib():
         L.dd_dataset_ann_index.argtypes = [vp, vp, vp, vp]
         L.dd_project_nearest_noalloc.argtypes = [vp, vp, c_int64, vp, vp, vp]
         L.dd_solvers_step.argtypes = [POINTER(vp), c_int, POINTER(dd_iter_info)]
+        L.dd_server_start.argtypes = [vp, POINTER(dd_server_opts), POINTER(vp)]
+        L.dd_server_submit.argtypes = [vp, POINTER(dd_mesh), POINTER(dd_load), c_uint64, POINTER(c_int64)]
+        L.dd_server_poll.argtypes = [vp, c_int64, c_double, POINTER(dd_result), POINTER(c_double)]
+        L.dd_server_get_stats.argtypes = [vp, POINTER(dd_server_stats)]
+        L.dd_server_stop.argtypes = [vp]
         L.dd_solve_batch.argtypes = [vp, c_int, POINTER(dd_mesh), POINTER(dd_load), POINTER(dd_solve_opts),
                                      POINTER(dd_result)]
         for name in EXPORTS:
@@ -373,3 +388,51 @@ def dd_solve_batch(ds, ctx, n_els, loads, mode: int = DD_SEARCH_EXACT_FP32, init
     finally:
         for r in outs:
             lib().dd_result_free(ctypes.byref(r))
+
+
+def dd_server_start(ds, ctx, mode: int = DD_SEARCH_EXACT_FP32, state_budget: int = 0, max_batch: int = 0,
+                    max_iter: int = 100, cg_rtol: float = 1e-12, cg_max_iter: int = 20000, certify: bool = True,
+                    f_d0: float = 0.0, f_d_final: float = 0.0, ramp_iters: int = 20, stall_iters: int = 3,
+                    cg_mode: int = 0):
+    so = dd_solve_opts(int(mode), int(certify), float(f_d0), float(f_d_final), int(ramp_iters), int(max_iter),
+                       float(cg_rtol), int(cg_max_iter), 0, None, int(stall_iters), int(cg_mode))
+    o = dd_server_opts(so, int(state_budget), int(max_batch))
+    srv = c_void_p()
+    _check(ctx, lib().dd_server_start(ds, ctypes.byref(o), ctypes.byref(srv)))
+    return srv
+
+
+def dd_server_submit(srv, n_el, load, seed: int = 0, lengths=(1.0, 1.0, 1.0)) -> int:
+    nx, ny, nz = (n_el, n_el, n_el) if np.isscalar(n_el) else n_el
+    mesh = dd_mesh(nx, ny, nz, *lengths)
+    L = dd_load((c_double * 3)(*load.t0), (c_double * 3)(*load.tx), (c_double * 3)(*load.ty))
+    t = c_int64()
+    st = lib().dd_server_submit(srv, ctypes.byref(mesh), ctypes.byref(L), int(seed), ctypes.byref(t))
+    if st != DD_OK:
+        raise DDError(st, "dd_server_submit")
+    return int(t.value)
+
+
+def dd_server_poll(srv, ctx, ticket: int, timeout_s: float = 0.0):
+    """(Result, latency_ms) once finished; None if not finished yet."""
+    r = dd_result()
+    lat = c_double()
+    st = lib().dd_server_poll(srv, int(ticket), float(timeout_s), ctypes.byref(r), ctypes.byref(lat))
+    if st == DD_ERR_TIMEOUT:
+        return None
+    try:
+        if st not in (DD_OK, DD_ERR_NOT_CONVERGED):
+            raise DDError(st, f"served request {ticket} failed")
+        return Result(r), float(lat.value)
+    finally:
+        lib().dd_result_free(ctypes.byref(r))
+
+
+def dd_server_get_stats(srv) -> dd_server_stats:
+    s = dd_server_stats()
+    lib().dd_server_get_stats(srv, ctypes.byref(s))
+    return s
+
+
+def dd_server_stop(srv) -> None:
+    lib().dd_server_stop(srv)

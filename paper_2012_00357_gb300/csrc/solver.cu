@@ -140,6 +140,14 @@ bool dd_solver_account(dd_solver *sv, const double hs[3], int cg_it, float cg_ms
     return sv->done;
 }
 
+// Device bytes of one solve's state (what dd_solver_create allocates).
+size_t dd_solver_state_bytes(dd_ctx *ctx, const dd_mesh &mesh) {
+    dd_solver tmp;
+    tmp.ctx = ctx;
+    tmp.g = fem_mesh(mesh);
+    return carve(&tmp, nullptr);
+}
+
 extern "C" dd_status dd_solver_create(dd_dataset *ds, const dd_mesh *mesh, const dd_load *load,
                                       const dd_solve_opts *opts, dd_solver **out) {
     if (!ds) return DD_ERR_ARG;
