@@ -26,6 +26,7 @@
 namespace {
 
 constexpr int kBThreads = 128;
+constexpr int kGroups = kBThreads / 8;     // nodes per block and pass
 
 struct SegCG {
     MeshDev g;
@@ -91,52 +92,64 @@ __global__ void __launch_bounds__(kBThreads) k_cg_batch(BCGArgs A) {
         sKf[t] = (float)S.Ke[t];
     }
     __syncthreads();
+    // node groups: 8 consecutive lanes per node, lane slot e = element slot
+    // for the product and component c = e (< 6) for the per-node updates
+    const int e = threadIdx.x & 7;
+    const int lane = threadIdx.x & 31;
+    const unsigned gmask = 0xffu << (lane & 24);
+    const int gbase = lane & 24;
+    const bool comp = e < 6;
+    const int c = comp ? e : 0, sy = c / 3;
     const unsigned G = gridDim.x;
     const int lb = blockIdx.x - S.blk0;
     const bool leader = (lb == 0 && threadIdx.x == 0);
-    const int64_t stride = (int64_t)S.nblk * blockDim.x;
-    const int64_t a0 = (int64_t)lb * blockDim.x + threadIdx.x;
+    const int64_t gstride = (int64_t)S.nblk * kGroups;
+    const int64_t a0 = (int64_t)lb * kGroups + (threadIdx.x >> 3);
     double *partA = A.part, *partB = A.part + (size_t)G * 8;
     int *outer_flag = A.flags, *inner_flag = A.flags + A.S;
     const double zb64[2] = {0.0, 0.0};
     double rr_true[2] = {0.0, 0.0}, bb[2] = {0.0, 0.0};
     int inner_count = 0;
+    // z_c = M^-1 r for component c of the node: the system's 3 residuals come
+    // from the group's lanes 3 sy .. 3 sy + 2
+    auto precond = [&](int64_t a, float rc) -> float {
+        float r0 = __shfl_sync(gmask, rc, gbase + 3 * sy + 0);
+        float r1 = __shfl_sync(gmask, rc, gbase + 3 * sy + 1);
+        float r2 = __shfl_sync(gmask, rc, gbase + 3 * sy + 2);
+        const double *Mi = S.Minv + a * 9 + 3 * (c % 3);
+        return (float)Mi[0] * r0 + (float)Mi[1] * r1 + (float)Mi[2] * r2;
+    };
     for (int outer = 0;; ++outer) {
         double v[6] = {0, 0, 0, 0, 0, 0};
-        for (int64_t a = a0; a < g.n_nodes; a += stride) {
+        for (int64_t a = a0; a < g.n_nodes; a += gstride) {
             double kx[6];
-            spmv_node_t<double>(g, sKe, a, S.x, nullptr, zb64, kx);
-            float rf[6], zf[6];
-#pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                double bc = S.b[a * 6 + c];
-                double r64 = bc - kx[c];
-                rf[c] = (float)r64;
-                v[2 + c / 3] += r64 * r64;
-                v[4 + c / 3] += bc * bc;
-            }
-            apply_minv_f(S.Minv + a * 9, rf, zf);
-#pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                S.r[a * 6 + c] = rf[c];
-                S.z[a * 6 + c] = zf[c];
-                S.p0[a * 6 + c] = zf[c];
+            spmv_group<double>(g, sKe, a, e, gmask, S.x, nullptr, zb64, kx);
+            const double bc = comp ? S.b[a * 6 + c] : 0.0;
+            const double r64 = comp ? bc - pick6(kx, c) : 0.0;
+            const float rf = (float)r64;
+            const float zf = precond(a, rf);
+            if (comp) {
+                S.r[a * 6 + c] = rf;
+                S.z[a * 6 + c] = zf;
+                S.p0[a * 6 + c] = zf;
                 S.d[a * 6 + c] = 0.f;
-                v[c / 3] += (double)rf[c] * (double)zf[c];
+                (sy ? v[1] : v[0]) += (double)rf * (double)zf;
+                (sy ? v[3] : v[2]) += r64 * r64;
+                (sy ? v[5] : v[4]) += bc * bc;
             }
         }
         block_sum<6>(v, sh);
         if (threadIdx.x == 0)
-            for (int c = 0; c < 6; ++c) partB[blockIdx.x * 8 + c] = v[c];
+            for (int k = 0; k < 6; ++k) partB[blockIdx.x * 8 + k] = v[k];
         if (!grid_barrier(A.bar, G, A.err)) return;
         double tot[6];
         range_total<6>(partB, S.blk0, S.nblk, tot, sh);
         double rz[2] = {tot[0], tot[1]};
         bool conv[2];
-        for (int s = 0; s < 2; ++s) {
-            rr_true[s] = tot[2 + s];
-            bb[s] = tot[4 + s];
-            conv[s] = !(rr_true[s] > A.rtol2 * bb[s]) || bb[s] == 0.0;
+        for (int s2 = 0; s2 < 2; ++s2) {
+            rr_true[s2] = tot[2 + s2];
+            bb[s2] = tot[4 + s2];
+            conv[s2] = !(rr_true[s2] > A.rtol2 * bb[s2]) || bb[s2] == 0.0;
         }
         const bool more = !(conv[0] && conv[1]) && outer < A.max_outer;
         if (leader) {
@@ -145,10 +158,9 @@ __global__ void __launch_bounds__(kBThreads) k_cg_batch(BCGArgs A) {
         }
         if (!grid_barrier(A.bar, G, A.err)) return;
         if (count_flags(outer_flag, A.S, sh) == 0) {
-            for (int s = 0; s < 2; ++s)
-                if (bb[s] == 0.0)
-                    for (int64_t a = a0; a < g.n_nodes; a += stride)
-                        for (int c = 0; c < 3; ++c) S.x[a * 6 + 3 * s + c] = 0.0;
+            for (int s2 = 0; s2 < 2; ++s2)
+                if (bb[s2] == 0.0 && comp && sy == s2)
+                    for (int64_t a = a0; a < g.n_nodes; a += gstride) S.x[a * 6 + c] = 0.0;
             break;
         }
         const double target[2] = {A.in_rtol2 * rr_true[0], A.in_rtol2 * rr_true[1]};
@@ -159,15 +171,15 @@ __global__ void __launch_bounds__(kBThreads) k_cg_batch(BCGArgs A) {
             const bool act = !(ic[0] && ic[1]);
             double w[2] = {0, 0};
             if (act) {
-                for (int64_t a = a0; a < g.n_nodes; a += stride) {
+                for (int64_t a = a0; a < g.n_nodes; a += gstride) {
                     float kq[6];
-                    spmv_node_t<float>(g, sKf, a, S.z, pold, beta, kq);
-#pragma unroll
-                    for (int c = 0; c < 6; ++c) {
-                        float pn = S.z[a * 6 + c] + beta[c / 3] * pold[a * 6 + c];
+                    spmv_group<float>(g, sKf, a, e, gmask, S.z, pold, beta, kq);
+                    if (comp) {
+                        const float pn = S.z[a * 6 + c] + (sy ? beta[1] : beta[0]) * pold[a * 6 + c];
+                        const float qc = pick6(kq, c);
                         pnew[a * 6 + c] = pn;
-                        S.q[a * 6 + c] = kq[c];
-                        w[c / 3] += (double)pn * (double)kq[c];
+                        S.q[a * 6 + c] = qc;
+                        (sy ? w[1] : w[0]) += (double)pn * (double)qc;
                     }
                 }
             }
@@ -182,40 +194,37 @@ __global__ void __launch_bounds__(kBThreads) k_cg_batch(BCGArgs A) {
             double pq[2];
             range_total<2>(partA, S.blk0, S.nblk, pq, sh);
             float alpha[2];
-            for (int s = 0; s < 2; ++s) alpha[s] = (ic[s] || !(pq[s] > 0.0)) ? 0.f : (float)(rz[s] / pq[s]);
+            for (int s2 = 0; s2 < 2; ++s2) alpha[s2] = (ic[s2] || !(pq[s2] > 0.0)) ? 0.f : (float)(rz[s2] / pq[s2]);
             double u[4] = {0, 0, 0, 0};
             if (act) {
-                for (int64_t a = a0; a < g.n_nodes; a += stride) {
-                    float rv[6], zv[6];
-#pragma unroll
-                    for (int c = 0; c < 6; ++c) {
-                        float al = alpha[c / 3];
-                        S.d[a * 6 + c] += al * pnew[a * 6 + c];
-                        rv[c] = S.r[a * 6 + c] - al * S.q[a * 6 + c];
-                        S.r[a * 6 + c] = rv[c];
+                for (int64_t a = a0; a < g.n_nodes; a += gstride) {
+                    float rv = 0.f;
+                    if (comp) {
+                        S.d[a * 6 + c] += (sy ? alpha[1] : alpha[0]) * pnew[a * 6 + c];
+                        rv = S.r[a * 6 + c] - (sy ? alpha[1] : alpha[0]) * S.q[a * 6 + c];
+                        S.r[a * 6 + c] = rv;
                     }
-                    apply_minv_f(S.Minv + a * 9, rv, zv);
-#pragma unroll
-                    for (int c = 0; c < 6; ++c) {
-                        S.z[a * 6 + c] = zv[c];
-                        u[c / 3] += (double)rv[c] * (double)zv[c];
-                        u[2 + c / 3] += (double)rv[c] * (double)rv[c];
+                    const float zv = precond(a, rv);
+                    if (comp) {
+                        S.z[a * 6 + c] = zv;
+                        (sy ? u[1] : u[0]) += (double)rv * (double)zv;
+                        (sy ? u[3] : u[2]) += (double)rv * (double)rv;
                     }
                 }
             }
             block_sum<4>(u, sh);
             if (threadIdx.x == 0)
-                for (int c = 0; c < 4; ++c) partB[blockIdx.x * 8 + c] = u[c];
+                for (int k = 0; k < 4; ++k) partB[blockIdx.x * 8 + k] = u[k];
             if (!grid_barrier(A.bar, G, A.err)) return;
             double t4[4];
             range_total<4>(partB, S.blk0, S.nblk, t4, sh);
-            for (int s = 0; s < 2; ++s) {
-                if (!ic[s]) {
-                    beta[s] = (rz[s] != 0.0) ? (float)(t4[s] / rz[s]) : 0.f;
-                    rz[s] = t4[s];
-                    ic[s] = !(t4[2 + s] > target[s]) || !(pq[s] > 0.0);
+            for (int s2 = 0; s2 < 2; ++s2) {
+                if (!ic[s2]) {
+                    beta[s2] = (rz[s2] != 0.0) ? (float)(t4[s2] / rz[s2]) : 0.f;
+                    rz[s2] = t4[s2];
+                    ic[s2] = !(t4[2 + s2] > target[s2]) || !(pq[s2] > 0.0);
                 } else {
-                    beta[s] = 0.f;
+                    beta[s2] = 0.f;
                 }
             }
             if (act) ++inner_count;
@@ -224,9 +233,8 @@ __global__ void __launch_bounds__(kBThreads) k_cg_batch(BCGArgs A) {
             pold = pnew;
             pnew = t;
         }
-        for (int64_t a = a0; a < g.n_nodes; a += stride)
-#pragma unroll
-            for (int c = 0; c < 6; ++c) S.x[a * 6 + c] += (double)S.d[a * 6 + c];
+        if (comp)
+            for (int64_t a = a0; a < g.n_nodes; a += gstride) S.x[a * 6 + c] += (double)S.d[a * 6 + c];
         if (!grid_barrier(A.bar, G, A.err)) return;
     }
     if (leader) A.it_out[sidx] = inner_count;
@@ -238,6 +246,90 @@ __global__ void k_fill_f(float *p, int64_t n, float v) {
 }
 
 }  // namespace
+
+// Mixed-precision CG of n systems in one cooperative launch.  *it_dev points
+// at the per-system inner iteration counts (device) after the launch.
+dd_status dd_cg_segments(dd_ctx *ctx, const MeshDev *const *gs, const CGBuffers *const *cbs, int n, double rtol,
+                         int max_it, cudaStream_t s, int **it_dev) {
+    int64_t nodes = 0;
+    for (int i = 0; i < n; ++i) nodes += gs[i]->n_nodes;
+    int occ = 0;
+    DD_TRY_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg_batch, kBThreads, 0));
+    const int cap = std::max(1, std::min(occ, 2)) * ctx->n_sm;
+    if (n > cap) return dd_fail(ctx, DD_ERR_ARG, "more solves than resident CG blocks");
+    std::vector<int> nblk(n);
+    int total = 0;
+    for (int i = 0; i < n; ++i) {
+        const int64_t nn = gs[i]->n_nodes;
+        int64_t want = (nn + kGroups - 1) / kGroups;
+        int64_t share = (int64_t)((double)cap * (double)nn / (double)nodes);
+        nblk[i] = (int)std::max<int64_t>(1, std::min(want, share));
+        total += nblk[i];
+    }
+    while (total > cap) {   // trim the largest shares until the grid is co-resident
+        int k = (int)(std::max_element(nblk.begin(), nblk.end()) - nblk.begin());
+        if (nblk[k] <= 1) return dd_fail(ctx, DD_ERR_ARG, "cannot fit the CG grid");
+        --nblk[k];
+        --total;
+    }
+    std::vector<SegCG> seg(n);
+    std::vector<int> blk_seg(total);
+    int b0 = 0;
+    for (int i = 0; i < n; ++i) {
+        const CGBuffers &cb = *cbs[i];
+        const size_t n6 = (size_t)gs[i]->n_nodes * 6;
+        SegCG &S = seg[i];
+        S.g = *gs[i];
+        S.Ke = cb.Ke;
+        S.Minv = cb.Minv;
+        S.b = cb.b;
+        S.x = cb.x;
+        S.r = reinterpret_cast<float *>(cb.r);
+        S.d = S.r + n6;                 // the FP64 work arrays hold two FP32 vectors each
+        S.z = reinterpret_cast<float *>(cb.z);
+        S.p0 = reinterpret_cast<float *>(cb.p0);
+        S.p1 = reinterpret_cast<float *>(cb.p1);
+        S.q = reinterpret_cast<float *>(cb.q);
+        S.blk0 = b0;
+        S.nblk = nblk[i];
+        for (int k = 0; k < nblk[i]; ++k) blk_seg[b0 + k] = i;
+        b0 += nblk[i];
+    }
+    auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t b_seg = r256(n * sizeof(SegCG)), b_bs = r256(total * sizeof(int)),
+                 b_part = r256((size_t)2 * total * 8 * 8), b_flags = r256((size_t)2 * n * sizeof(int)),
+                 b_it = r256(n * sizeof(int));
+    void *w = nullptr;
+    DD_TRY(dd_workspace(ctx, WS_BATCH_CG, b_seg + b_bs + b_part + b_flags + b_it + 256, &w));
+    char *c = (char *)w;
+    SegCG *d_seg = (SegCG *)c;
+    int *d_bs = (int *)(c + b_seg);
+    double *d_part = (double *)(c + b_seg + b_bs);
+    int *d_flags = (int *)(c + b_seg + b_bs + b_part);
+    *it_dev = (int *)(c + b_seg + b_bs + b_part + b_flags);
+    unsigned *d_bar = (unsigned *)(c + b_seg + b_bs + b_part + b_flags + b_it);
+    DD_TRY_CUDA(ctx, cudaMemcpyAsync(d_seg, seg.data(), n * sizeof(SegCG), cudaMemcpyHostToDevice, s));
+    DD_TRY_CUDA(ctx, cudaMemcpyAsync(d_bs, blk_seg.data(), total * sizeof(int), cudaMemcpyHostToDevice, s));
+    DD_TRY_CUDA(ctx, cudaMemsetAsync(d_bar, 0, 2 * sizeof(unsigned), s));
+    BCGArgs A;
+    A.seg = d_seg;
+    A.blk_seg = d_bs;
+    A.S = n;
+    A.part = d_part;
+    A.flags = d_flags;
+    A.bar = d_bar;
+    A.err = ctx->dev_err;
+    A.rtol2 = rtol * rtol;
+    A.in_rtol2 = 1e-8;                  // each refinement step gains four digits
+    A.max_outer = 30;
+    A.max_inner = max_it;
+    A.it_out = *it_dev;
+    void *args[] = {&A};
+    ctx->launches++;
+    DD_TRY_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)k_cg_batch, dim3(total), dim3(kBThreads), args, 0, s));
+    return DD_OK;
+}
+
 
 extern "C" dd_status dd_solvers_step(dd_solver **svs, int n, dd_iter_info *infos) {
     if (!svs || n < 1 || !svs[0]) return DD_ERR_ARG;
@@ -272,81 +364,13 @@ extern "C" dd_status dd_solvers_step(dd_solver **svs, int n, dd_iter_info *infos
     if (o0.cg_mode == 1) {
         for (int i = 0; i < n; ++i) DD_TRY(fem_cg(ctx, svs[i]->g, svs[i]->cb, o0.cg_rtol, o0.cg_max_iter, s));
     } else {
-        int occ = 0;
-        DD_TRY_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg_batch, kBThreads, 0));
-        const int cap = std::max(1, std::min(occ, 8)) * ctx->n_sm;
-        if (n > cap) return dd_fail(ctx, DD_ERR_ARG, "dd_solvers_step: more solves than resident CG blocks");
-        std::vector<int> nblk(n);
-        int total = 0;
+        std::vector<const MeshDev *> gs(n);
+        std::vector<const CGBuffers *> cbs(n);
         for (int i = 0; i < n; ++i) {
-            const int64_t nn = svs[i]->g.n_nodes;
-            int64_t want = (nn + kBThreads - 1) / kBThreads;
-            int64_t share = (int64_t)((double)cap * (double)nn / (double)nodes);
-            nblk[i] = (int)std::max<int64_t>(1, std::min(want, share));
-            total += nblk[i];
+            gs[i] = &svs[i]->g;
+            cbs[i] = &svs[i]->cb;
         }
-        while (total > cap) {   // trim the largest shares until the grid is co-resident
-            int k = (int)(std::max_element(nblk.begin(), nblk.end()) - nblk.begin());
-            if (nblk[k] <= 1) return dd_fail(ctx, DD_ERR_ARG, "dd_solvers_step: cannot fit the CG grid");
-            --nblk[k];
-            --total;
-        }
-        std::vector<SegCG> seg(n);
-        std::vector<int> blk_seg(total);
-        int b0 = 0;
-        for (int i = 0; i < n; ++i) {
-            dd_solver *sv = svs[i];
-            const size_t n6 = (size_t)sv->g.n_nodes * 6;
-            SegCG &S = seg[i];
-            S.g = sv->g;
-            S.Ke = sv->cb.Ke;
-            S.Minv = sv->cb.Minv;
-            S.b = sv->cb.b;
-            S.x = sv->cb.x;
-            S.r = reinterpret_cast<float *>(sv->cb.r);
-            S.d = S.r + n6;
-            S.z = reinterpret_cast<float *>(sv->cb.z);
-            S.p0 = reinterpret_cast<float *>(sv->cb.p0);
-            S.p1 = reinterpret_cast<float *>(sv->cb.p1);
-            S.q = reinterpret_cast<float *>(sv->cb.q);
-            S.blk0 = b0;
-            S.nblk = nblk[i];
-            for (int k = 0; k < nblk[i]; ++k) blk_seg[b0 + k] = i;
-            b0 += nblk[i];
-        }
-        auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
-        const size_t b_seg = r256(n * sizeof(SegCG)), b_bs = r256(total * sizeof(int)),
-                     b_part = r256((size_t)2 * total * 8 * 8), b_flags = r256((size_t)2 * n * sizeof(int)),
-                     b_it = r256(n * sizeof(int));
-        void *w = nullptr;
-        DD_TRY(dd_workspace(ctx, WS_BATCH_CG, b_seg + b_bs + b_part + b_flags + b_it + 256, &w));
-        char *c = (char *)w;
-        SegCG *d_seg = (SegCG *)c;
-        int *d_bs = (int *)(c + b_seg);
-        double *d_part = (double *)(c + b_seg + b_bs);
-        int *d_flags = (int *)(c + b_seg + b_bs + b_part);
-        it_dev = (int *)(c + b_seg + b_bs + b_part + b_flags);
-        unsigned *d_bar = (unsigned *)(c + b_seg + b_bs + b_part + b_flags + b_it);
-        DD_TRY_CUDA(ctx, cudaMemcpyAsync(d_seg, seg.data(), n * sizeof(SegCG), cudaMemcpyHostToDevice, s));
-        DD_TRY_CUDA(ctx, cudaMemcpyAsync(d_bs, blk_seg.data(), total * sizeof(int), cudaMemcpyHostToDevice, s));
-        DD_TRY_CUDA(ctx, cudaMemsetAsync(d_bar, 0, 2 * sizeof(unsigned), s));
-        BCGArgs A;
-        A.seg = d_seg;
-        A.blk_seg = d_bs;
-        A.S = n;
-        A.part = d_part;
-        A.flags = d_flags;
-        A.bar = d_bar;
-        A.err = ctx->dev_err;
-        A.rtol2 = o0.cg_rtol * o0.cg_rtol;
-        A.in_rtol2 = 1e-8;
-        A.max_outer = 30;
-        A.max_inner = o0.cg_max_iter;
-        A.it_out = it_dev;
-        void *args[] = {&A};
-        ctx->launches++;
-        DD_TRY_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)k_cg_batch, dim3(total), dim3(kBThreads), args, 0, s));
-        // host pageable copies below wait for it
+        DD_TRY(dd_cg_segments(ctx, gs.data(), cbs.data(), n, o0.cg_rtol, o0.cg_max_iter, s, &it_dev));
     }
     DD_TRY_CUDA(ctx, cudaEventRecord(ev[1], s));
     for (int i = 0; i < n; ++i) DD_TRY(fem_recover(ds, svs[i]->g, svs[i]->ops, svs[i]->cb.x, svs[i]->star, svs[i]->y,

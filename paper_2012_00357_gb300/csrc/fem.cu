@@ -314,176 +314,6 @@ __global__ void __launch_bounds__(kCgThreads) k_cg(CGArgs A) {
 }
 
 // ---------------------------------------------------------------------------
-// Mixed-precision CG: FP64 iterative refinement around an FP32 PCG.
-//
-// GB300 executes FP64 at a small fraction of its FP32 rate, so the Krylov
-// iterations run in FP32 on the correction d of K d = r, while the residual
-// r = b - K x and the solution x stay in FP64:
-//   repeat: r = b - K x (FP64); stop when |r| <= rtol |b| per system;
-//           FP32 PCG on K d = r until |r_d| <= in_rtol |r|; x += d (FP64).
-// The stop test is the same FP64 residual test as the pure FP64 CG, so the
-// returned x meets the same tolerance (refinement converges while
-// cond(K) * 2^-24 << 1).
-// ---------------------------------------------------------------------------
-constexpr int kCgmThreads = 128;
-
-struct CGMArgs {
-    MeshDev g;
-    const double *Ke;
-    const double *Minv;
-    const double *b;
-    double *x;
-    float *r, *z, *p0, *p1, *q, *d;
-    double *part;
-    unsigned *bar;
-    unsigned *err;
-    double rtol2, in_rtol2;
-    int max_outer, max_inner;
-    int *it_out;
-    double *res_out;
-};
-
-__global__ void __launch_bounds__(kCgmThreads) k_cg_mixed(CGMArgs A) {
-    __shared__ double sKe[576];
-    __shared__ float sKf[576];
-    __shared__ double sh[8 * 32];
-    const MeshDev &g = A.g;
-    for (int t = threadIdx.x; t < 576; t += blockDim.x) {
-        sKe[t] = A.Ke[t];
-        sKf[t] = (float)A.Ke[t];
-    }
-    __syncthreads();
-    const unsigned G = gridDim.x;
-    const int64_t stride = (int64_t)G * blockDim.x;
-    const int64_t a0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    double *partA = A.part, *partB = A.part + (size_t)G * 8;
-    const double zb64[2] = {0.0, 0.0};
-    double rr_true[2] = {0.0, 0.0}, bb[2] = {0.0, 0.0};
-    int total_inner = 0;
-    for (int outer = 0;; ++outer) {
-        // FP64 residual; inner vectors start at d = 0, r = b - K x, p = z = M^-1 r
-        double v[6] = {0, 0, 0, 0, 0, 0};
-        for (int64_t a = a0; a < g.n_nodes; a += stride) {
-            double kx[6];
-            spmv_node_t<double>(g, sKe, a, A.x, nullptr, zb64, kx);
-            float rf[6], zf[6];
-#pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                double bc = A.b[a * 6 + c];
-                double r64 = bc - kx[c];
-                rf[c] = (float)r64;
-                v[2 + c / 3] += r64 * r64;
-                v[4 + c / 3] += bc * bc;
-            }
-            apply_minv_f(A.Minv + a * 9, rf, zf);
-#pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                A.r[a * 6 + c] = rf[c];
-                A.z[a * 6 + c] = zf[c];
-                A.p0[a * 6 + c] = zf[c];
-                A.d[a * 6 + c] = 0.f;
-                v[c / 3] += (double)rf[c] * (double)zf[c];
-            }
-        }
-        block_sum<6>(v, sh);
-        if (threadIdx.x == 0)
-            for (int c = 0; c < 6; ++c) partB[blockIdx.x * 8 + c] = v[c];
-        if (!grid_barrier(A.bar, G, A.err)) return;
-        double tot[6];
-        grid_total<6>(partB, G, tot, sh);
-        double rz[2] = {tot[0], tot[1]};
-        bool conv[2];
-        for (int s = 0; s < 2; ++s) {
-            rr_true[s] = tot[2 + s];
-            bb[s] = tot[4 + s];
-            conv[s] = !(rr_true[s] > A.rtol2 * bb[s]) || bb[s] == 0.0;
-        }
-        if ((conv[0] && conv[1]) || outer >= A.max_outer) {
-            // a system with b = 0 has the solution x = 0
-            for (int s = 0; s < 2; ++s)
-                if (bb[s] == 0.0)
-                    for (int64_t a = a0; a < g.n_nodes; a += stride)
-                        for (int c = 0; c < 3; ++c) A.x[a * 6 + 3 * s + c] = 0.0;
-            break;
-        }
-        const double target[2] = {A.in_rtol2 * rr_true[0], A.in_rtol2 * rr_true[1]};
-        bool ic[2] = {conv[0], conv[1]};
-        float beta[2] = {0.f, 0.f};
-        float *pold = A.p0, *pnew = A.p1;
-        for (int it = 0; it < A.max_inner && !(ic[0] && ic[1]); ++it) {
-            double w[2] = {0, 0};
-            for (int64_t a = a0; a < g.n_nodes; a += stride) {
-                float kq[6];
-                spmv_node_t<float>(g, sKf, a, A.z, pold, beta, kq);
-#pragma unroll
-                for (int c = 0; c < 6; ++c) {
-                    float pn = A.z[a * 6 + c] + beta[c / 3] * pold[a * 6 + c];
-                    pnew[a * 6 + c] = pn;
-                    A.q[a * 6 + c] = kq[c];
-                    w[c / 3] += (double)pn * (double)kq[c];
-                }
-            }
-            block_sum<2>(w, sh);
-            if (threadIdx.x == 0) {
-                partA[blockIdx.x * 8 + 0] = w[0];
-                partA[blockIdx.x * 8 + 1] = w[1];
-            }
-            if (!grid_barrier(A.bar, G, A.err)) return;
-            double pq[2];
-            grid_total<2>(partA, G, pq, sh);
-            float alpha[2];
-            for (int s = 0; s < 2; ++s) alpha[s] = (ic[s] || !(pq[s] > 0.0)) ? 0.f : (float)(rz[s] / pq[s]);
-            double u[4] = {0, 0, 0, 0};
-            for (int64_t a = a0; a < g.n_nodes; a += stride) {
-                float rv[6], zv[6];
-#pragma unroll
-                for (int c = 0; c < 6; ++c) {
-                    float al = alpha[c / 3];
-                    A.d[a * 6 + c] += al * pnew[a * 6 + c];
-                    rv[c] = A.r[a * 6 + c] - al * A.q[a * 6 + c];
-                    A.r[a * 6 + c] = rv[c];
-                }
-                apply_minv_f(A.Minv + a * 9, rv, zv);
-#pragma unroll
-                for (int c = 0; c < 6; ++c) {
-                    A.z[a * 6 + c] = zv[c];
-                    u[c / 3] += (double)rv[c] * (double)zv[c];
-                    u[2 + c / 3] += (double)rv[c] * (double)rv[c];
-                }
-            }
-            block_sum<4>(u, sh);
-            if (threadIdx.x == 0)
-                for (int c = 0; c < 4; ++c) partB[blockIdx.x * 8 + c] = u[c];
-            if (!grid_barrier(A.bar, G, A.err)) return;
-            double t4[4];
-            grid_total<4>(partB, G, t4, sh);
-            for (int s = 0; s < 2; ++s) {
-                if (!ic[s]) {
-                    beta[s] = (rz[s] != 0.0) ? (float)(t4[s] / rz[s]) : 0.f;
-                    rz[s] = t4[s];
-                    ic[s] = !(t4[2 + s] > target[s]) || !(pq[s] > 0.0);
-                } else {
-                    beta[s] = 0.f;
-                }
-            }
-            float *t = pold;
-            pold = pnew;
-            pnew = t;
-            ++total_inner;
-        }
-        for (int64_t a = a0; a < g.n_nodes; a += stride)
-#pragma unroll
-            for (int c = 0; c < 6; ++c) A.x[a * 6 + c] += (double)A.d[a * 6 + c];
-        if (!grid_barrier(A.bar, G, A.err)) return;   // the next residual reads neighbours' x
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        *A.it_out = total_inner;
-        A.res_out[0] = bb[0] > 0 ? sqrt(rr_true[0] / bb[0]) : 0.0;
-        A.res_out[1] = bb[1] > 0 ? sqrt(rr_true[1] / bb[1]) : 0.0;
-    }
-}
-
-// ---------------------------------------------------------------------------
 __global__ void k_recover(MeshDev g, ElemOps ops, MetricMaps M, const double *__restrict__ x,
                           const double *__restrict__ star, double *__restrict__ y,
                           double *__restrict__ dpc) {
@@ -665,39 +495,15 @@ dd_status fem_block_jacobi(dd_ctx *ctx, const MeshDev &g, const double *Ke, doub
     return DD_OK;
 }
 
+// Mixed-precision CG (FP32 Krylov iterations inside FP64 iterative
+// refinement, batch.cu) of one system.
 dd_status fem_cg_mixed(dd_ctx *ctx, const MeshDev &g, const CGBuffers &B, double rtol, int max_it,
                        cudaStream_t s) {
-    int occ = 0;
-    DD_TRY_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg_mixed, kCgmThreads, 0));
-    if (occ < 1) return dd_fail(ctx, DD_ERR_CUDA, "CG kernel cannot be resident");
-    int64_t want = (g.n_nodes + kCgmThreads - 1) / kCgmThreads;
-    int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)std::min(occ, 8) * ctx->n_sm));
-    const size_t n6 = (size_t)g.n_nodes * 6;
-    CGMArgs A;
-    A.g = g;
-    A.Ke = B.Ke;
-    A.Minv = B.Minv;
-    A.b = B.b;
-    A.x = B.x;
-    A.r = reinterpret_cast<float *>(B.r);
-    A.d = A.r + n6;                      // the FP64 work arrays hold two FP32 vectors each
-    A.z = reinterpret_cast<float *>(B.z);
-    A.p0 = reinterpret_cast<float *>(B.p0);
-    A.p1 = reinterpret_cast<float *>(B.p1);
-    A.q = reinterpret_cast<float *>(B.q);
-    A.part = B.part;
-    A.bar = B.bar;
-    A.err = ctx->dev_err;
-    A.rtol2 = rtol * rtol;
-    A.in_rtol2 = 1e-8;                   // each refinement step gains four digits
-    A.max_outer = 30;
-    A.max_inner = max_it;
-    A.it_out = B.it_out;
-    A.res_out = B.res_out;
-    DD_TRY_CUDA(ctx, cudaMemsetAsync(B.bar, 0, 2 * sizeof(unsigned), s));
-    void *args[] = {&A};
-    ctx->launches++;
-    DD_TRY_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)k_cg_mixed, dim3(grid), dim3(kCgmThreads), args, 0, s));
+    const MeshDev *gs[1] = {&g};
+    const CGBuffers *cbs[1] = {&B};
+    int *it_dev = nullptr;
+    DD_TRY(dd_cg_segments(ctx, gs, cbs, 1, rtol, max_it, s, &it_dev));
+    DD_TRY_CUDA(ctx, cudaMemcpyAsync(B.it_out, it_dev, sizeof(int), cudaMemcpyDeviceToDevice, s));
     return DD_OK;
 }
 

@@ -52,6 +52,8 @@ dd_status fem_cg(dd_ctx *ctx, const MeshDev &g, const CGBuffers &B, double rtol,
                  cudaStream_t s);
 dd_status fem_cg_mixed(dd_ctx *ctx, const MeshDev &g, const CGBuffers &B, double rtol, int max_it,
                        cudaStream_t s);
+dd_status dd_cg_segments(dd_ctx *ctx, const MeshDev *const *gs, const CGBuffers *const *cbs, int n, double rtol,
+                         int max_it, cudaStream_t s, int **it_dev);
 dd_status fem_recover(dd_dataset *ds, const MeshDev &g, const ElemOps &ops, const double *x,
                       const double *star, double *y, double *dpc, cudaStream_t s);
 dd_status fem_iter_stats(dd_ctx *ctx, const int32_t *idx_new, const int32_t *idx_old, const double *d2,

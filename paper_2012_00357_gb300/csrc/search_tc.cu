@@ -43,8 +43,10 @@ constexpr int kTN = 128;            // data points per tile (MMA N)
 constexpr int kTM = 128;            // queries per CTA (MMA M)
 constexpr int kStages = 6;
 constexpr int kCap = 8;
-constexpr int kThreadsTC = 320;     // producer, MMA issuer, 8 epilogue warps
-constexpr int kEpiWarps = 8;
+// EPI epilogue warps (4 or 8) after the producer and MMA warps; with 8, two
+// warps share a TMEM lane quarter and take half of the tile's columns each
+template <int EPI>
+constexpr int tc_threads() { return 64 + 32 * EPI; }
 constexpr uint32_t kTileBytes = 4096;   // 128 rows x 16 fp16
 constexpr uint32_t kTmemCols = 256;
 
@@ -268,9 +270,17 @@ __global__ void k_prep_tc(const double *__restrict__ y, int64_t m, int64_t m_pad
     }
 }
 
+// Rare path of the epilogue (some score of the chunk is inside the window):
+// kept out of line so the hot loop stays small in the instruction cache.
+__device__ __noinline__ void epi_insert_chunk(CandState &cs, const float *v, int64_t j0, int64_t N, float w2,
+                                              float2 *buf, int st, bool topk) {
+    for (int k = 0; k < 32; ++k)
+        if (v[k] <= cs.lim && j0 + k < N) cand_insert(cs, v[k], (int)(j0 + k), w2, buf, st, kCap, topk);
+}
+
 // ---- the contraction kernel ------------------------------------------------------
-template <int KC>
-__global__ void __launch_bounds__(kThreadsTC, 2)
+template <int KC, int EPI>
+__global__ void __launch_bounds__(tc_threads<EPI>(), 2)
     k_scan_tc(const __half *__restrict__ zhi, const __half *__restrict__ zlo, int64_t N, int64_t n_tiles,
               const __half *__restrict__ qa, const QueryRec *__restrict__ rec, int64_t m, int splits, int64_t tps,
               CandHeader *__restrict__ hdr, float2 *__restrict__ cand, bool topk, unsigned *__restrict__ err) {
@@ -296,7 +306,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2)
         }
         for (int a = 0; a < 2; ++a) {
             dd_mbar_init(dd_smem_addr(&bar_tfull[a]), 1);
-            dd_mbar_init(dd_smem_addr(&bar_tempty[a]), kEpiWarps);
+            dd_mbar_init(dd_smem_addr(&bar_tempty[a]), EPI);
         }
         dd_mbar_init(dd_smem_addr(&bar_a), 1);
         dd_mbar_init(dd_smem_addr(&bar_done), 1);
@@ -379,13 +389,15 @@ __global__ void __launch_bounds__(kThreadsTC, 2)
             if (!dd_mbar_wait(dd_smem_addr(&bar_done), 0)) atomicOr(err, DEV_ERR_TIMEOUT);
         }
     } else {
-        // ---------------- epilogue: one query row and one column half per thread ----------------
+        // ---------------- epilogue: one query row (and column share) per thread ----------------
+        constexpr int kCols = kTN * 4 / EPI;          // columns per warp: 128 or 64
         const int quarter = warp & 3;
-        const int half = (warp - 2) >> 2;
+        const int half = (warp - 2) >> 2;             // 0 with 4 epilogue warps
         const int row = quarter * 32 + lane;
         const int64_t qi = (int64_t)blockIdx.x * kTM + row;
         const bool active = qi < m;
         const float w2 = active ? rec[qi].w2 : 0.f;
+        constexpr int kSt = kTM * EPI / 4;            // candidate buffer stride
         CandState cs;
         cand_init(cs, active);
         float2 *buf = sCand + half * kTM + row;
@@ -399,27 +411,21 @@ __global__ void __launch_bounds__(kThreadsTC, 2)
                 break;
             }
             tc_fence_after();
-            float v[64];
-            tmem_ld64(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)ab * kTN + (uint32_t)half * 64, v);
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) dd_mbar_arrive(dd_smem_addr(&bar_tempty[ab]));
-            const int64_t jb = (t_begin + t) * kTN + half * 64;
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                float u[32];
-#pragma unroll
-                for (int k = 0; k < 32; ++k) u[k] = v[32 * c + k];
-                const float mn = min32(u);
-                if (mn <= cs.lim) {
-                    const int64_t j0 = jb + 32 * c;
-#pragma unroll
-                    for (int k = 0; k < 32; ++k)
-                        if (u[k] <= cs.lim && j0 + k < N) cand_insert(cs, u[k], (int)(j0 + k), w2, buf, 2 * kTM, kCap, topk);
+            const int64_t jb = (t_begin + t) * kTN + half * kCols;
+#pragma unroll 1
+            for (int c = 0; c < kCols / 32; ++c) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)ab * kTN + (uint32_t)(half * kCols + c * 32),
+                          v);
+                if (c == kCols / 32 - 1) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) dd_mbar_arrive(dd_smem_addr(&bar_tempty[ab]));
                 }
+                if (min32(v) <= cs.lim) epi_insert_chunk(cs, v, jb + c * 32, N, w2, buf, kSt, topk);
             }
         }
-        if (active) cand_store(cs, buf, 2 * kTM, kCap, ((size_t)qi * splits + split) * 2 + half, hdr, cand);
+        if (active) cand_store(cs, buf, kSt, kCap, ((size_t)qi * splits + split) * (EPI / 4) + half, hdr, cand);
     }
     __syncthreads();
     if (warp == 1) {
@@ -431,7 +437,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2)
 
 template <int KC>
 size_t tc_smem_bytes() {
-    size_t s = KC * kTileBytes + kStages * (KC == 1 ? 1 : 2) * kTileBytes + kCap * 2 * kTM * 8 + 1024;
+    size_t s = KC * kTileBytes + kStages * (KC == 1 ? 1 : 2) * kTileBytes + kCap * 2 * kTM * 8 + 1024;   // EPI <= 8
     return s < 100 * 1024 ? 100 * 1024 : s;   // at most two CTAs (2 x 256 TMEM columns) per SM
 }
 
@@ -474,6 +480,30 @@ dd_status dd_build_fp16(dd_dataset *ds) {
     return DD_OK;
 }
 
+template <int KC, int EPI>
+static dd_status launch_tc(dd_ctx *ctx, dim3 grid, dd_dataset *ds, int64_t n_tiles, const __half *qa,
+                           const QueryRec *rec, int64_t m, int splits, int64_t tps, CandHeader *hdr, float2 *cand,
+                           bool topk, cudaStream_t s) {
+    const size_t sm = tc_smem_bytes<KC>();
+    DD_TRY_CUDA(ctx, cudaFuncSetAttribute(k_scan_tc<KC, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    ctx->launches++;
+    k_scan_tc<KC, EPI><<<grid, tc_threads<EPI>(), sm, s>>>(ds->z16hi, ds->z16lo, ds->N, n_tiles, qa, rec, m, splits,
+                                                           tps, hdr, cand, topk, ctx->dev_err);
+    DD_TRY_CUDA(ctx, cudaGetLastError());
+    return DD_OK;
+}
+
+static dd_status launch_tc_any(dd_ctx *ctx, int kc, int epi, dim3 grid, dd_dataset *ds, int64_t n_tiles,
+                               const __half *qa, const QueryRec *rec, int64_t m, int splits, int64_t tps,
+                               CandHeader *hdr, float2 *cand, cudaStream_t s) {
+    if (kc == 3) {
+        if (epi == 8) return launch_tc<3, 8>(ctx, grid, ds, n_tiles, qa, rec, m, splits, tps, hdr, cand, false, s);
+        return launch_tc<3, 4>(ctx, grid, ds, n_tiles, qa, rec, m, splits, tps, hdr, cand, false, s);
+    }
+    if (epi == 8) return launch_tc<1, 8>(ctx, grid, ds, n_tiles, qa, rec, m, splits, tps, hdr, cand, true, s);
+    return launch_tc<1, 4>(ctx, grid, ds, n_tiles, qa, rec, m, splits, tps, hdr, cand, true, s);
+}
+
 dd_status dd_search_exact_tc(dd_dataset *ds, const double *y_dev, int64_t m, int certify, SearchOut out,
                              dd_search_stats *st, cudaStream_t s) {
     dd_ctx *ctx = ds->ctx;
@@ -498,27 +528,36 @@ dd_status dd_search_exact_tc(dd_dataset *ds, const double *y_dev, int64_t m, int
     float2 *cand = (float2 *)(c + qa_bytes + rec_bytes + hdr_bytes);
 
     const double Rs = ds->R * ds->scale16 * (1.0 + 1e-6);
-    ctx->launches += 2;
+    ctx->launches++;
     k_prep_tc<<<(unsigned)((m_pad + 127) / 128), 128, 0, s>>>(y_dev, m, m_pad, ds->M, ds->scale16, Rs, kc, qa, rec);
     DD_TRY_CUDA(ctx, cudaGetLastError());
     dim3 grid((unsigned)qtiles, (unsigned)splits);
-    if (st) DD_TRY_CUDA(ctx, cudaEventRecord(ctx->ev_scan[0], s));
-    if (kc == 3) {
-        size_t sm = tc_smem_bytes<3>();
-        DD_TRY_CUDA(ctx, cudaFuncSetAttribute(k_scan_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_scan_tc<3><<<grid, kThreadsTC, sm, s>>>(ds->z16hi, ds->z16lo, ds->N, n_tiles, qa, rec, m, splits, tps, hdr,
-                                                  cand, false, ctx->dev_err);
-    } else {
-        size_t sm = tc_smem_bytes<1>();
-        DD_TRY_CUDA(ctx, cudaFuncSetAttribute(k_scan_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_scan_tc<1><<<grid, kThreadsTC, sm, s>>>(ds->z16hi, ds->z16lo, ds->N, n_tiles, qa, rec, m, splits, tps, hdr,
-                                                  cand, true, ctx->dev_err);
+    // Autotuner: the first large call of each precision times both epilogue
+    // layouts (4 or 8 epilogue warps) on the live problem and keeps the faster
+    // one for this context; both return the same certified candidates.
+    int &epi = ctx->tc_epi[kc == 3 ? 1 : 0];
+    if (epi == 0 && (double)m * (double)ds->N >= 1e9) {
+        float best = 1e30f;
+        for (int e : {4, 8}) {
+            DD_TRY_CUDA(ctx, cudaEventRecord(ctx->ev_scan[0], s));
+            DD_TRY(launch_tc_any(ctx, kc, e, grid, ds, n_tiles, qa, rec, m, splits, tps, hdr, cand, s));
+            DD_TRY_CUDA(ctx, cudaEventRecord(ctx->ev_scan[1], s));
+            DD_TRY_CUDA(ctx, cudaEventSynchronize(ctx->ev_scan[1]));
+            float ms = 0.f;
+            DD_TRY_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev_scan[0], ctx->ev_scan[1]));
+            if (ms < best) {
+                best = ms;
+                epi = e;
+            }
+        }
     }
-    DD_TRY_CUDA(ctx, cudaGetLastError());
+    const int use_epi = epi ? epi : 4;
+    if (st) DD_TRY_CUDA(ctx, cudaEventRecord(ctx->ev_scan[0], s));
+    DD_TRY(launch_tc_any(ctx, kc, use_epi, grid, ds, n_tiles, qa, rec, m, splits, tps, hdr, cand, s));
     if (st) DD_TRY_CUDA(ctx, cudaEventRecord(ctx->ev_scan[1], s));
     if (st) st->distances += m * ds->N;
-    DD_TRY(dd_merge_rescore(ds, y_dev, m, 2 * splits, kCap, hdr, cand, rec, certify, 1.0 / (ds->scale16 * ds->scale16),
-                            out, st, s));
+    DD_TRY(dd_merge_rescore(ds, y_dev, m, splits * (use_epi / 4), kCap, hdr, cand, rec, certify,
+                            1.0 / (ds->scale16 * ds->scale16), out, st, s));
     if (st) {
         float ms = 0.f;
         DD_TRY_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev_scan[0], ctx->ev_scan[1]));
