@@ -102,6 +102,10 @@ typedef struct dd_dataset_opts {
     int borrow;         /* 1 and eps_sig is a device pointer: keep using the
                            caller's buffer instead of copying it; it must stay
                            valid and unchanged until dd_free_dataset */
+    int ann_levels;     /* 1 (default): ann_nlist k-means clusters in one level;
+                           2: a two-level k-means tree, about sqrt(ann_nlist)
+                           coarse cells each split into leaves, ann_nlist
+                           leaves in total (for 10^8 - 10^9 points) */
 } dd_dataset_opts;
 
 /* Load a material data set D = {(eps_j, sig_j)}, j = 0..N-1 (Sec. 2) and

@@ -41,7 +41,7 @@ class DDError(RuntimeError):
 
 class dd_dataset_opts(ctypes.Structure):
     _fields_ = [("build_fp16", c_int), ("ann_nlist", c_int), ("ann_train_iters", c_int),
-                ("ann_sample", c_int64), ("seed", c_uint64), ("borrow", c_int)]
+                ("ann_sample", c_int64), ("seed", c_uint64), ("borrow", c_int), ("ann_levels", c_int)]
 
 
 class dd_search_opts(ctypes.Structure):
@@ -200,11 +200,11 @@ def dd_bytes_in_use(ctx) -> int:
 
 
 def dd_load_dataset(ctx, eps_sig, C, build_fp16: bool = False, ann_nlist: int = 0, ann_train_iters: int = 0,
-                    ann_sample: int = 0, seed: int = 0, borrow: bool = False):
+                    ann_sample: int = 0, seed: int = 0, borrow: bool = False, ann_levels: int = 1):
     N = int(eps_sig.shape[0])
     assert tuple(eps_sig.shape[1:]) == (12,)
     opts = dd_dataset_opts(int(build_fp16), int(ann_nlist), int(ann_train_iters), int(ann_sample), int(seed),
-                           int(borrow))
+                           int(borrow), int(ann_levels))
     ds = c_void_p()
     _check(ctx, lib().dd_load_dataset(ctx, _ptr(eps_sig), N, _Cmat(C), ctypes.byref(opts), ctypes.byref(ds)))
     return ds

@@ -366,6 +366,256 @@ __global__ void k_ann_finish(const float *__restrict__ raw, MetricMaps M, const 
     if (d2nd) d2nd[i] = 2.0 * (double)d2f[i];
 }
 
+// ---------------------------------------------------------------------------
+// Two-level tree: coarse cells of k-means centroids, each split into L2
+// k-means leaves (the k-means tree of Sec. 4.2 with wide branching).
+// ---------------------------------------------------------------------------
+__global__ void k_scatter_idx(const int32_t *__restrict__ asg, int64_t n, const int64_t *__restrict__ offs,
+                              unsigned *__restrict__ cursor, int32_t *__restrict__ perm1) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int c = asg[j];
+    perm1[offs[c] + atomicAdd(cursor + c, 1u)] = (int32_t)j;
+}
+
+__global__ void k_cell_sorted(const int32_t *__restrict__ perm1, const int32_t *__restrict__ asg1, int64_t n,
+                              int32_t *__restrict__ c1s) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p < n) c1s[p] = asg1[perm1[p]];
+}
+
+// leaf f of cell C starts at the cell's member of rank floor(f n_C / L2)
+__global__ void k_fine_init(const float *__restrict__ z, const int32_t *__restrict__ perm1,
+                            const int64_t *__restrict__ offs1, int L1, int L2, const float *__restrict__ cent1,
+                            float *__restrict__ centf) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)L1 * L2) return;
+    const int C = (int)(t / L2), f = (int)(t % L2);
+    const int64_t n_c = offs1[C + 1] - offs1[C];
+    const float *src = cent1 + (size_t)C * 12;
+    if (n_c > 0) src = z + (size_t)perm1[offs1[C] + (int64_t)f * n_c / L2] * 12;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) centf[t * 12 + k] = src[k];
+}
+
+// Nearest leaf of every point among its own cell's L2 leaves.  Points are
+// visited in cell order (p = sorted position), so a block meets few cells;
+// each cell's leaf centroids stream through shared memory once per block.
+__global__ void __launch_bounds__(256) k_assign_fine(const float *__restrict__ z, const int32_t *__restrict__ perm1,
+                                                     const int32_t *__restrict__ c1s, int64_t n,
+                                                     const float *__restrict__ centf, const float *__restrict__ cnf,
+                                                     int L2, int32_t *__restrict__ fasg) {
+    __shared__ __align__(16) float sc[kTileC * 12];
+    __shared__ float sn[kTileC];
+    __shared__ int s_first, s_last;
+    const int64_t p0 = (int64_t)blockIdx.x * blockDim.x;
+    const int64_t p = p0 + threadIdx.x;
+    const bool act = p < n;
+    float q[12];
+    int my_c = -1;
+    if (act) {
+        my_c = c1s[p];
+        const float *zp = z + (size_t)perm1[p] * 12;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) q[k] = -2.f * zp[k];
+    } else {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) q[k] = 0.f;
+    }
+    if (threadIdx.x == 0) {
+        s_first = c1s[p0];
+        s_last = c1s[min(n, p0 + (int64_t)blockDim.x) - 1];
+    }
+    __syncthreads();
+    const int cf = s_first, cl = s_last;
+    float best = INFINITY;
+    int bi = 0;
+    for (int c = cf; c <= cl; ++c) {
+        for (int t0 = 0; t0 < L2; t0 += kTileC) {
+            const int nt = min(kTileC, L2 - t0);
+            __syncthreads();
+            const float *src = centf + ((size_t)c * L2 + t0) * 12;
+            for (int t = threadIdx.x; t < nt * 12; t += blockDim.x) sc[t] = src[t];
+            for (int t = threadIdx.x; t < nt; t += blockDim.x) sn[t] = cnf[(size_t)c * L2 + t0 + t];
+            __syncthreads();
+            if (my_c == c) {
+                for (int f = 0; f < nt; ++f) {
+                    const float4 *pc = reinterpret_cast<const float4 *>(sc + f * 12);
+                    float4 a = pc[0], b = pc[1], d = pc[2];
+                    float v = sn[f];
+                    v = fmaf(q[0], a.x, v); v = fmaf(q[1], a.y, v); v = fmaf(q[2], a.z, v); v = fmaf(q[3], a.w, v);
+                    v = fmaf(q[4], b.x, v); v = fmaf(q[5], b.y, v); v = fmaf(q[6], b.z, v); v = fmaf(q[7], b.w, v);
+                    v = fmaf(q[8], d.x, v); v = fmaf(q[9], d.y, v); v = fmaf(q[10], d.z, v); v = fmaf(q[11], d.w, v);
+                    if (v < best) {
+                        best = v;
+                        bi = t0 + f;
+                    }
+                }
+            }
+        }
+    }
+    if (act) fasg[p] = bi;
+}
+
+__global__ void k_accum_fine(const float *__restrict__ z, const int32_t *__restrict__ perm1,
+                             const int32_t *__restrict__ c1s, const int32_t *__restrict__ fasg, int64_t n, int L2,
+                             double *__restrict__ sums, unsigned *__restrict__ cnt) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int64_t leaf = (int64_t)c1s[p] * L2 + fasg[p];
+    const float *zp = z + (size_t)perm1[p] * 12;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) atomicAdd(sums + leaf * 12 + k, (double)zp[k]);
+    atomicAdd(cnt + leaf, 1u);
+}
+
+__global__ void k_leaf_of(const int32_t *__restrict__ perm1, const int32_t *__restrict__ c1s,
+                          const int32_t *__restrict__ fasg, int64_t n, int L2, int32_t *__restrict__ leaf_of) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p < n) leaf_of[perm1[p]] = c1s[p] * L2 + fasg[p];
+}
+
+__global__ void k_radius_orig(const float *__restrict__ z, const int32_t *__restrict__ asg, int64_t n,
+                              const float *__restrict__ cent, unsigned *__restrict__ rbits) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int c = asg[j];
+    float q[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) q[k] = cent[(size_t)c * 12 + k];
+    float d = sqrtf(dist2_12(z + j * 12, q));
+    atomicMax(rbits + c, __float_as_uint(d * 1.000001f + 1e-30f));
+}
+
+struct Probe2Args {
+    ProbeArgs A;                // leaves in A.radius / A.offs / A.zs / A.perm / A.cluster_of; cand_* are coarse cells
+    const float *centf;         // [L x 12] leaf centroids
+    const float *rad1;          // [L1] coarse radii
+    int L1, L2;
+    float r1max;
+};
+
+constexpr int kFine = 8;        // leaves visited per cell at most
+constexpr int kFinePerLane = 16;   // L2 <= 512
+
+__global__ void __launch_bounds__(256) k_ann_probe2(Probe2Args P) {
+    const ProbeArgs &A = P.A;
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (i >= A.m) return;
+    float q[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) q[k] = A.rec[i].q[k];
+    Best b{INFINITY, 0x7fffffff, INFINITY};
+    int l0 = -1;
+    unsigned long long scanned = 0;
+    if (A.prev) {
+        const int j0 = A.prev[i];
+        if (j0 >= 0 && j0 < A.N) {
+            const float d0 = dist2_12(A.z32 + (size_t)j0 * 12, q);
+            if (A.mot_q) {
+                float mv = 0.f;
+#pragma unroll
+                for (int k = 0; k < 12; ++k) {
+                    float t = q[k] - A.mot_q[i * 12 + k];
+                    mv = fmaf(t, t, mv);
+                }
+                mv = sqrtf(mv);
+                const float r1 = A.mot_d[i * 2], r2 = A.mot_d[i * 2 + 1];
+                if (mv < 0.5f * (r2 - r1)) {      // Eq. (14)
+                    if (lane == 0) {
+                        A.idx[i] = j0;
+                        A.d1[i] = d0;
+                        float lb = fmaxf(r2 - mv, 0.f);
+                        A.d2[i] = lb * lb;
+                        atomicAdd(A.counters + 1, 1ull);
+                    }
+                    return;
+                }
+            }
+            b.d = d0;
+            b.j = j0;
+            l0 = A.cluster_of[j0];
+        }
+    }
+    auto scan = [&](int l) {
+        const int64_t p0 = A.offs[l], p1 = A.offs[l + 1];
+        for (int64_t p = p0 + lane; p < p1; p += 32) best_update(b, dist2_12(A.zs + p * 12, q), A.perm[p]);
+        scanned += (unsigned long long)(p1 - p0);
+        best_warp(b);
+    };
+    if (l0 >= 0) scan(l0);
+    float dc = sqrtf(b.d);
+    const float f_d = A.fd_q ? A.fd_q[i] : A.f_d;
+    bool incomplete = false;
+    for (int k1 = 0; k1 < kCand; ++k1) {
+        const int C = A.cand_cl[i * kCand + k1];
+        if (C < 0) break;
+        const float dC = A.cand_d[i * kCand + k1];
+        if (!(k1 == 0 || dC - f_d * P.rad1[C] < dc)) continue;
+        // rank the cell's leaves: lane holds leaves f = lane + 32 t
+        float fd[kFinePerLane];
+        unsigned vis = 0;
+#pragma unroll
+        for (int t = 0; t < kFinePerLane; ++t) {
+            const int f = lane + 32 * t;
+            fd[t] = (f < P.L2) ? sqrtf(dist2_12(P.centf + ((size_t)C * P.L2 + f) * 12, q)) : INFINITY;
+        }
+        scanned += (unsigned long long)P.L2;
+        for (int k2 = 0; k2 < kFine; ++k2) {
+            float md = INFINITY;
+            int mt = -1;
+#pragma unroll
+            for (int t = 0; t < kFinePerLane; ++t)
+                if (!((vis >> t) & 1u) && fd[t] < md) {
+                    md = fd[t];
+                    mt = t;
+                }
+            int ml = mt >= 0 ? lane + 32 * mt : 0x7fffffff;
+            for (int o = 16; o > 0; o >>= 1) {
+                float od = __shfl_xor_sync(0xffffffffu, md, o);
+                int ol = __shfl_xor_sync(0xffffffffu, ml, o);
+                if (od < md || (od == md && ol < ml)) {
+                    md = od;
+                    ml = ol;
+                }
+            }
+            if (!(md < INFINITY)) break;
+            if ((ml & 31) == lane) vis |= 1u << (ml >> 5);
+            const int l = C * P.L2 + ml;
+            if ((k1 == 0 && k2 == 0) || md - f_d * A.radius[l] < dc) {
+                if (l != l0) {
+                    scan(l);
+                    dc = sqrtf(b.d);
+                }
+            }
+        }
+        // leaves of this cell beyond the kFine nearest (exact requests only)
+        if (f_d >= 1.0f && P.L2 > kFine) {
+            float md = INFINITY;
+#pragma unroll
+            for (int t = 0; t < kFinePerLane; ++t)
+                if (!((vis >> t) & 1u)) md = fminf(md, fd[t]);
+            for (int o = 16; o > 0; o >>= 1) md = fminf(md, __shfl_xor_sync(0xffffffffu, md, o));
+            if (md - f_d * A.rmax < dc) incomplete = true;
+        }
+    }
+    if (f_d >= 1.0f && P.L1 > kCand) {
+        const float dP = A.cand_d[i * kCand + kCand - 1];
+        if (dP - f_d * P.r1max < dc) incomplete = true;
+    }
+    if (lane == 0) {
+        atomicAdd(A.counters, scanned);
+        if (incomplete) {
+            unsigned long long t = atomicAdd(A.fb_count, 1ull);
+            A.fb_list[t] = i;
+        }
+        A.idx[i] = b.j;
+        A.d1[i] = b.d;
+        A.d2[i] = b.s;
+    }
+}
+
 __global__ void k_motion_update(const QueryRec *__restrict__ rec, int64_t m, const double *__restrict__ d2,
                                 const double *__restrict__ d2nd, float *__restrict__ mq, float *__restrict__ md) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -475,10 +725,19 @@ void dd_free_ann(dd_dataset *ds) {
     dd_free(ctx, a.perm, (size_t)ds->N * 4);
     dd_free(ctx, a.cluster_of, (size_t)ds->N * 4);
     dd_free(ctx, a.zs, (size_t)ds->N * 48);
+    if (a.levels == 2) {
+        size_t L1p = (size_t)(a.L1 + 255) / 256 * 256;
+        dd_free(ctx, a.cent1, L1p * 48);
+        dd_free(ctx, a.cn1, L1p * 4);
+        dd_free(ctx, a.rad1, L1p * 4);
+    }
     a = AnnIndex();
 }
 
+static dd_status build_tree2(dd_dataset *ds, const dd_dataset_opts &o);
+
 dd_status dd_build_ann(dd_dataset *ds, const dd_dataset_opts &o) {
+    if (o.ann_levels == 2) return build_tree2(ds, o);
     dd_ctx *ctx = ds->ctx;
     cudaStream_t s = ctx->stream;
     AnnIndex &a = ds->ann;
@@ -574,6 +833,150 @@ dd_status dd_build_ann(dd_dataset *ds, const dd_dataset_opts &o) {
     return DD_OK;
 }
 
+// Two-level tree: coarse k-means cells (Lloyd on a sample), every cell split
+// into L2 k-means leaves (Lloyd over the cell's members), points stored in
+// leaf order.  Leaf C * L2 + f belongs to cell C.
+static dd_status build_tree2(dd_dataset *ds, const dd_dataset_opts &o) {
+    dd_ctx *ctx = ds->ctx;
+    cudaStream_t s = ctx->stream;
+    AnnIndex &a = ds->ann;
+    const int64_t N = ds->N;
+    int L1 = 1 << (int)std::lround(std::log2(std::sqrt((double)std::max(1, o.ann_nlist))));
+    L1 = (int)std::max<int64_t>(1, std::min<int64_t>(L1, N));
+    const int L2 = (int)std::min<int64_t>(512, std::max<int64_t>(1, (o.ann_nlist + L1 - 1) / L1));
+    const int L = L1 * L2;
+    const int64_t Lp = (L + 255) / 256 * 256, L1p = (L1 + 255) / 256 * 256;
+    const int iters = o.ann_train_iters > 0 ? o.ann_train_iters : 8;
+    int64_t S1 = o.ann_sample > 0 ? o.ann_sample : (int64_t)64 * L1;
+    S1 = std::max<int64_t>(std::min<int64_t>(S1, N), L1);
+    a.levels = 2;
+    a.nlist = L;
+    a.L1 = L1;
+    a.L2 = L2;
+    void *p = nullptr;
+    DD_TRY(dd_alloc(ctx, &p, Lp * 48, "ANN leaf centroids"));
+    a.cent = (float *)p;
+    DD_TRY(dd_alloc(ctx, &p, Lp * 4, "ANN leaf norms"));
+    a.cn = (float *)p;
+    DD_TRY(dd_alloc(ctx, &p, Lp * 4, "ANN leaf radii"));
+    a.radius = (float *)p;
+    DD_TRY(dd_alloc(ctx, &p, (Lp + 1) * 8, "ANN offsets"));
+    a.offs = (int64_t *)p;
+    DD_TRY(dd_alloc(ctx, &p, (size_t)N * 4, "ANN permutation"));
+    a.perm = (int32_t *)p;
+    DD_TRY(dd_alloc(ctx, &p, (size_t)N * 4, "ANN leaf map"));
+    a.cluster_of = (int32_t *)p;
+    DD_TRY(dd_alloc(ctx, &p, (size_t)N * 48, "ANN sorted data"));
+    a.zs = (float *)p;
+    DD_TRY(dd_alloc(ctx, &p, L1p * 48, "ANN cell centroids"));
+    a.cent1 = (float *)p;
+    DD_TRY(dd_alloc(ctx, &p, L1p * 4, "ANN cell norms"));
+    a.cn1 = (float *)p;
+    DD_TRY(dd_alloc(ctx, &p, L1p * 4, "ANN cell radii"));
+    a.rad1 = (float *)p;
+    ds->bytes += Lp * 60 + (size_t)N * 56 + L1p * 56;
+
+    auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t b_sample = r256((size_t)S1 * 48), b_n = r256((size_t)N * 4), b_sums = r256((size_t)Lp * 96),
+                 b_cnt = r256((size_t)Lp * 4), b_offs1 = r256((size_t)(L1p + 1) * 8);
+    void *w = nullptr;
+    DD_TRY(dd_workspace(ctx, WS_ANN_BUILD, b_sample + 4 * b_n + b_sums + b_cnt + b_offs1, &w));
+    char *c = (char *)w;
+    float *sample = (float *)c;
+    int32_t *asg1 = (int32_t *)(c + b_sample);
+    int32_t *perm1 = (int32_t *)(c + b_sample + b_n);
+    int32_t *c1s = (int32_t *)(c + b_sample + 2 * b_n);
+    int32_t *fasg = (int32_t *)(c + b_sample + 3 * b_n);
+    double *sums = (double *)(c + b_sample + 4 * b_n);
+    unsigned *cnt = (unsigned *)(c + b_sample + 4 * b_n + b_sums);
+    int64_t *offs1 = (int64_t *)(c + b_sample + 4 * b_n + b_sums + b_cnt);
+    const unsigned gN = (unsigned)((N + 255) / 256);
+
+    // ---- coarse level ----
+    ctx->launches += 2;
+    k_gather_rows<<<(unsigned)((S1 + 255) / 256), 256, 0, s>>>(ds->z32, N, S1, sample);
+    DD_TRY_CUDA(ctx, cudaMemsetAsync(a.cent1, 0, L1p * 48, s));
+    k_gather_rows<<<(unsigned)((L1 + 255) / 256), 256, 0, s>>>(sample, S1, L1, a.cent1);
+    DD_TRY_CUDA(ctx, cudaMemsetAsync(sums, 0, b_sums, s));
+    DD_TRY_CUDA(ctx, cudaMemsetAsync(cnt, 0, b_cnt, s));
+    ctx->launches++;
+    k_update<<<(unsigned)((L1 + 255) / 256), 256, 0, s>>>(sums, cnt, a.cent1, a.cn1, L1);
+    for (int it = 0; it < iters; ++it) {
+        ctx->launches += 3;
+        k_assign<<<(unsigned)((S1 + 255) / 256), 256, 0, s>>>(sample, S1, a.cent1, a.cn1, L1, asg1);
+        k_accum<<<(unsigned)((S1 + 255) / 256), 256, 0, s>>>(sample, S1, asg1, sums, cnt);
+        k_update<<<(unsigned)((L1 + 255) / 256), 256, 0, s>>>(sums, cnt, a.cent1, a.cn1, L1);
+    }
+    if (L1p > L1) {
+        std::vector<float> big((size_t)(L1p - L1), 1e30f);
+        DD_TRY_CUDA(ctx, cudaMemcpyAsync(a.cn1 + L1, big.data(), (L1p - L1) * 4, cudaMemcpyHostToDevice, s));
+    }
+    ctx->launches += 2;
+    k_assign<<<gN, 256, 0, s>>>(ds->z32, N, a.cent1, a.cn1, L1, asg1);
+    DD_TRY_CUDA(ctx, cudaMemsetAsync(cnt, 0, b_cnt, s));
+    k_hist<<<gN, 256, 0, s>>>(asg1, N, cnt);
+    DD_TRY_CUDA(ctx, cudaGetLastError());
+    std::vector<unsigned> hc1(L1);
+    std::vector<int64_t> ho1((size_t)L1p + 1, 0);
+    DD_TRY_CUDA(ctx, cudaMemcpyAsync(hc1.data(), cnt, (size_t)L1 * 4, cudaMemcpyDeviceToHost, s));
+    DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+    for (int l = 0; l < L1; ++l) ho1[l + 1] = ho1[l] + hc1[l];
+    for (int64_t l = L1; l < L1p; ++l) ho1[l + 1] = ho1[l];
+    DD_TRY_CUDA(ctx, cudaMemcpyAsync(offs1, ho1.data(), (L1p + 1) * 8, cudaMemcpyHostToDevice, s));
+    DD_TRY_CUDA(ctx, cudaMemsetAsync(cnt, 0, b_cnt, s));
+    ctx->launches += 3;
+    k_scatter_idx<<<gN, 256, 0, s>>>(asg1, N, offs1, cnt, perm1);
+    k_cell_sorted<<<gN, 256, 0, s>>>(perm1, asg1, N, c1s);
+    // ---- leaves: Lloyd inside every cell ----
+    k_fine_init<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(ds->z32, perm1, offs1, L1, L2, a.cent1, a.cent);
+    DD_TRY_CUDA(ctx, cudaMemsetAsync(sums, 0, b_sums, s));
+    DD_TRY_CUDA(ctx, cudaMemsetAsync(cnt, 0, b_cnt, s));
+    ctx->launches++;
+    k_update<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(sums, cnt, a.cent, a.cn, L);
+    for (int it = 0; it < iters; ++it) {
+        ctx->launches += 3;
+        k_assign_fine<<<gN, 256, 0, s>>>(ds->z32, perm1, c1s, N, a.cent, a.cn, L2, fasg);
+        k_accum_fine<<<gN, 256, 0, s>>>(ds->z32, perm1, c1s, fasg, N, L2, sums, cnt);
+        k_update<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(sums, cnt, a.cent, a.cn, L);
+    }
+    ctx->launches += 2;
+    k_assign_fine<<<gN, 256, 0, s>>>(ds->z32, perm1, c1s, N, a.cent, a.cn, L2, fasg);
+    k_leaf_of<<<gN, 256, 0, s>>>(perm1, c1s, fasg, N, L2, a.cluster_of);
+    // ---- leaf order, radii ----
+    DD_TRY_CUDA(ctx, cudaMemsetAsync(cnt, 0, b_cnt, s));
+    ctx->launches++;
+    k_hist<<<gN, 256, 0, s>>>(a.cluster_of, N, cnt);
+    DD_TRY_CUDA(ctx, cudaGetLastError());
+    std::vector<unsigned> hc(L);
+    std::vector<int64_t> ho((size_t)Lp + 1, 0);
+    DD_TRY_CUDA(ctx, cudaMemcpyAsync(hc.data(), cnt, (size_t)L * 4, cudaMemcpyDeviceToHost, s));
+    DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+    for (int l = 0; l < L; ++l) ho[l + 1] = ho[l] + hc[l];
+    for (int64_t l = L; l < Lp; ++l) ho[l + 1] = ho[l];
+    DD_TRY_CUDA(ctx, cudaMemcpyAsync(a.offs, ho.data(), (Lp + 1) * 8, cudaMemcpyHostToDevice, s));
+    DD_TRY_CUDA(ctx, cudaMemsetAsync(cnt, 0, b_cnt, s));
+    DD_TRY_CUDA(ctx, cudaMemsetAsync(a.radius, 0, Lp * 4, s));
+    DD_TRY_CUDA(ctx, cudaMemsetAsync(a.rad1, 0, L1p * 4, s));
+    ctx->launches += 3;
+    k_scatter<<<gN, 256, 0, s>>>(ds->z32, a.cluster_of, N, a.offs, cnt, a.zs, a.perm);
+    k_radius<<<gN, 256, 0, s>>>(a.zs, a.perm, a.cluster_of, N, a.cent, (unsigned *)a.radius);
+    k_radius_orig<<<gN, 256, 0, s>>>(ds->z32, asg1, N, a.cent1, (unsigned *)a.rad1);
+    DD_TRY_CUDA(ctx, cudaGetLastError());
+    std::vector<float> hr(L), hr1(L1);
+    DD_TRY_CUDA(ctx, cudaMemcpyAsync(hr.data(), a.radius, (size_t)L * 4, cudaMemcpyDeviceToHost, s));
+    DD_TRY_CUDA(ctx, cudaMemcpyAsync(hr1.data(), a.rad1, (size_t)L1 * 4, cudaMemcpyDeviceToHost, s));
+    DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+    a.rmax = 0.f;
+    a.r1max = 0.f;
+    a.nonempty = 0;
+    for (int l = 0; l < L; ++l) {
+        a.rmax = std::max(a.rmax, hr[l]);
+        a.nonempty += hc[l] > 0;
+    }
+    for (int l = 0; l < L1; ++l) a.r1max = std::max(a.r1max, hr1[l]);
+    return DD_OK;
+}
+
 dd_status dd_search_ann(dd_dataset *ds, const double *y_dev, int64_t m, double f_d, const int32_t *prev_idx_dev,
                         SearchOut out, dd_search_stats *st, cudaStream_t s) {
     return dd_search_ann_motion(ds, y_dev, m, f_d, nullptr, prev_idx_dev, nullptr, out, st, s);
@@ -605,9 +1008,13 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
     CandHeader *hdr = nullptr;
     float2 *cand = nullptr;
     if (st) DD_TRY_CUDA(ctx, cudaEventRecord(ctx->ev_scan[0], s));
-    DD_TRY(dd_scan_fp32_raw(ctx, a.cent, a.cn, a.nlist, rec, m, true, WS_ANN_SCAN, &splits, &cap, &hdr, &cand, s));
+    const bool two = a.levels == 2;
+    const float *rank_cent = two ? a.cent1 : a.cent;
+    DD_TRY(dd_scan_fp32_raw(ctx, rank_cent, two ? a.cn1 : a.cn, two ? a.L1 : a.nlist, rec, m, true, WS_ANN_SCAN,
+                            &splits, &cap, &hdr, &cand, s));
     ctx->launches += 3;
-    k_ann_cands<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(hdr, cand, splits, cap, rec, m, a.cent, cand_cl, cand_d);
+    k_ann_cands<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(hdr, cand, splits, cap, rec, m, rank_cent, cand_cl,
+                                                            cand_d);
     ProbeArgs A;
     A.zs = a.zs;
     A.perm = a.perm;
@@ -633,7 +1040,12 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
     A.fb_list = fb_list;
     A.fb_count = counters + 2;
     A.counters = counters;
-    k_ann_probe<<<(unsigned)((m * 32 + 255) / 256), 256, 0, s>>>(A);
+    if (two) {
+        Probe2Args P2{A, a.cent, a.rad1, a.L1, a.L2, a.r1max};
+        k_ann_probe2<<<(unsigned)((m * 32 + 255) / 256), 256, 0, s>>>(P2);
+    } else {
+        k_ann_probe<<<(unsigned)((m * 32 + 255) / 256), 256, 0, s>>>(A);
+    }
     DD_TRY_CUDA(ctx, cudaGetLastError());
     if (st) DD_TRY_CUDA(ctx, cudaEventRecord(ctx->ev_scan[1], s));
     k_ann_finish<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(ds->raw, ds->M, y_dev, m, out.idx, d2f, out.d2,
@@ -654,7 +1066,7 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
         float ms = 0.f;
         DD_TRY_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev_scan[0], ctx->ev_scan[1]));
         st->scan_ms += ms;
-        st->distances += (int64_t)h[0] + m * (int64_t)a.nlist + (int64_t)n_fb * ds->N;
+        st->distances += (int64_t)h[0] + m * (int64_t)(two ? a.L1 : a.nlist) + (int64_t)n_fb * ds->N;
         st->skipped += (int64_t)h[1];
         st->uncertified += (int64_t)n_fb;
     }

@@ -100,6 +100,14 @@ struct AnnIndex {
     float *zs = nullptr;        // [N x 12] mapped coordinates in sorted order
     float rmax = 0.f;           // largest radius
     int nonempty = 0;
+    // two-level tree (levels == 2): L1 coarse cells, each with L2 leaves
+    // (leaf C * L2 + f belongs to cell C); the leaves above are the fine level
+    int levels = 1;
+    int L1 = 0, L2 = 0;
+    float *cent1 = nullptr;     // [L1p x 12]
+    float *cn1 = nullptr;       // [L1p]
+    float *rad1 = nullptr;      // [L1p]
+    float r1max = 0.f;
 };
 
 // Moving-query record of the approximate search (Eq. 14), per query:

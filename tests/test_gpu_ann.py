@@ -121,3 +121,59 @@ def test_ann_solve_ramp_close_to_exact(ctx):
     assert ra.converged
     assert rel < 0.05
     assert np.all(np.diff(ra.d2_pd[5:]) <= 1e-12 * ra.d2_pd[0]) or True
+
+
+@pytest.fixture(scope="module")
+def treeset(ctx):
+    data = I.make_dataset(40000, I.NONLINEAR, seed=18)
+    ds = P.dd_load_dataset(ctx, data, C, ann_nlist=256, ann_levels=2, seed=5)
+    yield data, ds
+    P.dd_free_dataset(ds)
+
+
+def test_tree2_leaves_cover_members(ctx, treeset):
+    data, ds = treeset
+    cl, cent, rad = P.dd_dataset_ann_index(ds, ctx)
+    Z = metric.to_z(data.astype(np.float64), C)
+    d = np.sqrt(((Z - cent[cl]) ** 2).sum(1))
+    for l in np.unique(cl):
+        assert d[cl == l].max() <= rad[l] * (1 + 1e-5) + 1e-12
+
+
+def test_tree2_fd_one_is_exact(ctx, treeset):
+    data, ds = treeset
+    y = I.make_states(1500, I.NONLINEAR, seed=19, spread=0.3)
+    idx, d2, st = search(ctx, ds, y, 1.0)
+    assert_nn_parity(idx, d2, data, y, C)
+
+
+def test_tree2_warm_start_and_recall(ctx, treeset):
+    data, ds = treeset
+    Z = metric.to_z(data.astype(np.float64), C)
+    y = I.make_states(1500, I.NONLINEAR, seed=20, spread=0.02)
+    zq = metric.to_z(y, C)
+    prev = np.random.default_rng(3).integers(0, len(data), len(y)).astype(np.int32)
+    from gpu_util import oracle_nn
+    i1, _, _ = oracle_nn(data, y, C)
+    for f_d in (0.0, 0.4):
+        idx, d2, st = search(ctx, ds, y, f_d, prev)
+        dg = ((Z[idx] - zq) ** 2).sum(1)
+        assert np.all(dg <= ((Z[prev] - zq) ** 2).sum(1) * (1 + 1e-6))
+        print(f"tree2 f_d={f_d}: recall {np.mean(idx == i1):.4f}, points/query {st.distances / len(y):.0f}")
+        assert np.mean(idx == i1) >= (0.6 if f_d == 0.0 else 0.9)
+
+
+def test_tree2_solve_close_to_exact(ctx):
+    data = I.make_dataset(60000, I.NONLINEAR, seed=24)
+    load = I.load_case("torsion", 1e-3)
+    init = I.initial_association(8 * 64, len(data), seed=24)
+    ds = P.dd_load_dataset(ctx, data, C, ann_nlist=256, ann_levels=2, seed=6)
+    try:
+        re = P.dd_solve(ds, ctx, 4, load, init_idx=init)
+        ra = P.dd_solve(ds, ctx, 4, load, mode=P.DD_SEARCH_ANN, f_d0=0.0, f_d_final=0.6, ramp_iters=10,
+                        init_idx=init, max_iter=200)
+    finally:
+        P.dd_free_dataset(ds)
+    rel = abs(ra.d2_pd[-1] - re.d2_pd[-1]) / re.d2_pd[-1]
+    print(f"tree2 solve: exact d2 {re.d2_pd[-1]:.6e}, ANN d2 {ra.d2_pd[-1]:.6e}, rel {rel:.3e}")
+    assert ra.converged and rel < 0.05
