@@ -25,7 +25,7 @@
 
 namespace {
 
-constexpr int kBThreads = 128;
+constexpr int kBThreads = 256;
 constexpr int kGroups = kBThreads / 8;     // nodes per block and pass
 
 struct SegCG {
@@ -101,6 +101,7 @@ __global__ void __launch_bounds__(kBThreads) k_cg_batch(BCGArgs A) {
     const bool comp = e < 6;
     const int c = comp ? e : 0, sy = c / 3;
     const unsigned G = gridDim.x;
+    GridBar gbar{A.bar, G, 0u};
     const int lb = blockIdx.x - S.blk0;
     const bool leader = (lb == 0 && threadIdx.x == 0);
     const int64_t gstride = (int64_t)S.nblk * kGroups;
@@ -141,7 +142,7 @@ __global__ void __launch_bounds__(kBThreads) k_cg_batch(BCGArgs A) {
         block_sum<6>(v, sh);
         if (threadIdx.x == 0)
             for (int k = 0; k < 6; ++k) partB[blockIdx.x * 8 + k] = v[k];
-        if (!grid_barrier(A.bar, G, A.err)) return;
+        if (!grid_sync(gbar, A.err)) return;
         double tot[6];
         range_total<6>(partB, S.blk0, S.nblk, tot, sh);
         double rz[2] = {tot[0], tot[1]};
@@ -156,14 +157,17 @@ __global__ void __launch_bounds__(kBThreads) k_cg_batch(BCGArgs A) {
             outer_flag[sidx] = more ? 1 : 0;
             inner_flag[sidx] = more ? 1 : 0;
         }
-        if (!grid_barrier(A.bar, G, A.err)) return;
+        if (!grid_sync(gbar, A.err)) return;
         if (count_flags(outer_flag, A.S, sh) == 0) {
             for (int s2 = 0; s2 < 2; ++s2)
                 if (bb[s2] == 0.0 && comp && sy == s2)
                     for (int64_t a = a0; a < g.n_nodes; a += gstride) S.x[a * 6 + c] = 0.0;
             break;
         }
-        const double target[2] = {A.in_rtol2 * rr_true[0], A.in_rtol2 * rr_true[1]};
+        // gain four digits per refinement step, but never solve below a tenth
+        // of the final tolerance
+        const double target[2] = {fmax(A.in_rtol2 * rr_true[0], 0.01 * A.rtol2 * bb[0]),
+                                  fmax(A.in_rtol2 * rr_true[1], 0.01 * A.rtol2 * bb[1])};
         bool ic[2] = {conv[0] || !more, conv[1] || !more};
         float beta[2] = {0.f, 0.f};
         float *pold = S.p0, *pnew = S.p1;
@@ -188,7 +192,7 @@ __global__ void __launch_bounds__(kBThreads) k_cg_batch(BCGArgs A) {
                 partA[blockIdx.x * 8 + 0] = w[0];
                 partA[blockIdx.x * 8 + 1] = w[1];
             }
-            if (!grid_barrier(A.bar, G, A.err)) return;
+            if (!grid_sync(gbar, A.err)) return;
             // lagged stop: the leaders published their activity before this barrier
             if (count_flags(inner_flag, A.S, sh) == 0) break;
             double pq[2];
@@ -215,7 +219,7 @@ __global__ void __launch_bounds__(kBThreads) k_cg_batch(BCGArgs A) {
             block_sum<4>(u, sh);
             if (threadIdx.x == 0)
                 for (int k = 0; k < 4; ++k) partB[blockIdx.x * 8 + k] = u[k];
-            if (!grid_barrier(A.bar, G, A.err)) return;
+            if (!grid_sync(gbar, A.err)) return;
             double t4[4];
             range_total<4>(partB, S.blk0, S.nblk, t4, sh);
             for (int s2 = 0; s2 < 2; ++s2) {
@@ -235,7 +239,7 @@ __global__ void __launch_bounds__(kBThreads) k_cg_batch(BCGArgs A) {
         }
         if (comp)
             for (int64_t a = a0; a < g.n_nodes; a += gstride) S.x[a * 6 + c] += (double)S.d[a * 6 + c];
-        if (!grid_barrier(A.bar, G, A.err)) return;
+        if (!grid_sync(gbar, A.err)) return;
     }
     if (leader) A.it_out[sidx] = inner_count;
 }
@@ -255,7 +259,7 @@ dd_status dd_cg_segments(dd_ctx *ctx, const MeshDev *const *gs, const CGBuffers 
     for (int i = 0; i < n; ++i) nodes += gs[i]->n_nodes;
     int occ = 0;
     DD_TRY_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg_batch, kBThreads, 0));
-    const int cap = std::max(1, std::min(occ, 2)) * ctx->n_sm;
+    const int cap = std::max(1, std::min(occ, 1)) * ctx->n_sm;   // one block per SM: fewer barrier arrivals
     if (n > cap) return dd_fail(ctx, DD_ERR_ARG, "more solves than resident CG blocks");
     std::vector<int> nblk(n);
     int total = 0;

@@ -234,23 +234,23 @@ __device__ __forceinline__ double dd_eq3(const MetricMaps &M, const double *y, c
     return a + b;
 }
 
-// Bounded mbarrier wait.  Returns false on timeout.  The suspend-time hint
-// (20 us) lets a waiting thread sleep until the phase completes instead of
-// spinning and taking issue slots from the warps doing the work.
+// Bounded mbarrier wait.  Returns false on timeout.
 __device__ __forceinline__ bool dd_mbar_wait(uint32_t bar, uint32_t parity) {
     uint32_t done = 0;
     unsigned long long t0 = 0;
     for (int spin = 0;; ++spin) {
         asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
             " selp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(done)
-            : "r"(bar), "r"(parity), "r"(20000u)
+            : "r"(bar), "r"(parity)
             : "memory");
         if (done) return true;
-        unsigned long long t = dd_globaltimer();
-        if (t0 == 0) t0 = t;
-        else if (t - t0 > kWaitLimitNs) return false;
+        if ((spin & 63) == 0) {
+            unsigned long long t = dd_globaltimer();
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > kWaitLimitNs) return false;
+        }
     }
 }
 

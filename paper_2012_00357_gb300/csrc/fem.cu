@@ -201,6 +201,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg(CGArgs A) {
     for (int t = threadIdx.x; t < 576; t += blockDim.x) sKe[t] = A.Ke[t];
     __syncthreads();
     const unsigned G = gridDim.x;
+    GridBar gbar{A.bar, G, 0u};
     const int64_t stride = (int64_t)G * blockDim.x;
     const int64_t a0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const double zero_beta[2] = {0.0, 0.0};
@@ -233,7 +234,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg(CGArgs A) {
         if (threadIdx.x == 0)
             for (int c = 0; c < 6; ++c) partB[blockIdx.x * 8 + c] = v[c];
     }
-    if (!grid_barrier(A.bar, G, A.err)) return;
+    if (!grid_sync(gbar, A.err)) return;
     double tot[6];
     grid_total<6>(partB, G, tot, sh);
     double rz[2] = {tot[0], tot[1]}, rr[2] = {tot[2], tot[3]}, bb[2] = {tot[4], tot[5]};
@@ -262,7 +263,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg(CGArgs A) {
             partA[blockIdx.x * 8 + 0] = v[0];
             partA[blockIdx.x * 8 + 1] = v[1];
         }
-        if (!grid_barrier(A.bar, G, A.err)) return;
+        if (!grid_sync(gbar, A.err)) return;
         double pq[2];
         grid_total<2>(partA, G, pq, sh);
         double alpha[2];
@@ -289,7 +290,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg(CGArgs A) {
         block_sum<4>(w, sh);
         if (threadIdx.x == 0)
             for (int c = 0; c < 4; ++c) partB[blockIdx.x * 8 + c] = w[c];
-        if (!grid_barrier(A.bar, G, A.err)) return;
+        if (!grid_sync(gbar, A.err)) return;
         double t4[4];
         grid_total<4>(partB, G, t4, sh);
         for (int s = 0; s < 2; ++s) {

@@ -29,32 +29,42 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
     return v;
 }
 
-// Bounded grid barrier for a cooperative launch.  Returns false if any block
-// reported a timeout.
-__device__ bool grid_barrier(unsigned *bar, unsigned nblocks, unsigned *err) {
+// Bounded grid barrier for a cooperative launch: one monotonic arrival
+// counter (zeroed before the launch); barrier number k of the launch completes
+// when the counter reaches k * nblocks.  One release-add per block and
+// acquire polling, no reset round trip.  Returns false if any block reported
+// a timeout.
+struct GridBar {
+    unsigned *count;
+    unsigned nblocks;
+    unsigned epoch;
+};
+
+__device__ __forceinline__ void red_release_add(unsigned *p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ bool grid_sync(GridBar &gb, unsigned *err) {
     __shared__ int s_ok;
     __syncthreads();
+    gb.epoch++;
     if (threadIdx.x == 0) {
         int ok = 1;
-        unsigned g0 = ld_acquire(bar + 1);
-        __threadfence();
-        unsigned old = atomicAdd(bar, 1u);
-        if (old == nblocks - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            unsigned long long t0 = dd_globaltimer();
-            int spin = 0;
-            while (ld_acquire(bar + 1) == g0) {
-                if ((++spin & 31) == 0 && dd_globaltimer() - t0 > kWaitLimitNs) {
+        const unsigned target = gb.epoch * gb.nblocks;
+        red_release_add(gb.count, 1u);
+        unsigned long long t0 = 0;
+        int spin = 0;
+        while ((int)(ld_acquire(gb.count) - target) < 0) {
+            if ((++spin & 63) == 0) {
+                unsigned long long t = dd_globaltimer();
+                if (t0 == 0) t0 = t;
+                else if (t - t0 > kWaitLimitNs) {
                     atomicOr(err, DEV_ERR_TIMEOUT);
                     ok = 0;
                     break;
                 }
             }
         }
-        __threadfence();
         if (ok && (ld_acquire(err) & DEV_ERR_TIMEOUT)) ok = 0;
         s_ok = ok;
     }
