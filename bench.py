@@ -172,8 +172,11 @@ def run_ours(args, world, rank, local):
     raw = torch.empty((W.N, 12), dtype=torch.float32, device="cuda")
     P.dd_synth_dataset(ctx, raw, W.law, C, seed=W.seed)
     t_build = time.perf_counter()
+    levels = args.ann_levels or (2 if W.N >= 300_000_000 else 1)
+    if mode == P.DD_SEARCH_ANN and levels == 2 and not args.nlist:
+        nlist = 1 << 18
     ds = P.dd_load_dataset(ctx, raw, C, borrow=True, build_fp16=(mode == P.DD_SEARCH_EXACT_TC), ann_nlist=nlist,
-                           seed=1)
+                           seed=1, ann_levels=levels)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t_build
     load = I.load_case(*W.loads[0])
@@ -183,16 +186,27 @@ def run_ours(args, world, rank, local):
     ann_kw = dict(f_d0=0.0, f_d_final=args.fd_final, ramp_iters=20) if mode == P.DD_SEARCH_ANN else {}
     flush_l2 = data_bytes < 2 * L2_BYTES
 
-    def new_solver():
-        return P.dd_solver_create(ds, ctx, W.n_el, load, mode=mode, certify=certify, init_idx=init,
+    loads = [I.load_case(*lc) for lc in W.loads]
+    nload = len(loads)
+
+    def new_solver(k=0):
+        return P.dd_solver_create(ds, ctx, W.n_el, loads[k], mode=mode, certify=certify, init_idx=init,
                                   max_iter=100000, **ann_kw)
 
-    sv = new_solver()
+    svs = [new_solver(k) for k in range(nload)]
+
+    def step():
+        """One iteration of every load case (one batched call when there are several)."""
+        for k in range(nload):
+            if P.dd_solver_done(svs[k]):
+                P.dd_solver_free(svs[k])
+                svs[k] = new_solver(k)
+        if nload == 1:
+            return [P.dd_solver_step(svs[0], ctx)]
+        return P.dd_solvers_step(svs, ctx)
+
     for _ in range(args.warmup):
-        if P.dd_solver_done(sv):
-            P.dd_solver_free(sv)
-            sv = new_solver()
-        P.dd_solver_step(sv, ctx)
+        step()
 
     barrier(world)
     torch.cuda.synchronize()
@@ -202,14 +216,11 @@ def run_ours(args, world, rank, local):
     wall0 = time.perf_counter()
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
-            if P.dd_solver_done(sv):
-                P.dd_solver_free(sv)
-                sv = new_solver()
             if flush_l2:
                 flush.fill_(1.0)
             torch.cuda.synchronize()
             t = time.perf_counter()
-            info = P.dd_solver_step(sv, ctx)     # synchronous
+            info = step()[0]                     # synchronous; batched phases are shared
             step_ms.append((time.perf_counter() - t) * 1e3)
             scan_ms.append(info.scan_ms)
             infos.append(info)
@@ -223,19 +234,44 @@ def run_ours(args, world, rank, local):
     dev_ms = [i.cg_ms + i.other_ms + i.search_ms for i in infos]
     total_ms = sum(dev_ms)
     total_ms = max_over_ranks(total_ms, world)
-    searches = W.m * args.steps * world
+    searches = W.m * nload * args.steps * world
     value = searches / (total_ms / 1e3)
 
-    # full solve time from the random association (one solve, outside the steps)
+    # full solve time from the random association (all load cases together,
+    # outside the timed steps)
     t = time.perf_counter()
-    r = P.dd_solve(ds, ctx, W.n_el, load, mode=mode, certify=certify, init_idx=init, max_iter=200, **ann_kw)
+    if nload == 1:
+        rs = [P.dd_solve(ds, ctx, W.n_el, loads[0], mode=mode, certify=certify, init_idx=init, max_iter=200,
+                         **ann_kw)]
+    else:
+        rs = P.dd_solve_batch(ds, ctx, [W.n_el] * nload, loads, mode=mode, certify=certify, init_idx=init,
+                              max_iter=200, **ann_kw)
     solve_s = time.perf_counter() - t
+    r = rs[0]
+    accuracy = None
+    if mode == P.DD_SEARCH_ANN and args.ann_check > 0:
+        # agreement of the approximate answers with the certified exact search
+        # on a sample of the final states (FP32 scan + FP64 rescoring)
+        ys = np.concatenate([np.concatenate([rr.eps, rr.sig], axis=1) for rr in rs])
+        pick = np.random.default_rng(0).choice(len(ys), min(args.ann_check, len(ys)), replace=False)
+        ysel = np.ascontiguousarray(ys[pick])
+        prev = np.ascontiguousarray(np.concatenate([rr.idx for rr in rs])[pick])
+        ia = np.empty(len(pick), np.int32)
+        da = np.empty(len(pick))
+        ie = np.empty(len(pick), np.int32)
+        de = np.empty(len(pick))
+        P.dd_project_nearest(ds, ctx, ysel, ia, da, mode=P.DD_SEARCH_ANN, f_d=args.fd_final, prev_idx=prev)
+        P.dd_project_nearest(ds, ctx, ysel, ie, de, mode=P.DD_SEARCH_EXACT_FP32)
+        accuracy = {"sample": int(len(pick)), "same_index": float(np.mean(ia == ie)),
+                    "mean_rel_distance_excess": float(np.mean((da - de) / np.maximum(de, 1e-300))),
+                    "f_d": args.fd_final}
 
     # end-to-end through the public API with host buffers (pinned): one
     # projection of the step's m states per call, copies inside the timed region
-    y = torch.from_numpy(I.make_states(W.m, W.law, seed=7, spread=0.05)).pin_memory()
-    idx_h = torch.empty(W.m, dtype=torch.int32).pin_memory()
-    d2_h = torch.empty(W.m, dtype=torch.float64).pin_memory()
+    m_e2e = W.m * nload
+    y = torch.from_numpy(I.make_states(m_e2e, W.law, seed=7, spread=0.05)).pin_memory()
+    idx_h = torch.empty(m_e2e, dtype=torch.int32).pin_memory()
+    d2_h = torch.empty(m_e2e, dtype=torch.float64).pin_memory()
     P.dd_project_nearest(ds, ctx, y.numpy(), idx_h.numpy(), d2_h.numpy(), mode=mode, certify=certify)
     reps = max(3, args.steps)
     t = time.perf_counter()
@@ -249,8 +285,9 @@ def run_ours(args, world, rank, local):
     if mode == P.DD_SEARCH_ANN:
         # centroid ranking (FP32 scan over L centroids) + warp scans of the probed
         # clusters: algorithmic bytes = points scanned x 48 B + queries x 48 B + centroids
-        scanned = statistics.mean(i.distances - W.m * nlist for i in infos)
-        byts = scanned * 48 + W.m * 48 + nlist * 52
+        coarse = (1 << int(round(np.log2(np.sqrt(nlist))))) if levels == 2 else nlist
+        scanned = statistics.mean(i.distances - W.m * nload * coarse for i in infos)
+        byts = scanned * 48 + W.m * nload * 48 + coarse * 52
         achieved = byts / (scan_avg / 1e3) / 1e9
         roof = {"kernel": "k_ann_probe + centroid scan", "bound": "hbm", "achieved": achieved,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
@@ -280,13 +317,13 @@ def run_ours(args, world, rank, local):
         "vs_baseline": None, "dtype": "f64 (P_C, rescoring) + " + ("fp16 split, f32 accum" if kc == 3 and mode == 1
                                                                     else "fp16, f32 accum" if mode == 1 else "f32"),
         "data": "synthetic (dd_inputs generator, made on device)",
-        "config": {"workload": W.name, "mesh": f"{W.n_el}^3 hex, 2x2x2 Gauss", "material_points": W.m,
+        "config": {"workload": W.name, "mesh": f"{W.n_el}^3 hex, 2x2x2 Gauss", "material_points": W.m * nload,
                    "data_points": W.N, "law": W.law.kind, "load": W.loads[0][0], "search": args.mode,
                    "l2": "flushed before every step" if flush_l2 else "inputs larger than L2",
                    "parallelism": f"replicas x{world}"},
         "roofline": roof,
-        "e2e": {"value": W.m * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": W.m * 96,
-                "d2h_bytes_per_step": W.m * 12,
+        "e2e": {"value": m_e2e * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": m_e2e * 96,
+                "d2h_bytes_per_step": m_e2e * 12,
                 "what": "dd_project_nearest with pinned host buffers (states in, indices + distances out)"},
         "gpu_launches": launches,
         "clocks": clk.summary(),
@@ -299,13 +336,16 @@ def run_ours(args, world, rank, local):
             "wall_ms_per_step": statistics.mean(step_ms),
             "solve_s": solve_s, "solve_iters": r.iters, "solve_converged": r.converged,
             "solve_search_ms": r.search_ms, "solve_cg_ms": r.cg_ms, "solve_d2": float(r.d2_pd[-1]),
-            "index_build_s": build_s, "nlist": nlist,
+            "index_build_s": build_s, "nlist": nlist, "ann_levels": levels, "ann_vs_exact": accuracy,
+            "load_cases": [lc[0] for lc in W.loads],
+            "solve_d2_all": [float(rr.d2_pd[-1]) for rr in rs], "solve_iters_all": [rr.iters for rr in rs],
             "skipped": sum(getattr(i, "skipped", 0) for i in infos),
             "distances_per_query": statistics.mean(i.distances for i in infos) / W.m,
         },
     }
+    for sv in svs:
+        P.dd_solver_free(sv)
     P.dd_free_dataset(ds)
-    P.dd_solver_free(sv)
     P.dd_destroy(ctx)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_searches_per_s(W, C, target_s=args.cpu_seconds)
@@ -344,6 +384,8 @@ def main():
     ap.add_argument("--mode", default="tc", choices=["tc", "tc_topk", "fp32", "ann"])
     ap.add_argument("--fd-final", type=float, default=0.4)
     ap.add_argument("--nlist", type=int, default=0)
+    ap.add_argument("--ann-levels", type=int, default=0)
+    ap.add_argument("--ann-check", type=int, default=2048)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()
