@@ -352,6 +352,84 @@ def run_ours(args, world, rank, local):
     return line
 
 
+def run_serve(args, world, rank, local):
+    """Serving: resident data set, Poisson arrivals, continuous batching."""
+    import threading as th
+
+    import torch
+
+    import paper_2012_00357_gb300 as P
+
+    P.build()
+    torch.cuda.set_device(local)
+    W = make_workload(args.workload)
+    C = I.isotropic_C(W.law.E, W.law.nu)
+    ex = W.extra
+    ctx = P.dd_create(local)
+    raw = torch.empty((W.N, 12), dtype=torch.float32, device="cuda")
+    P.dd_synth_dataset(ctx, raw, W.law, C, seed=W.seed)
+    nlist = args.nlist or max(64, 1 << int(np.log2(max(W.N // 3000, 64))))
+    ds = P.dd_load_dataset(ctx, raw, C, borrow=True, ann_nlist=nlist, seed=1)
+    kw = dict(mode=P.DD_SEARCH_ANN, f_d0=0.0, f_d_final=args.fd_final, ramp_iters=20, max_iter=200)
+    n_req = ex["requests"]
+
+    def serve(reqs, budget):
+        srv = P.dd_server_start(ds, ctx, state_budget=budget, max_batch=args.max_batch, **kw)
+        tickets, lat, iters, m_tot = [None] * len(reqs), [None] * len(reqs), [0] * len(reqs), [0] * len(reqs)
+        t0 = time.perf_counter()
+
+        def submitter():
+            for r, (edge, load, at, seed) in enumerate(reqs):
+                dt = t0 + at - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                tickets[r] = P.dd_server_submit(srv, edge, load, seed=seed)
+
+        th_sub = th.Thread(target=submitter)
+        th_sub.start()
+        for r in range(len(reqs)):
+            while tickets[r] is None:
+                time.sleep(0.0005)
+            res, lat[r] = P.dd_server_poll(srv, ctx, tickets[r], timeout_s=600.0)
+            iters[r], m_tot[r] = res.iters, res.n_gp
+        th_sub.join()
+        makespan = time.perf_counter() - t0
+        st = P.dd_server_get_stats(srv)
+        P.dd_server_stop(srv)
+        return lat, iters, m_tot, makespan, st
+
+    budget = int(args.serve_budget_gb * 2 ** 30)
+    # calibration: a closed-loop burst gives the service rate
+    burst = [(e, L, 0.0, s) for (e, L, _, s) in I.serve_requests(W.seed + 1, 48, ex["edge_min"], ex["edge_max"],
+                                                                 ex["t_min"], ex["t_max"], 1.0)]
+    _, _, _, mk, _ = serve(burst, budget)
+    rate = 0.8 * len(burst) / mk
+    reqs = I.serve_requests(W.seed, n_req, ex["edge_min"], ex["edge_max"], ex["t_min"], ex["t_max"], rate)
+    with ClockSampler(local) as clk:
+        lat, iters, m_tot, makespan, st = serve(reqs, budget)
+    searches = sum(i * m for i, m in zip(iters, m_tot))
+    lat_s = sorted(lat)
+    line = {
+        "metric": METRIC, "value": searches / makespan, "unit": UNIT, "n_gpus": 1, "steps": n_req, "warmup": 48,
+        "ms_per_step": makespan * 1e3 / n_req, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 (P_C refinement, rescoring) + f32", "data": "synthetic (dd_inputs generator, made on device)",
+        "config": {"workload": W.name, "data_points": W.N, "requests": n_req, "edges": f"U{{{ex['edge_min']}..{ex['edge_max']}}}",
+                   "traction": f"U[{ex['t_min']}, {ex['t_max']}] random direction", "search": "ann",
+                   "f_d_final": args.fd_final, "nlist": nlist, "state_budget_gb": args.serve_budget_gb,
+                   "arrivals": f"Poisson, rate {rate:.2f}/s = 0.8 x calibrated service rate",
+                   "l2": "inputs larger than L2", "parallelism": "replicas x1"},
+        "serve": {"p50_ms": float(np.percentile(lat_s, 50)), "p99_ms": float(np.percentile(lat_s, 99)),
+                  "mean_ms": float(np.mean(lat_s)), "solves_per_s": n_req / makespan, "makespan_s": makespan,
+                  "lambda_per_s": rate, "max_active": int(st.max_active), "batched_steps": int(st.steps),
+                  "mean_iterations": float(np.mean(iters))},
+        "gpu_launches": int(P.dd_launch_count(ctx)),
+        "clocks": clk.summary(),
+    }
+    P.dd_free_dataset(ds)
+    P.dd_destroy(ctx)
+    return line
+
+
 def run_reference(args, world, rank):
     """The FP64 oracle on the host cores, same workload and metric."""
     if rank != 0:
@@ -381,7 +459,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cube16_N1e6_exact")
-    ap.add_argument("--mode", default="tc", choices=["tc", "tc_topk", "fp32", "ann"])
+    ap.add_argument("--mode", default="tc", choices=["tc", "tc_topk", "fp32", "ann", "serve"])
+    ap.add_argument("--max-batch", type=int, default=64)
+    ap.add_argument("--serve-budget-gb", type=float, default=16.0)
     ap.add_argument("--fd-final", type=float, default=0.4)
     ap.add_argument("--nlist", type=int, default=0)
     ap.add_argument("--ann-levels", type=int, default=0)
@@ -392,6 +472,8 @@ def main():
     world, rank, local = dist_setup()
     if args.impl == "reference":
         line = run_reference(args, world, rank)
+    elif args.mode == "serve":
+        line = run_serve(args, world, rank, local)
     else:
         line = run_ours(args, world, rank, local)
     if rank == 0 and line is not None:

@@ -236,6 +236,20 @@ def random_load(seed: int, r: int, tmin: float, tmax: float) -> Load:
     return Load(t0=(mag * sz * math.cos(phi), mag * sz * math.sin(phi), mag * cz))
 
 
+def serve_requests(seed: int, n: int, edge_min: int, edge_max: int, t_min: float, t_max: float,
+                   rate: float):
+    """Serving stream: for request r, a cube edge uniform in {edge_min..edge_max}
+    (elements), a random load (random_load) and an arrival time of a Poisson
+    process of the given rate (exponential gaps from uniform draws)."""
+    key = stream_key(seed, 99)
+    u = uniform53(draws(key, np.arange(2 * n, dtype=np.uint64))).reshape(n, 2)
+    edges = edge_min + np.minimum((u[:, 0] * (edge_max - edge_min + 1)).astype(np.int64), edge_max - edge_min)
+    gaps = -np.log1p(-u[:, 1]) / rate
+    arrivals = np.cumsum(gaps) - gaps[0]
+    return [(int(edges[r]), random_load(seed, r, t_min, t_max), int(arrivals[r] * 1e6) / 1e6, 1000 + r)
+            for r in range(n)]
+
+
 @dataclass(frozen=True)
 class Workload:
     name: str

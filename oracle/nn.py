@@ -22,11 +22,14 @@ _lib = None
 def build(force: bool = False) -> str:
     """Compile nn.c with gcc (OpenMP, no FP contraction) into oracle/_build."""
     src = os.path.join(_HERE, "nn.c")
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+    gen_src = os.path.join(os.path.dirname(_HERE), "dd_inputs", "gen.c")
+    newest = max(os.path.getmtime(src), os.path.getmtime(gen_src))
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < newest:
         os.makedirs(os.path.dirname(_SO), exist_ok=True)
         tmp = _SO + f".{os.getpid()}.tmp"
+        gen = os.path.join(os.path.dirname(_HERE), "dd_inputs", "gen.c")
         subprocess.run(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
-                        src, "-o", tmp, "-lm"], check=True)
+                        src, gen, "-o", tmp, "-lm"], check=True)
         os.replace(tmp, _SO)
     return _SO
 
@@ -42,6 +45,11 @@ def _load():
                                            ip, dp, ip, dp]
             lib.oracle_nn_top2.restype = None
             lib.oracle_nn_threads.restype = ctypes.c_int
+            vp = ctypes.c_void_p
+            lib.oracle_nn_stream.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_double, vp, ctypes.c_uint64, ctypes.c_int64, vp, vp, vp,
+                                             ctypes.c_int64, vp, vp]
+            lib.oracle_nn_stream.restype = None
             _lib = lib
     return _lib
 
@@ -72,3 +80,22 @@ def nn_top2(zd: np.ndarray, zq: np.ndarray):
                        i1.ctypes.data_as(ip), d1.ctypes.data_as(dp),
                        i2.ctypes.data_as(ip), d2.ctypes.data_as(dp))
     return i1, d1, i2, d2
+
+
+def nn_stream(law, seed: int, N: int, C, zq):
+    """Exact nearest point of every mapped query over the seeded data set of
+    N points (law: dd_inputs.DataLaw), generated chunk by chunk in C.
+    Returns (index int64, squared mapped distance)."""
+    from . import metric
+    lib = _load()
+    C = np.ascontiguousarray(C, dtype=np.float64)
+    Ch, Cmh = metric.metric_roots(C)
+    Ch = np.ascontiguousarray(Ch)
+    Cmh = np.ascontiguousarray(Cmh)
+    zq = np.ascontiguousarray(zq, dtype=np.float64)
+    m = len(zq)
+    i1 = np.empty(m, np.int64)
+    d1 = np.empty(m)
+    lib.oracle_nn_stream(law.code, law.eps_lo, law.eps_hi, law.noise_std, law.beta, C.ctypes.data, seed, N,
+                         Ch.ctypes.data, Cmh.ctypes.data, zq.ctypes.data, m, i1.ctypes.data, d1.ctypes.data)
+    return i1, d1

@@ -1,0 +1,62 @@
+"""Full-size sampled parity: the 10^8-point data set of the 32^3 workload,
+all 262 144 material-point queries through the kernels as benchmarked, a
+sample checked against the oracle's streaming brute force (which regenerates
+the data set itself from the seed, chunk by chunk)."""
+import numpy as np
+import pytest
+
+import dd_inputs as I
+from oracle import metric, nn
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2012_00357_gb300 as P  # noqa: E402
+
+C = I.isotropic_C()
+W = I.WORKLOADS["cube32_N1e8_ann"]
+
+
+@pytest.fixture(scope="module")
+def big():
+    P.build()
+    ctx = P.dd_create(0)
+    raw = torch.empty((W.N, 12), dtype=torch.float32, device="cuda")
+    P.dd_synth_dataset(ctx, raw, W.law, C, seed=W.seed)
+    ds = P.dd_load_dataset(ctx, raw, C, borrow=True, ann_nlist=1 << 15, ann_levels=2, seed=1)
+    y = I.make_states(W.m, W.law, seed=41, spread=0.02)
+    sample = np.random.default_rng(4).choice(W.m, 12, replace=False)
+    oi, od = nn.nn_stream(W.law, W.seed, W.N, C, metric.to_z(y[sample], C))
+    yield ctx, ds, y, sample, oi, od
+    P.dd_free_dataset(ds)
+    del raw
+    P.dd_destroy(ctx)
+
+
+def run(ctx, ds, y, **kw):
+    yd = torch.from_numpy(y).cuda()
+    idx = torch.empty(len(y), dtype=torch.int32, device="cuda")
+    d2 = torch.empty(len(y), dtype=torch.float64, device="cuda")
+    st = P.dd_project_nearest(ds, ctx, yd, idx, d2, **kw)
+    torch.cuda.synchronize()
+    return idx.cpu().numpy(), d2.cpu().numpy(), st
+
+
+def test_exact_fp32_full_size(big):
+    ctx, ds, y, sample, oi, od = big
+    idx, d2, st = run(ctx, ds, y, mode=P.DD_SEARCH_EXACT_FP32)
+    assert np.array_equal(idx[sample], oi)
+    assert np.allclose(d2[sample], 2 * od, rtol=1e-9)
+    print(f"exact N=1e8, m={len(y)}: uncertified {st.uncertified}, scan {st.scan_ms:.1f} ms")
+
+
+def test_ann_tree_fd_one_full_size(big):
+    ctx, ds, y, sample, oi, od = big
+    prev = np.random.default_rng(5).integers(0, W.N, len(sample)).astype(np.int32)
+    idx, d2, st = run(ctx, ds, np.ascontiguousarray(y[sample]), mode=P.DD_SEARCH_ANN, f_d=1.0,
+                      prev_idx=torch.from_numpy(prev).cuda())
+    assert np.array_equal(idx, oi)
+    assert np.allclose(d2, 2 * od, rtol=1e-9)

@@ -75,3 +75,11 @@ def test_load_cases():
     L = I.random_load(0, 3, 1e-4, 2e-3)
     mag = np.linalg.norm(L.t0)
     assert 1e-4 <= mag <= 2e-3
+
+
+def test_c_generator_bit_identical():
+    from dd_inputs import cgen
+    for law, start in ((I.LINEAR, 0), (I.NONLINEAR, 987654)):
+        a = I.make_dataset(4000, law, seed=3, start=start)
+        b = cgen.make_dataset(4000, law, seed=3, start=start)
+        assert np.array_equal(a.view(np.uint32), b.view(np.uint32))

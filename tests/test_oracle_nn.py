@@ -52,3 +52,15 @@ def test_min_and_second_min_property():
     s = np.sort(full, axis=1)
     assert np.allclose(d1, s[:, 0], rtol=1e-13) and np.allclose(d2, s[:, 1], rtol=1e-13)
     assert np.array_equal(i1, full.argmin(1))
+
+
+def test_streaming_scan_equals_in_memory_scan():
+    """The chunked scan over generated data equals the in-memory scan."""
+    law = I.NONLINEAR
+    C = I.isotropic_C()
+    N = (1 << 20) + 4321                    # more than one chunk, ragged tail
+    data = I.make_dataset(N, law, seed=6)
+    zq = M.to_z(I.make_states(24, law, seed=7, spread=0.1), C)
+    i1, d1, _, _ = nn.nn_top2(M.to_z(data, C), zq)
+    j1, e1 = nn.nn_stream(law, 6, N, C, zq)
+    assert np.array_equal(i1, j1) and np.allclose(d1, e1, rtol=1e-12)
