@@ -179,6 +179,8 @@ typedef struct dd_search_stats {
     double ms;                /* device time of the call (CUDA events) */
     double scan_ms;           /* device time of the dominant scan kernel alone
                                  (CUDA events on the launching stream) */
+    int64_t points;           /* data points read by the approximate search
+                                 (the rest of `distances` are centroids) */
 } dd_search_stats;
 
 /* Nearest data point of each state y_i (Eq. 7):
@@ -310,6 +312,7 @@ typedef struct dd_iter_info {
     int done;                 /* 1: the stop rule fired or max_iter reached */
     int64_t skipped;          /* ANN: queries kept by the moving-query radius
                                  (Eq. 14) without a search */
+    int64_t points;           /* ANN: data points read by the search */
 } dd_iter_info;
 
 /* Set up a DD problem (mesh, load, options as for dd_solve) on the data set:

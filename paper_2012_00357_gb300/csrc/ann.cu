@@ -561,7 +561,7 @@ __global__ void __launch_bounds__(256) k_ann_probe2(Probe2Args P) {
             const int f = lane + 32 * t;
             fd[t] = (f < P.L2) ? sqrtf(dist2_12(P.centf + ((size_t)C * P.L2 + f) * 12, q)) : INFINITY;
         }
-        scanned += (unsigned long long)P.L2;
+        if (lane == 0) atomicAdd(A.counters + 3, (unsigned long long)P.L2);
         for (int k2 = 0; k2 < kFine; ++k2) {
             float md = INFINITY;
             int mt = -1;
@@ -1060,13 +1060,14 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
     }
     if (mot && out.d2 && out.d2nd) DD_TRY(dd_ann_motion_update(ctx, rec, m, out.d2, out.d2nd, mot, s));
     if (st) {
-        unsigned long long h[3];
+        unsigned long long h[4];
         DD_TRY_CUDA(ctx, cudaMemcpyAsync(h, counters, sizeof(h), cudaMemcpyDeviceToHost, s));
         DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
         float ms = 0.f;
         DD_TRY_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev_scan[0], ctx->ev_scan[1]));
         st->scan_ms += ms;
-        st->distances += (int64_t)h[0] + m * (int64_t)(two ? a.L1 : a.nlist) + (int64_t)n_fb * ds->N;
+        st->distances += (int64_t)h[0] + (int64_t)h[3] + m * (int64_t)(two ? a.L1 : a.nlist) + (int64_t)n_fb * ds->N;
+        st->points += (int64_t)h[0] + (int64_t)n_fb * ds->N;
         st->skipped += (int64_t)h[1];
         st->uncertified += (int64_t)n_fb;
     }

@@ -25,15 +25,26 @@
 
 namespace {
 
+// The product K v runs on node tiles of tx x ty x tz free nodes (k >= 1: the
+// clamped face carries no unknowns, and every vector is zero there): the
+// block stages the tile and a one-node halo of v in shared memory, and every
+// thread applies the 27-point stencil of its node (fem_stencil_table) from
+// there, with the 3x3 blocks of its boundary class.
 constexpr int kBThreads = 256;
-constexpr int kGroups = kBThreads / 8;     // nodes per block and pass
+constexpr int kTileMax = 16;                 // tile edge bound (nodes)
+constexpr int kHaloMax = 1024;               // (tx + 2)(ty + 2)(tz + 2) bound
+constexpr int kSt32 = 27 * 27 * 12;          // FP32 stencil table (floats)
+constexpr size_t kDynSmem = kSt32 * 4 + (size_t)kHaloMax * 6 * 8;
 
 struct SegCG {
     MeshDev g;
-    const double *Ke, *Minv, *b;
+    const double *St64, *Minv, *b;
+    const float *St32;
     double *x;
-    float *r, *z, *p0, *p1, *q, *d;
+    float *r, *z, *p0, *p1, *q, *d, *Mf;
     int blk0, nblk;
+    int tx, ty, tz;                          // tile shape (nodes)
+    int ntx, nty, ntiles;
 };
 
 struct BCGArgs {
@@ -41,7 +52,7 @@ struct BCGArgs {
     const int *blk_seg;        // [grid] solve of every block
     int S;
     double *part;              // [2 x grid x 8]
-    int *flags;                // [2 x S]: outer activity, inner activity (written by segment leaders)
+    int *flags;                // [S]: outer activity (written by segment leaders)
     unsigned *bar, *err;
     double rtol2, in_rtol2;
     int max_outer, max_inner;
@@ -68,6 +79,32 @@ __device__ void range_total(const double *part, int b0, int nb, double (&tot)[NV
     __syncthreads();
 }
 
+// Slots [0, NV) summed over the blocks [b0, b0 + nb) of this solve, and slot 7
+// (activity) over all G blocks, in one fixed-order pass.  Returns the latter.
+template <int NV>
+__device__ double seg_totals(const double *part, int G, int b0, int nb, double (&tot)[NV], double *sh) {
+    double v[NV + 1];
+#pragma unroll
+    for (int c = 0; c <= NV; ++c) v[c] = 0.0;
+    for (int t = threadIdx.x; t < G; t += blockDim.x) {
+        if (t >= b0 && t < b0 + nb)
+#pragma unroll
+            for (int c = 0; c < NV; ++c) v[c] += __ldcg(part + (size_t)t * 8 + c);
+        v[NV] += __ldcg(part + (size_t)t * 8 + 7);
+    }
+    block_sum<NV + 1>(v, sh);
+    __shared__ double s_tot[8];
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int c = 0; c <= NV; ++c) s_tot[c] = v[c];
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < NV; ++c) tot[c] = s_tot[c];
+    const double all = s_tot[NV];
+    __syncthreads();
+    return all;
+}
+
 __device__ int count_flags(const int *flags, int S, double *sh) {
     double v[1] = {0.0};
     for (int t = threadIdx.x; t < S; t += blockDim.x) v[0] += (double)__ldcg(flags + t);
@@ -80,63 +117,223 @@ __device__ int count_flags(const int *flags, int S, double *sh) {
     return r;
 }
 
-__global__ void __launch_bounds__(kBThreads) k_cg_batch(BCGArgs A) {
-    __shared__ double sKe[576];
-    __shared__ float sKf[576];
+// This thread's node in tile `tile` of a solve.
+struct TileNode {
+    int X0, Y0, Z0;   // tile origin
+    int64_t a;        // node id
+    int cls;          // stencil class
+    bool ok;
+};
+
+__device__ __forceinline__ TileNode tile_node(const SegCG &S, int64_t tile, int lx, int ly, int lz, bool lane_ok) {
+    TileNode n;
+    n.X0 = (int)(tile % S.ntx) * S.tx;
+    n.Y0 = (int)((tile / S.ntx) % S.nty) * S.ty;
+    n.Z0 = 1 + (int)(tile / ((int64_t)S.ntx * S.nty)) * S.tz;
+    const int X = n.X0 + lx, Y = n.Y0 + ly, Z = n.Z0 + lz;
+    n.ok = lane_ok && X <= S.g.nx && Y <= S.g.ny && Z <= S.g.nz;
+    n.a = n.ok ? node_id(S.g, X, Y, Z) : 0;
+    const int cx = X == 0 ? 0 : (X == S.g.nx ? 2 : 1);
+    const int cy = Y == 0 ? 0 : (Y == S.g.ny ? 2 : 1);
+    const int cz = Z == S.g.nz ? 2 : 1;
+    n.cls = cx + 3 * cy + 9 * cz;
+    return n;
+}
+
+// sv[h] = vz + beta .* vp (vp may be null) at every node h of the tile's
+// halo; nodes outside the box or on the clamped face hold 0.
+__device__ __forceinline__ void stage_f(const SegCG &S, const TileNode &n, const float *vz, const float *vp,
+                                        const float beta[2], float *sv) {
+    const int hx = S.tx + 2, hy = S.ty + 2, nh = hx * hy * (S.tz + 2);
+    for (int h = threadIdx.x; h < nh; h += blockDim.x) {
+        const int X = n.X0 - 1 + h % hx, Y = n.Y0 - 1 + (h / hx) % hy, Z = n.Z0 - 1 + h / (hx * hy);
+        float2 v0 = make_float2(0.f, 0.f), v1 = v0, v2 = v0;
+        if (X >= 0 && Y >= 0 && Z >= 1 && X <= S.g.nx && Y <= S.g.ny && Z <= S.g.nz) {
+            const float2 *pz = reinterpret_cast<const float2 *>(vz + node_id(S.g, X, Y, Z) * 6);
+            v0 = __ldcg(pz);
+            v1 = __ldcg(pz + 1);
+            v2 = __ldcg(pz + 2);
+            if (vp) {
+                const float2 *pp = reinterpret_cast<const float2 *>(vp + node_id(S.g, X, Y, Z) * 6);
+                const float2 w0 = __ldcg(pp), w1 = __ldcg(pp + 1), w2 = __ldcg(pp + 2);
+                v0.x = fmaf(beta[0], w0.x, v0.x);
+                v0.y = fmaf(beta[0], w0.y, v0.y);
+                v1.x = fmaf(beta[0], w1.x, v1.x);
+                v1.y = fmaf(beta[1], w1.y, v1.y);
+                v2.x = fmaf(beta[1], w2.x, v2.x);
+                v2.y = fmaf(beta[1], w2.y, v2.y);
+            }
+        }
+        float2 *o = reinterpret_cast<float2 *>(sv + h * 6);
+        o[0] = v0;
+        o[1] = v1;
+        o[2] = v2;
+    }
+}
+
+__device__ __forceinline__ void stage_d(const SegCG &S, const TileNode &n, const double *vz, double *sv) {
+    const int hx = S.tx + 2, hy = S.ty + 2, nh = hx * hy * (S.tz + 2);
+    for (int h = threadIdx.x; h < nh; h += blockDim.x) {
+        const int X = n.X0 - 1 + h % hx, Y = n.Y0 - 1 + (h / hx) % hy, Z = n.Z0 - 1 + h / (hx * hy);
+        double2 v0 = make_double2(0.0, 0.0), v1 = v0, v2 = v0;
+        if (X >= 0 && Y >= 0 && Z >= 1 && X <= S.g.nx && Y <= S.g.ny && Z <= S.g.nz) {
+            const double2 *pz = reinterpret_cast<const double2 *>(vz + node_id(S.g, X, Y, Z) * 6);
+            v0 = __ldcg(pz);
+            v1 = __ldcg(pz + 1);
+            v2 = __ldcg(pz + 2);
+        }
+        double2 *o = reinterpret_cast<double2 *>(sv + h * 6);
+        o[0] = v0;
+        o[1] = v1;
+        o[2] = v2;
+    }
+}
+
+// (K v) of the node at halo index hc, FP32: table blocks [r0 | r1 | r2 | pad]
+// of 12 floats in shared memory.
+__device__ __forceinline__ void stencil_f(const float *sS, const float *sv, int hc, int hx, int hxy, int cls,
+                                          float y[6]) {
+    const float *Sc = sS + cls * (27 * 12);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) y[k] = 0.f;
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int d = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
+                const float2 *xv = reinterpret_cast<const float2 *>(sv + (hc + dx + dy * hx + dz * hxy) * 6);
+                const float2 x01 = xv[0], x23 = xv[1], x45 = xv[2];
+                const float4 *kb = reinterpret_cast<const float4 *>(Sc + d * 12);
+                const float4 k0 = kb[0], k1 = kb[1], k2 = kb[2];
+                // rows (k0.x k0.y k0.z), (k0.w k1.x k1.y), (k1.z k1.w k2.x)
+                y[0] = fmaf(k0.x, x01.x, fmaf(k0.y, x01.y, fmaf(k0.z, x23.x, y[0])));
+                y[1] = fmaf(k0.w, x01.x, fmaf(k1.x, x01.y, fmaf(k1.y, x23.x, y[1])));
+                y[2] = fmaf(k1.z, x01.x, fmaf(k1.w, x01.y, fmaf(k2.x, x23.x, y[2])));
+                y[3] = fmaf(k0.x, x23.y, fmaf(k0.y, x45.x, fmaf(k0.z, x45.y, y[3])));
+                y[4] = fmaf(k0.w, x23.y, fmaf(k1.x, x45.x, fmaf(k1.y, x45.y, y[4])));
+                y[5] = fmaf(k1.z, x23.y, fmaf(k1.w, x45.x, fmaf(k2.x, x45.y, y[5])));
+            }
+}
+
+// The same in FP64 with the table read through the read-only cache.
+__device__ __forceinline__ void stencil_d(const double *St, const double *sv, int hc, int hx, int hxy, int cls,
+                                          double y[6]) {
+    const double *Sc = St + cls * (27 * 9);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) y[k] = 0.0;
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int d = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
+                const double *xv = sv + (hc + dx + dy * hx + dz * hxy) * 6;
+                double k9[9];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) k9[k] = __ldg(Sc + d * 9 + k);
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    y[r] = fma(k9[3 * r], xv[0], fma(k9[3 * r + 1], xv[1], fma(k9[3 * r + 2], xv[2], y[r])));
+                    y[3 + r] = fma(k9[3 * r], xv[3], fma(k9[3 * r + 1], xv[4], fma(k9[3 * r + 2], xv[5], y[3 + r])));
+                }
+            }
+}
+
+// z = M^-1 r with the symmetric 3x3 block packed as (m00 m11 m22 m12 m02 m01).
+__device__ __forceinline__ void precond_f(const float *Mf, const float r[6], float z[6]) {
+    const float2 *m = reinterpret_cast<const float2 *>(Mf);
+    const float2 a = __ldcg(m), b = __ldcg(m + 1), c = __ldcg(m + 2);
+    const float m00 = a.x, m11 = a.y, m22 = b.x, m12 = b.y, m02 = c.x, m01 = c.y;
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const float r0 = r[3 * s], r1 = r[3 * s + 1], r2 = r[3 * s + 2];
+        z[3 * s + 0] = fmaf(m00, r0, fmaf(m01, r1, m02 * r2));
+        z[3 * s + 1] = fmaf(m01, r0, fmaf(m11, r1, m12 * r2));
+        z[3 * s + 2] = fmaf(m02, r0, fmaf(m12, r1, m22 * r2));
+    }
+}
+
+__device__ __forceinline__ void ld6(const float *p, float v[6]) {
+    const float2 *q = reinterpret_cast<const float2 *>(p);
+    const float2 a = __ldcg(q), b = __ldcg(q + 1), c = __ldcg(q + 2);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = c.x; v[5] = c.y;
+}
+
+__device__ __forceinline__ void st6(float *p, const float v[6]) {
+    float2 *q = reinterpret_cast<float2 *>(p);
+    q[0] = make_float2(v[0], v[1]);
+    q[1] = make_float2(v[2], v[3]);
+    q[2] = make_float2(v[4], v[5]);
+}
+
+__device__ __forceinline__ float dot3(const float *a, const float *b) {
+    return fmaf(a[0], b[0], fmaf(a[1], b[1], a[2] * b[2]));
+}
+
+__global__ void __launch_bounds__(kBThreads, 1) k_cg_batch(BCGArgs A) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    float *sS = reinterpret_cast<float *>(dsm);                 // [kSt32]
+    double *sv64 = reinterpret_cast<double *>(dsm + kSt32 * 4);  // [kHaloMax x 6]; the FP32 halo reuses it
+    float *sv32 = reinterpret_cast<float *>(sv64);
     __shared__ double sh[8 * 32];
     const int sidx = A.blk_seg[blockIdx.x];
     const SegCG S = A.seg[sidx];
-    const MeshDev &g = S.g;
-    for (int t = threadIdx.x; t < 576; t += blockDim.x) {
-        sKe[t] = S.Ke[t];
-        sKf[t] = (float)S.Ke[t];
-    }
+    for (int t = threadIdx.x; t < kSt32 / 4; t += blockDim.x)
+        reinterpret_cast<float4 *>(sS)[t] = __ldg(reinterpret_cast<const float4 *>(S.St32) + t);
     __syncthreads();
-    // node groups: 8 consecutive lanes per node, lane slot e = element slot
-    // for the product and component c = e (< 6) for the per-node updates
-    const int e = threadIdx.x & 7;
-    const int lane = threadIdx.x & 31;
-    const unsigned gmask = 0xffu << (lane & 24);
-    const int gbase = lane & 24;
-    const bool comp = e < 6;
-    const int c = comp ? e : 0, sy = c / 3;
     const unsigned G = gridDim.x;
     GridBar gbar{A.bar, G, 0u};
     const int lb = blockIdx.x - S.blk0;
     const bool leader = (lb == 0 && threadIdx.x == 0);
-    const int64_t gstride = (int64_t)S.nblk * kGroups;
-    const int64_t a0 = (int64_t)lb * kGroups + (threadIdx.x >> 3);
+    const bool lane_ok = threadIdx.x < S.tx * S.ty * S.tz;
+    const int lx = threadIdx.x % S.tx, ly = (threadIdx.x / S.tx) % S.ty, lz = threadIdx.x / (S.tx * S.ty);
+    const int hx = S.tx + 2, hxy = hx * (S.ty + 2);
+    const int hc = (lx + 1) + hx * (ly + 1) + hxy * (lz + 1);
+    const double ndof = 3.0 * (S.g.nx + 1) * (double)(S.g.ny + 1) * (double)S.g.nz;
     double *partA = A.part, *partB = A.part + (size_t)G * 8;
-    int *outer_flag = A.flags, *inner_flag = A.flags + A.S;
-    const double zb64[2] = {0.0, 0.0};
-    double rr_true[2] = {0.0, 0.0}, bb[2] = {0.0, 0.0};
+    int *outer_flag = A.flags;
     int inner_count = 0;
-    // z_c = M^-1 r for component c of the node: the system's 3 residuals come
-    // from the group's lanes 3 sy .. 3 sy + 2
-    auto precond = [&](int64_t a, float rc) -> float {
-        float r0 = __shfl_sync(gmask, rc, gbase + 3 * sy + 0);
-        float r1 = __shfl_sync(gmask, rc, gbase + 3 * sy + 1);
-        float r2 = __shfl_sync(gmask, rc, gbase + 3 * sy + 2);
-        const double *Mi = S.Minv + a * 9 + 3 * (c % 3);
-        return (float)Mi[0] * r0 + (float)Mi[1] * r1 + (float)Mi[2] * r2;
-    };
     for (int outer = 0;; ++outer) {
-        double v[6] = {0, 0, 0, 0, 0, 0};
-        for (int64_t a = a0; a < g.n_nodes; a += gstride) {
-            double kx[6];
-            spmv_group<double>(g, sKe, a, e, gmask, S.x, nullptr, zb64, kx);
-            const double bc = comp ? S.b[a * 6 + c] : 0.0;
-            const double r64 = comp ? bc - pick6(kx, c) : 0.0;
-            const float rf = (float)r64;
-            const float zf = precond(a, rf);
-            if (comp) {
-                S.r[a * 6 + c] = rf;
-                S.z[a * 6 + c] = zf;
-                S.p0[a * 6 + c] = zf;
-                S.d[a * 6 + c] = 0.f;
-                (sy ? v[1] : v[0]) += (double)rf * (double)zf;
-                (sy ? v[3] : v[2]) += r64 * r64;
-                (sy ? v[5] : v[4]) += bc * bc;
+        // ---- FP64 residual r = b - K x, preconditioned, and the norms ----
+        double v[6] = {0, 0, 0, 0, 0, 0};   // r.z (2), r.r (2), b.b (2)
+        for (int64_t tile = lb; tile < S.ntiles; tile += S.nblk) {
+            const TileNode n = tile_node(S, tile, lx, ly, lz, lane_ok);
+            __syncthreads();
+            stage_d(S, n, S.x, sv64);
+            __syncthreads();
+            if (n.ok) {
+                const int64_t a = n.a;
+                double kx[6];
+                stencil_d(S.St64, sv64, hc, hx, hxy, n.cls, kx);
+                const double *Mi = S.Minv + a * 9;
+                float mf[6] = {(float)Mi[0], (float)Mi[4], (float)Mi[8], (float)Mi[5], (float)Mi[2], (float)Mi[1]};
+                st6(S.Mf + a * 6, mf);
+                float rf[6], zf[6];
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    const double bc = S.b[a * 6 + k];
+                    const double r64 = bc - kx[k];
+                    rf[k] = (float)r64;
+                    v[2 + k / 3] += r64 * r64;
+                    v[4 + k / 3] += bc * bc;
+                }
+                const float *m = mf;
+#pragma unroll
+                for (int s2 = 0; s2 < 2; ++s2) {
+                    const float r0 = rf[3 * s2], r1 = rf[3 * s2 + 1], r2 = rf[3 * s2 + 2];
+                    zf[3 * s2 + 0] = fmaf(m[0], r0, fmaf(m[5], r1, m[4] * r2));
+                    zf[3 * s2 + 1] = fmaf(m[5], r0, fmaf(m[1], r1, m[3] * r2));
+                    zf[3 * s2 + 2] = fmaf(m[4], r0, fmaf(m[3], r1, m[2] * r2));
+                }
+                st6(S.r + a * 6, rf);
+                st6(S.z + a * 6, zf);
+                const float zero6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                st6(S.d + a * 6, zero6);
+#pragma unroll
+                for (int k = 0; k < 6; ++k) v[k / 3] += (double)rf[k] * (double)zf[k];
             }
         }
         block_sum<6>(v, sh);
@@ -145,45 +342,76 @@ __global__ void __launch_bounds__(kBThreads) k_cg_batch(BCGArgs A) {
         if (!grid_sync(gbar, A.err)) return;
         double tot[6];
         range_total<6>(partB, S.blk0, S.nblk, tot, sh);
-        double rz[2] = {tot[0], tot[1]};
+        double rr_true[2], bb[2], rz[2], scale[2], unscale[2];
         bool conv[2];
         for (int s2 = 0; s2 < 2; ++s2) {
             rr_true[s2] = tot[2 + s2];
             bb[s2] = tot[4 + s2];
             conv[s2] = !(rr_true[s2] > A.rtol2 * bb[s2]) || bb[s2] == 0.0;
+            // the inner FP32 iterations run on r scaled by a power of two to an
+            // RMS near 1 (exact), so that their products stay far from underflow
+            int e = 0;
+            if (rr_true[s2] > 0.0) frexp(sqrt(rr_true[s2] / ndof), &e);
+            scale[s2] = ldexp(1.0, -e);
+            unscale[s2] = ldexp(1.0, e);
+            rz[s2] = tot[s2] * scale[s2] * scale[s2];
         }
         const bool more = !(conv[0] && conv[1]) && outer < A.max_outer;
-        if (leader) {
-            outer_flag[sidx] = more ? 1 : 0;
-            inner_flag[sidx] = more ? 1 : 0;
-        }
+        if (more)
+            for (int64_t tile = lb; tile < S.ntiles; tile += S.nblk) {
+                const TileNode n = tile_node(S, tile, lx, ly, lz, lane_ok);
+                if (!n.ok) continue;
+                float rv[6], zv[6];
+                ld6(S.r + n.a * 6, rv);
+                ld6(S.z + n.a * 6, zv);
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    rv[k] *= (float)scale[k / 3];
+                    zv[k] *= (float)scale[k / 3];
+                }
+                st6(S.r + n.a * 6, rv);
+                st6(S.z + n.a * 6, zv);
+            }
+        if (leader) outer_flag[sidx] = more ? 1 : 0;
         if (!grid_sync(gbar, A.err)) return;
         if (count_flags(outer_flag, A.S, sh) == 0) {
             for (int s2 = 0; s2 < 2; ++s2)
-                if (bb[s2] == 0.0 && comp && sy == s2)
-                    for (int64_t a = a0; a < g.n_nodes; a += gstride) S.x[a * 6 + c] = 0.0;
+                if (bb[s2] == 0.0)
+                    for (int64_t tile = lb; tile < S.ntiles; tile += S.nblk) {
+                        const TileNode n = tile_node(S, tile, lx, ly, lz, lane_ok);
+                        if (n.ok)
+                            for (int k = 0; k < 3; ++k) S.x[n.a * 6 + 3 * s2 + k] = 0.0;
+                    }
             break;
         }
         // gain four digits per refinement step, but never solve below a tenth
-        // of the final tolerance
-        const double target[2] = {fmax(A.in_rtol2 * rr_true[0], 0.01 * A.rtol2 * bb[0]),
-                                  fmax(A.in_rtol2 * rr_true[1], 0.01 * A.rtol2 * bb[1])};
+        // of the final tolerance (in the scaled units of the inner iterations)
+        double target[2];
+        for (int s2 = 0; s2 < 2; ++s2)
+            target[s2] = fmax(A.in_rtol2 * rr_true[s2], 0.01 * A.rtol2 * bb[s2]) * scale[s2] * scale[s2];
         bool ic[2] = {conv[0] || !more, conv[1] || !more};
         float beta[2] = {0.f, 0.f};
         float *pold = S.p0, *pnew = S.p1;
         for (int it = 0; it < A.max_inner; ++it) {
             const bool act = !(ic[0] && ic[1]);
+            // ---- p = z + beta p_old, q = K p, p.q ----
             double w[2] = {0, 0};
             if (act) {
-                for (int64_t a = a0; a < g.n_nodes; a += gstride) {
-                    float kq[6];
-                    spmv_group<float>(g, sKf, a, e, gmask, S.z, pold, beta, kq);
-                    if (comp) {
-                        const float pn = S.z[a * 6 + c] + (sy ? beta[1] : beta[0]) * pold[a * 6 + c];
-                        const float qc = pick6(kq, c);
-                        pnew[a * 6 + c] = pn;
-                        S.q[a * 6 + c] = qc;
-                        (sy ? w[1] : w[0]) += (double)pn * (double)qc;
+                for (int64_t tile = lb; tile < S.ntiles; tile += S.nblk) {
+                    const TileNode n = tile_node(S, tile, lx, ly, lz, lane_ok);
+                    __syncthreads();
+                    stage_f(S, n, S.z, it ? pold : nullptr, beta, sv32);
+                    __syncthreads();
+                    if (n.ok) {
+                        float kq[6], pn[6];
+                        stencil_f(sS, sv32, hc, hx, hxy, n.cls, kq);
+                        const float2 *own = reinterpret_cast<const float2 *>(sv32 + hc * 6);
+                        const float2 p01 = own[0], p23 = own[1], p45 = own[2];
+                        pn[0] = p01.x; pn[1] = p01.y; pn[2] = p23.x; pn[3] = p23.y; pn[4] = p45.x; pn[5] = p45.y;
+                        st6(pnew + n.a * 6, pn);
+                        st6(S.q + n.a * 6, kq);
+                        w[0] += (double)dot3(pn, kq);
+                        w[1] += (double)dot3(pn + 3, kq + 3);
                     }
                 }
             }
@@ -191,29 +419,39 @@ __global__ void __launch_bounds__(kBThreads) k_cg_batch(BCGArgs A) {
             if (threadIdx.x == 0) {
                 partA[blockIdx.x * 8 + 0] = w[0];
                 partA[blockIdx.x * 8 + 1] = w[1];
+                partA[blockIdx.x * 8 + 7] = act ? 1.0 : 0.0;
             }
             if (!grid_sync(gbar, A.err)) return;
-            // lagged stop: the leaders published their activity before this barrier
-            if (count_flags(inner_flag, A.S, sh) == 0) break;
             double pq[2];
-            range_total<2>(partA, S.blk0, S.nblk, pq, sh);
+            // lagged stop: every block published its solve's activity before the barrier
+            if (seg_totals<2>(partA, (int)G, S.blk0, S.nblk, pq, sh) == 0.0) break;
             float alpha[2];
             for (int s2 = 0; s2 < 2; ++s2) alpha[s2] = (ic[s2] || !(pq[s2] > 0.0)) ? 0.f : (float)(rz[s2] / pq[s2]);
+            // ---- d += alpha p, r -= alpha q, z = M^-1 r, r.z, r.r ----
             double u[4] = {0, 0, 0, 0};
             if (act) {
-                for (int64_t a = a0; a < g.n_nodes; a += gstride) {
-                    float rv = 0.f;
-                    if (comp) {
-                        S.d[a * 6 + c] += (sy ? alpha[1] : alpha[0]) * pnew[a * 6 + c];
-                        rv = S.r[a * 6 + c] - (sy ? alpha[1] : alpha[0]) * S.q[a * 6 + c];
-                        S.r[a * 6 + c] = rv;
+                for (int64_t tile = lb; tile < S.ntiles; tile += S.nblk) {
+                    const TileNode n = tile_node(S, tile, lx, ly, lz, lane_ok);
+                    if (!n.ok) continue;
+                    const int64_t a = n.a;
+                    float pv[6], dv[6], rv[6], qv[6], zv[6];
+                    ld6(pnew + a * 6, pv);
+                    ld6(S.d + a * 6, dv);
+                    ld6(S.r + a * 6, rv);
+                    ld6(S.q + a * 6, qv);
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) {
+                        dv[k] = fmaf(alpha[k / 3], pv[k], dv[k]);
+                        rv[k] = fmaf(-alpha[k / 3], qv[k], rv[k]);
                     }
-                    const float zv = precond(a, rv);
-                    if (comp) {
-                        S.z[a * 6 + c] = zv;
-                        (sy ? u[1] : u[0]) += (double)rv * (double)zv;
-                        (sy ? u[3] : u[2]) += (double)rv * (double)rv;
-                    }
+                    precond_f(S.Mf + a * 6, rv, zv);
+                    st6(S.d + a * 6, dv);
+                    st6(S.r + a * 6, rv);
+                    st6(S.z + a * 6, zv);
+                    u[0] += (double)dot3(rv, zv);
+                    u[1] += (double)dot3(rv + 3, zv + 3);
+                    u[2] += (double)dot3(rv, rv);
+                    u[3] += (double)dot3(rv + 3, rv + 3);
                 }
             }
             block_sum<4>(u, sh);
@@ -232,13 +470,17 @@ __global__ void __launch_bounds__(kBThreads) k_cg_batch(BCGArgs A) {
                 }
             }
             if (act) ++inner_count;
-            if (leader) inner_flag[sidx] = (ic[0] && ic[1]) ? 0 : 1;
             float *t = pold;
             pold = pnew;
             pnew = t;
         }
-        if (comp)
-            for (int64_t a = a0; a < g.n_nodes; a += gstride) S.x[a * 6 + c] += (double)S.d[a * 6 + c];
+        // ---- x += d (back in the units of x) ----
+        for (int64_t tile = lb; tile < S.ntiles; tile += S.nblk) {
+            const TileNode n = tile_node(S, tile, lx, ly, lz, lane_ok);
+            if (!n.ok) continue;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) S.x[n.a * 6 + k] += (double)S.d[n.a * 6 + k] * unscale[k / 3];
+        }
         if (!grid_sync(gbar, A.err)) return;
     }
     if (leader) A.it_out[sidx] = inner_count;
@@ -251,23 +493,55 @@ __global__ void k_fill_f(float *p, int64_t n, float v) {
 
 }  // namespace
 
+// Tile shape for a solve that gets nblk blocks: fewest estimated cycles for
+// the passes over its tiles (a halo round per 256 staged nodes, the stencil
+// per warp, the per-node update).
+static void pick_tiles(const MeshDev &g, int nblk, SegCG &S) {
+    const int n1[3] = {g.nx + 1, g.ny + 1, g.nz};
+    double best = 1e300;
+    for (int tx = 1; tx <= std::min(n1[0], kTileMax); ++tx)
+        for (int ty = 1; ty <= std::min(n1[1], kTileMax); ++ty)
+            for (int tz = 1; tz <= std::min(n1[2], kTileMax); ++tz) {
+                const int T = tx * ty * tz;
+                if (T > kBThreads) break;
+                const int halo = (tx + 2) * (ty + 2) * (tz + 2);
+                if (halo > kHaloMax) continue;
+                const int64_t nt = (int64_t)((n1[0] + tx - 1) / tx) * ((n1[1] + ty - 1) / ty) * ((n1[2] + tz - 1) / tz);
+                const int64_t passes = (nt + nblk - 1) / nblk;
+                const double cost = (double)passes * (700.0 * ((halo + kBThreads - 1) / kBThreads) +
+                                                      200.0 * ((T + 31) / 32) + 700.0);
+                if (cost < best) {
+                    best = cost;
+                    S.tx = tx;
+                    S.ty = ty;
+                    S.tz = tz;
+                    S.ntx = (n1[0] + tx - 1) / tx;
+                    S.nty = (n1[1] + ty - 1) / ty;
+                    S.ntiles = (int)nt;
+                }
+            }
+}
+
 // Mixed-precision CG of n systems in one cooperative launch.  *it_dev points
 // at the per-system inner iteration counts (device) after the launch.
 dd_status dd_cg_segments(dd_ctx *ctx, const MeshDev *const *gs, const CGBuffers *const *cbs, int n, double rtol,
                          int max_it, cudaStream_t s, int **it_dev) {
     int64_t nodes = 0;
     for (int i = 0; i < n; ++i) nodes += gs[i]->n_nodes;
+    DD_TRY_CUDA(ctx, cudaFuncSetAttribute((const void *)k_cg_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)kDynSmem));
     int occ = 0;
-    DD_TRY_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg_batch, kBThreads, 0));
-    const int cap = std::max(1, std::min(occ, 1)) * ctx->n_sm;   // one block per SM: fewer barrier arrivals
+    DD_TRY_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg_batch, kBThreads, kDynSmem));
+    if (occ < 1) return dd_fail(ctx, DD_ERR_CUDA, "CG kernel cannot be resident");
+    const int cap = ctx->n_sm;   // one block per SM: fewer barrier arrivals
     if (n > cap) return dd_fail(ctx, DD_ERR_ARG, "more solves than resident CG blocks");
+    std::vector<SegCG> seg(n);
     std::vector<int> nblk(n);
     int total = 0;
     for (int i = 0; i < n; ++i) {
-        const int64_t nn = gs[i]->n_nodes;
-        int64_t want = (nn + kGroups - 1) / kGroups;
-        int64_t share = (int64_t)((double)cap * (double)nn / (double)nodes);
-        nblk[i] = (int)std::max<int64_t>(1, std::min(want, share));
+        const int64_t share = std::max<int64_t>(1, (int64_t)((double)cap * (double)gs[i]->n_nodes / (double)nodes));
+        pick_tiles(*gs[i], (int)share, seg[i]);
+        nblk[i] = (int)std::min<int64_t>(share, seg[i].ntiles);
         total += nblk[i];
     }
     while (total > cap) {   // trim the largest shares until the grid is co-resident
@@ -276,7 +550,6 @@ dd_status dd_cg_segments(dd_ctx *ctx, const MeshDev *const *gs, const CGBuffers 
         --nblk[k];
         --total;
     }
-    std::vector<SegCG> seg(n);
     std::vector<int> blk_seg(total);
     int b0 = 0;
     for (int i = 0; i < n; ++i) {
@@ -284,13 +557,16 @@ dd_status dd_cg_segments(dd_ctx *ctx, const MeshDev *const *gs, const CGBuffers 
         const size_t n6 = (size_t)gs[i]->n_nodes * 6;
         SegCG &S = seg[i];
         S.g = *gs[i];
-        S.Ke = cb.Ke;
+        S.St64 = cb.St64;
+        S.St32 = cb.St32;
         S.Minv = cb.Minv;
         S.b = cb.b;
         S.x = cb.x;
+        // the FP64 work arrays hold two FP32 vectors each
         S.r = reinterpret_cast<float *>(cb.r);
-        S.d = S.r + n6;                 // the FP64 work arrays hold two FP32 vectors each
+        S.d = S.r + n6;
         S.z = reinterpret_cast<float *>(cb.z);
+        S.Mf = S.z + n6;
         S.p0 = reinterpret_cast<float *>(cb.p0);
         S.p1 = reinterpret_cast<float *>(cb.p1);
         S.q = reinterpret_cast<float *>(cb.q);
@@ -301,7 +577,7 @@ dd_status dd_cg_segments(dd_ctx *ctx, const MeshDev *const *gs, const CGBuffers 
     }
     auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
     const size_t b_seg = r256(n * sizeof(SegCG)), b_bs = r256(total * sizeof(int)),
-                 b_part = r256((size_t)2 * total * 8 * 8), b_flags = r256((size_t)2 * n * sizeof(int)),
+                 b_part = r256((size_t)2 * total * 8 * 8), b_flags = r256((size_t)n * sizeof(int)),
                  b_it = r256(n * sizeof(int));
     void *w = nullptr;
     DD_TRY(dd_workspace(ctx, WS_BATCH_CG, b_seg + b_bs + b_part + b_flags + b_it + 256, &w));
@@ -330,7 +606,8 @@ dd_status dd_cg_segments(dd_ctx *ctx, const MeshDev *const *gs, const CGBuffers 
     A.it_out = *it_dev;
     void *args[] = {&A};
     ctx->launches++;
-    DD_TRY_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)k_cg_batch, dim3(total), dim3(kBThreads), args, 0, s));
+    DD_TRY_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)k_cg_batch, dim3(total), dim3(kBThreads), args,
+                                                 kDynSmem, s));
     return DD_OK;
 }
 

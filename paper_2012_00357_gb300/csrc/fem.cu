@@ -452,6 +452,40 @@ void fem_element_stiffness(const MeshDev &g, const ElemOps &ops, const double *C
     }
 }
 
+// The assembled K of the uniform box as a 27-point stencil of 3x3 blocks.
+// The block coupling node a with its neighbour a + d is the sum of the Ke
+// blocks [la, lb] over the elements that contain both nodes; which of those
+// elements exist depends only on whether a lies on the low face, inside, or on
+// the high face of the box along each axis.  Class c = cx + 3 cy + 9 cz with
+// cx = 0 (i = 0), 1 (0 < i < nx), 2 (i = nx); offset d = (dx + 1) + 3 (dy + 1)
+// + 9 (dz + 1).  Same operator as the element-by-element sum of Eq. 5, only
+// the summation order differs.
+void fem_stencil_table(const double *Ke, double *S) {
+    for (int c = 0; c < 27; ++c) {
+        const int cl[3] = {c % 3, (c / 3) % 3, c / 9};
+        for (int d = 0; d < 27; ++d) {
+            const int dd[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
+            double blk[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+            for (int e = 0; e < 8; ++e) {   // bit ax of e set: the element on the low side along ax
+                int la = 0, lb = 0;
+                bool ok = true;
+                for (int ax = 0; ax < 3 && ok; ++ax) {
+                    const bool low = (e >> ax) & 1;
+                    if (low ? cl[ax] == 0 : cl[ax] == 2) ok = false;   // no element there
+                    const int l_a = low ? 1 : 0, l_b = l_a + dd[ax];
+                    if (l_b < 0 || l_b > 1) ok = false;                // neighbour not in this element
+                    la |= l_a << ax;
+                    lb |= (l_b & 1) << ax;
+                }
+                if (!ok) continue;
+                for (int r = 0; r < 3; ++r)
+                    for (int k = 0; k < 3; ++k) blk[3 * r + k] += Ke[(3 * la + r) * 24 + 3 * lb + k];
+            }
+            for (int k = 0; k < 9; ++k) S[(c * 27 + d) * 9 + k] = blk[k];
+        }
+    }
+}
+
 void fem_traction_force(const MeshDev &g, const dd_load &L, double lx, double ly, double *f) {
     for (int64_t i = 0; i < g.n_nodes * 3; ++i) f[i] = 0.0;
     const double hx = g.hx, hy = g.hy, wq = hx * hy / 4.0;

@@ -18,6 +18,8 @@ struct ElemOps {
 
 struct CGBuffers {
     const double *Ke, *Minv, *b;
+    const double *St64;   // stencil table [27 classes][27 offsets][9] (fem_stencil_table)
+    const float *St32;    // the same in FP32, blocks padded to 12 values
     double *x, *r, *z, *p0, *p1, *q, *part;
     unsigned *bar;
     int *it_out;
@@ -41,6 +43,7 @@ inline MeshDev fem_mesh(const dd_mesh &m) {
 
 void fem_elem_ops(const MeshDev &g, ElemOps *ops);
 void fem_element_stiffness(const MeshDev &g, const ElemOps &ops, const double *C, double *Ke);
+void fem_stencil_table(const double *Ke, double *S);
 void fem_traction_force(const MeshDev &g, const dd_load &L, double lx, double ly, double *f);
 
 dd_status fem_gather_star(dd_dataset *ds, const int32_t *idx, int64_t n_gp, double *star, double *ce,

@@ -115,100 +115,4 @@ __device__ void grid_total(const double *part, int nblk, double (&tot)[NV], doub
     __syncthreads();
 }
 
-template <typename T>
-__device__ __forceinline__ void spmv_node_t(const MeshDev &g, const T *sKe, int64_t a, const T *vz, const T *vp,
-                                            const T beta[2], T y[6]) {
-    int i, j, k;
-    node_ijk(g, a, i, j, k);
-#pragma unroll
-    for (int c = 0; c < 6; ++c) y[c] = T(0);
-    if (k == 0) return;
-    for (int oz = -1; oz <= 0; ++oz)
-        for (int oy = -1; oy <= 0; ++oy)
-            for (int ox = -1; ox <= 0; ++ox) {
-                int ei = i + ox, ej = j + oy, ek = k + oz;
-                if (ei < 0 || ej < 0 || ek < 0 || ei >= g.nx || ej >= g.ny || ek >= g.nz) continue;
-                int la = (-ox) + 2 * (-oy) + 4 * (-oz);
-#pragma unroll
-                for (int lb = 0; lb < 8; ++lb) {
-                    int64_t nb = node_id(g, ei + (lb & 1), ej + ((lb >> 1) & 1), ek + ((lb >> 2) & 1));
-                    T xv[6];
-#pragma unroll
-                    for (int c = 0; c < 6; ++c) {
-                        T t = __ldcg(vz + nb * 6 + c);
-                        if (vp) t += beta[c / 3] * __ldcg(vp + nb * 6 + c);
-                        xv[c] = t;
-                    }
-                    const T *kb = sKe + (3 * la) * 24 + 3 * lb;
-#pragma unroll
-                    for (int r = 0; r < 3; ++r) {
-                        T k0 = kb[r * 24 + 0], k1 = kb[r * 24 + 1], k2 = kb[r * 24 + 2];
-                        y[r] += k0 * xv[0] + k1 * xv[1] + k2 * xv[2];
-                        y[3 + r] += k0 * xv[3] + k1 * xv[4] + k2 * xv[5];
-                    }
-                }
-            }
-}
-
-__device__ __forceinline__ void apply_minv_f(const double *Mi, const float *r, float *z) {
-    float m[9];
-#pragma unroll
-    for (int c = 0; c < 9; ++c) m[c] = (float)Mi[c];
-#pragma unroll
-    for (int s = 0; s < 2; ++s)
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-            z[3 * s + a] = m[3 * a] * r[3 * s] + m[3 * a + 1] * r[3 * s + 1] + m[3 * a + 2] * r[3 * s + 2];
-}
-
-
-// Element-parallel product: the 8 threads of a node group (8 consecutive
-// lanes) each take one of the (up to) 8 elements around node a (slot e is the
-// element in which a has local index e) and gather Ke[e, :] * v over its 8
-// nodes; a group-masked butterfly leaves the sum (K v)_a in all 8 lanes.
-// v = vz + beta .* vp (vp may be null).  Fixed nodes (k = 0) give 0.
-template <typename T>
-__device__ __forceinline__ void spmv_group(const MeshDev &g, const T *sKe, int64_t a, int e, unsigned gmask,
-                                           const T *vz, const T *vp, const T beta[2], T y[6]) {
-    int i, j, k;
-    node_ijk(g, a, i, j, k);
-#pragma unroll
-    for (int c = 0; c < 6; ++c) y[c] = T(0);
-    const int ei = i - (e & 1), ej = j - ((e >> 1) & 1), ek = k - ((e >> 2) & 1);
-    if (k > 0 && ei >= 0 && ej >= 0 && ek >= 0 && ei < g.nx && ej < g.ny && ek < g.nz) {
-#pragma unroll
-        for (int lb = 0; lb < 8; ++lb) {
-            int64_t nb = node_id(g, ei + (lb & 1), ej + ((lb >> 1) & 1), ek + ((lb >> 2) & 1));
-            T xv[6];
-#pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                T t = __ldcg(vz + nb * 6 + c);
-                if (vp) t += beta[c / 3] * __ldcg(vp + nb * 6 + c);
-                xv[c] = t;
-            }
-            const T *kb = sKe + (3 * e) * 24 + 3 * lb;
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                T k0 = kb[r * 24 + 0], k1 = kb[r * 24 + 1], k2 = kb[r * 24 + 2];
-                y[r] += k0 * xv[0] + k1 * xv[1] + k2 * xv[2];
-                y[3 + r] += k0 * xv[3] + k1 * xv[4] + k2 * xv[5];
-            }
-        }
-    }
-#pragma unroll
-    for (int o = 1; o < 8; o <<= 1)
-#pragma unroll
-        for (int c = 0; c < 6; ++c) y[c] += __shfl_xor_sync(gmask, y[c], o);
-}
-
-// y[c] for a run-time component c without dynamic register indexing.
-template <typename T>
-__device__ __forceinline__ T pick6(const T (&y)[6], int c) {
-    T r = y[0];
-#pragma unroll
-    for (int k = 1; k < 6; ++k)
-        if (c == k) r = y[k];
-    return r;
-}
-
 }  // namespace

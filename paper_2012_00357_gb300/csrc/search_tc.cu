@@ -270,14 +270,6 @@ __global__ void k_prep_tc(const double *__restrict__ y, int64_t m, int64_t m_pad
     }
 }
 
-// Rare path of the epilogue (some score of the chunk is inside the window):
-// kept out of line so the hot loop stays small in the instruction cache.
-__device__ __noinline__ void epi_insert_chunk(CandState &cs, const float *v, int64_t j0, int64_t N, float w2,
-                                              float2 *buf, int st, bool topk) {
-    for (int k = 0; k < 32; ++k)
-        if (v[k] <= cs.lim && j0 + k < N) cand_insert(cs, v[k], (int)(j0 + k), w2, buf, st, kCap, topk);
-}
-
 // ---- the contraction kernel ------------------------------------------------------
 template <int KC, int EPI>
 __global__ void __launch_bounds__(tc_threads<EPI>(), 2)
@@ -422,7 +414,12 @@ __global__ void __launch_bounds__(tc_threads<EPI>(), 2)
                     __syncwarp();
                     if (lane == 0) dd_mbar_arrive(dd_smem_addr(&bar_tempty[ab]));
                 }
-                if (min32(v) <= cs.lim) epi_insert_chunk(cs, v, jb + c * 32, N, w2, buf, kSt, topk);
+                if (min32(v) <= cs.lim) {
+                    const int64_t j0 = jb + c * 32;
+#pragma unroll
+                    for (int k = 0; k < 32; ++k)
+                        if (v[k] <= cs.lim && j0 + k < N) cand_insert(cs, v[k], (int)(j0 + k), w2, buf, kSt, kCap, topk);
+                }
             }
         }
         if (active) cand_store(cs, buf, kSt, kCap, ((size_t)qi * splits + split) * (EPI / 4) + half, hdr, cand);

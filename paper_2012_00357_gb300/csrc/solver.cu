@@ -66,6 +66,8 @@ size_t carve(dd_solver *sv, char *base) {
     sv->Minv = bp.take<double>(nn * 9);
     cb.Minv = sv->Minv;
     cb.Ke = sv->Ke;
+    cb.St64 = sv->St64 = bp.take<double>(27 * 27 * 9);
+    cb.St32 = sv->St32 = bp.take<float>(27 * 27 * 12);
     cb.part = bp.take<double>((size_t)2 * sv->ctx->n_sm * 32 * 8);
     cb.bar = bp.take<unsigned>(16);
     cb.it_out = bp.take<int>(16);
@@ -136,6 +138,7 @@ bool dd_solver_account(dd_solver *sv, const double hs[3], int cg_it, float cg_ms
         info->f_d = f_d;
         info->done = sv->done ? 1 : 0;
         info->skipped = sst.skipped;
+        info->points = sst.points;
     }
     return sv->done;
 }
@@ -197,9 +200,16 @@ extern "C" dd_status dd_solver_create(dd_dataset *ds, const dd_mesh *mesh, const
     const size_t nn = sv->g.n_nodes, ng = sv->g.n_gp;
     std::vector<double> Ke(576), f(nn * 3);
     fem_element_stiffness(sv->g, sv->ops, ds->M.C, Ke.data());
+    std::vector<double> St64(27 * 27 * 9);
+    std::vector<float> St32(27 * 27 * 12, 0.f);
+    fem_stencil_table(Ke.data(), St64.data());
+    for (int cd = 0; cd < 27 * 27; ++cd)
+        for (int k = 0; k < 9; ++k) St32[cd * 12 + k] = (float)St64[cd * 9 + k];
     fem_traction_force(sv->g, *load, mesh->lx, mesh->ly, f.data());
     cudaStream_t s = ctx->stream;
     if (cudaMemcpyAsync(sv->Ke, Ke.data(), 576 * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(sv->St64, St64.data(), St64.size() * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(sv->St32, St32.data(), St32.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(sv->f, f.data(), nn * 3 * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(sv->cb.x, 0, nn * 6 * 8, s) != cudaSuccess ||
         cudaMemsetAsync(sv->mot.d, 0, ng * 2 * sizeof(float), s) != cudaSuccess)

@@ -16,6 +16,8 @@ struct dd_solver {
     void *block = nullptr;
     size_t block_bytes = 0;
     double *Ke = nullptr, *f = nullptr, *Minv = nullptr, *star = nullptr, *ce = nullptr, *y = nullptr;
+    double *St64 = nullptr;
+    float *St32 = nullptr;
     double *dpc = nullptr, *d2 = nullptr, *d2nd = nullptr, *stats = nullptr;
     int32_t *cur = nullptr, *nxt = nullptr;
     AnnMotion mot{nullptr, nullptr};    // Eq. 14 record of the approximate search
