@@ -275,6 +275,9 @@ WORKLOADS = {
     "cube32_N1e9_ann_4loads": Workload(
         "cube32_N1e9_ann_4loads", 32, 1_000_000_000, NONLINEAR,
         loads=(("tension", 1e-3), ("shear", 1e-3), ("bending", 1e-3), ("torsion", 1e-3))),
+    # the 32^3 constraint projection with a small data set: a profiling case
+    # for the CG (the search is cheap here)
+    "cube32_N1e5_exact": Workload("cube32_N1e5_exact", 32, 100_000, NONLINEAR),
     "serve_N1e7": Workload("serve_N1e7", 0, 10_000_000, NONLINEAR,
                            extra={"requests": 512, "edge_min": 4, "edge_max": 24,
                                   "t_min": 1e-4, "t_max": 2e-3}),

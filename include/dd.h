@@ -313,6 +313,8 @@ typedef struct dd_iter_info {
     int64_t skipped;          /* ANN: queries kept by the moving-query radius
                                  (Eq. 14) without a search */
     int64_t points;           /* ANN: data points read by the search */
+    int graph;                /* 1: dd_solvers_step replayed (or captured) the
+                                 step as a CUDA graph; 0: launched eagerly */
 } dd_iter_info;
 
 /* Set up a DD problem (mesh, load, options as for dd_solve) on the data set:

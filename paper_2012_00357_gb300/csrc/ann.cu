@@ -1053,13 +1053,18 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
     DD_TRY_CUDA(ctx, cudaGetLastError());
     // exact re-search where the candidate list may be incomplete (f_d = 1)
     unsigned long long n_fb = 0;
-    if (f_d >= 1.0 || fd_q) {
+    // (a captured step never holds f_d = 1: its caller checks)
+    if ((f_d >= 1.0 || fd_q) && !ctx->defer) {
         DD_TRY_CUDA(ctx, cudaMemcpyAsync(&n_fb, counters + 2, sizeof(n_fb), cudaMemcpyDeviceToHost, s));
         DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
         if (n_fb) DD_TRY(ann_exact_subset(ds, y_dev, fb_list, (int64_t)n_fb, out, s));
     }
     if (mot && out.d2 && out.d2nd) DD_TRY(dd_ann_motion_update(ctx, rec, m, out.d2, out.d2nd, mot, s));
-    if (st) {
+    if (st && ctx->defer) {
+        DD_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->defer->ann, counters, 4 * sizeof(unsigned long long),
+                                         cudaMemcpyDeviceToDevice, s));
+        st->distances += m * (int64_t)(two ? a.L1 : a.nlist);
+    } else if (st) {
         unsigned long long h[4];
         DD_TRY_CUDA(ctx, cudaMemcpyAsync(h, counters, sizeof(h), cudaMemcpyDeviceToHost, s));
         DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));

@@ -491,6 +491,11 @@ __global__ void k_fill_f(float *p, int64_t n, float v) {
     if (i < n) p[i] = v;
 }
 
+__global__ void k_fill_fd(float *p, int64_t n, const float *v) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) p[i] = *v;
+}
+
 }  // namespace
 
 // Tile shape for a solve that gets nblk blocks: fewest estimated cycles for
@@ -522,10 +527,48 @@ static void pick_tiles(const MeshDev &g, int nblk, SegCG &S) {
             }
 }
 
-// Mixed-precision CG of n systems in one cooperative launch.  *it_dev points
-// at the per-system inner iteration counts (device) after the launch.
-dd_status dd_cg_segments(dd_ctx *ctx, const MeshDev *const *gs, const CGBuffers *const *cbs, int n, double rtol,
-                         int max_it, cudaStream_t s, int **it_dev) {
+static size_t r256(size_t b) { return (b + 255) / 256 * 256; }
+
+// Launch tables of one CG launch over n solves (built on the host).
+struct CGTables {
+    std::vector<SegCG> seg;
+    std::vector<int> blk_seg;
+    int n = 0, total = 0;
+};
+
+// Where those tables and the launch's scratch live on the device.
+struct CGDev {
+    SegCG *seg = nullptr;
+    int *blk_seg = nullptr;
+    double *part = nullptr;
+    int *flags = nullptr;
+    int *it = nullptr;           // [n] inner iterations of every solve (output)
+    unsigned *bar = nullptr;
+};
+
+static size_t cg_dev_bytes(const CGTables &T) {
+    return r256(T.n * sizeof(SegCG)) + r256(T.total * sizeof(int)) + r256((size_t)2 * T.total * 8 * 8) +
+           2 * r256((size_t)T.n * sizeof(int)) + 256;
+}
+
+static CGDev cg_carve(const CGTables &T, void *base) {
+    char *c = (char *)base;
+    CGDev D;
+    D.seg = (SegCG *)c;
+    c += r256(T.n * sizeof(SegCG));
+    D.blk_seg = (int *)c;
+    c += r256(T.total * sizeof(int));
+    D.part = (double *)c;
+    c += r256((size_t)2 * T.total * 8 * 8);
+    D.flags = (int *)c;
+    c += r256((size_t)T.n * sizeof(int));
+    D.it = (int *)c;
+    c += r256((size_t)T.n * sizeof(int));
+    D.bar = (unsigned *)c;
+    return D;
+}
+
+static dd_status cg_tables(dd_ctx *ctx, const MeshDev *const *gs, const CGBuffers *const *cbs, int n, CGTables &T) {
     int64_t nodes = 0;
     for (int i = 0; i < n; ++i) nodes += gs[i]->n_nodes;
     DD_TRY_CUDA(ctx, cudaFuncSetAttribute((const void *)k_cg_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -535,13 +578,14 @@ dd_status dd_cg_segments(dd_ctx *ctx, const MeshDev *const *gs, const CGBuffers 
     if (occ < 1) return dd_fail(ctx, DD_ERR_CUDA, "CG kernel cannot be resident");
     const int cap = ctx->n_sm;   // one block per SM: fewer barrier arrivals
     if (n > cap) return dd_fail(ctx, DD_ERR_ARG, "more solves than resident CG blocks");
-    std::vector<SegCG> seg(n);
+    T.n = n;
+    T.seg.assign(n, SegCG{});
     std::vector<int> nblk(n);
     int total = 0;
     for (int i = 0; i < n; ++i) {
         const int64_t share = std::max<int64_t>(1, (int64_t)((double)cap * (double)gs[i]->n_nodes / (double)nodes));
-        pick_tiles(*gs[i], (int)share, seg[i]);
-        nblk[i] = (int)std::min<int64_t>(share, seg[i].ntiles);
+        pick_tiles(*gs[i], (int)share, T.seg[i]);
+        nblk[i] = (int)std::min<int64_t>(share, T.seg[i].ntiles);
         total += nblk[i];
     }
     while (total > cap) {   // trim the largest shares until the grid is co-resident
@@ -550,12 +594,13 @@ dd_status dd_cg_segments(dd_ctx *ctx, const MeshDev *const *gs, const CGBuffers 
         --nblk[k];
         --total;
     }
-    std::vector<int> blk_seg(total);
+    T.total = total;
+    T.blk_seg.assign(total, 0);
     int b0 = 0;
     for (int i = 0; i < n; ++i) {
         const CGBuffers &cb = *cbs[i];
         const size_t n6 = (size_t)gs[i]->n_nodes * 6;
-        SegCG &S = seg[i];
+        SegCG &S = T.seg[i];
         S.g = *gs[i];
         S.St64 = cb.St64;
         S.St32 = cb.St32;
@@ -572,78 +617,127 @@ dd_status dd_cg_segments(dd_ctx *ctx, const MeshDev *const *gs, const CGBuffers 
         S.q = reinterpret_cast<float *>(cb.q);
         S.blk0 = b0;
         S.nblk = nblk[i];
-        for (int k = 0; k < nblk[i]; ++k) blk_seg[b0 + k] = i;
+        for (int k = 0; k < nblk[i]; ++k) T.blk_seg[b0 + k] = i;
         b0 += nblk[i];
     }
-    auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
-    const size_t b_seg = r256(n * sizeof(SegCG)), b_bs = r256(total * sizeof(int)),
-                 b_part = r256((size_t)2 * total * 8 * 8), b_flags = r256((size_t)n * sizeof(int)),
-                 b_it = r256(n * sizeof(int));
-    void *w = nullptr;
-    DD_TRY(dd_workspace(ctx, WS_BATCH_CG, b_seg + b_bs + b_part + b_flags + b_it + 256, &w));
-    char *c = (char *)w;
-    SegCG *d_seg = (SegCG *)c;
-    int *d_bs = (int *)(c + b_seg);
-    double *d_part = (double *)(c + b_seg + b_bs);
-    int *d_flags = (int *)(c + b_seg + b_bs + b_part);
-    *it_dev = (int *)(c + b_seg + b_bs + b_part + b_flags);
-    unsigned *d_bar = (unsigned *)(c + b_seg + b_bs + b_part + b_flags + b_it);
-    DD_TRY_CUDA(ctx, cudaMemcpyAsync(d_seg, seg.data(), n * sizeof(SegCG), cudaMemcpyHostToDevice, s));
-    DD_TRY_CUDA(ctx, cudaMemcpyAsync(d_bs, blk_seg.data(), total * sizeof(int), cudaMemcpyHostToDevice, s));
-    DD_TRY_CUDA(ctx, cudaMemsetAsync(d_bar, 0, 2 * sizeof(unsigned), s));
+    return DD_OK;
+}
+
+static dd_status cg_upload(dd_ctx *ctx, const CGTables &T, const CGDev &D, cudaStream_t s) {
+    DD_TRY_CUDA(ctx, cudaMemcpyAsync(D.seg, T.seg.data(), T.n * sizeof(SegCG), cudaMemcpyHostToDevice, s));
+    DD_TRY_CUDA(ctx, cudaMemcpyAsync(D.blk_seg, T.blk_seg.data(), T.total * sizeof(int), cudaMemcpyHostToDevice, s));
+    return DD_OK;
+}
+
+static dd_status cg_launch(dd_ctx *ctx, const CGTables &T, const CGDev &D, double rtol, int max_it, cudaStream_t s) {
+    DD_TRY_CUDA(ctx, cudaMemsetAsync(D.bar, 0, 2 * sizeof(unsigned), s));
     BCGArgs A;
-    A.seg = d_seg;
-    A.blk_seg = d_bs;
-    A.S = n;
-    A.part = d_part;
-    A.flags = d_flags;
-    A.bar = d_bar;
+    A.seg = D.seg;
+    A.blk_seg = D.blk_seg;
+    A.S = T.n;
+    A.part = D.part;
+    A.flags = D.flags;
+    A.bar = D.bar;
     A.err = ctx->dev_err;
     A.rtol2 = rtol * rtol;
     A.in_rtol2 = 1e-8;                  // each refinement step gains four digits
     A.max_outer = 30;
     A.max_inner = max_it;
-    A.it_out = *it_dev;
+    A.it_out = D.it;
     void *args[] = {&A};
     ctx->launches++;
-    DD_TRY_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)k_cg_batch, dim3(total), dim3(kBThreads), args,
+    DD_TRY_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)k_cg_batch, dim3(T.total), dim3(kBThreads), args,
                                                  kDynSmem, s));
     return DD_OK;
 }
 
+// Mixed-precision CG of n systems in one cooperative launch.  *it_dev points
+// at the per-system inner iteration counts (device) after the launch.
+dd_status dd_cg_segments(dd_ctx *ctx, const MeshDev *const *gs, const CGBuffers *const *cbs, int n, double rtol,
+                         int max_it, cudaStream_t s, int **it_dev) {
+    CGTables T;
+    DD_TRY(cg_tables(ctx, gs, cbs, n, T));
+    void *w = nullptr;
+    DD_TRY(dd_workspace(ctx, WS_BATCH_CG, cg_dev_bytes(T), &w));
+    const CGDev D = cg_carve(T, w);
+    DD_TRY(cg_upload(ctx, T, D, s));
+    DD_TRY(cg_launch(ctx, T, D, rtol, max_it, s));
+    *it_dev = D.it;
+    return DD_OK;
+}
 
-extern "C" dd_status dd_solvers_step(dd_solver **svs, int n, dd_iter_info *infos) {
-    if (!svs || n < 1 || !svs[0]) return DD_ERR_ARG;
+// ---------------------------------------------------------------------------
+// One batched DD iteration
+// ---------------------------------------------------------------------------
+namespace {
+
+// Buffers of one batched step: the concatenated search state, optional
+// uploaded CG tables and per-solve f_d (captured form), and the host buffers
+// that receive the per-solve statistics.
+struct StepIO {
+    const CGTables *cgt = nullptr;      // null: built and uploaded per call
+    const CGDev *cgd = nullptr;
+    double *y_cat = nullptr;
+    int32_t *prev_cat = nullptr, *idx_cat = nullptr;
+    double *d2_cat = nullptr, *d2nd_cat = nullptr;
+    float *fd_cat = nullptr;
+    AnnMotion mot{nullptr, nullptr};
+    const float *fd_dev = nullptr;      // [n] f_d of every solve in device memory, or null (host values)
+    double *h_stats = nullptr;          // [3 n] host copy of (changed, d2 after P_D, d2 after P_C)
+    int *h_it = nullptr;                // [n] host copy of the CG iteration counts
+    DeferredStats *defer_dev = nullptr, *h_defer = nullptr;
+};
+
+size_t concat_bytes(int64_t M) {
+    return r256((size_t)M * 96) + 2 * r256((size_t)M * 4) + 2 * r256((size_t)M * 8) + r256((size_t)M * 4) +
+           r256((size_t)M * 48) + r256((size_t)M * 8);
+}
+
+void concat_carve(StepIO &io, int64_t M, void *base) {
+    char *c = (char *)base;
+    io.y_cat = (double *)c;
+    c += r256((size_t)M * 96);
+    io.prev_cat = (int32_t *)c;
+    c += r256((size_t)M * 4);
+    io.idx_cat = (int32_t *)c;
+    c += r256((size_t)M * 4);
+    io.d2_cat = (double *)c;
+    c += r256((size_t)M * 8);
+    io.d2nd_cat = (double *)c;
+    c += r256((size_t)M * 8);
+    io.fd_cat = (float *)c;
+    c += r256((size_t)M * 4);
+    io.mot.q = (float *)c;
+    c += r256((size_t)M * 48);
+    io.mot.d = (float *)c;
+}
+
+// Every device operation of one batched iteration, on stream s and without a
+// host synchronisation unless the search needs one (an exact re-search at
+// f_d = 1, never in a captured step): per-solve gather and RHS, ONE CG launch,
+// per-solve recovery, ONE search over the concatenated states, scatter,
+// per-solve statistics and their copy to the host buffers of io.
+dd_status enqueue_step(dd_solver **svs, int n, const StepIO &io, const std::vector<double> &fds,
+                       dd_search_stats &sst, cudaStream_t s) {
     dd_ctx *ctx = svs[0]->ctx;
     dd_dataset *ds = svs[0]->ds;
     const dd_solve_opts &o0 = svs[0]->o;
-    int64_t M = 0, nodes = 0;
-    for (int i = 0; i < n; ++i) {
-        dd_solver *sv = svs[i];
-        if (!sv || sv->ds != ds) return dd_fail(ctx, DD_ERR_ARG, "dd_solvers_step: solvers must share one data set");
-        if (sv->done) return dd_fail(ctx, DD_ERR_STATE, "dd_solvers_step: a solve has already finished");
-        if (sv->o.mode != o0.mode || sv->o.certify != o0.certify || sv->o.cg_mode != o0.cg_mode)
-            return dd_fail(ctx, DD_ERR_ARG, "dd_solvers_step: solvers must share search mode, certify and cg_mode");
-        for (int j = 0; j < i; ++j)
-            if (svs[j] == sv) return dd_fail(ctx, DD_ERR_ARG, "dd_solvers_step: a solver appears twice");
-        M += sv->g.n_gp;
-        nodes += sv->g.n_nodes;
-    }
-    DD_TRY_CUDA(ctx, cudaSetDevice(ctx->device));
-    cudaStream_t s = ctx->stream;
+    int64_t M = 0;
+    for (int i = 0; i < n; ++i) M += svs[i]->g.n_gp;
     cudaEvent_t *ev = svs[0]->ev;   // batch-level phase events
     DD_TRY_CUDA(ctx, cudaEventRecord(ev[0], s));
     for (int i = 0; i < n; ++i) {
         dd_solver *sv = svs[i];
-        ++sv->it;
         DD_TRY(fem_gather_star(ds, sv->cur, sv->g.n_gp, sv->star, sv->ce, s));
         DD_TRY(fem_assemble_rhs(ctx, sv->g, sv->ops, sv->star, sv->ce, sv->f, const_cast<double *>(sv->cb.b), s));
     }
     // ---- one cooperative CG launch for every solve ----
-    std::vector<int> it_host(n, 0);
     int *it_dev = nullptr;
     if (o0.cg_mode == 1) {
         for (int i = 0; i < n; ++i) DD_TRY(fem_cg(ctx, svs[i]->g, svs[i]->cb, o0.cg_rtol, o0.cg_max_iter, s));
+    } else if (io.cgt) {
+        DD_TRY(cg_launch(ctx, *io.cgt, *io.cgd, o0.cg_rtol, o0.cg_max_iter, s));
+        it_dev = io.cgd->it;
     } else {
         std::vector<const MeshDev *> gs(n);
         std::vector<const CGBuffers *> cbs(n);
@@ -659,55 +753,42 @@ extern "C" dd_status dd_solvers_step(dd_solver **svs, int n, dd_iter_info *infos
     DD_TRY_CUDA(ctx, cudaEventRecord(ev[2], s));
 
     // ---- one search over the concatenated states ----
-    auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
-    const size_t b_y = r256((size_t)M * 96), b_i = r256((size_t)M * 4), b_d = r256((size_t)M * 8),
-                 b_fd = r256((size_t)M * 4), b_mq = r256((size_t)M * 48), b_md = r256((size_t)M * 8);
-    void *w = nullptr;
-    DD_TRY(dd_workspace(ctx, WS_BATCH, b_y + 2 * b_i + 2 * b_d + b_fd + b_mq + b_md, &w));
-    char *c = (char *)w;
-    double *y_cat = (double *)c;
-    int32_t *prev_cat = (int32_t *)(c + b_y);
-    int32_t *idx_cat = (int32_t *)(c + b_y + b_i);
-    double *d2_cat = (double *)(c + b_y + 2 * b_i);
-    double *d2nd_cat = (double *)(c + b_y + 2 * b_i + b_d);
-    float *fd_cat = (float *)(c + b_y + 2 * b_i + 2 * b_d);
-    AnnMotion mot_cat{(float *)(c + b_y + 2 * b_i + 2 * b_d + b_fd), (float *)(c + b_y + 2 * b_i + 2 * b_d + b_fd + b_mq)};
     const bool ann = o0.mode == DD_SEARCH_ANN;
-    std::vector<double> fds(n);
     int64_t off = 0;
     for (int i = 0; i < n; ++i) {
         dd_solver *sv = svs[i];
         const int64_t ng = sv->g.n_gp;
-        fds[i] = dd_solver_fd(sv, sv->it);
-        DD_TRY_CUDA(ctx, cudaMemcpyAsync(y_cat + off * 12, sv->y, ng * 96, cudaMemcpyDeviceToDevice, s));
+        DD_TRY_CUDA(ctx, cudaMemcpyAsync(io.y_cat + off * 12, sv->y, ng * 96, cudaMemcpyDeviceToDevice, s));
         if (ann) {
-            DD_TRY_CUDA(ctx, cudaMemcpyAsync(prev_cat + off, sv->cur, ng * 4, cudaMemcpyDeviceToDevice, s));
-            DD_TRY_CUDA(ctx, cudaMemcpyAsync(mot_cat.q + off * 12, sv->mot.q, ng * 48, cudaMemcpyDeviceToDevice, s));
-            DD_TRY_CUDA(ctx, cudaMemcpyAsync(mot_cat.d + off * 2, sv->mot.d, ng * 8, cudaMemcpyDeviceToDevice, s));
+            DD_TRY_CUDA(ctx, cudaMemcpyAsync(io.prev_cat + off, sv->cur, ng * 4, cudaMemcpyDeviceToDevice, s));
+            DD_TRY_CUDA(ctx, cudaMemcpyAsync(io.mot.q + off * 12, sv->mot.q, ng * 48, cudaMemcpyDeviceToDevice, s));
+            DD_TRY_CUDA(ctx, cudaMemcpyAsync(io.mot.d + off * 2, sv->mot.d, ng * 8, cudaMemcpyDeviceToDevice, s));
             ctx->launches++;
-            k_fill_f<<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(fd_cat + off, ng, (float)fds[i]);
+            if (io.fd_dev)
+                k_fill_fd<<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(io.fd_cat + off, ng, io.fd_dev + i);
+            else
+                k_fill_f<<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(io.fd_cat + off, ng, (float)fds[i]);
         }
         off += ng;
     }
-    dd_search_stats sst;
-    std::memset(&sst, 0, sizeof(sst));
-    SearchOut so{idx_cat, d2_cat, d2nd_cat};
+    SearchOut so{io.idx_cat, io.d2_cat, io.d2nd_cat};
+    AnnMotion mot = io.mot;
     if (ann) {
         if (!ds->ann.nlist) return dd_fail(ctx, DD_ERR_STATE, "ANN search needs the partition (ann_nlist)");
-        DD_TRY(dd_search_ann_motion(ds, y_cat, M, fds[0], fd_cat, prev_cat, &mot_cat, so, &sst, s));
+        DD_TRY(dd_search_ann_motion(ds, io.y_cat, M, fds[0], io.fd_cat, io.prev_cat, &mot, so, &sst, s));
     } else {
-        DD_TRY(dd_run_search(ds, o0.mode, o0.certify, o0.f_d_final, nullptr, y_cat, M, so, &sst, s));
+        DD_TRY(dd_run_search(ds, o0.mode, o0.certify, o0.f_d_final, nullptr, io.y_cat, M, so, &sst, s));
     }
     off = 0;
     for (int i = 0; i < n; ++i) {
         dd_solver *sv = svs[i];
         const int64_t ng = sv->g.n_gp;
-        DD_TRY_CUDA(ctx, cudaMemcpyAsync(sv->nxt, idx_cat + off, ng * 4, cudaMemcpyDeviceToDevice, s));
-        DD_TRY_CUDA(ctx, cudaMemcpyAsync(sv->d2, d2_cat + off, ng * 8, cudaMemcpyDeviceToDevice, s));
-        DD_TRY_CUDA(ctx, cudaMemcpyAsync(sv->d2nd, d2nd_cat + off, ng * 8, cudaMemcpyDeviceToDevice, s));
+        DD_TRY_CUDA(ctx, cudaMemcpyAsync(sv->nxt, io.idx_cat + off, ng * 4, cudaMemcpyDeviceToDevice, s));
+        DD_TRY_CUDA(ctx, cudaMemcpyAsync(sv->d2, io.d2_cat + off, ng * 8, cudaMemcpyDeviceToDevice, s));
+        DD_TRY_CUDA(ctx, cudaMemcpyAsync(sv->d2nd, io.d2nd_cat + off, ng * 8, cudaMemcpyDeviceToDevice, s));
         if (ann) {
-            DD_TRY_CUDA(ctx, cudaMemcpyAsync(sv->mot.q, mot_cat.q + off * 12, ng * 48, cudaMemcpyDeviceToDevice, s));
-            DD_TRY_CUDA(ctx, cudaMemcpyAsync(sv->mot.d, mot_cat.d + off * 2, ng * 8, cudaMemcpyDeviceToDevice, s));
+            DD_TRY_CUDA(ctx, cudaMemcpyAsync(sv->mot.q, io.mot.q + off * 12, ng * 48, cudaMemcpyDeviceToDevice, s));
+            DD_TRY_CUDA(ctx, cudaMemcpyAsync(sv->mot.d, io.mot.d + off * 2, ng * 8, cudaMemcpyDeviceToDevice, s));
         }
         off += ng;
     }
@@ -715,25 +796,282 @@ extern "C" dd_status dd_solvers_step(dd_solver **svs, int n, dd_iter_info *infos
     for (int i = 0; i < n; ++i)
         DD_TRY(fem_iter_stats(ctx, svs[i]->nxt, svs[i]->cur, svs[i]->d2, svs[i]->dpc, svs[i]->g.n_gp, svs[i]->g.w,
                               svs[i]->stats, s));
-    std::vector<double> hs((size_t)n * 3);
     for (int i = 0; i < n; ++i)
-        DD_TRY_CUDA(ctx, cudaMemcpyAsync(&hs[(size_t)i * 3], svs[i]->stats, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        DD_TRY_CUDA(ctx, cudaMemcpyAsync(io.h_stats + (size_t)i * 3, svs[i]->stats, 3 * sizeof(double),
+                                         cudaMemcpyDeviceToHost, s));
     if (it_dev) {
-        DD_TRY_CUDA(ctx, cudaMemcpyAsync(it_host.data(), it_dev, n * sizeof(int), cudaMemcpyDeviceToHost, s));
+        DD_TRY_CUDA(ctx, cudaMemcpyAsync(io.h_it, it_dev, n * sizeof(int), cudaMemcpyDeviceToHost, s));
     } else {
         for (int i = 0; i < n; ++i)
-            DD_TRY_CUDA(ctx, cudaMemcpyAsync(&it_host[i], svs[i]->cb.it_out, sizeof(int), cudaMemcpyDeviceToHost, s));
+            DD_TRY_CUDA(ctx, cudaMemcpyAsync(io.h_it + i, svs[i]->cb.it_out, sizeof(int), cudaMemcpyDeviceToHost, s));
     }
-    DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
-    DD_TRY(dd_check_device_error(ctx, s, "dd_solvers_step"));
+    if (io.h_defer)
+        DD_TRY_CUDA(ctx, cudaMemcpyAsync(io.h_defer, io.defer_dev, sizeof(DeferredStats), cudaMemcpyDeviceToHost, s));
+    return DD_OK;
+}
+
+// After the step's stream has drained: phase times, deferred search
+// counters, and every solve's bookkeeping and stop rule.
+void finish_step(dd_solver **svs, int n, const double *hs, const int *its, dd_search_stats sst,
+                 const std::vector<double> &fds, const DeferredStats *dfr, bool graph, dd_iter_info *infos) {
+    dd_ctx *ctx = svs[0]->ctx;
+    cudaEvent_t *ev = svs[0]->ev;
     float t01 = 0, t12 = 0, t23 = 0;
     cudaEventElapsedTime(&t01, ev[0], ev[1]);
     cudaEventElapsedTime(&t12, ev[1], ev[2]);
     cudaEventElapsedTime(&t23, ev[2], ev[3]);
+    if (dfr) {
+        const int64_t N = svs[0]->ds->N;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ctx->ev_scan[0], ctx->ev_scan[1]) == cudaSuccess) sst.scan_ms += ms;
+        sst.uncertified += (int64_t)(dfr->fb + dfr->ann[2]);
+        sst.distances += (int64_t)dfr->fb * N + (int64_t)dfr->ann[0] + (int64_t)dfr->ann[3] + (int64_t)dfr->ann[2] * N;
+        sst.points += (int64_t)dfr->ann[0] + (int64_t)dfr->ann[2] * N;
+        sst.skipped += (int64_t)dfr->ann[1];
+    }
     for (int i = 0; i < n; ++i) {
         dd_search_stats si = sst;   // the shared search is reported to every solve
-        dd_solver_account(svs[i], &hs[(size_t)i * 3], it_host[i], t01, t12, t23, si, fds[i], infos ? &infos[i] : nullptr);
+        dd_solver_account(svs[i], hs + (size_t)i * 3, its[i], t01, t12, t23, si, fds[i], infos ? &infos[i] : nullptr);
+        if (infos) infos[i].graph = graph ? 1 : 0;
     }
+}
+
+}  // namespace
+
+// A batched step of a fixed list of solves, kept while the same list is
+// stepped again: its own device copies of the CG tables and of the
+// concatenated search state (no workspace that another call could move),
+// pinned host buffers for f_d and the statistics, and the step captured as a
+// CUDA graph once per parity of the solves' association buffers.
+struct StepPlan {
+    std::vector<uint64_t> ids;
+    int n = 0;
+    CGTables cgt;
+    CGDev cgd;
+    StepIO io;
+    void *dev = nullptr;
+    size_t dev_bytes = 0;
+    void *pin = nullptr;
+    float *fd_host = nullptr;            // pinned [n]
+    bool no_graph = false;               // capture failed once: run this list eagerly
+    struct Variant {
+        std::vector<char> parity;
+        cudaGraphExec_t exec = nullptr;
+        uint64_t ws_gen = 0;
+        int64_t launches = 0;            // kernels in the graph
+        dd_search_stats sst;             // search statistics fixed at capture
+    };
+    std::vector<Variant> var;
+};
+
+static void plan_free(dd_ctx *ctx, StepPlan *P) {
+    for (auto &v : P->var)
+        if (v.exec) cudaGraphExecDestroy(v.exec);
+    if (P->dev) dd_free(ctx, P->dev, P->dev_bytes);
+    if (P->pin) cudaFreeHost(P->pin);
+    delete P;
+}
+
+void dd_plans_drop(dd_ctx *ctx, uint64_t id) {
+    if (ctx->plans.empty()) return;
+    cudaStreamSynchronize(ctx->stream);
+    std::vector<StepPlan *> keep;
+    for (StepPlan *P : ctx->plans) {
+        if (id == 0 || std::find(P->ids.begin(), P->ids.end(), id) != P->ids.end()) plan_free(ctx, P);
+        else keep.push_back(P);
+    }
+    ctx->plans.swap(keep);
+    if (id == 0 || std::find(ctx->last_batch.begin(), ctx->last_batch.end(), id) != ctx->last_batch.end())
+        ctx->last_batch.clear();
+}
+
+static dd_status plan_make(dd_solver **svs, int n, int64_t M, StepPlan **out) {
+    dd_ctx *ctx = svs[0]->ctx;
+    const bool cg_seg = svs[0]->o.cg_mode != 1;
+    StepPlan *P = new StepPlan();
+    P->n = n;
+    for (int i = 0; i < n; ++i) P->ids.push_back(svs[i]->id);
+    auto fail = [&](dd_status st) {
+        plan_free(ctx, P);
+        return st;
+    };
+    if (cg_seg) {
+        std::vector<const MeshDev *> gs(n);
+        std::vector<const CGBuffers *> cbs(n);
+        for (int i = 0; i < n; ++i) {
+            gs[i] = &svs[i]->g;
+            cbs[i] = &svs[i]->cb;
+        }
+        dd_status st = cg_tables(ctx, gs.data(), cbs.data(), n, P->cgt);
+        if (st != DD_OK) return fail(st);
+    }
+    const size_t b_cg = cg_seg ? r256(cg_dev_bytes(P->cgt)) : 0, b_cat = concat_bytes(M), b_fd = r256((size_t)n * 4),
+                 b_def = r256(sizeof(DeferredStats));
+    P->dev_bytes = b_cg + b_cat + b_fd + b_def;
+    dd_status st = dd_alloc(ctx, &P->dev, P->dev_bytes, "batched step plan");
+    if (st != DD_OK) {
+        P->dev = nullptr;
+        return fail(st);
+    }
+    char *c = (char *)P->dev;
+    if (cg_seg) {
+        P->cgd = cg_carve(P->cgt, c);
+        P->io.cgt = &P->cgt;
+        P->io.cgd = &P->cgd;
+    }
+    concat_carve(P->io, M, c + b_cg);
+    float *fd_dev = (float *)(c + b_cg + b_cat);
+    P->io.fd_dev = fd_dev;
+    P->io.defer_dev = (DeferredStats *)(c + b_cg + b_cat + b_fd);
+    const size_t h_stats = r256((size_t)n * 24), h_it = r256((size_t)n * 4), h_fd = r256((size_t)n * 4);
+    if (cudaHostAlloc(&P->pin, h_stats + h_it + h_fd + r256(sizeof(DeferredStats)), cudaHostAllocDefault) !=
+        cudaSuccess) {
+        P->pin = nullptr;
+        return fail(dd_fail(ctx, DD_ERR_OOM, "batched step plan: pinned host buffers"));
+    }
+    char *h = (char *)P->pin;
+    P->io.h_stats = (double *)h;
+    P->io.h_it = (int *)(h + h_stats);
+    P->fd_host = (float *)(h + h_stats + h_it);
+    P->io.h_defer = (DeferredStats *)(h + h_stats + h_it + h_fd);
+    cudaStream_t s = ctx->stream;
+    if ((cg_seg && (st = cg_upload(ctx, P->cgt, P->cgd, s)) != DD_OK)) return fail(st);
+    if (cudaMemsetAsync(P->io.defer_dev, 0, sizeof(DeferredStats), s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return fail(dd_fail(ctx, DD_ERR_CUDA, "batched step plan: upload"));
+    if (ctx->plans.size() >= 4) {   // keep the four most recent lists
+        plan_free(ctx, ctx->plans.front());
+        ctx->plans.erase(ctx->plans.begin());
+    }
+    ctx->plans.push_back(P);
+    *out = P;
+    return DD_OK;
+}
+
+// Capture the step into a graph for the current parity; null when capture is
+// not possible (the caller then runs the step eagerly).
+static StepPlan::Variant *plan_capture(StepPlan *P, dd_solver **svs, int n, const std::vector<char> &par,
+                                       const std::vector<double> &fds) {
+    dd_ctx *ctx = svs[0]->ctx;
+    cudaStream_t s = ctx->stream;
+    StepPlan::Variant v;
+    v.parity = par;
+    std::memset(&v.sst, 0, sizeof(v.sst));
+    const int64_t l0 = ctx->launches;
+    const std::string err0 = ctx->err;
+    ctx->capturing = true;
+    ctx->defer = P->io.defer_dev;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
+    dd_status st = DD_OK;
+    if (e == cudaSuccess) {
+        st = enqueue_step(svs, n, P->io, fds, v.sst, s);
+        const cudaError_t e2 = cudaStreamEndCapture(s, &g);
+        if (e == cudaSuccess) e = e2;
+    }
+    ctx->capturing = false;
+    ctx->defer = nullptr;
+    v.launches = ctx->launches - l0;
+    ctx->launches = l0;          // nothing ran yet; every replay adds v.launches
+    v.ws_gen = ctx->ws_gen;
+    if (e == cudaSuccess && st == DD_OK && g) e = cudaGraphInstantiate(&v.exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess || st != DD_OK || !v.exec) {
+        cudaGetLastError();      // clear the capture error; this list runs eagerly from now on
+        ctx->err = err0;
+        P->no_graph = true;
+        return nullptr;
+    }
+    P->var.push_back(v);
+    return &P->var.back();
+}
+
+extern "C" dd_status dd_solvers_step(dd_solver **svs, int n, dd_iter_info *infos) {
+    if (!svs || n < 1 || !svs[0]) return DD_ERR_ARG;
+    dd_ctx *ctx = svs[0]->ctx;
+    dd_dataset *ds = svs[0]->ds;
+    const dd_solve_opts &o0 = svs[0]->o;
+    int64_t M = 0;
+    for (int i = 0; i < n; ++i) {
+        dd_solver *sv = svs[i];
+        if (!sv || sv->ds != ds) return dd_fail(ctx, DD_ERR_ARG, "dd_solvers_step: solvers must share one data set");
+        if (sv->done) return dd_fail(ctx, DD_ERR_STATE, "dd_solvers_step: a solve has already finished");
+        if (sv->o.mode != o0.mode || sv->o.certify != o0.certify || sv->o.cg_mode != o0.cg_mode)
+            return dd_fail(ctx, DD_ERR_ARG, "dd_solvers_step: solvers must share search mode, certify and cg_mode");
+        for (int j = 0; j < i; ++j)
+            if (svs[j] == sv) return dd_fail(ctx, DD_ERR_ARG, "dd_solvers_step: a solver appears twice");
+        M += sv->g.n_gp;
+    }
+    DD_TRY_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t s = ctx->stream;
+    const bool ann = o0.mode == DD_SEARCH_ANN;
+    std::vector<double> fds(n);
+    bool full_fd = false;   // f_d = 1 may need an exact re-search sized on the host
+    std::vector<uint64_t> ids(n);
+    for (int i = 0; i < n; ++i) {
+        ++svs[i]->it;
+        fds[i] = dd_solver_fd(svs[i], svs[i]->it);
+        full_fd |= ann && fds[i] >= 1.0;
+        ids[i] = svs[i]->id;
+    }
+    // ---- the same list as the previous step: replay its captured graph ----
+    const bool repeat = ids == ctx->last_batch;
+    ctx->last_batch = ids;
+    StepPlan *P = nullptr;
+    if (repeat && !full_fd) {
+        for (StepPlan *q : ctx->plans)
+            if (q->ids == ids) P = q;
+        if (!P) {
+            const std::string err0 = ctx->err;
+            if (plan_make(svs, n, M, &P) != DD_OK) {
+                P = nullptr;     // not enough memory for a plan: step eagerly
+                ctx->err = err0;
+            }
+        }
+    }
+    if (P && !P->no_graph) {
+        std::vector<char> par(n);
+        for (int i = 0; i < n; ++i) par[i] = svs[i]->cur != svs[i]->idx_a;
+        StepPlan::Variant *v = nullptr;
+        for (auto it = P->var.begin(); it != P->var.end(); ++it)
+            if (it->parity == par) {
+                if (it->ws_gen != ctx->ws_gen) {   // a workspace it uses has moved
+                    cudaGraphExecDestroy(it->exec);
+                    P->var.erase(it);
+                } else {
+                    v = &*it;
+                }
+                break;
+            }
+        for (int i = 0; i < n; ++i) P->fd_host[i] = (float)fds[i];
+        if (!v) v = plan_capture(P, svs, n, par, fds);
+        if (v) {
+            // this step's f_d values, read by the graph's fill kernels
+            DD_TRY_CUDA(ctx, cudaMemcpyAsync((void *)P->io.fd_dev, P->fd_host, n * sizeof(float),
+                                             cudaMemcpyHostToDevice, s));
+            ctx->launches += v->launches;
+            DD_TRY_CUDA(ctx, cudaGraphLaunch(v->exec, s));
+            DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+            DD_TRY(dd_check_device_error(ctx, s, "dd_solvers_step"));
+            finish_step(svs, n, P->io.h_stats, P->io.h_it, v->sst, fds, P->io.h_defer, true, infos);
+            return DD_OK;
+        }
+    }
+    // ---- eager step ----
+    StepIO io;
+    void *w = nullptr;
+    DD_TRY(dd_workspace(ctx, WS_BATCH, concat_bytes(M), &w));
+    concat_carve(io, M, w);
+    std::vector<double> hs((size_t)n * 3);
+    std::vector<int> its(n, 0);
+    io.h_stats = hs.data();
+    io.h_it = its.data();
+    dd_search_stats sst;
+    std::memset(&sst, 0, sizeof(sst));
+    DD_TRY(enqueue_step(svs, n, io, fds, sst, s));
+    DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+    DD_TRY(dd_check_device_error(ctx, s, "dd_solvers_step"));
+    finish_step(svs, n, hs.data(), its.data(), sst, fds, nullptr, false, infos);
     return DD_OK;
 }
 

@@ -50,6 +50,7 @@ dd_status dd_workspace(dd_ctx *ctx, int slot, size_t bytes, void **out) {
         *out = w.ptr;
         return DD_OK;
     }
+    if (ctx->capturing) return dd_fail(ctx, DD_ERR_STATE, "workspace would grow while a step is captured");
     if (w.ptr) {
         DD_TRY_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         DD_TRY_CUDA(ctx, cudaDeviceSynchronize());
@@ -60,6 +61,7 @@ dd_status dd_workspace(dd_ctx *ctx, int slot, size_t bytes, void **out) {
     size_t nb = std::max<size_t>(bytes + bytes / 4, 4096);
     DD_TRY(dd_alloc(ctx, &w.ptr, nb, "workspace"));
     w.bytes = nb;
+    ctx->ws_gen++;
     *out = w.ptr;
     return DD_OK;
 }
@@ -131,6 +133,7 @@ extern "C" void dd_destroy(dd_ctx *ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    dd_plans_drop(ctx, 0);
     for (auto &w : ctx->ws)
         if (w.ptr) cudaFree(w.ptr);
     cudaFree(ctx->dev_err);
@@ -206,6 +209,7 @@ extern "C" void dd_free_dataset(dd_dataset *ds) {
     dd_ctx *ctx = ds->ctx;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    dd_plans_drop(ctx, 0);
     if (ds->owns_raw) dd_free(ctx, (void *)ds->raw, (size_t)ds->N * 48);
     dd_free(ctx, ds->z32, (size_t)ds->N_pad * 48);
     dd_free(ctx, ds->zn, (size_t)ds->N_pad * 4);

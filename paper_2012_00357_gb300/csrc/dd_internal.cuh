@@ -69,6 +69,16 @@ struct Workspace {
     size_t bytes = 0;
 };
 
+// Search counters that a step captured into a CUDA graph copies to device
+// memory instead of reading them back in the middle of the step; the host
+// reads them after the step.
+struct DeferredStats {
+    unsigned long long fb;       // exact search: queries re-searched in FP64
+    unsigned long long ann[4];   // approximate search: points scanned, skipped, exact re-search, fine centroids
+};
+
+struct StepPlan;
+
 struct dd_ctx {
     int device = 0;
     int n_sm = 0;
@@ -82,7 +92,16 @@ struct dd_ctx {
     int64_t launches = 0;               // kernels launched (instrumentation)
     int tc_epi[2] = {0, 0};             // tuned epilogue warps of the tensor-core scan (top-k, certified)
     cudaEvent_t ev_scan[2] = {nullptr, nullptr};   // brackets the dominant scan kernel
+    uint64_t ws_gen = 0;                // bumped whenever a workspace is reallocated
+    bool capturing = false;             // a step is being captured: no host syncs, no allocation
+    DeferredStats *defer = nullptr;     // set while enqueuing a captured step (device counters)
+    std::vector<StepPlan *> plans;      // cached batched-step plans (batch.cu)
+    std::vector<uint64_t> last_batch;   // solver ids of the previous batched step
 };
+
+// Free the cached batched-step plans that hold solver `id` (all plans if id
+// is 0); they keep device pointers into the solvers' state.
+void dd_plans_drop(dd_ctx *ctx, uint64_t id);
 
 enum WsSlot {
     WS_SEARCH = 0, WS_QUERY = 1, WS_MISC = 2, WS_SOLVE = 3, WS_TC = 4, WS_ANN = 5, WS_ANN_SCAN = 6, WS_ANN_BUILD = 7,

@@ -370,7 +370,9 @@ dd_status dd_merge_rescore(dd_dataset *ds, const double *y_dev, int64_t m, int s
                                              out.idx, out.d2, out.d2nd);
         DD_TRY_CUDA(ctx, cudaGetLastError());
     }
-    if (st) {
+    if (st && ctx->defer) {
+        DD_TRY_CUDA(ctx, cudaMemcpyAsync(&ctx->defer->fb, fb_count, sizeof(*fb_count), cudaMemcpyDeviceToDevice, s));
+    } else if (st) {
         unsigned long long n = 0;
         DD_TRY_CUDA(ctx, cudaMemcpyAsync(&n, fb_count, sizeof(n), cudaMemcpyDeviceToHost, s));
         DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
@@ -434,7 +436,7 @@ dd_status dd_search_exact_fp32(dd_dataset *ds, const double *y_dev, int64_t m, i
     if (st) DD_TRY_CUDA(ctx, cudaEventRecord(ctx->ev_scan[1], s));
     if (st) st->distances += m * ds->N;
     DD_TRY(dd_merge_rescore(ds, y_dev, m, splits, kCap, hdr, cand, rec, certify, 1.0, out, st, s));
-    if (st) {
+    if (st && !ctx->defer) {
         float ms = 0.f;
         DD_TRY_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev_scan[0], ctx->ev_scan[1]));
         st->scan_ms += ms;

@@ -533,7 +533,7 @@ dd_status dd_search_exact_tc(dd_dataset *ds, const double *y_dev, int64_t m, int
     // layouts (4 or 8 epilogue warps) on the live problem and keeps the faster
     // one for this context; both return the same certified candidates.
     int &epi = ctx->tc_epi[kc == 3 ? 1 : 0];
-    if (epi == 0 && (double)m * (double)ds->N >= 1e9) {
+    if (epi == 0 && !ctx->capturing && (double)m * (double)ds->N >= 1e9) {
         float best = 1e30f;
         for (int e : {4, 8}) {
             DD_TRY_CUDA(ctx, cudaEventRecord(ctx->ev_scan[0], s));
@@ -555,7 +555,7 @@ dd_status dd_search_exact_tc(dd_dataset *ds, const double *y_dev, int64_t m, int
     if (st) st->distances += m * ds->N;
     DD_TRY(dd_merge_rescore(ds, y_dev, m, splits * (use_epi / 4), kCap, hdr, cand, rec, certify,
                             1.0 / (ds->scale16 * ds->scale16), out, st, s));
-    if (st) {
+    if (st && !ctx->defer) {
         float ms = 0.f;
         DD_TRY_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev_scan[0], ctx->ev_scan[1]));
         st->scan_ms += ms;

@@ -12,6 +12,7 @@
 // change (exact search, Sec. 2), or for the approximate search the global
 // distance Eq. (2) stopped decreasing.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -80,6 +81,7 @@ size_t carve(dd_solver *sv, char *base) {
     sv->d2nd = bp.take<double>(ng);
     sv->cur = bp.take<int32_t>(ng);
     sv->nxt = bp.take<int32_t>(ng);
+    sv->idx_a = sv->cur;
     sv->stats = bp.take<double>(8);
     sv->mot.q = bp.take<float>(ng * 12);
     sv->mot.d = bp.take<float>(ng * 2);
@@ -139,6 +141,7 @@ bool dd_solver_account(dd_solver *sv, const double hs[3], int cg_it, float cg_ms
         info->done = sv->done ? 1 : 0;
         info->skipped = sst.skipped;
         info->points = sst.points;
+        info->graph = 0;
     }
     return sv->done;
 }
@@ -179,7 +182,9 @@ extern "C" dd_status dd_solver_create(dd_dataset *ds, const dd_mesh *mesh, const
         if (!std::isfinite(load->t0[c]) || !std::isfinite(load->tx[c]) || !std::isfinite(load->ty[c]))
             return dd_fail(ctx, DD_ERR_ARG, "dd_solver_create: non-finite load");
     DD_TRY_CUDA(ctx, cudaSetDevice(ctx->device));
+    static std::atomic<uint64_t> next_id{1};
     dd_solver *sv = new dd_solver();
+    sv->id = next_id++;
     sv->ds = ds;
     sv->ctx = ctx;
     sv->mesh = *mesh;
@@ -231,6 +236,7 @@ extern "C" void dd_solver_free(dd_solver *sv) {
     if (!sv) return;
     cudaSetDevice(sv->ctx->device);
     cudaStreamSynchronize(sv->ctx->stream);
+    dd_plans_drop(sv->ctx, sv->id);
     for (auto &e : sv->ev)
         if (e) cudaEventDestroy(e);
     dd_free(sv->ctx, sv->block, sv->block_bytes);

@@ -20,6 +20,8 @@ struct dd_solver {
     float *St32 = nullptr;
     double *dpc = nullptr, *d2 = nullptr, *d2nd = nullptr, *stats = nullptr;
     int32_t *cur = nullptr, *nxt = nullptr;
+    int32_t *idx_a = nullptr;           // the first of the two association buffers (cur or nxt)
+    uint64_t id = 0;                    // unique per process (keys the cached step plans)
     AnnMotion mot{nullptr, nullptr};    // Eq. 14 record of the approximate search
     CGBuffers cb;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
