@@ -1007,7 +1007,7 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
     int splits = 0, cap = 0;
     CandHeader *hdr = nullptr;
     float2 *cand = nullptr;
-    if (st) DD_TRY_CUDA(ctx, cudaEventRecord(ctx->ev_scan[0], s));
+    if (st) DD_TRY_CUDA(ctx, dd_event_record(ctx, ctx->ev_scan[0], s));
     const bool two = a.levels == 2;
     const float *rank_cent = two ? a.cent1 : a.cent;
     DD_TRY(dd_scan_fp32_raw(ctx, rank_cent, two ? a.cn1 : a.cn, two ? a.L1 : a.nlist, rec, m, true, WS_ANN_SCAN,
@@ -1047,7 +1047,7 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
         k_ann_probe<<<(unsigned)((m * 32 + 255) / 256), 256, 0, s>>>(A);
     }
     DD_TRY_CUDA(ctx, cudaGetLastError());
-    if (st) DD_TRY_CUDA(ctx, cudaEventRecord(ctx->ev_scan[1], s));
+    if (st) DD_TRY_CUDA(ctx, dd_event_record(ctx, ctx->ev_scan[1], s));
     k_ann_finish<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(ds->raw, ds->M, y_dev, m, out.idx, d2f, out.d2,
                                                              out.d2nd);
     DD_TRY_CUDA(ctx, cudaGetLastError());

@@ -725,7 +725,7 @@ dd_status enqueue_step(dd_solver **svs, int n, const StepIO &io, const std::vect
     int64_t M = 0;
     for (int i = 0; i < n; ++i) M += svs[i]->g.n_gp;
     cudaEvent_t *ev = svs[0]->ev;   // batch-level phase events
-    DD_TRY_CUDA(ctx, cudaEventRecord(ev[0], s));
+    DD_TRY_CUDA(ctx, dd_event_record(ctx, ev[0], s));
     for (int i = 0; i < n; ++i) {
         dd_solver *sv = svs[i];
         DD_TRY(fem_gather_star(ds, sv->cur, sv->g.n_gp, sv->star, sv->ce, s));
@@ -747,10 +747,10 @@ dd_status enqueue_step(dd_solver **svs, int n, const StepIO &io, const std::vect
         }
         DD_TRY(dd_cg_segments(ctx, gs.data(), cbs.data(), n, o0.cg_rtol, o0.cg_max_iter, s, &it_dev));
     }
-    DD_TRY_CUDA(ctx, cudaEventRecord(ev[1], s));
+    DD_TRY_CUDA(ctx, dd_event_record(ctx, ev[1], s));
     for (int i = 0; i < n; ++i) DD_TRY(fem_recover(ds, svs[i]->g, svs[i]->ops, svs[i]->cb.x, svs[i]->star, svs[i]->y,
                                                    svs[i]->dpc, s));
-    DD_TRY_CUDA(ctx, cudaEventRecord(ev[2], s));
+    DD_TRY_CUDA(ctx, dd_event_record(ctx, ev[2], s));
 
     // ---- one search over the concatenated states ----
     const bool ann = o0.mode == DD_SEARCH_ANN;
@@ -792,7 +792,7 @@ dd_status enqueue_step(dd_solver **svs, int n, const StepIO &io, const std::vect
         }
         off += ng;
     }
-    DD_TRY_CUDA(ctx, cudaEventRecord(ev[3], s));
+    DD_TRY_CUDA(ctx, dd_event_record(ctx, ev[3], s));
     for (int i = 0; i < n; ++i)
         DD_TRY(fem_iter_stats(ctx, svs[i]->nxt, svs[i]->cur, svs[i]->d2, svs[i]->dpc, svs[i]->g.n_gp, svs[i]->g.w,
                               svs[i]->stats, s));
@@ -816,14 +816,19 @@ void finish_step(dd_solver **svs, int n, const double *hs, const int *its, dd_se
                  const std::vector<double> &fds, const DeferredStats *dfr, bool graph, dd_iter_info *infos) {
     dd_ctx *ctx = svs[0]->ctx;
     cudaEvent_t *ev = svs[0]->ev;
-    float t01 = 0, t12 = 0, t23 = 0;
-    cudaEventElapsedTime(&t01, ev[0], ev[1]);
-    cudaEventElapsedTime(&t12, ev[1], ev[2]);
-    cudaEventElapsedTime(&t23, ev[2], ev[3]);
+    // (a failed query must not leave a sticky error for the next call)
+    auto elapsed = [](cudaEvent_t a, cudaEvent_t b) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+            cudaGetLastError();
+            ms = 0.f;
+        }
+        return ms;
+    };
+    const float t01 = elapsed(ev[0], ev[1]), t12 = elapsed(ev[1], ev[2]), t23 = elapsed(ev[2], ev[3]);
     if (dfr) {
         const int64_t N = svs[0]->ds->N;
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, ctx->ev_scan[0], ctx->ev_scan[1]) == cudaSuccess) sst.scan_ms += ms;
+        sst.scan_ms += elapsed(ctx->ev_scan[0], ctx->ev_scan[1]);
         sst.uncertified += (int64_t)(dfr->fb + dfr->ann[2]);
         sst.distances += (int64_t)dfr->fb * N + (int64_t)dfr->ann[0] + (int64_t)dfr->ann[3] + (int64_t)dfr->ann[2] * N;
         sst.points += (int64_t)dfr->ann[0] + (int64_t)dfr->ann[2] * N;

@@ -99,6 +99,12 @@ struct dd_ctx {
     std::vector<uint64_t> last_batch;   // solver ids of the previous batched step
 };
 
+// Record a timing event on s; while a step is being captured the record
+// becomes a node of the graph, so that every replay records it again.
+inline cudaError_t dd_event_record(const dd_ctx *ctx, cudaEvent_t e, cudaStream_t s) {
+    return ctx->capturing ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) : cudaEventRecord(e, s);
+}
+
 // Free the cached batched-step plans that hold solver `id` (all plans if id
 // is 0); they keep device pointers into the solvers' state.
 void dd_plans_drop(dd_ctx *ctx, uint64_t id);

@@ -429,11 +429,11 @@ dd_status dd_search_exact_fp32(dd_dataset *ds, const double *y_dev, int64_t m, i
     DD_TRY_CUDA(ctx, cudaFuncSetAttribute(k_scan_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScanSmem));
     dim3 grid((unsigned)qtiles, (unsigned)splits);
     ctx->launches++;
-    if (st) DD_TRY_CUDA(ctx, cudaEventRecord(ctx->ev_scan[0], s));
+    if (st) DD_TRY_CUDA(ctx, dd_event_record(ctx, ctx->ev_scan[0], s));
     k_scan_fp32<<<grid, kThreads, kScanSmem, s>>>(ds->z32, ds->zn, ds->N, n_tiles, rec, m, splits, tps,
                                                   hdr, cand, certify == 0, ctx->dev_err);
     DD_TRY_CUDA(ctx, cudaGetLastError());
-    if (st) DD_TRY_CUDA(ctx, cudaEventRecord(ctx->ev_scan[1], s));
+    if (st) DD_TRY_CUDA(ctx, dd_event_record(ctx, ctx->ev_scan[1], s));
     if (st) st->distances += m * ds->N;
     DD_TRY(dd_merge_rescore(ds, y_dev, m, splits, kCap, hdr, cand, rec, certify, 1.0, out, st, s));
     if (st && !ctx->defer) {

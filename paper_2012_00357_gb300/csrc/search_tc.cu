@@ -536,9 +536,9 @@ dd_status dd_search_exact_tc(dd_dataset *ds, const double *y_dev, int64_t m, int
     if (epi == 0 && !ctx->capturing && (double)m * (double)ds->N >= 1e9) {
         float best = 1e30f;
         for (int e : {4, 8}) {
-            DD_TRY_CUDA(ctx, cudaEventRecord(ctx->ev_scan[0], s));
+            DD_TRY_CUDA(ctx, dd_event_record(ctx, ctx->ev_scan[0], s));
             DD_TRY(launch_tc_any(ctx, kc, e, grid, ds, n_tiles, qa, rec, m, splits, tps, hdr, cand, s));
-            DD_TRY_CUDA(ctx, cudaEventRecord(ctx->ev_scan[1], s));
+            DD_TRY_CUDA(ctx, dd_event_record(ctx, ctx->ev_scan[1], s));
             DD_TRY_CUDA(ctx, cudaEventSynchronize(ctx->ev_scan[1]));
             float ms = 0.f;
             DD_TRY_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev_scan[0], ctx->ev_scan[1]));
@@ -549,9 +549,9 @@ dd_status dd_search_exact_tc(dd_dataset *ds, const double *y_dev, int64_t m, int
         }
     }
     const int use_epi = epi ? epi : 4;
-    if (st) DD_TRY_CUDA(ctx, cudaEventRecord(ctx->ev_scan[0], s));
+    if (st) DD_TRY_CUDA(ctx, dd_event_record(ctx, ctx->ev_scan[0], s));
     DD_TRY(launch_tc_any(ctx, kc, use_epi, grid, ds, n_tiles, qa, rec, m, splits, tps, hdr, cand, s));
-    if (st) DD_TRY_CUDA(ctx, cudaEventRecord(ctx->ev_scan[1], s));
+    if (st) DD_TRY_CUDA(ctx, dd_event_record(ctx, ctx->ev_scan[1], s));
     if (st) st->distances += m * ds->N;
     DD_TRY(dd_merge_rescore(ds, y_dev, m, splits * (use_epi / 4), kCap, hdr, cand, rec, certify,
                             1.0 / (ds->scale16 * ds->scale16), out, st, s));
