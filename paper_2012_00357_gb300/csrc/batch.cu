@@ -30,27 +30,48 @@ namespace {
 // block stages the tile and a one-node halo of v in shared memory, and every
 // thread applies the 27-point stencil of its node (fem_stencil_table) from
 // there, with the 3x3 blocks of its boundary class.
+//
+// The inner FP32 iterations are preconditioned by one multigrid V-cycle
+// (nested trilinear spaces: the operator of level l is 2^l K of level 0, and
+// restriction is the transpose of trilinear prolongation) with one damped
+// block-Jacobi sweep before and after the coarse correction; the coarsest
+// levels of each solve run inside its first block, in shared memory.
 constexpr int kBThreads = 256;
 constexpr int kTileMax = 16;                 // tile edge bound (nodes)
 constexpr int kHaloMax = 1024;               // (tx + 2)(ty + 2)(tz + 2) bound
 constexpr int kSt32 = 27 * 27 * 12;          // FP32 stencil table (floats)
-constexpr size_t kDynSmem = kSt32 * 4 + (size_t)kHaloMax * 6 * 8;
+constexpr int kCoarseSweeps = 8;             // Jacobi sweeps on the coarsest level
+constexpr size_t kSmemSt = (size_t)kSt32 * 4;
+constexpr size_t kSmemHalo = (size_t)kHaloMax * 6 * 8;
+constexpr size_t kSmemLev = (size_t)kMgBlockNodes * 18 * 4;
+constexpr size_t kSmemDi = 27 * 6 * 4 + 16;
+constexpr size_t kDynSmem = kSmemSt + kSmemHalo + kSmemLev + kSmemDi;
+
+struct Level {
+    int nx, ny, nz;                          // elements
+    int tx, ty, tz, ntx, nty, ntiles;        // tiles (levels run by the whole grid)
+    float *r, *z, *t;                        // vectors [nodes x 6] (grid levels)
+    int soff;                                // shared-memory offset in floats (in-block levels)
+    float h;                                 // 2^level
+};
 
 struct SegCG {
-    MeshDev g;
-    const double *St64, *Minv, *b;
+    const double *St64, *b;
     const float *St32;
     double *x;
-    float *r, *z, *p0, *p1, *q, *d, *Mf;
+    float *r, *z, *p0, *p1, *q, *d;
+    float *zg;                               // result of the in-block cycle
     int blk0, nblk;
-    int tx, ty, tz;                          // tile shape (nodes)
-    int ntx, nty, ntiles;
+    int nlev, glev;
+    float omega;
+    Level lv[kMgMaxLev];
 };
 
 struct BCGArgs {
     const SegCG *seg;
     const int *blk_seg;        // [grid] solve of every block
     int S;
+    int G;                     // largest number of grid levels over the solves
     double *part;              // [2 x grid x 8]
     int *flags;                // [S]: outer activity (written by segment leaders)
     unsigned *bar, *err;
@@ -117,67 +138,111 @@ __device__ int count_flags(const int *flags, int S, double *sh) {
     return r;
 }
 
-// This thread's node in tile `tile` of a solve.
+__device__ __forceinline__ int lnode(const Level &L, int X, int Y, int Z) { return X + (L.nx + 1) * (Y + (L.ny + 1) * Z); }
+
+__device__ __forceinline__ int lclass(const Level &L, int X, int Y, int Z) {
+    const int cx = X == 0 ? 0 : (X == L.nx ? 2 : 1);
+    const int cy = Y == 0 ? 0 : (Y == L.ny ? 2 : 1);
+    const int cz = Z == L.nz ? 2 : 1;
+    return cx + 3 * cy + 9 * cz;
+}
+
+// This thread's place in a tile of level L, and the decomposition of its
+// halo slots h = threadIdx.x + k * kBThreads (packed x | y << 8 | z << 16).
+struct Lane {
+    int lx, ly, lz, hx, hxy, hc, nh;
+    bool ok;
+    int hs[4];
+};
+
+__device__ __forceinline__ Lane lane_of(const Level &L) {
+    Lane n;
+    const int t = threadIdx.x;
+    n.ok = t < L.tx * L.ty * L.tz;
+    n.lx = t % L.tx;
+    n.ly = (t / L.tx) % L.ty;
+    n.lz = t / (L.tx * L.ty);
+    n.hx = L.tx + 2;
+    n.hxy = n.hx * (L.ty + 2);
+    n.hc = (n.lx + 1) + n.hx * (n.ly + 1) + n.hxy * (n.lz + 1);
+    n.nh = n.hxy * (L.tz + 2);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int h = t + k * kBThreads;
+        n.hs[k] = (h % n.hx) | (((h / n.hx) % (L.ty + 2)) << 8) | ((h / n.hxy) << 16);
+    }
+    return n;
+}
+
+// This thread's node in tile `tile` of level L.
 struct TileNode {
     int X0, Y0, Z0;   // tile origin
-    int64_t a;        // node id
+    int a;            // node id
     int cls;          // stencil class
     bool ok;
 };
 
-__device__ __forceinline__ TileNode tile_node(const SegCG &S, int64_t tile, int lx, int ly, int lz, bool lane_ok) {
+__device__ __forceinline__ TileNode tile_node(const Level &L, const Lane &ln, int tile) {
     TileNode n;
-    n.X0 = (int)(tile % S.ntx) * S.tx;
-    n.Y0 = (int)((tile / S.ntx) % S.nty) * S.ty;
-    n.Z0 = 1 + (int)(tile / ((int64_t)S.ntx * S.nty)) * S.tz;
-    const int X = n.X0 + lx, Y = n.Y0 + ly, Z = n.Z0 + lz;
-    n.ok = lane_ok && X <= S.g.nx && Y <= S.g.ny && Z <= S.g.nz;
-    n.a = n.ok ? node_id(S.g, X, Y, Z) : 0;
-    const int cx = X == 0 ? 0 : (X == S.g.nx ? 2 : 1);
-    const int cy = Y == 0 ? 0 : (Y == S.g.ny ? 2 : 1);
-    const int cz = Z == S.g.nz ? 2 : 1;
-    n.cls = cx + 3 * cy + 9 * cz;
+    n.X0 = (tile % L.ntx) * L.tx;
+    n.Y0 = ((tile / L.ntx) % L.nty) * L.ty;
+    n.Z0 = 1 + (tile / (L.ntx * L.nty)) * L.tz;
+    const int X = n.X0 + ln.lx, Y = n.Y0 + ln.ly, Z = n.Z0 + ln.lz;
+    n.ok = ln.ok && X <= L.nx && Y <= L.ny && Z <= L.nz;
+    n.a = n.ok ? lnode(L, X, Y, Z) : 0;
+    n.cls = lclass(L, X, Y, Z);
     return n;
 }
 
 // sv[h] = vz + beta .* vp (vp may be null) at every node h of the tile's
-// halo; nodes outside the box or on the clamped face hold 0.
-__device__ __forceinline__ void stage_f(const SegCG &S, const TileNode &n, const float *vz, const float *vp,
-                                        const float beta[2], float *sv) {
-    const int hx = S.tx + 2, hy = S.ty + 2, nh = hx * hy * (S.tz + 2);
-    for (int h = threadIdx.x; h < nh; h += blockDim.x) {
-        const int X = n.X0 - 1 + h % hx, Y = n.Y0 - 1 + (h / hx) % hy, Z = n.Z0 - 1 + h / (hx * hy);
-        float2 v0 = make_float2(0.f, 0.f), v1 = v0, v2 = v0;
-        if (X >= 0 && Y >= 0 && Z >= 1 && X <= S.g.nx && Y <= S.g.ny && Z <= S.g.nz) {
-            const float2 *pz = reinterpret_cast<const float2 *>(vz + node_id(S.g, X, Y, Z) * 6);
-            v0 = __ldcg(pz);
-            v1 = __ldcg(pz + 1);
-            v2 = __ldcg(pz + 2);
+// halo; nodes outside the box or on the clamped face hold 0.  All loads of a
+// thread are issued before its stores.
+__device__ __forceinline__ void stage_f(const Level &L, const Lane &ln, const TileNode &n, const float *vz,
+                                        const float *vp, const float beta[2], float *sv) {
+    float2 v[4][3];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int h = threadIdx.x + k * kBThreads;
+        const int X = n.X0 - 1 + (ln.hs[k] & 255), Y = n.Y0 - 1 + ((ln.hs[k] >> 8) & 255),
+                  Z = n.Z0 - 1 + (ln.hs[k] >> 16);
+        v[k][0] = v[k][1] = v[k][2] = make_float2(0.f, 0.f);
+        if (h < ln.nh && X >= 0 && Y >= 0 && Z >= 1 && X <= L.nx && Y <= L.ny && Z <= L.nz) {
+            const int a = lnode(L, X, Y, Z);
+            const float2 *pz = reinterpret_cast<const float2 *>(vz + (size_t)a * 6);
+            v[k][0] = __ldcg(pz);
+            v[k][1] = __ldcg(pz + 1);
+            v[k][2] = __ldcg(pz + 2);
             if (vp) {
-                const float2 *pp = reinterpret_cast<const float2 *>(vp + node_id(S.g, X, Y, Z) * 6);
+                const float2 *pp = reinterpret_cast<const float2 *>(vp + (size_t)a * 6);
                 const float2 w0 = __ldcg(pp), w1 = __ldcg(pp + 1), w2 = __ldcg(pp + 2);
-                v0.x = fmaf(beta[0], w0.x, v0.x);
-                v0.y = fmaf(beta[0], w0.y, v0.y);
-                v1.x = fmaf(beta[0], w1.x, v1.x);
-                v1.y = fmaf(beta[1], w1.y, v1.y);
-                v2.x = fmaf(beta[1], w2.x, v2.x);
-                v2.y = fmaf(beta[1], w2.y, v2.y);
+                v[k][0].x = fmaf(beta[0], w0.x, v[k][0].x);
+                v[k][0].y = fmaf(beta[0], w0.y, v[k][0].y);
+                v[k][1].x = fmaf(beta[0], w1.x, v[k][1].x);
+                v[k][1].y = fmaf(beta[1], w1.y, v[k][1].y);
+                v[k][2].x = fmaf(beta[1], w2.x, v[k][2].x);
+                v[k][2].y = fmaf(beta[1], w2.y, v[k][2].y);
             }
         }
-        float2 *o = reinterpret_cast<float2 *>(sv + h * 6);
-        o[0] = v0;
-        o[1] = v1;
-        o[2] = v2;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int h = threadIdx.x + k * kBThreads;
+        if (h < ln.nh) {
+            float2 *o = reinterpret_cast<float2 *>(sv + h * 6);
+            o[0] = v[k][0];
+            o[1] = v[k][1];
+            o[2] = v[k][2];
+        }
     }
 }
 
-__device__ __forceinline__ void stage_d(const SegCG &S, const TileNode &n, const double *vz, double *sv) {
-    const int hx = S.tx + 2, hy = S.ty + 2, nh = hx * hy * (S.tz + 2);
-    for (int h = threadIdx.x; h < nh; h += blockDim.x) {
-        const int X = n.X0 - 1 + h % hx, Y = n.Y0 - 1 + (h / hx) % hy, Z = n.Z0 - 1 + h / (hx * hy);
+__device__ __forceinline__ void stage_d(const Level &L, const Lane &ln, const TileNode &n, const double *vz,
+                                        double *sv) {
+    for (int h = threadIdx.x; h < ln.nh; h += blockDim.x) {
+        const int X = n.X0 - 1 + h % ln.hx, Y = n.Y0 - 1 + (h / ln.hx) % (L.ty + 2), Z = n.Z0 - 1 + h / ln.hxy;
         double2 v0 = make_double2(0.0, 0.0), v1 = v0, v2 = v0;
-        if (X >= 0 && Y >= 0 && Z >= 1 && X <= S.g.nx && Y <= S.g.ny && Z <= S.g.nz) {
-            const double2 *pz = reinterpret_cast<const double2 *>(vz + node_id(S.g, X, Y, Z) * 6);
+        if (X >= 0 && Y >= 0 && Z >= 1 && X <= L.nx && Y <= L.ny && Z <= L.nz) {
+            const double2 *pz = reinterpret_cast<const double2 *>(vz + (size_t)lnode(L, X, Y, Z) * 6);
             v0 = __ldcg(pz);
             v1 = __ldcg(pz + 1);
             v2 = __ldcg(pz + 2);
@@ -189,8 +254,22 @@ __device__ __forceinline__ void stage_d(const SegCG &S, const TileNode &n, const
     }
 }
 
-// (K v) of the node at halo index hc, FP32: table blocks [r0 | r1 | r2 | pad]
-// of 12 floats in shared memory.
+// y += (3x3 block kb) applied to both systems of the node values xv.
+__device__ __forceinline__ void block_apply(const float *Sc, int d, const float *xv, float y[6]) {
+    const float2 *x2 = reinterpret_cast<const float2 *>(xv);
+    const float2 x01 = x2[0], x23 = x2[1], x45 = x2[2];
+    const float4 *kb = reinterpret_cast<const float4 *>(Sc + d * 12);
+    const float4 k0 = kb[0], k1 = kb[1], k2 = kb[2];
+    // rows (k0.x k0.y k0.z), (k0.w k1.x k1.y), (k1.z k1.w k2.x)
+    y[0] = fmaf(k0.x, x01.x, fmaf(k0.y, x01.y, fmaf(k0.z, x23.x, y[0])));
+    y[1] = fmaf(k0.w, x01.x, fmaf(k1.x, x01.y, fmaf(k1.y, x23.x, y[1])));
+    y[2] = fmaf(k1.z, x01.x, fmaf(k1.w, x01.y, fmaf(k2.x, x23.x, y[2])));
+    y[3] = fmaf(k0.x, x23.y, fmaf(k0.y, x45.x, fmaf(k0.z, x45.y, y[3])));
+    y[4] = fmaf(k0.w, x23.y, fmaf(k1.x, x45.x, fmaf(k1.y, x45.y, y[4])));
+    y[5] = fmaf(k1.z, x23.y, fmaf(k1.w, x45.x, fmaf(k2.x, x45.y, y[5])));
+}
+
+// (K v) of the node at halo index hc, FP32 (level-0 table).
 __device__ __forceinline__ void stencil_f(const float *sS, const float *sv, int hc, int hx, int hxy, int cls,
                                           float y[6]) {
     const float *Sc = sS + cls * (27 * 12);
@@ -201,20 +280,8 @@ __device__ __forceinline__ void stencil_f(const float *sS, const float *sv, int 
 #pragma unroll
         for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
-            for (int dx = -1; dx <= 1; ++dx) {
-                const int d = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
-                const float2 *xv = reinterpret_cast<const float2 *>(sv + (hc + dx + dy * hx + dz * hxy) * 6);
-                const float2 x01 = xv[0], x23 = xv[1], x45 = xv[2];
-                const float4 *kb = reinterpret_cast<const float4 *>(Sc + d * 12);
-                const float4 k0 = kb[0], k1 = kb[1], k2 = kb[2];
-                // rows (k0.x k0.y k0.z), (k0.w k1.x k1.y), (k1.z k1.w k2.x)
-                y[0] = fmaf(k0.x, x01.x, fmaf(k0.y, x01.y, fmaf(k0.z, x23.x, y[0])));
-                y[1] = fmaf(k0.w, x01.x, fmaf(k1.x, x01.y, fmaf(k1.y, x23.x, y[1])));
-                y[2] = fmaf(k1.z, x01.x, fmaf(k1.w, x01.y, fmaf(k2.x, x23.x, y[2])));
-                y[3] = fmaf(k0.x, x23.y, fmaf(k0.y, x45.x, fmaf(k0.z, x45.y, y[3])));
-                y[4] = fmaf(k0.w, x23.y, fmaf(k1.x, x45.x, fmaf(k1.y, x45.y, y[4])));
-                y[5] = fmaf(k1.z, x23.y, fmaf(k1.w, x45.x, fmaf(k2.x, x45.y, y[5])));
-            }
+            for (int dx = -1; dx <= 1; ++dx)
+                block_apply(Sc, (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1), sv + (hc + dx + dy * hx + dz * hxy) * 6, y);
 }
 
 // The same in FP64 with the table read through the read-only cache.
@@ -223,7 +290,7 @@ __device__ __forceinline__ void stencil_d(const double *St, const double *sv, in
     const double *Sc = St + cls * (27 * 9);
 #pragma unroll
     for (int k = 0; k < 6; ++k) y[k] = 0.0;
-#pragma unroll
+#pragma unroll 1
     for (int dz = -1; dz <= 1; ++dz)
 #pragma unroll
         for (int dy = -1; dy <= 1; ++dy)
@@ -242,17 +309,16 @@ __device__ __forceinline__ void stencil_d(const double *St, const double *sv, in
             }
 }
 
-// z = M^-1 r with the symmetric 3x3 block packed as (m00 m11 m22 m12 m02 m01).
-__device__ __forceinline__ void precond_f(const float *Mf, const float r[6], float z[6]) {
-    const float2 *m = reinterpret_cast<const float2 *>(Mf);
-    const float2 a = __ldcg(m), b = __ldcg(m + 1), c = __ldcg(m + 2);
-    const float m00 = a.x, m11 = a.y, m22 = b.x, m12 = b.y, m02 = c.x, m01 = c.y;
+// y = s * D^-1 x for both systems, D^-1 of class cls packed (m00 m11 m22 m12 m02 m01).
+__device__ __forceinline__ void dinv_apply(const float *sDi, int cls, float s, const float x[6], float y[6]) {
+    const float *m = sDi + cls * 6;
+    const float m00 = m[0] * s, m11 = m[1] * s, m22 = m[2] * s, m12 = m[3] * s, m02 = m[4] * s, m01 = m[5] * s;
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
-        const float r0 = r[3 * s], r1 = r[3 * s + 1], r2 = r[3 * s + 2];
-        z[3 * s + 0] = fmaf(m00, r0, fmaf(m01, r1, m02 * r2));
-        z[3 * s + 1] = fmaf(m01, r0, fmaf(m11, r1, m12 * r2));
-        z[3 * s + 2] = fmaf(m02, r0, fmaf(m12, r1, m22 * r2));
+    for (int q = 0; q < 2; ++q) {
+        const float r0 = x[3 * q], r1 = x[3 * q + 1], r2 = x[3 * q + 2];
+        y[3 * q + 0] = fmaf(m00, r0, fmaf(m01, r1, m02 * r2));
+        y[3 * q + 1] = fmaf(m01, r0, fmaf(m11, r1, m12 * r2));
+        y[3 * q + 2] = fmaf(m02, r0, fmaf(m12, r1, m22 * r2));
     }
 }
 
@@ -273,80 +339,376 @@ __device__ __forceinline__ float dot3(const float *a, const float *b) {
     return fmaf(a[0], b[0], fmaf(a[1], b[1], a[2] * b[2]));
 }
 
+// Trilinear transfer weights along one axis: fine index i and coarse index I.
+__device__ __forceinline__ float tw(int i, int I) {
+    const int d = i - 2 * I;
+    return d == 0 ? 1.f : ((d == 1 || d == -1) ? 0.5f : 0.f);
+}
+
+// r_C = sum over the fine nodes around 2C of the trilinear weights times t
+// (restriction = transpose of prolongation); fine nodes outside the box or
+// on the clamped face contribute 0.  get(a) reads the 6 values of fine node a.
+template <typename Get>
+__device__ __forceinline__ void restrict_node(const Level &F, int X, int Y, int Z, Get get, float r[6]) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) r[k] = 0.f;
+    for (int dz = -1; dz <= 1; ++dz) {
+        const int z = 2 * Z + dz;
+        if (z < 1 || z > F.nz) continue;
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int y = 2 * Y + dy;
+            if (y < 0 || y > F.ny) continue;
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int x = 2 * X + dx;
+                if (x < 0 || x > F.nx) continue;
+                const float w = (dx ? 0.5f : 1.f) * (dy ? 0.5f : 1.f) * (dz ? 0.5f : 1.f);
+                float v[6];
+                get(lnode(F, x, y, z), v);
+#pragma unroll
+                for (int k = 0; k < 6; ++k) r[k] = fmaf(w, v[k], r[k]);
+            }
+        }
+    }
+}
+
+// e_f = sum over the (up to 8) coarse nodes of fine node (X, Y, Z) of the
+// trilinear weights times the coarse values; coarse nodes on the clamped face
+// hold 0.  get(A) reads the 6 values of coarse node A.
+template <typename Get>
+__device__ __forceinline__ void prolong_node(const Level &Cl, int X, int Y, int Z, Get get, float e[6]) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) e[k] = 0.f;
+    const int I0 = X >> 1, J0 = Y >> 1, K0 = Z >> 1;
+    const int I1 = (X + 1) >> 1, J1 = (Y + 1) >> 1, K1 = (Z + 1) >> 1;
+    for (int K = K0; K <= K1; ++K) {
+        if (K < 1) continue;
+        const float wz = tw(Z, K);
+        for (int J = J0; J <= J1; ++J) {
+            const float wy = wz * tw(Y, J);
+            for (int I = I0; I <= I1; ++I) {
+                const float w = wy * tw(X, I);
+                float v[6];
+                get(lnode(Cl, I, J, K), v);
+#pragma unroll
+                for (int k = 0; k < 6; ++k) e[k] = fmaf(w, v[k], e[k]);
+            }
+        }
+    }
+}
+
+// ---- levels run inside one block, in shared memory ----
+__device__ __forceinline__ int lnodes(const Level &L) { return (L.nx + 1) * (L.ny + 1) * (L.nz + 1); }
+
+// t = r - h K z on an in-block level (shared arrays, all nodes; clamped nodes 0).
+__device__ void blk_residual(const Level &L, const float *sS, const float *r, const float *z, float *t) {
+    const int nn = lnodes(L);
+    for (int a = threadIdx.x; a < nn; a += blockDim.x) {
+        const int X = a % (L.nx + 1), Y = (a / (L.nx + 1)) % (L.ny + 1), Z = a / ((L.nx + 1) * (L.ny + 1));
+        float y[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (Z >= 1) {
+            const float *Sc = sS + lclass(L, X, Y, Z) * (27 * 12);
+            for (int d = 0; d < 27; ++d) {
+                const int x = X + d % 3 - 1, yy = Y + (d / 3) % 3 - 1, zz = Z + d / 9 - 1;
+                if (x < 0 || yy < 0 || zz < 1 || x > L.nx || yy > L.ny || zz > L.nz) continue;
+                block_apply(Sc, d, z + lnode(L, x, yy, zz) * 6, y);
+            }
+#pragma unroll
+            for (int k = 0; k < 6; ++k) y[k] = r[a * 6 + k] - L.h * y[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) t[a * 6 + k] = y[k];
+    }
+}
+
+// z (+)= omega / h D^-1 x on an in-block level.
+__device__ void blk_jacobi(const Level &L, const float *sDi, float om, const float *x, float *z, bool add) {
+    const int nn = lnodes(L);
+    for (int a = threadIdx.x; a < nn; a += blockDim.x) {
+        const int X = a % (L.nx + 1), Y = (a / (L.nx + 1)) % (L.ny + 1), Z = a / ((L.nx + 1) * (L.ny + 1));
+        float y[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (Z >= 1) dinv_apply(sDi, lclass(L, X, Y, Z), om / L.h, x + a * 6, y);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) z[a * 6 + k] = (add ? z[a * 6 + k] : 0.f) + y[k];
+    }
+}
+
+// The V-cycle below level glev - 1, in block 0 of the solve: restrict the
+// residual t of the last grid level, cycle through the in-block levels, and
+// write their correction to S.zg.
+__device__ void inblock_cycle(const SegCG &S, const float *sS, const float *sDi, float *sLev) {
+    const int g = S.glev;
+    const Level &F = S.lv[g - 1];
+    float *r[kMgMaxLev], *z[kMgMaxLev], *t[kMgMaxLev];
+    for (int l = g; l < S.nlev; ++l) {
+        const int n6 = lnodes(S.lv[l]) * 6;
+        r[l] = sLev + S.lv[l].soff;
+        z[l] = r[l] + n6;
+        t[l] = z[l] + n6;
+    }
+    {
+        const Level &L = S.lv[g];
+        const float *tf = F.t;
+        for (int a = threadIdx.x; a < lnodes(L); a += blockDim.x) {
+            const int X = a % (L.nx + 1), Y = (a / (L.nx + 1)) % (L.ny + 1), Z = a / ((L.nx + 1) * (L.ny + 1));
+            float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (Z >= 1) restrict_node(F, X, Y, Z, [&](int b, float *o) { ld6(tf + (size_t)b * 6, o); }, v);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) r[g][a * 6 + k] = v[k];
+        }
+    }
+    __syncthreads();
+    const float om = S.omega;
+    for (int l = g; l < S.nlev - 1; ++l) {              // down
+        const Level &L = S.lv[l], &C = S.lv[l + 1];
+        blk_jacobi(L, sDi, om, r[l], z[l], false);
+        __syncthreads();
+        blk_residual(L, sS, r[l], z[l], t[l]);
+        __syncthreads();
+        const float *tl = t[l];
+        for (int a = threadIdx.x; a < lnodes(C); a += blockDim.x) {
+            const int X = a % (C.nx + 1), Y = (a / (C.nx + 1)) % (C.ny + 1), Z = a / ((C.nx + 1) * (C.ny + 1));
+            float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (Z >= 1)
+                restrict_node(L, X, Y, Z, [&](int b, float *o) {
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) o[k] = tl[b * 6 + k];
+                }, v);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) r[l + 1][a * 6 + k] = v[k];
+        }
+        __syncthreads();
+    }
+    {                                                   // coarsest: Jacobi sweeps from zero
+        const int c = S.nlev - 1;
+        const Level &L = S.lv[c];
+        blk_jacobi(L, sDi, om, r[c], z[c], false);
+        __syncthreads();
+        for (int s2 = 1; s2 < kCoarseSweeps; ++s2) {
+            blk_residual(L, sS, r[c], z[c], t[c]);
+            __syncthreads();
+            blk_jacobi(L, sDi, om, t[c], z[c], true);
+            __syncthreads();
+        }
+    }
+    for (int l = S.nlev - 2; l >= g; --l) {             // up
+        const Level &L = S.lv[l], &C = S.lv[l + 1];
+        const float *zc = z[l + 1];
+        for (int a = threadIdx.x; a < lnodes(L); a += blockDim.x) {
+            const int X = a % (L.nx + 1), Y = (a / (L.nx + 1)) % (L.ny + 1), Z = a / ((L.nx + 1) * (L.ny + 1));
+            if (Z < 1) continue;
+            float e[6];
+            prolong_node(C, X, Y, Z, [&](int b, float *o) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) o[k] = zc[b * 6 + k];
+            }, e);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) z[l][a * 6 + k] += e[k];
+        }
+        __syncthreads();
+        blk_residual(L, sS, r[l], z[l], t[l]);
+        __syncthreads();
+        blk_jacobi(L, sDi, om, t[l], z[l], true);
+        __syncthreads();
+    }
+    const int n6 = lnodes(S.lv[g]) * 6;
+    for (int k = threadIdx.x; k < n6; k += blockDim.x) S.zg[k] = z[g][k];
+}
+
+// ---- grid-level operations (all blocks of the solve, node tiles) ----
+
+// t = r - h K z at grid level l.
+__device__ void grid_residual(const Level &L, int lb, int nblk, const float *sS, float *sv) {
+    const Lane ln = lane_of(L);
+    const float zb[2] = {0.f, 0.f};
+    for (int tile = lb; tile < L.ntiles; tile += nblk) {
+        const TileNode n = tile_node(L, ln, tile);
+        __syncthreads();
+        stage_f(L, ln, n, L.z, nullptr, zb, sv);
+        __syncthreads();
+        if (n.ok) {
+            float kz[6], rv[6];
+            stencil_f(sS, sv, ln.hc, ln.hx, ln.hxy, n.cls, kz);
+            ld6(L.r + (size_t)n.a * 6, rv);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) kz[k] = fmaf(-L.h, kz[k], rv[k]);
+            st6(L.t + (size_t)n.a * 6, kz);
+        }
+    }
+}
+
+// z = t + omega / h D^-1 (r - h K t) at grid level l (t holds z + P e);
+// level 0 also accumulates (r.z, r.r) of both systems.
+__device__ void grid_post_smooth(const Level &L, int lb, int nblk, const float *sS, const float *sDi, float om,
+                                 float *sv, double (&dots)[4]) {
+    const Lane ln = lane_of(L);
+    const float zb[2] = {0.f, 0.f};
+    for (int tile = lb; tile < L.ntiles; tile += nblk) {
+        const TileNode n = tile_node(L, ln, tile);
+        __syncthreads();
+        stage_f(L, ln, n, L.t, nullptr, zb, sv);
+        __syncthreads();
+        if (n.ok) {
+            float kz[6], rv[6], zv[6], dz[6];
+            stencil_f(sS, sv, ln.hc, ln.hx, ln.hxy, n.cls, kz);
+            ld6(L.r + (size_t)n.a * 6, rv);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) kz[k] = fmaf(-L.h, kz[k], rv[k]);
+            dinv_apply(sDi, n.cls, om / L.h, kz, dz);
+            const float *own = sv + ln.hc * 6;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) zv[k] = own[k] + dz[k];
+            st6(L.z + (size_t)n.a * 6, zv);
+            dots[0] += (double)dot3(rv, zv);
+            dots[1] += (double)dot3(rv + 3, zv + 3);
+            dots[2] += (double)dot3(rv, rv);
+            dots[3] += (double)dot3(rv + 3, rv + 3);
+        }
+    }
+}
+
+// Coarse level C = l + 1 run by the grid: r_C = P^T t_l, z_C = omega / h D^-1 r_C.
+__device__ void grid_restrict(const Level &F, const Level &C, int lb, int nblk, const float *sDi, float om) {
+    const Lane ln = lane_of(C);
+    for (int tile = lb; tile < C.ntiles; tile += nblk) {
+        const TileNode n = tile_node(C, ln, tile);
+        if (!n.ok) continue;
+        const int X = n.X0 + ln.lx, Y = n.Y0 + ln.ly, Z = n.Z0 + ln.lz;
+        float rv[6], zv[6];
+        restrict_node(F, X, Y, Z, [&](int b, float *o) { ld6(F.t + (size_t)b * 6, o); }, rv);
+        dinv_apply(sDi, n.cls, om / C.h, rv, zv);
+        st6(C.r + (size_t)n.a * 6, rv);
+        st6(C.z + (size_t)n.a * 6, zv);
+    }
+}
+
+// t_l = z_l + P z_C at grid level l (zc: the coarse correction, all nodes of C).
+__device__ void grid_prolong(const Level &L, const Level &C, const float *zc, int lb, int nblk) {
+    const Lane ln = lane_of(L);
+    for (int tile = lb; tile < L.ntiles; tile += nblk) {
+        const TileNode n = tile_node(L, ln, tile);
+        if (!n.ok) continue;
+        const int X = n.X0 + ln.lx, Y = n.Y0 + ln.ly, Z = n.Z0 + ln.lz;
+        float e[6], zv[6];
+        if (zc) {
+            prolong_node(C, X, Y, Z, [&](int b, float *o) { ld6(zc + (size_t)b * 6, o); }, e);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) e[k] = 0.f;
+        }
+        ld6(L.z + (size_t)n.a * 6, zv);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) zv[k] += e[k];
+        st6(L.t + (size_t)n.a * 6, zv);
+    }
+}
+
+// The rest of one V-cycle after the level-0 pre-smoothing z_0 = omega D^-1 r
+// (done by the caller and followed by a grid barrier): residual and
+// restriction down the grid levels, the in-block cycle, prolongation and
+// post-smoothing back up.  Every block passes the same 4 G - 1 barriers;
+// blocks of a solve that is inactive or has fewer grid levels only wait.
+// The final level-0 post-smoothing writes S.z and this block's (r.z, r.r).
+__device__ bool vcycle_rest(const SegCG &S, int lb, bool act, int G, GridBar &gb, unsigned *err, const float *sS,
+                            const float *sDi, float *sv, float *sLev, double (&dots)[4]) {
+    const float om = S.omega;
+    for (int l = 0; l < G; ++l) {
+        if (act && l < S.glev) grid_residual(S.lv[l], lb, S.nblk, sS, sv);
+        if (!grid_sync(gb, err)) return false;
+        if (act && l + 1 < S.glev) grid_restrict(S.lv[l], S.lv[l + 1], lb, S.nblk, sDi, om);
+        if (act && l + 1 == S.glev && S.glev < S.nlev && lb == 0) inblock_cycle(S, sS, sDi, sLev);
+        if (!grid_sync(gb, err)) return false;
+    }
+    for (int l = G - 1; l >= 0; --l) {
+        if (act && l < S.glev) {
+            const float *zc = l + 1 < S.glev ? S.lv[l + 1].z : (l + 1 < S.nlev ? S.zg : nullptr);
+            grid_prolong(S.lv[l], S.lv[l + 1 < S.nlev ? l + 1 : l], zc, lb, S.nblk);
+        }
+        if (!grid_sync(gb, err)) return false;
+        if (act && l < S.glev) {
+            double dd[4] = {0, 0, 0, 0};
+            grid_post_smooth(S.lv[l], lb, S.nblk, sS, sDi, om, sv, l == 0 ? dots : dd);
+        }
+        if (l > 0 && !grid_sync(gb, err)) return false;
+    }
+    return true;
+}
+
 __global__ void __launch_bounds__(kBThreads, 1) k_cg_batch(BCGArgs A) {
     extern __shared__ __align__(16) unsigned char dsm[];
-    float *sS = reinterpret_cast<float *>(dsm);                 // [kSt32]
-    double *sv64 = reinterpret_cast<double *>(dsm + kSt32 * 4);  // [kHaloMax x 6]; the FP32 halo reuses it
-    float *sv32 = reinterpret_cast<float *>(sv64);
+    float *sS = reinterpret_cast<float *>(dsm);                                  // [kSt32]
+    double *sv64 = reinterpret_cast<double *>(dsm + kSmemSt);                     // [kHaloMax x 6]
+    float *sv32 = reinterpret_cast<float *>(sv64);                               // the FP32 halo reuses it
+    float *sLev = reinterpret_cast<float *>(dsm + kSmemSt + kSmemHalo);           // in-block levels
+    float *sDi = reinterpret_cast<float *>(dsm + kSmemSt + kSmemHalo + kSmemLev); // [27 x 6]
     __shared__ double sh[8 * 32];
     const int sidx = A.blk_seg[blockIdx.x];
-    const SegCG S = A.seg[sidx];
+    const SegCG &S = A.seg[sidx];
     for (int t = threadIdx.x; t < kSt32 / 4; t += blockDim.x)
         reinterpret_cast<float4 *>(sS)[t] = __ldg(reinterpret_cast<const float4 *>(S.St32) + t);
+    __syncthreads();
+    if (threadIdx.x < 27) {   // inverse of the diagonal block of every class, packed symmetric
+        const float *D = sS + (threadIdx.x * 27 + 13) * 12;
+        const float d00 = D[0], d01 = D[1], d02 = D[2], d11 = D[4], d12 = D[5], d22 = D[8];
+        const float c00 = d11 * d22 - d12 * d12, c01 = d02 * d12 - d01 * d22, c02 = d01 * d12 - d02 * d11;
+        const float det = d00 * c00 + d01 * c01 + d02 * c02;
+        const float id = 1.f / det;
+        float *m = sDi + threadIdx.x * 6;
+        m[0] = c00 * id;
+        m[1] = (d00 * d22 - d02 * d02) * id;
+        m[2] = (d00 * d11 - d01 * d01) * id;
+        m[3] = (d01 * d02 - d00 * d12) * id;
+        m[4] = c02 * id;
+        m[5] = c01 * id;
+    }
     __syncthreads();
     const unsigned G = gridDim.x;
     GridBar gbar{A.bar, G, 0u};
     const int lb = blockIdx.x - S.blk0;
     const bool leader = (lb == 0 && threadIdx.x == 0);
-    const bool lane_ok = threadIdx.x < S.tx * S.ty * S.tz;
-    const int lx = threadIdx.x % S.tx, ly = (threadIdx.x / S.tx) % S.ty, lz = threadIdx.x / (S.tx * S.ty);
-    const int hx = S.tx + 2, hxy = hx * (S.ty + 2);
-    const int hc = (lx + 1) + hx * (ly + 1) + hxy * (lz + 1);
-    const double ndof = 3.0 * (S.g.nx + 1) * (double)(S.g.ny + 1) * (double)S.g.nz;
+    const Level L0 = S.lv[0];
+    const Lane ln0 = lane_of(L0);
+    const float om = S.omega;
+    const double ndof = 3.0 * (L0.nx + 1) * (double)(L0.ny + 1) * (double)L0.nz;
     double *partA = A.part, *partB = A.part + (size_t)G * 8;
     int *outer_flag = A.flags;
     int inner_count = 0;
     for (int outer = 0;; ++outer) {
-        // ---- FP64 residual r = b - K x, preconditioned, and the norms ----
-        double v[6] = {0, 0, 0, 0, 0, 0};   // r.z (2), r.r (2), b.b (2)
-        for (int64_t tile = lb; tile < S.ntiles; tile += S.nblk) {
-            const TileNode n = tile_node(S, tile, lx, ly, lz, lane_ok);
+        // ---- FP64 residual r = b - K x and the norms ----
+        double v[4] = {0, 0, 0, 0};   // r.r (2), b.b (2)
+        for (int tile = lb; tile < L0.ntiles; tile += S.nblk) {
+            const TileNode n = tile_node(L0, ln0, tile);
             __syncthreads();
-            stage_d(S, n, S.x, sv64);
+            stage_d(L0, ln0, n, S.x, sv64);
             __syncthreads();
             if (n.ok) {
-                const int64_t a = n.a;
+                const size_t a = n.a;
                 double kx[6];
-                stencil_d(S.St64, sv64, hc, hx, hxy, n.cls, kx);
-                const double *Mi = S.Minv + a * 9;
-                float mf[6] = {(float)Mi[0], (float)Mi[4], (float)Mi[8], (float)Mi[5], (float)Mi[2], (float)Mi[1]};
-                st6(S.Mf + a * 6, mf);
-                float rf[6], zf[6];
+                stencil_d(S.St64, sv64, ln0.hc, ln0.hx, ln0.hxy, n.cls, kx);
+                float rf[6];
 #pragma unroll
                 for (int k = 0; k < 6; ++k) {
                     const double bc = S.b[a * 6 + k];
                     const double r64 = bc - kx[k];
                     rf[k] = (float)r64;
-                    v[2 + k / 3] += r64 * r64;
-                    v[4 + k / 3] += bc * bc;
-                }
-                const float *m = mf;
-#pragma unroll
-                for (int s2 = 0; s2 < 2; ++s2) {
-                    const float r0 = rf[3 * s2], r1 = rf[3 * s2 + 1], r2 = rf[3 * s2 + 2];
-                    zf[3 * s2 + 0] = fmaf(m[0], r0, fmaf(m[5], r1, m[4] * r2));
-                    zf[3 * s2 + 1] = fmaf(m[5], r0, fmaf(m[1], r1, m[3] * r2));
-                    zf[3 * s2 + 2] = fmaf(m[4], r0, fmaf(m[3], r1, m[2] * r2));
+                    v[k / 3] += r64 * r64;
+                    v[2 + k / 3] += bc * bc;
                 }
                 st6(S.r + a * 6, rf);
-                st6(S.z + a * 6, zf);
                 const float zero6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                 st6(S.d + a * 6, zero6);
-#pragma unroll
-                for (int k = 0; k < 6; ++k) v[k / 3] += (double)rf[k] * (double)zf[k];
             }
         }
-        block_sum<6>(v, sh);
+        block_sum<4>(v, sh);
         if (threadIdx.x == 0)
-            for (int k = 0; k < 6; ++k) partB[blockIdx.x * 8 + k] = v[k];
+            for (int k = 0; k < 4; ++k) partB[blockIdx.x * 8 + k] = v[k];
         if (!grid_sync(gbar, A.err)) return;
-        double tot[6];
-        range_total<6>(partB, S.blk0, S.nblk, tot, sh);
-        double rr_true[2], bb[2], rz[2], scale[2], unscale[2];
+        double tot[4];
+        range_total<4>(partB, S.blk0, S.nblk, tot, sh);
+        double rr_true[2], bb[2], scale[2], unscale[2];
         bool conv[2];
         for (int s2 = 0; s2 < 2; ++s2) {
-            rr_true[s2] = tot[2 + s2];
-            bb[s2] = tot[4 + s2];
+            rr_true[s2] = tot[s2];
+            bb[s2] = tot[2 + s2];
             conv[s2] = !(rr_true[s2] > A.rtol2 * bb[s2]) || bb[s2] == 0.0;
             // the inner FP32 iterations run on r scaled by a power of two to an
             // RMS near 1 (exact), so that their products stay far from underflow
@@ -354,36 +716,42 @@ __global__ void __launch_bounds__(kBThreads, 1) k_cg_batch(BCGArgs A) {
             if (rr_true[s2] > 0.0) frexp(sqrt(rr_true[s2] / ndof), &e);
             scale[s2] = ldexp(1.0, -e);
             unscale[s2] = ldexp(1.0, e);
-            rz[s2] = tot[s2] * scale[s2] * scale[s2];
         }
         const bool more = !(conv[0] && conv[1]) && outer < A.max_outer;
-        if (more)
-            for (int64_t tile = lb; tile < S.ntiles; tile += S.nblk) {
-                const TileNode n = tile_node(S, tile, lx, ly, lz, lane_ok);
+        if (more)   // scale r, and the first smoothing step of the preconditioner
+            for (int tile = lb; tile < L0.ntiles; tile += S.nblk) {
+                const TileNode n = tile_node(L0, ln0, tile);
                 if (!n.ok) continue;
                 float rv[6], zv[6];
-                ld6(S.r + n.a * 6, rv);
-                ld6(S.z + n.a * 6, zv);
+                ld6(S.r + (size_t)n.a * 6, rv);
 #pragma unroll
-                for (int k = 0; k < 6; ++k) {
-                    rv[k] *= (float)scale[k / 3];
-                    zv[k] *= (float)scale[k / 3];
-                }
-                st6(S.r + n.a * 6, rv);
-                st6(S.z + n.a * 6, zv);
+                for (int k = 0; k < 6; ++k) rv[k] *= (float)scale[k / 3];
+                st6(S.r + (size_t)n.a * 6, rv);
+                dinv_apply(sDi, n.cls, om, rv, zv);
+                st6(S.z + (size_t)n.a * 6, zv);
             }
         if (leader) outer_flag[sidx] = more ? 1 : 0;
         if (!grid_sync(gbar, A.err)) return;
         if (count_flags(outer_flag, A.S, sh) == 0) {
             for (int s2 = 0; s2 < 2; ++s2)
                 if (bb[s2] == 0.0)
-                    for (int64_t tile = lb; tile < S.ntiles; tile += S.nblk) {
-                        const TileNode n = tile_node(S, tile, lx, ly, lz, lane_ok);
+                    for (int tile = lb; tile < L0.ntiles; tile += S.nblk) {
+                        const TileNode n = tile_node(L0, ln0, tile);
                         if (n.ok)
-                            for (int k = 0; k < 3; ++k) S.x[n.a * 6 + 3 * s2 + k] = 0.0;
+                            for (int k = 0; k < 3; ++k) S.x[(size_t)n.a * 6 + 3 * s2 + k] = 0.0;
                     }
             break;
         }
+        // ---- z = M r, r.z ----
+        double u[4] = {0, 0, 0, 0};
+        if (!vcycle_rest(S, lb, more, A.G, gbar, A.err, sS, sDi, sv32, sLev, u)) return;
+        block_sum<4>(u, sh);
+        if (threadIdx.x == 0)
+            for (int k = 0; k < 4; ++k) partB[blockIdx.x * 8 + k] = u[k];
+        if (!grid_sync(gbar, A.err)) return;
+        double t4[4];
+        range_total<4>(partB, S.blk0, S.nblk, t4, sh);
+        double rz[2] = {t4[0], t4[1]};
         // gain four digits per refinement step, but never solve below a tenth
         // of the final tolerance (in the scaled units of the inner iterations)
         double target[2];
@@ -397,19 +765,19 @@ __global__ void __launch_bounds__(kBThreads, 1) k_cg_batch(BCGArgs A) {
             // ---- p = z + beta p_old, q = K p, p.q ----
             double w[2] = {0, 0};
             if (act) {
-                for (int64_t tile = lb; tile < S.ntiles; tile += S.nblk) {
-                    const TileNode n = tile_node(S, tile, lx, ly, lz, lane_ok);
+                for (int tile = lb; tile < L0.ntiles; tile += S.nblk) {
+                    const TileNode n = tile_node(L0, ln0, tile);
                     __syncthreads();
-                    stage_f(S, n, S.z, it ? pold : nullptr, beta, sv32);
+                    stage_f(L0, ln0, n, S.z, it ? pold : nullptr, beta, sv32);
                     __syncthreads();
                     if (n.ok) {
                         float kq[6], pn[6];
-                        stencil_f(sS, sv32, hc, hx, hxy, n.cls, kq);
-                        const float2 *own = reinterpret_cast<const float2 *>(sv32 + hc * 6);
-                        const float2 p01 = own[0], p23 = own[1], p45 = own[2];
-                        pn[0] = p01.x; pn[1] = p01.y; pn[2] = p23.x; pn[3] = p23.y; pn[4] = p45.x; pn[5] = p45.y;
-                        st6(pnew + n.a * 6, pn);
-                        st6(S.q + n.a * 6, kq);
+                        stencil_f(sS, sv32, ln0.hc, ln0.hx, ln0.hxy, n.cls, kq);
+                        const float *own = sv32 + ln0.hc * 6;
+#pragma unroll
+                        for (int k = 0; k < 6; ++k) pn[k] = own[k];
+                        st6(pnew + (size_t)n.a * 6, pn);
+                        st6(S.q + (size_t)n.a * 6, kq);
                         w[0] += (double)dot3(pn, kq);
                         w[1] += (double)dot3(pn + 3, kq + 3);
                     }
@@ -427,13 +795,12 @@ __global__ void __launch_bounds__(kBThreads, 1) k_cg_batch(BCGArgs A) {
             if (seg_totals<2>(partA, (int)G, S.blk0, S.nblk, pq, sh) == 0.0) break;
             float alpha[2];
             for (int s2 = 0; s2 < 2; ++s2) alpha[s2] = (ic[s2] || !(pq[s2] > 0.0)) ? 0.f : (float)(rz[s2] / pq[s2]);
-            // ---- d += alpha p, r -= alpha q, z = M^-1 r, r.z, r.r ----
-            double u[4] = {0, 0, 0, 0};
+            // ---- d += alpha p, r -= alpha q, first smoothing step z = omega D^-1 r ----
             if (act) {
-                for (int64_t tile = lb; tile < S.ntiles; tile += S.nblk) {
-                    const TileNode n = tile_node(S, tile, lx, ly, lz, lane_ok);
+                for (int tile = lb; tile < L0.ntiles; tile += S.nblk) {
+                    const TileNode n = tile_node(L0, ln0, tile);
                     if (!n.ok) continue;
-                    const int64_t a = n.a;
+                    const size_t a = n.a;
                     float pv[6], dv[6], rv[6], qv[6], zv[6];
                     ld6(pnew + a * 6, pv);
                     ld6(S.d + a * 6, dv);
@@ -444,21 +811,20 @@ __global__ void __launch_bounds__(kBThreads, 1) k_cg_batch(BCGArgs A) {
                         dv[k] = fmaf(alpha[k / 3], pv[k], dv[k]);
                         rv[k] = fmaf(-alpha[k / 3], qv[k], rv[k]);
                     }
-                    precond_f(S.Mf + a * 6, rv, zv);
+                    dinv_apply(sDi, n.cls, om, rv, zv);
                     st6(S.d + a * 6, dv);
                     st6(S.r + a * 6, rv);
                     st6(S.z + a * 6, zv);
-                    u[0] += (double)dot3(rv, zv);
-                    u[1] += (double)dot3(rv + 3, zv + 3);
-                    u[2] += (double)dot3(rv, rv);
-                    u[3] += (double)dot3(rv + 3, rv + 3);
                 }
             }
-            block_sum<4>(u, sh);
-            if (threadIdx.x == 0)
-                for (int k = 0; k < 4; ++k) partB[blockIdx.x * 8 + k] = u[k];
             if (!grid_sync(gbar, A.err)) return;
-            double t4[4];
+            // ---- rest of the V-cycle: z = M r, with r.z and r.r ----
+            double u2[4] = {0, 0, 0, 0};
+            if (!vcycle_rest(S, lb, act, A.G, gbar, A.err, sS, sDi, sv32, sLev, u2)) return;
+            block_sum<4>(u2, sh);
+            if (threadIdx.x == 0)
+                for (int k = 0; k < 4; ++k) partB[blockIdx.x * 8 + k] = u2[k];
+            if (!grid_sync(gbar, A.err)) return;
             range_total<4>(partB, S.blk0, S.nblk, t4, sh);
             for (int s2 = 0; s2 < 2; ++s2) {
                 if (!ic[s2]) {
@@ -475,11 +841,12 @@ __global__ void __launch_bounds__(kBThreads, 1) k_cg_batch(BCGArgs A) {
             pnew = t;
         }
         // ---- x += d (back in the units of x) ----
-        for (int64_t tile = lb; tile < S.ntiles; tile += S.nblk) {
-            const TileNode n = tile_node(S, tile, lx, ly, lz, lane_ok);
+        for (int tile = lb; tile < L0.ntiles; tile += S.nblk) {
+            const TileNode n = tile_node(L0, ln0, tile);
             if (!n.ok) continue;
 #pragma unroll
-            for (int k = 0; k < 6; ++k) S.x[n.a * 6 + k] += (double)S.d[n.a * 6 + k] * unscale[k / 3];
+            for (int k = 0; k < 6; ++k)
+                S.x[(size_t)n.a * 6 + k] += (double)S.d[(size_t)n.a * 6 + k] * unscale[k / 3];
         }
         if (!grid_sync(gbar, A.err)) return;
     }
@@ -498,11 +865,11 @@ __global__ void k_fill_fd(float *p, int64_t n, const float *v) {
 
 }  // namespace
 
-// Tile shape for a solve that gets nblk blocks: fewest estimated cycles for
-// the passes over its tiles (a halo round per 256 staged nodes, the stencil
-// per warp, the per-node update).
-static void pick_tiles(const MeshDev &g, int nblk, SegCG &S) {
-    const int n1[3] = {g.nx + 1, g.ny + 1, g.nz};
+// Tile shape for a level of a solve that gets nblk blocks: fewest estimated
+// cycles for the passes over its tiles (a halo round per 256 staged nodes,
+// the stencil per warp, the per-node update).
+static void pick_tiles(int nx, int ny, int nz, int nblk, Level &L) {
+    const int n1[3] = {nx + 1, ny + 1, nz};
     double best = 1e300;
     for (int tx = 1; tx <= std::min(n1[0], kTileMax); ++tx)
         for (int ty = 1; ty <= std::min(n1[1], kTileMax); ++ty)
@@ -517,12 +884,12 @@ static void pick_tiles(const MeshDev &g, int nblk, SegCG &S) {
                                                       200.0 * ((T + 31) / 32) + 700.0);
                 if (cost < best) {
                     best = cost;
-                    S.tx = tx;
-                    S.ty = ty;
-                    S.tz = tz;
-                    S.ntx = (n1[0] + tx - 1) / tx;
-                    S.nty = (n1[1] + ty - 1) / ty;
-                    S.ntiles = (int)nt;
+                    L.tx = tx;
+                    L.ty = ty;
+                    L.tz = tz;
+                    L.ntx = (n1[0] + tx - 1) / tx;
+                    L.nty = (n1[1] + ty - 1) / ty;
+                    L.ntiles = (int)nt;
                 }
             }
 }
@@ -534,6 +901,7 @@ struct CGTables {
     std::vector<SegCG> seg;
     std::vector<int> blk_seg;
     int n = 0, total = 0;
+    int G = 1;                   // largest number of grid levels
 };
 
 // Where those tables and the launch's scratch live on the device.
@@ -579,13 +947,14 @@ static dd_status cg_tables(dd_ctx *ctx, const MeshDev *const *gs, const CGBuffer
     const int cap = ctx->n_sm;   // one block per SM: fewer barrier arrivals
     if (n > cap) return dd_fail(ctx, DD_ERR_ARG, "more solves than resident CG blocks");
     T.n = n;
+    T.G = 1;
     T.seg.assign(n, SegCG{});
     std::vector<int> nblk(n);
     int total = 0;
     for (int i = 0; i < n; ++i) {
         const int64_t share = std::max<int64_t>(1, (int64_t)((double)cap * (double)gs[i]->n_nodes / (double)nodes));
-        pick_tiles(*gs[i], (int)share, T.seg[i]);
-        nblk[i] = (int)std::min<int64_t>(share, T.seg[i].ntiles);
+        pick_tiles(gs[i]->nx, gs[i]->ny, gs[i]->nz, (int)share, T.seg[i].lv[0]);
+        nblk[i] = (int)std::min<int64_t>(share, T.seg[i].lv[0].ntiles);
         total += nblk[i];
     }
     while (total > cap) {   // trim the largest shares until the grid is co-resident
@@ -601,22 +970,46 @@ static dd_status cg_tables(dd_ctx *ctx, const MeshDev *const *gs, const CGBuffer
         const CGBuffers &cb = *cbs[i];
         const size_t n6 = (size_t)gs[i]->n_nodes * 6;
         SegCG &S = T.seg[i];
-        S.g = *gs[i];
         S.St64 = cb.St64;
         S.St32 = cb.St32;
-        S.Minv = cb.Minv;
         S.b = cb.b;
         S.x = cb.x;
         // the FP64 work arrays hold two FP32 vectors each
         S.r = reinterpret_cast<float *>(cb.r);
         S.d = S.r + n6;
         S.z = reinterpret_cast<float *>(cb.z);
-        S.Mf = S.z + n6;
         S.p0 = reinterpret_cast<float *>(cb.p0);
         S.p1 = reinterpret_cast<float *>(cb.p1);
         S.q = reinterpret_cast<float *>(cb.q);
+        S.zg = cb.mg_zg;
         S.blk0 = b0;
         S.nblk = nblk[i];
+        S.nlev = cb.nlev;
+        S.glev = cb.glev;
+        S.omega = (float)cb.omega;
+        int soff = 0;
+        for (int l = 0; l < cb.nlev; ++l) {
+            Level &L = S.lv[l];
+            L.nx = cb.lnx[l];
+            L.ny = cb.lny[l];
+            L.nz = cb.lnz[l];
+            L.h = (float)(1 << l);
+            if (l > 0 && l < cb.glev) pick_tiles(L.nx, L.ny, L.nz, S.nblk, L);
+            if (l == 0) {
+                L.r = S.r;
+                L.z = S.z;
+                L.t = cb.mg_t0;
+            } else if (l < cb.glev) {
+                L.r = cb.mg_r[l];
+                L.z = cb.mg_z[l];
+                L.t = cb.mg_t[l];
+            } else {
+                L.soff = soff;
+                soff += 18 * (L.nx + 1) * (L.ny + 1) * (L.nz + 1);
+            }
+        }
+        if (soff > kMgBlockNodes * 18) return dd_fail(ctx, DD_ERR_ARG, "multigrid levels exceed the block budget");
+        T.G = std::max(T.G, cb.glev);
         for (int k = 0; k < nblk[i]; ++k) T.blk_seg[b0 + k] = i;
         b0 += nblk[i];
     }
@@ -635,6 +1028,7 @@ static dd_status cg_launch(dd_ctx *ctx, const CGTables &T, const CGDev &D, doubl
     A.seg = D.seg;
     A.blk_seg = D.blk_seg;
     A.S = T.n;
+    A.G = T.G;
     A.part = D.part;
     A.flags = D.flags;
     A.bar = D.bar;

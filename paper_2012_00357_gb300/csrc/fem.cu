@@ -17,6 +17,7 @@
 // fixed-order reductions (deterministic), warm-started from the previous DD
 // iteration's (u, eta).
 #include <cmath>
+#include <vector>
 
 #include "dd_internal.cuh"
 #include "fem.cuh"
@@ -484,6 +485,83 @@ void fem_stencil_table(const double *Ke, double *S) {
             for (int k = 0; k < 9; ++k) S[(c * 27 + d) * 9 + k] = blk[k];
         }
     }
+}
+
+void fem_mg_plan(const MeshDev &g, CGBuffers &cb) {
+    cb.nlev = 1;
+    cb.lnx[0] = g.nx;
+    cb.lny[0] = g.ny;
+    cb.lnz[0] = g.nz;
+    while (cb.nlev < kMgMaxLev) {
+        const int l = cb.nlev - 1;
+        if (cb.lnx[l] % 2 || cb.lny[l] % 2 || cb.lnz[l] % 2) break;
+        cb.lnx[l + 1] = cb.lnx[l] / 2;
+        cb.lny[l + 1] = cb.lny[l] / 2;
+        cb.lnz[l + 1] = cb.lnz[l] / 2;
+        cb.nlev++;
+    }
+    cb.glev = cb.nlev;
+    for (int l = 1; l < cb.nlev; ++l) {
+        int64_t tail = 0;
+        for (int k = l; k < cb.nlev; ++k) tail += (int64_t)(cb.lnx[k] + 1) * (cb.lny[k] + 1) * (cb.lnz[k] + 1);
+        if (tail <= kMgBlockNodes) {
+            cb.glev = l;
+            break;
+        }
+    }
+}
+
+double fem_jacobi_lambda_max(const double *St) {
+    const int n = 6, n1 = n + 1;          // 6^3 elements, clamped at z = 0
+    auto id = [&](int i, int j, int k) { return i + n1 * (j + n1 * k); };
+    const int nn = n1 * n1 * n1;
+    std::vector<double> x(nn * 3, 0.0), y(nn * 3, 0.0);
+    uint64_t st = 0x9E3779B97F4A7C15ull;
+    for (int a = n1 * n1; a < nn; ++a)
+        for (int c = 0; c < 3; ++c) {
+            st = st * 6364136223846793005ull + 1442695040888963407ull;
+            x[a * 3 + c] = (double)(st >> 11) / 9007199254740992.0 - 0.5;
+        }
+    auto cls = [&](int i, int j, int k) {
+        const int cx = i == 0 ? 0 : (i == n ? 2 : 1), cy = j == 0 ? 0 : (j == n ? 2 : 1), cz = k == n ? 2 : 1;
+        return cx + 3 * cy + 9 * cz;
+    };
+    double lam = 0.0;
+    for (int it = 0; it < 120; ++it) {
+        double nx2 = 0.0, ny2 = 0.0;
+        for (int k = 1; k <= n; ++k)
+            for (int j = 0; j <= n; ++j)
+                for (int i = 0; i <= n; ++i) {
+                    const int c = cls(i, j, k);
+                    double kx[3] = {0, 0, 0};
+                    for (int d = 0; d < 27; ++d) {
+                        const int I = i + d % 3 - 1, J = j + (d / 3) % 3 - 1, K = k + d / 9 - 1;
+                        if (I < 0 || J < 0 || K < 1 || I > n || J > n || K > n) continue;
+                        const double *B = St + (c * 27 + d) * 9;
+                        const double *v = &x[id(I, J, K) * 3];
+                        for (int r = 0; r < 3; ++r) kx[r] += B[3 * r] * v[0] + B[3 * r + 1] * v[1] + B[3 * r + 2] * v[2];
+                    }
+                    // solve D y = K x with the node's diagonal block
+                    const double *D = St + (c * 27 + 13) * 9;
+                    const double det = D[0] * (D[4] * D[8] - D[5] * D[7]) - D[1] * (D[3] * D[8] - D[5] * D[6]) +
+                                       D[2] * (D[3] * D[7] - D[4] * D[6]);
+                    const double I9[9] = {(D[4] * D[8] - D[5] * D[7]) / det, (D[2] * D[7] - D[1] * D[8]) / det,
+                                          (D[1] * D[5] - D[2] * D[4]) / det, (D[5] * D[6] - D[3] * D[8]) / det,
+                                          (D[0] * D[8] - D[2] * D[6]) / det, (D[2] * D[3] - D[0] * D[5]) / det,
+                                          (D[3] * D[7] - D[4] * D[6]) / det, (D[1] * D[6] - D[0] * D[7]) / det,
+                                          (D[0] * D[4] - D[1] * D[3]) / det};
+                    double *o = &y[id(i, j, k) * 3];
+                    for (int r = 0; r < 3; ++r) o[r] = I9[3 * r] * kx[0] + I9[3 * r + 1] * kx[1] + I9[3 * r + 2] * kx[2];
+                }
+        for (int a = 0; a < nn * 3; ++a) {
+            nx2 += x[a] * x[a];
+            ny2 += y[a] * y[a];
+        }
+        lam = std::sqrt(ny2 / nx2);
+        const double s = 1.0 / std::sqrt(ny2);
+        for (int a = 0; a < nn * 3; ++a) x[a] = y[a] * s;
+    }
+    return lam;
 }
 
 void fem_traction_force(const MeshDev &g, const dd_load &L, double lx, double ly, double *f) {

@@ -16,10 +16,24 @@ struct ElemOps {
     double dN[8][8][3];
 };
 
+// Geometric multigrid of the constraint projection: level l is the box with
+// the element counts divided by 2^l (while all of them are even).  Levels
+// whose nodes (with all coarser ones) fit kMgBlockNodes run inside one block
+// of their solve, in shared memory; the finer ones run on the whole grid.
+constexpr int kMgMaxLev = 8;
+constexpr int kMgBlockNodes = 1200;
+
 struct CGBuffers {
     const double *Ke, *Minv, *b;
     const double *St64;   // stencil table [27 classes][27 offsets][9] (fem_stencil_table)
     const float *St32;    // the same in FP32, blocks padded to 12 values
+    // multigrid hierarchy (fem_mg_plan)
+    int nlev = 1, glev = 1;                    // levels; levels run by the whole grid
+    int lnx[kMgMaxLev], lny[kMgMaxLev], lnz[kMgMaxLev];
+    float *mg_t0 = nullptr;                    // level-0 scratch [nodes x 6]
+    float *mg_r[kMgMaxLev], *mg_z[kMgMaxLev], *mg_t[kMgMaxLev];   // grid levels 1 .. glev-1
+    float *mg_zg = nullptr;                    // result of the in-block cycle (level glev, all nodes)
+    double omega = 0.5;                        // damped block-Jacobi weight of the smoother
     double *x, *r, *z, *p0, *p1, *q, *part;
     unsigned *bar;
     int *it_out;
@@ -44,6 +58,12 @@ inline MeshDev fem_mesh(const dd_mesh &m) {
 void fem_elem_ops(const MeshDev &g, ElemOps *ops);
 void fem_element_stiffness(const MeshDev &g, const ElemOps &ops, const double *C, double *Ke);
 void fem_stencil_table(const double *Ke, double *S);
+// Levels of the multigrid hierarchy of a box: element counts per level and
+// the number of levels run by the whole grid (fills nlev, glev, lnx, lny, lnz).
+void fem_mg_plan(const MeshDev &g, CGBuffers &cb);
+// Largest eigenvalue of D^-1 K (D: the 3x3 diagonal blocks) by power
+// iteration on a small box with the same elements, from the stencil table.
+double fem_jacobi_lambda_max(const double *St64);
 void fem_traction_force(const MeshDev &g, const dd_load &L, double lx, double ly, double *f);
 
 dd_status fem_gather_star(dd_dataset *ds, const int32_t *idx, int64_t n_gp, double *star, double *ce,

@@ -69,6 +69,18 @@ size_t carve(dd_solver *sv, char *base) {
     cb.Ke = sv->Ke;
     cb.St64 = sv->St64 = bp.take<double>(27 * 27 * 9);
     cb.St32 = sv->St32 = bp.take<float>(27 * 27 * 12);
+    fem_mg_plan(sv->g, cb);
+    cb.mg_t0 = bp.take<float>(nn * 6);
+    for (int l = 1; l < cb.glev; ++l) {
+        const size_t n6 = (size_t)(cb.lnx[l] + 1) * (cb.lny[l] + 1) * (cb.lnz[l] + 1) * 6;
+        cb.mg_r[l] = bp.take<float>(n6);
+        cb.mg_z[l] = bp.take<float>(n6);
+        cb.mg_t[l] = bp.take<float>(n6);
+    }
+    if (cb.glev < cb.nlev) {
+        const int l = cb.glev;
+        cb.mg_zg = bp.take<float>((size_t)(cb.lnx[l] + 1) * (cb.lny[l] + 1) * (cb.lnz[l] + 1) * 6);
+    }
     cb.part = bp.take<double>((size_t)2 * sv->ctx->n_sm * 32 * 8);
     cb.bar = bp.take<unsigned>(16);
     cb.it_out = bp.take<int>(16);
@@ -208,6 +220,7 @@ extern "C" dd_status dd_solver_create(dd_dataset *ds, const dd_mesh *mesh, const
     std::vector<double> St64(27 * 27 * 9);
     std::vector<float> St32(27 * 27 * 12, 0.f);
     fem_stencil_table(Ke.data(), St64.data());
+    sv->cb.omega = 4.0 / (3.0 * fem_jacobi_lambda_max(St64.data()));
     for (int cd = 0; cd < 27 * 27; ++cd)
         for (int k = 0; k < 9; ++k) St32[cd * 12 + k] = (float)St64[cd * 9 + k];
     fem_traction_force(sv->g, *load, mesh->lx, mesh->ly, f.data());
