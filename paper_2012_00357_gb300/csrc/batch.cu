@@ -100,11 +100,13 @@ __device__ void range_total(const double *part, int b0, int nb, double (&tot)[NV
     __syncthreads();
 }
 
-// Slots [0, NV) summed over the blocks [b0, b0 + nb) of this solve, and slot 7
-// (activity) over all G blocks, in one fixed-order pass.  Returns the latter.
+// Slots [0, NV) summed over the blocks [b0, b0 + nb) of this solve, slot 7
+// (activity) summed over all G blocks and slot 6 (multigrid depth) maxed over
+// them, in one fixed-order pass.  Returns the activity; *gmax the depth.
 template <int NV>
-__device__ double seg_totals(const double *part, int G, int b0, int nb, double (&tot)[NV], double *sh) {
+__device__ double seg_totals(const double *part, int G, int b0, int nb, double (&tot)[NV], double *sh, int *gmax) {
     double v[NV + 1];
+    int gm = 0;
 #pragma unroll
     for (int c = 0; c <= NV; ++c) v[c] = 0.0;
     for (int t = threadIdx.x; t < G; t += blockDim.x) {
@@ -112,30 +114,55 @@ __device__ double seg_totals(const double *part, int G, int b0, int nb, double (
 #pragma unroll
             for (int c = 0; c < NV; ++c) v[c] += __ldcg(part + (size_t)t * 8 + c);
         v[NV] += __ldcg(part + (size_t)t * 8 + 7);
+        gm = max(gm, (int)__ldcg(part + (size_t)t * 8 + 6));
     }
+    for (int o = 16; o > 0; o >>= 1) gm = max(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+    __shared__ int s_gm[32];
+    if ((threadIdx.x & 31) == 0) s_gm[threadIdx.x >> 5] = gm;
     block_sum<NV + 1>(v, sh);
     __shared__ double s_tot[8];
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0) {
 #pragma unroll
         for (int c = 0; c <= NV; ++c) s_tot[c] = v[c];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) s_gm[0] = max(s_gm[0], s_gm[w]);
+    }
     __syncthreads();
 #pragma unroll
     for (int c = 0; c < NV; ++c) tot[c] = s_tot[c];
     const double all = s_tot[NV];
+    *gmax = s_gm[0];
     __syncthreads();
     return all;
 }
 
-__device__ int count_flags(const int *flags, int S, double *sh) {
-    double v[1] = {0.0};
-    for (int t = threadIdx.x; t < S; t += blockDim.x) v[0] += (double)__ldcg(flags + t);
-    block_sum<1>(v, sh);
-    __shared__ int s_cnt;
-    if (threadIdx.x == 0) s_cnt = (int)v[0];
+// Sum and maximum of the per-solve flags (written by the solve leaders).
+__device__ void flag_stats(const int *flags, int S, double *sh, int *sum, int *mx) {
+    int c = 0, m = 0;
+    for (int t = threadIdx.x; t < S; t += blockDim.x) {
+        const int f = __ldcg(flags + t);
+        c += f > 0;
+        m = max(m, f);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+        m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    }
+    __shared__ int s_c[32], s_m[32];
+    if ((threadIdx.x & 31) == 0) {
+        s_c[threadIdx.x >> 5] = c;
+        s_m[threadIdx.x >> 5] = m;
+    }
     __syncthreads();
-    int r = s_cnt;
+    if (threadIdx.x == 0)
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            s_c[0] += s_c[w];
+            s_m[0] = max(s_m[0], s_m[w]);
+        }
     __syncthreads();
-    return r;
+    *sum = s_c[0];
+    *mx = s_m[0];
+    __syncthreads();
+    (void)sh;
 }
 
 __device__ __forceinline__ int lnode(const Level &L, int X, int Y, int Z) { return X + (L.nx + 1) * (Y + (L.ny + 1) * Z); }
@@ -339,60 +366,60 @@ __device__ __forceinline__ float dot3(const float *a, const float *b) {
     return fmaf(a[0], b[0], fmaf(a[1], b[1], a[2] * b[2]));
 }
 
-// Trilinear transfer weights along one axis: fine index i and coarse index I.
-__device__ __forceinline__ float tw(int i, int I) {
-    const int d = i - 2 * I;
-    return d == 0 ? 1.f : ((d == 1 || d == -1) ? 0.5f : 0.f);
-}
-
 // r_C = sum over the fine nodes around 2C of the trilinear weights times t
 // (restriction = transpose of prolongation); fine nodes outside the box or
-// on the clamped face contribute 0.  get(a) reads the 6 values of fine node a.
+// on the clamped face contribute 0.  get(a, v) reads the 6 values of fine
+// node a; the loops are unrolled so that all 27 gathers are issued together.
 template <typename Get>
 __device__ __forceinline__ void restrict_node(const Level &F, int X, int Y, int Z, Get get, float r[6]) {
+    float v[27][6];
+#pragma unroll
+    for (int d = 0; d < 27; ++d) {
+        const int x = 2 * X + d % 3 - 1, y = 2 * Y + (d / 3) % 3 - 1, z = 2 * Z + d / 9 - 1;
+        if (x >= 0 && y >= 0 && z >= 1 && x <= F.nx && y <= F.ny && z <= F.nz) {
+            get(lnode(F, x, y, z), v[d]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) v[d][k] = 0.f;
+        }
+    }
 #pragma unroll
     for (int k = 0; k < 6; ++k) r[k] = 0.f;
-    for (int dz = -1; dz <= 1; ++dz) {
-        const int z = 2 * Z + dz;
-        if (z < 1 || z > F.nz) continue;
-        for (int dy = -1; dy <= 1; ++dy) {
-            const int y = 2 * Y + dy;
-            if (y < 0 || y > F.ny) continue;
-            for (int dx = -1; dx <= 1; ++dx) {
-                const int x = 2 * X + dx;
-                if (x < 0 || x > F.nx) continue;
-                const float w = (dx ? 0.5f : 1.f) * (dy ? 0.5f : 1.f) * (dz ? 0.5f : 1.f);
-                float v[6];
-                get(lnode(F, x, y, z), v);
 #pragma unroll
-                for (int k = 0; k < 6; ++k) r[k] = fmaf(w, v[k], r[k]);
-            }
-        }
+    for (int d = 0; d < 27; ++d) {
+        const float w = (d % 3 == 1 ? 1.f : 0.5f) * ((d / 3) % 3 == 1 ? 1.f : 0.5f) * (d / 9 == 1 ? 1.f : 0.5f);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) r[k] = fmaf(w, v[d][k], r[k]);
     }
 }
 
 // e_f = sum over the (up to 8) coarse nodes of fine node (X, Y, Z) of the
 // trilinear weights times the coarse values; coarse nodes on the clamped face
-// hold 0.  get(A) reads the 6 values of coarse node A.
+// hold 0.  get(A, v) reads the 6 values of coarse node A.
 template <typename Get>
 __device__ __forceinline__ void prolong_node(const Level &Cl, int X, int Y, int Z, Get get, float e[6]) {
+    const int I[2] = {X >> 1, (X + 1) >> 1}, J[2] = {Y >> 1, (Y + 1) >> 1}, K[2] = {Z >> 1, (Z + 1) >> 1};
+    const float wx = (X & 1) ? 0.5f : 1.f, wy = (Y & 1) ? 0.5f : 1.f, wz = (Z & 1) ? 0.5f : 1.f;
+    float v[8][6];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) e[k] = 0.f;
-    const int I0 = X >> 1, J0 = Y >> 1, K0 = Z >> 1;
-    const int I1 = (X + 1) >> 1, J1 = (Y + 1) >> 1, K1 = (Z + 1) >> 1;
-    for (int K = K0; K <= K1; ++K) {
-        if (K < 1) continue;
-        const float wz = tw(Z, K);
-        for (int J = J0; J <= J1; ++J) {
-            const float wy = wz * tw(Y, J);
-            for (int I = I0; I <= I1; ++I) {
-                const float w = wy * tw(X, I);
-                float v[6];
-                get(lnode(Cl, I, J, K), v);
+    for (int c = 0; c < 8; ++c) {
+        // odd coordinates take both neighbours, even ones the coincident node once
+        const bool use = (c & 1 ? (X & 1) : 1) && (c & 2 ? (Y & 1) : 1) && (c & 4 ? (Z & 1) : 1) &&
+                         K[(c >> 2) & 1] >= 1;
+        if (use) {
+            get(lnode(Cl, I[c & 1], J[(c >> 1) & 1], K[(c >> 2) & 1]), v[c]);
+        } else {
 #pragma unroll
-                for (int k = 0; k < 6; ++k) e[k] = fmaf(w, v[k], e[k]);
-            }
+            for (int k = 0; k < 6; ++k) v[c][k] = 0.f;
         }
+    }
+    const float w = wx * wy * wz;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        float acc = 0.f;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc += v[c][k];
+        e[k] = w * acc;
     }
 }
 
@@ -407,10 +434,12 @@ __device__ void blk_residual(const Level &L, const float *sS, const float *r, co
         float y[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (Z >= 1) {
             const float *Sc = sS + lclass(L, X, Y, Z) * (27 * 12);
+            const float zero6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
             for (int d = 0; d < 27; ++d) {
                 const int x = X + d % 3 - 1, yy = Y + (d / 3) % 3 - 1, zz = Z + d / 9 - 1;
-                if (x < 0 || yy < 0 || zz < 1 || x > L.nx || yy > L.ny || zz > L.nz) continue;
-                block_apply(Sc, d, z + lnode(L, x, yy, zz) * 6, y);
+                const bool in = x >= 0 && yy >= 0 && zz >= 1 && x <= L.nx && yy <= L.ny && zz <= L.nz;
+                block_apply(Sc, d, in ? z + lnode(L, x, yy, zz) * 6 : zero6, y);
             }
 #pragma unroll
             for (int k = 0; k < 6; ++k) y[k] = r[a * 6 + k] - L.h * y[k];
@@ -671,6 +700,8 @@ __global__ void __launch_bounds__(kBThreads, 1) k_cg_batch(BCGArgs A) {
     const double ndof = 3.0 * (L0.nx + 1) * (double)(L0.ny + 1) * (double)L0.nz;
     double *partA = A.part, *partB = A.part + (size_t)G * 8;
     int *outer_flag = A.flags;
+    // multigrid depth of this solve (0: one level, plain block-Jacobi)
+    const int gdepth = S.nlev > 1 ? S.glev : 0;
     int inner_count = 0;
     for (int outer = 0;; ++outer) {
         // ---- FP64 residual r = b - K x and the norms ----
@@ -718,6 +749,7 @@ __global__ void __launch_bounds__(kBThreads, 1) k_cg_batch(BCGArgs A) {
             unscale[s2] = ldexp(1.0, e);
         }
         const bool more = !(conv[0] && conv[1]) && outer < A.max_outer;
+        double u[4] = {0, 0, 0, 0};   // r.z (2), r.r (2) of the preconditioned residual
         if (more)   // scale r, and the first smoothing step of the preconditioner
             for (int tile = lb; tile < L0.ntiles; tile += S.nblk) {
                 const TileNode n = tile_node(L0, ln0, tile);
@@ -729,10 +761,17 @@ __global__ void __launch_bounds__(kBThreads, 1) k_cg_batch(BCGArgs A) {
                 st6(S.r + (size_t)n.a * 6, rv);
                 dinv_apply(sDi, n.cls, om, rv, zv);
                 st6(S.z + (size_t)n.a * 6, zv);
+                if (gdepth == 0) {
+                    u[0] += (double)dot3(rv, zv);
+                    u[1] += (double)dot3(rv + 3, zv + 3);
+                }
             }
-        if (leader) outer_flag[sidx] = more ? 1 : 0;
+        if (leader) outer_flag[sidx] = more ? 1 + gdepth : 0;
         if (!grid_sync(gbar, A.err)) return;
-        if (count_flags(outer_flag, A.S, sh) == 0) {
+        int n_more = 0, gmax = 0;
+        flag_stats(outer_flag, A.S, sh, &n_more, &gmax);
+        const int Gd = gmax > 0 ? gmax - 1 : 0;   // V-cycle depth of the solves still refining
+        if (n_more == 0) {
             for (int s2 = 0; s2 < 2; ++s2)
                 if (bb[s2] == 0.0)
                     for (int tile = lb; tile < L0.ntiles; tile += S.nblk) {
@@ -743,8 +782,7 @@ __global__ void __launch_bounds__(kBThreads, 1) k_cg_batch(BCGArgs A) {
             break;
         }
         // ---- z = M r, r.z ----
-        double u[4] = {0, 0, 0, 0};
-        if (!vcycle_rest(S, lb, more, A.G, gbar, A.err, sS, sDi, sv32, sLev, u)) return;
+        if (Gd > 0 && !vcycle_rest(S, lb, more && gdepth > 0, Gd, gbar, A.err, sS, sDi, sv32, sLev, u)) return;
         block_sum<4>(u, sh);
         if (threadIdx.x == 0)
             for (int k = 0; k < 4; ++k) partB[blockIdx.x * 8 + k] = u[k];
@@ -787,15 +825,18 @@ __global__ void __launch_bounds__(kBThreads, 1) k_cg_batch(BCGArgs A) {
             if (threadIdx.x == 0) {
                 partA[blockIdx.x * 8 + 0] = w[0];
                 partA[blockIdx.x * 8 + 1] = w[1];
+                partA[blockIdx.x * 8 + 6] = act ? (double)gdepth : 0.0;
                 partA[blockIdx.x * 8 + 7] = act ? 1.0 : 0.0;
             }
             if (!grid_sync(gbar, A.err)) return;
             double pq[2];
+            int Gi = 0;   // V-cycle depth of the solves still iterating
             // lagged stop: every block published its solve's activity before the barrier
-            if (seg_totals<2>(partA, (int)G, S.blk0, S.nblk, pq, sh) == 0.0) break;
+            if (seg_totals<2>(partA, (int)G, S.blk0, S.nblk, pq, sh, &Gi) == 0.0) break;
             float alpha[2];
             for (int s2 = 0; s2 < 2; ++s2) alpha[s2] = (ic[s2] || !(pq[s2] > 0.0)) ? 0.f : (float)(rz[s2] / pq[s2]);
             // ---- d += alpha p, r -= alpha q, first smoothing step z = omega D^-1 r ----
+            double u2[4] = {0, 0, 0, 0};
             if (act) {
                 for (int tile = lb; tile < L0.ntiles; tile += S.nblk) {
                     const TileNode n = tile_node(L0, ln0, tile);
@@ -815,12 +856,19 @@ __global__ void __launch_bounds__(kBThreads, 1) k_cg_batch(BCGArgs A) {
                     st6(S.d + a * 6, dv);
                     st6(S.r + a * 6, rv);
                     st6(S.z + a * 6, zv);
+                    if (gdepth == 0) {
+                        u2[0] += (double)dot3(rv, zv);
+                        u2[1] += (double)dot3(rv + 3, zv + 3);
+                        u2[2] += (double)dot3(rv, rv);
+                        u2[3] += (double)dot3(rv + 3, rv + 3);
+                    }
                 }
             }
-            if (!grid_sync(gbar, A.err)) return;
             // ---- rest of the V-cycle: z = M r, with r.z and r.r ----
-            double u2[4] = {0, 0, 0, 0};
-            if (!vcycle_rest(S, lb, act, A.G, gbar, A.err, sS, sDi, sv32, sLev, u2)) return;
+            if (Gi > 0) {
+                if (!grid_sync(gbar, A.err)) return;
+                if (!vcycle_rest(S, lb, act && gdepth > 0, Gi, gbar, A.err, sS, sDi, sv32, sLev, u2)) return;
+            }
             block_sum<4>(u2, sh);
             if (threadIdx.x == 0)
                 for (int k = 0; k < 4; ++k) partB[blockIdx.x * 8 + k] = u2[k];
