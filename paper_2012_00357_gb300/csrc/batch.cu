@@ -165,9 +165,9 @@ __device__ void flag_stats(const int *flags, int S, double *sh, int *sum, int *m
     (void)sh;
 }
 
-__device__ __forceinline__ int lnode(const Level &L, int X, int Y, int Z) { return X + (L.nx + 1) * (Y + (L.ny + 1) * Z); }
+__device__ __forceinline__ int lnode(const Level L, int X, int Y, int Z) { return X + (L.nx + 1) * (Y + (L.ny + 1) * Z); }
 
-__device__ __forceinline__ int lclass(const Level &L, int X, int Y, int Z) {
+__device__ __forceinline__ int lclass(const Level L, int X, int Y, int Z) {
     const int cx = X == 0 ? 0 : (X == L.nx ? 2 : 1);
     const int cy = Y == 0 ? 0 : (Y == L.ny ? 2 : 1);
     const int cz = Z == L.nz ? 2 : 1;
@@ -182,7 +182,7 @@ struct Lane {
     int hs[4];
 };
 
-__device__ __forceinline__ Lane lane_of(const Level &L) {
+__device__ __forceinline__ Lane lane_of(const Level L) {
     Lane n;
     const int t = threadIdx.x;
     n.ok = t < L.tx * L.ty * L.tz;
@@ -209,7 +209,7 @@ struct TileNode {
     bool ok;
 };
 
-__device__ __forceinline__ TileNode tile_node(const Level &L, const Lane &ln, int tile) {
+__device__ __forceinline__ TileNode tile_node(const Level L, const Lane &ln, int tile) {
     TileNode n;
     n.X0 = (tile % L.ntx) * L.tx;
     n.Y0 = ((tile / L.ntx) % L.nty) * L.ty;
@@ -224,7 +224,7 @@ __device__ __forceinline__ TileNode tile_node(const Level &L, const Lane &ln, in
 // sv[h] = vz + beta .* vp (vp may be null) at every node h of the tile's
 // halo; nodes outside the box or on the clamped face hold 0.  All loads of a
 // thread are issued before its stores.
-__device__ __forceinline__ void stage_f(const Level &L, const Lane &ln, const TileNode &n, const float *vz,
+__device__ __forceinline__ void stage_f(const Level L, const Lane &ln, const TileNode &n, const float *vz,
                                         const float *vp, const float beta[2], float *sv) {
     float2 v[4][3];
 #pragma unroll
@@ -263,7 +263,7 @@ __device__ __forceinline__ void stage_f(const Level &L, const Lane &ln, const Ti
     }
 }
 
-__device__ __forceinline__ void stage_d(const Level &L, const Lane &ln, const TileNode &n, const double *vz,
+__device__ __forceinline__ void stage_d(const Level L, const Lane &ln, const TileNode &n, const double *vz,
                                         double *sv) {
     for (int h = threadIdx.x; h < ln.nh; h += blockDim.x) {
         const int X = n.X0 - 1 + h % ln.hx, Y = n.Y0 - 1 + (h / ln.hx) % (L.ty + 2), Z = n.Z0 - 1 + h / ln.hxy;
@@ -371,25 +371,29 @@ __device__ __forceinline__ float dot3(const float *a, const float *b) {
 // on the clamped face contribute 0.  get(a, v) reads the 6 values of fine
 // node a; the loops are unrolled so that all 27 gathers are issued together.
 template <typename Get>
-__device__ __forceinline__ void restrict_node(const Level &F, int X, int Y, int Z, Get get, float r[6]) {
-    float v[27][6];
-#pragma unroll
-    for (int d = 0; d < 27; ++d) {
-        const int x = 2 * X + d % 3 - 1, y = 2 * Y + (d / 3) % 3 - 1, z = 2 * Z + d / 9 - 1;
-        if (x >= 0 && y >= 0 && z >= 1 && x <= F.nx && y <= F.ny && z <= F.nz) {
-            get(lnode(F, x, y, z), v[d]);
-        } else {
-#pragma unroll
-            for (int k = 0; k < 6; ++k) v[d][k] = 0.f;
-        }
-    }
+__device__ __forceinline__ void restrict_node(const Level F, int X, int Y, int Z, Get get, float r[6]) {
 #pragma unroll
     for (int k = 0; k < 6; ++k) r[k] = 0.f;
 #pragma unroll
-    for (int d = 0; d < 27; ++d) {
-        const float w = (d % 3 == 1 ? 1.f : 0.5f) * ((d / 3) % 3 == 1 ? 1.f : 0.5f) * (d / 9 == 1 ? 1.f : 0.5f);
+    for (int pz = 0; pz < 3; ++pz) {   // one plane of 9 fine nodes per round of gathers
+        const int z = 2 * Z + pz - 1;
+        float v[9][6];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) r[k] = fmaf(w, v[d][k], r[k]);
+        for (int d = 0; d < 9; ++d) {
+            const int x = 2 * X + d % 3 - 1, y = 2 * Y + d / 3 - 1;
+            if (x >= 0 && y >= 0 && z >= 1 && x <= F.nx && y <= F.ny && z <= F.nz) {
+                get(lnode(F, x, y, z), v[d]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) v[d][k] = 0.f;
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < 9; ++d) {
+            const float w = (d % 3 == 1 ? 1.f : 0.5f) * (d / 3 == 1 ? 1.f : 0.5f) * (pz == 1 ? 1.f : 0.5f);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) r[k] = fmaf(w, v[d][k], r[k]);
+        }
     }
 }
 
@@ -397,7 +401,7 @@ __device__ __forceinline__ void restrict_node(const Level &F, int X, int Y, int 
 // trilinear weights times the coarse values; coarse nodes on the clamped face
 // hold 0.  get(A, v) reads the 6 values of coarse node A.
 template <typename Get>
-__device__ __forceinline__ void prolong_node(const Level &Cl, int X, int Y, int Z, Get get, float e[6]) {
+__device__ __forceinline__ void prolong_node(const Level Cl, int X, int Y, int Z, Get get, float e[6]) {
     const int I[2] = {X >> 1, (X + 1) >> 1}, J[2] = {Y >> 1, (Y + 1) >> 1}, K[2] = {Z >> 1, (Z + 1) >> 1};
     const float wx = (X & 1) ? 0.5f : 1.f, wy = (Y & 1) ? 0.5f : 1.f, wz = (Z & 1) ? 0.5f : 1.f;
     float v[8][6];
@@ -424,10 +428,10 @@ __device__ __forceinline__ void prolong_node(const Level &Cl, int X, int Y, int 
 }
 
 // ---- levels run inside one block, in shared memory ----
-__device__ __forceinline__ int lnodes(const Level &L) { return (L.nx + 1) * (L.ny + 1) * (L.nz + 1); }
+__device__ __forceinline__ int lnodes(const Level L) { return (L.nx + 1) * (L.ny + 1) * (L.nz + 1); }
 
 // t = r - h K z on an in-block level (shared arrays, all nodes; clamped nodes 0).
-__device__ void blk_residual(const Level &L, const float *sS, const float *r, const float *z, float *t) {
+__device__ void blk_residual(const Level L, const float *sS, const float *r, const float *z, float *t) {
     const int nn = lnodes(L);
     for (int a = threadIdx.x; a < nn; a += blockDim.x) {
         const int X = a % (L.nx + 1), Y = (a / (L.nx + 1)) % (L.ny + 1), Z = a / ((L.nx + 1) * (L.ny + 1));
@@ -450,7 +454,7 @@ __device__ void blk_residual(const Level &L, const float *sS, const float *r, co
 }
 
 // z (+)= omega / h D^-1 x on an in-block level.
-__device__ void blk_jacobi(const Level &L, const float *sDi, float om, const float *x, float *z, bool add) {
+__device__ void blk_jacobi(const Level L, const float *sDi, float om, const float *x, float *z, bool add) {
     const int nn = lnodes(L);
     for (int a = threadIdx.x; a < nn; a += blockDim.x) {
         const int X = a % (L.nx + 1), Y = (a / (L.nx + 1)) % (L.ny + 1), Z = a / ((L.nx + 1) * (L.ny + 1));
@@ -466,7 +470,7 @@ __device__ void blk_jacobi(const Level &L, const float *sDi, float om, const flo
 // write their correction to S.zg.
 __device__ void inblock_cycle(const SegCG &S, const float *sS, const float *sDi, float *sLev) {
     const int g = S.glev;
-    const Level &F = S.lv[g - 1];
+    const Level F = S.lv[g - 1];
     float *r[kMgMaxLev], *z[kMgMaxLev], *t[kMgMaxLev];
     for (int l = g; l < S.nlev; ++l) {
         const int n6 = lnodes(S.lv[l]) * 6;
@@ -475,7 +479,7 @@ __device__ void inblock_cycle(const SegCG &S, const float *sS, const float *sDi,
         t[l] = z[l] + n6;
     }
     {
-        const Level &L = S.lv[g];
+        const Level L = S.lv[g];
         const float *tf = F.t;
         for (int a = threadIdx.x; a < lnodes(L); a += blockDim.x) {
             const int X = a % (L.nx + 1), Y = (a / (L.nx + 1)) % (L.ny + 1), Z = a / ((L.nx + 1) * (L.ny + 1));
@@ -488,7 +492,7 @@ __device__ void inblock_cycle(const SegCG &S, const float *sS, const float *sDi,
     __syncthreads();
     const float om = S.omega;
     for (int l = g; l < S.nlev - 1; ++l) {              // down
-        const Level &L = S.lv[l], &C = S.lv[l + 1];
+        const Level L = S.lv[l], C = S.lv[l + 1];
         blk_jacobi(L, sDi, om, r[l], z[l], false);
         __syncthreads();
         blk_residual(L, sS, r[l], z[l], t[l]);
@@ -509,7 +513,7 @@ __device__ void inblock_cycle(const SegCG &S, const float *sS, const float *sDi,
     }
     {                                                   // coarsest: Jacobi sweeps from zero
         const int c = S.nlev - 1;
-        const Level &L = S.lv[c];
+        const Level L = S.lv[c];
         blk_jacobi(L, sDi, om, r[c], z[c], false);
         __syncthreads();
         for (int s2 = 1; s2 < kCoarseSweeps; ++s2) {
@@ -520,7 +524,7 @@ __device__ void inblock_cycle(const SegCG &S, const float *sS, const float *sDi,
         }
     }
     for (int l = S.nlev - 2; l >= g; --l) {             // up
-        const Level &L = S.lv[l], &C = S.lv[l + 1];
+        const Level L = S.lv[l], C = S.lv[l + 1];
         const float *zc = z[l + 1];
         for (int a = threadIdx.x; a < lnodes(L); a += blockDim.x) {
             const int X = a % (L.nx + 1), Y = (a / (L.nx + 1)) % (L.ny + 1), Z = a / ((L.nx + 1) * (L.ny + 1));
@@ -546,7 +550,7 @@ __device__ void inblock_cycle(const SegCG &S, const float *sS, const float *sDi,
 // ---- grid-level operations (all blocks of the solve, node tiles) ----
 
 // t = r - h K z at grid level l.
-__device__ void grid_residual(const Level &L, int lb, int nblk, const float *sS, float *sv) {
+__device__ void grid_residual(const Level L, int lb, int nblk, const float *sS, float *sv) {
     const Lane ln = lane_of(L);
     const float zb[2] = {0.f, 0.f};
     for (int tile = lb; tile < L.ntiles; tile += nblk) {
@@ -567,7 +571,7 @@ __device__ void grid_residual(const Level &L, int lb, int nblk, const float *sS,
 
 // z = t + omega / h D^-1 (r - h K t) at grid level l (t holds z + P e);
 // level 0 also accumulates (r.z, r.r) of both systems.
-__device__ void grid_post_smooth(const Level &L, int lb, int nblk, const float *sS, const float *sDi, float om,
+__device__ void grid_post_smooth(const Level L, int lb, int nblk, const float *sS, const float *sDi, float om,
                                  float *sv, double (&dots)[4]) {
     const Lane ln = lane_of(L);
     const float zb[2] = {0.f, 0.f};
@@ -596,7 +600,7 @@ __device__ void grid_post_smooth(const Level &L, int lb, int nblk, const float *
 }
 
 // Coarse level C = l + 1 run by the grid: r_C = P^T t_l, z_C = omega / h D^-1 r_C.
-__device__ void grid_restrict(const Level &F, const Level &C, int lb, int nblk, const float *sDi, float om) {
+__device__ void grid_restrict(const Level F, const Level C, int lb, int nblk, const float *sDi, float om) {
     const Lane ln = lane_of(C);
     for (int tile = lb; tile < C.ntiles; tile += nblk) {
         const TileNode n = tile_node(C, ln, tile);
@@ -611,7 +615,7 @@ __device__ void grid_restrict(const Level &F, const Level &C, int lb, int nblk, 
 }
 
 // t_l = z_l + P z_C at grid level l (zc: the coarse correction, all nodes of C).
-__device__ void grid_prolong(const Level &L, const Level &C, const float *zc, int lb, int nblk) {
+__device__ void grid_prolong(const Level L, const Level C, const float *zc, int lb, int nblk) {
     const Lane ln = lane_of(L);
     for (int tile = lb; tile < L.ntiles; tile += nblk) {
         const TileNode n = tile_node(L, ln, tile);
@@ -640,22 +644,24 @@ __device__ void grid_prolong(const Level &L, const Level &C, const float *zc, in
 __device__ bool vcycle_rest(const SegCG &S, int lb, bool act, int G, GridBar &gb, unsigned *err, const float *sS,
                             const float *sDi, float *sv, float *sLev, double (&dots)[4]) {
     const float om = S.omega;
+    const int glev = S.glev, nlev = S.nlev, nblk = S.nblk;
+    const float *const zg = S.zg;
     for (int l = 0; l < G; ++l) {
-        if (act && l < S.glev) grid_residual(S.lv[l], lb, S.nblk, sS, sv);
+        if (act && l < glev) grid_residual(S.lv[l], lb, nblk, sS, sv);
         if (!grid_sync(gb, err)) return false;
-        if (act && l + 1 < S.glev) grid_restrict(S.lv[l], S.lv[l + 1], lb, S.nblk, sDi, om);
-        if (act && l + 1 == S.glev && S.glev < S.nlev && lb == 0) inblock_cycle(S, sS, sDi, sLev);
+        if (act && l + 1 < glev) grid_restrict(S.lv[l], S.lv[l + 1], lb, nblk, sDi, om);
+        if (act && l + 1 == glev && glev < nlev && lb == 0) inblock_cycle(S, sS, sDi, sLev);
         if (!grid_sync(gb, err)) return false;
     }
     for (int l = G - 1; l >= 0; --l) {
-        if (act && l < S.glev) {
-            const float *zc = l + 1 < S.glev ? S.lv[l + 1].z : (l + 1 < S.nlev ? S.zg : nullptr);
-            grid_prolong(S.lv[l], S.lv[l + 1 < S.nlev ? l + 1 : l], zc, lb, S.nblk);
+        if (act && l < glev) {
+            const float *zc = l + 1 < glev ? S.lv[l + 1].z : (l + 1 < nlev ? zg : nullptr);
+            grid_prolong(S.lv[l], S.lv[l + 1 < nlev ? l + 1 : l], zc, lb, nblk);
         }
         if (!grid_sync(gb, err)) return false;
-        if (act && l < S.glev) {
+        if (act && l < glev) {
             double dd[4] = {0, 0, 0, 0};
-            grid_post_smooth(S.lv[l], lb, S.nblk, sS, sDi, om, sv, l == 0 ? dots : dd);
+            grid_post_smooth(S.lv[l], lb, nblk, sS, sDi, om, sv, l == 0 ? dots : dd);
         }
         if (l > 0 && !grid_sync(gb, err)) return false;
     }
@@ -697,6 +703,10 @@ __global__ void __launch_bounds__(kBThreads, 1) k_cg_batch(BCGArgs A) {
     const Level L0 = S.lv[0];
     const Lane ln0 = lane_of(L0);
     const float om = S.omega;
+    const int nblk = S.nblk, blk0 = S.blk0;
+    float *const Sr = S.r, *const Sz = S.z, *const Sd = S.d, *const Sq = S.q;
+    double *const Sx = S.x;
+    const double *const Sb = S.b, *const St64 = S.St64;
     const double ndof = 3.0 * (L0.nx + 1) * (double)(L0.ny + 1) * (double)L0.nz;
     double *partA = A.part, *partB = A.part + (size_t)G * 8;
     int *outer_flag = A.flags;
@@ -706,27 +716,27 @@ __global__ void __launch_bounds__(kBThreads, 1) k_cg_batch(BCGArgs A) {
     for (int outer = 0;; ++outer) {
         // ---- FP64 residual r = b - K x and the norms ----
         double v[4] = {0, 0, 0, 0};   // r.r (2), b.b (2)
-        for (int tile = lb; tile < L0.ntiles; tile += S.nblk) {
+        for (int tile = lb; tile < L0.ntiles; tile += nblk) {
             const TileNode n = tile_node(L0, ln0, tile);
             __syncthreads();
-            stage_d(L0, ln0, n, S.x, sv64);
+            stage_d(L0, ln0, n, Sx, sv64);
             __syncthreads();
             if (n.ok) {
                 const size_t a = n.a;
                 double kx[6];
-                stencil_d(S.St64, sv64, ln0.hc, ln0.hx, ln0.hxy, n.cls, kx);
+                stencil_d(St64, sv64, ln0.hc, ln0.hx, ln0.hxy, n.cls, kx);
                 float rf[6];
 #pragma unroll
                 for (int k = 0; k < 6; ++k) {
-                    const double bc = S.b[a * 6 + k];
+                    const double bc = Sb[a * 6 + k];
                     const double r64 = bc - kx[k];
                     rf[k] = (float)r64;
                     v[k / 3] += r64 * r64;
                     v[2 + k / 3] += bc * bc;
                 }
-                st6(S.r + a * 6, rf);
+                st6(Sr + a * 6, rf);
                 const float zero6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                st6(S.d + a * 6, zero6);
+                st6(Sd + a * 6, zero6);
             }
         }
         block_sum<4>(v, sh);
@@ -734,7 +744,7 @@ __global__ void __launch_bounds__(kBThreads, 1) k_cg_batch(BCGArgs A) {
             for (int k = 0; k < 4; ++k) partB[blockIdx.x * 8 + k] = v[k];
         if (!grid_sync(gbar, A.err)) return;
         double tot[4];
-        range_total<4>(partB, S.blk0, S.nblk, tot, sh);
+        range_total<4>(partB, blk0, nblk, tot, sh);
         double rr_true[2], bb[2], scale[2], unscale[2];
         bool conv[2];
         for (int s2 = 0; s2 < 2; ++s2) {
@@ -751,16 +761,16 @@ __global__ void __launch_bounds__(kBThreads, 1) k_cg_batch(BCGArgs A) {
         const bool more = !(conv[0] && conv[1]) && outer < A.max_outer;
         double u[4] = {0, 0, 0, 0};   // r.z (2), r.r (2) of the preconditioned residual
         if (more)   // scale r, and the first smoothing step of the preconditioner
-            for (int tile = lb; tile < L0.ntiles; tile += S.nblk) {
+            for (int tile = lb; tile < L0.ntiles; tile += nblk) {
                 const TileNode n = tile_node(L0, ln0, tile);
                 if (!n.ok) continue;
                 float rv[6], zv[6];
-                ld6(S.r + (size_t)n.a * 6, rv);
+                ld6(Sr + (size_t)n.a * 6, rv);
 #pragma unroll
                 for (int k = 0; k < 6; ++k) rv[k] *= (float)scale[k / 3];
-                st6(S.r + (size_t)n.a * 6, rv);
+                st6(Sr + (size_t)n.a * 6, rv);
                 dinv_apply(sDi, n.cls, om, rv, zv);
-                st6(S.z + (size_t)n.a * 6, zv);
+                st6(Sz + (size_t)n.a * 6, zv);
                 if (gdepth == 0) {
                     u[0] += (double)dot3(rv, zv);
                     u[1] += (double)dot3(rv + 3, zv + 3);
@@ -774,10 +784,10 @@ __global__ void __launch_bounds__(kBThreads, 1) k_cg_batch(BCGArgs A) {
         if (n_more == 0) {
             for (int s2 = 0; s2 < 2; ++s2)
                 if (bb[s2] == 0.0)
-                    for (int tile = lb; tile < L0.ntiles; tile += S.nblk) {
+                    for (int tile = lb; tile < L0.ntiles; tile += nblk) {
                         const TileNode n = tile_node(L0, ln0, tile);
                         if (n.ok)
-                            for (int k = 0; k < 3; ++k) S.x[(size_t)n.a * 6 + 3 * s2 + k] = 0.0;
+                            for (int k = 0; k < 3; ++k) Sx[(size_t)n.a * 6 + 3 * s2 + k] = 0.0;
                     }
             break;
         }
@@ -788,7 +798,7 @@ __global__ void __launch_bounds__(kBThreads, 1) k_cg_batch(BCGArgs A) {
             for (int k = 0; k < 4; ++k) partB[blockIdx.x * 8 + k] = u[k];
         if (!grid_sync(gbar, A.err)) return;
         double t4[4];
-        range_total<4>(partB, S.blk0, S.nblk, t4, sh);
+        range_total<4>(partB, blk0, nblk, t4, sh);
         double rz[2] = {t4[0], t4[1]};
         // gain four digits per refinement step, but never solve below a tenth
         // of the final tolerance (in the scaled units of the inner iterations)
@@ -803,10 +813,10 @@ __global__ void __launch_bounds__(kBThreads, 1) k_cg_batch(BCGArgs A) {
             // ---- p = z + beta p_old, q = K p, p.q ----
             double w[2] = {0, 0};
             if (act) {
-                for (int tile = lb; tile < L0.ntiles; tile += S.nblk) {
+                for (int tile = lb; tile < L0.ntiles; tile += nblk) {
                     const TileNode n = tile_node(L0, ln0, tile);
                     __syncthreads();
-                    stage_f(L0, ln0, n, S.z, it ? pold : nullptr, beta, sv32);
+                    stage_f(L0, ln0, n, Sz, it ? pold : nullptr, beta, sv32);
                     __syncthreads();
                     if (n.ok) {
                         float kq[6], pn[6];
@@ -815,7 +825,7 @@ __global__ void __launch_bounds__(kBThreads, 1) k_cg_batch(BCGArgs A) {
 #pragma unroll
                         for (int k = 0; k < 6; ++k) pn[k] = own[k];
                         st6(pnew + (size_t)n.a * 6, pn);
-                        st6(S.q + (size_t)n.a * 6, kq);
+                        st6(Sq + (size_t)n.a * 6, kq);
                         w[0] += (double)dot3(pn, kq);
                         w[1] += (double)dot3(pn + 3, kq + 3);
                     }
@@ -832,30 +842,30 @@ __global__ void __launch_bounds__(kBThreads, 1) k_cg_batch(BCGArgs A) {
             double pq[2];
             int Gi = 0;   // V-cycle depth of the solves still iterating
             // lagged stop: every block published its solve's activity before the barrier
-            if (seg_totals<2>(partA, (int)G, S.blk0, S.nblk, pq, sh, &Gi) == 0.0) break;
+            if (seg_totals<2>(partA, (int)G, blk0, nblk, pq, sh, &Gi) == 0.0) break;
             float alpha[2];
             for (int s2 = 0; s2 < 2; ++s2) alpha[s2] = (ic[s2] || !(pq[s2] > 0.0)) ? 0.f : (float)(rz[s2] / pq[s2]);
             // ---- d += alpha p, r -= alpha q, first smoothing step z = omega D^-1 r ----
             double u2[4] = {0, 0, 0, 0};
             if (act) {
-                for (int tile = lb; tile < L0.ntiles; tile += S.nblk) {
+                for (int tile = lb; tile < L0.ntiles; tile += nblk) {
                     const TileNode n = tile_node(L0, ln0, tile);
                     if (!n.ok) continue;
                     const size_t a = n.a;
                     float pv[6], dv[6], rv[6], qv[6], zv[6];
                     ld6(pnew + a * 6, pv);
-                    ld6(S.d + a * 6, dv);
-                    ld6(S.r + a * 6, rv);
-                    ld6(S.q + a * 6, qv);
+                    ld6(Sd + a * 6, dv);
+                    ld6(Sr + a * 6, rv);
+                    ld6(Sq + a * 6, qv);
 #pragma unroll
                     for (int k = 0; k < 6; ++k) {
                         dv[k] = fmaf(alpha[k / 3], pv[k], dv[k]);
                         rv[k] = fmaf(-alpha[k / 3], qv[k], rv[k]);
                     }
                     dinv_apply(sDi, n.cls, om, rv, zv);
-                    st6(S.d + a * 6, dv);
-                    st6(S.r + a * 6, rv);
-                    st6(S.z + a * 6, zv);
+                    st6(Sd + a * 6, dv);
+                    st6(Sr + a * 6, rv);
+                    st6(Sz + a * 6, zv);
                     if (gdepth == 0) {
                         u2[0] += (double)dot3(rv, zv);
                         u2[1] += (double)dot3(rv + 3, zv + 3);
@@ -873,7 +883,7 @@ __global__ void __launch_bounds__(kBThreads, 1) k_cg_batch(BCGArgs A) {
             if (threadIdx.x == 0)
                 for (int k = 0; k < 4; ++k) partB[blockIdx.x * 8 + k] = u2[k];
             if (!grid_sync(gbar, A.err)) return;
-            range_total<4>(partB, S.blk0, S.nblk, t4, sh);
+            range_total<4>(partB, blk0, nblk, t4, sh);
             for (int s2 = 0; s2 < 2; ++s2) {
                 if (!ic[s2]) {
                     beta[s2] = (rz[s2] != 0.0) ? (float)(t4[s2] / rz[s2]) : 0.f;
@@ -889,12 +899,12 @@ __global__ void __launch_bounds__(kBThreads, 1) k_cg_batch(BCGArgs A) {
             pnew = t;
         }
         // ---- x += d (back in the units of x) ----
-        for (int tile = lb; tile < L0.ntiles; tile += S.nblk) {
+        for (int tile = lb; tile < L0.ntiles; tile += nblk) {
             const TileNode n = tile_node(L0, ln0, tile);
             if (!n.ok) continue;
 #pragma unroll
             for (int k = 0; k < 6; ++k)
-                S.x[(size_t)n.a * 6 + k] += (double)S.d[(size_t)n.a * 6 + k] * unscale[k / 3];
+                Sx[(size_t)n.a * 6 + k] += (double)Sd[(size_t)n.a * 6 + k] * unscale[k / 3];
         }
         if (!grid_sync(gbar, A.err)) return;
     }
