@@ -422,7 +422,10 @@ def run_serve(args, world, rank, local):
         "serve": {"p50_ms": float(np.percentile(lat_s, 50)), "p99_ms": float(np.percentile(lat_s, 99)),
                   "mean_ms": float(np.mean(lat_s)), "solves_per_s": n_req / makespan, "makespan_s": makespan,
                   "lambda_per_s": rate, "max_active": int(st.max_active), "batched_steps": int(st.steps),
-                  "mean_iterations": float(np.mean(iters))},
+                  "mean_iterations": float(np.mean(iters)),
+                  "step_ms": {"busy": st.busy_ms / max(1, st.steps), "cg": st.cg_ms / max(1, st.steps),
+                              "search": st.search_ms / max(1, st.steps), "other": st.other_ms / max(1, st.steps)},
+                  "graph_steps": int(st.graph_steps)},
         "gpu_launches": int(P.dd_launch_count(ctx)),
         "clocks": clk.summary(),
     }

@@ -373,6 +373,9 @@ typedef struct dd_server_opts {
 typedef struct dd_server_stats {
     int64_t submitted, completed, active, pending, steps, max_active;
     double busy_ms;           /* host time spent in batched steps */
+    double cg_ms, search_ms, other_ms;   /* device time of those steps by phase:
+                                            P_C solves, P_D search, the rest */
+    int64_t graph_steps;      /* steps replayed as a CUDA graph */
 } dd_server_stats;
 
 /* Start a worker thread that serves DD solves on ds.  From then on the worker

@@ -82,7 +82,8 @@ class dd_server_opts(ctypes.Structure):
 
 class dd_server_stats(ctypes.Structure):
     _fields_ = [("submitted", c_int64), ("completed", c_int64), ("active", c_int64), ("pending", c_int64),
-                ("steps", c_int64), ("max_active", c_int64), ("busy_ms", c_double)]
+                ("steps", c_int64), ("max_active", c_int64), ("busy_ms", c_double), ("cg_ms", c_double),
+                ("search_ms", c_double), ("other_ms", c_double), ("graph_steps", c_int64)]
 
 
 class dd_result(ctypes.Structure):

@@ -32,10 +32,12 @@ namespace {
 // there, with the 3x3 blocks of its boundary class.
 //
 // The inner FP32 iterations are preconditioned by one multigrid V-cycle
-// (nested trilinear spaces: the operator of level l is 2^l K of level 0, and
-// restriction is the transpose of trilinear prolongation) with one damped
-// block-Jacobi sweep before and after the coarse correction; the coarsest
-// levels of each solve run inside its first block, in shared memory.
+// (trilinear spaces with the element size doubled per level, so that the
+// operator of level l is 2^l K of level 0; restriction is the transpose of
+// trilinear prolongation) with one damped block-Jacobi sweep before and after
+// the coarse correction; the smallest levels of each solve run inside its
+// first block, in shared memory.  A solve whose mesh cannot coarsen uses
+// block-Jacobi alone.
 constexpr int kBThreads = 256;
 constexpr int kTileMax = 16;                 // tile edge bound (nodes)
 constexpr int kHaloMax = 1024;               // (tx + 2)(ty + 2)(tz + 2) bound

@@ -16,6 +16,7 @@
 // runs as one cooperative persistent kernel with bounded grid barriers and
 // fixed-order reductions (deterministic), warm-started from the previous DD
 // iteration's (u, eta).
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -494,10 +495,10 @@ void fem_mg_plan(const MeshDev &g, CGBuffers &cb) {
     cb.lnz[0] = g.nz;
     while (cb.nlev < kMgMaxLev) {
         const int l = cb.nlev - 1;
-        if (cb.lnx[l] % 2 || cb.lny[l] % 2 || cb.lnz[l] % 2) break;
-        cb.lnx[l + 1] = cb.lnx[l] / 2;
-        cb.lny[l + 1] = cb.lny[l] / 2;
-        cb.lnz[l + 1] = cb.lnz[l] / 2;
+        if (std::min(cb.lnx[l], std::min(cb.lny[l], cb.lnz[l])) < 2) break;
+        cb.lnx[l + 1] = (cb.lnx[l] + 1) / 2;
+        cb.lny[l + 1] = (cb.lny[l] + 1) / 2;
+        cb.lnz[l + 1] = (cb.lnz[l] + 1) / 2;
         cb.nlev++;
     }
     cb.glev = cb.nlev;

@@ -16,12 +16,16 @@ struct ElemOps {
     double dN[8][8][3];
 };
 
-// Geometric multigrid of the constraint projection: level l is the box with
-// the element counts divided by 2^l (while all of them are even).  Levels
-// whose nodes (with all coarser ones) fit kMgBlockNodes run inside one block
-// of their solve, in shared memory; the finer ones run on the whole grid.
+// Geometric multigrid of the constraint projection: level l + 1 halves the
+// element counts of level l (rounding up) and doubles the element size, while
+// every count is at least 2.  For even counts the coarse space is nested and
+// its stiffness is exactly the Galerkin product; an odd count gives a coarse
+// box one fine layer longer (not nested: the coarse operator is the
+// rediscretised one, and the V-cycle stays symmetric positive definite).
+// Levels whose nodes (with all coarser ones) fit kMgBlockNodes run inside one
+// block of their solve, in shared memory; the finer ones on the whole grid.
 constexpr int kMgMaxLev = 8;
-constexpr int kMgBlockNodes = 1200;
+constexpr int kMgBlockNodes = 200;
 
 struct CGBuffers {
     const double *Ke, *Minv, *b;

@@ -135,12 +135,19 @@ static void worker_loop(dd_server *S) {
         if (S->active.empty()) continue;
         std::vector<dd_solver *> svs;
         for (auto &a : S->active) svs.push_back(a.sv);
+        std::vector<dd_iter_info> infos(svs.size());
         const double t0 = now_ms();
-        dd_status st = dd_solvers_step(svs.data(), (int)svs.size(), nullptr);
+        dd_status st = dd_solvers_step(svs.data(), (int)svs.size(), infos.data());
         {
             std::lock_guard<std::mutex> lk(S->mu);
             S->stats.steps++;
             S->stats.busy_ms += now_ms() - t0;
+            if (st == DD_OK) {   // the batch's phases are shared by all its solves
+                S->stats.cg_ms += infos[0].cg_ms;
+                S->stats.search_ms += infos[0].search_ms;
+                S->stats.other_ms += infos[0].other_ms;
+                S->stats.graph_steps += infos[0].graph;
+            }
             S->stats.max_active = std::max<int64_t>(S->stats.max_active, (int64_t)svs.size());
         }
         std::vector<Active> keep;
