@@ -35,17 +35,16 @@ namespace {
 // (trilinear spaces with the element size doubled per level, so that the
 // operator of level l is 2^l K of level 0; restriction is the transpose of
 // trilinear prolongation) with one damped block-Jacobi sweep before and after
-// the coarse correction; the smallest levels of each solve run inside its
-// first block, in shared memory.  A solve whose mesh cannot coarsen uses
-// block-Jacobi alone.
+// the coarse correction; the coarsest level is solved exactly with a dense
+// inverse by the first block of each solve.  A solve whose mesh cannot
+// coarsen uses block-Jacobi alone.
 constexpr int kBThreads = 256;
 constexpr int kTileMax = 16;                 // tile edge bound (nodes)
 constexpr int kHaloMax = 1024;               // (tx + 2)(ty + 2)(tz + 2) bound
 constexpr int kSt32 = 27 * 27 * 12;          // FP32 stencil table (floats)
-constexpr int kCoarseSweeps = 8;             // Jacobi sweeps on the coarsest level
 constexpr size_t kSmemSt = (size_t)kSt32 * 4;
 constexpr size_t kSmemHalo = (size_t)kHaloMax * 6 * 8;
-constexpr size_t kSmemLev = (size_t)kMgBlockNodes * 18 * 4;
+constexpr size_t kSmemLev = (size_t)(kMgDirectDofs / 3 + 1) * 6 * 4;
 constexpr size_t kSmemDi = 27 * 6 * 4 + 16;
 constexpr size_t kDynSmem = kSmemSt + kSmemHalo + kSmemLev + kSmemDi;
 
@@ -53,7 +52,6 @@ struct Level {
     int nx, ny, nz;                          // elements
     int tx, ty, tz, ntx, nty, ntiles;        // tiles (levels run by the whole grid)
     float *r, *z, *t;                        // vectors [nodes x 6] (grid levels)
-    int soff;                                // shared-memory offset in floats (in-block levels)
     float h;                                 // 2^level
 };
 
@@ -62,7 +60,9 @@ struct SegCG {
     const float *St32;
     double *x;
     float *r, *z, *p0, *p1, *q, *d;
-    float *zg;                               // result of the in-block cycle
+    float *zg;                               // solution of the coarsest level (all its nodes)
+    const float *inv;                        // dense inverse of the coarsest level's K
+    int ndof;                                // its free DOFs
     int blk0, nblk;
     int nlev, glev;
     float omega;
@@ -429,124 +429,42 @@ __device__ __forceinline__ void prolong_node(const Level Cl, int X, int Y, int Z
     }
 }
 
-// ---- levels run inside one block, in shared memory ----
-__device__ __forceinline__ int lnodes(const Level L) { return (L.nx + 1) * (L.ny + 1) * (L.nz + 1); }
-
-// t = r - h K z on an in-block level (shared arrays, all nodes; clamped nodes 0).
-__device__ void blk_residual(const Level L, const float *sS, const float *r, const float *z, float *t) {
-    const int nn = lnodes(L);
-    for (int a = threadIdx.x; a < nn; a += blockDim.x) {
-        const int X = a % (L.nx + 1), Y = (a / (L.nx + 1)) % (L.ny + 1), Z = a / ((L.nx + 1) * (L.ny + 1));
-        float y[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (Z >= 1) {
-            const float *Sc = sS + lclass(L, X, Y, Z) * (27 * 12);
-            const float zero6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int d = 0; d < 27; ++d) {
-                const int x = X + d % 3 - 1, yy = Y + (d / 3) % 3 - 1, zz = Z + d / 9 - 1;
-                const bool in = x >= 0 && yy >= 0 && zz >= 1 && x <= L.nx && yy <= L.ny && zz <= L.nz;
-                block_apply(Sc, d, in ? z + lnode(L, x, yy, zz) * 6 : zero6, y);
-            }
-#pragma unroll
-            for (int k = 0; k < 6; ++k) y[k] = r[a * 6 + k] - L.h * y[k];
-        }
-#pragma unroll
-        for (int k = 0; k < 6; ++k) t[a * 6 + k] = y[k];
-    }
-}
-
-// z (+)= omega / h D^-1 x on an in-block level.
-__device__ void blk_jacobi(const Level L, const float *sDi, float om, const float *x, float *z, bool add) {
-    const int nn = lnodes(L);
-    for (int a = threadIdx.x; a < nn; a += blockDim.x) {
-        const int X = a % (L.nx + 1), Y = (a / (L.nx + 1)) % (L.ny + 1), Z = a / ((L.nx + 1) * (L.ny + 1));
-        float y[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (Z >= 1) dinv_apply(sDi, lclass(L, X, Y, Z), om / L.h, x + a * 6, y);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) z[a * 6 + k] = (add ? z[a * 6 + k] : 0.f) + y[k];
-    }
-}
-
-// The V-cycle below level glev - 1, in block 0 of the solve: restrict the
-// residual t of the last grid level, cycle through the in-block levels, and
-// write their correction to S.zg.
-__device__ void inblock_cycle(const SegCG &S, const float *sS, const float *sDi, float *sLev) {
+// ---- the coarsest level, solved exactly by block 0 of the solve ----
+// Restrict the residual t of the last grid level to the free nodes of the
+// coarsest level (shared memory), apply its dense inverse to both systems
+// and write the coarse solution of all its nodes to S.zg.
+__device__ void coarse_direct(const SegCG &S, float *sr) {
     const int g = S.glev;
-    const Level F = S.lv[g - 1];
-    float *r[kMgMaxLev], *z[kMgMaxLev], *t[kMgMaxLev];
-    for (int l = g; l < S.nlev; ++l) {
-        const int n6 = lnodes(S.lv[l]) * 6;
-        r[l] = sLev + S.lv[l].soff;
-        z[l] = r[l] + n6;
-        t[l] = z[l] + n6;
-    }
-    {
-        const Level L = S.lv[g];
-        const float *tf = F.t;
-        for (int a = threadIdx.x; a < lnodes(L); a += blockDim.x) {
-            const int X = a % (L.nx + 1), Y = (a / (L.nx + 1)) % (L.ny + 1), Z = a / ((L.nx + 1) * (L.ny + 1));
-            float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            if (Z >= 1) restrict_node(F, X, Y, Z, [&](int b, float *o) { ld6(tf + (size_t)b * 6, o); }, v);
+    const Level F = S.lv[g - 1], Cl = S.lv[g];
+    const int plane = (Cl.nx + 1) * (Cl.ny + 1), nfree = plane * Cl.nz, n = S.ndof;
+    const float *tf = F.t;
+    for (int f = threadIdx.x; f < nfree; f += blockDim.x) {
+        const int a = plane + f;
+        const int X = a % (Cl.nx + 1), Y = (a / (Cl.nx + 1)) % (Cl.ny + 1), Z = a / plane;
+        float v[6];
+        restrict_node(F, X, Y, Z, [&](int b, float *o) { ld6(tf + (size_t)b * 6, o); }, v);
 #pragma unroll
-            for (int k = 0; k < 6; ++k) r[g][a * 6 + k] = v[k];
-        }
+        for (int k = 0; k < 6; ++k) sr[f * 6 + k] = v[k];
     }
     __syncthreads();
-    const float om = S.omega;
-    for (int l = g; l < S.nlev - 1; ++l) {              // down
-        const Level L = S.lv[l], C = S.lv[l + 1];
-        blk_jacobi(L, sDi, om, r[l], z[l], false);
-        __syncthreads();
-        blk_residual(L, sS, r[l], z[l], t[l]);
-        __syncthreads();
-        const float *tl = t[l];
-        for (int a = threadIdx.x; a < lnodes(C); a += blockDim.x) {
-            const int X = a % (C.nx + 1), Y = (a / (C.nx + 1)) % (C.ny + 1), Z = a / ((C.nx + 1) * (C.ny + 1));
-            float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            if (Z >= 1)
-                restrict_node(L, X, Y, Z, [&](int b, float *o) {
+    const float *inv = S.inv;
+    float *zg = S.zg;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {   // K^-1 is symmetric: row i read as column i
+        float a0 = 0.f, a1 = 0.f;
+        for (int fn = 0; fn < nfree; ++fn) {
+            const float *rj = sr + fn * 6;
 #pragma unroll
-                    for (int k = 0; k < 6; ++k) o[k] = tl[b * 6 + k];
-                }, v);
-#pragma unroll
-            for (int k = 0; k < 6; ++k) r[l + 1][a * 6 + k] = v[k];
+            for (int c = 0; c < 3; ++c) {
+                const float A = __ldg(inv + (size_t)(3 * fn + c) * n + i);
+                a0 = fmaf(A, rj[c], a0);
+                a1 = fmaf(A, rj[3 + c], a1);
+            }
         }
-        __syncthreads();
+        const int fi = i / 3, ci = i % 3;
+        zg[(size_t)(plane + fi) * 6 + ci] = a0;
+        zg[(size_t)(plane + fi) * 6 + 3 + ci] = a1;
     }
-    {                                                   // coarsest: Jacobi sweeps from zero
-        const int c = S.nlev - 1;
-        const Level L = S.lv[c];
-        blk_jacobi(L, sDi, om, r[c], z[c], false);
-        __syncthreads();
-        for (int s2 = 1; s2 < kCoarseSweeps; ++s2) {
-            blk_residual(L, sS, r[c], z[c], t[c]);
-            __syncthreads();
-            blk_jacobi(L, sDi, om, t[c], z[c], true);
-            __syncthreads();
-        }
-    }
-    for (int l = S.nlev - 2; l >= g; --l) {             // up
-        const Level L = S.lv[l], C = S.lv[l + 1];
-        const float *zc = z[l + 1];
-        for (int a = threadIdx.x; a < lnodes(L); a += blockDim.x) {
-            const int X = a % (L.nx + 1), Y = (a / (L.nx + 1)) % (L.ny + 1), Z = a / ((L.nx + 1) * (L.ny + 1));
-            if (Z < 1) continue;
-            float e[6];
-            prolong_node(C, X, Y, Z, [&](int b, float *o) {
-#pragma unroll
-                for (int k = 0; k < 6; ++k) o[k] = zc[b * 6 + k];
-            }, e);
-#pragma unroll
-            for (int k = 0; k < 6; ++k) z[l][a * 6 + k] += e[k];
-        }
-        __syncthreads();
-        blk_residual(L, sS, r[l], z[l], t[l]);
-        __syncthreads();
-        blk_jacobi(L, sDi, om, t[l], z[l], true);
-        __syncthreads();
-    }
-    const int n6 = lnodes(S.lv[g]) * 6;
-    for (int k = threadIdx.x; k < n6; k += blockDim.x) S.zg[k] = z[g][k];
+    for (int k = threadIdx.x; k < plane * 6; k += blockDim.x) zg[k] = 0.f;
 }
 
 // ---- grid-level operations (all blocks of the solve, node tiles) ----
@@ -639,7 +557,7 @@ __device__ void grid_prolong(const Level L, const Level C, const float *zc, int 
 
 // The rest of one V-cycle after the level-0 pre-smoothing z_0 = omega D^-1 r
 // (done by the caller and followed by a grid barrier): residual and
-// restriction down the grid levels, the in-block cycle, prolongation and
+// restriction down the grid levels, the exact coarse solve, prolongation and
 // post-smoothing back up.  Every block passes the same 4 G - 1 barriers;
 // blocks of a solve that is inactive or has fewer grid levels only wait.
 // The final level-0 post-smoothing writes S.z and this block's (r.z, r.r).
@@ -652,7 +570,7 @@ __device__ bool vcycle_rest(const SegCG &S, int lb, bool act, int G, GridBar &gb
         if (act && l < glev) grid_residual(S.lv[l], lb, nblk, sS, sv);
         if (!grid_sync(gb, err)) return false;
         if (act && l + 1 < glev) grid_restrict(S.lv[l], S.lv[l + 1], lb, nblk, sDi, om);
-        if (act && l + 1 == glev && glev < nlev && lb == 0) inblock_cycle(S, sS, sDi, sLev);
+        if (act && l + 1 == glev && glev < nlev && lb == 0) coarse_direct(S, sLev);
         if (!grid_sync(gb, err)) return false;
     }
     for (int l = G - 1; l >= 0; --l) {
@@ -675,7 +593,7 @@ __global__ void __launch_bounds__(kBThreads, 1) k_cg_batch(BCGArgs A) {
     float *sS = reinterpret_cast<float *>(dsm);                                  // [kSt32]
     double *sv64 = reinterpret_cast<double *>(dsm + kSmemSt);                     // [kHaloMax x 6]
     float *sv32 = reinterpret_cast<float *>(sv64);                               // the FP32 halo reuses it
-    float *sLev = reinterpret_cast<float *>(dsm + kSmemSt + kSmemHalo);           // in-block levels
+    float *sLev = reinterpret_cast<float *>(dsm + kSmemSt + kSmemHalo);           // coarse residual
     float *sDi = reinterpret_cast<float *>(dsm + kSmemSt + kSmemHalo + kSmemLev); // [27 x 6]
     __shared__ double sh[8 * 32];
     const int sidx = A.blk_seg[blockIdx.x];
@@ -1042,12 +960,13 @@ static dd_status cg_tables(dd_ctx *ctx, const MeshDev *const *gs, const CGBuffer
         S.p1 = reinterpret_cast<float *>(cb.p1);
         S.q = reinterpret_cast<float *>(cb.q);
         S.zg = cb.mg_zg;
+        S.inv = cb.mg_inv;
+        S.ndof = cb.mg_ndof;
         S.blk0 = b0;
         S.nblk = nblk[i];
         S.nlev = cb.nlev;
         S.glev = cb.glev;
         S.omega = (float)cb.omega;
-        int soff = 0;
         for (int l = 0; l < cb.nlev; ++l) {
             Level &L = S.lv[l];
             L.nx = cb.lnx[l];
@@ -1063,12 +982,10 @@ static dd_status cg_tables(dd_ctx *ctx, const MeshDev *const *gs, const CGBuffer
                 L.r = cb.mg_r[l];
                 L.z = cb.mg_z[l];
                 L.t = cb.mg_t[l];
-            } else {
-                L.soff = soff;
-                soff += 18 * (L.nx + 1) * (L.ny + 1) * (L.nz + 1);
             }
         }
-        if (soff > kMgBlockNodes * 18) return dd_fail(ctx, DD_ERR_ARG, "multigrid levels exceed the block budget");
+        if (cb.glev < cb.nlev && cb.mg_ndof > kMgDirectDofs)
+            return dd_fail(ctx, DD_ERR_ARG, "coarsest multigrid level exceeds the direct-solve size");
         T.G = std::max(T.G, cb.glev);
         for (int k = 0; k < nblk[i]; ++k) T.blk_seg[b0 + k] = i;
         b0 += nblk[i];

@@ -502,14 +502,68 @@ void fem_mg_plan(const MeshDev &g, CGBuffers &cb) {
         cb.nlev++;
     }
     cb.glev = cb.nlev;
+    cb.mg_ndof = 0;
     for (int l = 1; l < cb.nlev; ++l) {
-        int64_t tail = 0;
-        for (int k = l; k < cb.nlev; ++k) tail += (int64_t)(cb.lnx[k] + 1) * (cb.lny[k] + 1) * (cb.lnz[k] + 1);
-        if (tail <= kMgBlockNodes) {
+        const int64_t dofs = 3 * (int64_t)(cb.lnx[l] + 1) * (cb.lny[l] + 1) * cb.lnz[l];
+        if (dofs <= kMgDirectDofs) {   // coarsest level: solved exactly
+            cb.nlev = l + 1;
             cb.glev = l;
+            cb.mg_ndof = (int)dofs;
             break;
         }
     }
+}
+
+void fem_mg_coarse_inverse(const CGBuffers &cb, const double *St, std::vector<float> &inv) {
+    const int c = cb.glev, nx = cb.lnx[c], ny = cb.lny[c], nz = cb.lnz[c], n = cb.mg_ndof;
+    const int plane = (nx + 1) * (ny + 1);
+    const double h = (double)(1 << c);
+    std::vector<double> K((size_t)n * n, 0.0);
+    for (int Z = 1; Z <= nz; ++Z)
+        for (int Y = 0; Y <= ny; ++Y)
+            for (int X = 0; X <= nx; ++X) {
+                const int cx = X == 0 ? 0 : (X == nx ? 2 : 1), cy = Y == 0 ? 0 : (Y == ny ? 2 : 1), cz = Z == nz ? 2 : 1;
+                const int cls = cx + 3 * cy + 9 * cz;
+                const int fa = X + (nx + 1) * (Y + (ny + 1) * Z) - plane;
+                for (int d = 0; d < 27; ++d) {
+                    const int x = X + d % 3 - 1, y = Y + (d / 3) % 3 - 1, z = Z + d / 9 - 1;
+                    if (x < 0 || y < 0 || z < 1 || x > nx || y > ny || z > nz) continue;
+                    const int fb = x + (nx + 1) * (y + (ny + 1) * z) - plane;
+                    const double *B = St + (cls * 27 + d) * 9;
+                    for (int r = 0; r < 3; ++r)
+                        for (int k = 0; k < 3; ++k) K[(size_t)(3 * fa + r) * n + 3 * fb + k] = h * B[3 * r + k];
+                }
+            }
+    // Cholesky K = L L^T, then K^-1 = L^-T L^-1 (column by column)
+    std::vector<double> L = K;
+    for (int j = 0; j < n; ++j) {
+        double d = L[(size_t)j * n + j];
+        for (int k = 0; k < j; ++k) d -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
+        d = std::sqrt(d);
+        L[(size_t)j * n + j] = d;
+        for (int i = j + 1; i < n; ++i) {
+            double v = L[(size_t)i * n + j];
+            for (int k = 0; k < j; ++k) v -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
+            L[(size_t)i * n + j] = v / d;
+        }
+    }
+    std::vector<double> Ainv((size_t)n * n, 0.0), y(n);
+    for (int col = 0; col < n; ++col) {
+        for (int i = 0; i < n; ++i) {   // L y = e_col
+            double v = i == col ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) v -= L[(size_t)i * n + k] * y[k];
+            y[i] = v / L[(size_t)i * n + i];
+        }
+        for (int i = n - 1; i >= 0; --i) {   // L^T x = y
+            double v = y[i];
+            for (int k = i + 1; k < n; ++k) v -= L[(size_t)k * n + i] * Ainv[(size_t)k * n + col];
+            Ainv[(size_t)i * n + col] = v / L[(size_t)i * n + i];
+        }
+    }
+    inv.assign((size_t)n * n, 0.f);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            inv[(size_t)i * n + j] = (float)(0.5 * (Ainv[(size_t)i * n + j] + Ainv[(size_t)j * n + i]));
 }
 
 double fem_jacobi_lambda_max(const double *St) {

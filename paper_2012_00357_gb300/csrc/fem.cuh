@@ -1,6 +1,8 @@
 // Finite-element operators of the constraint projection P_C (fem.cu).
 #pragma once
 
+#include <vector>
+
 #include "dd_internal.cuh"
 
 struct MeshDev {
@@ -22,21 +24,25 @@ struct ElemOps {
 // its stiffness is exactly the Galerkin product; an odd count gives a coarse
 // box one fine layer longer (not nested: the coarse operator is the
 // rediscretised one, and the V-cycle stays symmetric positive definite).
-// Levels whose nodes (with all coarser ones) fit kMgBlockNodes run inside one
-// block of their solve, in shared memory; the finer ones on the whole grid.
+// The hierarchy stops at the first coarse level with at most kMgDirectDofs
+// free degrees of freedom, which is solved exactly (a dense inverse applied
+// by one block of the solve); the finer levels run on the whole grid.
 constexpr int kMgMaxLev = 8;
-constexpr int kMgBlockNodes = 200;
+constexpr int kMgDirectDofs = 400;
 
 struct CGBuffers {
     const double *Ke, *Minv, *b;
     const double *St64;   // stencil table [27 classes][27 offsets][9] (fem_stencil_table)
     const float *St32;    // the same in FP32, blocks padded to 12 values
     // multigrid hierarchy (fem_mg_plan)
-    int nlev = 1, glev = 1;                    // levels; levels run by the whole grid
+    int nlev = 1, glev = 1;                    // levels; levels run by the whole grid (glev < nlev:
+                                               // level glev is solved directly)
     int lnx[kMgMaxLev], lny[kMgMaxLev], lnz[kMgMaxLev];
     float *mg_t0 = nullptr;                    // level-0 scratch [nodes x 6]
     float *mg_r[kMgMaxLev], *mg_z[kMgMaxLev], *mg_t[kMgMaxLev];   // grid levels 1 .. glev-1
-    float *mg_zg = nullptr;                    // result of the in-block cycle (level glev, all nodes)
+    float *mg_zg = nullptr;                    // coarse solution (level glev, all nodes)
+    float *mg_inv = nullptr;                   // inverse of level glev's K on its free DOFs [ndof x ndof]
+    int mg_ndof = 0;
     double omega = 0.5;                        // damped block-Jacobi weight of the smoother
     double *x, *r, *z, *p0, *p1, *q, *part;
     unsigned *bar;
@@ -65,6 +71,9 @@ void fem_stencil_table(const double *Ke, double *S);
 // Levels of the multigrid hierarchy of a box: element counts per level and
 // the number of levels run by the whole grid (fills nlev, glev, lnx, lny, lnz).
 void fem_mg_plan(const MeshDev &g, CGBuffers &cb);
+// Inverse of the stiffness of the directly solved level (cb.glev, when
+// cb.glev < cb.nlev) on its free DOFs, from the stencil table; symmetric, FP32.
+void fem_mg_coarse_inverse(const CGBuffers &cb, const double *St64, std::vector<float> &inv);
 // Largest eigenvalue of D^-1 K (D: the 3x3 diagonal blocks) by power
 // iteration on a small box with the same elements, from the stencil table.
 double fem_jacobi_lambda_max(const double *St64);

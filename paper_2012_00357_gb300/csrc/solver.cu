@@ -80,6 +80,7 @@ size_t carve(dd_solver *sv, char *base) {
     if (cb.glev < cb.nlev) {
         const int l = cb.glev;
         cb.mg_zg = bp.take<float>((size_t)(cb.lnx[l] + 1) * (cb.lny[l] + 1) * (cb.lnz[l] + 1) * 6);
+        cb.mg_inv = bp.take<float>((size_t)cb.mg_ndof * cb.mg_ndof);
     }
     cb.part = bp.take<double>((size_t)2 * sv->ctx->n_sm * 32 * 8);
     cb.bar = bp.take<unsigned>(16);
@@ -221,6 +222,8 @@ extern "C" dd_status dd_solver_create(dd_dataset *ds, const dd_mesh *mesh, const
     std::vector<float> St32(27 * 27 * 12, 0.f);
     fem_stencil_table(Ke.data(), St64.data());
     sv->cb.omega = 4.0 / (3.0 * fem_jacobi_lambda_max(St64.data()));
+    std::vector<float> Kinv;
+    if (sv->cb.glev < sv->cb.nlev) fem_mg_coarse_inverse(sv->cb, St64.data(), Kinv);
     for (int cd = 0; cd < 27 * 27; ++cd)
         for (int k = 0; k < 9; ++k) St32[cd * 12 + k] = (float)St64[cd * 9 + k];
     fem_traction_force(sv->g, *load, mesh->lx, mesh->ly, f.data());
@@ -228,6 +231,8 @@ extern "C" dd_status dd_solver_create(dd_dataset *ds, const dd_mesh *mesh, const
     if (cudaMemcpyAsync(sv->Ke, Ke.data(), 576 * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(sv->St64, St64.data(), St64.size() * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(sv->St32, St32.data(), St32.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        (!Kinv.empty() &&
+         cudaMemcpyAsync(sv->cb.mg_inv, Kinv.data(), Kinv.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) ||
         cudaMemcpyAsync(sv->f, f.data(), nn * 3 * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(sv->cb.x, 0, nn * 6 * 8, s) != cudaSuccess ||
         cudaMemsetAsync(sv->mot.d, 0, ng * 2 * sizeof(float), s) != cudaSuccess)
