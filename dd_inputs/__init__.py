@@ -275,8 +275,10 @@ WORKLOADS = {
     "cube32_N1e9_ann_4loads": Workload(
         "cube32_N1e9_ann_4loads", 32, 1_000_000_000, NONLINEAR,
         loads=(("tension", 1e-3), ("shear", 1e-3), ("bending", 1e-3), ("torsion", 1e-3))),
-    # the 32^3 constraint projection with a small data set: a profiling case
-    # for the CG (the search is cheap here)
+    # profiling cases of a few GB: the tree search (with --ann-levels 2) and
+    # the 32^3 constraint projection with a small data set
+    "cube16_N3e7_ann": Workload("cube16_N3e7_ann", 16, 30_000_000, NONLINEAR),
+    # (the search is cheap in the latter)
     "cube32_N1e5_exact": Workload("cube32_N1e5_exact", 32, 100_000, NONLINEAR),
     "serve_N1e7": Workload("serve_N1e7", 0, 10_000_000, NONLINEAR,
                            extra={"requests": 512, "edge_min": 4, "edge_max": 24,

@@ -181,6 +181,9 @@ typedef struct dd_search_stats {
                                  (CUDA events on the launching stream) */
     int64_t points;           /* data points read by the approximate search
                                  (the rest of `distances` are centroids) */
+    int64_t unique_points;    /* approximate search: points of the distinct
+                                 clusters it read (what it must fetch from
+                                 memory at least once) */
 } dd_search_stats;
 
 /* Nearest data point of each state y_i (Eq. 7):
@@ -313,6 +316,7 @@ typedef struct dd_iter_info {
     int64_t skipped;          /* ANN: queries kept by the moving-query radius
                                  (Eq. 14) without a search */
     int64_t points;           /* ANN: data points read by the search */
+    int64_t unique_points;    /* ANN: points of the distinct clusters read */
     int graph;                /* 1: dd_solvers_step replayed (or captured) the
                                  step as a CUDA graph; 0: launched eagerly */
 } dd_iter_info;

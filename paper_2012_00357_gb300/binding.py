@@ -51,14 +51,15 @@ class dd_search_opts(ctypes.Structure):
 
 class dd_search_stats(ctypes.Structure):
     _fields_ = [("uncertified", c_int64), ("distances", c_int64), ("skipped", c_int64), ("ms", c_double),
-                ("scan_ms", c_double), ("points", c_int64)]
+                ("scan_ms", c_double), ("points", c_int64), ("unique_points", c_int64)]
 
 
 class dd_iter_info(ctypes.Structure):
     _fields_ = [("iter", c_int), ("changed", c_int64), ("d2_pc", c_double), ("d2_pd", c_double),
                 ("cg_iters", c_int), ("cg_ms", c_double), ("search_ms", c_double), ("other_ms", c_double),
                 ("scan_ms", c_double), ("uncertified", c_int64), ("distances", c_int64), ("f_d", c_double),
-                ("done", c_int), ("skipped", c_int64), ("points", c_int64), ("graph", c_int)]
+                ("done", c_int), ("skipped", c_int64), ("points", c_int64), ("unique_points", c_int64),
+                ("graph", c_int)]
 
 
 class dd_mesh(ctypes.Structure):

@@ -271,7 +271,9 @@ struct ProbeArgs {
     float *d1, *d2;             // plain squared distances of the answer / second
     int64_t *fb_list;
     unsigned long long *fb_count;
-    unsigned long long *counters;   // [0] points scanned, [1] queries skipped
+    unsigned long long *counters;   // [0] points scanned, [1] queries skipped, [2] exact re-searches,
+                                    // [3] leaf centroids ranked, [4] distinct points scanned
+    unsigned *touched;              // [ceil(L / 32)] clusters scanned by any query of this search
 };
 
 __global__ void __launch_bounds__(256) k_ann_probe(ProbeArgs A) {
@@ -318,6 +320,7 @@ __global__ void __launch_bounds__(256) k_ann_probe(ProbeArgs A) {
         const int64_t p0 = A.offs[l], p1 = A.offs[l + 1];
         for (int64_t p = p0 + lane; p < p1; p += 32) best_update(b, dist2_12(A.zs + p * 12, q), A.perm[p]);
         scanned += (unsigned long long)(p1 - p0);
+        if (lane == 0) atomicOr(A.touched + (l >> 5), 1u << (l & 31));
         best_warp(b);
     };
     if (cl0 >= 0) scan(cl0);
@@ -542,6 +545,7 @@ __global__ void __launch_bounds__(256) k_ann_probe2(Probe2Args P) {
         const int64_t p0 = A.offs[l], p1 = A.offs[l + 1];
         for (int64_t p = p0 + lane; p < p1; p += 32) best_update(b, dist2_12(A.zs + p * 12, q), A.perm[p]);
         scanned += (unsigned long long)(p1 - p0);
+        if (lane == 0) atomicOr(A.touched + (l >> 5), 1u << (l & 31));
         best_warp(b);
     };
     if (l0 >= 0) scan(l0);
@@ -614,6 +618,25 @@ __global__ void __launch_bounds__(256) k_ann_probe2(Probe2Args P) {
         A.d1[i] = b.d;
         A.d2[i] = b.s;
     }
+}
+
+// Points in the clusters marked in the bitmap (the data a search must read
+// at least once).
+__global__ void k_touched_points(const unsigned *__restrict__ touched, int L, const int64_t *__restrict__ offs,
+                                 unsigned long long *__restrict__ out) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long n = 0;
+    if (w < (L + 31) / 32) {
+        unsigned bits = touched[w];
+        while (bits) {
+            const int b = __ffs(bits) - 1;
+            bits &= bits - 1;
+            const int l = w * 32 + b;
+            if (l < L) n += (unsigned long long)(offs[l + 1] - offs[l]);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+    if ((threadIdx.x & 31) == 0 && n) atomicAdd(out, n);
 }
 
 __global__ void k_motion_update(const QueryRec *__restrict__ rec, int64_t m, const double *__restrict__ d2,
@@ -990,9 +1013,10 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
     if (m == 0) return DD_OK;
     auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
     const size_t b_rec = r256((size_t)m * sizeof(QueryRec)), b_cl = r256((size_t)m * kCand * 4),
-                 b_cd = r256((size_t)m * kCand * 4), b_f = r256((size_t)m * 4), b_list = r256((size_t)m * 8);
+                 b_cd = r256((size_t)m * kCand * 4), b_f = r256((size_t)m * 4), b_list = r256((size_t)m * 8),
+                 b_bits = r256((size_t)(a.nlist + 31) / 32 * 4);
     void *w = nullptr;
-    DD_TRY(dd_workspace(ctx, WS_ANN, b_rec + b_cl + b_cd + 2 * b_f + b_list + 256, &w));
+    DD_TRY(dd_workspace(ctx, WS_ANN, b_rec + b_cl + b_cd + 2 * b_f + b_list + 256 + b_bits, &w));
     char *c = (char *)w;
     QueryRec *rec = (QueryRec *)c;
     int32_t *cand_cl = (int32_t *)(c + b_rec);
@@ -1001,7 +1025,9 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
     float *d2f = (float *)(c + b_rec + b_cl + b_cd + b_f);
     int64_t *fb_list = (int64_t *)(c + b_rec + b_cl + b_cd + 2 * b_f);
     unsigned long long *counters = (unsigned long long *)(c + b_rec + b_cl + b_cd + 2 * b_f + b_list);
-    DD_TRY_CUDA(ctx, cudaMemsetAsync(counters, 0, 32, s));
+    unsigned *touched = (unsigned *)(c + b_rec + b_cl + b_cd + 2 * b_f + b_list + 256);
+    DD_TRY_CUDA(ctx, cudaMemsetAsync(counters, 0, 64, s));
+    DD_TRY_CUDA(ctx, cudaMemsetAsync(touched, 0, b_bits, s));
 
     DD_TRY(dd_map_queries(ds, y_dev, m, nullptr, rec, s));
     int splits = 0, cap = 0;
@@ -1040,6 +1066,7 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
     A.fb_list = fb_list;
     A.fb_count = counters + 2;
     A.counters = counters;
+    A.touched = touched;
     if (two) {
         Probe2Args P2{A, a.cent, a.rad1, a.L1, a.L2, a.r1max};
         k_ann_probe2<<<(unsigned)((m * 32 + 255) / 256), 256, 0, s>>>(P2);
@@ -1060,12 +1087,18 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
         if (n_fb) DD_TRY(ann_exact_subset(ds, y_dev, fb_list, (int64_t)n_fb, out, s));
     }
     if (mot && out.d2 && out.d2nd) DD_TRY(dd_ann_motion_update(ctx, rec, m, out.d2, out.d2nd, mot, s));
+    if (st) {
+        const int words = (a.nlist + 31) / 32;
+        ctx->launches++;
+        k_touched_points<<<(unsigned)((words + 255) / 256), 256, 0, s>>>(touched, a.nlist, a.offs, counters + 4);
+        DD_TRY_CUDA(ctx, cudaGetLastError());
+    }
     if (st && ctx->defer) {
-        DD_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->defer->ann, counters, 4 * sizeof(unsigned long long),
+        DD_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->defer->ann, counters, 5 * sizeof(unsigned long long),
                                          cudaMemcpyDeviceToDevice, s));
         st->distances += m * (int64_t)(two ? a.L1 : a.nlist);
     } else if (st) {
-        unsigned long long h[4];
+        unsigned long long h[5];
         DD_TRY_CUDA(ctx, cudaMemcpyAsync(h, counters, sizeof(h), cudaMemcpyDeviceToHost, s));
         DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
         float ms = 0.f;
@@ -1073,6 +1106,7 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
         st->scan_ms += ms;
         st->distances += (int64_t)h[0] + (int64_t)h[3] + m * (int64_t)(two ? a.L1 : a.nlist) + (int64_t)n_fb * ds->N;
         st->points += (int64_t)h[0] + (int64_t)n_fb * ds->N;
+        st->unique_points += n_fb ? ds->N : (int64_t)h[4];
         st->skipped += (int64_t)h[1];
         st->uncertified += (int64_t)n_fb;
     }

@@ -74,7 +74,8 @@ struct Workspace {
 // reads them after the step.
 struct DeferredStats {
     unsigned long long fb;       // exact search: queries re-searched in FP64
-    unsigned long long ann[4];   // approximate search: points scanned, skipped, exact re-search, fine centroids
+    unsigned long long ann[5];   // approximate search: points scanned, skipped, exact re-search, fine
+                                 // centroids, distinct points scanned
 };
 
 struct StepPlan;

@@ -154,6 +154,7 @@ bool dd_solver_account(dd_solver *sv, const double hs[3], int cg_it, float cg_ms
         info->done = sv->done ? 1 : 0;
         info->skipped = sst.skipped;
         info->points = sst.points;
+        info->unique_points = sst.unique_points;
         info->graph = 0;
     }
     return sv->done;
