@@ -40,7 +40,7 @@ constexpr int kTileC = 256;       // centroids per shared-memory tile in k_assig
 
 __device__ __forceinline__ float dist2_12(const float *a, const float (&q)[12]) {
     const float4 *p = reinterpret_cast<const float4 *>(a);
-    float4 u = p[0], v = p[1], w = p[2];
+    const float4 u = __ldg(p), v = __ldg(p + 1), w = __ldg(p + 2);
     float d, s = 0.f;
     d = u.x - q[0]; s = fmaf(d, d, s);
     d = u.y - q[1]; s = fmaf(d, d, s);
@@ -229,6 +229,29 @@ __device__ __forceinline__ void best_update(Best &b, float d, int j) {
     }
 }
 
+// One warp scans the points [p0, p1) of the cluster-sorted copy for query q
+// (lane-strided, four points of a lane in flight at a time); the original
+// index is read only for a point that can become the best.
+__device__ __forceinline__ void scan_range(const float *zs, const int32_t *perm, int64_t p0, int64_t p1, int lane,
+                                           const float (&q)[12], Best &b) {
+    int64_t p = p0 + lane;
+    for (; p + 96 < p1; p += 128) {
+        float d[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) d[u] = dist2_12(zs + (p + 32 * u) * 12, q);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (d[u] <= b.d) best_update(b, d[u], __ldg(perm + p + 32 * u));
+            else if (d[u] < b.s) b.s = d[u];
+        }
+    }
+    for (; p < p1; p += 32) {
+        const float d = dist2_12(zs + p * 12, q);
+        if (d <= b.d) best_update(b, d, __ldg(perm + p));
+        else if (d < b.s) b.s = d;
+    }
+}
+
 // warp-wide merge: every lane ends with the same (best, index, second)
 __device__ __forceinline__ void best_warp(Best &b) {
     Best g = b;
@@ -318,7 +341,7 @@ __global__ void __launch_bounds__(256) k_ann_probe(ProbeArgs A) {
     }
     auto scan = [&](int l) {
         const int64_t p0 = A.offs[l], p1 = A.offs[l + 1];
-        for (int64_t p = p0 + lane; p < p1; p += 32) best_update(b, dist2_12(A.zs + p * 12, q), A.perm[p]);
+        scan_range(A.zs, A.perm, p0, p1, lane, q, b);
         scanned += (unsigned long long)(p1 - p0);
         if (lane == 0) atomicOr(A.touched + (l >> 5), 1u << (l & 31));
         best_warp(b);
@@ -543,7 +566,7 @@ __global__ void __launch_bounds__(256) k_ann_probe2(Probe2Args P) {
     }
     auto scan = [&](int l) {
         const int64_t p0 = A.offs[l], p1 = A.offs[l + 1];
-        for (int64_t p = p0 + lane; p < p1; p += 32) best_update(b, dist2_12(A.zs + p * 12, q), A.perm[p]);
+        scan_range(A.zs, A.perm, p0, p1, lane, q, b);
         scanned += (unsigned long long)(p1 - p0);
         if (lane == 0) atomicOr(A.touched + (l >> 5), 1u << (l & 31));
         best_warp(b);
