@@ -174,7 +174,7 @@ def run_ours(args, world, rank, local):
     t_build = time.perf_counter()
     levels = args.ann_levels or (2 if W.N >= 300_000_000 else 1)
     if mode == P.DD_SEARCH_ANN and levels == 2 and not args.nlist:
-        nlist = 1 << 18
+        nlist = 1 << 19
     ds = P.dd_load_dataset(ctx, raw, C, borrow=True, build_fp16=(mode == P.DD_SEARCH_EXACT_TC), ann_nlist=nlist,
                            seed=1, ann_levels=levels)
     torch.cuda.synchronize()

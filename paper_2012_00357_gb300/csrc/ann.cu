@@ -229,6 +229,18 @@ __device__ __forceinline__ void best_update(Best &b, float d, int j) {
     }
 }
 
+// Offer point p (squared distance d) to b; its original index is read only
+// when it can become the best, and the point that already is the best (the
+// warm start, met again in its own cluster) is not a second candidate.
+__device__ __forceinline__ void best_lazy(Best &b, float d, const int32_t *perm, int64_t p) {
+    if (d <= b.d) {
+        const int j = __ldg(perm + p);
+        if (j != b.j) best_update(b, d, j);
+    } else if (d < b.s) {
+        b.s = d;
+    }
+}
+
 // One warp scans the points [p0, p1) of the cluster-sorted copy for query q
 // (lane-strided, four points of a lane in flight at a time); the original
 // index is read only for a point that can become the best.
@@ -240,16 +252,9 @@ __device__ __forceinline__ void scan_range(const float *zs, const int32_t *perm,
 #pragma unroll
         for (int u = 0; u < 4; ++u) d[u] = dist2_12(zs + (p + 32 * u) * 12, q);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            if (d[u] <= b.d) best_update(b, d[u], __ldg(perm + p + 32 * u));
-            else if (d[u] < b.s) b.s = d[u];
-        }
+        for (int u = 0; u < 4; ++u) best_lazy(b, d[u], perm, p + 32 * u);
     }
-    for (; p < p1; p += 32) {
-        const float d = dist2_12(zs + p * 12, q);
-        if (d <= b.d) best_update(b, d, __ldg(perm + p));
-        else if (d < b.s) b.s = d;
-    }
+    for (; p < p1; p += 32) best_lazy(b, dist2_12(zs + p * 12, q), perm, p);
 }
 
 // warp-wide merge: every lane ends with the same (best, index, second)
@@ -294,8 +299,9 @@ struct ProbeArgs {
     float *d1, *d2;             // plain squared distances of the answer / second
     int64_t *fb_list;
     unsigned long long *fb_count;
-    unsigned long long *counters;   // [0] points scanned, [1] queries skipped, [2] exact re-searches,
-                                    // [3] leaf centroids ranked, [4] distinct points scanned
+    unsigned long long *counters;   // [0] point distances evaluated, [1] queries skipped, [2] exact
+                                    // re-searches, [3] leaf centroids ranked, [4] distinct points,
+                                    // [5] points read
     unsigned *touched;              // [ceil(L / 32)] clusters scanned by any query of this search
 };
 
@@ -369,6 +375,7 @@ __global__ void __launch_bounds__(256) k_ann_probe(ProbeArgs A) {
     }
     if (lane == 0) {
         atomicAdd(A.counters, scanned);
+        atomicAdd(A.counters + 5, scanned);
         if (incomplete) {
             unsigned long long t = atomicAdd(A.fb_count, 1ull);
             A.fb_list[t] = i;
@@ -513,6 +520,51 @@ __global__ void k_radius_orig(const float *__restrict__ z, const int32_t *__rest
     atomicMax(rbits + c, __float_as_uint(d * 1.000001f + 1e-30f));
 }
 
+constexpr int kFine = 8;        // leaves visited per cell at most
+constexpr int kFinePerLane = 16;   // L2 <= 512
+constexpr int kGrp = 8;         // queries per warp: the Gauss points of one element
+constexpr int kRemember = 64;   // leaves a warp remembers as scanned
+
+__device__ __forceinline__ float warp_minf(float v) {
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Scan one leaf for every query of the warp's group: each lane reads two
+// points at a time and updates its own best of every query (the queries sit
+// in shared memory and are read as broadcasts).
+__device__ __forceinline__ void scan_leaf_grp(const float *zs, const int32_t *perm, int64_t p0, int64_t p1, int lane,
+                                              const float *sq, int ng, Best (&b)[kGrp]) {
+    for (int64_t p = p0 + lane; p < p1; p += 64) {
+        const bool two = p + 32 < p1;
+        const float4 *y0 = reinterpret_cast<const float4 *>(zs + p * 12);
+        const float4 *y1 = reinterpret_cast<const float4 *>(zs + (two ? p + 32 : p) * 12);
+        const float4 a0 = __ldg(y0), a1 = __ldg(y0 + 1), a2 = __ldg(y0 + 2);
+        const float4 c0 = __ldg(y1), c1 = __ldg(y1 + 1), c2 = __ldg(y1 + 2);
+#pragma unroll
+        for (int g = 0; g < kGrp; ++g) {
+            if (g >= ng) break;
+            const float4 *qq = reinterpret_cast<const float4 *>(sq + g * 12);
+            const float4 q0 = qq[0], q1 = qq[1], q2 = qq[2];
+            float t, d0 = 0.f, d1 = 0.f;
+            t = a0.x - q0.x; d0 = fmaf(t, t, d0); t = c0.x - q0.x; d1 = fmaf(t, t, d1);
+            t = a0.y - q0.y; d0 = fmaf(t, t, d0); t = c0.y - q0.y; d1 = fmaf(t, t, d1);
+            t = a0.z - q0.z; d0 = fmaf(t, t, d0); t = c0.z - q0.z; d1 = fmaf(t, t, d1);
+            t = a0.w - q0.w; d0 = fmaf(t, t, d0); t = c0.w - q0.w; d1 = fmaf(t, t, d1);
+            t = a1.x - q1.x; d0 = fmaf(t, t, d0); t = c1.x - q1.x; d1 = fmaf(t, t, d1);
+            t = a1.y - q1.y; d0 = fmaf(t, t, d0); t = c1.y - q1.y; d1 = fmaf(t, t, d1);
+            t = a1.z - q1.z; d0 = fmaf(t, t, d0); t = c1.z - q1.z; d1 = fmaf(t, t, d1);
+            t = a1.w - q1.w; d0 = fmaf(t, t, d0); t = c1.w - q1.w; d1 = fmaf(t, t, d1);
+            t = a2.x - q2.x; d0 = fmaf(t, t, d0); t = c2.x - q2.x; d1 = fmaf(t, t, d1);
+            t = a2.y - q2.y; d0 = fmaf(t, t, d0); t = c2.y - q2.y; d1 = fmaf(t, t, d1);
+            t = a2.z - q2.z; d0 = fmaf(t, t, d0); t = c2.z - q2.z; d1 = fmaf(t, t, d1);
+            t = a2.w - q2.w; d0 = fmaf(t, t, d0); t = c2.w - q2.w; d1 = fmaf(t, t, d1);
+            best_lazy(b[g], d0, perm, p);
+            if (two) best_lazy(b[g], d1, perm, p + 32);
+        }
+    }
+}
+
 struct Probe2Args {
     ProbeArgs A;                // leaves in A.radius / A.offs / A.zs / A.perm / A.cluster_of; cand_* are coarse cells
     const float *centf;         // [L x 12] leaf centroids
@@ -521,125 +573,180 @@ struct Probe2Args {
     float r1max;
 };
 
-constexpr int kFine = 8;        // leaves visited per cell at most
-constexpr int kFinePerLane = 16;   // L2 <= 512
-
+// Tree search of Sec. 4 for the queries of one element per warp (its 8
+// Gauss points, consecutive in the query order, whose states are close).
+// Every query keeps its own warm start (Sec. 4.5), its own ranking of the
+// coarse cells and of their leaves, and its own Eq. (13) tests with its own
+// d_c; a leaf that any of them decides to scan is read once and evaluated
+// for all of them, and a leaf the warp has already scanned is not read
+// again.  A query therefore evaluates at least the points its own rules
+// select, and its answer can only be as near or nearer.
 __global__ void __launch_bounds__(256) k_ann_probe2(Probe2Args P) {
     const ProbeArgs &A = P.A;
-    const int lane = threadIdx.x & 31;
-    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (i >= A.m) return;
-    float q[12];
+    __shared__ __align__(16) float s_q[8][kGrp * 12];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t i0 = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * kGrp;
+    const int ng = A.m - i0 < kGrp ? (int)(A.m - i0) : kGrp;
+    float *sq = s_q[wib];
+    if (ng > 0)
+        for (int k = lane; k < ng * 12; k += 32) sq[k] = A.rec[i0 + k / 12].q[k % 12];
+    __syncwarp();
+    if (ng <= 0) return;
+    // warm start and Eq. (14), lane g for query g
+    float d0 = INFINITY;
+    int j0 = 0x7fffffff, l0 = -1;
+    bool skip = false;
+    if (lane < ng && A.prev) {
+        const int64_t i = i0 + lane;
+        const int jp = A.prev[i];
+        if (jp >= 0 && jp < A.N) {
+            float q[12];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) q[k] = A.rec[i].q[k];
-    Best b{INFINITY, 0x7fffffff, INFINITY};
-    int l0 = -1;
-    unsigned long long scanned = 0;
-    if (A.prev) {
-        const int j0 = A.prev[i];
-        if (j0 >= 0 && j0 < A.N) {
-            const float d0 = dist2_12(A.z32 + (size_t)j0 * 12, q);
+            for (int k = 0; k < 12; ++k) q[k] = sq[lane * 12 + k];
+            d0 = dist2_12(A.z32 + (size_t)jp * 12, q);
+            j0 = jp;
+            l0 = A.cluster_of[jp];
             if (A.mot_q) {
                 float mv = 0.f;
 #pragma unroll
                 for (int k = 0; k < 12; ++k) {
-                    float t = q[k] - A.mot_q[i * 12 + k];
+                    const float t = q[k] - A.mot_q[i * 12 + k];
                     mv = fmaf(t, t, mv);
                 }
                 mv = sqrtf(mv);
                 const float r1 = A.mot_d[i * 2], r2 = A.mot_d[i * 2 + 1];
-                if (mv < 0.5f * (r2 - r1)) {      // Eq. (14)
-                    if (lane == 0) {
-                        A.idx[i] = j0;
-                        A.d1[i] = d0;
-                        float lb = fmaxf(r2 - mv, 0.f);
-                        A.d2[i] = lb * lb;
-                        atomicAdd(A.counters + 1, 1ull);
-                    }
-                    return;
+                if (mv < 0.5f * (r2 - r1)) {
+                    skip = true;
+                    A.idx[i] = jp;
+                    A.d1[i] = d0;
+                    const float lb = fmaxf(r2 - mv, 0.f);
+                    A.d2[i] = lb * lb;
+                    atomicAdd(A.counters + 1, 1ull);
                 }
             }
-            b.d = d0;
-            b.j = j0;
-            l0 = A.cluster_of[j0];
         }
     }
-    auto scan = [&](int l) {
+    const unsigned skipmask = __ballot_sync(0xffffffffu, skip);
+    Best b[kGrp];
+    float dc[kGrp];
+#pragma unroll
+    for (int g = 0; g < kGrp; ++g) {
+        b[g].d = __shfl_sync(0xffffffffu, d0, g);
+        b[g].j = __shfl_sync(0xffffffffu, j0, g);
+        b[g].s = INFINITY;
+        dc[g] = sqrtf(b[g].d);
+    }
+    int rem0 = -1, rem1 = -1, nrem = 0;   // leaves scanned so far (lane k: entries k and k + 32)
+    unsigned long long read = 0, evals = 0;
+    auto scan_new = [&](int l) {
+        if (__any_sync(0xffffffffu, rem0 == l || rem1 == l)) return;
+        if (nrem < kRemember) {
+            if (lane == (nrem & 31)) {
+                if (nrem < 32) rem0 = l;
+                else rem1 = l;
+            }
+            ++nrem;
+        }
         const int64_t p0 = A.offs[l], p1 = A.offs[l + 1];
-        scan_range(A.zs, A.perm, p0, p1, lane, q, b);
-        scanned += (unsigned long long)(p1 - p0);
+        scan_leaf_grp(A.zs, A.perm, p0, p1, lane, sq, ng, b);
+        read += (unsigned long long)(p1 - p0);
+        evals += (unsigned long long)(p1 - p0) * (unsigned long long)ng;
         if (lane == 0) atomicOr(A.touched + (l >> 5), 1u << (l & 31));
-        best_warp(b);
+#pragma unroll
+        for (int g = 0; g < kGrp; ++g) dc[g] = sqrtf(warp_minf(b[g].d));
     };
-    if (l0 >= 0) scan(l0);
-    float dc = sqrtf(b.d);
-    const float f_d = A.fd_q ? A.fd_q[i] : A.f_d;
-    bool incomplete = false;
-    for (int k1 = 0; k1 < kCand; ++k1) {
-        const int C = A.cand_cl[i * kCand + k1];
-        if (C < 0) break;
-        const float dC = A.cand_d[i * kCand + k1];
-        if (!(k1 == 0 || dC - f_d * P.rad1[C] < dc)) continue;
-        // rank the cell's leaves: lane holds leaves f = lane + 32 t
-        float fd[kFinePerLane];
-        unsigned vis = 0;
+    for (int g = 0; g < ng; ++g) {
+        const int lg = __shfl_sync(0xffffffffu, l0, g);
+        if (!((skipmask >> g) & 1u) && lg >= 0) scan_new(lg);
+    }
+    unsigned incomplete = 0;
+    for (int g = 0; g < ng; ++g) {
+        if ((skipmask >> g) & 1u) continue;
+        const int64_t i = i0 + g;
+        const float f_d = A.fd_q ? A.fd_q[i] : A.f_d;
+        float q[12];
 #pragma unroll
-        for (int t = 0; t < kFinePerLane; ++t) {
-            const int f = lane + 32 * t;
-            fd[t] = (f < P.L2) ? sqrtf(dist2_12(P.centf + ((size_t)C * P.L2 + f) * 12, q)) : INFINITY;
-        }
-        if (lane == 0) atomicAdd(A.counters + 3, (unsigned long long)P.L2);
-        for (int k2 = 0; k2 < kFine; ++k2) {
-            float md = INFINITY;
-            int mt = -1;
+        for (int k = 0; k < 12; ++k) q[k] = sq[g * 12 + k];
+        float dcg = 0.f;
 #pragma unroll
-            for (int t = 0; t < kFinePerLane; ++t)
-                if (!((vis >> t) & 1u) && fd[t] < md) {
-                    md = fd[t];
-                    mt = t;
+        for (int k = 0; k < kGrp; ++k)
+            if (k == g) dcg = dc[k];
+        for (int k1 = 0; k1 < kCand; ++k1) {
+            const int C = A.cand_cl[i * kCand + k1];
+            if (C < 0) break;
+            const float dC = A.cand_d[i * kCand + k1];
+            if (!(k1 == 0 || dC - f_d * P.rad1[C] < dcg)) continue;
+            // rank the cell's leaves for this query: lane holds leaves f = lane + 32 t
+            float fd[kFinePerLane];
+            unsigned vis = 0;
+#pragma unroll
+            for (int t = 0; t < kFinePerLane; ++t) {
+                const int f = lane + 32 * t;
+                fd[t] = (f < P.L2) ? sqrtf(dist2_12(P.centf + ((size_t)C * P.L2 + f) * 12, q)) : INFINITY;
+            }
+            if (lane == 0) atomicAdd(A.counters + 3, (unsigned long long)P.L2);
+            for (int k2 = 0; k2 < kFine; ++k2) {
+                float md = INFINITY;
+                int mt = -1;
+#pragma unroll
+                for (int t = 0; t < kFinePerLane; ++t)
+                    if (!((vis >> t) & 1u) && fd[t] < md) {
+                        md = fd[t];
+                        mt = t;
+                    }
+                int ml = mt >= 0 ? lane + 32 * mt : 0x7fffffff;
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float od = __shfl_xor_sync(0xffffffffu, md, o);
+                    const int ol = __shfl_xor_sync(0xffffffffu, ml, o);
+                    if (od < md || (od == md && ol < ml)) {
+                        md = od;
+                        ml = ol;
+                    }
                 }
-            int ml = mt >= 0 ? lane + 32 * mt : 0x7fffffff;
-            for (int o = 16; o > 0; o >>= 1) {
-                float od = __shfl_xor_sync(0xffffffffu, md, o);
-                int ol = __shfl_xor_sync(0xffffffffu, ml, o);
-                if (od < md || (od == md && ol < ml)) {
-                    md = od;
-                    ml = ol;
+                if (!(md < INFINITY)) break;
+                if ((ml & 31) == lane) vis |= 1u << (ml >> 5);
+                const int l = C * P.L2 + ml;
+                if ((k1 == 0 && k2 == 0) || md - f_d * A.radius[l] < dcg) {
+                    scan_new(l);
+#pragma unroll
+                    for (int k = 0; k < kGrp; ++k)
+                        if (k == g) dcg = dc[k];
                 }
             }
-            if (!(md < INFINITY)) break;
-            if ((ml & 31) == lane) vis |= 1u << (ml >> 5);
-            const int l = C * P.L2 + ml;
-            if ((k1 == 0 && k2 == 0) || md - f_d * A.radius[l] < dc) {
-                if (l != l0) {
-                    scan(l);
-                    dc = sqrtf(b.d);
-                }
+            // leaves of this cell beyond the kFine nearest (exact requests only)
+            if (f_d >= 1.0f && P.L2 > kFine) {
+                float md = INFINITY;
+#pragma unroll
+                for (int t = 0; t < kFinePerLane; ++t)
+                    if (!((vis >> t) & 1u)) md = fminf(md, fd[t]);
+                md = warp_minf(md);
+                if (md - f_d * A.rmax < dcg) incomplete |= 1u << g;
             }
         }
-        // leaves of this cell beyond the kFine nearest (exact requests only)
-        if (f_d >= 1.0f && P.L2 > kFine) {
-            float md = INFINITY;
-#pragma unroll
-            for (int t = 0; t < kFinePerLane; ++t)
-                if (!((vis >> t) & 1u)) md = fminf(md, fd[t]);
-            for (int o = 16; o > 0; o >>= 1) md = fminf(md, __shfl_xor_sync(0xffffffffu, md, o));
-            if (md - f_d * A.rmax < dc) incomplete = true;
+        if (f_d >= 1.0f && P.L1 > kCand) {
+            const float dP = A.cand_d[i * kCand + kCand - 1];
+            if (dP - f_d * P.r1max < dcg) incomplete |= 1u << g;
         }
     }
-    if (f_d >= 1.0f && P.L1 > kCand) {
-        const float dP = A.cand_d[i * kCand + kCand - 1];
-        if (dP - f_d * P.r1max < dc) incomplete = true;
+    // merge every query's best over the lanes and write the answers
+#pragma unroll
+    for (int g = 0; g < kGrp; ++g) {
+        if (g >= ng) break;
+        best_warp(b[g]);
+        if (lane == g && !((skipmask >> g) & 1u)) {
+            const int64_t i = i0 + g;
+            if ((incomplete >> g) & 1u) {
+                const unsigned long long t = atomicAdd(A.fb_count, 1ull);
+                A.fb_list[t] = i;
+            }
+            A.idx[i] = b[g].j;
+            A.d1[i] = b[g].d;
+            A.d2[i] = b[g].s;
+        }
     }
     if (lane == 0) {
-        atomicAdd(A.counters, scanned);
-        if (incomplete) {
-            unsigned long long t = atomicAdd(A.fb_count, 1ull);
-            A.fb_list[t] = i;
-        }
-        A.idx[i] = b.j;
-        A.d1[i] = b.d;
-        A.d2[i] = b.s;
+        atomicAdd(A.counters, evals);
+        atomicAdd(A.counters + 5, read);
     }
 }
 
@@ -1092,7 +1199,8 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
     A.touched = touched;
     if (two) {
         Probe2Args P2{A, a.cent, a.rad1, a.L1, a.L2, a.r1max};
-        k_ann_probe2<<<(unsigned)((m * 32 + 255) / 256), 256, 0, s>>>(P2);
+        const int64_t warps = (m + kGrp - 1) / kGrp;
+        k_ann_probe2<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(P2);
     } else {
         k_ann_probe<<<(unsigned)((m * 32 + 255) / 256), 256, 0, s>>>(A);
     }
@@ -1117,18 +1225,18 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
         DD_TRY_CUDA(ctx, cudaGetLastError());
     }
     if (st && ctx->defer) {
-        DD_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->defer->ann, counters, 5 * sizeof(unsigned long long),
+        DD_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->defer->ann, counters, 6 * sizeof(unsigned long long),
                                          cudaMemcpyDeviceToDevice, s));
         st->distances += m * (int64_t)(two ? a.L1 : a.nlist);
     } else if (st) {
-        unsigned long long h[5];
+        unsigned long long h[6];
         DD_TRY_CUDA(ctx, cudaMemcpyAsync(h, counters, sizeof(h), cudaMemcpyDeviceToHost, s));
         DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
         float ms = 0.f;
         DD_TRY_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev_scan[0], ctx->ev_scan[1]));
         st->scan_ms += ms;
         st->distances += (int64_t)h[0] + (int64_t)h[3] + m * (int64_t)(two ? a.L1 : a.nlist) + (int64_t)n_fb * ds->N;
-        st->points += (int64_t)h[0] + (int64_t)n_fb * ds->N;
+        st->points += (int64_t)h[5] + (int64_t)n_fb * ds->N;
         st->unique_points += n_fb ? ds->N : (int64_t)h[4];
         st->skipped += (int64_t)h[1];
         st->uncertified += (int64_t)n_fb;

@@ -1202,7 +1202,7 @@ void finish_step(dd_solver **svs, int n, const double *hs, const int *its, dd_se
         sst.scan_ms += elapsed(ctx->ev_scan[0], ctx->ev_scan[1]);
         sst.uncertified += (int64_t)(dfr->fb + dfr->ann[2]);
         sst.distances += (int64_t)dfr->fb * N + (int64_t)dfr->ann[0] + (int64_t)dfr->ann[3] + (int64_t)dfr->ann[2] * N;
-        sst.points += (int64_t)dfr->ann[0] + (int64_t)dfr->ann[2] * N;
+        sst.points += (int64_t)dfr->ann[5] + (int64_t)dfr->ann[2] * N;
         sst.unique_points += dfr->ann[2] ? N : (int64_t)dfr->ann[4];
         sst.skipped += (int64_t)dfr->ann[1];
     }

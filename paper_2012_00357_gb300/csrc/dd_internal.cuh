@@ -74,8 +74,8 @@ struct Workspace {
 // reads them after the step.
 struct DeferredStats {
     unsigned long long fb;       // exact search: queries re-searched in FP64
-    unsigned long long ann[5];   // approximate search: points scanned, skipped, exact re-search, fine
-                                 // centroids, distinct points scanned
+    unsigned long long ann[6];   // approximate search: point distances, skipped, exact re-search, fine
+                                 // centroids, distinct points, points read
 };
 
 struct StepPlan;
