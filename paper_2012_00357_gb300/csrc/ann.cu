@@ -534,7 +534,7 @@ __device__ __forceinline__ float warp_minf(float v) {
 // points at a time and updates its own best of every query (the queries sit
 // in shared memory and are read as broadcasts).
 __device__ __forceinline__ void scan_leaf_grp(const float *zs, const int32_t *perm, int64_t p0, int64_t p1, int lane,
-                                              const float *sq, int ng, Best (&b)[kGrp]) {
+                                              const float *sq, int ng, unsigned mask, Best (&b)[kGrp]) {
     for (int64_t p = p0 + lane; p < p1; p += 64) {
         const bool two = p + 32 < p1;
         const float4 *y0 = reinterpret_cast<const float4 *>(zs + p * 12);
@@ -544,6 +544,7 @@ __device__ __forceinline__ void scan_leaf_grp(const float *zs, const int32_t *pe
 #pragma unroll
         for (int g = 0; g < kGrp; ++g) {
             if (g >= ng) break;
+            if (!((mask >> g) & 1u)) continue;
             const float4 *qq = reinterpret_cast<const float4 *>(sq + g * 12);
             const float4 q0 = qq[0], q1 = qq[1], q2 = qq[2];
             float t, d0 = 0.f, d1 = 0.f;
@@ -647,10 +648,25 @@ __global__ void __launch_bounds__(256) k_ann_probe2(Probe2Args P) {
             }
             ++nrem;
         }
+        // queries for which the leaf can hold a nearer point: its centroid
+        // distance minus its radius below their d_c (lane g decides for g)
+        bool want = false;
+        if (lane < ng && !((skipmask >> lane) & 1u)) {
+            float q[12];
+#pragma unroll
+            for (int k = 0; k < 12; ++k) q[k] = sq[lane * 12 + k];
+            float dg = 0.f;
+#pragma unroll
+            for (int k = 0; k < kGrp; ++k)
+                if (k == lane) dg = dc[k];
+            want = sqrtf(dist2_12(P.centf + (size_t)l * 12, q)) - A.radius[l] < dg;
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, want);
+        if (!mask) return;
         const int64_t p0 = A.offs[l], p1 = A.offs[l + 1];
-        scan_leaf_grp(A.zs, A.perm, p0, p1, lane, sq, ng, b);
+        scan_leaf_grp(A.zs, A.perm, p0, p1, lane, sq, ng, mask, b);
         read += (unsigned long long)(p1 - p0);
-        evals += (unsigned long long)(p1 - p0) * (unsigned long long)ng;
+        evals += (unsigned long long)(p1 - p0) * (unsigned long long)__popc(mask);
         if (lane == 0) atomicOr(A.touched + (l >> 5), 1u << (l & 31));
 #pragma unroll
         for (int g = 0; g < kGrp; ++g) dc[g] = sqrtf(warp_minf(b[g].d));
