@@ -637,32 +637,57 @@ __global__ void __launch_bounds__(256) k_ann_probe2(Probe2Args P) {
         b[g].s = INFINITY;
         dc[g] = sqrtf(b[g].d);
     }
-    int rem0 = -1, rem1 = -1, nrem = 0;   // leaves scanned so far (lane k: entries k and k + 32)
+    // leaves scanned so far and the queries each was evaluated for
+    // (lane k holds entries k and k + 32)
+    int rem0 = -1, rem1 = -1, nrem = 0;
+    unsigned msk0 = 0, msk1 = 0;
     unsigned long long read = 0, evals = 0;
-    auto scan_new = [&](int l) {
-        if (__any_sync(0xffffffffu, rem0 == l || rem1 == l)) return;
-        if (nrem < kRemember) {
-            if (lane == (nrem & 31)) {
-                if (nrem < 32) rem0 = l;
-                else rem1 = l;
+    // Evaluate leaf l for the queries whose own Eq. (13) test passes with
+    // their current d_c, and for the queries in `forced` (the one that
+    // selected it as its first leaf, or whose warm start lies in it).  A
+    // query left out fails its test now and, since d_c only decreases, later
+    // too; only a forced query can need a remembered leaf again.
+    auto scan_new = [&](int l, unsigned forced) {
+        const bool h0 = rem0 == l, h1 = rem1 == l;
+        const unsigned hit = __ballot_sync(0xffffffffu, h0 || h1);
+        unsigned mask;
+        if (hit) {
+            const int src = __ffs(hit) - 1;
+            const unsigned prev = __shfl_sync(0xffffffffu, h0 ? msk0 : msk1, src);
+            mask = forced & ~prev;
+            if (!mask) return;
+            if (lane == src) {
+                if (h0) msk0 |= mask;
+                else msk1 |= mask;
             }
-            ++nrem;
-        }
-        // queries for which the leaf can hold a nearer point: its centroid
-        // distance minus its radius below their d_c (lane g decides for g)
-        bool want = false;
-        if (lane < ng && !((skipmask >> lane) & 1u)) {
-            float q[12];
+        } else {
+            bool want = false;
+            if (lane < ng && !((skipmask >> lane) & 1u)) {
+                float q[12];
 #pragma unroll
-            for (int k = 0; k < 12; ++k) q[k] = sq[lane * 12 + k];
-            float dg = 0.f;
+                for (int k = 0; k < 12; ++k) q[k] = sq[lane * 12 + k];
+                float dg = 0.f;
 #pragma unroll
-            for (int k = 0; k < kGrp; ++k)
-                if (k == lane) dg = dc[k];
-            want = sqrtf(dist2_12(P.centf + (size_t)l * 12, q)) - A.radius[l] < dg;
+                for (int k = 0; k < kGrp; ++k)
+                    if (k == lane) dg = dc[k];
+                const float fdl = A.fd_q ? A.fd_q[i0 + lane] : A.f_d;
+                want = sqrtf(dist2_12(P.centf + (size_t)l * 12, q)) - fdl * A.radius[l] < dg;
+            }
+            mask = (__ballot_sync(0xffffffffu, want) | forced) & ~skipmask;
+            if (nrem < kRemember) {
+                if (lane == (nrem & 31)) {
+                    if (nrem < 32) {
+                        rem0 = l;
+                        msk0 = mask;
+                    } else {
+                        rem1 = l;
+                        msk1 = mask;
+                    }
+                }
+                ++nrem;
+            }
+            if (!mask) return;
         }
-        const unsigned mask = __ballot_sync(0xffffffffu, want);
-        if (!mask) return;
         const int64_t p0 = A.offs[l], p1 = A.offs[l + 1];
         scan_leaf_grp(A.zs, A.perm, p0, p1, lane, sq, ng, mask, b);
         read += (unsigned long long)(p1 - p0);
@@ -671,9 +696,15 @@ __global__ void __launch_bounds__(256) k_ann_probe2(Probe2Args P) {
 #pragma unroll
         for (int g = 0; g < kGrp; ++g) dc[g] = sqrtf(warp_minf(b[g].d));
     };
-    for (int g = 0; g < ng; ++g) {
-        const int lg = __shfl_sync(0xffffffffu, l0, g);
-        if (!((skipmask >> g) & 1u) && lg >= 0) scan_new(lg);
+    {   // warm-start leaves, each read once for the queries whose warm start it holds
+        unsigned todo = __ballot_sync(0xffffffffu, lane < ng && l0 >= 0) & ~skipmask;
+        while (todo) {
+            const int g = __ffs(todo) - 1;
+            const int lg = __shfl_sync(0xffffffffu, l0, g);
+            const unsigned same = __ballot_sync(0xffffffffu, lane < ng && l0 == lg) & todo;
+            scan_new(lg, same);
+            todo &= ~same;
+        }
     }
     unsigned incomplete = 0;
     for (int g = 0; g < ng; ++g) {
@@ -722,8 +753,9 @@ __global__ void __launch_bounds__(256) k_ann_probe2(Probe2Args P) {
                 if (!(md < INFINITY)) break;
                 if ((ml & 31) == lane) vis |= 1u << (ml >> 5);
                 const int l = C * P.L2 + ml;
-                if ((k1 == 0 && k2 == 0) || md - f_d * A.radius[l] < dcg) {
-                    scan_new(l);
+                const bool first = k1 == 0 && k2 == 0;
+                if (first || md - f_d * A.radius[l] < dcg) {
+                    scan_new(l, first ? 1u << g : 0u);
 #pragma unroll
                     for (int k = 0; k < kGrp; ++k)
                         if (k == g) dcg = dc[k];
