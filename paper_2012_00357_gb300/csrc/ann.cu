@@ -520,52 +520,6 @@ __global__ void k_radius_orig(const float *__restrict__ z, const int32_t *__rest
     atomicMax(rbits + c, __float_as_uint(d * 1.000001f + 1e-30f));
 }
 
-constexpr int kFine = 8;        // leaves visited per cell at most
-constexpr int kFinePerLane = 16;   // L2 <= 512
-constexpr int kGrp = 8;         // queries per warp: the Gauss points of one element
-constexpr int kRemember = 64;   // leaves a warp remembers as scanned
-
-__device__ __forceinline__ float warp_minf(float v) {
-    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
-// Scan one leaf for every query of the warp's group: each lane reads two
-// points at a time and updates its own best of every query (the queries sit
-// in shared memory and are read as broadcasts).
-__device__ __forceinline__ void scan_leaf_grp(const float *zs, const int32_t *perm, int64_t p0, int64_t p1, int lane,
-                                              const float *sq, int ng, unsigned mask, Best (&b)[kGrp]) {
-    for (int64_t p = p0 + lane; p < p1; p += 64) {
-        const bool two = p + 32 < p1;
-        const float4 *y0 = reinterpret_cast<const float4 *>(zs + p * 12);
-        const float4 *y1 = reinterpret_cast<const float4 *>(zs + (two ? p + 32 : p) * 12);
-        const float4 a0 = __ldg(y0), a1 = __ldg(y0 + 1), a2 = __ldg(y0 + 2);
-        const float4 c0 = __ldg(y1), c1 = __ldg(y1 + 1), c2 = __ldg(y1 + 2);
-#pragma unroll
-        for (int g = 0; g < kGrp; ++g) {
-            if (g >= ng) break;
-            if (!((mask >> g) & 1u)) continue;
-            const float4 *qq = reinterpret_cast<const float4 *>(sq + g * 12);
-            const float4 q0 = qq[0], q1 = qq[1], q2 = qq[2];
-            float t, d0 = 0.f, d1 = 0.f;
-            t = a0.x - q0.x; d0 = fmaf(t, t, d0); t = c0.x - q0.x; d1 = fmaf(t, t, d1);
-            t = a0.y - q0.y; d0 = fmaf(t, t, d0); t = c0.y - q0.y; d1 = fmaf(t, t, d1);
-            t = a0.z - q0.z; d0 = fmaf(t, t, d0); t = c0.z - q0.z; d1 = fmaf(t, t, d1);
-            t = a0.w - q0.w; d0 = fmaf(t, t, d0); t = c0.w - q0.w; d1 = fmaf(t, t, d1);
-            t = a1.x - q1.x; d0 = fmaf(t, t, d0); t = c1.x - q1.x; d1 = fmaf(t, t, d1);
-            t = a1.y - q1.y; d0 = fmaf(t, t, d0); t = c1.y - q1.y; d1 = fmaf(t, t, d1);
-            t = a1.z - q1.z; d0 = fmaf(t, t, d0); t = c1.z - q1.z; d1 = fmaf(t, t, d1);
-            t = a1.w - q1.w; d0 = fmaf(t, t, d0); t = c1.w - q1.w; d1 = fmaf(t, t, d1);
-            t = a2.x - q2.x; d0 = fmaf(t, t, d0); t = c2.x - q2.x; d1 = fmaf(t, t, d1);
-            t = a2.y - q2.y; d0 = fmaf(t, t, d0); t = c2.y - q2.y; d1 = fmaf(t, t, d1);
-            t = a2.z - q2.z; d0 = fmaf(t, t, d0); t = c2.z - q2.z; d1 = fmaf(t, t, d1);
-            t = a2.w - q2.w; d0 = fmaf(t, t, d0); t = c2.w - q2.w; d1 = fmaf(t, t, d1);
-            best_lazy(b[g], d0, perm, p);
-            if (two) best_lazy(b[g], d1, perm, p + 32);
-        }
-    }
-}
-
 struct Probe2Args {
     ProbeArgs A;                // leaves in A.radius / A.offs / A.zs / A.perm / A.cluster_of; cand_* are coarse cells
     const float *centf;         // [L x 12] leaf centroids
@@ -574,227 +528,126 @@ struct Probe2Args {
     float r1max;
 };
 
-// Tree search of Sec. 4 for the queries of one element per warp (its 8
-// Gauss points, consecutive in the query order, whose states are close).
-// Every query keeps its own warm start (Sec. 4.5), its own ranking of the
-// coarse cells and of their leaves, and its own Eq. (13) tests with its own
-// d_c; a leaf that any of them decides to scan is read once and evaluated
-// for all of them, and a leaf the warp has already scanned is not read
-// again.  A query therefore evaluates at least the points its own rules
-// select, and its answer can only be as near or nearer.
+constexpr int kFine = 8;        // leaves visited per cell at most
+constexpr int kFinePerLane = 16;   // L2 <= 512
+
 __global__ void __launch_bounds__(256) k_ann_probe2(Probe2Args P) {
     const ProbeArgs &A = P.A;
-    __shared__ __align__(16) float s_q[8][kGrp * 12];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int64_t i0 = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * kGrp;
-    const int ng = A.m - i0 < kGrp ? (int)(A.m - i0) : kGrp;
-    float *sq = s_q[wib];
-    if (ng > 0)
-        for (int k = lane; k < ng * 12; k += 32) sq[k] = A.rec[i0 + k / 12].q[k % 12];
-    __syncwarp();
-    if (ng <= 0) return;
-    // warm start and Eq. (14), lane g for query g
-    float d0 = INFINITY;
-    int j0 = 0x7fffffff, l0 = -1;
-    bool skip = false;
-    if (lane < ng && A.prev) {
-        const int64_t i = i0 + lane;
-        const int jp = A.prev[i];
-        if (jp >= 0 && jp < A.N) {
-            float q[12];
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (i >= A.m) return;
+    float q[12];
 #pragma unroll
-            for (int k = 0; k < 12; ++k) q[k] = sq[lane * 12 + k];
-            d0 = dist2_12(A.z32 + (size_t)jp * 12, q);
-            j0 = jp;
-            l0 = A.cluster_of[jp];
+    for (int k = 0; k < 12; ++k) q[k] = A.rec[i].q[k];
+    Best b{INFINITY, 0x7fffffff, INFINITY};
+    int l0 = -1;
+    unsigned long long scanned = 0;
+    if (A.prev) {
+        const int j0 = A.prev[i];
+        if (j0 >= 0 && j0 < A.N) {
+            const float d0 = dist2_12(A.z32 + (size_t)j0 * 12, q);
             if (A.mot_q) {
                 float mv = 0.f;
 #pragma unroll
                 for (int k = 0; k < 12; ++k) {
-                    const float t = q[k] - A.mot_q[i * 12 + k];
+                    float t = q[k] - A.mot_q[i * 12 + k];
                     mv = fmaf(t, t, mv);
                 }
                 mv = sqrtf(mv);
                 const float r1 = A.mot_d[i * 2], r2 = A.mot_d[i * 2 + 1];
-                if (mv < 0.5f * (r2 - r1)) {
-                    skip = true;
-                    A.idx[i] = jp;
-                    A.d1[i] = d0;
-                    const float lb = fmaxf(r2 - mv, 0.f);
-                    A.d2[i] = lb * lb;
-                    atomicAdd(A.counters + 1, 1ull);
-                }
-            }
-        }
-    }
-    const unsigned skipmask = __ballot_sync(0xffffffffu, skip);
-    Best b[kGrp];
-    float dc[kGrp];
-#pragma unroll
-    for (int g = 0; g < kGrp; ++g) {
-        b[g].d = __shfl_sync(0xffffffffu, d0, g);
-        b[g].j = __shfl_sync(0xffffffffu, j0, g);
-        b[g].s = INFINITY;
-        dc[g] = sqrtf(b[g].d);
-    }
-    // leaves scanned so far and the queries each was evaluated for
-    // (lane k holds entries k and k + 32)
-    int rem0 = -1, rem1 = -1, nrem = 0;
-    unsigned msk0 = 0, msk1 = 0;
-    unsigned long long read = 0, evals = 0;
-    // Evaluate leaf l for the queries whose own Eq. (13) test passes with
-    // their current d_c, and for the queries in `forced` (the one that
-    // selected it as its first leaf, or whose warm start lies in it).  A
-    // query left out fails its test now and, since d_c only decreases, later
-    // too; only a forced query can need a remembered leaf again.
-    auto scan_new = [&](int l, unsigned forced) {
-        const bool h0 = rem0 == l, h1 = rem1 == l;
-        const unsigned hit = __ballot_sync(0xffffffffu, h0 || h1);
-        unsigned mask;
-        if (hit) {
-            const int src = __ffs(hit) - 1;
-            const unsigned prev = __shfl_sync(0xffffffffu, h0 ? msk0 : msk1, src);
-            mask = forced & ~prev;
-            if (!mask) return;
-            if (lane == src) {
-                if (h0) msk0 |= mask;
-                else msk1 |= mask;
-            }
-        } else {
-            bool want = false;
-            if (lane < ng && !((skipmask >> lane) & 1u)) {
-                float q[12];
-#pragma unroll
-                for (int k = 0; k < 12; ++k) q[k] = sq[lane * 12 + k];
-                float dg = 0.f;
-#pragma unroll
-                for (int k = 0; k < kGrp; ++k)
-                    if (k == lane) dg = dc[k];
-                const float fdl = A.fd_q ? A.fd_q[i0 + lane] : A.f_d;
-                want = sqrtf(dist2_12(P.centf + (size_t)l * 12, q)) - fdl * A.radius[l] < dg;
-            }
-            mask = (__ballot_sync(0xffffffffu, want) | forced) & ~skipmask;
-            if (nrem < kRemember) {
-                if (lane == (nrem & 31)) {
-                    if (nrem < 32) {
-                        rem0 = l;
-                        msk0 = mask;
-                    } else {
-                        rem1 = l;
-                        msk1 = mask;
+                if (mv < 0.5f * (r2 - r1)) {      // Eq. (14)
+                    if (lane == 0) {
+                        A.idx[i] = j0;
+                        A.d1[i] = d0;
+                        float lb = fmaxf(r2 - mv, 0.f);
+                        A.d2[i] = lb * lb;
+                        atomicAdd(A.counters + 1, 1ull);
                     }
+                    return;
                 }
-                ++nrem;
             }
-            if (!mask) return;
+            b.d = d0;
+            b.j = j0;
+            l0 = A.cluster_of[j0];
         }
+    }
+    auto scan = [&](int l) {
         const int64_t p0 = A.offs[l], p1 = A.offs[l + 1];
-        scan_leaf_grp(A.zs, A.perm, p0, p1, lane, sq, ng, mask, b);
-        read += (unsigned long long)(p1 - p0);
-        evals += (unsigned long long)(p1 - p0) * (unsigned long long)__popc(mask);
+        scan_range(A.zs, A.perm, p0, p1, lane, q, b);
+        scanned += (unsigned long long)(p1 - p0);
         if (lane == 0) atomicOr(A.touched + (l >> 5), 1u << (l & 31));
-#pragma unroll
-        for (int g = 0; g < kGrp; ++g) dc[g] = sqrtf(warp_minf(b[g].d));
+        best_warp(b);
     };
-    {   // warm-start leaves, each read once for the queries whose warm start it holds
-        unsigned todo = __ballot_sync(0xffffffffu, lane < ng && l0 >= 0) & ~skipmask;
-        while (todo) {
-            const int g = __ffs(todo) - 1;
-            const int lg = __shfl_sync(0xffffffffu, l0, g);
-            const unsigned same = __ballot_sync(0xffffffffu, lane < ng && l0 == lg) & todo;
-            scan_new(lg, same);
-            todo &= ~same;
+    if (l0 >= 0) scan(l0);
+    float dc = sqrtf(b.d);
+    const float f_d = A.fd_q ? A.fd_q[i] : A.f_d;
+    bool incomplete = false;
+    for (int k1 = 0; k1 < kCand; ++k1) {
+        const int C = A.cand_cl[i * kCand + k1];
+        if (C < 0) break;
+        const float dC = A.cand_d[i * kCand + k1];
+        if (!(k1 == 0 || dC - f_d * P.rad1[C] < dc)) continue;
+        // rank the cell's leaves: lane holds leaves f = lane + 32 t
+        float fd[kFinePerLane];
+        unsigned vis = 0;
+#pragma unroll
+        for (int t = 0; t < kFinePerLane; ++t) {
+            const int f = lane + 32 * t;
+            fd[t] = (f < P.L2) ? sqrtf(dist2_12(P.centf + ((size_t)C * P.L2 + f) * 12, q)) : INFINITY;
         }
-    }
-    unsigned incomplete = 0;
-    for (int g = 0; g < ng; ++g) {
-        if ((skipmask >> g) & 1u) continue;
-        const int64_t i = i0 + g;
-        const float f_d = A.fd_q ? A.fd_q[i] : A.f_d;
-        float q[12];
+        if (lane == 0) atomicAdd(A.counters + 3, (unsigned long long)P.L2);
+        for (int k2 = 0; k2 < kFine; ++k2) {
+            float md = INFINITY;
+            int mt = -1;
 #pragma unroll
-        for (int k = 0; k < 12; ++k) q[k] = sq[g * 12 + k];
-        float dcg = 0.f;
-#pragma unroll
-        for (int k = 0; k < kGrp; ++k)
-            if (k == g) dcg = dc[k];
-        for (int k1 = 0; k1 < kCand; ++k1) {
-            const int C = A.cand_cl[i * kCand + k1];
-            if (C < 0) break;
-            const float dC = A.cand_d[i * kCand + k1];
-            if (!(k1 == 0 || dC - f_d * P.rad1[C] < dcg)) continue;
-            // rank the cell's leaves for this query: lane holds leaves f = lane + 32 t
-            float fd[kFinePerLane];
-            unsigned vis = 0;
-#pragma unroll
-            for (int t = 0; t < kFinePerLane; ++t) {
-                const int f = lane + 32 * t;
-                fd[t] = (f < P.L2) ? sqrtf(dist2_12(P.centf + ((size_t)C * P.L2 + f) * 12, q)) : INFINITY;
-            }
-            if (lane == 0) atomicAdd(A.counters + 3, (unsigned long long)P.L2);
-            for (int k2 = 0; k2 < kFine; ++k2) {
-                float md = INFINITY;
-                int mt = -1;
-#pragma unroll
-                for (int t = 0; t < kFinePerLane; ++t)
-                    if (!((vis >> t) & 1u) && fd[t] < md) {
-                        md = fd[t];
-                        mt = t;
-                    }
-                int ml = mt >= 0 ? lane + 32 * mt : 0x7fffffff;
-                for (int o = 16; o > 0; o >>= 1) {
-                    const float od = __shfl_xor_sync(0xffffffffu, md, o);
-                    const int ol = __shfl_xor_sync(0xffffffffu, ml, o);
-                    if (od < md || (od == md && ol < ml)) {
-                        md = od;
-                        ml = ol;
-                    }
+            for (int t = 0; t < kFinePerLane; ++t)
+                if (!((vis >> t) & 1u) && fd[t] < md) {
+                    md = fd[t];
+                    mt = t;
                 }
-                if (!(md < INFINITY)) break;
-                if ((ml & 31) == lane) vis |= 1u << (ml >> 5);
-                const int l = C * P.L2 + ml;
-                const bool first = k1 == 0 && k2 == 0;
-                if (first || md - f_d * A.radius[l] < dcg) {
-                    scan_new(l, first ? 1u << g : 0u);
-#pragma unroll
-                    for (int k = 0; k < kGrp; ++k)
-                        if (k == g) dcg = dc[k];
+            int ml = mt >= 0 ? lane + 32 * mt : 0x7fffffff;
+            for (int o = 16; o > 0; o >>= 1) {
+                float od = __shfl_xor_sync(0xffffffffu, md, o);
+                int ol = __shfl_xor_sync(0xffffffffu, ml, o);
+                if (od < md || (od == md && ol < ml)) {
+                    md = od;
+                    ml = ol;
                 }
             }
-            // leaves of this cell beyond the kFine nearest (exact requests only)
-            if (f_d >= 1.0f && P.L2 > kFine) {
-                float md = INFINITY;
-#pragma unroll
-                for (int t = 0; t < kFinePerLane; ++t)
-                    if (!((vis >> t) & 1u)) md = fminf(md, fd[t]);
-                md = warp_minf(md);
-                if (md - f_d * A.rmax < dcg) incomplete |= 1u << g;
+            if (!(md < INFINITY)) break;
+            if ((ml & 31) == lane) vis |= 1u << (ml >> 5);
+            const int l = C * P.L2 + ml;
+            if ((k1 == 0 && k2 == 0) || md - f_d * A.radius[l] < dc) {
+                if (l != l0) {
+                    scan(l);
+                    dc = sqrtf(b.d);
+                }
             }
         }
-        if (f_d >= 1.0f && P.L1 > kCand) {
-            const float dP = A.cand_d[i * kCand + kCand - 1];
-            if (dP - f_d * P.r1max < dcg) incomplete |= 1u << g;
+        // leaves of this cell beyond the kFine nearest (exact requests only)
+        if (f_d >= 1.0f && P.L2 > kFine) {
+            float md = INFINITY;
+#pragma unroll
+            for (int t = 0; t < kFinePerLane; ++t)
+                if (!((vis >> t) & 1u)) md = fminf(md, fd[t]);
+            for (int o = 16; o > 0; o >>= 1) md = fminf(md, __shfl_xor_sync(0xffffffffu, md, o));
+            if (md - f_d * A.rmax < dc) incomplete = true;
         }
     }
-    // merge every query's best over the lanes and write the answers
-#pragma unroll
-    for (int g = 0; g < kGrp; ++g) {
-        if (g >= ng) break;
-        best_warp(b[g]);
-        if (lane == g && !((skipmask >> g) & 1u)) {
-            const int64_t i = i0 + g;
-            if ((incomplete >> g) & 1u) {
-                const unsigned long long t = atomicAdd(A.fb_count, 1ull);
-                A.fb_list[t] = i;
-            }
-            A.idx[i] = b[g].j;
-            A.d1[i] = b[g].d;
-            A.d2[i] = b[g].s;
-        }
+    if (f_d >= 1.0f && P.L1 > kCand) {
+        const float dP = A.cand_d[i * kCand + kCand - 1];
+        if (dP - f_d * P.r1max < dc) incomplete = true;
     }
     if (lane == 0) {
-        atomicAdd(A.counters, evals);
-        atomicAdd(A.counters + 5, read);
+        atomicAdd(A.counters, scanned);
+        atomicAdd(A.counters + 5, scanned);
+        if (incomplete) {
+            unsigned long long t = atomicAdd(A.fb_count, 1ull);
+            A.fb_list[t] = i;
+        }
+        A.idx[i] = b.j;
+        A.d1[i] = b.d;
+        A.d2[i] = b.s;
     }
 }
 
@@ -1247,8 +1100,7 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
     A.touched = touched;
     if (two) {
         Probe2Args P2{A, a.cent, a.rad1, a.L1, a.L2, a.r1max};
-        const int64_t warps = (m + kGrp - 1) / kGrp;
-        k_ann_probe2<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(P2);
+        k_ann_probe2<<<(unsigned)((m * 32 + 255) / 256), 256, 0, s>>>(P2);
     } else {
         k_ann_probe<<<(unsigned)((m * 32 + 255) / 256), 256, 0, s>>>(A);
     }
