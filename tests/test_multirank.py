@@ -75,3 +75,37 @@ def test_reference_arm_rank0_only():
     real = [l for l in lines if l is not None]
     assert len(real) == 1 and real[0]["impl"] == "reference" and real[0]["value"] > 0
     assert real[0]["e2e"]["h2d_bytes_per_step"] == 0
+
+
+SHARD_WORKER = r"""
+import os, sys, json
+sys.path.insert(0, {root!r})
+import numpy as np
+import torch.distributed as dist
+import dd_inputs as I
+from oracle import metric, nn
+from paper_2012_00357_gb300.shard import merge_nearest
+dist.init_process_group("gloo", init_method="env://")
+rank, world = dist.get_rank(), dist.get_world_size()
+C = I.isotropic_C()
+data = I.make_dataset(3001, I.NONLINEAR, seed=12)
+y = I.make_states(257, I.NONLINEAR, seed=13, spread=0.05)
+zq = metric.to_z(y, C)
+bounds = np.linspace(0, len(data), world + 1).astype(int)
+lo, hi = bounds[rank], bounds[rank + 1]
+i1, d1, _, _ = nn.nn_top2(metric.to_z(data[lo:hi].astype(np.float64), C), zq)
+d, g = merge_nearest(d1, i1, lo)
+f1, fd, _, _ = nn.nn_top2(metric.to_z(data.astype(np.float64), C), zq)
+print(json.dumps({{"same_index": bool(np.array_equal(g.numpy(), f1)), "same_d2": bool(np.array_equal(d.numpy(), fd))}}))
+dist.destroy_process_group()
+"""
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_search_merge_equals_unsharded(world):
+    """The data set split over ranks, each searched alone (oracle scan), and
+    the per-query min-loc merge give exactly the unsharded exact answer."""
+    outs = run_ranks(SHARD_WORKER.format(root=ROOT), world=world)
+    for o in outs:
+        r = json.loads(o.strip().splitlines()[-1])
+        assert r["same_index"] and r["same_d2"]
