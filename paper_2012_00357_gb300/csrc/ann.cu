@@ -172,6 +172,86 @@ __global__ void k_radius(const float *__restrict__ zs, const int32_t *__restrict
 // ---------------------------------------------------------------------------
 // Merge the top-k lists of the centroid scan; keep the kCand nearest
 // centroids by exact FP32 distance (ties to the lower centroid index).
+// Nearest kCand centroids of every query when the centroid set is small:
+// one thread per query, centroids staged in shared memory and read as
+// broadcasts; top kCand by the expanded FP32 score |c|^2 - 2 c.q (ties to
+// the lower index), then ordered by the FP32 distance as from k_ann_cands.
+constexpr int kRankTile = 896;      // 896 x 52 B of static shared memory (< 48 KB)
+constexpr int kRankMax = 4096;    // larger sets go through the tiled FP32 scan
+
+__global__ void __launch_bounds__(256) k_rank_small(const QueryRec *__restrict__ rec, int64_t m,
+                                                    const float *__restrict__ cent, const float *__restrict__ cn,
+                                                    int L, int32_t *__restrict__ out_cl, float *__restrict__ out_d) {
+    __shared__ __align__(16) float sc[kRankTile * 12];
+    __shared__ float sn[kRankTile];
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool act = i < m;
+    float q[12], qm2[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        q[k] = act ? rec[i].q[k] : 0.f;
+        qm2[k] = -2.f * q[k];
+    }
+    float bs[kCand];
+    int bc[kCand];
+#pragma unroll
+    for (int k = 0; k < kCand; ++k) {
+        bs[k] = INFINITY;
+        bc[k] = -1;
+    }
+    for (int t0 = 0; t0 < L; t0 += kRankTile) {
+        const int nt = min(kRankTile, L - t0);
+        __syncthreads();
+        for (int k = threadIdx.x; k < nt * 12; k += blockDim.x) sc[k] = cent[(size_t)t0 * 12 + k];
+        for (int k = threadIdx.x; k < nt; k += blockDim.x) sn[k] = cn[t0 + k];
+        __syncthreads();
+        if (!act) continue;
+        for (int f = 0; f < nt; ++f) {
+            const float4 *pc = reinterpret_cast<const float4 *>(sc + f * 12);
+            const float4 a = pc[0], b = pc[1], d = pc[2];
+            float v = sn[f];
+            v = fmaf(qm2[0], a.x, v); v = fmaf(qm2[1], a.y, v); v = fmaf(qm2[2], a.z, v); v = fmaf(qm2[3], a.w, v);
+            v = fmaf(qm2[4], b.x, v); v = fmaf(qm2[5], b.y, v); v = fmaf(qm2[6], b.z, v); v = fmaf(qm2[7], b.w, v);
+            v = fmaf(qm2[8], d.x, v); v = fmaf(qm2[9], d.y, v); v = fmaf(qm2[10], d.z, v); v = fmaf(qm2[11], d.w, v);
+            if (v < bs[kCand - 1]) {
+                bs[kCand - 1] = v;
+                bc[kCand - 1] = t0 + f;
+#pragma unroll
+                for (int k = kCand - 1; k > 0; --k)
+                    if (bs[k] < bs[k - 1]) {
+                        const float tv = bs[k];
+                        bs[k] = bs[k - 1];
+                        bs[k - 1] = tv;
+                        const int tc = bc[k];
+                        bc[k] = bc[k - 1];
+                        bc[k - 1] = tc;
+                    }
+            }
+        }
+    }
+    if (!act) return;
+    float bd[kCand];
+#pragma unroll
+    for (int k = 0; k < kCand; ++k) bd[k] = bc[k] >= 0 ? dist2_12(cent + (size_t)bc[k] * 12, q) : INFINITY;
+#pragma unroll
+    for (int r = 1; r < kCand; ++r)       // insertion sort by (distance, index)
+#pragma unroll
+        for (int k = r; k > 0; --k)
+            if (bd[k] < bd[k - 1] || (bd[k] == bd[k - 1] && bc[k] >= 0 && bc[k] < bc[k - 1])) {
+                const float tv = bd[k];
+                bd[k] = bd[k - 1];
+                bd[k - 1] = tv;
+                const int tc = bc[k];
+                bc[k] = bc[k - 1];
+                bc[k - 1] = tc;
+            }
+#pragma unroll
+    for (int k = 0; k < kCand; ++k) {
+        out_cl[i * kCand + k] = bc[k];
+        out_d[i * kCand + k] = sqrtf(bd[k]);
+    }
+}
+
 __global__ void k_ann_cands(const CandHeader *__restrict__ hdr, const float2 *__restrict__ cand, int splits, int cap,
                             const QueryRec *__restrict__ rec, int64_t m, const float *__restrict__ cent,
                             int32_t *__restrict__ out_cl, float *__restrict__ out_d) {
@@ -1067,11 +1147,18 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
     if (st) DD_TRY_CUDA(ctx, dd_event_record(ctx, ctx->ev_scan[0], s));
     const bool two = a.levels == 2;
     const float *rank_cent = two ? a.cent1 : a.cent;
-    DD_TRY(dd_scan_fp32_raw(ctx, rank_cent, two ? a.cn1 : a.cn, two ? a.L1 : a.nlist, rec, m, true, WS_ANN_SCAN,
-                            &splits, &cap, &hdr, &cand, s));
-    ctx->launches += 3;
-    k_ann_cands<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(hdr, cand, splits, cap, rec, m, rank_cent, cand_cl,
-                                                            cand_d);
+    const int Lr = two ? a.L1 : a.nlist;
+    if (Lr <= kRankMax) {
+        ctx->launches += 2;
+        k_rank_small<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(rec, m, rank_cent, two ? a.cn1 : a.cn, Lr, cand_cl,
+                                                                 cand_d);
+    } else {
+        DD_TRY(dd_scan_fp32_raw(ctx, rank_cent, two ? a.cn1 : a.cn, Lr, rec, m, true, WS_ANN_SCAN, &splits, &cap,
+                                &hdr, &cand, s));
+        ctx->launches += 3;
+        k_ann_cands<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(hdr, cand, splits, cap, rec, m, rank_cent, cand_cl,
+                                                                cand_d);
+    }
     ProbeArgs A;
     A.zs = a.zs;
     A.perm = a.perm;

@@ -378,25 +378,46 @@ __global__ void k_recover(MeshDev g, ElemOps ops, MetricMaps M, const double *__
     dpc[e] = 0.5 * g.w * d;
 }
 
-// Iteration statistics in one block, fixed order: changed associations,
-// sum_e 1/2 w d_e^2 after P_D, sum after P_C.
-__global__ void __launch_bounds__(1024) k_iter_stats(const int32_t *__restrict__ idx_new,
-                                                     const int32_t *__restrict__ idx_old,
-                                                     const double *__restrict__ d2,
-                                                     const double *__restrict__ dpc, int64_t n,
-                                                     double w, double *__restrict__ out) {
+// Iteration statistics: changed associations, sum_e 1/2 w d_e^2 after P_D,
+// sum after P_C.  Every block sums a fixed share; the last block to finish
+// adds the block partials in index order (deterministic for a given n).
+// out: [0, 3) totals, [4] arrival counter (zero between calls), [8, 8 + 3 G)
+// block partials.
+constexpr int kStatsBlocks = 256;
+
+__global__ void __launch_bounds__(256) k_iter_stats(const int32_t *__restrict__ idx_new,
+                                                    const int32_t *__restrict__ idx_old,
+                                                    const double *__restrict__ d2,
+                                                    const double *__restrict__ dpc, int64_t n,
+                                                    double w, double *__restrict__ out) {
     __shared__ double sh[3 * 32];
+    __shared__ int last;
     double v[3] = {0, 0, 0};
-    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         v[0] += (idx_new[e] != idx_old[e]) ? 1.0 : 0.0;
         v[1] += 0.5 * w * d2[e];
         v[2] += dpc[e];
     }
     block_sum<3>(v, sh);
+    double *part = out + 8;
+    unsigned *cnt = reinterpret_cast<unsigned *>(out + 4);
     if (threadIdx.x == 0) {
-        out[0] = v[0];
-        out[1] = v[1];
-        out[2] = v[2];
+        for (int k = 0; k < 3; ++k) part[blockIdx.x * 3 + k] = v[k];
+        __threadfence();
+        last = atomicAdd(cnt, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double t[3] = {0, 0, 0};
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+        for (int k = 0; k < 3; ++k) t[k] += __ldcg(part + b * 3 + k);
+    block_sum<3>(t, sh);
+    if (threadIdx.x == 0) {
+        out[0] = t[0];
+        out[1] = t[1];
+        out[2] = t[2];
+        *cnt = 0u;
     }
 }
 
@@ -719,7 +740,8 @@ dd_status fem_recover(dd_dataset *ds, const MeshDev &g, const ElemOps &ops, cons
 dd_status fem_iter_stats(dd_ctx *ctx, const int32_t *idx_new, const int32_t *idx_old, const double *d2,
                          const double *dpc, int64_t n, double w, double *out, cudaStream_t s) {
     ctx->launches++;
-    k_iter_stats<<<1, 1024, 0, s>>>(idx_new, idx_old, d2, dpc, n, w, out);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(kStatsBlocks, (n + 1023) / 1024));
+    k_iter_stats<<<grid, 256, 0, s>>>(idx_new, idx_old, d2, dpc, n, w, out);
     DD_TRY_CUDA(ctx, cudaGetLastError());
     return DD_OK;
 }

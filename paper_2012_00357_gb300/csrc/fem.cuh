@@ -92,5 +92,7 @@ dd_status dd_cg_segments(dd_ctx *ctx, const MeshDev *const *gs, const CGBuffers 
                          int max_it, cudaStream_t s, int **it_dev);
 dd_status fem_recover(dd_dataset *ds, const MeshDev &g, const ElemOps &ops, const double *x,
                       const double *star, double *y, double *dpc, cudaStream_t s);
+// out must hold kIterStatsDoubles doubles, zeroed once before the first call.
+constexpr int kIterStatsDoubles = 8 + 3 * 256;
 dd_status fem_iter_stats(dd_ctx *ctx, const int32_t *idx_new, const int32_t *idx_old, const double *d2,
                          const double *dpc, int64_t n, double w, double *out, cudaStream_t s);

@@ -95,7 +95,7 @@ size_t carve(dd_solver *sv, char *base) {
     sv->cur = bp.take<int32_t>(ng);
     sv->nxt = bp.take<int32_t>(ng);
     sv->idx_a = sv->cur;
-    sv->stats = bp.take<double>(8);
+    sv->stats = bp.take<double>(kIterStatsDoubles);
     sv->mot.q = bp.take<float>(ng * 12);
     sv->mot.d = bp.take<float>(ng * 2);
     return bp.off;
@@ -236,7 +236,8 @@ extern "C" dd_status dd_solver_create(dd_dataset *ds, const dd_mesh *mesh, const
          cudaMemcpyAsync(sv->cb.mg_inv, Kinv.data(), Kinv.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) ||
         cudaMemcpyAsync(sv->f, f.data(), nn * 3 * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(sv->cb.x, 0, nn * 6 * 8, s) != cudaSuccess ||
-        cudaMemsetAsync(sv->mot.d, 0, ng * 2 * sizeof(float), s) != cudaSuccess)
+        cudaMemsetAsync(sv->mot.d, 0, ng * 2 * sizeof(float), s) != cudaSuccess ||
+        cudaMemsetAsync(sv->stats, 0, kIterStatsDoubles * sizeof(double), s) != cudaSuccess)
         return fail(dd_fail(ctx, DD_ERR_CUDA, "dd_solver_create: upload"));
     if ((st = fem_block_jacobi(ctx, sv->g, sv->Ke, sv->Minv, s)) != DD_OK) return fail(st);
     if (opts && opts->init_idx) {
