@@ -36,7 +36,7 @@ namespace {
 // operator of level l is 2^l K of level 0; restriction is the transpose of
 // trilinear prolongation) with one damped block-Jacobi sweep before and after
 // the coarse correction; the coarsest level is solved exactly with a dense
-// inverse by the first block of each solve.  A solve whose mesh cannot
+// inverse shared out over the blocks of each solve.  A solve whose mesh cannot
 // coarsen uses block-Jacobi alone.
 constexpr int kBThreads = 256;
 constexpr int kTileMax = 16;                 // tile edge bound (nodes)
@@ -429,11 +429,14 @@ __device__ __forceinline__ void prolong_node(const Level Cl, int X, int Y, int Z
     }
 }
 
-// ---- the coarsest level, solved exactly by block 0 of the solve ----
-// Restrict the residual t of the last grid level to the free nodes of the
-// coarsest level (shared memory), apply its dense inverse to both systems
-// and write the coarse solution of all its nodes to S.zg.
-__device__ void coarse_direct(const SegCG &S, float *sr) {
+// ---- the coarsest level, solved exactly by all blocks of the solve ----
+
+// Every block restricts the residual t of the last grid level to the free
+// nodes of the coarsest level (its own shared-memory copy); the rows of the
+// dense inverse are shared out over the solve's warps (one row per warp,
+// lanes over the columns), and each row's two outputs (both systems) go to
+// S.zg.  Block 0 also zeroes the clamped nodes.
+__device__ void coarse_direct(const SegCG &S, int lb, int nblk, float *sr) {
     const int g = S.glev;
     const Level F = S.lv[g - 1], Cl = S.lv[g];
     const int plane = (Cl.nx + 1) * (Cl.ny + 1), nfree = plane * Cl.nz, n = S.ndof;
@@ -449,22 +452,27 @@ __device__ void coarse_direct(const SegCG &S, float *sr) {
     __syncthreads();
     const float *inv = S.inv;
     float *zg = S.zg;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {   // K^-1 is symmetric: row i read as column i
+    const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+    for (int i = lb * warps + (threadIdx.x >> 5); i < n; i += nblk * warps) {
         float a0 = 0.f, a1 = 0.f;
-        for (int fn = 0; fn < nfree; ++fn) {
-            const float *rj = sr + fn * 6;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float A = __ldg(inv + (size_t)(3 * fn + c) * n + i);
-                a0 = fmaf(A, rj[c], a0);
-                a1 = fmaf(A, rj[3 + c], a1);
-            }
+        for (int j = lane; j < n; j += 32) {   // K^-1 is symmetric: row i
+            const float A = __ldg(inv + (size_t)i * n + j);
+            const float *rj = sr + (j / 3) * 6 + j % 3;
+            a0 = fmaf(A, rj[0], a0);
+            a1 = fmaf(A, rj[3], a1);
         }
-        const int fi = i / 3, ci = i % 3;
-        zg[(size_t)(plane + fi) * 6 + ci] = a0;
-        zg[(size_t)(plane + fi) * 6 + 3 + ci] = a1;
+        for (int o = 16; o > 0; o >>= 1) {
+            a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+        }
+        if (lane == 0) {
+            const int fi = i / 3, ci = i % 3;
+            zg[(size_t)(plane + fi) * 6 + ci] = a0;
+            zg[(size_t)(plane + fi) * 6 + 3 + ci] = a1;
+        }
     }
-    for (int k = threadIdx.x; k < plane * 6; k += blockDim.x) zg[k] = 0.f;
+    if (lb == 0)
+        for (int k = threadIdx.x; k < plane * 6; k += blockDim.x) zg[k] = 0.f;
 }
 
 // ---- grid-level operations (all blocks of the solve, node tiles) ----
@@ -570,7 +578,7 @@ __device__ bool vcycle_rest(const SegCG &S, int lb, bool act, int G, GridBar &gb
         if (act && l < glev) grid_residual(S.lv[l], lb, nblk, sS, sv);
         if (!grid_sync(gb, err)) return false;
         if (act && l + 1 < glev) grid_restrict(S.lv[l], S.lv[l + 1], lb, nblk, sDi, om);
-        if (act && l + 1 == glev && glev < nlev && lb == 0) coarse_direct(S, sLev);
+        if (act && l + 1 == glev && glev < nlev) coarse_direct(S, lb, nblk, sLev);
         if (!grid_sync(gb, err)) return false;
     }
     for (int l = G - 1; l >= 0; --l) {
