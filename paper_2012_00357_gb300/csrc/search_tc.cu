@@ -82,8 +82,10 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
+// Issue a 32-column TMEM load without waiting for it.  Its registers may be
+// used only after tmem_wait on the same array, which names them as read-write
+// operands so that no use is moved above the wait.
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%"
@@ -92,30 +94,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+        : "r"(taddr)
+        : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
-    uint32_t r[64];
-#define DD_LD32(OFF, R)                                                                                            \
-    asm volatile(                                                                                                  \
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "                                                                  \
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%" \
-        "28,%29,%30,%31}, [%32];"                                                                                 \
-        : "=r"(R[0]), "=r"(R[1]), "=r"(R[2]), "=r"(R[3]), "=r"(R[4]), "=r"(R[5]), "=r"(R[6]), "=r"(R[7]),         \
-          "=r"(R[8]), "=r"(R[9]), "=r"(R[10]), "=r"(R[11]), "=r"(R[12]), "=r"(R[13]), "=r"(R[14]), "=r"(R[15]),   \
-          "=r"(R[16]), "=r"(R[17]), "=r"(R[18]), "=r"(R[19]), "=r"(R[20]), "=r"(R[21]), "=r"(R[22]), "=r"(R[23]), \
-          "=r"(R[24]), "=r"(R[25]), "=r"(R[26]), "=r"(R[27]), "=r"(R[28]), "=r"(R[29]), "=r"(R[30]), "=r"(R[31]) \
-        : "r"(taddr + (OFF)))
-    DD_LD32(0, r);
-    DD_LD32(32, (r + 32));
-#undef DD_LD32
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+__device__ __forceinline__ void tmem_wait(uint32_t (&r)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
 }
 
 __device__ __forceinline__ float min3f(float a, float b, float c) {
@@ -404,22 +395,33 @@ __global__ void __launch_bounds__(tc_threads<EPI>(), 2)
             }
             tc_fence_after();
             const int64_t jb = (t_begin + t) * kTN + half * kCols;
-#pragma unroll 1
-            for (int c = 0; c < kCols / 32; ++c) {
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)ab * kTN + (uint32_t)(half * kCols + c * 32),
-                          v);
-                if (c == kCols / 32 - 1) {
+            // the next 32 columns are loaded while the current ones are filtered
+            constexpr int kChunks = kCols / 32;
+            const uint32_t base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)ab * kTN + (uint32_t)(half * kCols);
+            uint32_t ra[32], rb[32];
+            tmem_ld32_async(base, ra);
+            tmem_wait(ra);
+#pragma unroll
+            for (int c = 0; c < kChunks; ++c) {
+                uint32_t(&cur)[32] = (c & 1) ? rb : ra;
+                uint32_t(&nxt)[32] = (c & 1) ? ra : rb;
+                if (c + 1 < kChunks) {
+                    tmem_ld32_async(base + (uint32_t)((c + 1) * 32), nxt);
+                } else {   // every column of this accumulator is in registers: release it
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) dd_mbar_arrive(dd_smem_addr(&bar_tempty[ab]));
                 }
+                float v[32];
+#pragma unroll
+                for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(cur[k]);
                 if (min32(v) <= cs.lim) {
                     const int64_t j0 = jb + c * 32;
 #pragma unroll
                     for (int k = 0; k < 32; ++k)
                         if (v[k] <= cs.lim && j0 + k < N) cand_insert(cs, v[k], (int)(j0 + k), w2, buf, kSt, kCap, topk);
                 }
+                if (c + 1 < kChunks) tmem_wait(nxt);
             }
         }
         if (active) cand_store(cs, buf, kSt, kCap, ((size_t)qi * splits + split) * (EPI / 4) + half, hdr, cand);
