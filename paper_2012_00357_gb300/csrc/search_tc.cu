@@ -398,13 +398,11 @@ __global__ void __launch_bounds__(tc_threads<EPI>(), 2)
             // the next 32 columns are loaded while the current ones are filtered
             constexpr int kChunks = kCols / 32;
             const uint32_t base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)ab * kTN + (uint32_t)(half * kCols);
-            uint32_t ra[32], rb[32];
-            tmem_ld32_async(base, ra);
-            tmem_wait(ra);
-#pragma unroll
+            uint32_t cur[32], nxt[32];
+            tmem_ld32_async(base, cur);
+            tmem_wait(cur);
+#pragma unroll 1
             for (int c = 0; c < kChunks; ++c) {
-                uint32_t(&cur)[32] = (c & 1) ? rb : ra;
-                uint32_t(&nxt)[32] = (c & 1) ? ra : rb;
                 if (c + 1 < kChunks) {
                     tmem_ld32_async(base + (uint32_t)((c + 1) * 32), nxt);
                 } else {   // every column of this accumulator is in registers: release it
@@ -415,13 +413,25 @@ __global__ void __launch_bounds__(tc_threads<EPI>(), 2)
                 float v[32];
 #pragma unroll
                 for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(cur[k]);
-                if (min32(v) <= cs.lim) {
-                    const int64_t j0 = jb + c * 32;
+                if (min32(v) <= cs.lim) {   // rare: walk the columns inside the window
+                    unsigned msk = 0;
 #pragma unroll
-                    for (int k = 0; k < 32; ++k)
-                        if (v[k] <= cs.lim && j0 + k < N) cand_insert(cs, v[k], (int)(j0 + k), w2, buf, kSt, kCap, topk);
+                    for (int k = 0; k < 32; ++k) msk |= (v[k] <= cs.lim ? 1u : 0u) << k;
+                    const int64_t j0 = jb + c * 32;
+                    while (msk) {
+                        const int k = __ffs(msk) - 1;
+                        msk &= msk - 1;
+                        float vk = v[0];
+#pragma unroll
+                        for (int kk = 1; kk < 32; ++kk) vk = (k == kk) ? v[kk] : vk;
+                        if (vk <= cs.lim && j0 + k < N) cand_insert(cs, vk, (int)(j0 + k), w2, buf, kSt, kCap, topk);
+                    }
                 }
-                if (c + 1 < kChunks) tmem_wait(nxt);
+                if (c + 1 < kChunks) {
+                    tmem_wait(nxt);
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) cur[k] = nxt[k];
+                }
             }
         }
         if (active) cand_store(cs, buf, kSt, kCap, ((size_t)qi * splits + split) * (EPI / 4) + half, hdr, cand);
