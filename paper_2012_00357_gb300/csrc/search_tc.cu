@@ -396,23 +396,14 @@ __global__ void __launch_bounds__(tc_threads<EPI>(), 2)
             tc_fence_after();
             const int64_t jb = (t_begin + t) * kTN + half * kCols;
             // the next 32 columns are loaded while the current ones are filtered
+            // (two register buffers used in turn: no copies)
             constexpr int kChunks = kCols / 32;
             const uint32_t base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)ab * kTN + (uint32_t)(half * kCols);
-            uint32_t cur[32], nxt[32];
-            tmem_ld32_async(base, cur);
-            tmem_wait(cur);
-#pragma unroll 1
-            for (int c = 0; c < kChunks; ++c) {
-                if (c + 1 < kChunks) {
-                    tmem_ld32_async(base + (uint32_t)((c + 1) * 32), nxt);
-                } else {   // every column of this accumulator is in registers: release it
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) dd_mbar_arrive(dd_smem_addr(&bar_tempty[ab]));
-                }
+            uint32_t ra[32], rb[32];
+            auto filter = [&](const uint32_t(&r)[32], int c) {
                 float v[32];
 #pragma unroll
-                for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(cur[k]);
+                for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
                 if (min32(v) <= cs.lim) {   // rare: walk the columns inside the window
                     unsigned msk = 0;
 #pragma unroll
@@ -427,10 +418,25 @@ __global__ void __launch_bounds__(tc_threads<EPI>(), 2)
                         if (vk <= cs.lim && j0 + k < N) cand_insert(cs, vk, (int)(j0 + k), w2, buf, kSt, kCap, topk);
                     }
                 }
+            };
+            auto release = [&]() {   // every column of this accumulator is in registers
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) dd_mbar_arrive(dd_smem_addr(&bar_tempty[ab]));
+            };
+            tmem_ld32_async(base, ra);
+            tmem_wait(ra);
+#pragma unroll 1
+            for (int c = 0; c < kChunks; c += 2) {   // ra holds chunk c
+                if (c + 1 < kChunks) tmem_ld32_async(base + (uint32_t)((c + 1) * 32), rb);
+                else release();
+                filter(ra, c);
                 if (c + 1 < kChunks) {
-                    tmem_wait(nxt);
-#pragma unroll
-                    for (int k = 0; k < 32; ++k) cur[k] = nxt[k];
+                    tmem_wait(rb);                    // rb holds chunk c + 1
+                    if (c + 2 < kChunks) tmem_ld32_async(base + (uint32_t)((c + 2) * 32), ra);
+                    else release();
+                    filter(rb, c + 1);
+                    if (c + 2 < kChunks) tmem_wait(ra);
                 }
             }
         }
