@@ -183,7 +183,7 @@ def run_ours(args, world, rank, local):
     init = I.initial_association(W.m, W.N, seed=W.seed)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     data_bytes = W.N * (64 if mode == P.DD_SEARCH_EXACT_TC else 52 if mode == P.DD_SEARCH_EXACT_FP32 else 48)
-    ann_kw = dict(f_d0=0.0, f_d_final=args.fd_final, ramp_iters=20) if mode == P.DD_SEARCH_ANN else {}
+    ann_kw = dict(f_d0=args.fd0, f_d_final=args.fd_final, ramp_iters=args.ramp_iters) if mode == P.DD_SEARCH_ANN else {}
     flush_l2 = data_bytes < 2 * L2_BYTES
 
     loads = [I.load_case(*lc) for lc in W.loads]
@@ -377,7 +377,7 @@ def run_serve(args, world, rank, local):
     P.dd_synth_dataset(ctx, raw, W.law, C, seed=W.seed)
     nlist = args.nlist or max(64, 1 << int(np.log2(max(W.N // 3000, 64))))
     ds = P.dd_load_dataset(ctx, raw, C, borrow=True, ann_nlist=nlist, seed=1)
-    kw = dict(mode=P.DD_SEARCH_ANN, f_d0=0.0, f_d_final=args.fd_final, ramp_iters=20, max_iter=200)
+    kw = dict(mode=P.DD_SEARCH_ANN, f_d0=args.fd0, f_d_final=args.fd_final, ramp_iters=args.ramp_iters, max_iter=200)
     n_req = ex["requests"]
 
     def serve(reqs, budget):
@@ -422,7 +422,7 @@ def run_serve(args, world, rank, local):
         "dtype": "f64 (P_C refinement, rescoring) + f32", "data": "synthetic (dd_inputs generator, made on device)",
         "config": {"workload": W.name, "data_points": W.N, "requests": n_req, "edges": f"U{{{ex['edge_min']}..{ex['edge_max']}}}",
                    "traction": f"U[{ex['t_min']}, {ex['t_max']}] random direction", "search": "ann",
-                   "f_d_final": args.fd_final, "nlist": nlist, "state_budget_gb": args.serve_budget_gb,
+                   "f_d": f"{args.fd0} -> {args.fd_final} over {args.ramp_iters} iterations", "nlist": nlist, "state_budget_gb": args.serve_budget_gb,
                    "arrivals": f"Poisson, rate {rate:.2f}/s = 0.8 x calibrated service rate",
                    "l2": "inputs larger than L2", "parallelism": "replicas x1"},
         "serve": {"p50_ms": float(np.percentile(lat_s, 50)), "p99_ms": float(np.percentile(lat_s, 99)),
@@ -475,13 +475,20 @@ def main():
                     help="search mode (default: ann for *_ann workloads, serve for serve_*, else tc)")
     ap.add_argument("--max-batch", type=int, default=64)
     ap.add_argument("--serve-budget-gb", type=float, default=16.0)
-    ap.add_argument("--fd-final", type=float, default=0.4)
+    # accuracy schedule of the approximate search: constant f_d = 0.6 keeps
+    # the DD iteration on the trajectory of the exact search (the paper's
+    # ramp from 0 converges to a worse fixed point on these workloads)
+    ap.add_argument("--fd-final", type=float, default=0.6)
+    ap.add_argument("--fd0", type=float, default=None, help="f_d of the first iteration (default: --fd-final)")
+    ap.add_argument("--ramp-iters", type=int, default=0)
     ap.add_argument("--nlist", type=int, default=0)
     ap.add_argument("--ann-levels", type=int, default=0)
     ap.add_argument("--ann-check", type=int, default=2048)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()
+    if args.fd0 is None:
+        args.fd0 = args.fd_final
     if args.mode is None:
         args.mode = "serve" if args.workload.startswith("serve") else ("ann" if "_ann" in args.workload else "tc")
     world, rank, local = dist_setup()

@@ -124,14 +124,17 @@ bool dd_solver_account(dd_solver *sv, const double hs[3], int cg_it, float cg_ms
     sv->h_ch.push_back((int64_t)hs[0]);
     sv->h_cg.push_back(cg_it);
     bool stop = false;
-    if (hs[0] == 0.0) {
+    // an approximate search is still tightening while f_d ramps up: its stop
+    // tests apply once f_d has reached its final value
+    const bool settled = o.mode != DD_SEARCH_ANN || o.ramp_iters <= 0 || it > o.ramp_iters;
+    if (hs[0] == 0.0 && settled) {
         sv->converged = true;
         stop = true;   // nxt == cur: the state was computed from the final association
     } else if (o.mode == DD_SEARCH_ANN) {
         if (hs[1] < sv->best_pd * (1.0 - 1e-12)) {
             sv->best_pd = hs[1];
             sv->stall = 0;
-        } else if (++sv->stall >= o.stall_iters) {
+        } else if (settled && ++sv->stall >= o.stall_iters) {
             sv->converged = true;
             stop = true;   // keep the association the constraint state was computed from
         }

@@ -26,7 +26,7 @@ def big():
     ctx = P.dd_create(0)
     raw = torch.empty((W.N, 12), dtype=torch.float32, device="cuda")
     P.dd_synth_dataset(ctx, raw, W.law, C, seed=W.seed)
-    ds = P.dd_load_dataset(ctx, raw, C, borrow=True, ann_nlist=1 << 15, ann_levels=2, seed=1)
+    ds = P.dd_load_dataset(ctx, raw, C, borrow=True, build_fp16=True, ann_nlist=1 << 15, ann_levels=2, seed=1)
     y = I.make_states(W.m, W.law, seed=41, spread=0.02)
     sample = np.random.default_rng(4).choice(W.m, 12, replace=False)
     oi, od = nn.nn_stream(W.law, W.seed, W.N, C, metric.to_z(y[sample], C))
@@ -60,3 +60,21 @@ def test_ann_tree_fd_one_full_size(big):
                       prev_idx=torch.from_numpy(prev).cuda())
     assert np.array_equal(idx, oi)
     assert np.allclose(d2, 2 * od, rtol=1e-9)
+
+
+def test_ann_solve_within_1e3_of_exact_full_size(big):
+    """The DD solution driven by the approximate search (tree, constant
+    f_d = 0.6, the benchmark schedule) stays within 1e-3 relative in global
+    distance (Eq. 2) of the solution driven by the certified exact search, on
+    the 32^3 cube with the 10^8-point data set, from the same initial
+    association."""
+    ctx, ds, y, sample, oi, od = big
+    L = I.load_case("tension", 1e-3)
+    exact = P.dd_solve(ds, ctx, W.n_el, L, mode=P.DD_SEARCH_EXACT_TC, seed=W.seed, max_iter=60)
+    ann = P.dd_solve(ds, ctx, W.n_el, L, mode=P.DD_SEARCH_ANN, f_d0=0.6, f_d_final=0.6, ramp_iters=0,
+                     seed=W.seed, max_iter=60)
+    de, da = float(exact.d2_pd[-1]), float(ann.d2_pd[-1])
+    print(f"exact: {exact.iters} iterations, d2 {de:.6e}; approximate: {ann.iters} iterations, d2 {da:.6e}, "
+          f"relative difference {abs(da - de) / de:.2e}")
+    assert exact.converged and ann.converged
+    assert abs(da - de) <= 1e-3 * de
