@@ -209,6 +209,7 @@ class Load:
     t0: tuple = (0.0, 0.0, 0.0)
     tx: tuple = (0.0, 0.0, 0.0)
     ty: tuple = (0.0, 0.0, 0.0)
+    rot_z: float = 0.0        # prescribed rotation of the top face about the vertical axis (radians)
 
 
 def load_case(name: str, t: float) -> Load:
@@ -222,6 +223,13 @@ def load_case(name: str, t: float) -> Load:
     if name == "torsion":      # t = 2t (-(y - 1/2), x - 1/2, 0)
         return Load(tx=(0.0, 2.0 * t, 0.0), ty=(-2.0 * t, 0.0, 0.0))
     raise ValueError(name)
+
+
+def top_rotation(theta_deg: float) -> Load:
+    """The top face turned rigidly by theta_deg degrees about the vertical
+    axis through its centre, the bottom clamped, no traction (the paper's
+    own boundary-value problem, a 2 degree torsion)."""
+    return Load(rot_z=math.radians(theta_deg))
 
 
 def random_load(seed: int, r: int, tmin: float, tmax: float) -> Load:

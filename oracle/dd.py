@@ -50,16 +50,22 @@ class DDProblem:
         self.C = np.asarray(C, dtype=np.float64)
         self.fe = _fem.HexBox(n_el, n_el, n_el, self.C)
         self.Z = _metric.to_z(self.data, self.C)
-        fixed = self.fe.clamped_bottom() if fixed is None else fixed
+        rot = float(getattr(load, "rot_z", 0.0))
+        if fixed is None:
+            fixed = self.fe.clamped_bottom()
+            if rot != 0.0:                       # the top face is a Dirichlet boundary
+                fixed = fixed | self.fe.clamped_top()
         self.solver = _fem.DirectSolver(self.fe.K(), fixed)
-        self.f = self.fe.top_traction_force(load.t0, load.tx, load.ty)
+        # u takes the prescribed values on the top face; eta is zero there (Eq. 5)
+        self.u_d = self.fe.top_rotation(rot) if rot != 0.0 else None
+        self.f = np.zeros(self.fe.n_dof) if rot != 0.0 else self.fe.top_traction_force(load.t0, load.tx, load.ty)
         self.w = self.fe.w
 
     def project_C(self, idx: np.ndarray):
         """P_C of the data states z_i = data[idx] (Eq. 5, Eq. 6)."""
         star = self.data[idx]
         eps_s, sig_s = star[:, :6], star[:, 6:]
-        u = self.solver.solve(self.fe.assemble_BT(eps_s @ self.C.T))
+        u = self.solver.solve(self.fe.assemble_BT(eps_s @ self.C.T), prescribed=self.u_d)
         eta = self.solver.solve(self.f - self.fe.assemble_BT(sig_s))
         eps = self.fe.strains(u)
         sig = sig_s + self.fe.strains(eta) @ self.C.T

@@ -129,6 +129,25 @@ class HexBox:
                                 f[3 * n:3 * n + 3] += N * t * wq
         return f
 
+    def top_rotation(self, theta: float) -> np.ndarray:
+        """Displacement of the nodes on z = lz when the top face turns rigidly by
+        theta (radians) about the vertical axis through its centre:
+        u = (R(theta) - I)(x - x_c, y - y_c), u_z = 0; zero elsewhere."""
+        xyz = self.node_coords()
+        top = np.isclose(xyz[:, 2], self.lz)
+        dx, dy = xyz[:, 0] - self.lx / 2, xyz[:, 1] - self.ly / 2
+        c, s = np.cos(theta), np.sin(theta)
+        u = np.zeros((self.n_nodes, 3))
+        u[top, 0] = ((c - 1.0) * dx - s * dy)[top]
+        u[top, 1] = (s * dx + (c - 1.0) * dy)[top]
+        return u.ravel()
+
+    def clamped_top(self) -> np.ndarray:
+        """Boolean mask of every dof of the nodes on z = lz."""
+        fixed = np.zeros(self.n_dof, dtype=bool)
+        fixed[np.repeat(np.isclose(self.node_coords()[:, 2], self.lz), 3)] = True
+        return fixed
+
     def clamped_bottom(self) -> np.ndarray:
         """Boolean mask of the fixed dofs: every dof of the nodes on z = 0."""
         fixed = np.zeros(self.n_dof, dtype=bool)
@@ -138,16 +157,23 @@ class HexBox:
 
 
 class DirectSolver:
-    """K restricted to the free dofs, factorised once by sparse LU; solves
-    with homogeneous values on the fixed dofs."""
+    """K restricted to the free dofs, factorised once by sparse LU.  A solve
+    takes the values of the fixed dofs (zero by default) and moves their
+    coupling to the right-hand side: K_ff x_f = rhs_f - K_fd x_d."""
 
     def __init__(self, K: sp.csr_matrix, fixed: np.ndarray):
         self.free = ~np.asarray(fixed, dtype=bool)
         Kff = K[self.free][:, self.free].tocsc()
+        self.Kfd = K[self.free][:, ~self.free].tocsr()
         self.lu = spla.splu(Kff)
         self.n = K.shape[0]
 
-    def solve(self, rhs: np.ndarray) -> np.ndarray:
+    def solve(self, rhs: np.ndarray, prescribed: np.ndarray | None = None) -> np.ndarray:
         x = np.zeros(self.n)
-        x[self.free] = self.lu.solve(np.asarray(rhs, dtype=np.float64)[self.free])
+        b = np.asarray(rhs, dtype=np.float64)[self.free]
+        if prescribed is not None:
+            xd = np.asarray(prescribed, dtype=np.float64)[~self.free]
+            x[~self.free] = xd
+            b = b - self.Kfd @ xd
+        x[self.free] = self.lu.solve(b)
         return x

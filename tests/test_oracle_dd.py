@@ -83,3 +83,21 @@ def test_distance_history_consistent_with_eq2():
     r = P.solve(I.initial_association(P.fe.m, len(data), seed=9))
     # after P_D the recorded distance is sum w |dq|^2 = sum 1/2 w d_e^2 of the new association
     assert np.isclose(P.global_d2(r.eps, r.sig, r.idx), r.d2_after_pd[-1], rtol=1e-12)
+
+
+def test_top_rotation_problem_monotone_and_prescribed():
+    """The paper's own boundary-value problem (top face turned by 2 degrees,
+    bottom clamped): the DD distance never increases (alternating
+    minimisation) and every P_C state keeps the prescribed top values, with
+    eta zero on both faces."""
+    data = I.make_dataset(1500, I.LINEAR, seed=5)
+    C = I.isotropic_C()
+    p = dd.DDProblem(data, C, 3, I.top_rotation(2.0))
+    init = I.initial_association(p.fe.m, len(data), seed=2)
+    r = p.solve(init, max_iter=40)
+    h = np.array([x for pair in zip(r.d2_after_pc, r.d2_after_pd) for x in pair])
+    assert np.all(np.diff(h) <= 1e-12 * h[0])
+    fixed = p.fe.clamped_bottom() | p.fe.clamped_top()
+    assert np.array_equal(r.u[fixed], p.u_d[fixed])
+    assert np.all(r.eta[fixed] == 0.0)
+    assert np.abs(p.u_d).max() > 0
