@@ -236,11 +236,16 @@ typedef struct dd_mesh {
     double lx, ly, lz;
 } dd_mesh;
 
-/* Boundary conditions: every dof on z = 0 is clamped; the face z = lz carries
- * the traction t(x,y) = t0 + tx (x - lx/2) + ty (y - ly/2), integrated into
- * consistent nodal forces f (2x2 Gauss per face). */
+/* Boundary conditions: every dof on z = 0 is clamped.  With rot_z == 0 the
+ * face z = lz carries the traction t(x,y) = t0 + tx (x - lx/2) + ty (y - ly/2),
+ * integrated into consistent nodal forces f (2x2 Gauss per face).  With
+ * rot_z != 0 the face z = lz is turned rigidly by rot_z radians about the
+ * vertical axis through its centre instead: u = (R(rot_z) - I)(x - lx/2,
+ * y - ly/2, 0) there, eta = 0 there, no traction (the paper's torsion
+ * problem); t0, tx, ty must then be zero (DD_ERR_ARG otherwise) and nz >= 2. */
 typedef struct dd_load {
     double t0[3], tx[3], ty[3];
+    double rot_z;             /* prescribed rotation of the top face (radians), 0: traction */
 } dd_load;
 
 typedef struct dd_solve_opts {

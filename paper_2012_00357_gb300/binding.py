@@ -68,7 +68,13 @@ class dd_mesh(ctypes.Structure):
 
 
 class dd_load(ctypes.Structure):
-    _fields_ = [("t0", c_double * 3), ("tx", c_double * 3), ("ty", c_double * 3)]
+    _fields_ = [("t0", c_double * 3), ("tx", c_double * 3), ("ty", c_double * 3), ("rot_z", c_double)]
+
+
+def _load(L) -> dd_load:
+    """dd_load of a dd_inputs.Load (traction field or prescribed top rotation)."""
+    return dd_load((c_double * 3)(*L.t0), (c_double * 3)(*L.tx), (c_double * 3)(*L.ty),
+                   float(getattr(L, "rot_z", 0.0)))
 
 
 class dd_solve_opts(ctypes.Structure):
@@ -268,7 +274,7 @@ def dd_solve(ds, ctx, n_el, load, mode: int = DD_SEARCH_EXACT_FP32, init_idx=Non
     """Solve one cube problem; `load` is a dd_inputs.Load.  Returns a Result."""
     nx, ny, nz = (n_el, n_el, n_el) if np.isscalar(n_el) else n_el
     mesh = dd_mesh(nx, ny, nz, *lengths)
-    L = dd_load((c_double * 3)(*load.t0), (c_double * 3)(*load.tx), (c_double * 3)(*load.ty))
+    L = _load(load)
     ii = None if init_idx is None else np.ascontiguousarray(init_idx, dtype=np.int32)
     opts = dd_solve_opts(int(mode), int(certify), float(f_d0), float(f_d_final), int(ramp_iters), int(max_iter),
                          float(cg_rtol), int(cg_max_iter), int(seed), _ptr(ii), int(stall_iters), int(cg_mode))
@@ -292,7 +298,7 @@ def _solve_args(n_el, load, mode, init_idx, max_iter, cg_rtol, cg_max_iter, cert
                 seed, stall_iters, lengths, cg_mode=0):
     nx, ny, nz = (n_el, n_el, n_el) if np.isscalar(n_el) else n_el
     mesh = dd_mesh(nx, ny, nz, *lengths)
-    L = dd_load((c_double * 3)(*load.t0), (c_double * 3)(*load.tx), (c_double * 3)(*load.ty))
+    L = _load(load)
     ii = None if init_idx is None else np.ascontiguousarray(init_idx, dtype=np.int32)
     opts = dd_solve_opts(int(mode), int(certify), float(f_d0), float(f_d_final), int(ramp_iters), int(max_iter),
                          float(cg_rtol), int(cg_max_iter), int(seed), _ptr(ii), int(stall_iters), int(cg_mode))
@@ -377,7 +383,7 @@ def dd_solve_batch(ds, ctx, n_els, loads, mode: int = DD_SEARCH_EXACT_FP32, init
     """Solve several cube problems together; n_els[i] edge elements, loads[i]."""
     n = len(n_els)
     meshes = (dd_mesh * n)(*[dd_mesh(k, k, k, 1.0, 1.0, 1.0) for k in n_els])
-    Ls = (dd_load * n)(*[dd_load((c_double * 3)(*L.t0), (c_double * 3)(*L.tx), (c_double * 3)(*L.ty))
+    Ls = (dd_load * n)(*[_load(L)
                          for L in loads])
     _, _, opts, ii = _solve_args(n_els[0], loads[0], mode, init_idx, max_iter, cg_rtol, cg_max_iter, certify, f_d0,
                                  f_d_final, ramp_iters, seed, stall_iters, (1.0, 1.0, 1.0), cg_mode)
@@ -407,7 +413,7 @@ def dd_server_start(ds, ctx, mode: int = DD_SEARCH_EXACT_FP32, state_budget: int
 def dd_server_submit(srv, n_el, load, seed: int = 0, lengths=(1.0, 1.0, 1.0)) -> int:
     nx, ny, nz = (n_el, n_el, n_el) if np.isscalar(n_el) else n_el
     mesh = dd_mesh(nx, ny, nz, *lengths)
-    L = dd_load((c_double * 3)(*load.t0), (c_double * 3)(*load.tx), (c_double * 3)(*load.ty))
+    L = _load(load)
     t = c_int64()
     st = lib().dd_server_submit(srv, ctypes.byref(mesh), ctypes.byref(L), int(seed), ctypes.byref(t))
     if st != DD_OK:

@@ -50,6 +50,7 @@ constexpr size_t kDynSmem = kSmemSt + kSmemHalo + kSmemLev + kSmemDi;
 
 struct Level {
     int nx, ny, nz;                          // elements
+    int top;                                 // 1: the top layer of nodes is fixed (free layers 1 .. nz - top)
     int tx, ty, tz, ntx, nty, ntiles;        // tiles (levels run by the whole grid)
     float *r, *z, *t;                        // vectors [nodes x 6] (grid levels)
     float h;                                 // 2^level
@@ -217,7 +218,7 @@ __device__ __forceinline__ TileNode tile_node(const Level L, const Lane &ln, int
     n.Y0 = ((tile / L.ntx) % L.nty) * L.ty;
     n.Z0 = 1 + (tile / (L.ntx * L.nty)) * L.tz;
     const int X = n.X0 + ln.lx, Y = n.Y0 + ln.ly, Z = n.Z0 + ln.lz;
-    n.ok = ln.ok && X <= L.nx && Y <= L.ny && Z <= L.nz;
+    n.ok = ln.ok && X <= L.nx && Y <= L.ny && Z <= L.nz - L.top;
     n.a = n.ok ? lnode(L, X, Y, Z) : 0;
     n.cls = lclass(L, X, Y, Z);
     return n;
@@ -235,7 +236,7 @@ __device__ __forceinline__ void stage_f(const Level L, const Lane &ln, const Til
         const int X = n.X0 - 1 + (ln.hs[k] & 255), Y = n.Y0 - 1 + ((ln.hs[k] >> 8) & 255),
                   Z = n.Z0 - 1 + (ln.hs[k] >> 16);
         v[k][0] = v[k][1] = v[k][2] = make_float2(0.f, 0.f);
-        if (h < ln.nh && X >= 0 && Y >= 0 && Z >= 1 && X <= L.nx && Y <= L.ny && Z <= L.nz) {
+        if (h < ln.nh && X >= 0 && Y >= 0 && Z >= 1 && X <= L.nx && Y <= L.ny && Z <= L.nz - L.top) {
             const int a = lnode(L, X, Y, Z);
             const float2 *pz = reinterpret_cast<const float2 *>(vz + (size_t)a * 6);
             v[k][0] = __ldcg(pz);
@@ -338,6 +339,27 @@ __device__ __forceinline__ void stencil_d(const double *St, const double *sv, in
             }
 }
 
+// The part of (K v) of the node at halo index hc from its 9 neighbours in
+// the layer above (dz = +1), FP64.
+__device__ __forceinline__ void stencil_d_up(const double *St, const double *sv, int hc, int hx, int hxy, int cls,
+                                             double y[6]) {
+    const double *Sc = St + cls * (27 * 9);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) y[k] = 0.0;
+    for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+            const int d = (dx + 1) + 3 * (dy + 1) + 18;
+            const double *xv = sv + (hc + dx + dy * hx + hxy) * 6;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const double k0 = __ldg(Sc + d * 9 + 3 * r), k1 = __ldg(Sc + d * 9 + 3 * r + 1),
+                             k2 = __ldg(Sc + d * 9 + 3 * r + 2);
+                y[r] = fma(k0, xv[0], fma(k1, xv[1], fma(k2, xv[2], y[r])));
+                y[3 + r] = fma(k0, xv[3], fma(k1, xv[4], fma(k2, xv[5], y[3 + r])));
+            }
+        }
+}
+
 // y = s * D^-1 x for both systems, D^-1 of class cls packed (m00 m11 m22 m12 m02 m01).
 __device__ __forceinline__ void dinv_apply(const float *sDi, int cls, float s, const float x[6], float y[6]) {
     const float *m = sDi + cls * 6;
@@ -383,7 +405,7 @@ __device__ __forceinline__ void restrict_node(const Level F, int X, int Y, int Z
 #pragma unroll
         for (int d = 0; d < 9; ++d) {
             const int x = 2 * X + d % 3 - 1, y = 2 * Y + d / 3 - 1;
-            if (x >= 0 && y >= 0 && z >= 1 && x <= F.nx && y <= F.ny && z <= F.nz) {
+            if (x >= 0 && y >= 0 && z >= 1 && x <= F.nx && y <= F.ny && z <= F.nz - F.top) {
                 get(lnode(F, x, y, z), v[d]);
             } else {
 #pragma unroll
@@ -411,7 +433,7 @@ __device__ __forceinline__ void prolong_node(const Level Cl, int X, int Y, int Z
     for (int c = 0; c < 8; ++c) {
         // odd coordinates take both neighbours, even ones the coincident node once
         const bool use = (c & 1 ? (X & 1) : 1) && (c & 2 ? (Y & 1) : 1) && (c & 4 ? (Z & 1) : 1) &&
-                         K[(c >> 2) & 1] >= 1;
+                         K[(c >> 2) & 1] >= 1 && K[(c >> 2) & 1] <= Cl.nz - Cl.top;
         if (use) {
             get(lnode(Cl, I[c & 1], J[(c >> 1) & 1], K[(c >> 2) & 1]), v[c]);
         } else {
@@ -439,7 +461,7 @@ __device__ __forceinline__ void prolong_node(const Level Cl, int X, int Y, int Z
 __device__ void coarse_direct(const SegCG &S, int lb, int nblk, float *sr) {
     const int g = S.glev;
     const Level F = S.lv[g - 1], Cl = S.lv[g];
-    const int plane = (Cl.nx + 1) * (Cl.ny + 1), nfree = plane * Cl.nz, n = S.ndof;
+    const int plane = (Cl.nx + 1) * (Cl.ny + 1), nfree = plane * (Cl.nz - Cl.top), n = S.ndof;
     const float *tf = F.t;
     for (int f = threadIdx.x; f < nfree; f += blockDim.x) {
         const int a = plane + f;
@@ -471,8 +493,11 @@ __device__ void coarse_direct(const SegCG &S, int lb, int nblk, float *sr) {
             zg[(size_t)(plane + fi) * 6 + 3 + ci] = a1;
         }
     }
-    if (lb == 0)
+    if (lb == 0) {   // fixed nodes: the bottom plane, and the top plane when it is fixed
         for (int k = threadIdx.x; k < plane * 6; k += blockDim.x) zg[k] = 0.f;
+        if (Cl.top)
+            for (int k = threadIdx.x; k < plane * 6; k += blockDim.x) zg[(size_t)plane * Cl.nz * 6 + k] = 0.f;
+    }
 }
 
 // ---- grid-level operations (all blocks of the solve, node tiles) ----
@@ -635,7 +660,7 @@ __global__ void __launch_bounds__(kBThreads, 1) k_cg_batch(BCGArgs A) {
     float *const Sr = S.r, *const Sz = S.z, *const Sd = S.d, *const Sq = S.q;
     double *const Sx = S.x;
     const double *const Sb = S.b, *const St64 = S.St64;
-    const double ndof = 3.0 * (L0.nx + 1) * (double)(L0.ny + 1) * (double)L0.nz;
+    const double ndof = 3.0 * (L0.nx + 1) * (double)(L0.ny + 1) * (double)(L0.nz - L0.top);
     double *partA = A.part, *partB = A.part + (size_t)G * 8;
     int *outer_flag = A.flags;
     // multigrid depth of this solve (0: one level, plain block-Jacobi)
@@ -651,8 +676,11 @@ __global__ void __launch_bounds__(kBThreads, 1) k_cg_batch(BCGArgs A) {
             __syncthreads();
             if (n.ok) {
                 const size_t a = n.a;
-                double kx[6];
+                double kx[6], lift[6] = {0, 0, 0, 0, 0, 0};
                 stencil_d(St64, sv64, ln0.hc, ln0.hx, ln0.hxy, n.cls, kx);
+                // below a fixed top: the coupling to the prescribed values, which
+                // moves to the right-hand side of the free dofs (the reference norm)
+                if (L0.top && n.Z0 + ln0.lz == L0.nz - 1) stencil_d_up(St64, sv64, ln0.hc, ln0.hx, ln0.hxy, n.cls, lift);
                 float rf[6];
 #pragma unroll
                 for (int k = 0; k < 6; ++k) {
@@ -660,7 +688,7 @@ __global__ void __launch_bounds__(kBThreads, 1) k_cg_batch(BCGArgs A) {
                     const double r64 = bc - kx[k];
                     rf[k] = (float)r64;
                     v[k / 3] += r64 * r64;
-                    v[2 + k / 3] += bc * bc;
+                    v[2 + k / 3] += (bc - lift[k]) * (bc - lift[k]);
                 }
                 st6(Sr + a * 6, rf);
                 const float zero6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -855,7 +883,7 @@ __global__ void k_fill_fd(float *p, int64_t n, const float *v) {
 // cycles for the passes over its tiles (a halo round per 256 staged nodes,
 // the stencil per warp, the per-node update).
 static void pick_tiles(int nx, int ny, int nz, int nblk, Level &L) {
-    const int n1[3] = {nx + 1, ny + 1, nz};
+    const int n1[3] = {nx + 1, ny + 1, nz};   // nz: the layers of free nodes
     double best = 1e300;
     for (int tx = 1; tx <= std::min(n1[0], kTileMax); ++tx)
         for (int ty = 1; ty <= std::min(n1[1], kTileMax); ++ty)
@@ -939,7 +967,7 @@ static dd_status cg_tables(dd_ctx *ctx, const MeshDev *const *gs, const CGBuffer
     int total = 0;
     for (int i = 0; i < n; ++i) {
         const int64_t share = std::max<int64_t>(1, (int64_t)((double)cap * (double)gs[i]->n_nodes / (double)nodes));
-        pick_tiles(gs[i]->nx, gs[i]->ny, gs[i]->nz, (int)share, T.seg[i].lv[0]);
+        pick_tiles(gs[i]->nx, gs[i]->ny, gs[i]->nz - cbs[i]->top, (int)share, T.seg[i].lv[0]);
         nblk[i] = (int)std::min<int64_t>(share, T.seg[i].lv[0].ntiles);
         total += nblk[i];
     }
@@ -981,7 +1009,8 @@ static dd_status cg_tables(dd_ctx *ctx, const MeshDev *const *gs, const CGBuffer
             L.ny = cb.lny[l];
             L.nz = cb.lnz[l];
             L.h = (float)(1 << l);
-            if (l > 0 && l < cb.glev) pick_tiles(L.nx, L.ny, L.nz, S.nblk, L);
+            L.top = cb.top;
+            if (l > 0 && l < cb.glev) pick_tiles(L.nx, L.ny, L.nz - cb.top, S.nblk, L);
             if (l == 0) {
                 L.r = S.r;
                 L.z = S.z;

@@ -60,7 +60,7 @@ __global__ void k_assemble_rhs(MeshDev g, ElemOps ops, const double *__restrict_
     int i, j, k;
     node_ijk(g, a, i, j, k);
     double out[6] = {0, 0, 0, 0, 0, 0};
-    if (k > 0) {
+    if (k > 0 && !(g.top_fixed && k == g.nz)) {   // free node
         out[3] = f[a * 3 + 0];
         out[4] = f[a * 3 + 1];
         out[5] = f[a * 3 + 2];
@@ -101,7 +101,7 @@ __global__ void k_block_jacobi(MeshDev g, const double *__restrict__ Ke, double 
     int i, j, k;
     node_ijk(g, a, i, j, k);
     double D[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    if (k > 0) {
+    if (k > 0 && !(g.top_fixed && k == g.nz)) {   // free node
         for (int oz = -1; oz <= 0; ++oz)
             for (int oy = -1; oy <= 0; ++oy)
                 for (int ox = -1; ox <= 0; ++ox) {
@@ -160,7 +160,7 @@ __device__ __forceinline__ void spmv_node(const MeshDev &g, const double *sKe, i
     node_ijk(g, a, i, j, k);
 #pragma unroll
     for (int c = 0; c < 6; ++c) y[c] = 0.0;
-    if (k == 0) return;
+    if (k == 0 || (g.top_fixed && k == g.nz)) return;   // fixed rows
     for (int oz = -1; oz <= 0; ++oz)
         for (int oy = -1; oy <= 0; ++oy)
             for (int ox = -1; ox <= 0; ++ox) {
@@ -514,9 +514,11 @@ void fem_mg_plan(const MeshDev &g, CGBuffers &cb) {
     cb.lnx[0] = g.nx;
     cb.lny[0] = g.ny;
     cb.lnz[0] = g.nz;
+    cb.top = g.top_fixed;
     while (cb.nlev < kMgMaxLev) {
         const int l = cb.nlev - 1;
         if (std::min(cb.lnx[l], std::min(cb.lny[l], cb.lnz[l])) < 2) break;
+        if (cb.top && cb.lnz[l] < 3) break;   // the coarser level keeps a layer of free nodes
         cb.lnx[l + 1] = (cb.lnx[l] + 1) / 2;
         cb.lny[l + 1] = (cb.lny[l] + 1) / 2;
         cb.lnz[l + 1] = (cb.lnz[l] + 1) / 2;
@@ -525,7 +527,7 @@ void fem_mg_plan(const MeshDev &g, CGBuffers &cb) {
     cb.glev = cb.nlev;
     cb.mg_ndof = 0;
     for (int l = 1; l < cb.nlev; ++l) {
-        const int64_t dofs = 3 * (int64_t)(cb.lnx[l] + 1) * (cb.lny[l] + 1) * cb.lnz[l];
+        const int64_t dofs = 3 * (int64_t)(cb.lnx[l] + 1) * (cb.lny[l] + 1) * (cb.lnz[l] - cb.top);
         if (dofs <= kMgDirectDofs) {   // coarsest level: solved exactly
             cb.nlev = l + 1;
             cb.glev = l;
@@ -537,10 +539,10 @@ void fem_mg_plan(const MeshDev &g, CGBuffers &cb) {
 
 void fem_mg_coarse_inverse(const CGBuffers &cb, const double *St, std::vector<float> &inv) {
     const int c = cb.glev, nx = cb.lnx[c], ny = cb.lny[c], nz = cb.lnz[c], n = cb.mg_ndof;
-    const int plane = (nx + 1) * (ny + 1);
+    const int plane = (nx + 1) * (ny + 1), zf = nz - cb.top;   // free layers 1 .. zf
     const double h = (double)(1 << c);
     std::vector<double> K((size_t)n * n, 0.0);
-    for (int Z = 1; Z <= nz; ++Z)
+    for (int Z = 1; Z <= zf; ++Z)
         for (int Y = 0; Y <= ny; ++Y)
             for (int X = 0; X <= nx; ++X) {
                 const int cx = X == 0 ? 0 : (X == nx ? 2 : 1), cy = Y == 0 ? 0 : (Y == ny ? 2 : 1), cz = Z == nz ? 2 : 1;
@@ -548,7 +550,7 @@ void fem_mg_coarse_inverse(const CGBuffers &cb, const double *St, std::vector<fl
                 const int fa = X + (nx + 1) * (Y + (ny + 1) * Z) - plane;
                 for (int d = 0; d < 27; ++d) {
                     const int x = X + d % 3 - 1, y = Y + (d / 3) % 3 - 1, z = Z + d / 9 - 1;
-                    if (x < 0 || y < 0 || z < 1 || x > nx || y > ny || z > nz) continue;
+                    if (x < 0 || y < 0 || z < 1 || x > nx || y > ny || z > zf) continue;
                     const int fb = x + (nx + 1) * (y + (ny + 1) * z) - plane;
                     const double *B = St + (cls * 27 + d) * 9;
                     for (int r = 0; r < 3; ++r)
@@ -638,6 +640,18 @@ double fem_jacobi_lambda_max(const double *St) {
         for (int a = 0; a < nn * 3; ++a) x[a] = y[a] * s;
     }
     return lam;
+}
+
+void fem_top_rotation(const MeshDev &g, double theta, double lx, double ly, double *x) {
+    const double c = std::cos(theta), s = std::sin(theta);
+    for (int j = 0; j <= g.ny; ++j)
+        for (int i = 0; i <= g.nx; ++i) {
+            const double dx = i * g.hx - 0.5 * lx, dy = j * g.hy - 0.5 * ly;
+            double *u = x + (size_t)(i + (int64_t)(g.nx + 1) * (j + (int64_t)(g.ny + 1) * g.nz)) * 6;
+            u[0] = (c - 1.0) * dx - s * dy;
+            u[1] = s * dx + (c - 1.0) * dy;
+            u[2] = 0.0;
+        }
 }
 
 void fem_traction_force(const MeshDev &g, const dd_load &L, double lx, double ly, double *f) {

@@ -10,6 +10,7 @@ struct MeshDev {
     int64_t n_nodes, n_el, n_gp;
     double hx, hy, hz;
     double w;            // Gauss weight * det J = hx hy hz / 8
+    int top_fixed;       // 1: the face z = lz is a Dirichlet boundary too (prescribed rotation)
 };
 
 // Physical shape-function gradients dN[gauss point][local node][x,y,z] of
@@ -35,6 +36,7 @@ struct CGBuffers {
     const double *St64;   // stencil table [27 classes][27 offsets][9] (fem_stencil_table)
     const float *St32;    // the same in FP32, blocks padded to 12 values
     // multigrid hierarchy (fem_mg_plan)
+    int top = 0;                               // the top layer of nodes is fixed on every level
     int nlev = 1, glev = 1;                    // levels; levels run by the whole grid (glev < nlev:
                                                // level glev is solved directly)
     int lnx[kMgMaxLev], lny[kMgMaxLev], lnz[kMgMaxLev];
@@ -62,6 +64,7 @@ inline MeshDev fem_mesh(const dd_mesh &m) {
     g.hy = m.ly / m.ny;
     g.hz = m.lz / m.nz;
     g.w = g.hx * g.hy * g.hz / 8.0;
+    g.top_fixed = 0;
     return g;
 }
 
@@ -78,6 +81,10 @@ void fem_mg_coarse_inverse(const CGBuffers &cb, const double *St64, std::vector<
 // iteration on a small box with the same elements, from the stencil table.
 double fem_jacobi_lambda_max(const double *St64);
 void fem_traction_force(const MeshDev &g, const dd_load &L, double lx, double ly, double *f);
+// Prescribed displacement of the top face turned by theta about the vertical
+// axis through its centre, written into the u part of x [n_nodes x 6]
+// (the other entries untouched).
+void fem_top_rotation(const MeshDev &g, double theta, double lx, double ly, double *x);
 
 dd_status fem_gather_star(dd_dataset *ds, const int32_t *idx, int64_t n_gp, double *star, double *ce,
                           cudaStream_t s);

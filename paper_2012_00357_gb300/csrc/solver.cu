@@ -198,6 +198,14 @@ extern "C" dd_status dd_solver_create(dd_dataset *ds, const dd_mesh *mesh, const
     for (int c = 0; c < 3; ++c)
         if (!std::isfinite(load->t0[c]) || !std::isfinite(load->tx[c]) || !std::isfinite(load->ty[c]))
             return dd_fail(ctx, DD_ERR_ARG, "dd_solver_create: non-finite load");
+    const bool rotate = load->rot_z != 0.0;
+    if (rotate) {
+        if (!std::isfinite(load->rot_z)) return dd_fail(ctx, DD_ERR_ARG, "dd_solver_create: non-finite rotation");
+        for (int c = 0; c < 3; ++c)
+            if (load->t0[c] != 0.0 || load->tx[c] != 0.0 || load->ty[c] != 0.0)
+                return dd_fail(ctx, DD_ERR_ARG, "dd_solver_create: traction and prescribed rotation on the same face");
+        if (mesh->nz < 2) return dd_fail(ctx, DD_ERR_ARG, "dd_solver_create: a prescribed rotation needs nz >= 2");
+    }
     DD_TRY_CUDA(ctx, cudaSetDevice(ctx->device));
     static std::atomic<uint64_t> next_id{1};
     dd_solver *sv = new dd_solver();
@@ -208,6 +216,7 @@ extern "C" dd_status dd_solver_create(dd_dataset *ds, const dd_mesh *mesh, const
     sv->o = o;
     sv->o.init_idx = nullptr;
     sv->g = fem_mesh(*mesh);
+    sv->g.top_fixed = rotate ? 1 : 0;
     fem_elem_ops(sv->g, &sv->ops);
     auto fail = [&](dd_status st) {
         dd_solver_free(sv);
@@ -231,6 +240,11 @@ extern "C" dd_status dd_solver_create(dd_dataset *ds, const dd_mesh *mesh, const
     for (int cd = 0; cd < 27 * 27; ++cd)
         for (int k = 0; k < 9; ++k) St32[cd * 12 + k] = (float)St64[cd * 9 + k];
     fem_traction_force(sv->g, *load, mesh->lx, mesh->ly, f.data());
+    // x starts at zero, with the prescribed top displacement in its u part;
+    // the solves keep those entries (fixed dofs) and the residual b - K x
+    // carries their coupling to the free dofs
+    std::vector<double> x0(nn * 6, 0.0);
+    if (rotate) fem_top_rotation(sv->g, load->rot_z, mesh->lx, mesh->ly, x0.data());
     cudaStream_t s = ctx->stream;
     if (cudaMemcpyAsync(sv->Ke, Ke.data(), 576 * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(sv->St64, St64.data(), St64.size() * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -238,7 +252,7 @@ extern "C" dd_status dd_solver_create(dd_dataset *ds, const dd_mesh *mesh, const
         (!Kinv.empty() &&
          cudaMemcpyAsync(sv->cb.mg_inv, Kinv.data(), Kinv.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) ||
         cudaMemcpyAsync(sv->f, f.data(), nn * 3 * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemsetAsync(sv->cb.x, 0, nn * 6 * 8, s) != cudaSuccess ||
+        cudaMemcpyAsync(sv->cb.x, x0.data(), nn * 6 * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(sv->mot.d, 0, ng * 2 * sizeof(float), s) != cudaSuccess ||
         cudaMemsetAsync(sv->stats, 0, kIterStatsDoubles * sizeof(double), s) != cudaSuccess)
         return fail(dd_fail(ctx, DD_ERR_CUDA, "dd_solver_create: upload"));

@@ -96,3 +96,46 @@ def test_mixed_precision_cg_matches_fp64_cg(ctx):
     assert r64.iters == rmx.iters and np.array_equal(r64.idx, rmx.idx)
     assert np.allclose(rmx.u, r64.u, rtol=0, atol=1e-9 * np.abs(r64.u).max())
     assert np.allclose(rmx.eta, r64.eta, rtol=0, atol=1e-9 * np.abs(r64.eta).max() + 1e-300)
+
+
+@pytest.mark.parametrize("n_el,deg", [(3, 0.1), (4, 0.1), (5, 2.0), (6, 0.1)])
+def test_top_rotation_matches_oracle(ctx, n_el, deg):
+    """The paper's own boundary-value problem: the top face turned by a
+    prescribed angle about the vertical axis (non-homogeneous Dirichlet
+    values for u, homogeneous for eta), bottom clamped.  Meshes with even and
+    odd element counts (both multigrid coarsenings with a fixed top)."""
+    data = I.make_dataset(5000, I.LINEAR, seed=11)
+    load = I.top_rotation(deg)
+    init = I.initial_association(8 * n_el ** 3, len(data), seed=12)
+    ds = P.dd_load_dataset(ctx, data, C)
+    try:
+        r = P.dd_solve(ds, ctx, n_el, load, init_idx=init)
+    finally:
+        P.dd_free_dataset(ds)
+    o = odd.DDProblem(data, C, n_el, load).solve(init)
+    compare(r, o)
+
+
+def test_top_rotation_mixed_cg_matches_fp64_cg(ctx):
+    data = I.make_dataset(6000, I.NONLINEAR, seed=13)
+    load = I.top_rotation(0.5)
+    init = I.initial_association(8 * 64, len(data), seed=14)
+    ds = P.dd_load_dataset(ctx, data, C)
+    try:
+        r64 = P.dd_solve(ds, ctx, 4, load, init_idx=init, cg_mode=1)
+        rmx = P.dd_solve(ds, ctx, 4, load, init_idx=init, cg_mode=0)
+    finally:
+        P.dd_free_dataset(ds)
+    assert r64.iters == rmx.iters and np.array_equal(r64.idx, rmx.idx)
+    assert np.allclose(rmx.u, r64.u, rtol=0, atol=1e-9 * np.abs(r64.u).max())
+
+
+def test_rotation_with_traction_is_rejected(ctx):
+    data = I.make_dataset(500, I.LINEAR, seed=1)
+    ds = P.dd_load_dataset(ctx, data, C)
+    try:
+        bad = I.Load(t0=(0.0, 0.0, 1e-3), rot_z=0.01)
+        with pytest.raises(P.DDError):
+            P.dd_solve(ds, ctx, 3, bad)
+    finally:
+        P.dd_free_dataset(ds)
