@@ -13,6 +13,7 @@ independent replica (the search does not shard).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -32,6 +33,23 @@ METRIC = "DD searches/s & solve time at N=1e9 (ANN vs exact); p50/p99 serve late
 UNIT = "searches/s"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 L2_BYTES = 129 * 2 ** 20
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per search of
+# the dominant kernels, from one-pass ncu captures of the same workload and
+# mode, keyed by the sha256 of the kernels' source file: a changed source
+# reports null until it is captured again.
+TRAFFIC = {
+    # (workload, mode): (source file under the package's csrc/, sha256, bytes per launch)
+}
+
+
+def captured_traffic(workload: str, mode: str):
+    t = TRAFFIC.get((workload, mode))
+    if t is None:
+        return None
+    path, sha, byts = t
+    with open(os.path.join(ROOT, "paper_2012_00357_gb300", "csrc", path), "rb") as f:
+        return byts if hashlib.sha256(f.read()).hexdigest() == sha else None
 
 
 def load_peaks():
@@ -283,27 +301,30 @@ def run_ours(args, world, rank, local):
     kc = 3 if (mode == P.DD_SEARCH_EXACT_TC and certify) else 1
     scan_avg = statistics.mean(scan_ms)
     if mode == P.DD_SEARCH_ANN:
-        # centroid ranking + warp scans of the probed clusters.  Algorithmic HBM
-        # bytes = the distinct clusters the search read (each must come from
-        # memory at least once) x 48 B per point + 48 B per query + the
-        # centroid table once; clusters probed by several queries are re-read
-        # from L2, reported beside as the on-chip read rate.
+        # centroid ranking + warp scans of the probed clusters.  Algorithmic
+        # bytes per launch = the probed clusters' points of every non-skipped
+        # query x 48 B + 48 B per query.  Clusters probed by several queries
+        # come from L1/L2, so the rate can pass the HBM copy bandwidth; the
+        # distinct clusters read (each must come from memory at least once)
+        # are reported beside it.
         unique = statistics.mean(i.unique_points for i in infos)
         scanned = statistics.mean(i.points for i in infos)
-        byts = unique * 48 + W.m * nload * 48 + nlist * 52
+        byts = scanned * 48 + W.m * nload * 48
         achieved = byts / (scan_avg / 1e3) / 1e9
         roof = {"kernel": "k_ann_probe2 + centroid scan" if levels == 2 else "k_ann_probe + centroid scan",
                 "bound": "hbm", "achieved": achieved,
-                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                "traffic": captured_traffic(W.name, args.mode),
                 "peak_source": f"{peaks['source']} copy bandwidth",
-                "algorithmic": "48 B x points of the distinct clusters read + 48 B x queries + 52 B x centroids, per launch",
-                "points_read_gbs": (scanned * 48 + W.m * nload * 48) / (scan_avg / 1e3) / 1e9}
+                "algorithmic": "48 B x points of the clusters each non-skipped query probed + 48 B x queries, per launch",
+                "distinct_gbs": (unique * 48 + W.m * nload * 48 + nlist * 52) / (scan_avg / 1e3) / 1e9,
+                "algorithmic_bytes": byts}
     elif mode == P.DD_SEARCH_EXACT_TC:
         flops = 2.0 * W.m * W.N * 16 * kc
         achieved = flops / (scan_avg / 1e3) / 1e12
         roof = {"kernel": f"k_scan_tc<{kc}>", "bound": "tensor", "achieved": achieved,
                 "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "frac": achieved / peaks["bf16_tflops"],
-                "traffic": None, "peak_source": f"{peaks['source']} bf16 dense burst (fp16 same rate)",
+                "traffic": captured_traffic(W.name, args.mode), "peak_source": f"{peaks['source']} bf16 dense burst (fp16 same rate)",
                 "algorithmic": f"2*m*N*16*{kc} flops per launch (K padded to 16 per FP16 term)"}
     else:
         # FP32 CUDA-core scan: 12 FFMA per (query, point); peak from unit counts and clocks
@@ -312,7 +333,7 @@ def run_ours(args, world, rank, local):
         flops = 2.0 * 12 * W.m * W.N
         achieved = flops / (scan_avg / 1e3) / 1e12
         roof = {"kernel": "k_scan_fp32", "bound": "alu", "achieved": achieved, "peak": peak_tflops,
-                "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": captured_traffic(W.name, args.mode),
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock",
                 "algorithmic": "2*12*m*N flops per launch (12 FFMA per pair)"}
 
@@ -325,7 +346,9 @@ def run_ours(args, world, rank, local):
         "config": {"workload": W.name, "mesh": f"{W.n_el}^3 hex, 2x2x2 Gauss", "material_points": W.m * nload,
                    "data_points": W.N, "law": W.law.kind, "load": W.loads[0][0], "search": args.mode,
                    "l2": "flushed before every step" if flush_l2 else "inputs larger than L2",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}",
+                   **({"f_d": f"{args.fd0} -> {args.fd_final} over {args.ramp_iters} iterations",
+                       "nlist": nlist, "ann_levels": levels} if mode == P.DD_SEARCH_ANN else {})},
         "roofline": roof,
         "e2e": {"value": m_e2e * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": m_e2e * 96,
                 "d2h_bytes_per_step": m_e2e * 12,
@@ -479,9 +502,10 @@ def main():
     # iterations keeps the DD solution within 1e-3 of the exact-search one
     # (the paper's ramp from 0, or a final f_d below 0.6, ends at a worse
     # fixed point on these workloads)
-    ap.add_argument("--fd-final", type=float, default=0.6)
-    ap.add_argument("--fd0", type=float, default=0.3, help="f_d of the first iteration")
-    ap.add_argument("--ramp-iters", type=int, default=5)
+    ap.add_argument("--fd-final", type=float, default=None,
+                    help="final f_d of the approximate search (default: the workload's schedule, else 0.6)")
+    ap.add_argument("--fd0", type=float, default=None, help="f_d of the first iteration (default: workload's, else 0.3)")
+    ap.add_argument("--ramp-iters", type=int, default=None, help="iterations of the f_d ramp (default: workload's, else 5)")
     ap.add_argument("--nlist", type=int, default=0)
     ap.add_argument("--ann-levels", type=int, default=0)
     ap.add_argument("--ann-check", type=int, default=2048)
@@ -490,6 +514,11 @@ def main():
     args = ap.parse_args()
     if args.mode is None:
         args.mode = "serve" if args.workload.startswith("serve") else ("ann" if "_ann" in args.workload else "tc")
+    # f_d schedule of the approximate search: the workload's, unless given
+    sched = I.WORKLOADS[args.workload].extra.get("schedule", (0.3, 0.6, 5))
+    args.fd0 = sched[0] if args.fd0 is None else args.fd0
+    args.fd_final = sched[1] if args.fd_final is None else args.fd_final
+    args.ramp_iters = sched[2] if args.ramp_iters is None else args.ramp_iters
     world, rank, local = dist_setup()
     if args.impl == "reference":
         line = run_reference(args, world, rank)

@@ -222,6 +222,8 @@ def load_case(name: str, t: float) -> Load:
         return Load(tx=(0.0, 0.0, 2.0 * t))
     if name == "torsion":      # t = 2t (-(y - 1/2), x - 1/2, 0)
         return Load(tx=(0.0, 2.0 * t, 0.0), ty=(-2.0 * t, 0.0, 0.0))
+    if name == "rotation":     # prescribed top rotation, t in degrees
+        return top_rotation(t)
     raise ValueError(name)
 
 
@@ -275,6 +277,9 @@ class Workload:
 
 LINEAR = DataLaw("linear", -2e-3, 2e-3, 1e-5)
 NONLINEAR = DataLaw("nonlinear", -5e-3, 5e-3, 1e-5)
+# the strain range of the paper's torsion data (Sec. 3.1: [-0.025, 0.025]),
+# with a milder stiffening (the factor 1 + beta |eps| stays below 1.6)
+TORSION_LAW = DataLaw("nonlinear", -0.025, 0.025, 1e-5, beta=10.0)
 
 WORKLOADS = {
     "cube4_N1e4_exact_fp64": Workload("cube4_N1e4_exact_fp64", 4, 10_000, LINEAR),
@@ -288,6 +293,13 @@ WORKLOADS = {
     "cube16_N3e7_ann": Workload("cube16_N3e7_ann", 16, 30_000_000, NONLINEAR),
     # (the search is cheap in the latter)
     "cube32_N1e5_exact": Workload("cube32_N1e5_exact", 32, 100_000, NONLINEAR),
+    # the paper's own problem (Sec. 3.1): 20^3 cube, top face turned by 2
+    # degrees, 64 000 material points; approximate-search schedule f_d 0.4 ->
+    # 0.8 over 5 iterations (f_d0, f_d_final, ramp)
+    "cube20_N1e9_rot2_ann": Workload("cube20_N1e9_rot2_ann", 20, 1_000_000_000, TORSION_LAW,
+                                     loads=(("rotation", 2.0),), extra={"schedule": (0.4, 0.8, 5)}),
+    "cube20_N1e8_rot2_ann": Workload("cube20_N1e8_rot2_ann", 20, 100_000_000, TORSION_LAW,
+                                     loads=(("rotation", 2.0),), extra={"schedule": (0.4, 0.8, 5)}),
     "serve_N1e7": Workload("serve_N1e7", 0, 10_000_000, NONLINEAR,
                            extra={"requests": 512, "edge_min": 4, "edge_max": 24,
                                   "t_min": 1e-4, "t_max": 2e-3}),
