@@ -181,20 +181,22 @@ def run_ours(args, world, rank, local):
     W = make_workload(args.workload)
     C = I.isotropic_C(W.law.E, W.law.nu)
     mode = {"tc": P.DD_SEARCH_EXACT_TC, "tc_topk": P.DD_SEARCH_EXACT_TC, "fp32": P.DD_SEARCH_EXACT_FP32,
-            "ann": P.DD_SEARCH_ANN}[args.mode]
+            "ann": P.DD_SEARCH_ANN, "knng": P.DD_SEARCH_KNNG}[args.mode]
+    approx = mode in (P.DD_SEARCH_ANN, P.DD_SEARCH_KNNG)
     nlist = 0
-    if mode == P.DD_SEARCH_ANN:
+    if approx:
         nlist = args.nlist or max(64, 1 << int(np.log2(max(W.N // 3000, 64))))
     certify = args.mode != "tc_topk"
     ctx = P.dd_create(local)
     raw = torch.empty((W.N, 12), dtype=torch.float32, device="cuda")
     P.dd_synth_dataset(ctx, raw, W.law, C, seed=W.seed)
     t_build = time.perf_counter()
-    levels = args.ann_levels or (2 if W.N >= 300_000_000 else 1)
-    if mode == P.DD_SEARCH_ANN and levels == 2 and not args.nlist:
-        nlist = 1 << 20
+    levels = args.ann_levels or (2 if W.N >= 300_000_000 or mode == P.DD_SEARCH_KNNG else 1)
+    if approx and levels == 2 and not args.nlist:
+        nlist = 1 << 20 if W.N >= 300_000_000 else 1 << 17
+    knn = dict(knn_k=args.knn_k, knn_fd=args.knn_fd) if mode == P.DD_SEARCH_KNNG else {}
     ds = P.dd_load_dataset(ctx, raw, C, borrow=True, build_fp16=(mode == P.DD_SEARCH_EXACT_TC), ann_nlist=nlist,
-                           seed=1, ann_levels=levels)
+                           seed=1, ann_levels=levels, **knn)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t_build
     load = I.load_case(*W.loads[0])
@@ -202,6 +204,8 @@ def run_ours(args, world, rank, local):
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     data_bytes = W.N * (64 if mode == P.DD_SEARCH_EXACT_TC else 52 if mode == P.DD_SEARCH_EXACT_FP32 else 48)
     ann_kw = dict(f_d0=args.fd0, f_d_final=args.fd_final, ramp_iters=args.ramp_iters) if mode == P.DD_SEARCH_ANN else {}
+    if mode == P.DD_SEARCH_KNNG:
+        ann_kw = dict(f_s=args.f_s)
     flush_l2 = data_bytes < 2 * L2_BYTES
 
     loads = [I.load_case(*lc) for lc in W.loads]
@@ -267,7 +271,7 @@ def run_ours(args, world, rank, local):
     solve_s = time.perf_counter() - t
     r = rs[0]
     accuracy = None
-    if mode == P.DD_SEARCH_ANN and args.ann_check > 0:
+    if approx and args.ann_check > 0:
         # agreement of the approximate answers with the certified exact search
         # on a sample of the final states (FP32 scan + FP64 rescoring)
         ys = np.concatenate([np.concatenate([rr.eps, rr.sig], axis=1) for rr in rs])
@@ -278,11 +282,15 @@ def run_ours(args, world, rank, local):
         da = np.empty(len(pick))
         ie = np.empty(len(pick), np.int32)
         de = np.empty(len(pick))
-        P.dd_project_nearest(ds, ctx, ysel, ia, da, mode=P.DD_SEARCH_ANN, f_d=args.fd_final, prev_idx=prev)
+        P.dd_project_nearest(ds, ctx, ysel, ia, da, mode=mode, f_d=args.fd_final, prev_idx=prev, f_s=args.f_s)
+        torch.cuda.synchronize()
+        t_ex = time.perf_counter()
         P.dd_project_nearest(ds, ctx, ysel, ie, de, mode=P.DD_SEARCH_EXACT_FP32)
+        t_ex = time.perf_counter() - t_ex
         accuracy = {"sample": int(len(pick)), "same_index": float(np.mean(ia == ie)),
                     "mean_rel_distance_excess": float(np.mean((da - de) / np.maximum(de, 1e-300))),
-                    "f_d": args.fd_final}
+                    **({"f_d": args.fd_final} if mode == P.DD_SEARCH_ANN else {"f_s": args.f_s, "k": args.knn_k}),
+                    "exact_fp32_searches_per_s": len(pick) / t_ex}
 
     # end-to-end through the public API with host buffers (pinned): one
     # projection of the step's m states per call, copies inside the timed region
@@ -290,11 +298,12 @@ def run_ours(args, world, rank, local):
     y = torch.from_numpy(I.make_states(m_e2e, W.law, seed=7, spread=0.05)).pin_memory()
     idx_h = torch.empty(m_e2e, dtype=torch.int32).pin_memory()
     d2_h = torch.empty(m_e2e, dtype=torch.float64).pin_memory()
-    P.dd_project_nearest(ds, ctx, y.numpy(), idx_h.numpy(), d2_h.numpy(), mode=mode, certify=certify)
+    e2e_kw = dict(mode=mode, certify=certify, f_d=args.fd_final, f_s=args.f_s)
+    P.dd_project_nearest(ds, ctx, y.numpy(), idx_h.numpy(), d2_h.numpy(), **e2e_kw)
     reps = max(3, args.steps)
     t = time.perf_counter()
     for _ in range(reps):
-        P.dd_project_nearest(ds, ctx, y.numpy(), idx_h.numpy(), d2_h.numpy(), mode=mode, certify=certify)
+        P.dd_project_nearest(ds, ctx, y.numpy(), idx_h.numpy(), d2_h.numpy(), **e2e_kw)
     e2e_s = max_over_ranks((time.perf_counter() - t) / reps, world)
 
     peaks = load_peaks()
@@ -319,6 +328,16 @@ def run_ours(args, world, rank, local):
                 "algorithmic": "48 B x points of the clusters each non-skipped query probed + 48 B x queries, per launch",
                 "distinct_gbs": (unique * 48 + W.m * nload * 48 + nlist * 52) / (scan_avg / 1e3) / 1e9,
                 "algorithmic_bytes": byts}
+    elif mode == P.DD_SEARCH_KNNG:
+        # greedy walks: every evaluated neighbour costs its 4 B index and its
+        # 48 B row, every query its 48 B record
+        evals = statistics.mean(i.points for i in infos)
+        byts = evals * 52 + W.m * nload * 48
+        achieved = byts / (scan_avg / 1e3) / 1e9
+        roof = {"kernel": "k_knng_walk", "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": captured_traffic(W.name, args.mode),
+                "peak_source": f"{peaks['source']} copy bandwidth",
+                "algorithmic": "52 B x neighbours evaluated + 48 B x queries, per launch", "algorithmic_bytes": byts}
     elif mode == P.DD_SEARCH_EXACT_TC:
         flops = 2.0 * W.m * W.N * 16 * kc
         achieved = flops / (scan_avg / 1e3) / 1e12
@@ -348,7 +367,9 @@ def run_ours(args, world, rank, local):
                    "l2": "flushed before every step" if flush_l2 else "inputs larger than L2",
                    "parallelism": f"replicas x{world}",
                    **({"f_d": f"{args.fd0} -> {args.fd_final} over {args.ramp_iters} iterations",
-                       "nlist": nlist, "ann_levels": levels} if mode == P.DD_SEARCH_ANN else {})},
+                       "nlist": nlist, "ann_levels": levels} if mode == P.DD_SEARCH_ANN else {}),
+                   **({"knn_k": args.knn_k, "knn_fd": args.knn_fd, "f_s": args.f_s, "nlist": nlist}
+                      if mode == P.DD_SEARCH_KNNG else {})},
         "roofline": roof,
         "e2e": {"value": m_e2e * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": m_e2e * 96,
                 "d2h_bytes_per_step": m_e2e * 12,
@@ -371,6 +392,7 @@ def run_ours(args, world, rank, local):
             "distances_per_query": statistics.mean(i.distances for i in infos) / (W.m * nload),
             "points_per_query": statistics.mean(i.points for i in infos) / (W.m * nload),
             "distinct_points_per_step": statistics.mean(i.unique_points for i in infos),
+            "walk_moves_per_query": statistics.mean(i.moves for i in infos) / (W.m * nload),
         },
     }
     for sv in svs:
@@ -494,7 +516,7 @@ def main():
     # the headline metric is quoted at N = 10^9: the 32^3 cube with 4 load
     # cases on 10^9 points, approximate search (the other workloads by flag)
     ap.add_argument("--workload", default="cube32_N1e9_ann_4loads")
-    ap.add_argument("--mode", default=None, choices=["tc", "tc_topk", "fp32", "ann", "serve"],
+    ap.add_argument("--mode", default=None, choices=["tc", "tc_topk", "fp32", "ann", "knng", "serve"],
                     help="search mode (default: ann for *_ann workloads, serve for serve_*, else tc)")
     ap.add_argument("--max-batch", type=int, default=64)
     ap.add_argument("--serve-budget-gb", type=float, default=16.0)
@@ -509,11 +531,15 @@ def main():
     ap.add_argument("--nlist", type=int, default=0)
     ap.add_argument("--ann-levels", type=int, default=0)
     ap.add_argument("--ann-check", type=int, default=2048)
+    ap.add_argument("--knn-k", type=int, default=32, help="k of the k-NN graph (graph search)")
+    ap.add_argument("--knn-fd", type=float, default=0.6, help="f_d of the graph build")
+    ap.add_argument("--f-s", type=int, default=0, help="node-change bound of the graph walk (0: none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()
     if args.mode is None:
-        args.mode = "serve" if args.workload.startswith("serve") else ("ann" if "_ann" in args.workload else "tc")
+        args.mode = ("serve" if args.workload.startswith("serve") else "ann" if "_ann" in args.workload
+                     else "knng" if "_knng" in args.workload else "tc")
     # f_d schedule of the approximate search: the workload's, unless given
     sched = I.WORKLOADS[args.workload].extra.get("schedule", (0.3, 0.6, 5))
     args.fd0 = sched[0] if args.fd0 is None else args.fd0

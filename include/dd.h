@@ -64,8 +64,12 @@ enum {
     DD_SEARCH_EXACT_FP32 = 0,  /* exact: FP32 streaming scan + FP64 rescoring */
     DD_SEARCH_EXACT_TC = 1,    /* exact: FP16 tensor-core contraction, FP32
                                   accumulation, candidates rescored in FP64 */
-    DD_SEARCH_ANN = 2          /* approximate k-means partition search (Eq. 13),
+    DD_SEARCH_ANN = 2,         /* approximate k-means partition search (Eq. 13),
                                   warm-started from the previous neighbour */
+    DD_SEARCH_KNNG = 3         /* approximate greedy walk in the k-nearest-
+                                  neighbour graph (Sec. 4.4), warm-started from
+                                  the previous neighbour; needs a data set
+                                  loaded with knn_k > 0 */
 };
 
 /* ------------------------------------------------------------------------ */
@@ -106,6 +110,15 @@ typedef struct dd_dataset_opts {
                            2: a two-level k-means tree, about sqrt(ann_nlist)
                            coarse cells each split into leaves, ann_nlist
                            leaves in total (for 10^8 - 10^9 points) */
+    int knn_k;          /* 1..32: also build the k-nearest-neighbour graph of
+                           DD_SEARCH_KNNG (Sec. 4.4): every point linked to the
+                           knn_k nearest other points that a search of the
+                           two-level tree (ann_levels = 2, required) finds
+                           for it at accuracy knn_fd (Eq. 13); 4 * knn_k + 4
+                           bytes per point.  0: no graph */
+    double knn_fd;      /* f_d of the graph build (0 .. 1; 1 with at most 8
+                           coarse cells of at most 8 leaves gives the exact
+                           graph) */
 } dd_dataset_opts;
 
 /* Load a material data set D = {(eps_j, sig_j)}, j = 0..N-1 (Sec. 2) and
@@ -140,6 +153,15 @@ size_t dd_dataset_bytes(const dd_dataset *ds);
 int dd_dataset_ann_nlist(const dd_dataset *ds);
 dd_status dd_dataset_ann_index(dd_dataset *ds, int32_t *cluster_of, double *centroids, double *radii);
 
+/* The k-nearest-neighbour graph of DD_SEARCH_KNNG (Sec. 4.4, built when
+ * knn_k > 0): its k (0 if none), and a host copy.
+ *   nbr  host int32 [N x k]: row j holds the data indices of the neighbours
+ *        of point j, nearest first (FP32 distances in the mapped coordinates,
+ *        ties to the lower sorted position); -1 where fewer than k were found
+ * Errors: DD_ERR_STATE if no graph was built.  Synchronous. */
+int dd_dataset_knn_k(const dd_dataset *ds);
+dd_status dd_dataset_knn_graph(dd_dataset *ds, int32_t *nbr);
+
 /* Write points start .. start+N-1 of the seeded synthetic data set into the
  * device buffer out_dev (float32 [N x 12]).  This is the device copy of the
  * input generator of the Python module dd_inputs (SplitMix64 counter stream,
@@ -169,6 +191,12 @@ typedef struct dd_search_opts {
     const int32_t *prev_idx;  /* DD_SEARCH_ANN: previous neighbour of each
                                  query (warm start), host or device, or NULL */
     void *stream;             /* cudaStream_t for device pointers, NULL = ctx */
+    int f_s;                  /* DD_SEARCH_KNNG: at most f_s node changes per
+                                 walk (the bound of Sec. 4.4); 0 = walk to a
+                                 local minimum of the graph.  Without
+                                 prev_idx the walk of query i starts at data
+                                 point SplitMix64(i) mod N (the first output
+                                 of SplitMix64 seeded with i) */
 } dd_search_opts;
 
 typedef struct dd_search_stats {
@@ -184,6 +212,7 @@ typedef struct dd_search_stats {
     int64_t unique_points;    /* approximate search: points of the distinct
                                  clusters it read (what it must fetch from
                                  memory at least once) */
+    int64_t moves;            /* DD_SEARCH_KNNG: node changes of all walks */
 } dd_search_stats;
 
 /* Nearest data point of each state y_i (Eq. 7):
@@ -269,6 +298,8 @@ typedef struct dd_solve_opts {
                                  (residual b - K x and x in FP64, stop test
                                  |b - K x| <= cg_rtol |b| in FP64); 1 = FP64
                                  preconditioned CG throughout */
+    int f_s;                  /* DD_SEARCH_KNNG: node-change bound of every
+                                 walk, as in dd_search_opts (0 = none) */
 } dd_solve_opts;
 
 /* Result of a solve: the constraint-set state y = (u, eps, sig) of the last
@@ -324,6 +355,7 @@ typedef struct dd_iter_info {
     int64_t unique_points;    /* ANN: points of the distinct clusters read */
     int graph;                /* 1: dd_solvers_step replayed (or captured) the
                                  step as a CUDA graph; 0: launched eagerly */
+    int64_t moves;            /* DD_SEARCH_KNNG: node changes of the walks */
 } dd_iter_info;
 
 /* Set up a DD problem (mesh, load, options as for dd_solve) on the data set:

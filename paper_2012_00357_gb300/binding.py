@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libdd.so")
 DD_OK, DD_ERR_ARG, DD_ERR_NOT_SPD, DD_ERR_OOM, DD_ERR_CUDA, DD_ERR_TIMEOUT, DD_ERR_NOT_CONVERGED, DD_ERR_STATE = range(8)
 STATUS_NAMES = ["DD_OK", "DD_ERR_ARG", "DD_ERR_NOT_SPD", "DD_ERR_OOM", "DD_ERR_CUDA", "DD_ERR_TIMEOUT",
                 "DD_ERR_NOT_CONVERGED", "DD_ERR_STATE"]
-DD_SEARCH_EXACT_FP32, DD_SEARCH_EXACT_TC, DD_SEARCH_ANN = 0, 1, 2
+DD_SEARCH_EXACT_FP32, DD_SEARCH_EXACT_TC, DD_SEARCH_ANN, DD_SEARCH_KNNG = 0, 1, 2, 3
 
 # Entry points declared in include/dd.h (checked by the tests).
 EXPORTS = [
@@ -27,6 +27,7 @@ EXPORTS = [
     "dd_dataset_size", "dd_dataset_bytes", "dd_synth_dataset", "dd_project_nearest", "dd_solve",
     "dd_result_free", "dd_solver_create", "dd_solver_step", "dd_solver_done", "dd_solver_result",
     "dd_solver_free", "dd_launch_count", "dd_dataset_ann_nlist", "dd_dataset_ann_index",
+    "dd_dataset_knn_k", "dd_dataset_knn_graph",
     "dd_project_nearest_noalloc", "dd_solvers_step", "dd_solve_batch", "dd_server_start", "dd_server_submit",
     "dd_server_poll", "dd_server_get_stats", "dd_server_stop",
 ]
@@ -41,17 +42,19 @@ class DDError(RuntimeError):
 
 class dd_dataset_opts(ctypes.Structure):
     _fields_ = [("build_fp16", c_int), ("ann_nlist", c_int), ("ann_train_iters", c_int),
-                ("ann_sample", c_int64), ("seed", c_uint64), ("borrow", c_int), ("ann_levels", c_int)]
+                ("ann_sample", c_int64), ("seed", c_uint64), ("borrow", c_int), ("ann_levels", c_int),
+                ("knn_k", c_int), ("knn_fd", c_double)]
 
 
 class dd_search_opts(ctypes.Structure):
     _fields_ = [("mode", c_int), ("certify", c_int), ("f_d", c_double), ("prev_idx", c_void_p),
-                ("stream", c_void_p)]
+                ("stream", c_void_p), ("f_s", c_int)]
 
 
 class dd_search_stats(ctypes.Structure):
     _fields_ = [("uncertified", c_int64), ("distances", c_int64), ("skipped", c_int64), ("ms", c_double),
-                ("scan_ms", c_double), ("points", c_int64), ("unique_points", c_int64)]
+                ("scan_ms", c_double), ("points", c_int64), ("unique_points", c_int64),
+                ("moves", c_int64)]
 
 
 class dd_iter_info(ctypes.Structure):
@@ -59,7 +62,7 @@ class dd_iter_info(ctypes.Structure):
                 ("cg_iters", c_int), ("cg_ms", c_double), ("search_ms", c_double), ("other_ms", c_double),
                 ("scan_ms", c_double), ("uncertified", c_int64), ("distances", c_int64), ("f_d", c_double),
                 ("done", c_int), ("skipped", c_int64), ("points", c_int64), ("unique_points", c_int64),
-                ("graph", c_int)]
+                ("graph", c_int), ("moves", c_int64)]
 
 
 class dd_mesh(ctypes.Structure):
@@ -80,7 +83,8 @@ def _load(L) -> dd_load:
 class dd_solve_opts(ctypes.Structure):
     _fields_ = [("mode", c_int), ("certify", c_int), ("f_d0", c_double), ("f_d_final", c_double),
                 ("ramp_iters", c_int), ("max_iter", c_int), ("cg_rtol", c_double), ("cg_max_iter", c_int),
-                ("seed", c_uint64), ("init_idx", c_void_p), ("stall_iters", c_int), ("cg_mode", c_int)]
+                ("seed", c_uint64), ("init_idx", c_void_p), ("stall_iters", c_int), ("cg_mode", c_int),
+                ("f_s", c_int)]
 
 
 class dd_server_opts(ctypes.Structure):
@@ -146,6 +150,9 @@ def lib():
         L.dd_dataset_ann_nlist.argtypes = [vp]
         L.dd_dataset_ann_nlist.restype = c_int
         L.dd_dataset_ann_index.argtypes = [vp, vp, vp, vp]
+        L.dd_dataset_knn_k.argtypes = [vp]
+        L.dd_dataset_knn_k.restype = c_int
+        L.dd_dataset_knn_graph.argtypes = [vp, vp]
         L.dd_project_nearest_noalloc.argtypes = [vp, vp, c_int64, vp, vp, vp]
         L.dd_solvers_step.argtypes = [POINTER(vp), c_int, POINTER(dd_iter_info)]
         L.dd_server_start.argtypes = [vp, POINTER(dd_server_opts), POINTER(vp)]
@@ -208,11 +215,12 @@ def dd_bytes_in_use(ctx) -> int:
 
 
 def dd_load_dataset(ctx, eps_sig, C, build_fp16: bool = False, ann_nlist: int = 0, ann_train_iters: int = 0,
-                    ann_sample: int = 0, seed: int = 0, borrow: bool = False, ann_levels: int = 1):
+                    ann_sample: int = 0, seed: int = 0, borrow: bool = False, ann_levels: int = 1,
+                    knn_k: int = 0, knn_fd: float = 0.6):
     N = int(eps_sig.shape[0])
     assert tuple(eps_sig.shape[1:]) == (12,)
     opts = dd_dataset_opts(int(build_fp16), int(ann_nlist), int(ann_train_iters), int(ann_sample), int(seed),
-                           int(borrow), int(ann_levels))
+                           int(borrow), int(ann_levels), int(knn_k), float(knn_fd))
     ds = c_void_p()
     _check(ctx, lib().dd_load_dataset(ctx, _ptr(eps_sig), N, _Cmat(C), ctypes.byref(opts), ctypes.byref(ds)))
     return ds
@@ -238,9 +246,9 @@ def dd_synth_dataset(ctx, out_dev, law, C, seed: int = 0, start: int = 0, stream
 
 
 def dd_project_nearest(ds, ctx, y, idx, d2=None, mode: int = DD_SEARCH_EXACT_FP32, certify: bool = True,
-                       f_d: float = 0.0, prev_idx=None, stream=None, want_stats: bool = True):
+                       f_d: float = 0.0, prev_idx=None, stream=None, want_stats: bool = True, f_s: int = 0):
     m = int(y.shape[0])
-    opts = dd_search_opts(int(mode), int(certify), float(f_d), _ptr(prev_idx), stream)
+    opts = dd_search_opts(int(mode), int(certify), float(f_d), _ptr(prev_idx), stream, int(f_s))
     st = dd_search_stats()
     _check(ctx, lib().dd_project_nearest(ds, _ptr(y), m, ctypes.byref(opts), _ptr(idx), _ptr(d2),
                                          ctypes.byref(st) if want_stats else None))
@@ -270,14 +278,15 @@ class Result:
 def dd_solve(ds, ctx, n_el, load, mode: int = DD_SEARCH_EXACT_FP32, init_idx=None, max_iter: int = 100,
              cg_rtol: float = 1e-12, cg_max_iter: int = 20000, certify: bool = True, f_d0: float = 0.0,
              f_d_final: float = 0.0, ramp_iters: int = 20, seed: int = 0, stall_iters: int = 3,
-             lengths=(1.0, 1.0, 1.0), allow_not_converged: bool = True, cg_mode: int = 0):
+             lengths=(1.0, 1.0, 1.0), allow_not_converged: bool = True, cg_mode: int = 0, f_s: int = 0):
     """Solve one cube problem; `load` is a dd_inputs.Load.  Returns a Result."""
     nx, ny, nz = (n_el, n_el, n_el) if np.isscalar(n_el) else n_el
     mesh = dd_mesh(nx, ny, nz, *lengths)
     L = _load(load)
     ii = None if init_idx is None else np.ascontiguousarray(init_idx, dtype=np.int32)
     opts = dd_solve_opts(int(mode), int(certify), float(f_d0), float(f_d_final), int(ramp_iters), int(max_iter),
-                         float(cg_rtol), int(cg_max_iter), int(seed), _ptr(ii), int(stall_iters), int(cg_mode))
+                         float(cg_rtol), int(cg_max_iter), int(seed), _ptr(ii), int(stall_iters), int(cg_mode),
+                         int(f_s))
     r = dd_result()
     st = lib().dd_solve(ds, ctypes.byref(mesh), ctypes.byref(L), ctypes.byref(opts), ctypes.byref(r))
     try:
@@ -295,22 +304,23 @@ def dd_result_free(r: dd_result) -> None:
 
 
 def _solve_args(n_el, load, mode, init_idx, max_iter, cg_rtol, cg_max_iter, certify, f_d0, f_d_final, ramp_iters,
-                seed, stall_iters, lengths, cg_mode=0):
+                seed, stall_iters, lengths, cg_mode=0, f_s=0):
     nx, ny, nz = (n_el, n_el, n_el) if np.isscalar(n_el) else n_el
     mesh = dd_mesh(nx, ny, nz, *lengths)
     L = _load(load)
     ii = None if init_idx is None else np.ascontiguousarray(init_idx, dtype=np.int32)
     opts = dd_solve_opts(int(mode), int(certify), float(f_d0), float(f_d_final), int(ramp_iters), int(max_iter),
-                         float(cg_rtol), int(cg_max_iter), int(seed), _ptr(ii), int(stall_iters), int(cg_mode))
+                         float(cg_rtol), int(cg_max_iter), int(seed), _ptr(ii), int(stall_iters), int(cg_mode),
+                         int(f_s))
     return mesh, L, opts, ii
 
 
 def dd_solver_create(ds, ctx, n_el, load, mode: int = DD_SEARCH_EXACT_FP32, init_idx=None, max_iter: int = 100,
                      cg_rtol: float = 1e-12, cg_max_iter: int = 20000, certify: bool = True, f_d0: float = 0.0,
                      f_d_final: float = 0.0, ramp_iters: int = 20, seed: int = 0, stall_iters: int = 3,
-                     lengths=(1.0, 1.0, 1.0), cg_mode: int = 0):
+                     lengths=(1.0, 1.0, 1.0), cg_mode: int = 0, f_s: int = 0):
     mesh, L, opts, ii = _solve_args(n_el, load, mode, init_idx, max_iter, cg_rtol, cg_max_iter, certify, f_d0,
-                                    f_d_final, ramp_iters, seed, stall_iters, lengths, cg_mode)
+                                    f_d_final, ramp_iters, seed, stall_iters, lengths, cg_mode, f_s)
     sv = c_void_p()
     _check(ctx, lib().dd_solver_create(ds, ctypes.byref(mesh), ctypes.byref(L), ctypes.byref(opts),
                                        ctypes.byref(sv)))
@@ -359,6 +369,19 @@ def dd_dataset_ann_index(ds, ctx):
     return cl, cent, rad
 
 
+def dd_dataset_knn_k(ds) -> int:
+    return int(lib().dd_dataset_knn_k(ds))
+
+
+def dd_dataset_knn_graph(ds, ctx):
+    """Host copy of the k-nearest-neighbour graph: int32 [N, k] data indices,
+    nearest first, -1 where fewer than k neighbours were found."""
+    k = dd_dataset_knn_k(ds)
+    nbr = np.empty((dd_dataset_size(ds), k), np.int32)
+    _check(ctx, lib().dd_dataset_knn_graph(ds, _ptr(nbr)))
+    return nbr
+
+
 def dd_project_nearest_noalloc(ds, ctx, y_dev, idx_dev, d2_dev, stream=None) -> None:
     """Exact projection that allocates no device memory (device buffers only;
     asynchronous on `stream`).  For callers that cannot allocate during a
@@ -379,14 +402,14 @@ def dd_solvers_step(svs, ctx):
 def dd_solve_batch(ds, ctx, n_els, loads, mode: int = DD_SEARCH_EXACT_FP32, init_idx=None, max_iter: int = 100,
                    cg_rtol: float = 1e-12, cg_max_iter: int = 20000, certify: bool = True, f_d0: float = 0.0,
                    f_d_final: float = 0.0, ramp_iters: int = 20, seed: int = 0, stall_iters: int = 3,
-                   cg_mode: int = 0, allow_not_converged: bool = True):
+                   cg_mode: int = 0, allow_not_converged: bool = True, f_s: int = 0):
     """Solve several cube problems together; n_els[i] edge elements, loads[i]."""
     n = len(n_els)
     meshes = (dd_mesh * n)(*[dd_mesh(k, k, k, 1.0, 1.0, 1.0) for k in n_els])
     Ls = (dd_load * n)(*[_load(L)
                          for L in loads])
     _, _, opts, ii = _solve_args(n_els[0], loads[0], mode, init_idx, max_iter, cg_rtol, cg_max_iter, certify, f_d0,
-                                 f_d_final, ramp_iters, seed, stall_iters, (1.0, 1.0, 1.0), cg_mode)
+                                 f_d_final, ramp_iters, seed, stall_iters, (1.0, 1.0, 1.0), cg_mode, f_s)
     outs = (dd_result * n)()
     st = lib().dd_solve_batch(ds, n, meshes, Ls, ctypes.byref(opts), outs)
     try:
@@ -401,9 +424,9 @@ def dd_solve_batch(ds, ctx, n_els, loads, mode: int = DD_SEARCH_EXACT_FP32, init
 def dd_server_start(ds, ctx, mode: int = DD_SEARCH_EXACT_FP32, state_budget: int = 0, max_batch: int = 0,
                     max_iter: int = 100, cg_rtol: float = 1e-12, cg_max_iter: int = 20000, certify: bool = True,
                     f_d0: float = 0.0, f_d_final: float = 0.0, ramp_iters: int = 20, stall_iters: int = 3,
-                    cg_mode: int = 0):
+                    cg_mode: int = 0, f_s: int = 0):
     so = dd_solve_opts(int(mode), int(certify), float(f_d0), float(f_d_final), int(ramp_iters), int(max_iter),
-                       float(cg_rtol), int(cg_max_iter), 0, None, int(stall_iters), int(cg_mode))
+                       float(cg_rtol), int(cg_max_iter), 0, None, int(stall_iters), int(cg_mode), int(f_s))
     o = dd_server_opts(so, int(state_budget), int(max_batch))
     srv = c_void_p()
     _check(ctx, lib().dd_server_start(ds, ctypes.byref(o), ctypes.byref(srv)))

@@ -35,7 +35,7 @@
 
 namespace {
 
-constexpr int kCand = 8;          // candidate clusters per query
+constexpr int kCand = kAnnCand;   // candidate clusters per query
 constexpr int kTileC = 256;       // centroids per shared-memory tile in k_assign
 
 __device__ __forceinline__ float dist2_12(const float *a, const float (&q)[12]) {
@@ -1111,6 +1111,40 @@ static dd_status build_tree2(dd_dataset *ds, const dd_dataset_opts &o) {
     return DD_OK;
 }
 
+dd_status dd_ann_rank_cells(dd_dataset *ds, const QueryRec *rec, int64_t m, int32_t *cand_cl, float *cand_d,
+                            cudaStream_t s) {
+    dd_ctx *ctx = ds->ctx;
+    const AnnIndex &a = ds->ann;
+    const bool two = a.levels == 2;
+    const float *rank_cent = two ? a.cent1 : a.cent;
+    const float *rank_cn = two ? a.cn1 : a.cn;
+    const int Lr = two ? a.L1 : a.nlist;
+    if (Lr <= kRankMax) {
+        ctx->launches++;
+        k_rank_small<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(rec, m, rank_cent, rank_cn, Lr, cand_cl, cand_d);
+    } else {
+        int splits = 0, cap = 0;
+        CandHeader *hdr = nullptr;
+        float2 *cand = nullptr;
+        DD_TRY(dd_scan_fp32_raw(ctx, rank_cent, rank_cn, Lr, rec, m, true, WS_ANN_SCAN, &splits, &cap, &hdr, &cand,
+                                s));
+        ctx->launches += 2;
+        k_ann_cands<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(hdr, cand, splits, cap, rec, m, rank_cent, cand_cl,
+                                                                cand_d);
+    }
+    DD_TRY_CUDA(ctx, cudaGetLastError());
+    return DD_OK;
+}
+
+dd_status dd_ann_finish(dd_dataset *ds, const double *y_dev, int64_t m, const int32_t *idx, const float *d2f,
+                        double *d2, double *d2nd, cudaStream_t s) {
+    dd_ctx *ctx = ds->ctx;
+    ctx->launches++;
+    k_ann_finish<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(ds->raw, ds->M, y_dev, m, idx, d2f, d2, d2nd);
+    DD_TRY_CUDA(ctx, cudaGetLastError());
+    return DD_OK;
+}
+
 dd_status dd_search_ann(dd_dataset *ds, const double *y_dev, int64_t m, double f_d, const int32_t *prev_idx_dev,
                         SearchOut out, dd_search_stats *st, cudaStream_t s) {
     return dd_search_ann_motion(ds, y_dev, m, f_d, nullptr, prev_idx_dev, nullptr, out, st, s);
@@ -1141,24 +1175,9 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
     DD_TRY_CUDA(ctx, cudaMemsetAsync(touched, 0, b_bits, s));
 
     DD_TRY(dd_map_queries(ds, y_dev, m, nullptr, rec, s));
-    int splits = 0, cap = 0;
-    CandHeader *hdr = nullptr;
-    float2 *cand = nullptr;
     if (st) DD_TRY_CUDA(ctx, dd_event_record(ctx, ctx->ev_scan[0], s));
     const bool two = a.levels == 2;
-    const float *rank_cent = two ? a.cent1 : a.cent;
-    const int Lr = two ? a.L1 : a.nlist;
-    if (Lr <= kRankMax) {
-        ctx->launches += 2;
-        k_rank_small<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(rec, m, rank_cent, two ? a.cn1 : a.cn, Lr, cand_cl,
-                                                                 cand_d);
-    } else {
-        DD_TRY(dd_scan_fp32_raw(ctx, rank_cent, two ? a.cn1 : a.cn, Lr, rec, m, true, WS_ANN_SCAN, &splits, &cap,
-                                &hdr, &cand, s));
-        ctx->launches += 3;
-        k_ann_cands<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(hdr, cand, splits, cap, rec, m, rank_cent, cand_cl,
-                                                                cand_d);
-    }
+    DD_TRY(dd_ann_rank_cells(ds, rec, m, cand_cl, cand_d, s));
     ProbeArgs A;
     A.zs = a.zs;
     A.perm = a.perm;
@@ -1185,6 +1204,7 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
     A.fb_count = counters + 2;
     A.counters = counters;
     A.touched = touched;
+    ctx->launches++;
     if (two) {
         Probe2Args P2{A, a.cent, a.rad1, a.L1, a.L2, a.r1max};
         k_ann_probe2<<<(unsigned)((m * 32 + 255) / 256), 256, 0, s>>>(P2);
@@ -1193,9 +1213,7 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
     }
     DD_TRY_CUDA(ctx, cudaGetLastError());
     if (st) DD_TRY_CUDA(ctx, dd_event_record(ctx, ctx->ev_scan[1], s));
-    k_ann_finish<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(ds->raw, ds->M, y_dev, m, out.idx, d2f, out.d2,
-                                                             out.d2nd);
-    DD_TRY_CUDA(ctx, cudaGetLastError());
+    DD_TRY(dd_ann_finish(ds, y_dev, m, out.idx, d2f, out.d2, out.d2nd, s));
     // exact re-search where the candidate list may be incomplete (f_d = 1)
     unsigned long long n_fb = 0;
     // (a captured step never holds f_d = 1: its caller checks)
@@ -1212,7 +1230,7 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
         DD_TRY_CUDA(ctx, cudaGetLastError());
     }
     if (st && ctx->defer) {
-        DD_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->defer->ann, counters, 6 * sizeof(unsigned long long),
+        DD_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->defer->ann, counters, 8 * sizeof(unsigned long long),
                                          cudaMemcpyDeviceToDevice, s));
         st->distances += m * (int64_t)(two ? a.L1 : a.nlist);
     } else if (st) {

@@ -1162,15 +1162,18 @@ dd_status enqueue_step(dd_solver **svs, int n, const StepIO &io, const std::vect
 
     // ---- one search over the concatenated states ----
     const bool ann = o0.mode == DD_SEARCH_ANN;
+    const bool approx = ann || o0.mode == DD_SEARCH_KNNG;   // warm start and motion record
     int64_t off = 0;
     for (int i = 0; i < n; ++i) {
         dd_solver *sv = svs[i];
         const int64_t ng = sv->g.n_gp;
         DD_TRY_CUDA(ctx, cudaMemcpyAsync(io.y_cat + off * 12, sv->y, ng * 96, cudaMemcpyDeviceToDevice, s));
-        if (ann) {
+        if (approx) {
             DD_TRY_CUDA(ctx, cudaMemcpyAsync(io.prev_cat + off, sv->cur, ng * 4, cudaMemcpyDeviceToDevice, s));
             DD_TRY_CUDA(ctx, cudaMemcpyAsync(io.mot.q + off * 12, sv->mot.q, ng * 48, cudaMemcpyDeviceToDevice, s));
             DD_TRY_CUDA(ctx, cudaMemcpyAsync(io.mot.d + off * 2, sv->mot.d, ng * 8, cudaMemcpyDeviceToDevice, s));
+        }
+        if (ann) {
             ctx->launches++;
             if (io.fd_dev)
                 k_fill_fd<<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(io.fd_cat + off, ng, io.fd_dev + i);
@@ -1184,8 +1187,10 @@ dd_status enqueue_step(dd_solver **svs, int n, const StepIO &io, const std::vect
     if (ann) {
         if (!ds->ann.nlist) return dd_fail(ctx, DD_ERR_STATE, "ANN search needs the partition (ann_nlist)");
         DD_TRY(dd_search_ann_motion(ds, io.y_cat, M, fds[0], io.fd_cat, io.prev_cat, &mot, so, &sst, s));
+    } else if (o0.mode == DD_SEARCH_KNNG) {
+        DD_TRY(dd_search_knng(ds, io.y_cat, M, o0.f_s, io.prev_cat, &mot, so, &sst, s));
     } else {
-        DD_TRY(dd_run_search(ds, o0.mode, o0.certify, o0.f_d_final, nullptr, io.y_cat, M, so, &sst, s));
+        DD_TRY(dd_run_search(ds, o0.mode, o0.certify, o0.f_d_final, o0.f_s, nullptr, io.y_cat, M, so, &sst, s));
     }
     off = 0;
     for (int i = 0; i < n; ++i) {
@@ -1194,7 +1199,7 @@ dd_status enqueue_step(dd_solver **svs, int n, const StepIO &io, const std::vect
         DD_TRY_CUDA(ctx, cudaMemcpyAsync(sv->nxt, io.idx_cat + off, ng * 4, cudaMemcpyDeviceToDevice, s));
         DD_TRY_CUDA(ctx, cudaMemcpyAsync(sv->d2, io.d2_cat + off, ng * 8, cudaMemcpyDeviceToDevice, s));
         DD_TRY_CUDA(ctx, cudaMemcpyAsync(sv->d2nd, io.d2nd_cat + off, ng * 8, cudaMemcpyDeviceToDevice, s));
-        if (ann) {
+        if (approx) {
             DD_TRY_CUDA(ctx, cudaMemcpyAsync(sv->mot.q, io.mot.q + off * 12, ng * 48, cudaMemcpyDeviceToDevice, s));
             DD_TRY_CUDA(ctx, cudaMemcpyAsync(sv->mot.d, io.mot.d + off * 2, ng * 8, cudaMemcpyDeviceToDevice, s));
         }
@@ -1242,6 +1247,7 @@ void finish_step(dd_solver **svs, int n, const double *hs, const int *its, dd_se
         sst.points += (int64_t)dfr->ann[5] + (int64_t)dfr->ann[2] * N;
         sst.unique_points += dfr->ann[2] ? N : (int64_t)dfr->ann[4];
         sst.skipped += (int64_t)dfr->ann[1];
+        sst.moves += (int64_t)dfr->ann[6];
     }
     for (int i = 0; i < n; ++i) {
         dd_search_stats si = sst;   // the shared search is reported to every solve
@@ -1410,8 +1416,9 @@ extern "C" dd_status dd_solvers_step(dd_solver **svs, int n, dd_iter_info *infos
         dd_solver *sv = svs[i];
         if (!sv || sv->ds != ds) return dd_fail(ctx, DD_ERR_ARG, "dd_solvers_step: solvers must share one data set");
         if (sv->done) return dd_fail(ctx, DD_ERR_STATE, "dd_solvers_step: a solve has already finished");
-        if (sv->o.mode != o0.mode || sv->o.certify != o0.certify || sv->o.cg_mode != o0.cg_mode)
-            return dd_fail(ctx, DD_ERR_ARG, "dd_solvers_step: solvers must share search mode, certify and cg_mode");
+        if (sv->o.mode != o0.mode || sv->o.certify != o0.certify || sv->o.cg_mode != o0.cg_mode ||
+            sv->o.f_s != o0.f_s)
+            return dd_fail(ctx, DD_ERR_ARG, "dd_solvers_step: solvers must share search mode, certify, cg_mode and f_s");
         for (int j = 0; j < i; ++j)
             if (svs[j] == sv) return dd_fail(ctx, DD_ERR_ARG, "dd_solvers_step: a solver appears twice");
         M += sv->g.n_gp;

@@ -198,6 +198,7 @@ extern "C" dd_status dd_load_dataset(dd_ctx *ctx, const float *eps_sig, int64_t 
     if ((st = dd_transform_dataset(ds)) != DD_OK) return fail(st);
     if (o.build_fp16 && (st = dd_build_fp16(ds)) != DD_OK) return fail(st);
     if (o.ann_nlist > 0 && (st = dd_build_ann(ds, o)) != DD_OK) return fail(st);
+    if (o.knn_k != 0 && (st = dd_build_knng(ds, o)) != DD_OK) return fail(st);
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return fail(dd_fail(ctx, DD_ERR_CUDA, cudaGetErrorString(e)));
     *out = ds;
@@ -215,6 +216,7 @@ extern "C" void dd_free_dataset(dd_dataset *ds) {
     dd_free(ctx, ds->zn, (size_t)ds->N_pad * 4);
     if (ds->z16hi) dd_free(ctx, ds->z16hi, (size_t)ds->N_pad * 32);
     if (ds->z16lo) dd_free(ctx, ds->z16lo, (size_t)ds->N_pad * 32);
+    dd_free_knng(ds);
     dd_free_ann(ds);
     delete ds;
 }
@@ -226,7 +228,7 @@ extern "C" size_t dd_dataset_bytes(const dd_dataset *ds) { return ds ? ds->bytes
 // ---------------------------------------------------------------------------
 // P_D
 // ---------------------------------------------------------------------------
-dd_status dd_run_search(dd_dataset *ds, int mode, int certify, double f_d, const int32_t *prev_dev,
+dd_status dd_run_search(dd_dataset *ds, int mode, int certify, double f_d, int f_s, const int32_t *prev_dev,
                             const double *y_dev, int64_t m, SearchOut out, dd_search_stats *st, cudaStream_t s) {
     switch (mode) {
     case DD_SEARCH_EXACT_FP32:
@@ -237,6 +239,8 @@ dd_status dd_run_search(dd_dataset *ds, int mode, int certify, double f_d, const
     case DD_SEARCH_ANN:
         if (!ds->ann.nlist) return dd_fail(ds->ctx, DD_ERR_STATE, "ANN search needs the partition (ann_nlist)");
         return dd_search_ann(ds, y_dev, m, f_d, prev_dev, out, st, s);
+    case DD_SEARCH_KNNG:
+        return dd_search_knng(ds, y_dev, m, f_s, prev_dev, nullptr, out, st, s);
     default:
         return dd_fail(ds->ctx, DD_ERR_ARG, "unknown search mode");
     }
@@ -255,6 +259,7 @@ extern "C" dd_status dd_project_nearest(dd_dataset *ds, const double *y, int64_t
     if (opts) o = *opts;
     if (o.mode == DD_SEARCH_ANN && !(o.f_d >= 0.0 && o.f_d <= 1.0))
         return dd_fail(ctx, DD_ERR_ARG, "dd_project_nearest: f_d outside [0, 1]");
+    if (o.mode == DD_SEARCH_KNNG && o.f_s < 0) return dd_fail(ctx, DD_ERR_ARG, "dd_project_nearest: f_s < 0");
     DD_TRY_CUDA(ctx, cudaSetDevice(ctx->device));
     const bool dev = dd_is_device_ptr(y);
     if (dd_is_device_ptr(idx) != dev || (d2 && dd_is_device_ptr(d2) != dev))
@@ -290,7 +295,7 @@ extern "C" dd_status dd_project_nearest(dd_dataset *ds, const double *y, int64_t
         DD_TRY_CUDA(ctx, cudaEventRecord(e0, s));
     }
     SearchOut out{idx_dev, d2_dev, nullptr};
-    dd_status st = dd_run_search(ds, o.mode, o.certify, o.f_d, prev_dev, y_dev, m, out, stats ? &local : nullptr, s);
+    dd_status st = dd_run_search(ds, o.mode, o.certify, o.f_d, o.f_s, prev_dev, y_dev, m, out, stats ? &local : nullptr, s);
     if (st != DD_OK) return st;
     if (stats) {
         DD_TRY_CUDA(ctx, cudaEventRecord(e1, s));

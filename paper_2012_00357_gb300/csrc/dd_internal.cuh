@@ -74,8 +74,9 @@ struct Workspace {
 // reads them after the step.
 struct DeferredStats {
     unsigned long long fb;       // exact search: queries re-searched in FP64
-    unsigned long long ann[6];   // approximate search: point distances, skipped, exact re-search, fine
-                                 // centroids, distinct points, points read
+    unsigned long long ann[8];   // approximate search: point distances, skipped, exact re-search, fine
+                                 // centroids, distinct points, points read, graph node changes,
+                                 // walks stopped by f_s
 };
 
 struct StepPlan;
@@ -113,6 +114,18 @@ void dd_plans_drop(dd_ctx *ctx, uint64_t id);
 enum WsSlot {
     WS_SEARCH = 0, WS_QUERY = 1, WS_MISC = 2, WS_SOLVE = 3, WS_TC = 4, WS_ANN = 5, WS_ANN_SCAN = 6, WS_ANN_BUILD = 7,
     WS_BATCH = 8, WS_BATCH_CG = 9
+};
+
+// Coarse cells a tree search ranks per query (ann.cu).
+constexpr int kAnnCand = 8;
+
+// k-nearest-neighbour graph of DD_SEARCH_KNNG (knng.cu).  Nodes are positions
+// of the cluster-sorted copy AnnIndex::zs.
+struct KnnGraph {
+    int k = 0;
+    float fd = 0.f;
+    int32_t *nbr = nullptr;     // [N x k] neighbour positions, nearest first (-1: none)
+    int32_t *pos_of = nullptr;  // [N] sorted position of every original point
 };
 
 struct AnnIndex {
@@ -160,6 +173,7 @@ struct dd_dataset {
     __half *z16lo = nullptr;     // [N_pad x 16]
     double scale16 = 0.0;        // power-of-two scale s
     AnnIndex ann;
+    KnnGraph knn;
     size_t bytes = 0;
 };
 
@@ -213,9 +227,23 @@ dd_status dd_fallback_exact(dd_dataset *ds, const double *y_dev, const int64_t *
 // Record (q, d1, d2) of the last search for the moving-query test.
 dd_status dd_ann_motion_update(dd_ctx *ctx, const QueryRec *rec, int64_t m, const double *d2, const double *d2nd,
                                AnnMotion *mot, cudaStream_t s);
-dd_status dd_run_search(dd_dataset *ds, int mode, int certify, double f_d, const int32_t *prev_dev,
+dd_status dd_run_search(dd_dataset *ds, int mode, int certify, double f_d, int f_s, const int32_t *prev_dev,
                         const double *y_dev, int64_t m, SearchOut out, dd_search_stats *st, cudaStream_t s);
 void dd_free_ann(dd_dataset *ds);
+// The kAnnCand nearest coarse cells of every query (two-level tree), sorted by
+// FP32 distance (plain, not squared); -1 pads.
+dd_status dd_ann_rank_cells(dd_dataset *ds, const QueryRec *rec, int64_t m, int32_t *cand_cl, float *cand_d,
+                            cudaStream_t s);
+// FP64 Eq. (3) distance of every answer, and the second distance (FP32 plain
+// squared, mapped coordinates) in Eq. (3) units.
+dd_status dd_ann_finish(dd_dataset *ds, const double *y_dev, int64_t m, const int32_t *idx, const float *d2f,
+                        double *d2, double *d2nd, cudaStream_t s);
+
+// k-nearest-neighbour graph (knng.cu)
+dd_status dd_build_knng(dd_dataset *ds, const dd_dataset_opts &o);
+dd_status dd_search_knng(dd_dataset *ds, const double *y_dev, int64_t m, int f_s, const int32_t *prev_idx_dev,
+                         AnnMotion *mot, SearchOut out, dd_search_stats *st, cudaStream_t s);
+void dd_free_knng(dd_dataset *ds);
 
 // FP32 scan of mapped queries against any point set (z32 [N_pad x 12], zn
 // [N_pad], rows padded to 128): per (query, split) candidate windows, or the

@@ -171,7 +171,7 @@ extern "C" dd_status dd_server_start(dd_dataset *ds, const dd_server_opts *opts,
     S->ctx = ctx;
     std::memset(&S->o, 0, sizeof(S->o));
     if (opts) S->o = *opts;
-    if (S->o.solve.mode < 0 || S->o.solve.mode > 2) {
+    if (S->o.solve.mode < 0 || S->o.solve.mode > 3) {
         delete S;
         return dd_fail(ctx, DD_ERR_ARG, "dd_server_start: unknown search mode");
     }

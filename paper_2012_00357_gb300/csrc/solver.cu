@@ -130,7 +130,7 @@ bool dd_solver_account(dd_solver *sv, const double hs[3], int cg_it, float cg_ms
     if (hs[0] == 0.0 && settled) {
         sv->converged = true;
         stop = true;   // nxt == cur: the state was computed from the final association
-    } else if (o.mode == DD_SEARCH_ANN) {
+    } else if (o.mode == DD_SEARCH_ANN || o.mode == DD_SEARCH_KNNG) {
         if (hs[1] < sv->best_pd * (1.0 - 1e-12)) {
             sv->best_pd = hs[1];
             sv->stall = 0;
@@ -159,6 +159,7 @@ bool dd_solver_account(dd_solver *sv, const double hs[3], int cg_it, float cg_ms
         info->points = sst.points;
         info->unique_points = sst.unique_points;
         info->graph = 0;
+        info->moves = sst.moves;
     }
     return sv->done;
 }
@@ -191,7 +192,10 @@ extern "C" dd_status dd_solver_create(dd_dataset *ds, const dd_mesh *mesh, const
         if (o.ramp_iters < 0) o.ramp_iters = 0;
         if (o.stall_iters <= 0) o.stall_iters = 3;
     }
-    if (o.mode < 0 || o.mode > 2) return dd_fail(ctx, DD_ERR_ARG, "dd_solver_create: unknown mode");
+    if (o.mode < 0 || o.mode > 3) return dd_fail(ctx, DD_ERR_ARG, "dd_solver_create: unknown mode");
+    if (o.mode == DD_SEARCH_KNNG && o.f_s < 0) return dd_fail(ctx, DD_ERR_ARG, "dd_solver_create: f_s < 0");
+    if (o.mode == DD_SEARCH_KNNG && !ds->knn.k)
+        return dd_fail(ctx, DD_ERR_STATE, "dd_solver_create: graph search needs the k-NN graph (knn_k)");
     if (o.cg_mode < 0 || o.cg_mode > 1) return dd_fail(ctx, DD_ERR_ARG, "dd_solver_create: unknown cg_mode");
     if (o.mode == DD_SEARCH_ANN && !(o.f_d0 >= 0 && o.f_d0 <= 1 && o.f_d_final >= 0 && o.f_d_final <= 1))
         return dd_fail(ctx, DD_ERR_ARG, "dd_solver_create: f_d outside [0, 1]");
@@ -308,8 +312,10 @@ extern "C" dd_status dd_solver_step(dd_solver *sv, dd_iter_info *info) {
     if (o.mode == DD_SEARCH_ANN) {
         if (!ds->ann.nlist) return dd_fail(ctx, DD_ERR_STATE, "ANN search needs the partition (ann_nlist)");
         DD_TRY(dd_search_ann_motion(ds, sv->y, ng, f_d, nullptr, sv->cur, &sv->mot, so, &sst, s));
+    } else if (o.mode == DD_SEARCH_KNNG) {
+        DD_TRY(dd_search_knng(ds, sv->y, ng, o.f_s, sv->cur, &sv->mot, so, &sst, s));
     } else {
-        DD_TRY(dd_run_search(ds, o.mode, o.certify, f_d, sv->cur, sv->y, ng, so, &sst, s));
+        DD_TRY(dd_run_search(ds, o.mode, o.certify, f_d, o.f_s, sv->cur, sv->y, ng, so, &sst, s));
     }
     DD_TRY_CUDA(ctx, cudaEventRecord(sv->ev[3], s));
     DD_TRY(fem_iter_stats(ctx, sv->nxt, sv->cur, sv->d2, sv->dpc, ng, g.w, sv->stats, s));
