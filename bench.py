@@ -531,9 +531,10 @@ def main():
     ap.add_argument("--nlist", type=int, default=0)
     ap.add_argument("--ann-levels", type=int, default=0)
     ap.add_argument("--ann-check", type=int, default=2048)
-    ap.add_argument("--knn-k", type=int, default=32, help="k of the k-NN graph (graph search)")
-    ap.add_argument("--knn-fd", type=float, default=0.6, help="f_d of the graph build")
-    ap.add_argument("--f-s", type=int, default=0, help="node-change bound of the graph walk (0: none)")
+    ap.add_argument("--knn-k", type=int, default=None, help="k of the k-NN graph (default: the workload's, else 128)")
+    ap.add_argument("--knn-fd", type=float, default=None, help="f_d of the graph build (default: workload's, else 0.8)")
+    ap.add_argument("--f-s", type=int, default=None, help="node-change bound of the graph walk (0: none; default: "
+                    "the workload's, else 2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()
@@ -545,6 +546,10 @@ def main():
     args.fd0 = sched[0] if args.fd0 is None else args.fd0
     args.fd_final = sched[1] if args.fd_final is None else args.fd_final
     args.ramp_iters = sched[2] if args.ramp_iters is None else args.ramp_iters
+    ex = I.WORKLOADS[args.workload].extra
+    args.knn_k = ex.get("knn_k", 128) if args.knn_k is None else args.knn_k
+    args.knn_fd = ex.get("knn_fd", 0.8) if args.knn_fd is None else args.knn_fd
+    args.f_s = ex.get("f_s", 2) if args.f_s is None else args.f_s
     world, rank, local = dist_setup()
     if args.impl == "reference":
         line = run_reference(args, world, rank)

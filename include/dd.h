@@ -110,12 +110,12 @@ typedef struct dd_dataset_opts {
                            2: a two-level k-means tree, about sqrt(ann_nlist)
                            coarse cells each split into leaves, ann_nlist
                            leaves in total (for 10^8 - 10^9 points) */
-    int knn_k;          /* 1..32: also build the k-nearest-neighbour graph of
-                           DD_SEARCH_KNNG (Sec. 4.4): every point linked to the
-                           knn_k nearest other points that a search of the
-                           two-level tree (ann_levels = 2, required) finds
-                           for it at accuracy knn_fd (Eq. 13); 4 * knn_k + 4
-                           bytes per point.  0: no graph */
+    int knn_k;          /* 1..128: also build the k-nearest-neighbour graph
+                           of DD_SEARCH_KNNG (Sec. 4.4): every point linked to
+                           the knn_k nearest other points that a search of
+                           the two-level tree (ann_levels = 2, required)
+                           finds for it at accuracy knn_fd (Eq. 13);
+                           4 * knn_k + 4 bytes per point.  0: no graph */
     double knn_fd;      /* f_d of the graph build (0 .. 1; 1 with at most 8
                            coarse cells of at most 8 leaves gives the exact
                            graph) */

@@ -54,18 +54,49 @@ __device__ __forceinline__ float dist2_12(const float *a, const float (&q)[12]) 
 
 __device__ __forceinline__ bool pair_less(float a, int pa, float b, int pb) { return a < b || (a == b && pa < pb); }
 
-// Lane-distributed list of (squared distance, position), ascending over the
-// lanes; entries with d = +inf are empty.
+// Lane-distributed list of R x 32 (squared distance, position) entries in
+// ascending order: entry 32 r + lane is (d[r], p[r]) of that lane; entries
+// with d = +inf are empty.
+template <int R>
 struct TopK {
-    float d;
-    int p;
+    float d[R];
+    int p[R];
 };
 
-// Offer one candidate per lane (d = +inf: none).  Keeps the 32 smallest of
-// list and candidates in order; candidates not below entry k-1 are dropped.
-__device__ __forceinline__ void topk_offer(TopK &L, float d, int p, int k, int lane) {
-    const float td = __shfl_sync(kFull, L.d, k - 1);
-    const int tp = __shfl_sync(kFull, L.p, k - 1);
+__device__ __forceinline__ void cas(float &d, int &p, int st, bool keep_min, int lane) {
+    const float od = __shfl_xor_sync(kFull, d, st);
+    const int op = __shfl_xor_sync(kFull, p, st);
+    const bool olt = pair_less(od, op, d, p);
+    if (keep_min == ((lane & st) == 0) ? olt : !olt) {
+        d = od;
+        p = op;
+    }
+}
+
+// ascending sort of a bitonic sequence held one entry per lane
+__device__ __forceinline__ void bitonic_clean(float &d, int &p, int lane) {
+#pragma unroll
+    for (int st = 16; st > 0; st >>= 1) cas(d, p, st, true, lane);
+}
+
+// Offer one candidate per lane (d = +inf: none).  Keeps the R x 32 smallest
+// of list and candidates in order; candidates not below entry k-1 are
+// dropped.  The sorted candidates cascade through the list: at level r the
+// 32 smallest of (level r, carry) stay and the 32 largest are carried on,
+// so every level stays sorted and not below the one before it.
+template <int R>
+__device__ __forceinline__ void topk_offer(TopK<R> &L, float d, int p, int k, int lane) {
+    const int rk = (k - 1) >> 5, lk = (k - 1) & 31;
+    float td = L.d[0];
+    int tp = L.p[0];
+#pragma unroll
+    for (int r = 1; r < R; ++r)
+        if (r == rk) {
+            td = L.d[r];
+            tp = L.p[r];
+        }
+    td = __shfl_sync(kFull, td, lk);
+    tp = __shfl_sync(kFull, tp, lk);
     const bool pass = pair_less(d, p, td, tp);
     if (!__any_sync(kFull, pass)) return;
     if (!pass) {
@@ -76,36 +107,26 @@ __device__ __forceinline__ void topk_offer(TopK &L, float d, int p, int k, int l
 #pragma unroll
     for (int size = 2; size <= 32; size <<= 1) {
 #pragma unroll
-        for (int st = size >> 1; st > 0; st >>= 1) {
-            const float od = __shfl_xor_sync(kFull, d, st);
-            const int op = __shfl_xor_sync(kFull, p, st);
-            const bool up = (lane & size) == 0;
-            const bool lo = (lane & st) == 0;
-            const bool olt = pair_less(od, op, d, p);
-            if (lo == up ? olt : !olt) {
-                d = od;
-                p = op;
-            }
-        }
-    }
-    // the i-th smallest of the list against the (31-i)-th candidate: the
-    // elementwise minimum is a bitonic sequence of the 32 smallest of both
-    const float rd = __shfl_sync(kFull, d, 31 - lane);
-    const int rp = __shfl_sync(kFull, p, 31 - lane);
-    if (pair_less(rd, rp, L.d, L.p)) {
-        L.d = rd;
-        L.p = rp;
+        for (int st = size >> 1; st > 0; st >>= 1) cas(d, p, st, (lane & size) == 0, lane);
     }
 #pragma unroll
-    for (int st = 16; st > 0; st >>= 1) {
-        const float od = __shfl_xor_sync(kFull, L.d, st);
-        const int op = __shfl_xor_sync(kFull, L.p, st);
-        const bool lo = (lane & st) == 0;
-        const bool olt = pair_less(od, op, L.d, L.p);
-        if (lo ? olt : !olt) {
-            L.d = od;
-            L.p = op;
+    for (int r = 0; r < R; ++r) {
+        // the i-th entry of the level against the (31-i)-th carried one:
+        // elementwise min and max are bitonic halves of the 64
+        const float rd = __shfl_sync(kFull, d, 31 - lane);
+        const int rp = __shfl_sync(kFull, p, 31 - lane);
+        const bool rl = pair_less(rd, rp, L.d[r], L.p[r]);
+        const float hd = rl ? L.d[r] : rd;
+        const int hp = rl ? L.p[r] : rp;
+        if (rl) {
+            L.d[r] = rd;
+            L.p[r] = rp;
         }
+        bitonic_clean(L.d[r], L.p[r], lane);
+        if (r + 1 == R || !__any_sync(kFull, hd < INFINITY)) break;
+        d = hd;
+        p = hp;
+        bitonic_clean(d, p, lane);
     }
 }
 
@@ -147,6 +168,7 @@ struct BuildArgs {
 // the current k-th distance: the nearest cell and its nearest leaf always, a
 // further cell or leaf (in order of centroid distance, at most kFineB leaves
 // per cell) when d(x, c) - f_d r < d_c.
+template <int R>
 __global__ void __launch_bounds__(256) k_knn_build(BuildArgs A) {
     const int lane = threadIdx.x & 31;
     const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -155,9 +177,21 @@ __global__ void __launch_bounds__(256) k_knn_build(BuildArgs A) {
     float q[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) q[k] = A.rec[t].q[k];
-    TopK L{INFINITY, INT_MAX};
+    TopK<R> L;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        L.d[r] = INFINITY;
+        L.p[r] = INT_MAX;
+    }
     unsigned long long ev = 0;
-    auto dc = [&]() { return sqrtf(__shfl_sync(kFull, L.d, A.k - 1)); };
+    const int rk = (A.k - 1) >> 5, lk = (A.k - 1) & 31;
+    auto dc = [&]() {
+        float v = L.d[0];
+#pragma unroll
+        for (int r = 1; r < R; ++r)
+            if (r == rk) v = L.d[r];
+        return sqrtf(__shfl_sync(kFull, v, lk));
+    };
     auto scan = [&](int l) {
         const int64_t a = A.offs[l], b = A.offs[l + 1];
         for (int64_t base = a; base < b; base += 32) {
@@ -168,7 +202,7 @@ __global__ void __launch_bounds__(256) k_knn_build(BuildArgs A) {
                 d = dist2_12(A.zs + p * 12, q);
                 pp = (int)p;
             }
-            topk_offer(L, d, pp, A.k, lane);
+            topk_offer<R>(L, d, pp, A.k, lane);
         }
         ev += (unsigned long long)(b - a);
     };
@@ -208,7 +242,9 @@ __global__ void __launch_bounds__(256) k_knn_build(BuildArgs A) {
             if ((k1 == 0 && k2 == 0) || md - A.f_d * A.radius[l] < dc()) scan(l);
         }
     }
-    if (lane < A.k) A.nbr[self * A.k + lane] = L.d < INFINITY ? L.p : -1;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        if (32 * r + lane < A.k) A.nbr[self * A.k + 32 * r + lane] = L.d[r] < INFINITY ? L.p[r] : -1;
     if (lane == 0) atomicAdd(A.evals, ev);
 }
 
@@ -297,27 +333,41 @@ __device__ __forceinline__ void walk_one(const WalkArgs &A, int64_t i, int lane,
             bounded = true;
             break;
         }
-        const int t = lane < A.k ? A.nbr[(size_t)p * A.k + lane] : -1;
-        const float d = t >= 0 ? dist2_12(A.zs + (size_t)t * 12, q) : INFINITY;
-        ev += (unsigned long long)__popc(__ballot_sync(kFull, t >= 0));
-        float bd = d;
-        for (int o = 16; o > 0; o >>= 1) bd = fminf(bd, __shfl_xor_sync(kFull, bd, o));
-        const bool at_min = t >= 0 && d == bd;
-        const unsigned tie = __ballot_sync(kFull, at_min);
+        // nearest neighbour over chunks of 32 (ties to the lower data index),
+        // and the smallest distance among the others
+        float bd = INFINITY, od = INFINITY;
         int bt = -1;
-        if (__popc(tie) == 1) {
-            bt = __shfl_sync(kFull, t, __ffs(tie) - 1);
-        } else if (tie) {
-            // equal distances: the lower data index
-            const int j = at_min ? A.perm[t] : INT_MAX;
-            int jb = j;
-            for (int o = 16; o > 0; o >>= 1) jb = min(jb, __shfl_xor_sync(kFull, jb, o));
-            const unsigned w = __ballot_sync(kFull, at_min && j == jb);
-            bt = __shfl_sync(kFull, t, __ffs(w) - 1);
+        for (int c0 = 0; c0 < A.k; c0 += 32) {
+            const int t = c0 + lane < A.k ? A.nbr[(size_t)p * A.k + c0 + lane] : -1;
+            const float d = t >= 0 ? dist2_12(A.zs + (size_t)t * 12, q) : INFINITY;
+            ev += (unsigned long long)__popc(__ballot_sync(kFull, t >= 0));
+            float cd = d;
+            for (int o = 16; o > 0; o >>= 1) cd = fminf(cd, __shfl_xor_sync(kFull, cd, o));
+            const bool at_min = t >= 0 && d == cd;
+            const unsigned tie = __ballot_sync(kFull, at_min);
+            int ct = -1;
+            if (__popc(tie) == 1) {
+                ct = __shfl_sync(kFull, t, __ffs(tie) - 1);
+            } else if (tie) {
+                const int j = at_min ? A.perm[t] : INT_MAX;
+                int jb = j;
+                for (int o = 16; o > 0; o >>= 1) jb = min(jb, __shfl_xor_sync(kFull, jb, o));
+                const unsigned w = __ballot_sync(kFull, at_min && j == jb);
+                ct = __shfl_sync(kFull, t, __ffs(w) - 1);
+            }
+            float co = (t == ct) ? INFINITY : d;
+            for (int o = 16; o > 0; o >>= 1) co = fminf(co, __shfl_xor_sync(kFull, co, o));
+            if (ct < 0) continue;
+            bool better = cd < bd;
+            if (cd == bd && bt >= 0) better = A.perm[ct] < A.perm[bt];
+            if (better) {
+                od = fminf(od, fminf(bd, co));
+                bd = cd;
+                bt = ct;
+            } else {
+                od = fminf(od, fminf(cd, co));
+            }
         }
-        // smallest distance among the other neighbours
-        float od = (t == bt) ? INFINITY : d;
-        for (int o = 16; o > 0; o >>= 1) od = fminf(od, __shfl_xor_sync(kFull, od, o));
         if (bt >= 0 && bd < dcur) {
             second = fminf(second, fminf(dcur, od));
             dcur = bd;
@@ -364,7 +414,7 @@ dd_status dd_build_knng(dd_dataset *ds, const dd_dataset_opts &o) {
     dd_ctx *ctx = ds->ctx;
     const AnnIndex &a = ds->ann;
     KnnGraph &g = ds->knn;
-    if (o.knn_k < 1 || o.knn_k > 32) return dd_fail(ctx, DD_ERR_ARG, "knn_k must be 1 .. 32");
+    if (o.knn_k < 1 || o.knn_k > 128) return dd_fail(ctx, DD_ERR_ARG, "knn_k must be 1 .. 128");
     if (!(o.knn_fd >= 0.0 && o.knn_fd <= 1.0)) return dd_fail(ctx, DD_ERR_ARG, "knn_fd outside [0, 1]");
     if (a.levels != 2 || !a.nlist)
         return dd_fail(ctx, DD_ERR_ARG, "the k-NN graph is built with the two-level tree (ann_levels = 2)");
@@ -403,7 +453,11 @@ dd_status dd_build_knng(dd_dataset *ds, const dd_dataset_opts &o) {
         DD_TRY(dd_ann_rank_cells(ds, rec, n, cand_cl, cand_d, s));
         BuildArgs A{a.zs, a.offs, a.radius, a.cent, a.rad1, a.L2, rec, cand_cl, cand_d, p0, n, g.k, g.fd, g.nbr,
                     evals};
-        k_knn_build<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(A);
+        const unsigned grid = (unsigned)((n * 32 + 255) / 256);
+        if (g.k <= 32) k_knn_build<1><<<grid, 256, 0, s>>>(A);
+        else if (g.k <= 64) k_knn_build<2><<<grid, 256, 0, s>>>(A);
+        else if (g.k <= 96) k_knn_build<3><<<grid, 256, 0, s>>>(A);
+        else k_knn_build<4><<<grid, 256, 0, s>>>(A);
         DD_TRY_CUDA(ctx, cudaGetLastError());
     }
     ds->bytes += (size_t)N * (g.k + 1) * 4;

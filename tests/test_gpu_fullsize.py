@@ -62,7 +62,14 @@ def test_ann_tree_fd_one_full_size(big):
     assert np.allclose(d2, 2 * od, rtol=1e-9)
 
 
-def test_ann_solve_within_1e3_of_exact_full_size(big):
+@pytest.fixture(scope="module")
+def exact_solve(big):
+    ctx, ds, y, sample, oi, od = big
+    return P.dd_solve(ds, ctx, W.n_el, I.load_case("tension", 1e-3), mode=P.DD_SEARCH_EXACT_TC, seed=W.seed,
+                      max_iter=60)
+
+
+def test_ann_solve_within_1e3_of_exact_full_size(big, exact_solve):
     """The DD solution driven by the approximate search (tree, f_d from 0.3
     to 0.6 over 5 iterations, the benchmark schedule) stays within 1e-3 relative in global
     distance (Eq. 2) of the solution driven by the certified exact search, on
@@ -70,7 +77,7 @@ def test_ann_solve_within_1e3_of_exact_full_size(big):
     association."""
     ctx, ds, y, sample, oi, od = big
     L = I.load_case("tension", 1e-3)
-    exact = P.dd_solve(ds, ctx, W.n_el, L, mode=P.DD_SEARCH_EXACT_TC, seed=W.seed, max_iter=60)
+    exact = exact_solve
     ann = P.dd_solve(ds, ctx, W.n_el, L, mode=P.DD_SEARCH_ANN, f_d0=0.3, f_d_final=0.6, ramp_iters=5,
                      seed=W.seed, max_iter=60)
     de, da = float(exact.d2_pd[-1]), float(ann.d2_pd[-1])
@@ -78,6 +85,32 @@ def test_ann_solve_within_1e3_of_exact_full_size(big):
           f"relative difference {abs(da - de) / de:.2e}")
     assert exact.converged and ann.converged
     assert abs(da - de) <= 1e-3 * de
+
+
+def test_graph_solve_full_size(big, exact_solve):
+    """The DD solve driven by the greedy walk in the k-NN graph (Sec. 4.4;
+    k = 128 built at f_d = 0.8, at most 2 node changes per walk) on the 32^3
+    cube with 10^8 points ends within 1 % above the certified exact-search
+    solution, from the same initial association (bounded walks may end at a
+    better fixed point), and the walk evaluates a few hundred neighbours per
+    query, not the millions of points of a scan."""
+    ctx, ds, y, sample, oi, od = big
+    Wg = I.WORKLOADS["cube32_N1e8_knng"]
+    raw = torch.empty((W.N, 12), dtype=torch.float32, device="cuda")
+    P.dd_synth_dataset(ctx, raw, W.law, C, seed=W.seed)
+    dg = P.dd_load_dataset(ctx, raw, C, borrow=True, ann_nlist=1 << 17, ann_levels=2, seed=1,
+                           knn_k=Wg.extra["knn_k"], knn_fd=Wg.extra["knn_fd"])
+    try:
+        g = P.dd_solve(dg, ctx, W.n_el, I.load_case("tension", 1e-3), mode=P.DD_SEARCH_KNNG, f_s=Wg.extra["f_s"],
+                       seed=W.seed, max_iter=200)
+    finally:
+        P.dd_free_dataset(dg)
+        del raw
+    de, dgr = float(exact_solve.d2_pd[-1]), float(g.d2_pd[-1])
+    print(f"exact d2 {de:.6e}; graph walk: {g.iters} iterations, d2 {dgr:.6e}, relative {(dgr - de) / de:+.2e}, "
+          f"{g.distances / W.m / g.iters:.0f} distances per query and iteration")
+    assert g.converged and dgr <= 1.01 * de
+    assert g.distances / W.m / g.iters < 1000
 
 
 def test_paper_problem_ann_within_1e3_of_exact():

@@ -52,6 +52,31 @@ def test_graph_at_fd_one_is_exact(ctx):
     print(f"rows equal: {same.mean():.4f}")
 
 
+@pytest.mark.parametrize("k", [40, 75, 128])
+def test_wide_graph_at_fd_one_is_exact(ctx, k):
+    """k above 32: the list spans several registers per lane; the build at
+    f_d = 1 still gives the exact k-NN graph, and a walk over k neighbours
+    matches the oracle's."""
+    data = I.make_dataset(2500, I.NONLINEAR, seed=49)
+    ds = P.dd_load_dataset(ctx, data, C, ann_nlist=64, ann_levels=2, seed=3, knn_k=k, knn_fd=1.0)
+    try:
+        g = P.dd_dataset_knn_graph(ds, ctx)
+        y = I.make_states(400, I.NONLINEAR, seed=50, spread=0.1)
+        prev = np.random.default_rng(7).integers(0, len(data), len(y)).astype(np.int32)
+        idx, d2, st = walk(ctx, ds, y, prev)
+    finally:
+        P.dd_free_dataset(ds)
+    Z = metric.to_z(data.astype(np.float64), C)
+    go = knng.knn_graph(Z, k)
+    dg = np.array([((Z[g[i]] - Z[i]) ** 2).sum(1) for i in range(len(Z))])
+    do = np.array([((Z[go[i]] - Z[i]) ** 2).sum(1) for i in range(len(Z))])
+    assert np.allclose(dg, do, rtol=1e-5, atol=0)
+    same = np.mean([set(g[i]) == set(go[i]) for i in range(len(Z))])
+    assert same >= 0.99
+    oi, od, osec, omv, oev = knng.walk_all(Z, g, metric.to_z(y, C), prev)
+    assert np.mean(idx == oi) >= 0.98 and abs(st.moves - omv.sum()) <= 0.02 * omv.sum() + 5
+
+
 def test_small_data_set_pads_rows(ctx):
     """N - 1 < k: every other point is a neighbour, the rest of a row is -1."""
     data = I.make_dataset(20, I.LINEAR, seed=42)
@@ -162,8 +187,8 @@ def test_graph_errors(ctx):
     data = I.make_dataset(500, I.LINEAR, seed=48)
     with pytest.raises(P.DDError):       # the graph needs the two-level tree
         P.dd_load_dataset(ctx, data, C, ann_nlist=16, ann_levels=1, knn_k=8)
-    with pytest.raises(P.DDError):       # k at most 32
-        P.dd_load_dataset(ctx, data, C, ann_nlist=16, ann_levels=2, knn_k=33)
+    with pytest.raises(P.DDError):       # k at most 128
+        P.dd_load_dataset(ctx, data, C, ann_nlist=16, ann_levels=2, knn_k=129)
     ds = P.dd_load_dataset(ctx, data, C, ann_nlist=16, ann_levels=2)
     try:
         y = I.make_states(4, I.LINEAR, seed=1, spread=0.1)
