@@ -145,6 +145,8 @@ def oracle_searches_per_s(W: I.Workload, C, target_s: float = 12.0, max_queries:
     t0 = time.time()
     n_pts = min(W.N, max_points)
     data = I.make_dataset(n_pts, W.law, seed=W.seed)
+    if C is None:       # the data-derived metric (Sec. 3.1) of the sample
+        C = metric.pca_metric(data.astype(np.float64))
     Z = metric.to_z(data, C)
     gen_s = time.time() - t0
     y = I.make_states(max_queries, W.law, seed=99, spread=0.05)
@@ -191,6 +193,8 @@ def run_ours(args, world, rank, local):
     raw = torch.empty((W.N, 12), dtype=torch.float32, device="cuda")
     P.dd_synth_dataset(ctx, raw, W.law, C, seed=W.seed)
     t_build = time.perf_counter()
+    if W.extra.get("metric") == "pca":
+        C = P.dd_pca_metric(ctx, raw)          # the data-derived metric of Sec. 3.1
     levels = args.ann_levels or (2 if W.N >= 300_000_000 or mode == P.DD_SEARCH_KNNG else 1)
     if approx and levels == 2 and not args.nlist:
         nlist = 1 << 20 if W.N >= 300_000_000 else 1 << 17
@@ -203,7 +207,8 @@ def run_ours(args, world, rank, local):
     init = I.initial_association(W.m, W.N, seed=W.seed)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     data_bytes = W.N * (64 if mode == P.DD_SEARCH_EXACT_TC else 52 if mode == P.DD_SEARCH_EXACT_FP32 else 48)
-    ann_kw = dict(f_d0=args.fd0, f_d_final=args.fd_final, ramp_iters=args.ramp_iters) if mode == P.DD_SEARCH_ANN else {}
+    ann_kw = dict(f_d0=args.fd0, f_d_final=args.fd_final, ramp_iters=args.ramp_iters,
+                  ann_budget=args.ann_budget) if mode == P.DD_SEARCH_ANN else {}
     if mode == P.DD_SEARCH_KNNG:
         ann_kw = dict(f_s=args.f_s)
     flush_l2 = data_bytes < 2 * L2_BYTES
@@ -282,7 +287,8 @@ def run_ours(args, world, rank, local):
         da = np.empty(len(pick))
         ie = np.empty(len(pick), np.int32)
         de = np.empty(len(pick))
-        P.dd_project_nearest(ds, ctx, ysel, ia, da, mode=mode, f_d=args.fd_final, prev_idx=prev, f_s=args.f_s)
+        P.dd_project_nearest(ds, ctx, ysel, ia, da, mode=mode, f_d=args.fd_final, prev_idx=prev, f_s=args.f_s,
+                             ann_budget=args.ann_budget)
         torch.cuda.synchronize()
         t_ex = time.perf_counter()
         P.dd_project_nearest(ds, ctx, ysel, ie, de, mode=P.DD_SEARCH_EXACT_FP32)
@@ -298,7 +304,7 @@ def run_ours(args, world, rank, local):
     y = torch.from_numpy(I.make_states(m_e2e, W.law, seed=7, spread=0.05)).pin_memory()
     idx_h = torch.empty(m_e2e, dtype=torch.int32).pin_memory()
     d2_h = torch.empty(m_e2e, dtype=torch.float64).pin_memory()
-    e2e_kw = dict(mode=mode, certify=certify, f_d=args.fd_final, f_s=args.f_s)
+    e2e_kw = dict(mode=mode, certify=certify, f_d=args.fd_final, f_s=args.f_s, ann_budget=args.ann_budget)
     P.dd_project_nearest(ds, ctx, y.numpy(), idx_h.numpy(), d2_h.numpy(), **e2e_kw)
     reps = max(3, args.steps)
     t = time.perf_counter()
@@ -363,11 +369,12 @@ def run_ours(args, world, rank, local):
                                                                     else "fp16, f32 accum" if mode == 1 else "f32"),
         "data": "synthetic (dd_inputs generator, made on device)",
         "config": {"workload": W.name, "mesh": f"{W.n_el}^3 hex, 2x2x2 Gauss", "material_points": W.m * nload,
-                   "data_points": W.N, "law": W.law.kind, "load": W.loads[0][0], "search": args.mode,
+                   "data_points": W.N, "law": W.law.kind, "metric": W.extra.get("metric", "isotropic C of the law"),
+                   "load": W.loads[0][0], "search": args.mode,
                    "l2": "flushed before every step" if flush_l2 else "inputs larger than L2",
                    "parallelism": f"replicas x{world}",
                    **({"f_d": f"{args.fd0} -> {args.fd_final} over {args.ramp_iters} iterations",
-                       "nlist": nlist, "ann_levels": levels} if mode == P.DD_SEARCH_ANN else {}),
+                       "leaves": P.dd_dataset_ann_nlist(ds), "ann_levels": levels} if mode == P.DD_SEARCH_ANN else {}),
                    **({"knn_k": args.knn_k, "knn_fd": args.knn_fd, "f_s": args.f_s, "nlist": nlist}
                       if mode == P.DD_SEARCH_KNNG else {})},
         "roofline": roof,
@@ -490,7 +497,7 @@ def run_reference(args, world, rank):
     if rank != 0:
         return None
     W = make_workload(args.workload)
-    C = I.isotropic_C(W.law.E, W.law.nu)
+    C = None if W.extra.get("metric") == "pca" else I.isotropic_C(W.law.E, W.law.nu)
     per_step = max(4.0, 60.0 / max(1, args.steps + args.warmup))
     vals = []
     info = None
@@ -531,6 +538,8 @@ def main():
     ap.add_argument("--nlist", type=int, default=0)
     ap.add_argument("--ann-levels", type=int, default=0)
     ap.add_argument("--ann-check", type=int, default=2048)
+    ap.add_argument("--ann-budget", type=int, default=0,
+                    help="leaves a query's warp scans before the leaf-major pass (0: library default, -1: all)")
     ap.add_argument("--knn-k", type=int, default=None, help="k of the k-NN graph (default: the workload's, else 128)")
     ap.add_argument("--knn-fd", type=float, default=None, help="f_d of the graph build (default: workload's, else 0.8)")
     ap.add_argument("--f-s", type=int, default=None, help="node-change bound of the graph walk (0: none; default: "

@@ -128,6 +128,11 @@ class DataLaw:
     kind="linear":     sigma = C eps + noise
     kind="nonlinear":  sigma = C eps (1 + beta*|eps|) + noise   (|eps|: 2-norm
                        of the Voigt 6-vector as stored)
+    kind="eq9":        the isotropic cubic law of Eq. (9),
+                       sigma = 2 mu (eps + beta eps^3) + lam (tr eps + beta (tr eps)^3) I,
+                       eps^3 the tensor power, lam and mu the Lame constants of
+                       C (with lam = mu = E/2 and beta = alpha this is the
+                       paper's E (eps + alpha eps^3 + 0.5 (tr eps + alpha (tr eps)^3) I)
     eps components i.i.d. uniform in [eps_lo, eps_hi]; noise i.i.d. per stress
     component, std ``noise_std`` (Irwin-Hall).
     """
@@ -141,7 +146,46 @@ class DataLaw:
 
     @property
     def code(self) -> int:
-        return {"linear": 0, "nonlinear": 1}[self.kind]
+        return {"linear": 0, "nonlinear": 1, "eq9": 2}[self.kind]
+
+
+def _eq9_stress(C: np.ndarray, e: np.ndarray, beta: float) -> np.ndarray:
+    """Stress of the cubic law (kind "eq9") in Voigt order, tensor shear
+    stresses; every operation rounded once, in a fixed order shared with the
+    C and device copies of the generator."""
+    lam, mu = C[0, 1], C[3, 3]
+    a, b, c = e[:, 0], e[:, 1], e[:, 2]
+    d, g, f = 0.5 * e[:, 3], 0.5 * e[:, 4], 0.5 * e[:, 5]      # tensor shears e23, e13, e12
+    # P = E E
+    p11 = (a * a + f * f) + g * g
+    p22 = (f * f + b * b) + d * d
+    p33 = (g * g + d * d) + c * c
+    p23 = (f * g + b * d) + d * c
+    p13 = (a * g + f * d) + g * c
+    p12 = (a * f + f * b) + g * d
+    # Q = P E
+    q11 = (p11 * a + p12 * f) + p13 * g
+    q22 = (p12 * f + p22 * b) + p23 * d
+    q33 = (p13 * g + p23 * d) + p33 * c
+    q23 = (p12 * g + p22 * d) + p23 * c
+    q13 = (p11 * g + p12 * d) + p13 * c
+    q12 = (p11 * f + p12 * b) + p13 * d
+    tr = (a + b) + c
+    h = lam * (tr + beta * ((tr * tr) * tr))
+    m2 = 2.0 * mu
+    return np.stack([h + m2 * (a + beta * q11), h + m2 * (b + beta * q22), h + m2 * (c + beta * q33),
+                     m2 * (d + beta * q23), m2 * (g + beta * q13), m2 * (f + beta * q12)], axis=1)
+
+
+def law_stress(law: DataLaw, eps: np.ndarray) -> np.ndarray:
+    """Noise-free stress of the law at strains eps [n, 6] (float64)."""
+    C = isotropic_C(law.E, law.nu)
+    if law.kind == "eq9":
+        return _eq9_stress(C, eps, law.beta)
+    s = _matvec_ordered(C, eps)
+    if law.kind == "nonlinear":
+        s = s * (1.0 + law.beta * _norm_ordered(eps))[:, None]
+    return s
 
 
 def make_dataset(N: int, law: DataLaw, seed: int = 0, start: int = 0,
@@ -160,10 +204,7 @@ def make_dataset(N: int, law: DataLaw, seed: int = 0, start: int = 0,
         eps = law.eps_lo + width * uniform53(draws(key, ctr_e))
         ctr_n = base[:, None, None] + (np.uint64(8) + np.arange(36, dtype=np.uint64)).reshape(1, 6, 6)
         g = irwin_hall(draws(key, ctr_n))
-        s = _matvec_ordered(C, eps)
-        if law.kind == "nonlinear":
-            fac = 1.0 + law.beta * _norm_ordered(eps)
-            s = s * fac[:, None]
+        s = law_stress(law, eps)
         sig = s + law.noise_std * g
         out[c0:c0 + n, :6] = eps.astype(np.float32)
         out[c0:c0 + n, 6:] = sig.astype(np.float32)
@@ -183,9 +224,7 @@ def make_states(m: int, law: DataLaw, seed: int, spread: float,
     u = uniform53(draws(key, j + np.arange(18, dtype=np.uint64)[None, :]))
     width = law.eps_hi - law.eps_lo
     eps = law.eps_lo + width * u[:, :6]
-    s = _matvec_ordered(C, eps)
-    if law.kind == "nonlinear":
-        s = s * (1.0 + law.beta * _norm_ordered(eps))[:, None]
+    s = law_stress(law, eps)
     a = spread * width if scale is None else scale
     eps = eps + a * (u[:, 6:12] - 0.5)
     s = s + a * float(np.abs(C).max()) * (u[:, 12:18] - 0.5)
@@ -280,6 +319,9 @@ NONLINEAR = DataLaw("nonlinear", -5e-3, 5e-3, 1e-5)
 # the strain range of the paper's torsion data (Sec. 3.1: [-0.025, 0.025]),
 # with a milder stiffening (the factor 1 + beta |eps| stays below 1.6)
 TORSION_LAW = DataLaw("nonlinear", -0.025, 0.025, 1e-5, beta=10.0)
+# the paper's law, Eq. (9): E = 1000, alpha = 500, i.e. Lame constants
+# lam = mu = 500 (isotropic C with E' = 1250, nu = 0.25), no noise
+EQ9_LAW = DataLaw("eq9", -0.025, 0.025, 0.0, beta=500.0, E=1250.0, nu=0.25)
 
 WORKLOADS = {
     "cube4_N1e4_exact_fp64": Workload("cube4_N1e4_exact_fp64", 4, 10_000, LINEAR),
@@ -297,12 +339,15 @@ WORKLOADS = {
     # (the search is cheap in the latter)
     "cube32_N1e5_exact": Workload("cube32_N1e5_exact", 32, 100_000, NONLINEAR),
     # the paper's own problem (Sec. 3.1): 20^3 cube, top face turned by 2
-    # degrees, 64 000 material points; approximate-search schedule f_d 0.4 ->
-    # 0.8 over 5 iterations (f_d0, f_d_final, ramp)
-    "cube20_N1e9_rot2_ann": Workload("cube20_N1e9_rot2_ann", 20, 1_000_000_000, TORSION_LAW,
-                                     loads=(("rotation", 2.0),), extra={"schedule": (0.4, 0.8, 5)}),
-    "cube20_N1e8_rot2_ann": Workload("cube20_N1e8_rot2_ann", 20, 100_000_000, TORSION_LAW,
-                                     loads=(("rotation", 2.0),), extra={"schedule": (0.4, 0.8, 5)}),
+    # degrees, 64 000 material points, data from the law of Eq. (9), the
+    # metric from the data's principal components; approximate-search
+    # schedule f_d 0.4 -> 0.8 over 5 iterations (f_d0, f_d_final, ramp)
+    "cube20_N1e9_rot2_ann": Workload("cube20_N1e9_rot2_ann", 20, 1_000_000_000, EQ9_LAW,
+                                     loads=(("rotation", 2.0),),
+                                     extra={"schedule": (0.4, 0.8, 5), "metric": "pca"}),
+    "cube20_N1e8_rot2_ann": Workload("cube20_N1e8_rot2_ann", 20, 100_000_000, EQ9_LAW,
+                                     loads=(("rotation", 2.0),),
+                                     extra={"schedule": (0.4, 0.8, 5), "metric": "pca"}),
     "serve_N1e7": Workload("serve_N1e7", 0, 10_000_000, NONLINEAR,
                            extra={"requests": 512, "edge_min": 4, "edge_max": 24,
                                   "t_min": 1e-4, "t_max": 2e-3}),

@@ -162,11 +162,29 @@ dd_status dd_dataset_ann_index(dd_dataset *ds, int32_t *cluster_of, double *cent
 int dd_dataset_knn_k(const dd_dataset *ds);
 dd_status dd_dataset_knn_graph(dd_dataset *ds, int32_t *nbr);
 
+/* The data-derived metric of Sec. 3.1 (principal component analysis):
+ * the six principal component vectors of the data (eigenvectors of the
+ * covariance about the mean with the six largest eigenvalues) are the columns
+ * of A (12 x 6), A_eps its upper and A_sig its lower 6 x 6 block, and
+ *     C = sym(A_sig A_eps^{-1}),
+ * the paper's sym(A_eps^{-1} A_sig) with the components as rows of A; for
+ * data on a linear law sig = C0 eps it returns C0.  The moments are summed in
+ * FP64 on the device in a fixed order (the same result on every run).
+ *   eps_sig  host or device, float32 [N x 12] (eps[6], sig[6]), N >= 13.
+ *   C_out    host, 36 doubles (row-major), written on DD_OK.
+ * Errors: DD_ERR_ARG (null, N < 13, non-finite data), DD_ERR_NOT_SPD (the
+ * principal strain block is singular or the metric is not positive
+ * definite), DD_ERR_CUDA.  Synchronous. */
+dd_status dd_pca_metric(dd_ctx *ctx, const float *eps_sig, int64_t N, double *C_out);
+
 /* Write points start .. start+N-1 of the seeded synthetic data set into the
  * device buffer out_dev (float32 [N x 12]).  This is the device copy of the
  * input generator of the Python module dd_inputs (SplitMix64 counter stream,
  * uniform strains in [eps_lo, eps_hi], stress from the law `law` = 0:
- * sig = C eps, 1: sig = C eps (1 + beta |eps|), plus Irwin-Hall noise of std
+ * sig = C eps, 1: sig = C eps (1 + beta |eps|), 2: the cubic isotropic law
+ * of Eq. (9), sig = 2 mu (eps + beta eps^3) + lam (tr eps + beta (tr eps)^3) I
+ * with lam = C[0][1], mu = C[3][3] and eps^3 the tensor power, plus
+ * Irwin-Hall noise of std
  * noise_std), bit-identical to it.  It is not part of the DD method; it
  * exists so that data sets of 10^8-10^9 points can be made in place.
  * Asynchronous on `stream` (a cudaStream_t, NULL = the context's stream). */
@@ -197,6 +215,15 @@ typedef struct dd_search_opts {
                                  prev_idx the walk of query i starts at data
                                  point SplitMix64(i) mod N (the first output
                                  of SplitMix64 seeded with i) */
+    int ann_budget;           /* DD_SEARCH_ANN with the two-level tree: leaves
+                                 a query's warp scans itself, the warm-start
+                                 leaf first (d_c shrinking after each, as in
+                                 Sec. 4.3); its further Eq. (13) candidates,
+                                 tested with the d_c reached then, are scanned
+                                 leaf-major, up to 32 queries per read of a
+                                 leaf.  0 = default (2), -1 = every leaf in
+                                 the query's warp, < -1 = none (all leaves,
+                                 the warm-start one included, leaf-major) */
 } dd_search_opts;
 
 typedef struct dd_search_stats {
@@ -300,6 +327,7 @@ typedef struct dd_solve_opts {
                                  preconditioned CG throughout */
     int f_s;                  /* DD_SEARCH_KNNG: node-change bound of every
                                  walk, as in dd_search_opts (0 = none) */
+    int ann_budget;           /* DD_SEARCH_ANN: as in dd_search_opts */
 } dd_solve_opts;
 
 /* Result of a solve: the constraint-set state y = (u, eps, sig) of the last

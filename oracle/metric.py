@@ -46,3 +46,24 @@ def local_d2(y: np.ndarray, z: np.ndarray, C: np.ndarray) -> np.ndarray:
     ds = y[:, 6:] - z[:, 6:]
     Cinv = np.linalg.inv(C)
     return np.einsum("ni,ij,nj->n", de, C, de) + np.einsum("ni,ij,nj->n", ds, Cinv, ds)
+
+
+def pca_metric(data: np.ndarray) -> np.ndarray:
+    """The data-derived metric of Sec. 3.1: the 6 principal component vectors
+    of the 12-d data (eigenvectors of its covariance with the 6 largest
+    eigenvalues) are the columns of A (12 x 6); with A_eps its upper and
+    A_sig its lower 6 x 6 block, C = sym(A_sig A_eps^{-1}).
+
+    Reading: the paper writes sym(A_eps^{-1} A_sig); with the components as
+    the *rows* of A that is the same matrix, and it is the one that returns C
+    itself for data on a linear law sig = C eps (the columns of A span
+    {(x, C x)}, so A_sig = C A_eps).  The covariance is taken about the mean.
+    """
+    d = np.asarray(data, dtype=np.float64)
+    X = d - d.mean(axis=0)
+    S = X.T @ X / len(d)
+    w, V = np.linalg.eigh(S)
+    A = V[:, np.argsort(w)[::-1][:6]]
+    Ae, As = A[:6], A[6:]
+    M = np.linalg.solve(Ae.T, As.T).T           # A_sig A_eps^{-1}
+    return 0.5 * (M + M.T)

@@ -84,18 +84,21 @@ def nn_top2(zd: np.ndarray, zq: np.ndarray):
 
 def nn_stream(law, seed: int, N: int, C, zq):
     """Exact nearest point of every mapped query over the seeded data set of
-    N points (law: dd_inputs.DataLaw), generated chunk by chunk in C.
+    N points (law: dd_inputs.DataLaw, generated chunk by chunk in C with the
+    law's own stiffness), mapped with the metric C.
     Returns (index int64, squared mapped distance)."""
     from . import metric
+    import dd_inputs
     lib = _load()
     C = np.ascontiguousarray(C, dtype=np.float64)
     Ch, Cmh = metric.metric_roots(C)
+    C_law = np.ascontiguousarray(dd_inputs.isotropic_C(law.E, law.nu))
     Ch = np.ascontiguousarray(Ch)
     Cmh = np.ascontiguousarray(Cmh)
     zq = np.ascontiguousarray(zq, dtype=np.float64)
     m = len(zq)
     i1 = np.empty(m, np.int64)
     d1 = np.empty(m)
-    lib.oracle_nn_stream(law.code, law.eps_lo, law.eps_hi, law.noise_std, law.beta, C.ctypes.data, seed, N,
+    lib.oracle_nn_stream(law.code, law.eps_lo, law.eps_hi, law.noise_std, law.beta, C_law.ctypes.data, seed, N,
                          Ch.ctypes.data, Cmh.ctypes.data, zq.ctypes.data, m, i1.ctypes.data, d1.ctypes.data)
     return i1, d1

@@ -27,7 +27,7 @@ EXPORTS = [
     "dd_dataset_size", "dd_dataset_bytes", "dd_synth_dataset", "dd_project_nearest", "dd_solve",
     "dd_result_free", "dd_solver_create", "dd_solver_step", "dd_solver_done", "dd_solver_result",
     "dd_solver_free", "dd_launch_count", "dd_dataset_ann_nlist", "dd_dataset_ann_index",
-    "dd_dataset_knn_k", "dd_dataset_knn_graph",
+    "dd_dataset_knn_k", "dd_dataset_knn_graph", "dd_pca_metric",
     "dd_project_nearest_noalloc", "dd_solvers_step", "dd_solve_batch", "dd_server_start", "dd_server_submit",
     "dd_server_poll", "dd_server_get_stats", "dd_server_stop",
 ]
@@ -48,7 +48,7 @@ class dd_dataset_opts(ctypes.Structure):
 
 class dd_search_opts(ctypes.Structure):
     _fields_ = [("mode", c_int), ("certify", c_int), ("f_d", c_double), ("prev_idx", c_void_p),
-                ("stream", c_void_p), ("f_s", c_int)]
+                ("stream", c_void_p), ("f_s", c_int), ("ann_budget", c_int)]
 
 
 class dd_search_stats(ctypes.Structure):
@@ -84,7 +84,7 @@ class dd_solve_opts(ctypes.Structure):
     _fields_ = [("mode", c_int), ("certify", c_int), ("f_d0", c_double), ("f_d_final", c_double),
                 ("ramp_iters", c_int), ("max_iter", c_int), ("cg_rtol", c_double), ("cg_max_iter", c_int),
                 ("seed", c_uint64), ("init_idx", c_void_p), ("stall_iters", c_int), ("cg_mode", c_int),
-                ("f_s", c_int)]
+                ("f_s", c_int), ("ann_budget", c_int)]
 
 
 class dd_server_opts(ctypes.Structure):
@@ -153,6 +153,7 @@ def lib():
         L.dd_dataset_knn_k.argtypes = [vp]
         L.dd_dataset_knn_k.restype = c_int
         L.dd_dataset_knn_graph.argtypes = [vp, vp]
+        L.dd_pca_metric.argtypes = [vp, vp, c_int64, POINTER(c_double)]
         L.dd_project_nearest_noalloc.argtypes = [vp, vp, c_int64, vp, vp, vp]
         L.dd_solvers_step.argtypes = [POINTER(vp), c_int, POINTER(dd_iter_info)]
         L.dd_server_start.argtypes = [vp, POINTER(dd_server_opts), POINTER(vp)]
@@ -246,9 +247,10 @@ def dd_synth_dataset(ctx, out_dev, law, C, seed: int = 0, start: int = 0, stream
 
 
 def dd_project_nearest(ds, ctx, y, idx, d2=None, mode: int = DD_SEARCH_EXACT_FP32, certify: bool = True,
-                       f_d: float = 0.0, prev_idx=None, stream=None, want_stats: bool = True, f_s: int = 0):
+                       f_d: float = 0.0, prev_idx=None, stream=None, want_stats: bool = True, f_s: int = 0,
+                       ann_budget: int = 0):
     m = int(y.shape[0])
-    opts = dd_search_opts(int(mode), int(certify), float(f_d), _ptr(prev_idx), stream, int(f_s))
+    opts = dd_search_opts(int(mode), int(certify), float(f_d), _ptr(prev_idx), stream, int(f_s), int(ann_budget))
     st = dd_search_stats()
     _check(ctx, lib().dd_project_nearest(ds, _ptr(y), m, ctypes.byref(opts), _ptr(idx), _ptr(d2),
                                          ctypes.byref(st) if want_stats else None))
@@ -278,7 +280,8 @@ class Result:
 def dd_solve(ds, ctx, n_el, load, mode: int = DD_SEARCH_EXACT_FP32, init_idx=None, max_iter: int = 100,
              cg_rtol: float = 1e-12, cg_max_iter: int = 20000, certify: bool = True, f_d0: float = 0.0,
              f_d_final: float = 0.0, ramp_iters: int = 20, seed: int = 0, stall_iters: int = 3,
-             lengths=(1.0, 1.0, 1.0), allow_not_converged: bool = True, cg_mode: int = 0, f_s: int = 0):
+             lengths=(1.0, 1.0, 1.0), allow_not_converged: bool = True, cg_mode: int = 0, f_s: int = 0,
+             ann_budget: int = 0):
     """Solve one cube problem; `load` is a dd_inputs.Load.  Returns a Result."""
     nx, ny, nz = (n_el, n_el, n_el) if np.isscalar(n_el) else n_el
     mesh = dd_mesh(nx, ny, nz, *lengths)
@@ -286,7 +289,7 @@ def dd_solve(ds, ctx, n_el, load, mode: int = DD_SEARCH_EXACT_FP32, init_idx=Non
     ii = None if init_idx is None else np.ascontiguousarray(init_idx, dtype=np.int32)
     opts = dd_solve_opts(int(mode), int(certify), float(f_d0), float(f_d_final), int(ramp_iters), int(max_iter),
                          float(cg_rtol), int(cg_max_iter), int(seed), _ptr(ii), int(stall_iters), int(cg_mode),
-                         int(f_s))
+                         int(f_s), int(ann_budget))
     r = dd_result()
     st = lib().dd_solve(ds, ctypes.byref(mesh), ctypes.byref(L), ctypes.byref(opts), ctypes.byref(r))
     try:
@@ -304,23 +307,23 @@ def dd_result_free(r: dd_result) -> None:
 
 
 def _solve_args(n_el, load, mode, init_idx, max_iter, cg_rtol, cg_max_iter, certify, f_d0, f_d_final, ramp_iters,
-                seed, stall_iters, lengths, cg_mode=0, f_s=0):
+                seed, stall_iters, lengths, cg_mode=0, f_s=0, ann_budget=0):
     nx, ny, nz = (n_el, n_el, n_el) if np.isscalar(n_el) else n_el
     mesh = dd_mesh(nx, ny, nz, *lengths)
     L = _load(load)
     ii = None if init_idx is None else np.ascontiguousarray(init_idx, dtype=np.int32)
     opts = dd_solve_opts(int(mode), int(certify), float(f_d0), float(f_d_final), int(ramp_iters), int(max_iter),
                          float(cg_rtol), int(cg_max_iter), int(seed), _ptr(ii), int(stall_iters), int(cg_mode),
-                         int(f_s))
+                         int(f_s), int(ann_budget))
     return mesh, L, opts, ii
 
 
 def dd_solver_create(ds, ctx, n_el, load, mode: int = DD_SEARCH_EXACT_FP32, init_idx=None, max_iter: int = 100,
                      cg_rtol: float = 1e-12, cg_max_iter: int = 20000, certify: bool = True, f_d0: float = 0.0,
                      f_d_final: float = 0.0, ramp_iters: int = 20, seed: int = 0, stall_iters: int = 3,
-                     lengths=(1.0, 1.0, 1.0), cg_mode: int = 0, f_s: int = 0):
+                     lengths=(1.0, 1.0, 1.0), cg_mode: int = 0, f_s: int = 0, ann_budget: int = 0):
     mesh, L, opts, ii = _solve_args(n_el, load, mode, init_idx, max_iter, cg_rtol, cg_max_iter, certify, f_d0,
-                                    f_d_final, ramp_iters, seed, stall_iters, lengths, cg_mode, f_s)
+                                    f_d_final, ramp_iters, seed, stall_iters, lengths, cg_mode, f_s, ann_budget)
     sv = c_void_p()
     _check(ctx, lib().dd_solver_create(ds, ctypes.byref(mesh), ctypes.byref(L), ctypes.byref(opts),
                                        ctypes.byref(sv)))
@@ -369,6 +372,14 @@ def dd_dataset_ann_index(ds, ctx):
     return cl, cent, rad
 
 
+def dd_pca_metric(ctx, eps_sig) -> np.ndarray:
+    """Data-derived metric (Sec. 3.1) of float32 [N, 12] data (numpy array or
+    CUDA tensor): C = sym(A_sig A_eps^{-1}) of the six principal components."""
+    out = (c_double * 36)()
+    _check(ctx, lib().dd_pca_metric(ctx, _ptr(eps_sig), int(eps_sig.shape[0]), out))
+    return np.array(out[:]).reshape(6, 6)
+
+
 def dd_dataset_knn_k(ds) -> int:
     return int(lib().dd_dataset_knn_k(ds))
 
@@ -402,14 +413,15 @@ def dd_solvers_step(svs, ctx):
 def dd_solve_batch(ds, ctx, n_els, loads, mode: int = DD_SEARCH_EXACT_FP32, init_idx=None, max_iter: int = 100,
                    cg_rtol: float = 1e-12, cg_max_iter: int = 20000, certify: bool = True, f_d0: float = 0.0,
                    f_d_final: float = 0.0, ramp_iters: int = 20, seed: int = 0, stall_iters: int = 3,
-                   cg_mode: int = 0, allow_not_converged: bool = True, f_s: int = 0):
+                   cg_mode: int = 0, allow_not_converged: bool = True, f_s: int = 0, ann_budget: int = 0):
     """Solve several cube problems together; n_els[i] edge elements, loads[i]."""
     n = len(n_els)
     meshes = (dd_mesh * n)(*[dd_mesh(k, k, k, 1.0, 1.0, 1.0) for k in n_els])
     Ls = (dd_load * n)(*[_load(L)
                          for L in loads])
     _, _, opts, ii = _solve_args(n_els[0], loads[0], mode, init_idx, max_iter, cg_rtol, cg_max_iter, certify, f_d0,
-                                 f_d_final, ramp_iters, seed, stall_iters, (1.0, 1.0, 1.0), cg_mode, f_s)
+                                 f_d_final, ramp_iters, seed, stall_iters, (1.0, 1.0, 1.0), cg_mode, f_s,
+                                 ann_budget)
     outs = (dd_result * n)()
     st = lib().dd_solve_batch(ds, n, meshes, Ls, ctypes.byref(opts), outs)
     try:
@@ -424,9 +436,10 @@ def dd_solve_batch(ds, ctx, n_els, loads, mode: int = DD_SEARCH_EXACT_FP32, init
 def dd_server_start(ds, ctx, mode: int = DD_SEARCH_EXACT_FP32, state_budget: int = 0, max_batch: int = 0,
                     max_iter: int = 100, cg_rtol: float = 1e-12, cg_max_iter: int = 20000, certify: bool = True,
                     f_d0: float = 0.0, f_d_final: float = 0.0, ramp_iters: int = 20, stall_iters: int = 3,
-                    cg_mode: int = 0, f_s: int = 0):
+                    cg_mode: int = 0, f_s: int = 0, ann_budget: int = 0):
     so = dd_solve_opts(int(mode), int(certify), float(f_d0), float(f_d_final), int(ramp_iters), int(max_iter),
-                       float(cg_rtol), int(cg_max_iter), 0, None, int(stall_iters), int(cg_mode), int(f_s))
+                       float(cg_rtol), int(cg_max_iter), 0, None, int(stall_iters), int(cg_mode), int(f_s),
+                       int(ann_budget))
     o = dd_server_opts(so, int(state_budget), int(max_batch))
     srv = c_void_p()
     _check(ctx, lib().dd_server_start(ds, ctypes.byref(o), ctypes.byref(srv)))

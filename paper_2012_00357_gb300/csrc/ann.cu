@@ -97,29 +97,36 @@ __global__ void __launch_bounds__(256) k_assign(const float *__restrict__ z, int
     if (j < n) out[j] = bi;
 }
 
-__global__ void k_accum(const float *__restrict__ z, int64_t n, const int32_t *__restrict__ asg,
-                        double *__restrict__ sums, unsigned *__restrict__ cnt) {
+// Cluster sums are accumulated in 64-bit fixed point (coordinates scaled by
+// a power of two fs with |z| fs <= 2^30): integer addition does not depend on
+// the order of the atomics, so the k-means build is the same on every run.
+__device__ __forceinline__ unsigned long long to_fixed(float v, double fs) {
+    return (unsigned long long)__double2ll_rn((double)v * fs);
+}
+
+__global__ void k_accum(const float *__restrict__ z, int64_t n, const int32_t *__restrict__ asg, double fs,
+                        unsigned long long *__restrict__ sums, unsigned *__restrict__ cnt) {
     int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= n) return;
     int c = asg[j];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) atomicAdd(sums + (size_t)c * 12 + k, (double)z[j * 12 + k]);
+    for (int k = 0; k < 12; ++k) atomicAdd(sums + (size_t)c * 12 + k, to_fixed(z[j * 12 + k], fs));
     atomicAdd(cnt + c, 1u);
 }
 
 // centroid = mean of its members (kept when empty); norms; reset accumulators
-__global__ void k_update(double *__restrict__ sums, unsigned *__restrict__ cnt, float *__restrict__ cent,
-                         float *__restrict__ cn, int L) {
+__global__ void k_update(unsigned long long *__restrict__ sums, unsigned *__restrict__ cnt, double fs,
+                         float *__restrict__ cent, float *__restrict__ cn, int L) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= L) return;
     unsigned k = cnt[c];
     double n2 = 0.0;
 #pragma unroll
     for (int a = 0; a < 12; ++a) {
-        if (k) cent[(size_t)c * 12 + a] = (float)(sums[(size_t)c * 12 + a] / (double)k);
+        if (k) cent[(size_t)c * 12 + a] = (float)((double)(long long)sums[(size_t)c * 12 + a] / fs / (double)k);
         double v = cent[(size_t)c * 12 + a];
         n2 += v * v;
-        sums[(size_t)c * 12 + a] = 0.0;
+        sums[(size_t)c * 12 + a] = 0ull;
     }
     cn[c] = (float)n2;
     cnt[c] = 0;
@@ -483,12 +490,54 @@ __global__ void k_ann_finish(const float *__restrict__ raw, MetricMaps M, const 
 // Two-level tree: coarse cells of k-means centroids, each split into L2
 // k-means leaves (the k-means tree of Sec. 4.2 with wide branching).
 // ---------------------------------------------------------------------------
-__global__ void k_scatter_idx(const int32_t *__restrict__ asg, int64_t n, const int64_t *__restrict__ offs,
-                              unsigned *__restrict__ cursor, int32_t *__restrict__ perm1) {
-    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    int c = asg[j];
-    perm1[offs[c] + atomicAdd(cursor + c, 1u)] = (int32_t)j;
+// Stable counting sort of the point indices by cell (members of a cell in
+// increasing index order, the same on every run): per-chunk histograms, their
+// per-cell prefix over chunks, then one warp per chunk placing its points in
+// index order.
+constexpr int kStableChunk = 1 << 16;
+
+__global__ void k_chunk_hist(const int32_t *__restrict__ asg, int64_t n, int nb, unsigned *__restrict__ hist) {
+    extern __shared__ unsigned sh_hist[];
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) sh_hist[b] = 0u;
+    __syncthreads();
+    const int64_t j0 = (int64_t)blockIdx.x * kStableChunk, j1 = min(n, j0 + kStableChunk);
+    for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) atomicAdd(sh_hist + asg[j], 1u);
+    __syncthreads();
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[(size_t)blockIdx.x * nb + b] = sh_hist[b];
+}
+
+__global__ void k_chunk_offsets(unsigned *__restrict__ hist, int nchunk, int nb, const int64_t *__restrict__ offs) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    unsigned run = (unsigned)offs[b];
+    for (int c = 0; c < nchunk; ++c) {
+        const unsigned v = hist[(size_t)c * nb + b];
+        hist[(size_t)c * nb + b] = run;
+        run += v;
+    }
+}
+
+__global__ void __launch_bounds__(32) k_stable_scatter(const int32_t *__restrict__ asg, int64_t n, int nb,
+                                                       const unsigned *__restrict__ off, int32_t *__restrict__ perm1) {
+    extern __shared__ unsigned cur[];
+    const int lane = threadIdx.x;
+    for (int b = lane; b < nb; b += 32) cur[b] = off[(size_t)blockIdx.x * nb + b];
+    __syncwarp();
+    const int64_t j0 = (int64_t)blockIdx.x * kStableChunk, j1 = min(n, j0 + kStableChunk);
+    for (int64_t g = j0; g < j1; g += 32) {
+        const int64_t j = g + lane;
+        const bool valid = j < j1;
+        const int b = valid ? asg[j] : -1;
+        const unsigned same = __match_any_sync(0xffffffffu, b);
+        const unsigned rank = __popc(same & ((1u << lane) - 1u));
+        const unsigned base = valid ? cur[b] : 0u;
+        __syncwarp();
+        if (valid) {
+            perm1[base + rank] = (int32_t)j;
+            if (rank == 0) cur[b] = base + __popc(same);
+        }
+        __syncwarp();
+    }
 }
 
 __global__ void k_cell_sorted(const int32_t *__restrict__ perm1, const int32_t *__restrict__ asg1, int64_t n,
@@ -572,13 +621,13 @@ __global__ void __launch_bounds__(256) k_assign_fine(const float *__restrict__ z
 
 __global__ void k_accum_fine(const float *__restrict__ z, const int32_t *__restrict__ perm1,
                              const int32_t *__restrict__ c1s, const int32_t *__restrict__ fasg, int64_t n, int L2,
-                             double *__restrict__ sums, unsigned *__restrict__ cnt) {
+                             double fs, unsigned long long *__restrict__ sums, unsigned *__restrict__ cnt) {
     int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= n) return;
     const int64_t leaf = (int64_t)c1s[p] * L2 + fasg[p];
     const float *zp = z + (size_t)perm1[p] * 12;
 #pragma unroll
-    for (int k = 0; k < 12; ++k) atomicAdd(sums + leaf * 12 + k, (double)zp[k]);
+    for (int k = 0; k < 12; ++k) atomicAdd(sums + leaf * 12 + k, to_fixed(zp[k], fs));
     atomicAdd(cnt + leaf, 1u);
 }
 
@@ -606,10 +655,17 @@ struct Probe2Args {
     const float *rad1;          // [L1] coarse radii
     int L1, L2;
     float r1max;
+    // leaf-major hand-off (all null: every leaf is scanned by the query's warp)
+    int budget;                 // leaves a warp scans itself beyond the warm-start leaf
+    int32_t *pair_leaf;         // [m x kPairMax] leaves left to the leaf-major scan
+    int *n_pairs;               // [m]
+    unsigned *leaf_cnt;         // [L] queries per leaf
 };
 
 constexpr int kFine = 8;        // leaves visited per cell at most
 constexpr int kFinePerLane = 16;   // L2 <= 512
+constexpr int kPairMax = kCand * kFine + 1;   // leaves a query can hand off (candidates + warm-start leaf)
+constexpr int kLeafBudget = 2;                // default leaves a query's warp scans itself
 
 __global__ void __launch_bounds__(256) k_ann_probe2(Probe2Args P) {
     const ProbeArgs &A = P.A;
@@ -642,6 +698,7 @@ __global__ void __launch_bounds__(256) k_ann_probe2(Probe2Args P) {
                         float lb = fmaxf(r2 - mv, 0.f);
                         A.d2[i] = lb * lb;
                         atomicAdd(A.counters + 1, 1ull);
+                        if (P.n_pairs) P.n_pairs[i] = 0;
                     }
                     return;
                 }
@@ -658,7 +715,20 @@ __global__ void __launch_bounds__(256) k_ann_probe2(Probe2Args P) {
         if (lane == 0) atomicOr(A.touched + (l >> 5), 1u << (l & 31));
         best_warp(b);
     };
-    if (l0 >= 0) scan(l0);
+    int nscan = 0, npair = 0;
+    if (l0 >= 0) {
+        if (!P.pair_leaf || P.budget > 0) {
+            scan(l0);
+            ++nscan;
+        } else {
+            // no leaf in the warp: the warm-start leaf goes leaf-major too
+            if (lane == 0) {
+                P.pair_leaf[i * kPairMax + npair] = l0;
+                atomicAdd(P.leaf_cnt + l0, 1u);
+            }
+            ++npair;
+        }
+    }
     float dc = sqrtf(b.d);
     const float f_d = A.fd_q ? A.fd_q[i] : A.f_d;
     bool incomplete = false;
@@ -699,8 +769,18 @@ __global__ void __launch_bounds__(256) k_ann_probe2(Probe2Args P) {
             const int l = C * P.L2 + ml;
             if ((k1 == 0 && k2 == 0) || md - f_d * A.radius[l] < dc) {
                 if (l != l0) {
-                    scan(l);
-                    dc = sqrtf(b.d);
+                    if (!P.pair_leaf || nscan < P.budget) {
+                        scan(l);
+                        dc = sqrtf(b.d);
+                        ++nscan;
+                    } else if (A.offs[l + 1] > A.offs[l]) {
+                        // hand the leaf to the leaf-major scan (Eq. 13 tested with the current d_c)
+                        if (lane == 0) {
+                            P.pair_leaf[i * kPairMax + npair] = l;
+                            atomicAdd(P.leaf_cnt + l, 1u);
+                        }
+                        ++npair;
+                    }
                 }
             }
         }
@@ -728,7 +808,243 @@ __global__ void __launch_bounds__(256) k_ann_probe2(Probe2Args P) {
         A.idx[i] = b.j;
         A.d1[i] = b.d;
         A.d2[i] = b.s;
+        if (P.n_pairs) P.n_pairs[i] = npair;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Leaf-major scan of the handed-off (leaf, query) pairs: the pairs are bucketed
+// by leaf (counting sort), and one warp takes up to 32 queries of one leaf, a
+// lane per query, reading each point of the leaf once for all of them.
+// ---------------------------------------------------------------------------
+constexpr int kScanBlock = 1024;   // leaves per block of the count scans
+
+// Inclusive block scan of 1024 values (256 threads x 4); returns the
+// exclusive prefix of this thread's first value, the block total in *tot.
+__device__ __forceinline__ unsigned block_scan4(unsigned (&v)[4], unsigned *sh, unsigned *tot) {
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    unsigned s = v[0] + v[1] + v[2] + v[3];
+    unsigned x = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        unsigned z = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0u;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, z, o);
+            if (lane >= o) z += y;
+        }
+        if (lane < (int)(blockDim.x >> 5)) sh[lane] = z;
+    }
+    __syncthreads();
+    const unsigned before = (w ? sh[w - 1] : 0u) + x - s;
+    *tot = sh[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before;
+}
+
+// per block of 1024 leaves: totals of queries and of 32-query chunks
+__global__ void __launch_bounds__(256) k_leaf_sums(const unsigned *__restrict__ cnt, int L,
+                                                    unsigned *__restrict__ bsum, unsigned *__restrict__ bitem) {
+    __shared__ unsigned sh[8];
+    const int base = blockIdx.x * kScanBlock + threadIdx.x * 4;
+    unsigned a[4], c[4], ta, tc;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        a[k] = base + k < L ? cnt[base + k] : 0u;
+        c[k] = (a[k] + 31u) >> 5;
+    }
+    block_scan4(a, sh, &ta);
+    block_scan4(c, sh, &tc);
+    if (threadIdx.x == 0) {
+        bsum[blockIdx.x] = ta;
+        bitem[blockIdx.x] = tc;
+    }
+}
+
+// exclusive scan of the block totals (one block; nb <= 4096)
+__global__ void __launch_bounds__(1024) k_leaf_sums_top(unsigned *__restrict__ bsum, unsigned *__restrict__ bitem,
+                                                        int nb) {
+    __shared__ unsigned sh[32];
+    for (int which = 0; which < 2; ++which) {
+        unsigned *a = which ? bitem : bsum;
+        unsigned v[4], tot;
+        const int base = threadIdx.x * 4;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = base + k < nb ? a[base + k] : 0u;
+        unsigned run = block_scan4(v, sh, &tot);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (base + k < nb) {
+                const unsigned x = v[k];
+                a[base + k] = run;
+                run += x;
+            }
+        __syncthreads();
+    }
+}
+
+// per-leaf exclusive offsets of pairs and chunks; entry L holds the totals
+__global__ void __launch_bounds__(256) k_leaf_offsets(const unsigned *__restrict__ cnt, int L,
+                                                       const unsigned *__restrict__ bsum,
+                                                       const unsigned *__restrict__ bitem,
+                                                       unsigned *__restrict__ pair_off, unsigned *__restrict__ item_off) {
+    __shared__ unsigned sh[8];
+    const int base = blockIdx.x * kScanBlock + threadIdx.x * 4;
+    unsigned a[4], c[4], ta, tc;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        a[k] = base + k < L ? cnt[base + k] : 0u;
+        c[k] = (a[k] + 31u) >> 5;
+    }
+    unsigned ra = block_scan4(a, sh, &ta) + bsum[blockIdx.x];
+    unsigned rc = block_scan4(c, sh, &tc) + bitem[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (base + k < L) {
+            pair_off[base + k] = ra;
+            item_off[base + k] = rc;
+        }
+        if (base + k == L - 1) {
+            pair_off[L] = ra + a[k];
+            item_off[L] = rc + c[k];
+        }
+        ra += a[k];
+        rc += c[k];
+    }
+}
+
+// bucket every handed-off pair by its leaf: bucket holds the pair slot
+// i * kPairMax + t (query i = slot / kPairMax)
+__global__ void k_pair_scatter(const int32_t *__restrict__ pair_leaf, const int *__restrict__ n_pairs, int64_t m,
+                               const unsigned *__restrict__ pair_off, unsigned *__restrict__ cursor,
+                               unsigned *__restrict__ bucket) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int n = n_pairs[i];
+    for (int t = 0; t < n; ++t) {
+        const int l = pair_leaf[i * kPairMax + t];
+        bucket[pair_off[l] + atomicAdd(cursor + l, 1u)] = (unsigned)(i * kPairMax + t);
+    }
+}
+
+struct PairRes {
+    float d1;       // best squared distance in the leaf
+    int p1;         // its sorted position
+    float d2;       // second best
+};
+
+struct LeafScanArgs {
+    const float *zs;
+    const int64_t *offs;
+    const QueryRec *rec;
+    const unsigned *bucket, *pair_off, *item_off;
+    int L;
+    PairRes *res;               // [m x kPairMax]
+    unsigned long long *counters;
+    unsigned *touched;
+};
+
+__global__ void __launch_bounds__(256) k_leaf_scan(LeafScanArgs A) {
+    __shared__ unsigned long long sc;
+    if (threadIdx.x == 0) sc = 0ull;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const unsigned nw = (gridDim.x * blockDim.x) >> 5;
+    const unsigned total = A.item_off[A.L];
+    for (unsigned it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < total; it += nw) {
+        // the leaf of this chunk: item_off[l] <= it < item_off[l + 1]
+        int lo = 0, hi = A.L;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (A.item_off[mid] <= it) lo = mid;
+            else hi = mid;
+        }
+        const int l = lo;
+        const unsigned q0 = A.pair_off[l] + 32u * (it - A.item_off[l]);
+        const unsigned qn = min(32u, A.pair_off[l + 1] - q0);
+        const bool act = (unsigned)lane < qn;
+        const unsigned slot = act ? A.bucket[q0 + lane] : 0u;
+        float q[12];
+        const QueryRec *r = A.rec + (act ? slot / kPairMax : 0);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) q[k] = r->q[k];
+        const int64_t p0 = A.offs[l], p1 = A.offs[l + 1];
+        float b1 = INFINITY, b2 = INFINITY;
+        int j1 = 0x7fffffff;
+        int64_t p = p0;
+        for (; p + 3 < p1; p += 4) {
+            float d[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) d[u] = dist2_12(A.zs + (p + u) * 12, q);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (d[u] < b1) {
+                    b2 = b1;
+                    b1 = d[u];
+                    j1 = (int)(p + u);
+                } else {
+                    b2 = fminf(b2, d[u]);
+                }
+            }
+        }
+        for (; p < p1; ++p) {
+            const float d = dist2_12(A.zs + p * 12, q);
+            if (d < b1) {
+                b2 = b1;
+                b1 = d;
+                j1 = (int)p;
+            } else {
+                b2 = fminf(b2, d);
+            }
+        }
+        if (act) A.res[slot] = PairRes{b1, j1, b2};
+        if (lane == 0) {
+            atomicOr(A.touched + (l >> 5), 1u << (l & 31));
+            atomicAdd(&sc, (unsigned long long)qn * (unsigned long long)(p1 - p0));
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && sc) {
+        atomicAdd(A.counters, sc);
+        atomicAdd(A.counters + 5, sc);
+    }
+}
+
+// fold the leaf-major results into every query's answer (ties to the lower
+// data index; the second distance over all points read)
+__global__ void k_pair_merge(const int *__restrict__ n_pairs, const PairRes *__restrict__ res,
+                             const int32_t *__restrict__ perm, int64_t m, int32_t *__restrict__ idx,
+                             float *__restrict__ d1, float *__restrict__ d2) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int n = n_pairs[i];
+    if (!n) return;
+    float bd = d1[i], bs = d2[i];
+    int bj = idx[i];
+    for (int t = 0; t < n; ++t) {
+        const PairRes r = res[i * kPairMax + t];
+        if (!(r.d1 < INFINITY)) continue;
+        const int j = perm[r.p1];
+        if (j == bj) {              // the warm-start point, met again in its handed-off leaf
+            bs = fminf(bs, r.d2);
+            continue;
+        }
+        if (r.d1 < bd || (r.d1 == bd && j < bj)) {
+            bs = fminf(bs, bd);
+            bd = r.d1;
+            bj = j;
+        } else {
+            bs = fminf(bs, r.d1);
+        }
+        bs = fminf(bs, r.d2);
+    }
+    idx[i] = bj;
+    d1[i] = bd;
+    d2[i] = bs;
 }
 
 // Points in the clusters marked in the bitmap (the data a search must read
@@ -791,6 +1107,13 @@ __global__ void k_scatter_results(const int64_t *__restrict__ list, int64_t n, c
 }
 
 }  // namespace
+
+// Power-of-two scale of the fixed-point cluster sums: |z| fs <= 2^30, so the
+// sum of up to 2^31 members stays below 2^61.
+static double fixed_scale(double maxabs) {
+    const double m = maxabs > 0 ? maxabs : 1.0;
+    return std::ldexp(1.0, 30 - (int)std::ceil(std::log2(m)));
+}
 
 // Certified exact search (FP32 scan + FP64 rescoring) of the listed queries.
 static dd_status ann_exact_subset(dd_dataset *ds, const double *y_dev, const int64_t *list, int64_t n, SearchOut out,
@@ -907,7 +1230,8 @@ dd_status dd_build_ann(dd_dataset *ds, const dd_dataset_opts &o) {
     char *c = (char *)w;
     float *sample = (float *)c;
     int32_t *asg = (int32_t *)(c + (b_sample + 255) / 256 * 256);
-    double *sums = (double *)((char *)asg + (b_asg + 255) / 256 * 256);
+    unsigned long long *sums = (unsigned long long *)((char *)asg + (b_asg + 255) / 256 * 256);
+    const double fs = fixed_scale(ds->maxabs);
     unsigned *cnt = (unsigned *)((char *)sums + b_sums);
 
     ctx->launches++;
@@ -920,12 +1244,12 @@ dd_status dd_build_ann(dd_dataset *ds, const dd_dataset_opts &o) {
     DD_TRY_CUDA(ctx, cudaMemsetAsync(sums, 0, b_sums, s));
     DD_TRY_CUDA(ctx, cudaMemsetAsync(cnt, 0, (size_t)Lp * 4, s));
     ctx->launches++;
-    k_update<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(sums, cnt, a.cent, a.cn, L);   // norms only
+    k_update<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(sums, cnt, fs, a.cent, a.cn, L);   // norms only
     for (int it = 0; it < iters; ++it) {
         ctx->launches += 3;
         k_assign<<<(unsigned)((S + 255) / 256), 256, 0, s>>>(sample, S, a.cent, a.cn, L, asg);
-        k_accum<<<(unsigned)((S + 255) / 256), 256, 0, s>>>(sample, S, asg, sums, cnt);
-        k_update<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(sums, cnt, a.cent, a.cn, L);
+        k_accum<<<(unsigned)((S + 255) / 256), 256, 0, s>>>(sample, S, asg, fs, sums, cnt);
+        k_update<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(sums, cnt, fs, a.cent, a.cn, L);
     }
     DD_TRY_CUDA(ctx, cudaGetLastError());
     // padding centroids: never selected by the scans
@@ -1021,7 +1345,8 @@ static dd_status build_tree2(dd_dataset *ds, const dd_dataset_opts &o) {
     int32_t *perm1 = (int32_t *)(c + b_sample + b_n);
     int32_t *c1s = (int32_t *)(c + b_sample + 2 * b_n);
     int32_t *fasg = (int32_t *)(c + b_sample + 3 * b_n);
-    double *sums = (double *)(c + b_sample + 4 * b_n);
+    unsigned long long *sums = (unsigned long long *)(c + b_sample + 4 * b_n);
+    const double fs = fixed_scale(ds->maxabs);
     unsigned *cnt = (unsigned *)(c + b_sample + 4 * b_n + b_sums);
     int64_t *offs1 = (int64_t *)(c + b_sample + 4 * b_n + b_sums + b_cnt);
     const unsigned gN = (unsigned)((N + 255) / 256);
@@ -1034,12 +1359,12 @@ static dd_status build_tree2(dd_dataset *ds, const dd_dataset_opts &o) {
     DD_TRY_CUDA(ctx, cudaMemsetAsync(sums, 0, b_sums, s));
     DD_TRY_CUDA(ctx, cudaMemsetAsync(cnt, 0, b_cnt, s));
     ctx->launches++;
-    k_update<<<(unsigned)((L1 + 255) / 256), 256, 0, s>>>(sums, cnt, a.cent1, a.cn1, L1);
+    k_update<<<(unsigned)((L1 + 255) / 256), 256, 0, s>>>(sums, cnt, fs, a.cent1, a.cn1, L1);
     for (int it = 0; it < iters; ++it) {
         ctx->launches += 3;
         k_assign<<<(unsigned)((S1 + 255) / 256), 256, 0, s>>>(sample, S1, a.cent1, a.cn1, L1, asg1);
-        k_accum<<<(unsigned)((S1 + 255) / 256), 256, 0, s>>>(sample, S1, asg1, sums, cnt);
-        k_update<<<(unsigned)((L1 + 255) / 256), 256, 0, s>>>(sums, cnt, a.cent1, a.cn1, L1);
+        k_accum<<<(unsigned)((S1 + 255) / 256), 256, 0, s>>>(sample, S1, asg1, fs, sums, cnt);
+        k_update<<<(unsigned)((L1 + 255) / 256), 256, 0, s>>>(sums, cnt, fs, a.cent1, a.cn1, L1);
     }
     if (L1p > L1) {
         std::vector<float> big((size_t)(L1p - L1), 1e30f);
@@ -1059,19 +1384,29 @@ static dd_status build_tree2(dd_dataset *ds, const dd_dataset_opts &o) {
     DD_TRY_CUDA(ctx, cudaMemcpyAsync(offs1, ho1.data(), (L1p + 1) * 8, cudaMemcpyHostToDevice, s));
     DD_TRY_CUDA(ctx, cudaMemsetAsync(cnt, 0, b_cnt, s));
     ctx->launches += 3;
-    k_scatter_idx<<<gN, 256, 0, s>>>(asg1, N, offs1, cnt, perm1);
+    {
+        // stable: the members of a cell in index order
+        const int nchunk = (int)((N + kStableChunk - 1) / kStableChunk);
+        void *wh = nullptr;
+        DD_TRY(dd_workspace(ctx, WS_ANN_PAIRS, (size_t)nchunk * L1 * 4, &wh));
+        unsigned *hist = (unsigned *)wh;
+        ctx->launches += 2;
+        k_chunk_hist<<<nchunk, 256, (size_t)L1 * 4, s>>>(asg1, N, L1, hist);
+        k_chunk_offsets<<<(L1 + 255) / 256, 256, 0, s>>>(hist, nchunk, L1, offs1);
+        k_stable_scatter<<<nchunk, 32, (size_t)L1 * 4, s>>>(asg1, N, L1, hist, perm1);
+    }
     k_cell_sorted<<<gN, 256, 0, s>>>(perm1, asg1, N, c1s);
     // ---- leaves: Lloyd inside every cell ----
     k_fine_init<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(ds->z32, perm1, offs1, L1, L2, a.cent1, a.cent);
     DD_TRY_CUDA(ctx, cudaMemsetAsync(sums, 0, b_sums, s));
     DD_TRY_CUDA(ctx, cudaMemsetAsync(cnt, 0, b_cnt, s));
     ctx->launches++;
-    k_update<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(sums, cnt, a.cent, a.cn, L);
+    k_update<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(sums, cnt, fs, a.cent, a.cn, L);
     for (int it = 0; it < iters; ++it) {
         ctx->launches += 3;
         k_assign_fine<<<gN, 256, 0, s>>>(ds->z32, perm1, c1s, N, a.cent, a.cn, L2, fasg);
-        k_accum_fine<<<gN, 256, 0, s>>>(ds->z32, perm1, c1s, fasg, N, L2, sums, cnt);
-        k_update<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(sums, cnt, a.cent, a.cn, L);
+        k_accum_fine<<<gN, 256, 0, s>>>(ds->z32, perm1, c1s, fasg, N, L2, fs, sums, cnt);
+        k_update<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(sums, cnt, fs, a.cent, a.cn, L);
     }
     ctx->launches += 2;
     k_assign_fine<<<gN, 256, 0, s>>>(ds->z32, perm1, c1s, N, a.cent, a.cn, L2, fasg);
@@ -1146,13 +1481,13 @@ dd_status dd_ann_finish(dd_dataset *ds, const double *y_dev, int64_t m, const in
 }
 
 dd_status dd_search_ann(dd_dataset *ds, const double *y_dev, int64_t m, double f_d, const int32_t *prev_idx_dev,
-                        SearchOut out, dd_search_stats *st, cudaStream_t s) {
-    return dd_search_ann_motion(ds, y_dev, m, f_d, nullptr, prev_idx_dev, nullptr, out, st, s);
+                        int budget, SearchOut out, dd_search_stats *st, cudaStream_t s) {
+    return dd_search_ann_motion(ds, y_dev, m, f_d, nullptr, prev_idx_dev, nullptr, budget, out, st, s);
 }
 
 dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, double f_d, const float *fd_q,
-                               const int32_t *prev_idx_dev, AnnMotion *mot, SearchOut out, dd_search_stats *st,
-                               cudaStream_t s) {
+                               const int32_t *prev_idx_dev, AnnMotion *mot, int budget, SearchOut out,
+                               dd_search_stats *st, cudaStream_t s) {
     dd_ctx *ctx = ds->ctx;
     AnnIndex &a = ds->ann;
     if (m == 0) return DD_OK;
@@ -1205,8 +1540,51 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
     A.counters = counters;
     A.touched = touched;
     ctx->launches++;
-    if (two) {
-        Probe2Args P2{A, a.cent, a.rad1, a.L1, a.L2, a.r1max};
+    if (budget == 0) budget = kLeafBudget;
+    if (budget < -1) budget = 0;
+    if (two && budget >= 0 && m * kPairMax < ((int64_t)1 << 31)) {
+        // the query's warp scans `budget` leaves itself (the warm-start leaf
+        // first); the further candidates of Eq. (13) go to the leaf-major scan
+        const int L = a.nlist, nb = (L + kScanBlock - 1) / kScanBlock;
+        const size_t b_pl = r256((size_t)m * kPairMax * 4), b_np = r256((size_t)m * 4),
+                     b_res = r256((size_t)m * kPairMax * sizeof(PairRes)), b_L = r256((size_t)L * 4),
+                     b_L1 = r256((size_t)(L + 1) * 4), b_nb = r256((size_t)nb * 4);
+        void *wp = nullptr;
+        DD_TRY(dd_workspace(ctx, WS_ANN_PAIRS, 2 * b_pl + b_np + b_res + 2 * b_L + 2 * b_L1 + 2 * b_nb, &wp));
+        char *cp = (char *)wp;
+        int32_t *pair_leaf = (int32_t *)cp;
+        cp += b_pl;
+        unsigned *bucket = (unsigned *)cp;
+        cp += b_pl;
+        int *n_pairs = (int *)cp;
+        cp += b_np;
+        PairRes *res = (PairRes *)cp;
+        cp += b_res;
+        unsigned *leaf_cnt = (unsigned *)cp;
+        cp += b_L;
+        unsigned *cursor = (unsigned *)cp;
+        cp += b_L;
+        unsigned *pair_off = (unsigned *)cp;
+        cp += b_L1;
+        unsigned *item_off = (unsigned *)cp;
+        cp += b_L1;
+        unsigned *bsum = (unsigned *)cp;
+        cp += b_nb;
+        unsigned *bitem = (unsigned *)cp;
+        DD_TRY_CUDA(ctx, cudaMemsetAsync(leaf_cnt, 0, 2 * b_L, s));   // counts and cursors
+        Probe2Args P2{A, a.cent, a.rad1, a.L1, a.L2, a.r1max, budget, pair_leaf, n_pairs, leaf_cnt};
+        k_ann_probe2<<<(unsigned)((m * 32 + 255) / 256), 256, 0, s>>>(P2);
+        DD_TRY_CUDA(ctx, cudaGetLastError());
+        ctx->launches += 6;
+        k_leaf_sums<<<nb, 256, 0, s>>>(leaf_cnt, L, bsum, bitem);
+        k_leaf_sums_top<<<1, 1024, 0, s>>>(bsum, bitem, nb);
+        k_leaf_offsets<<<nb, 256, 0, s>>>(leaf_cnt, L, bsum, bitem, pair_off, item_off);
+        k_pair_scatter<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(pair_leaf, n_pairs, m, pair_off, cursor, bucket);
+        LeafScanArgs LS{a.zs, a.offs, rec, bucket, pair_off, item_off, L, res, counters, touched};
+        k_leaf_scan<<<(unsigned)(ctx->n_sm * 8), 256, 0, s>>>(LS);
+        k_pair_merge<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(n_pairs, res, a.perm, m, out.idx, d1f, d2f);
+    } else if (two) {
+        Probe2Args P2{A, a.cent, a.rad1, a.L1, a.L2, a.r1max, 0, nullptr, nullptr, nullptr};
         k_ann_probe2<<<(unsigned)((m * 32 + 255) / 256), 256, 0, s>>>(P2);
     } else {
         k_ann_probe<<<(unsigned)((m * 32 + 255) / 256), 256, 0, s>>>(A);

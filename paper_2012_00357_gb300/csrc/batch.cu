@@ -1186,11 +1186,13 @@ dd_status enqueue_step(dd_solver **svs, int n, const StepIO &io, const std::vect
     AnnMotion mot = io.mot;
     if (ann) {
         if (!ds->ann.nlist) return dd_fail(ctx, DD_ERR_STATE, "ANN search needs the partition (ann_nlist)");
-        DD_TRY(dd_search_ann_motion(ds, io.y_cat, M, fds[0], io.fd_cat, io.prev_cat, &mot, so, &sst, s));
+        DD_TRY(dd_search_ann_motion(ds, io.y_cat, M, fds[0], io.fd_cat, io.prev_cat, &mot, o0.ann_budget, so, &sst,
+                                    s));
     } else if (o0.mode == DD_SEARCH_KNNG) {
         DD_TRY(dd_search_knng(ds, io.y_cat, M, o0.f_s, io.prev_cat, &mot, so, &sst, s));
     } else {
-        DD_TRY(dd_run_search(ds, o0.mode, o0.certify, o0.f_d_final, o0.f_s, nullptr, io.y_cat, M, so, &sst, s));
+        DD_TRY(dd_run_search(ds, o0.mode, o0.certify, o0.f_d_final, o0.f_s, o0.ann_budget, nullptr, io.y_cat, M, so,
+                             &sst, s));
     }
     off = 0;
     for (int i = 0; i < n; ++i) {
@@ -1417,8 +1419,9 @@ extern "C" dd_status dd_solvers_step(dd_solver **svs, int n, dd_iter_info *infos
         if (!sv || sv->ds != ds) return dd_fail(ctx, DD_ERR_ARG, "dd_solvers_step: solvers must share one data set");
         if (sv->done) return dd_fail(ctx, DD_ERR_STATE, "dd_solvers_step: a solve has already finished");
         if (sv->o.mode != o0.mode || sv->o.certify != o0.certify || sv->o.cg_mode != o0.cg_mode ||
-            sv->o.f_s != o0.f_s)
-            return dd_fail(ctx, DD_ERR_ARG, "dd_solvers_step: solvers must share search mode, certify, cg_mode and f_s");
+            sv->o.f_s != o0.f_s || sv->o.ann_budget != o0.ann_budget)
+            return dd_fail(ctx, DD_ERR_ARG,
+                           "dd_solvers_step: solvers must share search mode, certify, cg_mode, f_s and ann_budget");
         for (int j = 0; j < i; ++j)
             if (svs[j] == sv) return dd_fail(ctx, DD_ERR_ARG, "dd_solvers_step: a solver appears twice");
         M += sv->g.n_gp;

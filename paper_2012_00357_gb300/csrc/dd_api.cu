@@ -228,7 +228,8 @@ extern "C" size_t dd_dataset_bytes(const dd_dataset *ds) { return ds ? ds->bytes
 // ---------------------------------------------------------------------------
 // P_D
 // ---------------------------------------------------------------------------
-dd_status dd_run_search(dd_dataset *ds, int mode, int certify, double f_d, int f_s, const int32_t *prev_dev,
+dd_status dd_run_search(dd_dataset *ds, int mode, int certify, double f_d, int f_s, int budget,
+                        const int32_t *prev_dev,
                             const double *y_dev, int64_t m, SearchOut out, dd_search_stats *st, cudaStream_t s) {
     switch (mode) {
     case DD_SEARCH_EXACT_FP32:
@@ -238,7 +239,7 @@ dd_status dd_run_search(dd_dataset *ds, int mode, int certify, double f_d, int f
         return dd_search_exact_tc(ds, y_dev, m, certify, out, st, s);
     case DD_SEARCH_ANN:
         if (!ds->ann.nlist) return dd_fail(ds->ctx, DD_ERR_STATE, "ANN search needs the partition (ann_nlist)");
-        return dd_search_ann(ds, y_dev, m, f_d, prev_dev, out, st, s);
+        return dd_search_ann(ds, y_dev, m, f_d, prev_dev, budget, out, st, s);
     case DD_SEARCH_KNNG:
         return dd_search_knng(ds, y_dev, m, f_s, prev_dev, nullptr, out, st, s);
     default:
@@ -295,7 +296,7 @@ extern "C" dd_status dd_project_nearest(dd_dataset *ds, const double *y, int64_t
         DD_TRY_CUDA(ctx, cudaEventRecord(e0, s));
     }
     SearchOut out{idx_dev, d2_dev, nullptr};
-    dd_status st = dd_run_search(ds, o.mode, o.certify, o.f_d, o.f_s, prev_dev, y_dev, m, out, stats ? &local : nullptr, s);
+    dd_status st = dd_run_search(ds, o.mode, o.certify, o.f_d, o.f_s, o.ann_budget, prev_dev, y_dev, m, out, stats ? &local : nullptr, s);
     if (st != DD_OK) return st;
     if (stats) {
         DD_TRY_CUDA(ctx, cudaEventRecord(e1, s));

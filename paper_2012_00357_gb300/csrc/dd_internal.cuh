@@ -113,7 +113,7 @@ void dd_plans_drop(dd_ctx *ctx, uint64_t id);
 
 enum WsSlot {
     WS_SEARCH = 0, WS_QUERY = 1, WS_MISC = 2, WS_SOLVE = 3, WS_TC = 4, WS_ANN = 5, WS_ANN_SCAN = 6, WS_ANN_BUILD = 7,
-    WS_BATCH = 8, WS_BATCH_CG = 9
+    WS_BATCH = 8, WS_BATCH_CG = 9, WS_ANN_PAIRS = 10
 };
 
 // Coarse cells a tree search ranks per query (ann.cu).
@@ -186,6 +186,9 @@ bool dd_is_device_ptr(const void *p);
 
 // Host linear algebra (host_linalg.cu)
 bool dd_metric_maps(const double *C, MetricMaps *M);   // false: not SPD
+// Eigen-decomposition of the symmetric n x n A (n <= 12, row-major,
+// destroyed) by cyclic Jacobi rotations: eigenvectors as the columns of V.
+void dd_sym_eig(int n, double *A, double *V, double *w);
 
 // Padding granule of the data arrays (points).
 constexpr int64_t kDataTile = 256;
@@ -215,19 +218,24 @@ dd_status dd_search_exact_tc(dd_dataset *ds, const double *y_dev, int64_t m, int
                              SearchOut out, dd_search_stats *st, cudaStream_t s);
 dd_status dd_build_fp16(dd_dataset *ds);
 dd_status dd_search_ann(dd_dataset *ds, const double *y_dev, int64_t m, double f_d,
-                        const int32_t *prev_idx_dev, SearchOut out, dd_search_stats *st,
+                        const int32_t *prev_idx_dev, int budget, SearchOut out, dd_search_stats *st,
                         cudaStream_t s);
 dd_status dd_build_ann(dd_dataset *ds, const dd_dataset_opts &o);
+// budget (two-level tree): leaves a query's warp scans itself (the
+// warm-start leaf first) before the further Eq. (13) candidates go to the
+// leaf-major scan; 0 = the default, -1 = all leaves in the query's warp,
+// < -1 = none.
 dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, double f_d, const float *fd_q,
-                               const int32_t *prev_idx_dev, AnnMotion *mot, SearchOut out, dd_search_stats *st,
-                               cudaStream_t s);
+                               const int32_t *prev_idx_dev, AnnMotion *mot, int budget, SearchOut out,
+                               dd_search_stats *st, cudaStream_t s);
 // FP64 exhaustive re-search of the queries listed in fb_list (count on device).
 dd_status dd_fallback_exact(dd_dataset *ds, const double *y_dev, const int64_t *fb_list,
                             const unsigned long long *fb_count, int64_t m, SearchOut out, cudaStream_t s);
 // Record (q, d1, d2) of the last search for the moving-query test.
 dd_status dd_ann_motion_update(dd_ctx *ctx, const QueryRec *rec, int64_t m, const double *d2, const double *d2nd,
                                AnnMotion *mot, cudaStream_t s);
-dd_status dd_run_search(dd_dataset *ds, int mode, int certify, double f_d, int f_s, const int32_t *prev_dev,
+dd_status dd_run_search(dd_dataset *ds, int mode, int certify, double f_d, int f_s, int budget,
+                        const int32_t *prev_dev,
                         const double *y_dev, int64_t m, SearchOut out, dd_search_stats *st, cudaStream_t s);
 void dd_free_ann(dd_dataset *ds);
 // The kAnnCand nearest coarse cells of every query (two-level tree), sorted by

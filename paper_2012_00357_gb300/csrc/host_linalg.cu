@@ -7,43 +7,47 @@
 
 namespace {
 
-void jacobi6(double A[6][6], double V[6][6], double w[6]) {
-    for (int i = 0; i < 6; ++i)
-        for (int j = 0; j < 6; ++j) V[i][j] = (i == j) ? 1.0 : 0.0;
+// Cyclic Jacobi on the n x n symmetric A (row-major, stride n, destroyed):
+// V (row-major) holds the eigenvectors as columns, w the eigenvalues.
+void jacobi(int n, double *A, double *V, double *w) {
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) V[i * n + j] = (i == j) ? 1.0 : 0.0;
     for (int sweep = 0; sweep < 100; ++sweep) {
         double off = 0.0, diag = 0.0;
-        for (int p = 0; p < 6; ++p) {
-            diag += A[p][p] * A[p][p];
-            for (int q = p + 1; q < 6; ++q) off += A[p][q] * A[p][q];
+        for (int p = 0; p < n; ++p) {
+            diag += A[p * n + p] * A[p * n + p];
+            for (int q = p + 1; q < n; ++q) off += A[p * n + q] * A[p * n + q];
         }
         if (off <= 1e-34 * diag) break;
-        for (int p = 0; p < 6; ++p) {
-            for (int q = p + 1; q < 6; ++q) {
-                double apq = A[p][q];
+        for (int p = 0; p < n; ++p) {
+            for (int q = p + 1; q < n; ++q) {
+                double apq = A[p * n + q];
                 if (apq == 0.0) continue;
-                double theta = (A[q][q] - A[p][p]) / (2.0 * apq);
+                double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
                 double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
                 double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
-                for (int k = 0; k < 6; ++k) {          // A <- A J
-                    double akp = A[k][p], akq = A[k][q];
-                    A[k][p] = c * akp - s * akq;
-                    A[k][q] = s * akp + c * akq;
+                for (int k = 0; k < n; ++k) {          // A <- A J
+                    double akp = A[k * n + p], akq = A[k * n + q];
+                    A[k * n + p] = c * akp - s * akq;
+                    A[k * n + q] = s * akp + c * akq;
                 }
-                for (int k = 0; k < 6; ++k) {          // A <- J^T A
-                    double apk = A[p][k], aqk = A[q][k];
-                    A[p][k] = c * apk - s * aqk;
-                    A[q][k] = s * apk + c * aqk;
+                for (int k = 0; k < n; ++k) {          // A <- J^T A
+                    double apk = A[p * n + k], aqk = A[q * n + k];
+                    A[p * n + k] = c * apk - s * aqk;
+                    A[q * n + k] = s * apk + c * aqk;
                 }
-                for (int k = 0; k < 6; ++k) {          // V <- V J
-                    double vkp = V[k][p], vkq = V[k][q];
-                    V[k][p] = c * vkp - s * vkq;
-                    V[k][q] = s * vkp + c * vkq;
+                for (int k = 0; k < n; ++k) {          // V <- V J
+                    double vkp = V[k * n + p], vkq = V[k * n + q];
+                    V[k * n + p] = c * vkp - s * vkq;
+                    V[k * n + q] = s * vkp + c * vkq;
                 }
             }
         }
     }
-    for (int i = 0; i < 6; ++i) w[i] = A[i][i];
+    for (int i = 0; i < n; ++i) w[i] = A[i * n + i];
 }
+
+void jacobi6(double A[6][6], double V[6][6], double w[6]) { jacobi(6, &A[0][0], &V[0][0], w); }
 
 void spectral(const double V[6][6], const double f[6], double *out) {
     for (int i = 0; i < 6; ++i)
@@ -55,6 +59,8 @@ void spectral(const double V[6][6], const double f[6], double *out) {
 }
 
 }  // namespace
+
+void dd_sym_eig(int n, double *A, double *V, double *w) { jacobi(n, A, V, w); }
 
 bool dd_metric_maps(const double *C, MetricMaps *M) {
     double amax = 0.0;

@@ -311,11 +311,11 @@ extern "C" dd_status dd_solver_step(dd_solver *sv, dd_iter_info *info) {
     std::memset(&sst, 0, sizeof(sst));
     if (o.mode == DD_SEARCH_ANN) {
         if (!ds->ann.nlist) return dd_fail(ctx, DD_ERR_STATE, "ANN search needs the partition (ann_nlist)");
-        DD_TRY(dd_search_ann_motion(ds, sv->y, ng, f_d, nullptr, sv->cur, &sv->mot, so, &sst, s));
+        DD_TRY(dd_search_ann_motion(ds, sv->y, ng, f_d, nullptr, sv->cur, &sv->mot, o.ann_budget, so, &sst, s));
     } else if (o.mode == DD_SEARCH_KNNG) {
         DD_TRY(dd_search_knng(ds, sv->y, ng, o.f_s, sv->cur, &sv->mot, so, &sst, s));
     } else {
-        DD_TRY(dd_run_search(ds, o.mode, o.certify, f_d, o.f_s, sv->cur, sv->y, ng, so, &sst, s));
+        DD_TRY(dd_run_search(ds, o.mode, o.certify, f_d, o.f_s, o.ann_budget, sv->cur, sv->y, ng, so, &sst, s));
     }
     DD_TRY_CUDA(ctx, cudaEventRecord(sv->ev[3], s));
     DD_TRY(fem_iter_stats(ctx, sv->nxt, sv->cur, sv->d2, sv->dpc, ng, g.w, sv->stats, s));

@@ -55,6 +55,29 @@ __global__ void k_synth(SynthParams P, int64_t start, int64_t N, float *__restri
         double fac = __dadd_rn(1.0, __dmul_rn(P.beta, __dsqrt_rn(n2)));
 #pragma unroll
         for (int i = 0; i < 6; ++i) s[i] = __dmul_rn(s[i], fac);
+    } else if (P.law == 2) {
+        // cubic isotropic law of Eq. (9): 2 mu (E + beta E^3) + lam (tr + beta tr^3) I
+        const double lam = P.C[1], mu = P.C[21];
+        const double a = e[0], b = e[1], c = e[2];
+        const double d = __dmul_rn(0.5, e[3]), g = __dmul_rn(0.5, e[4]), f = __dmul_rn(0.5, e[5]);
+        auto dot3 = [](double x1, double y1, double x2, double y2, double x3, double y3) {
+            return __dadd_rn(__dadd_rn(__dmul_rn(x1, y1), __dmul_rn(x2, y2)), __dmul_rn(x3, y3));
+        };
+        const double p11 = dot3(a, a, f, f, g, g), p22 = dot3(f, f, b, b, d, d);
+        const double p33 = dot3(g, g, d, d, c, c), p23 = dot3(f, g, b, d, d, c);
+        const double p13 = dot3(a, g, f, d, g, c), p12 = dot3(a, f, f, b, g, d);
+        const double q11 = dot3(p11, a, p12, f, p13, g), q22 = dot3(p12, f, p22, b, p23, d);
+        const double q33 = dot3(p13, g, p23, d, p33, c), q23 = dot3(p12, g, p22, d, p23, c);
+        const double q13 = dot3(p11, g, p12, d, p13, c), q12 = dot3(p11, f, p12, b, p13, d);
+        const double tr = __dadd_rn(__dadd_rn(a, b), c);
+        const double h = __dmul_rn(lam, __dadd_rn(tr, __dmul_rn(P.beta, __dmul_rn(__dmul_rn(tr, tr), tr))));
+        const double m2 = __dmul_rn(2.0, mu);
+        s[0] = __dadd_rn(h, __dmul_rn(m2, __dadd_rn(a, __dmul_rn(P.beta, q11))));
+        s[1] = __dadd_rn(h, __dmul_rn(m2, __dadd_rn(b, __dmul_rn(P.beta, q22))));
+        s[2] = __dadd_rn(h, __dmul_rn(m2, __dadd_rn(c, __dmul_rn(P.beta, q33))));
+        s[3] = __dmul_rn(m2, __dadd_rn(d, __dmul_rn(P.beta, q23)));
+        s[4] = __dmul_rn(m2, __dadd_rn(g, __dmul_rn(P.beta, q13)));
+        s[5] = __dmul_rn(m2, __dadd_rn(f, __dmul_rn(P.beta, q12)));
     }
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
@@ -77,7 +100,7 @@ extern "C" dd_status dd_synth_dataset(dd_ctx *ctx, int law, double eps_lo, doubl
                                       double beta, const double *C, uint64_t seed, int64_t start, int64_t N,
                                       float *out_dev, void *stream) {
     if (!ctx) return DD_ERR_ARG;
-    if (!C || !out_dev || N < 0 || start < 0 || (law != 0 && law != 1))
+    if (!C || !out_dev || N < 0 || start < 0 || law < 0 || law > 2)
         return dd_fail(ctx, DD_ERR_ARG, "dd_synth_dataset: bad argument");
     if (N == 0) return DD_OK;
     if (!dd_is_device_ptr(out_dev)) return dd_fail(ctx, DD_ERR_ARG, "dd_synth_dataset: out_dev must be device memory");

@@ -35,11 +35,11 @@ def annset(ctx):
     P.dd_free_dataset(ds)
 
 
-def search(ctx, ds, y, f_d, prev=None):
+def search(ctx, ds, y, f_d, prev=None, ann_budget=0):
     m = len(y)
     idx = np.full(m, -7, np.int32)
     d2 = np.full(m, -1.0)
-    st = P.dd_project_nearest(ds, ctx, y, idx, d2, mode=P.DD_SEARCH_ANN, f_d=f_d,
+    st = P.dd_project_nearest(ds, ctx, y, idx, d2, mode=P.DD_SEARCH_ANN, f_d=f_d, ann_budget=ann_budget,
                               prev_idx=None if prev is None else np.ascontiguousarray(prev, np.int32))
     return idx, d2, st
 
@@ -164,6 +164,44 @@ def test_tree2_warm_start_and_recall(ctx, treeset):
         print(f"tree2 f_d={f_d}: recall {recall[-1]:.4f}, points/query {st.distances / len(y):.0f}")
     # accuracy grows with f_d (Sec. 4.1-4.2) and f_d = 1 is exact
     assert recall[0] >= 0.5 and recall[1] >= recall[0] and recall[2] == 1.0
+
+
+@pytest.mark.parametrize("f_d", [0.0, 0.4, 0.8])
+def test_tree2_leaf_major_never_worse(ctx, treeset, f_d):
+    """Leaves beyond a query's budget are tested against the d_c reached when
+    the budget ran out, which is never below the d_c of the all-in-warp
+    sequence, so the leaf-major search scans a superset of its leaves: every
+    answer is at least as near, and f_d = 1 stays exact."""
+    data, ds = treeset
+    Z = metric.to_z(data.astype(np.float64), C)
+    y = I.make_states(3000, I.NONLINEAR, seed=21, spread=0.05)
+    zq = metric.to_z(y, C)
+    prev = np.random.default_rng(4).integers(0, len(data), len(y)).astype(np.int32)
+    i_w, _, st_w = search(ctx, ds, y, f_d, prev, ann_budget=-1)
+    dw = ((Z[i_w] - zq) ** 2).sum(1)
+    for budget in (-2, 1, 2, 4):
+        i_l, _, st_l = search(ctx, ds, y, f_d, prev, ann_budget=budget)
+        dl = ((Z[i_l] - zq) ** 2).sum(1)
+        print(f"f_d={f_d} budget={budget}: same {np.mean(i_l == i_w):.4f}, points {st_l.points} vs {st_w.points}")
+        assert np.all(dl <= dw * (1 + 1e-6))
+        assert st_l.points >= st_w.points
+
+
+@pytest.mark.parametrize("levels,nlist", [(1, 64), (2, 256)])
+def test_index_build_is_deterministic(ctx, levels, nlist):
+    """Two builds of the same data set give the same index bit for bit
+    (cluster sums in fixed point, cells filled in index order)."""
+    data = I.make_dataset(80000, I.NONLINEAR, seed=23)
+    a = P.dd_load_dataset(ctx, data, C, ann_nlist=nlist, ann_levels=levels, seed=5)
+    b = P.dd_load_dataset(ctx, data, C, ann_nlist=nlist, ann_levels=levels, seed=5)
+    try:
+        for x, y in zip(P.dd_dataset_ann_index(a, ctx), P.dd_dataset_ann_index(b, ctx)):
+            assert np.array_equal(x, y)
+        y = I.make_states(2000, I.NONLINEAR, seed=24, spread=0.05)
+        assert np.array_equal(search(ctx, a, y, 0.5)[0], search(ctx, b, y, 0.5)[0])
+    finally:
+        P.dd_free_dataset(a)
+        P.dd_free_dataset(b)
 
 
 def test_tree2_solve_close_to_exact(ctx):

@@ -79,7 +79,57 @@ def test_load_cases():
 
 def test_c_generator_bit_identical():
     from dd_inputs import cgen
-    for law, start in ((I.LINEAR, 0), (I.NONLINEAR, 987654)):
+    for law, start in ((I.LINEAR, 0), (I.NONLINEAR, 987654), (I.EQ9_LAW, 55555)):
         a = I.make_dataset(4000, law, seed=3, start=start)
         b = cgen.make_dataset(4000, law, seed=3, start=start)
         assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+
+
+def voigt_to_tensor(e):
+    """Strain tensor from Voigt strains with engineering shears."""
+    return np.array([[e[0], e[5] / 2, e[4] / 2], [e[5] / 2, e[1], e[3] / 2], [e[4] / 2, e[3] / 2, e[2]]])
+
+
+def stress_to_voigt(S):
+    return np.array([S[0, 0], S[1, 1], S[2, 2], S[1, 2], S[0, 2], S[0, 1]])
+
+
+def test_eq9_law_is_the_papers_formula():
+    """With lam = mu = E/2 (E = 1000) and beta = alpha = 500 the generator's
+    law is E (eps + alpha eps^3 + 0.5 (tr eps + alpha (tr eps)^3) I) of
+    Eq. (9), eps^3 the matrix cube of the strain tensor, written out here
+    with numpy's matrix power."""
+    law = I.EQ9_LAW
+    Cm = I.isotropic_C(law.E, law.nu)
+    assert np.isclose(Cm[0, 1], 500.0) and np.isclose(Cm[3, 3], 500.0)
+    rng = np.random.default_rng(0)
+    eps = rng.uniform(-0.025, 0.025, (50, 6))
+    got = I.law_stress(law, eps)
+    E, alpha = 1000.0, 500.0
+    for k in range(len(eps)):
+        T = voigt_to_tensor(eps[k])
+        tr = np.trace(T)
+        S = E * (T + alpha * np.linalg.matrix_power(T, 3) + 0.5 * (tr + alpha * tr ** 3) * np.eye(3))
+        assert np.allclose(got[k], stress_to_voigt(S), rtol=1e-12, atol=1e-12)
+
+
+def test_eq9_law_closed_forms_and_isotropy():
+    law = I.EQ9_LAW
+    lam = mu = 500.0
+    beta = law.beta
+    x, gam = 0.02, 0.03
+    s = I.law_stress(law, np.array([[x, 0, 0, 0, 0, 0], [0, 0, 0, 0, 0, gam]]))
+    g = x + beta * x ** 3
+    assert np.allclose(s[0], [(lam + 2 * mu) * g, lam * g, lam * g, 0, 0, 0], rtol=1e-14)
+    h = gam / 2
+    assert np.allclose(s[1], [0, 0, 0, 0, 0, 2 * mu * (h + beta * h ** 3)], rtol=1e-14, atol=1e-15)
+    # an isotropic tensor function: rotating the strain rotates the stress
+    rng = np.random.default_rng(1)
+    Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    e = rng.uniform(-0.025, 0.025, 6)
+    Te = voigt_to_tensor(e)
+    Tr = Q @ Te @ Q.T
+    er = np.array([Tr[0, 0], Tr[1, 1], Tr[2, 2], 2 * Tr[1, 2], 2 * Tr[0, 2], 2 * Tr[0, 1]])
+    s0, s1 = I.law_stress(law, np.stack([e, er]))
+    S0 = np.array([[s0[0], s0[5], s0[4]], [s0[5], s0[1], s0[3]], [s0[4], s0[3], s0[2]]])
+    assert np.allclose(stress_to_voigt(Q @ S0 @ Q.T), s1, rtol=1e-12, atol=1e-12)

@@ -53,3 +53,35 @@ def test_rejects_non_spd():
     except ValueError:
         return
     raise AssertionError("non-SPD metric accepted")
+
+
+def test_pca_metric_recovers_a_linear_law():
+    """Data on sig = C0 eps (C0 SPD, not isotropic, strains from a
+    non-isotropic distribution): the principal subspace is {(x, C0 x)} and
+    the PCA metric is C0 itself."""
+    rng = np.random.default_rng(3)
+    B = rng.normal(size=(6, 6))
+    C0 = B @ B.T + 6 * np.eye(6)
+    eps = rng.uniform(-1, 1, (5000, 6)) * np.array([1, 2, 3, 0.5, 0.7, 1.3]) + 0.2
+    data = np.concatenate([eps, eps @ C0.T], axis=1)
+    C = M.pca_metric(data)
+    assert np.allclose(C, C0, rtol=1e-9, atol=1e-9 * np.abs(C0).max())
+    # invariant to the order of the data
+    assert np.allclose(M.pca_metric(data[::-1]), C, rtol=1e-12, atol=0)
+
+
+def test_pca_metric_of_the_papers_law():
+    """Eq. (9) data (strains in [-0.025, 0.025]^6): the PCA metric is
+    symmetric positive definite, stiffer than the law's tangent at zero
+    strain (the cubic terms stiffen), and nearly isotropic (the cube of
+    strains is symmetric under axis permutations)."""
+    law = I.EQ9_LAW
+    data = I.make_dataset(200000, law, seed=1).astype(np.float64)
+    C = M.pca_metric(data)
+    assert np.allclose(C, C.T)
+    w = np.linalg.eigvalsh(C)
+    assert w.min() > 0
+    C_lin = I.isotropic_C(law.E, law.nu)
+    assert np.all(np.diag(C) > np.diag(C_lin))
+    assert np.allclose(np.diag(C)[:3], np.diag(C)[:3].mean(), rtol=0.02)
+    assert np.allclose(np.diag(C)[3:], np.diag(C)[3:].mean(), rtol=0.02)
