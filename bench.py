@@ -326,7 +326,8 @@ def run_ours(args, world, rank, local):
         scanned = statistics.mean(i.points for i in infos)
         byts = scanned * 48 + W.m * nload * 48
         achieved = byts / (scan_avg / 1e3) / 1e9
-        roof = {"kernel": "k_ann_probe2 + centroid scan" if levels == 2 else "k_ann_probe + centroid scan",
+        roof = {"kernel": ("k_rank_small + k_ann_probe2 + k_leaf_scan (per step)" if levels == 2
+                           else "k_ann_probe + centroid scan"),
                 "bound": "hbm", "achieved": achieved,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                 "traffic": captured_traffic(W.name, args.mode),
@@ -532,7 +533,7 @@ def main():
     # (the paper's ramp from 0, or a final f_d below 0.6, ends at a worse
     # fixed point on these workloads)
     ap.add_argument("--fd-final", type=float, default=None,
-                    help="final f_d of the approximate search (default: the workload's schedule, else 0.6)")
+                    help="final f_d of the approximate search (default: the workload's schedule, else 0.7)")
     ap.add_argument("--fd0", type=float, default=None, help="f_d of the first iteration (default: workload's, else 0.3)")
     ap.add_argument("--ramp-iters", type=int, default=None, help="iterations of the f_d ramp (default: workload's, else 5)")
     ap.add_argument("--nlist", type=int, default=0)
@@ -551,7 +552,7 @@ def main():
         args.mode = ("serve" if args.workload.startswith("serve") else "ann" if "_ann" in args.workload
                      else "knng" if "_knng" in args.workload else "tc")
     # f_d schedule of the approximate search: the workload's, unless given
-    sched = I.WORKLOADS[args.workload].extra.get("schedule", (0.3, 0.6, 5))
+    sched = I.WORKLOADS[args.workload].extra.get("schedule", (0.3, 0.7, 5))
     args.fd0 = sched[0] if args.fd0 is None else args.fd0
     args.fd_final = sched[1] if args.fd_final is None else args.fd_final
     args.ramp_iters = sched[2] if args.ramp_iters is None else args.ramp_iters

@@ -328,6 +328,22 @@ typedef struct dd_solve_opts {
     int f_s;                  /* DD_SEARCH_KNNG: node-change bound of every
                                  walk, as in dd_search_opts (0 = none) */
     int ann_budget;           /* DD_SEARCH_ANN: as in dd_search_opts */
+    int fd_rule;              /* DD_SEARCH_ANN: the accuracy schedule
+                                 f = f(d, d_e, i) of Eq. (11):
+                                 0 (default) the linear ramp above;
+                                 1 global: f starts at f_d0 and rises by
+                                 (f_d_final - f_d0) / ramp_iters after every
+                                 iteration in which P_D reduced the global
+                                 distance by less than the fraction fd_tau
+                                 (1 - d_after_PD / d_after_PC < fd_tau), up to
+                                 f_d_final; fd_tau = 1 gives the ramp;
+                                 2 local: a material point whose distance
+                                 after P_C is at most fd_tau times the mean of
+                                 the previous iteration is searched with
+                                 f_d_final, the others with the ramp value.
+                                 The stop tests apply once f has reached
+                                 f_d_final (rule 1) or the ramp has ended. */
+    double fd_tau;            /* parameter of fd_rule 1 and 2 (>= 0) */
 } dd_solve_opts;
 
 /* Result of a solve: the constraint-set state y = (u, eps, sig) of the last

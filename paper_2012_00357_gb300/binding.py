@@ -84,7 +84,7 @@ class dd_solve_opts(ctypes.Structure):
     _fields_ = [("mode", c_int), ("certify", c_int), ("f_d0", c_double), ("f_d_final", c_double),
                 ("ramp_iters", c_int), ("max_iter", c_int), ("cg_rtol", c_double), ("cg_max_iter", c_int),
                 ("seed", c_uint64), ("init_idx", c_void_p), ("stall_iters", c_int), ("cg_mode", c_int),
-                ("f_s", c_int), ("ann_budget", c_int)]
+                ("f_s", c_int), ("ann_budget", c_int), ("fd_rule", c_int), ("fd_tau", c_double)]
 
 
 class dd_server_opts(ctypes.Structure):
@@ -250,7 +250,7 @@ def dd_project_nearest(ds, ctx, y, idx, d2=None, mode: int = DD_SEARCH_EXACT_FP3
                        f_d: float = 0.0, prev_idx=None, stream=None, want_stats: bool = True, f_s: int = 0,
                        ann_budget: int = 0):
     m = int(y.shape[0])
-    opts = dd_search_opts(int(mode), int(certify), float(f_d), _ptr(prev_idx), stream, int(f_s), int(ann_budget))
+    opts = dd_search_opts(int(mode), int(certify), float(f_d), _ptr(prev_idx), stream, int(f_s), int(ann_budget), int(fd_rule), float(fd_tau))
     st = dd_search_stats()
     _check(ctx, lib().dd_project_nearest(ds, _ptr(y), m, ctypes.byref(opts), _ptr(idx), _ptr(d2),
                                          ctypes.byref(st) if want_stats else None))
@@ -281,7 +281,7 @@ def dd_solve(ds, ctx, n_el, load, mode: int = DD_SEARCH_EXACT_FP32, init_idx=Non
              cg_rtol: float = 1e-12, cg_max_iter: int = 20000, certify: bool = True, f_d0: float = 0.0,
              f_d_final: float = 0.0, ramp_iters: int = 20, seed: int = 0, stall_iters: int = 3,
              lengths=(1.0, 1.0, 1.0), allow_not_converged: bool = True, cg_mode: int = 0, f_s: int = 0,
-             ann_budget: int = 0):
+             ann_budget: int = 0, fd_rule: int = 0, fd_tau: float = 0.0):
     """Solve one cube problem; `load` is a dd_inputs.Load.  Returns a Result."""
     nx, ny, nz = (n_el, n_el, n_el) if np.isscalar(n_el) else n_el
     mesh = dd_mesh(nx, ny, nz, *lengths)
@@ -289,7 +289,7 @@ def dd_solve(ds, ctx, n_el, load, mode: int = DD_SEARCH_EXACT_FP32, init_idx=Non
     ii = None if init_idx is None else np.ascontiguousarray(init_idx, dtype=np.int32)
     opts = dd_solve_opts(int(mode), int(certify), float(f_d0), float(f_d_final), int(ramp_iters), int(max_iter),
                          float(cg_rtol), int(cg_max_iter), int(seed), _ptr(ii), int(stall_iters), int(cg_mode),
-                         int(f_s), int(ann_budget))
+                         int(f_s), int(ann_budget), int(fd_rule), float(fd_tau))
     r = dd_result()
     st = lib().dd_solve(ds, ctypes.byref(mesh), ctypes.byref(L), ctypes.byref(opts), ctypes.byref(r))
     try:
@@ -307,23 +307,25 @@ def dd_result_free(r: dd_result) -> None:
 
 
 def _solve_args(n_el, load, mode, init_idx, max_iter, cg_rtol, cg_max_iter, certify, f_d0, f_d_final, ramp_iters,
-                seed, stall_iters, lengths, cg_mode=0, f_s=0, ann_budget=0):
+                seed, stall_iters, lengths, cg_mode=0, f_s=0, ann_budget=0, fd_rule=0, fd_tau=0.0):
     nx, ny, nz = (n_el, n_el, n_el) if np.isscalar(n_el) else n_el
     mesh = dd_mesh(nx, ny, nz, *lengths)
     L = _load(load)
     ii = None if init_idx is None else np.ascontiguousarray(init_idx, dtype=np.int32)
     opts = dd_solve_opts(int(mode), int(certify), float(f_d0), float(f_d_final), int(ramp_iters), int(max_iter),
                          float(cg_rtol), int(cg_max_iter), int(seed), _ptr(ii), int(stall_iters), int(cg_mode),
-                         int(f_s), int(ann_budget))
+                         int(f_s), int(ann_budget), int(fd_rule), float(fd_tau))
     return mesh, L, opts, ii
 
 
 def dd_solver_create(ds, ctx, n_el, load, mode: int = DD_SEARCH_EXACT_FP32, init_idx=None, max_iter: int = 100,
                      cg_rtol: float = 1e-12, cg_max_iter: int = 20000, certify: bool = True, f_d0: float = 0.0,
                      f_d_final: float = 0.0, ramp_iters: int = 20, seed: int = 0, stall_iters: int = 3,
-                     lengths=(1.0, 1.0, 1.0), cg_mode: int = 0, f_s: int = 0, ann_budget: int = 0):
+                     lengths=(1.0, 1.0, 1.0), cg_mode: int = 0, f_s: int = 0, ann_budget: int = 0,
+                     fd_rule: int = 0, fd_tau: float = 0.0):
     mesh, L, opts, ii = _solve_args(n_el, load, mode, init_idx, max_iter, cg_rtol, cg_max_iter, certify, f_d0,
-                                    f_d_final, ramp_iters, seed, stall_iters, lengths, cg_mode, f_s, ann_budget)
+                                    f_d_final, ramp_iters, seed, stall_iters, lengths, cg_mode, f_s, ann_budget,
+                                    fd_rule, fd_tau)
     sv = c_void_p()
     _check(ctx, lib().dd_solver_create(ds, ctypes.byref(mesh), ctypes.byref(L), ctypes.byref(opts),
                                        ctypes.byref(sv)))
@@ -413,7 +415,8 @@ def dd_solvers_step(svs, ctx):
 def dd_solve_batch(ds, ctx, n_els, loads, mode: int = DD_SEARCH_EXACT_FP32, init_idx=None, max_iter: int = 100,
                    cg_rtol: float = 1e-12, cg_max_iter: int = 20000, certify: bool = True, f_d0: float = 0.0,
                    f_d_final: float = 0.0, ramp_iters: int = 20, seed: int = 0, stall_iters: int = 3,
-                   cg_mode: int = 0, allow_not_converged: bool = True, f_s: int = 0, ann_budget: int = 0):
+                   cg_mode: int = 0, allow_not_converged: bool = True, f_s: int = 0, ann_budget: int = 0,
+                   fd_rule: int = 0, fd_tau: float = 0.0):
     """Solve several cube problems together; n_els[i] edge elements, loads[i]."""
     n = len(n_els)
     meshes = (dd_mesh * n)(*[dd_mesh(k, k, k, 1.0, 1.0, 1.0) for k in n_els])
@@ -421,7 +424,7 @@ def dd_solve_batch(ds, ctx, n_els, loads, mode: int = DD_SEARCH_EXACT_FP32, init
                          for L in loads])
     _, _, opts, ii = _solve_args(n_els[0], loads[0], mode, init_idx, max_iter, cg_rtol, cg_max_iter, certify, f_d0,
                                  f_d_final, ramp_iters, seed, stall_iters, (1.0, 1.0, 1.0), cg_mode, f_s,
-                                 ann_budget)
+                                 ann_budget, fd_rule, fd_tau)
     outs = (dd_result * n)()
     st = lib().dd_solve_batch(ds, n, meshes, Ls, ctypes.byref(opts), outs)
     try:
@@ -436,10 +439,10 @@ def dd_solve_batch(ds, ctx, n_els, loads, mode: int = DD_SEARCH_EXACT_FP32, init
 def dd_server_start(ds, ctx, mode: int = DD_SEARCH_EXACT_FP32, state_budget: int = 0, max_batch: int = 0,
                     max_iter: int = 100, cg_rtol: float = 1e-12, cg_max_iter: int = 20000, certify: bool = True,
                     f_d0: float = 0.0, f_d_final: float = 0.0, ramp_iters: int = 20, stall_iters: int = 3,
-                    cg_mode: int = 0, f_s: int = 0, ann_budget: int = 0):
+                    cg_mode: int = 0, f_s: int = 0, ann_budget: int = 0, fd_rule: int = 0, fd_tau: float = 0.0):
     so = dd_solve_opts(int(mode), int(certify), float(f_d0), float(f_d_final), int(ramp_iters), int(max_iter),
                        float(cg_rtol), int(cg_max_iter), 0, None, int(stall_iters), int(cg_mode), int(f_s),
-                       int(ann_budget))
+                       int(ann_budget), int(fd_rule), float(fd_tau))
     o = dd_server_opts(so, int(state_budget), int(max_batch))
     srv = c_void_p()
     _check(ctx, lib().dd_server_start(ds, ctypes.byref(o), ctypes.byref(srv)))

@@ -867,17 +867,25 @@ __global__ void __launch_bounds__(kBThreads, 1) k_cg_batch(BCGArgs A) {
     if (leader) A.it_out[sidx] = inner_count;
 }
 
-__global__ void k_fill_f(float *p, int64_t n, float v) {
+// f_d of every query of a solve (Eq. 11): f_near where the distance after
+// P_C is at most thr, f_far elsewhere; the parameter comes from device memory
+// (a captured step reads this step's values) or by value
+__global__ void k_fill_fd(float *p, int64_t n, const FdParam *pd, FdParam hp, const double *dpc) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) p[i] = v;
-}
-
-__global__ void k_fill_fd(float *p, int64_t n, const float *v) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) p[i] = *v;
+    if (i >= n) return;
+    const FdParam v = pd ? *pd : hp;
+    p[i] = (v.thr >= 0.f && dpc[i] <= (double)v.thr) ? v.f_near : v.f_far;
 }
 
 }  // namespace
+
+dd_status dd_fill_fd(dd_ctx *ctx, float *p, int64_t n, const FdParam *pd, FdParam hp, const double *dpc,
+                     cudaStream_t s) {
+    ctx->launches++;
+    k_fill_fd<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, n, pd, hp, dpc);
+    DD_TRY_CUDA(ctx, cudaGetLastError());
+    return DD_OK;
+}
 
 // Tile shape for a level of a solve that gets nblk blocks: fewest estimated
 // cycles for the passes over its tiles (a halo round per 256 staged nodes,
@@ -1090,7 +1098,7 @@ struct StepIO {
     double *d2_cat = nullptr, *d2nd_cat = nullptr;
     float *fd_cat = nullptr;
     AnnMotion mot{nullptr, nullptr};
-    const float *fd_dev = nullptr;      // [n] f_d of every solve in device memory, or null (host values)
+    const FdParam *fd_dev = nullptr;    // [n] f_d parameters of every solve in device memory, or null (host values)
     double *h_stats = nullptr;          // [3 n] host copy of (changed, d2 after P_D, d2 after P_C)
     int *h_it = nullptr;                // [n] host copy of the CG iteration counts
     DeferredStats *defer_dev = nullptr, *h_defer = nullptr;
@@ -1125,7 +1133,7 @@ void concat_carve(StepIO &io, int64_t M, void *base) {
 // f_d = 1, never in a captured step): per-solve gather and RHS, ONE CG launch,
 // per-solve recovery, ONE search over the concatenated states, scatter,
 // per-solve statistics and their copy to the host buffers of io.
-dd_status enqueue_step(dd_solver **svs, int n, const StepIO &io, const std::vector<double> &fds,
+dd_status enqueue_step(dd_solver **svs, int n, const StepIO &io, const std::vector<FdParam> &fps,
                        dd_search_stats &sst, cudaStream_t s) {
     dd_ctx *ctx = svs[0]->ctx;
     dd_dataset *ds = svs[0]->ds;
@@ -1175,10 +1183,8 @@ dd_status enqueue_step(dd_solver **svs, int n, const StepIO &io, const std::vect
         }
         if (ann) {
             ctx->launches++;
-            if (io.fd_dev)
-                k_fill_fd<<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(io.fd_cat + off, ng, io.fd_dev + i);
-            else
-                k_fill_f<<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(io.fd_cat + off, ng, (float)fds[i]);
+            k_fill_fd<<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(io.fd_cat + off, ng,
+                                                                   io.fd_dev ? io.fd_dev + i : nullptr, fps[i], sv->dpc);
         }
         off += ng;
     }
@@ -1186,8 +1192,8 @@ dd_status enqueue_step(dd_solver **svs, int n, const StepIO &io, const std::vect
     AnnMotion mot = io.mot;
     if (ann) {
         if (!ds->ann.nlist) return dd_fail(ctx, DD_ERR_STATE, "ANN search needs the partition (ann_nlist)");
-        DD_TRY(dd_search_ann_motion(ds, io.y_cat, M, fds[0], io.fd_cat, io.prev_cat, &mot, o0.ann_budget, so, &sst,
-                                    s));
+        DD_TRY(dd_search_ann_motion(ds, io.y_cat, M, fps[0].f_far, io.fd_cat, io.prev_cat, &mot, o0.ann_budget, so,
+                                    &sst, s));
     } else if (o0.mode == DD_SEARCH_KNNG) {
         DD_TRY(dd_search_knng(ds, io.y_cat, M, o0.f_s, io.prev_cat, &mot, so, &sst, s));
     } else {
@@ -1274,7 +1280,7 @@ struct StepPlan {
     void *dev = nullptr;
     size_t dev_bytes = 0;
     void *pin = nullptr;
-    float *fd_host = nullptr;            // pinned [n]
+    FdParam *fd_host = nullptr;          // pinned [n]
     bool no_graph = false;               // capture failed once: run this list eagerly
     struct Variant {
         std::vector<char> parity;
@@ -1327,7 +1333,8 @@ static dd_status plan_make(dd_solver **svs, int n, int64_t M, StepPlan **out) {
         dd_status st = cg_tables(ctx, gs.data(), cbs.data(), n, P->cgt);
         if (st != DD_OK) return fail(st);
     }
-    const size_t b_cg = cg_seg ? r256(cg_dev_bytes(P->cgt)) : 0, b_cat = concat_bytes(M), b_fd = r256((size_t)n * 4),
+    const size_t b_cg = cg_seg ? r256(cg_dev_bytes(P->cgt)) : 0, b_cat = concat_bytes(M),
+                 b_fd = r256((size_t)n * sizeof(FdParam)),
                  b_def = r256(sizeof(DeferredStats));
     P->dev_bytes = b_cg + b_cat + b_fd + b_def;
     dd_status st = dd_alloc(ctx, &P->dev, P->dev_bytes, "batched step plan");
@@ -1342,10 +1349,10 @@ static dd_status plan_make(dd_solver **svs, int n, int64_t M, StepPlan **out) {
         P->io.cgd = &P->cgd;
     }
     concat_carve(P->io, M, c + b_cg);
-    float *fd_dev = (float *)(c + b_cg + b_cat);
+    FdParam *fd_dev = (FdParam *)(c + b_cg + b_cat);
     P->io.fd_dev = fd_dev;
     P->io.defer_dev = (DeferredStats *)(c + b_cg + b_cat + b_fd);
-    const size_t h_stats = r256((size_t)n * 24), h_it = r256((size_t)n * 4), h_fd = r256((size_t)n * 4);
+    const size_t h_stats = r256((size_t)n * 24), h_it = r256((size_t)n * 4), h_fd = r256((size_t)n * sizeof(FdParam));
     if (cudaHostAlloc(&P->pin, h_stats + h_it + h_fd + r256(sizeof(DeferredStats)), cudaHostAllocDefault) !=
         cudaSuccess) {
         P->pin = nullptr;
@@ -1354,7 +1361,7 @@ static dd_status plan_make(dd_solver **svs, int n, int64_t M, StepPlan **out) {
     char *h = (char *)P->pin;
     P->io.h_stats = (double *)h;
     P->io.h_it = (int *)(h + h_stats);
-    P->fd_host = (float *)(h + h_stats + h_it);
+    P->fd_host = (FdParam *)(h + h_stats + h_it);
     P->io.h_defer = (DeferredStats *)(h + h_stats + h_it + h_fd);
     cudaStream_t s = ctx->stream;
     if ((cg_seg && (st = cg_upload(ctx, P->cgt, P->cgd, s)) != DD_OK)) return fail(st);
@@ -1373,7 +1380,7 @@ static dd_status plan_make(dd_solver **svs, int n, int64_t M, StepPlan **out) {
 // Capture the step into a graph for the current parity; null when capture is
 // not possible (the caller then runs the step eagerly).
 static StepPlan::Variant *plan_capture(StepPlan *P, dd_solver **svs, int n, const std::vector<char> &par,
-                                       const std::vector<double> &fds) {
+                                       const std::vector<FdParam> &fps) {
     dd_ctx *ctx = svs[0]->ctx;
     cudaStream_t s = ctx->stream;
     StepPlan::Variant v;
@@ -1387,7 +1394,7 @@ static StepPlan::Variant *plan_capture(StepPlan *P, dd_solver **svs, int n, cons
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
     dd_status st = DD_OK;
     if (e == cudaSuccess) {
-        st = enqueue_step(svs, n, P->io, fds, v.sst, s);
+        st = enqueue_step(svs, n, P->io, fps, v.sst, s);
         const cudaError_t e2 = cudaStreamEndCapture(s, &g);
         if (e == cudaSuccess) e = e2;
     }
@@ -1430,12 +1437,14 @@ extern "C" dd_status dd_solvers_step(dd_solver **svs, int n, dd_iter_info *infos
     cudaStream_t s = ctx->stream;
     const bool ann = o0.mode == DD_SEARCH_ANN;
     std::vector<double> fds(n);
+    std::vector<FdParam> fps(n);
     bool full_fd = false;   // f_d = 1 may need an exact re-search sized on the host
     std::vector<uint64_t> ids(n);
     for (int i = 0; i < n; ++i) {
         ++svs[i]->it;
-        fds[i] = dd_solver_fd(svs[i], svs[i]->it);
-        full_fd |= ann && fds[i] >= 1.0;
+        fps[i] = dd_solver_fd_param(svs[i], svs[i]->it);
+        fds[i] = fps[i].f_far;
+        full_fd |= ann && (fps[i].f_far >= 1.0f || (fps[i].thr >= 0.f && fps[i].f_near >= 1.0f));
         ids[i] = svs[i]->id;
     }
     // ---- the same list as the previous step: replay its captured graph ----
@@ -1467,11 +1476,11 @@ extern "C" dd_status dd_solvers_step(dd_solver **svs, int n, dd_iter_info *infos
                 }
                 break;
             }
-        for (int i = 0; i < n; ++i) P->fd_host[i] = (float)fds[i];
-        if (!v) v = plan_capture(P, svs, n, par, fds);
+        for (int i = 0; i < n; ++i) P->fd_host[i] = fps[i];
+        if (!v) v = plan_capture(P, svs, n, par, fps);
         if (v) {
             // this step's f_d values, read by the graph's fill kernels
-            DD_TRY_CUDA(ctx, cudaMemcpyAsync((void *)P->io.fd_dev, P->fd_host, n * sizeof(float),
+            DD_TRY_CUDA(ctx, cudaMemcpyAsync((void *)P->io.fd_dev, P->fd_host, n * sizeof(FdParam),
                                              cudaMemcpyHostToDevice, s));
             ctx->launches += v->launches;
             DD_TRY_CUDA(ctx, cudaGraphLaunch(v->exec, s));
@@ -1492,7 +1501,7 @@ extern "C" dd_status dd_solvers_step(dd_solver **svs, int n, dd_iter_info *infos
     io.h_it = its.data();
     dd_search_stats sst;
     std::memset(&sst, 0, sizeof(sst));
-    DD_TRY(enqueue_step(svs, n, io, fds, sst, s));
+    DD_TRY(enqueue_step(svs, n, io, fps, sst, s));
     DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
     DD_TRY(dd_check_device_error(ctx, s, "dd_solvers_step"));
     finish_step(svs, n, hs.data(), its.data(), sst, fds, nullptr, false, infos);

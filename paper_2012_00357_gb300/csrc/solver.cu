@@ -98,16 +98,35 @@ size_t carve(dd_solver *sv, char *base) {
     sv->stats = bp.take<double>(kIterStatsDoubles);
     sv->mot.q = bp.take<float>(ng * 12);
     sv->mot.d = bp.take<float>(ng * 2);
+    sv->fdq = bp.take<float>(ng);
     return bp.off;
 }
 
 }  // namespace
 
+// f_d after k steps of the ramp from f_d0 to f_d_final in ramp_iters steps
+static double ramp_fd(const dd_solve_opts &o, int k) {
+    if (o.ramp_iters <= 0) return o.f_d_final;
+    return o.f_d0 + (o.f_d_final - o.f_d0) * std::min(1.0, (double)k / (double)o.ramp_iters);
+}
+
 double dd_solver_fd(const dd_solver *sv, int it) {
     const dd_solve_opts &o = sv->o;
-    if (o.mode == DD_SEARCH_ANN && o.ramp_iters > 0)
-        return o.f_d0 + (o.f_d_final - o.f_d0) * std::min(1.0, (double)(it - 1) / (double)o.ramp_iters);
-    return o.f_d_final;
+    if (o.mode != DD_SEARCH_ANN) return o.f_d_final;
+    // the ramp takes one step per iteration; the global rule one per stalled iteration
+    return ramp_fd(o, o.fd_rule == 1 ? sv->fd_steps : it - 1);
+}
+
+FdParam dd_solver_fd_param(const dd_solver *sv, int it) {
+    const dd_solve_opts &o = sv->o;
+    const float f = (float)dd_solver_fd(sv, it);
+    FdParam p{f, f, -1.f, 0.f};
+    if (o.mode == DD_SEARCH_ANN && o.fd_rule == 2 && !sv->h_pc.empty()) {
+        // Eq. (11) with the local distance: near points at full accuracy
+        p.f_near = (float)o.f_d_final;
+        p.thr = (float)(o.fd_tau * sv->h_pc.back() / (double)sv->g.n_gp);
+    }
+    return p;
 }
 
 bool dd_solver_account(dd_solver *sv, const double hs[3], int cg_it, float cg_ms, float other_ms, float search_ms,
@@ -126,7 +145,14 @@ bool dd_solver_account(dd_solver *sv, const double hs[3], int cg_it, float cg_ms
     bool stop = false;
     // an approximate search is still tightening while f_d ramps up: its stop
     // tests apply once f_d has reached its final value
-    const bool settled = o.mode != DD_SEARCH_ANN || o.ramp_iters <= 0 || it > o.ramp_iters;
+    const int steps = o.fd_rule == 1 ? sv->fd_steps : it - 1;   // ramp steps behind this iteration's f_d
+    const bool settled = o.mode != DD_SEARCH_ANN || o.ramp_iters <= 0 || steps >= o.ramp_iters;
+    if (o.mode == DD_SEARCH_ANN && o.fd_rule == 1) {
+        // Eq. (11) with the global distance: one more ramp step after an
+        // iteration in which P_D gained less than the fraction fd_tau
+        const double gain = hs[2] > 0.0 ? 1.0 - hs[1] / hs[2] : 0.0;
+        if (gain < o.fd_tau && sv->fd_steps < o.ramp_iters) ++sv->fd_steps;
+    }
     if (hs[0] == 0.0 && settled) {
         sv->converged = true;
         stop = true;   // nxt == cur: the state was computed from the final association
@@ -199,6 +225,8 @@ extern "C" dd_status dd_solver_create(dd_dataset *ds, const dd_mesh *mesh, const
     if (o.cg_mode < 0 || o.cg_mode > 1) return dd_fail(ctx, DD_ERR_ARG, "dd_solver_create: unknown cg_mode");
     if (o.mode == DD_SEARCH_ANN && !(o.f_d0 >= 0 && o.f_d0 <= 1 && o.f_d_final >= 0 && o.f_d_final <= 1))
         return dd_fail(ctx, DD_ERR_ARG, "dd_solver_create: f_d outside [0, 1]");
+    if (o.fd_rule < 0 || o.fd_rule > 2 || !(o.fd_tau >= 0.0))
+        return dd_fail(ctx, DD_ERR_ARG, "dd_solver_create: unknown fd_rule or fd_tau < 0");
     for (int c = 0; c < 3; ++c)
         if (!std::isfinite(load->t0[c]) || !std::isfinite(load->tx[c]) || !std::isfinite(load->ty[c]))
             return dd_fail(ctx, DD_ERR_ARG, "dd_solver_create: non-finite load");
@@ -305,13 +333,19 @@ extern "C" dd_status dd_solver_step(dd_solver *sv, dd_iter_info *info) {
     DD_TRY_CUDA(ctx, cudaEventRecord(sv->ev[1], s));
     DD_TRY(fem_recover(ds, g, sv->ops, sv->cb.x, sv->star, sv->y, sv->dpc, s));
     DD_TRY_CUDA(ctx, cudaEventRecord(sv->ev[2], s));
-    const double f_d = dd_solver_fd(sv, it);
+    const FdParam fp = dd_solver_fd_param(sv, it);
+    const double f_d = fp.f_far;
     SearchOut so{sv->nxt, sv->d2, sv->d2nd};
     dd_search_stats sst;
     std::memset(&sst, 0, sizeof(sst));
     if (o.mode == DD_SEARCH_ANN) {
         if (!ds->ann.nlist) return dd_fail(ctx, DD_ERR_STATE, "ANN search needs the partition (ann_nlist)");
-        DD_TRY(dd_search_ann_motion(ds, sv->y, ng, f_d, nullptr, sv->cur, &sv->mot, o.ann_budget, so, &sst, s));
+        const float *fdq = nullptr;
+        if (fp.thr >= 0.f) {
+            DD_TRY(dd_fill_fd(ctx, sv->fdq, ng, nullptr, fp, sv->dpc, s));
+            fdq = sv->fdq;
+        }
+        DD_TRY(dd_search_ann_motion(ds, sv->y, ng, f_d, fdq, sv->cur, &sv->mot, o.ann_budget, so, &sst, s));
     } else if (o.mode == DD_SEARCH_KNNG) {
         DD_TRY(dd_search_knng(ds, sv->y, ng, o.f_s, sv->cur, &sv->mot, so, &sst, s));
     } else {

@@ -29,6 +29,8 @@ struct dd_solver {
     bool converged = false, done = false;
     int stall = 0;
     double best_pd = INFINITY;
+    int fd_steps = 0;                   // ramp steps taken by the global-distance rule (fd_rule 1)
+    float *fdq = nullptr;               // [n_gp] per-point f_d (fd_rule 2)
     std::vector<double> h_pc, h_pd;
     std::vector<int64_t> h_ch;
     std::vector<int> h_cg;
@@ -41,3 +43,15 @@ struct dd_solver {
 bool dd_solver_account(dd_solver *sv, const double hs[3], int cg_it, float cg_ms, float other_ms, float search_ms,
                        const dd_search_stats &sst, double f_d, dd_iter_info *info);
 double dd_solver_fd(const dd_solver *sv, int it);
+
+// f_d of the queries of one solve in one iteration: f_near for a point whose
+// distance after P_C (dpc) is at most thr, f_far for the others (thr < 0:
+// f_far for all).
+struct FdParam {
+    float f_far, f_near, thr, pad;
+};
+FdParam dd_solver_fd_param(const dd_solver *sv, int it);
+// p[e] = f_d of point e from the parameter in device memory (pd) or, when pd
+// is null, from hp.
+dd_status dd_fill_fd(dd_ctx *ctx, float *p, int64_t n, const FdParam *pd, FdParam hp, const double *dpc,
+                     cudaStream_t s);
