@@ -334,6 +334,8 @@ WORKLOADS = {
     # the 32^3 constraint projection with a small data set
     "cube16_N3e7_ann": Workload("cube16_N3e7_ann", 16, 30_000_000, NONLINEAR),
     "cube32_N3e7_ann": Workload("cube32_N3e7_ann", 32, 30_000_000, NONLINEAR),
+    "cube32_N1e7_knng": Workload("cube32_N1e7_knng", 32, 10_000_000, NONLINEAR,
+                                 extra={"knn_k": 128, "knn_fd": 0.8, "f_s": 2}),
     # the greedy walk in the k-NN graph (Sec. 4.4) on the 10^8-point data set
     "cube32_N1e8_knng": Workload("cube32_N1e8_knng", 32, 100_000_000, NONLINEAR,
                                  extra={"knn_k": 128, "knn_fd": 0.8, "f_s": 2}),

@@ -250,7 +250,7 @@ def dd_project_nearest(ds, ctx, y, idx, d2=None, mode: int = DD_SEARCH_EXACT_FP3
                        f_d: float = 0.0, prev_idx=None, stream=None, want_stats: bool = True, f_s: int = 0,
                        ann_budget: int = 0):
     m = int(y.shape[0])
-    opts = dd_search_opts(int(mode), int(certify), float(f_d), _ptr(prev_idx), stream, int(f_s), int(ann_budget), int(fd_rule), float(fd_tau))
+    opts = dd_search_opts(int(mode), int(certify), float(f_d), _ptr(prev_idx), stream, int(f_s), int(ann_budget))
     st = dd_search_stats()
     _check(ctx, lib().dd_project_nearest(ds, _ptr(y), m, ctypes.byref(opts), _ptr(idx), _ptr(d2),
                                          ctypes.byref(st) if want_stats else None))

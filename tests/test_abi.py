@@ -54,3 +54,29 @@ def test_no_cuda_device_is_reported_not_crashed(libdd):
     with pytest.raises(P.DDError) as e:
         P.dd_create(0)
     assert e.value.status == P.DD_ERR_CUDA
+
+
+def test_binding_functions_use_only_defined_names():
+    """Every name a function of the binding reads is a parameter, a local, a
+    module-level name or a builtin (the GPU calls cannot run here, so a
+    misspelt argument would otherwise go unnoticed)."""
+    import ast
+    import builtins
+    import os
+    src = open(os.path.join(os.path.dirname(__file__), "..", "paper_2012_00357_gb300", "binding.py")).read()
+    tree = ast.parse(src)
+    glob = {n.id for n in ast.walk(tree) if isinstance(n, ast.Name) and isinstance(n.ctx, ast.Store)}
+    glob |= {f.name for f in tree.body if isinstance(f, (ast.FunctionDef, ast.ClassDef))}
+    for node in tree.body:
+        if isinstance(node, (ast.Import, ast.ImportFrom)):
+            glob |= {(a.asname or a.name).split(".")[0] for a in node.names}
+    bad = []
+    for f in [n for n in ast.walk(tree) if isinstance(n, ast.FunctionDef)]:
+        known = {a.arg for a in f.args.args + f.args.kwonlyargs}
+        known |= {n.id for n in ast.walk(f) if isinstance(n, ast.Name) and isinstance(n.ctx, ast.Store)}
+        known |= {a.arg for n in ast.walk(f) if isinstance(n, ast.Lambda) for a in n.args.args}
+        for n in ast.walk(f):
+            if isinstance(n, ast.Name) and isinstance(n.ctx, ast.Load) and n.id not in known | glob \
+                    and not hasattr(builtins, n.id):
+                bad.append((f.name, n.id))
+    assert not bad
