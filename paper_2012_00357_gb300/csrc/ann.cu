@@ -818,6 +818,7 @@ __global__ void __launch_bounds__(256) k_ann_probe2(Probe2Args P) {
 // lane per query, reading each point of the leaf once for all of them.
 // ---------------------------------------------------------------------------
 constexpr int kScanBlock = 1024;   // leaves per block of the count scans
+constexpr int kLeafChunk = 64;     // queries of a leaf per warp of the leaf-major scan
 
 // Inclusive block scan of 1024 values (256 threads x 4); returns the
 // exclusive prefix of this thread's first value, the block total in *tot.
@@ -846,7 +847,7 @@ __device__ __forceinline__ unsigned block_scan4(unsigned (&v)[4], unsigned *sh, 
     return before;
 }
 
-// per block of 1024 leaves: totals of queries and of 32-query chunks
+// per block of 1024 leaves: totals of queries and of kLeafChunk-query chunks
 __global__ void __launch_bounds__(256) k_leaf_sums(const unsigned *__restrict__ cnt, int L,
                                                     unsigned *__restrict__ bsum, unsigned *__restrict__ bitem) {
     __shared__ unsigned sh[8];
@@ -855,7 +856,7 @@ __global__ void __launch_bounds__(256) k_leaf_sums(const unsigned *__restrict__ 
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         a[k] = base + k < L ? cnt[base + k] : 0u;
-        c[k] = (a[k] + 31u) >> 5;
+        c[k] = (a[k] + (unsigned)kLeafChunk - 1u) / (unsigned)kLeafChunk;
     }
     block_scan4(a, sh, &ta);
     block_scan4(c, sh, &tc);
@@ -898,7 +899,7 @@ __global__ void __launch_bounds__(256) k_leaf_offsets(const unsigned *__restrict
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         a[k] = base + k < L ? cnt[base + k] : 0u;
-        c[k] = (a[k] + 31u) >> 5;
+        c[k] = (a[k] + (unsigned)kLeafChunk - 1u) / (unsigned)kLeafChunk;
     }
     unsigned ra = block_scan4(a, sh, &ta) + bsum[blockIdx.x];
     unsigned rc = block_scan4(c, sh, &tc) + bitem[blockIdx.x];
@@ -948,6 +949,24 @@ struct LeafScanArgs {
     unsigned *touched;
 };
 
+// best and second best of the points [p0, p1) for one query
+struct LeafBest {
+    float b1 = INFINITY, b2 = INFINITY;
+    int j1 = 0x7fffffff;
+    __device__ __forceinline__ void offer(float d, int p) {
+        if (d < b1) {
+            b2 = b1;
+            b1 = d;
+            j1 = p;
+        } else {
+            b2 = fminf(b2, d);
+        }
+    }
+};
+
+// One warp per chunk of up to 64 queries of a leaf: lane l takes queries l
+// and l + 32, so every point read serves two distances (the scan is bound by
+// the L1 reads of the points, one broadcast read per point and warp).
 __global__ void __launch_bounds__(256) k_leaf_scan(LeafScanArgs A) {
     __shared__ unsigned long long sc;
     if (threadIdx.x == 0) sc = 0ull;
@@ -964,47 +983,53 @@ __global__ void __launch_bounds__(256) k_leaf_scan(LeafScanArgs A) {
             else hi = mid;
         }
         const int l = lo;
-        const unsigned q0 = A.pair_off[l] + 32u * (it - A.item_off[l]);
-        const unsigned qn = min(32u, A.pair_off[l + 1] - q0);
-        const bool act = (unsigned)lane < qn;
-        const unsigned slot = act ? A.bucket[q0 + lane] : 0u;
-        float q[12];
-        const QueryRec *r = A.rec + (act ? slot / kPairMax : 0);
+        const unsigned q0 = A.pair_off[l] + (unsigned)kLeafChunk * (it - A.item_off[l]);
+        const unsigned qn = min((unsigned)kLeafChunk, A.pair_off[l + 1] - q0);
+        const bool act0 = (unsigned)lane < qn, act1 = (unsigned)lane + 32u < qn;
+        const bool two = qn > 32u;                      // warp-uniform
+        const unsigned s0 = act0 ? A.bucket[q0 + lane] : 0u, s1 = act1 ? A.bucket[q0 + 32 + lane] : 0u;
+        float qa[12], qb[12];
+        const QueryRec *ra = A.rec + (act0 ? s0 / kPairMax : 0), *rb = A.rec + (act1 ? s1 / kPairMax : 0);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) q[k] = r->q[k];
+        for (int k = 0; k < 12; ++k) {
+            qa[k] = ra->q[k];
+            qb[k] = rb->q[k];
+        }
         const int64_t p0 = A.offs[l], p1 = A.offs[l + 1];
-        float b1 = INFINITY, b2 = INFINITY;
-        int j1 = 0x7fffffff;
-        int64_t p = p0;
-        for (; p + 3 < p1; p += 4) {
-            float d[4];
+        const float *zp = A.zs + p0 * 12;
+        const int n = (int)(p1 - p0);
+        LeafBest ba, bb;
+        if (two) {
+            for (int t = 0; t < n; ++t) {
+                const float4 *v = reinterpret_cast<const float4 *>(zp + (size_t)t * 12);
+                const float4 u0 = __ldg(v), u1 = __ldg(v + 1), u2 = __ldg(v + 2);
+                const float x[12] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w, u2.x, u2.y, u2.z, u2.w};
+                float da = 0.f, db = 0.f;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) d[u] = dist2_12(A.zs + (p + u) * 12, q);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (d[u] < b1) {
-                    b2 = b1;
-                    b1 = d[u];
-                    j1 = (int)(p + u);
-                } else {
-                    b2 = fminf(b2, d[u]);
+                for (int k = 0; k < 12; ++k) {
+                    const float ta = x[k] - qa[k], tb = x[k] - qb[k];
+                    da = fmaf(ta, ta, da);
+                    db = fmaf(tb, tb, db);
                 }
+                ba.offer(da, (int)p0 + t);
+                bb.offer(db, (int)p0 + t);
             }
-        }
-        for (; p < p1; ++p) {
-            const float d = dist2_12(A.zs + p * 12, q);
-            if (d < b1) {
-                b2 = b1;
-                b1 = d;
-                j1 = (int)p;
-            } else {
-                b2 = fminf(b2, d);
+        } else {
+            int t = 0;
+            for (; t + 3 < n; t += 4) {
+                float d[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) d[u] = dist2_12(zp + (size_t)(t + u) * 12, qa);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) ba.offer(d[u], (int)p0 + t + u);
             }
+            for (; t < n; ++t) ba.offer(dist2_12(zp + (size_t)t * 12, qa), (int)p0 + t);
         }
-        if (act) A.res[slot] = PairRes{b1, j1, b2};
+        if (act0) A.res[s0] = PairRes{ba.b1, ba.j1, ba.b2};
+        if (act1) A.res[s1] = PairRes{bb.b1, bb.j1, bb.b2};
         if (lane == 0) {
             atomicOr(A.touched + (l >> 5), 1u << (l & 31));
-            atomicAdd(&sc, (unsigned long long)qn * (unsigned long long)(p1 - p0));
+            atomicAdd(&sc, (unsigned long long)qn * (unsigned long long)n);
         }
     }
     __syncthreads();

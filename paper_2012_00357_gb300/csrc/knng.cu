@@ -288,6 +288,7 @@ struct WalkArgs {
                                     // [7] walks stopped by f_s
 };
 
+template <int NC>
 __device__ __forceinline__ void walk_one(const WalkArgs &A, int64_t i, int lane, unsigned long long *sc) {
     float q[12];
 #pragma unroll
@@ -333,41 +334,49 @@ __device__ __forceinline__ void walk_one(const WalkArgs &A, int64_t i, int lane,
             bounded = true;
             break;
         }
-        // nearest neighbour over chunks of 32 (ties to the lower data index),
-        // and the smallest distance among the others
-        float bd = INFINITY, od = INFINITY;
-        int bt = -1;
-        for (int c0 = 0; c0 < A.k; c0 += 32) {
-            const int t = c0 + lane < A.k ? A.nbr[(size_t)p * A.k + c0 + lane] : -1;
-            const float d = t >= 0 ? dist2_12(A.zs + (size_t)t * 12, q) : INFINITY;
-            ev += (unsigned long long)__popc(__ballot_sync(kFull, t >= 0));
-            float cd = d;
-            for (int o = 16; o > 0; o >>= 1) cd = fminf(cd, __shfl_xor_sync(kFull, cd, o));
-            const bool at_min = t >= 0 && d == cd;
-            const unsigned tie = __ballot_sync(kFull, at_min);
-            int ct = -1;
-            if (__popc(tie) == 1) {
-                ct = __shfl_sync(kFull, t, __ffs(tie) - 1);
-            } else if (tie) {
-                const int j = at_min ? A.perm[t] : INT_MAX;
-                int jb = j;
-                for (int o = 16; o > 0; o >>= 1) jb = min(jb, __shfl_xor_sync(kFull, jb, o));
-                const unsigned w = __ballot_sync(kFull, at_min && j == jb);
-                ct = __shfl_sync(kFull, t, __ffs(w) - 1);
-            }
-            float co = (t == ct) ? INFINITY : d;
-            for (int o = 16; o > 0; o >>= 1) co = fminf(co, __shfl_xor_sync(kFull, co, o));
-            if (ct < 0) continue;
-            bool better = cd < bd;
-            if (cd == bd && bt >= 0) better = A.perm[ct] < A.perm[bt];
+        // every lane takes up to NC neighbours (all loads issued before any
+        // reduction); nearest one (ties to the lower data index) and the
+        // smallest distance among the others
+        int t[NC];
+        float d[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) t[c] = 32 * c + lane < A.k ? A.nbr[(size_t)p * A.k + 32 * c + lane] : -1;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) d[c] = t[c] >= 0 ? dist2_12(A.zs + (size_t)t[c] * 12, q) : INFINITY;
+        float ld = INFINITY, ls = INFINITY;      // lane's nearest and the lane's other minimum
+        int lt = -1, nv = 0;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            if (t[c] < 0) continue;
+            ++nv;
+            bool better = d[c] < ld;
+            if (d[c] == ld && lt >= 0) better = A.perm[t[c]] < A.perm[lt];
             if (better) {
-                od = fminf(od, fminf(bd, co));
-                bd = cd;
-                bt = ct;
+                ls = fminf(ls, ld);
+                ld = d[c];
+                lt = t[c];
             } else {
-                od = fminf(od, fminf(cd, co));
+                ls = fminf(ls, d[c]);
             }
         }
+        for (int o = 16; o > 0; o >>= 1) nv += __shfl_xor_sync(kFull, nv, o);
+        ev += (unsigned long long)nv;
+        float bd = ld;
+        for (int o = 16; o > 0; o >>= 1) bd = fminf(bd, __shfl_xor_sync(kFull, bd, o));
+        const bool at_min = lt >= 0 && ld == bd;
+        const unsigned tie = __ballot_sync(kFull, at_min);
+        int bt = -1, wl = -1;
+        if (__popc(tie) == 1) {
+            wl = __ffs(tie) - 1;
+        } else if (tie) {
+            const int j = at_min ? A.perm[lt] : INT_MAX;
+            int jb = j;
+            for (int o = 16; o > 0; o >>= 1) jb = min(jb, __shfl_xor_sync(kFull, jb, o));
+            wl = __ffs(__ballot_sync(kFull, at_min && j == jb)) - 1;
+        }
+        if (wl >= 0) bt = __shfl_sync(kFull, lt, wl);
+        float od = lane == wl ? ls : fminf(ld, ls);
+        for (int o = 16; o > 0; o >>= 1) od = fminf(od, __shfl_xor_sync(kFull, od, o));
         if (bt >= 0 && bd < dcur) {
             second = fminf(second, fminf(dcur, od));
             dcur = bd;
@@ -390,12 +399,13 @@ __device__ __forceinline__ void walk_one(const WalkArgs &A, int64_t i, int lane,
     }
 }
 
+template <int NC>
 __global__ void __launch_bounds__(256) k_knng_walk(WalkArgs A) {
     __shared__ unsigned long long sc[4];
     if (threadIdx.x < 4) sc[threadIdx.x] = 0ull;
     __syncthreads();
     const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (i < A.m) walk_one(A, i, threadIdx.x & 31, sc);
+    if (i < A.m) walk_one<NC>(A, i, threadIdx.x & 31, sc);
     __syncthreads();
     if (threadIdx.x == 0) {
         if (sc[0]) {
@@ -494,7 +504,11 @@ dd_status dd_search_knng(dd_dataset *ds, const double *y_dev, int64_t m, int f_s
     WalkArgs A{ds->ann.zs, ds->ann.perm, g.pos_of, g.nbr, g.k, ds->z32, rec, m, ds->N, f_s, prev_idx_dev,
                mot ? mot->q : nullptr, mot ? mot->d : nullptr, out.idx, d1f, d2f, counters};
     ctx->launches++;
-    k_knng_walk<<<(unsigned)((m * 32 + 255) / 256), 256, 0, s>>>(A);
+    const unsigned grid = (unsigned)((m * 32 + 255) / 256);
+    if (g.k <= 32) k_knng_walk<1><<<grid, 256, 0, s>>>(A);
+    else if (g.k <= 64) k_knng_walk<2><<<grid, 256, 0, s>>>(A);
+    else if (g.k <= 96) k_knng_walk<3><<<grid, 256, 0, s>>>(A);
+    else k_knng_walk<4><<<grid, 256, 0, s>>>(A);
     DD_TRY_CUDA(ctx, cudaGetLastError());
     if (st) DD_TRY_CUDA(ctx, dd_event_record(ctx, ctx->ev_scan[1], s));
     DD_TRY(dd_ann_finish(ds, y_dev, m, out.idx, d2f, out.d2, out.d2nd, s));
