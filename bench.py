@@ -197,7 +197,9 @@ def run_ours(args, world, rank, local):
         C = P.dd_pca_metric(ctx, raw)          # the data-derived metric of Sec. 3.1
     levels = args.ann_levels or (2 if W.N >= 300_000_000 or mode == P.DD_SEARCH_KNNG else 1)
     if approx and levels == 2 and not args.nlist:
-        nlist = 1 << 20 if W.N >= 300_000_000 else 1 << 17
+        # 2^24 asks for the finest tree the search handles, 4096 cells of 512
+        # leaves (about 480 points per leaf at 10^9 points)
+        nlist = 1 << 24 if W.N >= 300_000_000 else 1 << 17
     knn = dict(knn_k=args.knn_k, knn_fd=args.knn_fd) if mode == P.DD_SEARCH_KNNG else {}
     ds = P.dd_load_dataset(ctx, raw, C, borrow=True, build_fp16=(mode == P.DD_SEARCH_EXACT_TC), ann_nlist=nlist,
                            seed=1, ann_levels=levels, **knn)

@@ -26,7 +26,9 @@ def big():
     ctx = P.dd_create(0)
     raw = torch.empty((W.N, 12), dtype=torch.float32, device="cuda")
     P.dd_synth_dataset(ctx, raw, W.law, C, seed=W.seed)
-    ds = P.dd_load_dataset(ctx, raw, C, borrow=True, build_fp16=True, ann_nlist=1 << 15, ann_levels=2, seed=1)
+    # 512 cells of 512 leaves, about 380 points per leaf (the benchmark's
+    # leaf size at 10^9 points)
+    ds = P.dd_load_dataset(ctx, raw, C, borrow=True, build_fp16=True, ann_nlist=1 << 18, ann_levels=2, seed=1)
     y = I.make_states(W.m, W.law, seed=41, spread=0.02)
     sample = np.random.default_rng(4).choice(W.m, 12, replace=False)
     oi, od = nn.nn_stream(W.law, W.seed, W.N, C, metric.to_z(y[sample], C))
@@ -130,7 +132,7 @@ def test_paper_problem_ann_within_1e3_of_exact():
     raw = torch.empty((Wr.N, 12), dtype=torch.float32, device="cuda")
     P.dd_synth_dataset(ctx, raw, Wr.law, I.isotropic_C(Wr.law.E, Wr.law.nu), seed=Wr.seed)
     Cp = P.dd_pca_metric(ctx, raw)          # the data-derived metric of Sec. 3.1
-    ds = P.dd_load_dataset(ctx, raw, Cp, borrow=True, build_fp16=True, ann_nlist=1 << 15, ann_levels=2, seed=1)
+    ds = P.dd_load_dataset(ctx, raw, Cp, borrow=True, build_fp16=True, ann_nlist=1 << 18, ann_levels=2, seed=1)
     try:
         L = I.load_case(*Wr.loads[0])
         init = I.initial_association(Wr.m, Wr.N, seed=Wr.seed)
