@@ -40,6 +40,10 @@ L2_BYTES = 129 * 2 ** 20
 # reports null until it is captured again.
 TRAFFIC = {
     # (workload, mode): (source file under the package's csrc/, sha256, bytes per launch)
+    # k_rank_small + k_ann_probe2 + k_leaf_scan of one search, mean of the 10
+    # timed steps (profiles/launches_cube32_N1e9_ann_4loads.md)
+    ("cube32_N1e9_ann_4loads", "ann"): ("ann.cu", "67cee421f41430ee7470bd50c61a0731bbab06e8d53a97bc95aa919d0d7bc547",
+                                       3781206656),
 }
 
 
