@@ -515,8 +515,12 @@ def run_reference(args, world, rank):
     v = statistics.mean(vals)
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (dd_inputs)", "config": {"workload": W.name, "material_points": W.m,
-                                                        "data_points": W.N},
+            "data": "synthetic (dd_inputs)",
+            "config": {"workload": W.name, "mesh": f"{W.n_el}^3 hex, 2x2x2 Gauss",
+                       "material_points": W.m * max(1, len(W.loads)), "data_points": W.N, "law": W.law.kind,
+                       "metric": W.extra.get("metric", "isotropic C of the law"), "load": W.loads[0][0],
+                       "search": "exact FP64 brute force (the oracle) on a bounded query sample",
+                       "parallelism": "host cores of rank 0"},
             "cpu_baseline": {**info, "value": v},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
