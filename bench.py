@@ -8,7 +8,11 @@ timed steps (whole job, all ranks).  Under torchrun every rank runs an
 independent replica (the search does not shard).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload NAME] [--mode tc|fp32|tc_topk]
+                    [--workload NAME] [--mode tc|tc_topk|fp32|ann|knng|serve]
+
+The default workload is the 32^3 cube with 4 load cases on 10^9 points with
+the approximate tree search; the workloads are listed in dd_inputs.WORKLOADS
+(the mode follows from the name unless given).
 """
 from __future__ import annotations
 
@@ -205,7 +209,11 @@ def run_ours(args, world, rank, local):
         # leaves (about 480 points per leaf at 10^9 points)
         nlist = 1 << 24 if W.N >= 300_000_000 else 1 << 17
     knn = dict(knn_k=args.knn_k, knn_fd=args.knn_fd) if mode == P.DD_SEARCH_KNNG else {}
-    ds = P.dd_load_dataset(ctx, raw, C, borrow=True, build_fp16=(mode == P.DD_SEARCH_EXACT_TC), ann_nlist=nlist,
+    # the approximate modes also get the FP16 operands when the check below
+    # times the certified tensor-core exact search on the same data set
+    exact_tc = approx and args.ann_check > 0 and args.exact_tc
+    ds = P.dd_load_dataset(ctx, raw, C, borrow=True, build_fp16=(mode == P.DD_SEARCH_EXACT_TC or exact_tc),
+                           ann_nlist=nlist,
                            seed=1, ann_levels=levels, **knn)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t_build
@@ -292,7 +300,8 @@ def run_ours(args, world, rank, local):
     accuracy = None
     if approx and args.ann_check > 0:
         # agreement of the approximate answers with the certified exact search
-        # on a sample of the final states (FP32 scan + FP64 rescoring)
+        # on a sample of the final states (tensor-core scan, or the FP32 scan,
+        # + FP64 rescoring), and the exact search's rate on that sample
         ys = np.concatenate([np.concatenate([rr.eps, rr.sig], axis=1) for rr in rs])
         pick = np.random.default_rng(0).choice(len(ys), min(args.ann_check, len(ys)), replace=False)
         ysel = np.ascontiguousarray(ys[pick])
@@ -303,14 +312,17 @@ def run_ours(args, world, rank, local):
         de = np.empty(len(pick))
         P.dd_project_nearest(ds, ctx, ysel, ia, da, mode=mode, f_d=args.fd_final, prev_idx=prev, f_s=args.f_s,
                              ann_budget=args.ann_budget)
+        exact_mode = P.DD_SEARCH_EXACT_TC if exact_tc else P.DD_SEARCH_EXACT_FP32
+        P.dd_project_nearest(ds, ctx, ysel[:256], ie[:256], de[:256], mode=exact_mode)   # tunes, warms up
         torch.cuda.synchronize()
         t_ex = time.perf_counter()
-        P.dd_project_nearest(ds, ctx, ysel, ie, de, mode=P.DD_SEARCH_EXACT_FP32)
+        st_ex = P.dd_project_nearest(ds, ctx, ysel, ie, de, mode=exact_mode)
         t_ex = time.perf_counter() - t_ex
         accuracy = {"sample": int(len(pick)), "same_index": float(np.mean(ia == ie)),
                     "mean_rel_distance_excess": float(np.mean((da - de) / np.maximum(de, 1e-300))),
                     **({"f_d": args.fd_final} if mode == P.DD_SEARCH_ANN else {"f_s": args.f_s, "k": args.knn_k}),
-                    "exact_fp32_searches_per_s": len(pick) / t_ex}
+                    "exact": "tensor-core split-FP16 scan, certified" if exact_tc else "FP32 scan, certified",
+                    "exact_searches_per_s": len(pick) / t_ex, "exact_uncertified": int(st_ex.uncertified)}
 
     # end-to-end through the public API with host buffers (pinned): one
     # projection of the step's m states per call, copies inside the timed region
@@ -564,7 +576,10 @@ def main():
     ap.add_argument("--ramp-iters", type=int, default=None, help="iterations of the f_d ramp (default: workload's, else 5)")
     ap.add_argument("--nlist", type=int, default=0)
     ap.add_argument("--ann-levels", type=int, default=0)
-    ap.add_argument("--ann-check", type=int, default=2048)
+    ap.add_argument("--ann-check", type=int, default=8192,
+                    help="final states checked against the certified exact search (0: none)")
+    ap.add_argument("--no-exact-tc", dest="exact_tc", action="store_false",
+                    help="check with the FP32 exact scan instead of the tensor-core one (no FP16 copy)")
     ap.add_argument("--ann-budget", type=int, default=0,
                     help="leaves a query's warp scans before the leaf-major pass (0: library default, -1: all)")
     ap.add_argument("--knn-k", type=int, default=None, help="k of the k-NN graph (default: the workload's, else 128)")
