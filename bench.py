@@ -5,7 +5,7 @@ A step is one DD iteration z_{i+1} = P_D(P_C(z_i)) of a running solve
 projection of every material point, convergence statistics) through the
 library's C ABI.  `value` = material-point searches per second over the
 timed steps (whole job, all ranks).  Under torchrun every rank runs an
-independent replica (the search does not shard; see DESIGN.md).
+independent replica (the search does not shard).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload NAME] [--mode tc|tc_topk|fp32|ann|knng|serve]
