@@ -667,7 +667,7 @@ constexpr int kFinePerLane = 16;   // L2 <= 512
 constexpr int kPairMax = kCand * kFine + 1;   // leaves a query can hand off (candidates + warm-start leaf)
 constexpr int kLeafBudget = 2;                // default leaves a query's warp scans itself
 
-__global__ void __launch_bounds__(256) k_ann_probe2(Probe2Args P) {
+__global__ void __launch_bounds__(256, 4) k_ann_probe2(Probe2Args P) {
     const ProbeArgs &A = P.A;
     const int lane = threadIdx.x & 31;
     const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
