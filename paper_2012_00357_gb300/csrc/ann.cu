@@ -653,6 +653,7 @@ struct Probe2Args {
     ProbeArgs A;                // leaves in A.radius / A.offs / A.zs / A.perm / A.cluster_of; cand_* are coarse cells
     const float *centf;         // [L x 12] leaf centroids
     const float *rad1;          // [L1] coarse radii
+    const float *lrad1;         // [L1] largest leaf radius of every cell
     int L1, L2;
     float r1max;
     // leaf-major hand-off (all null: every leaf is scanned by the query's warp)
@@ -740,6 +741,7 @@ __global__ void __launch_bounds__(256, 4) k_ann_probe2(Probe2Args P) {
         // rank the cell's leaves: lane holds leaves f = lane + 32 t
         float fd[kFinePerLane];
         unsigned vis = 0;
+        const float cell_lr = P.lrad1[C];
 #pragma unroll
         for (int t = 0; t < kFinePerLane; ++t) {
             const int f = lane + 32 * t;
@@ -765,6 +767,10 @@ __global__ void __launch_bounds__(256, 4) k_ann_probe2(Probe2Args P) {
                 }
             }
             if (!(md < INFINITY)) break;
+            // the remaining leaves of the cell are no nearer and no wider than
+            // the cell's widest: none can pass Eq. (13) with this d_c or a
+            // smaller one (exact requests keep the ordered walk)
+            if (f_d < 1.0f && !(k1 == 0 && k2 == 0) && md - f_d * cell_lr >= dc) break;
             if ((ml & 31) == lane) vis |= 1u << (ml >> 5);
             const int l = C * P.L2 + ml;
             if ((k1 == 0 && k2 == 0) || md - f_d * A.radius[l] < dc) {
@@ -1212,6 +1218,7 @@ void dd_free_ann(dd_dataset *ds) {
         dd_free(ctx, a.cent1, L1p * 48);
         dd_free(ctx, a.cn1, L1p * 4);
         dd_free(ctx, a.rad1, L1p * 4);
+        if (a.lrad1) dd_free(ctx, a.lrad1, L1p * 4);
     }
     a = AnnIndex();
 }
@@ -1468,6 +1475,16 @@ static dd_status build_tree2(dd_dataset *ds, const dd_dataset_opts &o) {
         a.nonempty += hc[l] > 0;
     }
     for (int l = 0; l < L1; ++l) a.r1max = std::max(a.r1max, hr1[l]);
+    // largest leaf radius per cell: no leaf of a cell can pass Eq. (13) once
+    // its centroid distance minus f_d times this exceeds d_c
+    {
+        std::vector<float> lr((size_t)L1p, 0.f);
+        for (int l = 0; l < L; ++l) lr[l / L2] = std::max(lr[l / L2], hr[l]);
+        void *p = nullptr;
+        DD_TRY(dd_alloc(ctx, &p, L1p * 4, "ANN cell leaf radii"));
+        a.lrad1 = (float *)p;
+        DD_TRY_CUDA(ctx, cudaMemcpy(a.lrad1, lr.data(), L1p * 4, cudaMemcpyHostToDevice));
+    }
     return DD_OK;
 }
 
@@ -1597,7 +1614,7 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
         cp += b_nb;
         unsigned *bitem = (unsigned *)cp;
         DD_TRY_CUDA(ctx, cudaMemsetAsync(leaf_cnt, 0, 2 * b_L, s));   // counts and cursors
-        Probe2Args P2{A, a.cent, a.rad1, a.L1, a.L2, a.r1max, budget, pair_leaf, n_pairs, leaf_cnt};
+        Probe2Args P2{A, a.cent, a.rad1, a.lrad1, a.L1, a.L2, a.r1max, budget, pair_leaf, n_pairs, leaf_cnt};
         k_ann_probe2<<<(unsigned)((m * 32 + 255) / 256), 256, 0, s>>>(P2);
         DD_TRY_CUDA(ctx, cudaGetLastError());
         ctx->launches += 6;
@@ -1609,7 +1626,7 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
         k_leaf_scan<<<(unsigned)(ctx->n_sm * 8), 256, 0, s>>>(LS);
         k_pair_merge<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(n_pairs, res, a.perm, m, out.idx, d1f, d2f);
     } else if (two) {
-        Probe2Args P2{A, a.cent, a.rad1, a.L1, a.L2, a.r1max, 0, nullptr, nullptr, nullptr};
+        Probe2Args P2{A, a.cent, a.rad1, a.lrad1, a.L1, a.L2, a.r1max, 0, nullptr, nullptr, nullptr};
         k_ann_probe2<<<(unsigned)((m * 32 + 255) / 256), 256, 0, s>>>(P2);
     } else {
         k_ann_probe<<<(unsigned)((m * 32 + 255) / 256), 256, 0, s>>>(A);

@@ -147,6 +147,7 @@ struct AnnIndex {
     float *cn1 = nullptr;       // [L1p]
     float *rad1 = nullptr;      // [L1p]
     float r1max = 0.f;
+    float *lrad1 = nullptr;     // [L1p] largest leaf radius of every cell
 };
 
 // Moving-query record of the approximate search (Eq. 14), per query:
