@@ -46,8 +46,8 @@ TRAFFIC = {
     # (workload, mode): (source file under the package's csrc/, sha256, bytes per launch)
     # k_rank_small + k_ann_probe2 + k_leaf_scan of one search, mean of the 10
     # timed steps (profiles/launches_cube32_N1e9_ann_4loads.md)
-    ("cube32_N1e9_ann_4loads", "ann"): ("ann.cu", "67cee421f41430ee7470bd50c61a0731bbab06e8d53a97bc95aa919d0d7bc547",
-                                       3781206656),
+    ("cube32_N1e9_ann_4loads", "ann"): ("ann.cu", "131a562c9d0baa0b9042a3159f76091948ed4c2d92ce828697eee96e4abdc890",
+                                       4116703641),
 }
 
 
