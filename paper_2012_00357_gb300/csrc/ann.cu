@@ -179,32 +179,41 @@ __global__ void k_radius(const float *__restrict__ zs, const int32_t *__restrict
 // ---------------------------------------------------------------------------
 // Merge the top-k lists of the centroid scan; keep the kCand nearest
 // centroids by exact FP32 distance (ties to the lower centroid index).
-// Nearest kCand centroids of every query when the centroid set is small:
-// one thread per query, centroids staged in shared memory and read as
-// broadcasts; top kCand by the expanded FP32 score |c|^2 - 2 c.q (ties to
-// the lower index), then ordered by the FP32 distance as from k_ann_cands.
+// Nearest kCand centroids of every listed query when the centroid set is
+// small: each thread ranks kRankQ queries, centroids staged in shared memory
+// and read as broadcasts (one read serves both queries); top kCand by the
+// expanded FP32 score |c|^2 - 2 c.q (ties to the lower index), then ordered by
+// the FP32 distance as from k_ann_cands.  `list` (may be null: queries
+// 0..m-1) holds the *n_list queries to rank, in any order.
 constexpr int kRankTile = 896;      // 896 x 52 B of static shared memory (< 48 KB)
 constexpr int kRankMax = 4096;    // larger sets go through the tiled FP32 scan
+constexpr int kRankQ = 2;         // queries per thread
 
-__global__ void __launch_bounds__(256) k_rank_small(const QueryRec *__restrict__ rec, int64_t m,
+__global__ void __launch_bounds__(256, 3) k_rank_small(const QueryRec *__restrict__ rec, int64_t m,
+                                                    const int32_t *__restrict__ list,
+                                                    const unsigned *__restrict__ n_list,
                                                     const float *__restrict__ cent, const float *__restrict__ cn,
                                                     int L, int32_t *__restrict__ out_cl, float *__restrict__ out_d) {
     __shared__ __align__(16) float sc[kRankTile * 12];
     __shared__ float sn[kRankTile];
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const bool act = i < m;
-    float q[12], qm2[12];
+    const int64_t nq = list ? (int64_t)*n_list : m;
+    const int64_t base = blockIdx.x * (int64_t)blockDim.x * kRankQ;
+    if (base >= nq) return;           // the whole block: before any barrier
+    int64_t qi[kRankQ];
+    float qm2[kRankQ][12];
+    float bs[kRankQ][kCand];
+    int bc[kRankQ][kCand];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {
-        q[k] = act ? rec[i].q[k] : 0.f;
-        qm2[k] = -2.f * q[k];
-    }
-    float bs[kCand];
-    int bc[kCand];
+    for (int r = 0; r < kRankQ; ++r) {
+        const int64_t t = base + r * blockDim.x + threadIdx.x;
+        qi[r] = t < nq ? (list ? (int64_t)list[t] : t) : -1;
 #pragma unroll
-    for (int k = 0; k < kCand; ++k) {
-        bs[k] = INFINITY;
-        bc[k] = -1;
+        for (int k = 0; k < 12; ++k) qm2[r][k] = qi[r] >= 0 ? -2.f * rec[qi[r]].q[k] : 0.f;
+#pragma unroll
+        for (int k = 0; k < kCand; ++k) {
+            bs[r][k] = INFINITY;
+            bc[r][k] = -1;
+        }
     }
     for (int t0 = 0; t0 < L; t0 += kRankTile) {
         const int nt = min(kRankTile, L - t0);
@@ -212,50 +221,65 @@ __global__ void __launch_bounds__(256) k_rank_small(const QueryRec *__restrict__
         for (int k = threadIdx.x; k < nt * 12; k += blockDim.x) sc[k] = cent[(size_t)t0 * 12 + k];
         for (int k = threadIdx.x; k < nt; k += blockDim.x) sn[k] = cn[t0 + k];
         __syncthreads();
-        if (!act) continue;
         for (int f = 0; f < nt; ++f) {
             const float4 *pc = reinterpret_cast<const float4 *>(sc + f * 12);
             const float4 a = pc[0], b = pc[1], d = pc[2];
-            float v = sn[f];
-            v = fmaf(qm2[0], a.x, v); v = fmaf(qm2[1], a.y, v); v = fmaf(qm2[2], a.z, v); v = fmaf(qm2[3], a.w, v);
-            v = fmaf(qm2[4], b.x, v); v = fmaf(qm2[5], b.y, v); v = fmaf(qm2[6], b.z, v); v = fmaf(qm2[7], b.w, v);
-            v = fmaf(qm2[8], d.x, v); v = fmaf(qm2[9], d.y, v); v = fmaf(qm2[10], d.z, v); v = fmaf(qm2[11], d.w, v);
-            if (v < bs[kCand - 1]) {
-                bs[kCand - 1] = v;
-                bc[kCand - 1] = t0 + f;
+            const float n2 = sn[f];
 #pragma unroll
-                for (int k = kCand - 1; k > 0; --k)
-                    if (bs[k] < bs[k - 1]) {
-                        const float tv = bs[k];
-                        bs[k] = bs[k - 1];
-                        bs[k - 1] = tv;
-                        const int tc = bc[k];
-                        bc[k] = bc[k - 1];
-                        bc[k - 1] = tc;
-                    }
+            for (int r = 0; r < kRankQ; ++r) {
+                const float *w = qm2[r];
+                float v = n2;
+                v = fmaf(w[0], a.x, v); v = fmaf(w[1], a.y, v); v = fmaf(w[2], a.z, v); v = fmaf(w[3], a.w, v);
+                v = fmaf(w[4], b.x, v); v = fmaf(w[5], b.y, v); v = fmaf(w[6], b.z, v); v = fmaf(w[7], b.w, v);
+                v = fmaf(w[8], d.x, v); v = fmaf(w[9], d.y, v); v = fmaf(w[10], d.z, v); v = fmaf(w[11], d.w, v);
+                if (v < bs[r][kCand - 1]) {
+                    bs[r][kCand - 1] = v;
+                    bc[r][kCand - 1] = t0 + f;
+#pragma unroll
+                    for (int k = kCand - 1; k > 0; --k)
+                        if (bs[r][k] < bs[r][k - 1]) {
+                            const float tv = bs[r][k];
+                            bs[r][k] = bs[r][k - 1];
+                            bs[r][k - 1] = tv;
+                            const int tc = bc[r][k];
+                            bc[r][k] = bc[r][k - 1];
+                            bc[r][k - 1] = tc;
+                        }
+                }
             }
         }
     }
-    if (!act) return;
-    float bd[kCand];
 #pragma unroll
-    for (int k = 0; k < kCand; ++k) bd[k] = bc[k] >= 0 ? dist2_12(cent + (size_t)bc[k] * 12, q) : INFINITY;
+    for (int r = 0; r < kRankQ; ++r) {
+        if (qi[r] < 0) continue;
+        const int64_t i = qi[r];
+        float q[12];
 #pragma unroll
-    for (int r = 1; r < kCand; ++r)       // insertion sort by (distance, index)
+        for (int k = 0; k < 12; ++k) q[k] = rec[i].q[k];
+        float bd[kCand];
+        int c8[kCand];
 #pragma unroll
-        for (int k = r; k > 0; --k)
-            if (bd[k] < bd[k - 1] || (bd[k] == bd[k - 1] && bc[k] >= 0 && bc[k] < bc[k - 1])) {
-                const float tv = bd[k];
-                bd[k] = bd[k - 1];
-                bd[k - 1] = tv;
-                const int tc = bc[k];
-                bc[k] = bc[k - 1];
-                bc[k - 1] = tc;
-            }
+        for (int k = 0; k < kCand; ++k) {
+            c8[k] = bc[r][k];
+            bd[k] = c8[k] >= 0 ? dist2_12(cent + (size_t)c8[k] * 12, q) : INFINITY;
+        }
 #pragma unroll
-    for (int k = 0; k < kCand; ++k) {
-        out_cl[i * kCand + k] = bc[k];
-        out_d[i * kCand + k] = sqrtf(bd[k]);
+        for (int a = 1; a < kCand; ++a)       // insertion sort by (distance, index)
+#pragma unroll
+            for (int k = a; k > 0; --k)
+                if (bd[k] < bd[k - 1] || (bd[k] == bd[k - 1] && c8[k] >= 0 && c8[k] < c8[k - 1])) {
+                    const float tv = bd[k];
+                    bd[k] = bd[k - 1];
+                    bd[k - 1] = tv;
+                    const int tc = c8[k];
+                    c8[k] = c8[k - 1];
+                    c8[k - 1] = tc;
+                }
+#pragma unroll
+        for (int k = 0; k < kCand; ++k) {
+            out_cl[i * kCand + k] = c8[k];
+            out_d[i * kCand + k] = sqrtf(bd[k]);
+        }
     }
 }
 
@@ -390,12 +414,90 @@ struct ProbeArgs {
                                     // re-searches, [3] leaf centroids ranked, [4] distinct points,
                                     // [5] points read
     unsigned *touched;              // [ceil(L / 32)] clusters scanned by any query of this search
+    int gated;                      // 1: k_ann_gate ran; cand_cl[i * kCand] == kGated marks a kept query
 };
+
+constexpr int kGated = -2;
+
+// Eq. (14) before the cell ranking: a query that moved less than half the gap
+// between its previous nearest and second distances keeps its warm-start
+// point without a search (its answer is written here and its first candidate
+// slot marked kGated); every other query is appended to the list the ranking
+// and the probes work on.  One thread per query; one list append, and one
+// update of each counter, per block.
+struct GateArgs {
+    const QueryRec *rec;
+    int64_t m, N;
+    const int32_t *prev;
+    const float *z32;
+    const float *mot_q, *mot_d;
+    int32_t *idx;
+    float *d1, *d2;
+    int32_t *cand_cl;
+    int32_t *list;
+    unsigned *n_list;
+    unsigned long long *counters;   // [1] queries kept, [3] += Lr per listed query (centroids ranked)
+    int Lr;
+};
+
+__global__ void __launch_bounds__(256) k_ann_gate(GateArgs G) {
+    __shared__ unsigned s_cnt[2][8];
+    __shared__ unsigned s_base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool keep = false;
+    if (i < G.m) {
+        const int j0 = G.prev[i];
+        if (j0 >= 0 && j0 < G.N) {
+            float q[12];
+#pragma unroll
+            for (int k = 0; k < 12; ++k) q[k] = G.rec[i].q[k];
+            float mv = 0.f;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                float t = q[k] - G.mot_q[i * 12 + k];
+                mv = fmaf(t, t, mv);
+            }
+            mv = sqrtf(mv);
+            const float r1 = G.mot_d[i * 2], r2 = G.mot_d[i * 2 + 1];
+            if (mv < 0.5f * (r2 - r1)) {
+                keep = true;
+                G.idx[i] = j0;
+                G.d1[i] = dist2_12(G.z32 + (size_t)j0 * 12, q);
+                float lb = fmaxf(r2 - mv, 0.f);
+                G.d2[i] = lb * lb;
+                G.cand_cl[i * kCand] = kGated;
+            }
+        }
+    }
+    const bool listed = i < G.m && !keep;
+    const unsigned mk = __ballot_sync(0xffffffffu, keep), ml = __ballot_sync(0xffffffffu, listed);
+    if (lane == 0) {
+        s_cnt[0][warp] = __popc(mk);
+        s_cnt[1][warp] = __popc(ml);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned nk = 0, nl = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            nk += s_cnt[0][w];
+            const unsigned c = s_cnt[1][w];
+            s_cnt[1][w] = nl;             // exclusive prefix of the warps' list entries
+            nl += c;
+        }
+        s_base = nl ? atomicAdd(G.n_list, nl) : 0u;
+        if (nk) atomicAdd(G.counters + 1, (unsigned long long)nk);
+        if (nl) atomicAdd(G.counters + 3, (unsigned long long)nl * (unsigned long long)G.Lr);
+    }
+    __syncthreads();
+    if (listed) G.list[s_base + s_cnt[1][warp] + __popc(ml & ((1u << lane) - 1u))] = (int32_t)i;
+}
 
 __global__ void __launch_bounds__(256) k_ann_probe(ProbeArgs A) {
     const int lane = threadIdx.x & 31;
     const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (i >= A.m) return;
+    if (A.gated && A.cand_cl[i * kCand] == kGated) return;   // kept by Eq. (14)
     float q[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) q[k] = A.rec[i].q[k];
@@ -673,6 +775,10 @@ __global__ void __launch_bounds__(256, 4) k_ann_probe2(Probe2Args P) {
     const int lane = threadIdx.x & 31;
     const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (i >= A.m) return;
+    if (A.gated && A.cand_cl[i * kCand] == kGated) {   // kept by Eq. (14)
+        if (lane == 0 && P.n_pairs) P.n_pairs[i] = 0;
+        return;
+    }
     float q[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) q[k] = A.rec[i].q[k];
@@ -1488,8 +1594,13 @@ static dd_status build_tree2(dd_dataset *ds, const dd_dataset_opts &o) {
     return DD_OK;
 }
 
-dd_status dd_ann_rank_cells(dd_dataset *ds, const QueryRec *rec, int64_t m, int32_t *cand_cl, float *cand_d,
-                            cudaStream_t s) {
+static bool rank_small(const AnnIndex &a) { return (a.levels == 2 ? a.L1 : a.nlist) <= kRankMax; }
+
+// As dd_ann_rank_cells, for the *n_list queries of `list` only (list and
+// n_list on the device; both null: every query).  A list needs the small
+// centroid set (rank_small).
+static dd_status ann_rank_listed(dd_dataset *ds, const QueryRec *rec, int64_t m, const int32_t *list,
+                                 const unsigned *n_list, int32_t *cand_cl, float *cand_d, cudaStream_t s) {
     dd_ctx *ctx = ds->ctx;
     const AnnIndex &a = ds->ann;
     const bool two = a.levels == 2;
@@ -1498,8 +1609,10 @@ dd_status dd_ann_rank_cells(dd_dataset *ds, const QueryRec *rec, int64_t m, int3
     const int Lr = two ? a.L1 : a.nlist;
     if (Lr <= kRankMax) {
         ctx->launches++;
-        k_rank_small<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(rec, m, rank_cent, rank_cn, Lr, cand_cl, cand_d);
+        k_rank_small<<<(unsigned)((m + 256 * kRankQ - 1) / (256 * kRankQ)), 256, 0, s>>>(
+            rec, m, list, n_list, rank_cent, rank_cn, Lr, cand_cl, cand_d);
     } else {
+        if (list) return dd_fail(ctx, DD_ERR_STATE, "cell ranking: a query list needs the small centroid set");
         int splits = 0, cap = 0;
         CandHeader *hdr = nullptr;
         float2 *cand = nullptr;
@@ -1511,6 +1624,11 @@ dd_status dd_ann_rank_cells(dd_dataset *ds, const QueryRec *rec, int64_t m, int3
     }
     DD_TRY_CUDA(ctx, cudaGetLastError());
     return DD_OK;
+}
+
+dd_status dd_ann_rank_cells(dd_dataset *ds, const QueryRec *rec, int64_t m, int32_t *cand_cl, float *cand_d,
+                            cudaStream_t s) {
+    return ann_rank_listed(ds, rec, m, nullptr, nullptr, cand_cl, cand_d, s);
 }
 
 dd_status dd_ann_finish(dd_dataset *ds, const double *y_dev, int64_t m, const int32_t *idx, const float *d2f,
@@ -1538,7 +1656,7 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
                  b_cd = r256((size_t)m * kCand * 4), b_f = r256((size_t)m * 4), b_list = r256((size_t)m * 8),
                  b_bits = r256((size_t)(a.nlist + 31) / 32 * 4);
     void *w = nullptr;
-    DD_TRY(dd_workspace(ctx, WS_ANN, b_rec + b_cl + b_cd + 2 * b_f + b_list + 256 + b_bits, &w));
+    DD_TRY(dd_workspace(ctx, WS_ANN, b_rec + b_cl + b_cd + 3 * b_f + b_list + 256 + b_bits, &w));
     char *c = (char *)w;
     QueryRec *rec = (QueryRec *)c;
     int32_t *cand_cl = (int32_t *)(c + b_rec);
@@ -1548,13 +1666,25 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
     int64_t *fb_list = (int64_t *)(c + b_rec + b_cl + b_cd + 2 * b_f);
     unsigned long long *counters = (unsigned long long *)(c + b_rec + b_cl + b_cd + 2 * b_f + b_list);
     unsigned *touched = (unsigned *)(c + b_rec + b_cl + b_cd + 2 * b_f + b_list + 256);
-    DD_TRY_CUDA(ctx, cudaMemsetAsync(counters, 0, 64, s));
+    int32_t *qlist = (int32_t *)(c + b_rec + b_cl + b_cd + 2 * b_f + b_list + 256 + b_bits);
+    unsigned *n_list = (unsigned *)(counters + 8);
+    DD_TRY_CUDA(ctx, cudaMemsetAsync(counters, 0, 128, s));
     DD_TRY_CUDA(ctx, cudaMemsetAsync(touched, 0, b_bits, s));
 
     DD_TRY(dd_map_queries(ds, y_dev, m, nullptr, rec, s));
     if (st) DD_TRY_CUDA(ctx, dd_event_record(ctx, ctx->ev_scan[0], s));
     const bool two = a.levels == 2;
-    DD_TRY(dd_ann_rank_cells(ds, rec, m, cand_cl, cand_d, s));
+    const int Lr = two ? a.L1 : a.nlist;
+    // Eq. (14) ahead of the ranking: kept queries are neither ranked nor probed
+    const bool gate = prev_idx_dev && mot && mot->q && rank_small(a);
+    if (gate) {
+        GateArgs G{rec, m, ds->N, prev_idx_dev, ds->z32, mot->q, mot->d, out.idx, d1f, d2f, cand_cl, qlist, n_list,
+                   counters, Lr};
+        ctx->launches++;
+        k_ann_gate<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(G);
+        DD_TRY_CUDA(ctx, cudaGetLastError());
+    }
+    DD_TRY(ann_rank_listed(ds, rec, m, gate ? qlist : nullptr, gate ? n_list : nullptr, cand_cl, cand_d, s));
     ProbeArgs A;
     A.zs = a.zs;
     A.perm = a.perm;
@@ -1572,8 +1702,9 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
     A.fd_q = fd_q;
     A.rmax = a.rmax;
     A.prev = prev_idx_dev;
-    A.mot_q = mot ? mot->q : nullptr;
-    A.mot_d = mot ? mot->d : nullptr;
+    A.mot_q = (mot && !gate) ? mot->q : nullptr;
+    A.mot_d = (mot && !gate) ? mot->d : nullptr;
+    A.gated = gate ? 1 : 0;
     A.idx = out.idx;
     A.d1 = d1f;
     A.d2 = d2f;
@@ -1652,7 +1783,7 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
     if (st && ctx->defer) {
         DD_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->defer->ann, counters, 8 * sizeof(unsigned long long),
                                          cudaMemcpyDeviceToDevice, s));
-        st->distances += m * (int64_t)(two ? a.L1 : a.nlist);
+        st->distances += gate ? 0 : m * (int64_t)Lr;   // gated: the ranked centroids are in counters[3]
     } else if (st) {
         unsigned long long h[6];
         DD_TRY_CUDA(ctx, cudaMemcpyAsync(h, counters, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -1660,7 +1791,7 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
         float ms = 0.f;
         DD_TRY_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev_scan[0], ctx->ev_scan[1]));
         st->scan_ms += ms;
-        st->distances += (int64_t)h[0] + (int64_t)h[3] + m * (int64_t)(two ? a.L1 : a.nlist) + (int64_t)n_fb * ds->N;
+        st->distances += (int64_t)h[0] + (int64_t)h[3] + (gate ? 0 : m * (int64_t)Lr) + (int64_t)n_fb * ds->N;
         st->points += (int64_t)h[5] + (int64_t)n_fb * ds->N;
         st->unique_points += n_fb ? ds->N : (int64_t)h[4];
         st->skipped += (int64_t)h[1];

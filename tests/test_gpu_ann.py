@@ -81,13 +81,15 @@ def test_rules_match_oracle(ctx, annset, f_d, warm):
     assert np.allclose(metric.local_d2(y, data[idx].astype(np.float64), C), d2, rtol=1e-10)
 
 
-def test_ann_solve_fd_one_matches_exact_solve(ctx):
+@pytest.mark.parametrize("levels,nlist", [(1, 32), (2, 64)])
+def test_ann_solve_fd_one_matches_exact_solve(ctx, levels, nlist):
     """With f_d = 1 every search is exact and the Eq. (14) skip is sound, so
-    the approximate solve reproduces the exact one."""
+    the approximate solve reproduces the exact one (flat partition and
+    two-level tree); the later iterations keep queries by Eq. (14)."""
     data = I.make_dataset(8000, I.LINEAR, seed=6)
     load = I.load_case("tension", 1e-3)
     init = I.initial_association(8 * 27, len(data), seed=6)
-    ds = P.dd_load_dataset(ctx, data, C, ann_nlist=32, seed=2)
+    ds = P.dd_load_dataset(ctx, data, C, ann_nlist=nlist, ann_levels=levels, seed=2)
     try:
         re = P.dd_solve(ds, ctx, 3, load, init_idx=init)
         sv = P.dd_solver_create(ds, ctx, 3, load, mode=P.DD_SEARCH_ANN, f_d0=1.0, f_d_final=1.0, init_idx=init)
@@ -100,6 +102,7 @@ def test_ann_solve_fd_one_matches_exact_solve(ctx):
         P.dd_free_dataset(ds)
     assert ra.converged and np.array_equal(ra.idx, re.idx)
     assert np.allclose(ra.u, re.u, rtol=0, atol=1e-9 * np.abs(re.u).max())
+    assert sum(i.skipped for i in infos) > 0
 
 
 def test_ann_solve_ramp_close_to_exact(ctx):
