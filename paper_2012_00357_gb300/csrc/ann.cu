@@ -1078,7 +1078,9 @@ struct LeafBest {
 
 // One warp per chunk of up to 64 queries of a leaf: lane l takes queries l
 // and l + 32, so every point read serves two distances (the scan is bound by
-// the L1 reads of the points, one broadcast read per point and warp).
+// the L1 reads of the points, one broadcast read per point and warp).  A
+// chunk of at most 16 queries (a leaf few queries reach, typical of the first
+// DD iterations) gives each query several lanes, which split the points.
 __global__ void __launch_bounds__(256) k_leaf_scan(LeafScanArgs A) {
     __shared__ unsigned long long sc;
     if (threadIdx.x == 0) sc = 0ull;
@@ -1097,9 +1099,13 @@ __global__ void __launch_bounds__(256) k_leaf_scan(LeafScanArgs A) {
         const int l = lo;
         const unsigned q0 = A.pair_off[l] + (unsigned)kLeafChunk * (it - A.item_off[l]);
         const unsigned qn = min((unsigned)kLeafChunk, A.pair_off[l + 1] - q0);
-        const bool act0 = (unsigned)lane < qn, act1 = (unsigned)lane + 32u < qn;
         const bool two = qn > 32u;                      // warp-uniform
-        const unsigned s0 = act0 ? A.bucket[q0 + lane] : 0u, s1 = act1 ? A.bucket[q0 + 32 + lane] : 0u;
+        // at most 16 queries: G lanes per query (G a power of two, qn * G <=
+        // 32), each taking every G-th point; the partial results are merged
+        const int G = qn <= 1u ? 32 : qn <= 2u ? 16 : qn <= 4u ? 8 : qn <= 8u ? 4 : qn <= 16u ? 2 : 1;
+        const unsigned slot = (unsigned)(lane / G), sub = (unsigned)(lane & (G - 1));
+        const bool act0 = slot < qn, act1 = (unsigned)lane + 32u < qn;
+        const unsigned s0 = act0 ? A.bucket[q0 + slot] : 0u, s1 = act1 ? A.bucket[q0 + 32 + lane] : 0u;
         float qa[12], qb[12];
         const QueryRec *ra = A.rec + (act0 ? s0 / kPairMax : 0), *rb = A.rec + (act1 ? s1 / kPairMax : 0);
 #pragma unroll
@@ -1127,17 +1133,30 @@ __global__ void __launch_bounds__(256) k_leaf_scan(LeafScanArgs A) {
                 bb.offer(db, (int)p0 + t);
             }
         } else {
-            int t = 0;
-            for (; t + 3 < n; t += 4) {
+            int t = (int)sub;
+            for (; t + 3 * G < n; t += 4 * G) {
                 float d[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) d[u] = dist2_12(zp + (size_t)(t + u) * 12, qa);
+                for (int u = 0; u < 4; ++u) d[u] = dist2_12(zp + (size_t)(t + u * G) * 12, qa);
 #pragma unroll
-                for (int u = 0; u < 4; ++u) ba.offer(d[u], (int)p0 + t + u);
+                for (int u = 0; u < 4; ++u) ba.offer(d[u], (int)p0 + t + u * G);
             }
-            for (; t < n; ++t) ba.offer(dist2_12(zp + (size_t)t * 12, qa), (int)p0 + t);
+            for (; t < n; t += G) ba.offer(dist2_12(zp + (size_t)t * 12, qa), (int)p0 + t);
+            // merge the G partial results of a query (ties to the lower point;
+            // the second distance is the second smallest of all points read)
+            for (int o = 1; o < G; o <<= 1) {
+                const float o1 = __shfl_xor_sync(0xffffffffu, ba.b1, o), o2 = __shfl_xor_sync(0xffffffffu, ba.b2, o);
+                const int oj = __shfl_xor_sync(0xffffffffu, ba.j1, o);
+                if (o1 < ba.b1 || (o1 == ba.b1 && oj < ba.j1)) {
+                    ba.b2 = fminf(ba.b1, o2);
+                    ba.b1 = o1;
+                    ba.j1 = oj;
+                } else {
+                    ba.b2 = fminf(ba.b2, o1);
+                }
+            }
         }
-        if (act0) A.res[s0] = PairRes{ba.b1, ba.j1, ba.b2};
+        if (act0 && sub == 0u) A.res[s0] = PairRes{ba.b1, ba.j1, ba.b2};
         if (act1) A.res[s1] = PairRes{bb.b1, bb.j1, bb.b2};
         if (lane == 0) {
             atomicOr(A.touched + (l >> 5), 1u << (l & 31));
