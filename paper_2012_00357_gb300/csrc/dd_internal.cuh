@@ -6,6 +6,8 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -158,6 +160,18 @@ struct AnnMotion {
     float *d;      // [m x 2]
 };
 
+// Host-side setup of the constraint projection for one mesh: element
+// stiffness, stencil tables, smoother weight and coarse-level inverse.  A
+// function of the mesh and the metric only, so the solves of a data set on
+// the same mesh share one copy.
+struct SolverSetup {
+    int nx = 0, ny = 0, nz = 0, top = 0;
+    double lx = 0, ly = 0, lz = 0;
+    std::vector<double> Ke, St64;
+    std::vector<float> St32, Kinv;
+    double omega = 0;
+};
+
 struct dd_dataset {
     dd_ctx *ctx = nullptr;
     int64_t N = 0, N_pad = 0;
@@ -176,6 +190,8 @@ struct dd_dataset {
     AnnIndex ann;
     KnnGraph knn;
     size_t bytes = 0;
+    std::vector<std::shared_ptr<const SolverSetup>> setups;   // most recent last
+    std::mutex setup_mu;
 };
 
 dd_status dd_fail(dd_ctx *ctx, dd_status st, const std::string &msg);

@@ -198,6 +198,38 @@ size_t dd_solver_state_bytes(dd_ctx *ctx, const dd_mesh &mesh) {
     return carve(&tmp, nullptr);
 }
 
+// The host-side setup of sv's mesh (sv->g and sv->cb planned): computed on
+// the first solve of a data set on that mesh, then shared.
+static std::shared_ptr<const SolverSetup> solver_setup(dd_dataset *ds, const dd_solver *sv) {
+    const MeshDev &g = sv->g;
+    const dd_mesh &m = sv->mesh;
+    std::lock_guard<std::mutex> lock(ds->setup_mu);
+    for (const auto &p : ds->setups)
+        if (p->nx == m.nx && p->ny == m.ny && p->nz == m.nz && p->top == g.top_fixed && p->lx == m.lx &&
+            p->ly == m.ly && p->lz == m.lz)
+            return p;
+    auto su = std::make_shared<SolverSetup>();
+    su->nx = m.nx;
+    su->ny = m.ny;
+    su->nz = m.nz;
+    su->top = g.top_fixed;
+    su->lx = m.lx;
+    su->ly = m.ly;
+    su->lz = m.lz;
+    su->Ke.assign(576, 0.0);
+    fem_element_stiffness(g, sv->ops, ds->M.C, su->Ke.data());
+    su->St64.assign(27 * 27 * 9, 0.0);
+    su->St32.assign(27 * 27 * 12, 0.f);
+    fem_stencil_table(su->Ke.data(), su->St64.data());
+    su->omega = 4.0 / (3.0 * fem_jacobi_lambda_max(su->St64.data()));
+    if (sv->cb.glev < sv->cb.nlev) fem_mg_coarse_inverse(sv->cb, su->St64.data(), su->Kinv);
+    for (int cd = 0; cd < 27 * 27; ++cd)
+        for (int k = 0; k < 9; ++k) su->St32[cd * 12 + k] = (float)su->St64[cd * 9 + k];
+    if (ds->setups.size() >= 16) ds->setups.erase(ds->setups.begin());
+    ds->setups.push_back(su);
+    return su;
+}
+
 extern "C" dd_status dd_solver_create(dd_dataset *ds, const dd_mesh *mesh, const dd_load *load,
                                       const dd_solve_opts *opts, dd_solver **out) {
     if (!ds) return DD_ERR_ARG;
@@ -261,16 +293,11 @@ extern "C" dd_status dd_solver_create(dd_dataset *ds, const dd_mesh *mesh, const
     for (auto &e : sv->ev)
         if (cudaEventCreate(&e) != cudaSuccess) return fail(dd_fail(ctx, DD_ERR_CUDA, "cudaEventCreate"));
     const size_t nn = sv->g.n_nodes, ng = sv->g.n_gp;
-    std::vector<double> Ke(576), f(nn * 3);
-    fem_element_stiffness(sv->g, sv->ops, ds->M.C, Ke.data());
-    std::vector<double> St64(27 * 27 * 9);
-    std::vector<float> St32(27 * 27 * 12, 0.f);
-    fem_stencil_table(Ke.data(), St64.data());
-    sv->cb.omega = 4.0 / (3.0 * fem_jacobi_lambda_max(St64.data()));
-    std::vector<float> Kinv;
-    if (sv->cb.glev < sv->cb.nlev) fem_mg_coarse_inverse(sv->cb, St64.data(), Kinv);
-    for (int cd = 0; cd < 27 * 27; ++cd)
-        for (int k = 0; k < 9; ++k) St32[cd * 12 + k] = (float)St64[cd * 9 + k];
+    const std::shared_ptr<const SolverSetup> su = solver_setup(ds, sv);
+    const std::vector<double> &Ke = su->Ke, &St64 = su->St64;
+    const std::vector<float> &St32 = su->St32, &Kinv = su->Kinv;
+    sv->cb.omega = su->omega;
+    std::vector<double> f(nn * 3);
     fem_traction_force(sv->g, *load, mesh->lx, mesh->ly, f.data());
     // x starts at zero, with the prescribed top displacement in its u part;
     // the solves keep those entries (fixed dofs) and the residual b - K x
