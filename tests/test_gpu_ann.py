@@ -81,12 +81,14 @@ def test_rules_match_oracle(ctx, annset, f_d, warm):
     assert np.allclose(metric.local_d2(y, data[idx].astype(np.float64), C), d2, rtol=1e-10)
 
 
-@pytest.mark.parametrize("levels,nlist", [(1, 32), (2, 64)])
-def test_ann_solve_fd_one_matches_exact_solve(ctx, levels, nlist):
+@pytest.mark.parametrize("levels,nlist,n", [(1, 32, 8000), (2, 64, 8000), (1, 8192, 60000)])
+def test_ann_solve_fd_one_matches_exact_solve(ctx, levels, nlist, n):
     """With f_d = 1 every search is exact and the Eq. (14) skip is sound, so
     the approximate solve reproduces the exact one (flat partition and
-    two-level tree); the later iterations keep queries by Eq. (14)."""
-    data = I.make_dataset(8000, I.LINEAR, seed=6)
+    two-level tree; above 4096 cells the cells are ranked by the tiled scan
+    and the probe takes the Eq. (14) test itself); the later iterations keep
+    queries by Eq. (14)."""
+    data = I.make_dataset(n, I.LINEAR, seed=6)
     load = I.load_case("tension", 1e-3)
     init = I.initial_association(8 * 27, len(data), seed=6)
     ds = P.dd_load_dataset(ctx, data, C, ann_nlist=nlist, ann_levels=levels, seed=2)
@@ -143,10 +145,16 @@ def test_tree2_leaves_cover_members(ctx, treeset):
         assert d[cl == l].max() <= rad[l] * (1 + 1e-5) + 1e-12
 
 
-def test_tree2_fd_one_is_exact(ctx, treeset):
+@pytest.mark.parametrize("budget,warm", [(0, False), (-2, True), (1, True), (-1, True)])
+def test_tree2_fd_one_is_exact(ctx, treeset, budget, warm):
+    """f_d = 1: exact answers whatever the split between the query's warp and
+    the leaf-major scan (-2: every leaf handed off; -1: none), with and
+    without a warm start; the handed-off leaves reach few queries each, so
+    their scan splits the points of a leaf across lanes."""
     data, ds = treeset
     y = I.make_states(1500, I.NONLINEAR, seed=19, spread=0.3)
-    idx, d2, st = search(ctx, ds, y, 1.0)
+    prev = np.random.default_rng(9).integers(0, len(data), len(y)).astype(np.int32) if warm else None
+    idx, d2, st = search(ctx, ds, y, 1.0, prev, ann_budget=budget)
     assert_nn_parity(idx, d2, data, y, C)
 
 
