@@ -46,8 +46,8 @@ TRAFFIC = {
     # (workload, mode): (source file under the package's csrc/, sha256, bytes per launch)
     # k_ann_gate + k_rank_small + k_ann_probe2 + k_leaf_scan of one search,
     # mean of the 10 timed steps (profiles/launches_cube32_N1e9_ann_4loads.md)
-    ("cube32_N1e9_ann_4loads", "ann"): ("ann.cu", "7b3c31dc426dafaeca5a78e80afcba703b07d14aeba0bac116534395848800b7",
-                                       4237623168),
+    ("cube32_N1e9_ann_4loads", "ann"): ("ann.cu", "37800db4edc72ec8201d1324befdff3c3a12d98afe240f2470661fa7473ad70c",
+                                       4244073113),
 }
 
 

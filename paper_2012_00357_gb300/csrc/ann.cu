@@ -844,14 +844,15 @@ __global__ void __launch_bounds__(256, 4) k_ann_probe2(Probe2Args P) {
         if (C < 0) break;
         const float dC = A.cand_d[i * kCand + k1];
         if (!(k1 == 0 || dC - f_d * P.rad1[C] < dc)) continue;
-        // rank the cell's leaves: lane holds leaves f = lane + 32 t
+        // rank the cell's leaves: lane holds leaves f = lane + 32 t (squared
+        // centroid distances; the plain distance is taken of the chosen ones)
         float fd[kFinePerLane];
         unsigned vis = 0;
         const float cell_lr = P.lrad1[C];
 #pragma unroll
         for (int t = 0; t < kFinePerLane; ++t) {
             const int f = lane + 32 * t;
-            fd[t] = (f < P.L2) ? sqrtf(dist2_12(P.centf + ((size_t)C * P.L2 + f) * 12, q)) : INFINITY;
+            fd[t] = (f < P.L2) ? dist2_12(P.centf + ((size_t)C * P.L2 + f) * 12, q) : INFINITY;
         }
         if (lane == 0) atomicAdd(A.counters + 3, (unsigned long long)P.L2);
         for (int k2 = 0; k2 < kFine; ++k2) {
@@ -873,6 +874,7 @@ __global__ void __launch_bounds__(256, 4) k_ann_probe2(Probe2Args P) {
                 }
             }
             if (!(md < INFINITY)) break;
+            md = sqrtf(md);
             // the remaining leaves of the cell are no nearer and no wider than
             // the cell's widest: none can pass Eq. (13) with this d_c or a
             // smaller one (exact requests keep the ordered walk)
@@ -903,7 +905,7 @@ __global__ void __launch_bounds__(256, 4) k_ann_probe2(Probe2Args P) {
             for (int t = 0; t < kFinePerLane; ++t)
                 if (!((vis >> t) & 1u)) md = fminf(md, fd[t]);
             for (int o = 16; o > 0; o >>= 1) md = fminf(md, __shfl_xor_sync(0xffffffffu, md, o));
-            if (md - f_d * A.rmax < dc) incomplete = true;
+            if (sqrtf(md) - f_d * A.rmax < dc) incomplete = true;
         }
     }
     if (f_d >= 1.0f && P.L1 > kCand) {
