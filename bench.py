@@ -46,7 +46,7 @@ TRAFFIC = {
     # (workload, mode): (source file under the package's csrc/, sha256, bytes per launch)
     # k_ann_gate + k_rank_small + k_ann_probe2 + k_leaf_scan of one search,
     # mean of the 10 timed steps (profiles/launches_cube32_N1e9_ann_4loads.md)
-    ("cube32_N1e9_ann_4loads", "ann"): ("ann.cu", "37800db4edc72ec8201d1324befdff3c3a12d98afe240f2470661fa7473ad70c",
+    ("cube32_N1e9_ann_4loads", "ann"): ("ann.cu", "d9fe69051be03a9269eaf8e5fb5535162394761f64fd2c7fd940d91b0c277f2c",
                                        4244073113),
 }
 

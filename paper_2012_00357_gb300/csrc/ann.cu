@@ -177,14 +177,12 @@ __global__ void k_radius(const float *__restrict__ zs, const int32_t *__restrict
 // ---------------------------------------------------------------------------
 // Query side
 // ---------------------------------------------------------------------------
-// Merge the top-k lists of the centroid scan; keep the kCand nearest
-// centroids by exact FP32 distance (ties to the lower centroid index).
 // Nearest kCand centroids of every listed query when the centroid set is
 // small: each thread ranks kRankQ queries, centroids staged in shared memory
-// and read as broadcasts (one read serves all of a thread's queries); top kCand by the
-// expanded FP32 score |c|^2 - 2 c.q (ties to the lower index), then ordered by
-// the FP32 distance as from k_ann_cands.  `list` (may be null: queries
-// 0..m-1) holds the *n_list queries to rank, in any order.
+// and read as broadcasts (one read serves all of a thread's queries); top
+// kCand by the expanded FP32 score |c|^2 - 2 c.q (ties to the lower index),
+// then ordered by the FP32 distance as from k_ann_cands.  `list` (may be
+// null: queries 0..m-1) holds the *n_list queries to rank, in any order.
 constexpr int kRankTile = 896;      // 896 x 52 B of static shared memory (< 48 KB)
 constexpr int kRankMax = 4096;    // larger sets go through the tiled FP32 scan
 constexpr int kRankQ = 1;         // queries per thread (two measured no faster)
@@ -283,6 +281,8 @@ __global__ void __launch_bounds__(256) k_rank_small(const QueryRec *__restrict__
     }
 }
 
+// Merge the top-k lists of the centroid scan; keep the kCand nearest
+// centroids by exact FP32 distance (ties to the lower centroid index).
 __global__ void k_ann_cands(const CandHeader *__restrict__ hdr, const float2 *__restrict__ cand, int splits, int cap,
                             const QueryRec *__restrict__ rec, int64_t m, const float *__restrict__ cent,
                             int32_t *__restrict__ out_cl, float *__restrict__ out_d) {
