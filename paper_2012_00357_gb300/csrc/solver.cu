@@ -199,15 +199,22 @@ size_t dd_solver_state_bytes(dd_ctx *ctx, const dd_mesh &mesh) {
 }
 
 // The host-side setup of sv's mesh (sv->g and sv->cb planned): computed on
-// the first solve of a data set on that mesh, then shared.
+// the first solve of a data set on that mesh, then shared; a data set keeps
+// the kSetupCache meshes used last (at most ~0.7 MB each).
+constexpr size_t kSetupCache = 64;
 static std::shared_ptr<const SolverSetup> solver_setup(dd_dataset *ds, const dd_solver *sv) {
     const MeshDev &g = sv->g;
     const dd_mesh &m = sv->mesh;
     std::lock_guard<std::mutex> lock(ds->setup_mu);
-    for (const auto &p : ds->setups)
+    for (size_t k = 0; k < ds->setups.size(); ++k) {
+        const auto p = ds->setups[k];
         if (p->nx == m.nx && p->ny == m.ny && p->nz == m.nz && p->top == g.top_fixed && p->lx == m.lx &&
-            p->ly == m.ly && p->lz == m.lz)
+            p->ly == m.ly && p->lz == m.lz) {
+            ds->setups.erase(ds->setups.begin() + (std::ptrdiff_t)k);   // most recently used last
+            ds->setups.push_back(p);
             return p;
+        }
+    }
     auto su = std::make_shared<SolverSetup>();
     su->nx = m.nx;
     su->ny = m.ny;
@@ -225,7 +232,7 @@ static std::shared_ptr<const SolverSetup> solver_setup(dd_dataset *ds, const dd_
     if (sv->cb.glev < sv->cb.nlev) fem_mg_coarse_inverse(sv->cb, su->St64.data(), su->Kinv);
     for (int cd = 0; cd < 27 * 27; ++cd)
         for (int k = 0; k < 9; ++k) su->St32[cd * 12 + k] = (float)su->St64[cd * 9 + k];
-    if (ds->setups.size() >= 16) ds->setups.erase(ds->setups.begin());
+    if (ds->setups.size() >= kSetupCache) ds->setups.erase(ds->setups.begin());   // least recently used
     ds->setups.push_back(su);
     return su;
 }
