@@ -570,18 +570,34 @@ void fem_mg_coarse_inverse(const CGBuffers &cb, const double *St, std::vector<fl
             L[(size_t)i * n + j] = v / d;
         }
     }
-    std::vector<double> Ainv((size_t)n * n, 0.0), y(n);
-    for (int col = 0; col < n; ++col) {
+    // columns in blocks of kB: each column takes the operations of a plain
+    // column-by-column solve in the same order (so the same bits), and the
+    // kB independent sums of a block keep the FMA units busy
+    constexpr int kB = 32;
+    std::vector<double> LT((size_t)n * n);
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) LT[(size_t)i * n + k] = L[(size_t)k * n + i];
+    std::vector<double> Ainv((size_t)n * n, 0.0), y((size_t)n * kB), x((size_t)n * kB);
+    for (int c0 = 0; c0 < n; c0 += kB) {
+        const int nb = std::min(kB, n - c0);
         for (int i = 0; i < n; ++i) {   // L y = e_col
-            double v = i == col ? 1.0 : 0.0;
-            for (int k = 0; k < i; ++k) v -= L[(size_t)i * n + k] * y[k];
-            y[i] = v / L[(size_t)i * n + i];
+            double v[kB];
+            for (int b = 0; b < kB; ++b) v[b] = (b < nb && i == c0 + b) ? 1.0 : 0.0;
+            const double *Li = &L[(size_t)i * n];
+            for (int k = 0; k < i; ++k)
+                for (int b = 0; b < kB; ++b) v[b] -= Li[k] * y[(size_t)k * kB + b];
+            for (int b = 0; b < kB; ++b) y[(size_t)i * kB + b] = v[b] / Li[i];
         }
         for (int i = n - 1; i >= 0; --i) {   // L^T x = y
-            double v = y[i];
-            for (int k = i + 1; k < n; ++k) v -= L[(size_t)k * n + i] * Ainv[(size_t)k * n + col];
-            Ainv[(size_t)i * n + col] = v / L[(size_t)i * n + i];
+            double v[kB];
+            for (int b = 0; b < kB; ++b) v[b] = y[(size_t)i * kB + b];
+            const double *Ti = &LT[(size_t)i * n];
+            for (int k = i + 1; k < n; ++k)
+                for (int b = 0; b < kB; ++b) v[b] -= Ti[k] * x[(size_t)k * kB + b];
+            for (int b = 0; b < kB; ++b) x[(size_t)i * kB + b] = v[b] / L[(size_t)i * n + i];
         }
+        for (int i = 0; i < n; ++i)
+            for (int b = 0; b < nb; ++b) Ainv[(size_t)i * n + c0 + b] = x[(size_t)i * kB + b];
     }
     inv.assign((size_t)n * n, 0.f);
     for (int i = 0; i < n; ++i)
