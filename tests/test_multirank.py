@@ -109,3 +109,24 @@ def test_sharded_search_merge_equals_unsharded(world):
     for o in outs:
         r = json.loads(o.strip().splitlines()[-1])
         assert r["same_index"] and r["same_d2"]
+
+
+def test_reference_arm_line_keeps_the_contract():
+    """One process: the reference arm's JSON line carries the keys its
+    contract names, on the arm's own workload, metric and unit."""
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                          "cube4_N1e4_exact_fp64", "--steps", "3", "--warmup", "3"], cwd=ROOT, capture_output=True,
+                         text=True, timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [json.loads(x) for x in out.stdout.splitlines() if x.startswith("{")]
+    assert len(lines) == 1
+    line = lines[0]
+    import bench
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["value"] > 0 and line["higher_is_better"] is True and line["steps"] == 3 and line["warmup"] == 3
+    assert line["config"]["workload"] == "cube4_N1e4_exact_fp64"
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and isinstance(cb["sample"], str)
+    e2e = line["e2e"]
+    assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
