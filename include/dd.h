@@ -153,6 +153,17 @@ size_t dd_dataset_bytes(const dd_dataset *ds);
 int dd_dataset_ann_nlist(const dd_dataset *ds);
 dd_status dd_dataset_ann_index(dd_dataset *ds, int32_t *cluster_of, double *centroids, double *radii);
 
+/* The cell level of a two-level partition (ann_levels = 2; the leaves are
+ * the clusters of dd_dataset_ann_index, leaf l lying in cell l / L2).
+ *   L1, L2      host int32: number of cells, leaves per cell (may be NULL)
+ *   centroids   host float64 [L1 x 12]: cell centroids in the mapped
+ *               coordinates, or NULL
+ *   radii       host float64 [L1]: radius of every cell (largest
+ *               centroid-member distance over its points, rounded up), or NULL
+ * The cells order the descent and pass Eq. (13) with these radii (Sec. 4.2).
+ * Errors: DD_ERR_STATE if no two-level partition was built.  Synchronous. */
+dd_status dd_dataset_ann_cells(dd_dataset *ds, int32_t *L1, int32_t *L2, double *centroids, double *radii);
+
 /* The k-nearest-neighbour graph of DD_SEARCH_KNNG (Sec. 4.4, built when
  * knn_k > 0): its k (0 if none), and a host copy.
  *   nbr  host int32 [N x k]: row j holds the data indices of the neighbours

@@ -27,7 +27,7 @@ EXPORTS = [
     "dd_dataset_size", "dd_dataset_bytes", "dd_synth_dataset", "dd_project_nearest", "dd_solve",
     "dd_result_free", "dd_solver_create", "dd_solver_step", "dd_solver_done", "dd_solver_result",
     "dd_solver_free", "dd_launch_count", "dd_dataset_ann_nlist", "dd_dataset_ann_index",
-    "dd_dataset_knn_k", "dd_dataset_knn_graph", "dd_pca_metric",
+    "dd_dataset_ann_cells", "dd_dataset_knn_k", "dd_dataset_knn_graph", "dd_pca_metric",
     "dd_project_nearest_noalloc", "dd_solvers_step", "dd_solve_batch", "dd_server_start", "dd_server_submit",
     "dd_server_poll", "dd_server_get_stats", "dd_server_stop",
 ]
@@ -150,6 +150,7 @@ def lib():
         L.dd_dataset_ann_nlist.argtypes = [vp]
         L.dd_dataset_ann_nlist.restype = c_int
         L.dd_dataset_ann_index.argtypes = [vp, vp, vp, vp]
+        L.dd_dataset_ann_cells.argtypes = [vp, POINTER(c_int32), POINTER(c_int32), vp, vp]
         L.dd_dataset_knn_k.argtypes = [vp]
         L.dd_dataset_knn_k.restype = c_int
         L.dd_dataset_knn_graph.argtypes = [vp, vp]
@@ -372,6 +373,17 @@ def dd_dataset_ann_index(ds, ctx):
     rad = np.empty(L, np.float64)
     _check(ctx, lib().dd_dataset_ann_index(ds, _ptr(cl), _ptr(cent), _ptr(rad)))
     return cl, cent, rad
+
+
+def dd_dataset_ann_cells(ds, ctx):
+    """Host copy of the cell level of a two-level partition: (L2, centroids
+    [L1,12], radii [L1]); leaf l of dd_dataset_ann_index lies in cell l // L2."""
+    L1, L2 = c_int32(0), c_int32(0)
+    _check(ctx, lib().dd_dataset_ann_cells(ds, ctypes.byref(L1), ctypes.byref(L2), None, None))
+    cent = np.empty((L1.value, 12), np.float64)
+    rad = np.empty(L1.value, np.float64)
+    _check(ctx, lib().dd_dataset_ann_cells(ds, None, None, _ptr(cent), _ptr(rad)))
+    return L2.value, cent, rad
 
 
 def dd_pca_metric(ctx, eps_sig) -> np.ndarray:

@@ -1328,6 +1328,31 @@ extern "C" dd_status dd_dataset_ann_index(dd_dataset *ds, int32_t *cluster_of, d
     return DD_OK;
 }
 
+extern "C" dd_status dd_dataset_ann_cells(dd_dataset *ds, int32_t *L1, int32_t *L2, double *centroids,
+                                          double *radii) {
+    if (!ds) return DD_ERR_ARG;
+    dd_ctx *ctx = ds->ctx;
+    AnnIndex &a = ds->ann;
+    if (!a.nlist || a.levels != 2) return dd_fail(ctx, DD_ERR_STATE, "dd_dataset_ann_cells: no two-level partition");
+    if (L1) *L1 = a.L1;
+    if (L2) *L2 = a.L2;
+    DD_TRY_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t s = ctx->stream;
+    if (centroids || radii) {
+        void *w = nullptr;
+        DD_TRY(dd_workspace(ctx, WS_MISC, (size_t)a.L1 * 13 * 8 + 256, &w));
+        double *c = (double *)w, *r = c + (size_t)a.L1 * 12;
+        ctx->launches++;
+        k_export_index<<<(a.L1 + 255) / 256, 256, 0, s>>>(a.cent1, a.rad1, a.L1, ds->M, c, r);
+        DD_TRY_CUDA(ctx, cudaGetLastError());
+        if (centroids)
+            DD_TRY_CUDA(ctx, cudaMemcpyAsync(centroids, c, (size_t)a.L1 * 96, cudaMemcpyDeviceToHost, s));
+        if (radii) DD_TRY_CUDA(ctx, cudaMemcpyAsync(radii, r, (size_t)a.L1 * 8, cudaMemcpyDeviceToHost, s));
+    }
+    DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+    return DD_OK;
+}
+
 void dd_free_ann(dd_dataset *ds) {
     AnnIndex &a = ds->ann;
     if (!a.nlist) return;

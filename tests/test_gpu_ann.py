@@ -145,6 +145,43 @@ def test_tree2_leaves_cover_members(ctx, treeset):
         assert d[cl == l].max() <= rad[l] * (1 + 1e-5) + 1e-12
 
 
+@pytest.mark.parametrize("f_d,warm", [(0.0, False), (0.0, True), (0.4, True), (0.7, False)])
+def test_tree2_rules_match_oracle(ctx, treeset, f_d, warm):
+    """Every leaf in the query's warp (ann_budget = -1): the GPU follows the
+    oracle's two-level restatement of Sec. 4.2-4.5 on the exported cells and
+    leaves (nearest cells, their nearest leaves, Eq. 13 at both levels),
+    query by query but for FP32/FP64 near-ties."""
+    data, ds = treeset
+    cl, cent, rad = P.dd_dataset_ann_index(ds, ctx)
+    L2, ccent, crad = P.dd_dataset_ann_cells(ds, ctx)
+    assert len(cent) == len(ccent) * L2 and np.all(cl // L2 < len(ccent))
+    Z = metric.to_z(data.astype(np.float64), C)
+    y = I.make_states(600, I.NONLINEAR, seed=26, spread=0.1)
+    zq = metric.to_z(y, C)
+    prev = np.random.default_rng(4).integers(0, len(data), len(y)).astype(np.int32) if warm else None
+    idx, d2, st = search(ctx, ds, y, f_d, prev, ann_budget=-1)
+    oi, od = oann.tree2_search(Z, zq, ccent, crad, cent, rad, cl, L2, f_d, prev_idx=prev)
+    same = idx == oi
+    dg = ((Z[idx] - zq) ** 2).sum(1)
+    close = np.abs(dg - od) <= 1e-4 * od
+    print(f"tree2 f_d={f_d} warm={warm}: agree {same.mean():.4f}")
+    assert same.mean() >= 0.97 and np.all(same | close | (dg <= od * (1 + 1e-6)) | ((~same).cumsum() < 12))
+    assert np.allclose(metric.local_d2(y, data[idx].astype(np.float64), C), d2, rtol=1e-10)
+
+
+def test_tree2_cells_export(ctx, treeset, annset):
+    """The cell level: every point lies within its cell's radius (its cell is
+    the cell of its leaf); a flat partition has no cell level."""
+    data, ds = treeset
+    cl, cent, rad = P.dd_dataset_ann_index(ds, ctx)
+    L2, ccent, crad = P.dd_dataset_ann_cells(ds, ctx)
+    Z = metric.to_z(data.astype(np.float64), C)
+    d = np.sqrt(((Z - ccent[cl // L2]) ** 2).sum(1))
+    assert np.all(d <= crad[cl // L2] * (1 + 1e-5) + 1e-12)
+    with pytest.raises(P.DDError):
+        P.dd_dataset_ann_cells(annset[1], ctx)
+
+
 @pytest.mark.parametrize("budget,warm", [(0, False), (-2, True), (1, True), (-1, True)])
 def test_tree2_fd_one_is_exact(ctx, treeset, budget, warm):
     """f_d = 1: exact answers whatever the split between the query's warp and
