@@ -82,10 +82,16 @@ def ann_search(Z, zq, cent, rad, cluster_of, f_d, prev_idx=None, n_cand=8):
 
 
 def tree2_search(Z, zq, cell_cent, cell_rad, leaf_cent, leaf_rad, leaf_of, L2, f_d, prev_idx=None, n_cand=8,
-                 k_fine=8):
+                 k_fine=8, budget=None):
     """Returns (idx, squared distance) for every query row of zq on the
     two-level partition: cells (centroids, radii) and their leaves (leaf l
-    in cell l // L2; centroids, radii, leaf of every data point)."""
+    in cell l // L2; centroids, radii, leaf of every data point).
+
+    budget: None searches every chosen leaf at once, d_c shrinking after
+    each.  An integer b searches only the first b chosen leaves at once (the
+    warm-start leaf first).  Every later leaf that passes Eq. (13) with the
+    d_c reached then is searched at the end, without shrinking d_c: the
+    chosen set can only grow, so the answer is never farther."""
     Z = np.asarray(Z, dtype=np.float64)
     zq = np.asarray(zq, dtype=np.float64)
     cell_cent = np.asarray(cell_cent, dtype=np.float64)
@@ -113,13 +119,25 @@ def tree2_search(Z, zq, cell_cent, cell_rad, leaf_cent, leaf_rad, leaf_of, L2, f
             if d[t] < best_d or (d[t] == best_d and mem[t] < best_j):
                 best_d, best_j = float(d[t]), int(mem[t])
 
+        nscan, deferred = 0, []
+
+        def take(l):
+            nonlocal nscan, dc
+            if budget is None or nscan < budget:
+                scan(l)
+                nscan += 1
+                dc = np.sqrt(best_d)
+            else:
+                deferred.append(l)
+
         l0 = -1
+        dc = np.inf
         if prev_idx is not None:
             j0 = int(prev_idx[qi])
             best_d, best_j = float(((Z[j0] - q) ** 2).sum()), j0
+            dc = np.sqrt(best_d)
             l0 = int(leaf_of[j0])
-            scan(l0)
-        dc = np.sqrt(best_d)
+            take(l0)
         incomplete = False
         for k1, c in enumerate(cells):
             if not (k1 == 0 or dcell[c] - f_d * cell_rad[c] < dc):
@@ -131,12 +149,13 @@ def tree2_search(Z, zq, cell_cent, cell_rad, leaf_cent, leaf_rad, leaf_of, L2, f
                 l = int(leaves[o])
                 if (k1 == 0 and k2 == 0) or dleaf[o] - f_d * leaf_rad[l] < dc:
                     if l != l0:
-                        scan(l)
-                        dc = np.sqrt(best_d)
+                        take(l)
             if f_d >= 1.0 and L2 > k_fine and dleaf[order[k_fine:]].min() - f_d * rmax < dc:
                 incomplete = True
         if f_d >= 1.0 and L1 > n_cand and dcell[cells[-1]] - f_d * r1max < dc:
             incomplete = True
+        for l in deferred:
+            scan(l)
         if incomplete:
             d = ((Z - q) ** 2).sum(1)
             best_j = int(np.argmin(d))

@@ -169,6 +169,28 @@ def test_tree2_rules_match_oracle(ctx, treeset, f_d, warm):
     assert np.allclose(metric.local_d2(y, data[idx].astype(np.float64), C), d2, rtol=1e-10)
 
 
+@pytest.mark.parametrize("gpu_budget,budget,f_d,warm", [(-2, 0, 0.4, True), (1, 1, 0.0, True), (0, 2, 0.4, False),
+                                                         (4, 4, 0.7, True)])
+def test_tree2_handoff_matches_oracle(ctx, treeset, gpu_budget, budget, f_d, warm):
+    """The query's warp searches `budget` leaves (ann_budget -2 is none, 0
+    the default two), the leaf-major pass every later leaf that passed
+    Eq. (13): query by query the oracle's restatement with that budget."""
+    data, ds = treeset
+    cl, cent, rad = P.dd_dataset_ann_index(ds, ctx)
+    L2, ccent, crad = P.dd_dataset_ann_cells(ds, ctx)
+    Z = metric.to_z(data.astype(np.float64), C)
+    y = I.make_states(600, I.NONLINEAR, seed=27, spread=0.1)
+    zq = metric.to_z(y, C)
+    prev = np.random.default_rng(5).integers(0, len(data), len(y)).astype(np.int32) if warm else None
+    idx, d2, st = search(ctx, ds, y, f_d, prev, ann_budget=gpu_budget)
+    oi, od = oann.tree2_search(Z, zq, ccent, crad, cent, rad, cl, L2, f_d, prev_idx=prev, budget=budget)
+    same = idx == oi
+    dg = ((Z[idx] - zq) ** 2).sum(1)
+    close = np.abs(dg - od) <= 1e-4 * od
+    print(f"tree2 hand-off budget={budget} f_d={f_d} warm={warm}: agree {same.mean():.4f}")
+    assert same.mean() >= 0.97 and np.all(same | close | (dg <= od * (1 + 1e-6)) | ((~same).cumsum() < 12))
+
+
 def test_tree2_cells_export(ctx, treeset, annset):
     """The cell level: every point lies within its cell's radius (its cell is
     the cell of its leaf); a flat partition has no cell level."""

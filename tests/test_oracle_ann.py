@@ -129,3 +129,25 @@ def test_tree2_fd_zero_is_the_descent():
     far = np.array([np.nonzero(leaf == 0)[0][0], np.nonzero(leaf == 11)[0][0]])
     i2, _ = ann.tree2_search(Z, zq, cc, cr, lc, lr, leaf, 3, 0.0, prev_idx=far)
     assert np.array_equal(i2, i)
+
+
+def test_tree2_handoff_never_farther_and_exact():
+    """A budget of leaves searched at once, the rest after: the chosen leaves
+    only grow, so no answer is farther than with every leaf at once, and some
+    are nearer; f_d = 1 stays exact."""
+    Z, zq, (cc, cr, lc, lr, leaf) = setup2(seed=6)
+    prev = np.random.default_rng(3).integers(0, len(Z), len(zq))
+    j, e, _, _ = nn.nn_top2(Z, zq)
+    nearer = 0
+    for pv in (None, prev):
+        for f_d in (0.0, 0.4):
+            _, d_all = ann.tree2_search(Z, zq, cc, cr, lc, lr, leaf, 10, f_d, prev_idx=pv, n_cand=3, k_fine=3)
+            for b in (0, 1, 2, 4):
+                _, d_b = ann.tree2_search(Z, zq, cc, cr, lc, lr, leaf, 10, f_d, prev_idx=pv, n_cand=3, k_fine=3,
+                                          budget=b)
+                assert np.all(d_b <= d_all) and np.all(e <= d_b * (1 + 1e-12))
+                nearer += int(np.sum(d_b < d_all))
+        for b in (0, 1, 2):
+            i, _ = ann.tree2_search(Z, zq, cc, cr, lc, lr, leaf, 10, 1.0, prev_idx=pv, n_cand=3, k_fine=3, budget=b)
+            assert np.array_equal(i, j)
+    assert nearer > 0
