@@ -22,6 +22,12 @@ data index is taken; the second distance reported for the moving-query radius
 of Eq. (14) is the smallest distance of any evaluated point other than the
 answer, and a walk stopped by f_s reports the answer's own distance there
 (radius 0: its answer is not a local minimum, so it is not kept unsearched).
+A walk that ended at a local minimum p1 evaluated every neighbour of p1, so
+that second distance bounds them from below; a query that moves by less than
+the Eq. (14) radius is then still strictly nearer to p1 than to any of them,
+and the walk from the warm start p1 would stay at p1.  The skip therefore
+returns exactly what the walk would (not the exact nearest point, which the
+walk does not promise either); tests/test_oracle_knng.py pins this.
 """
 from __future__ import annotations
 

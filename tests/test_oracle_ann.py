@@ -151,3 +151,132 @@ def test_tree2_handoff_never_farther_and_exact():
             i, _ = ann.tree2_search(Z, zq, cc, cr, lc, lr, leaf, 10, 1.0, prev_idx=pv, n_cand=3, k_fine=3, budget=b)
             assert np.array_equal(i, j)
     assert nearer > 0
+
+
+# ---------------------------------------------------------------------------
+# Eq. (14): the moving-query skip and the second bound it needs
+# ---------------------------------------------------------------------------
+def moved(zq, scale, seed):
+    """Queries displaced by random steps of plain length scale * U(0, 1)."""
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal(zq.shape)
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    return zq + v * (scale * rng.random((len(zq), 1)))
+
+
+def test_second_bound_below_brute_force_second_at_fd_one():
+    """At f_d = 1 the second bound never exceeds the distance of the
+    brute-force second-nearest point (C scan), flat and two-level, with
+    short candidate lists, warm and cold; and it is not vacuous."""
+    Z, zq, cent, rad, cl = setup(seed=8)
+    Z2, zq2, part = setup2(seed=9)
+    prev = np.random.default_rng(6).integers(0, len(Z), len(zq))
+    j, e, _, e2 = nn.nn_top2(Z, zq)
+    j2, f, _, f2 = nn.nn_top2(Z2, zq2)
+    tight = 0
+    for pv in (None, prev):
+        for n_cand in (3, 8, 24):
+            i, d, s = ann.ann_search(Z, zq, cent, rad, cl, 1.0, prev_idx=pv, n_cand=n_cand, with_second=True)
+            assert np.array_equal(i, j) and np.all(s <= e2 * (1 + 1e-12))
+            tight += int(np.sum(s > d))
+        i, d, s = ann.tree2_search(Z2, zq2, *part, 10, 1.0, prev_idx=None if pv is None else pv % len(Z2),
+                                   n_cand=3, k_fine=3, with_second=True)
+        assert np.array_equal(i, j2) and np.all(s <= f2 * (1 + 1e-12))
+        tight += int(np.sum(s > d))
+    assert tight > 0
+
+
+def test_kept_answers_equal_brute_force_at_fd_one():
+    """A search at f_d = 1, then the queries moved by steps around the Eq. (14)
+    radius: every query the record keeps gets the brute-force nearest point of
+    its new position, flat and two-level."""
+    Z, zq, cent, rad, cl = setup(N=4000, L=16, seed=10)
+    Z2, zq2, part = setup2(seed=11)
+    kept = 0
+    for k, (search, ZZ, qq) in enumerate((
+            (lambda q, **kw: ann.ann_search(Z, q, cent, rad, cl, 1.0, n_cand=4, **kw), Z, zq),
+            (lambda q, **kw: ann.tree2_search(Z2, q, *part, 10, 1.0, n_cand=3, k_fine=3, **kw), Z2, zq2))):
+        i1, d1, s1 = search(qq, with_second=True)
+        delta = 0.5 * (np.sqrt(s1) - np.sqrt(d1))
+        for scale in (0.5, 1.0, 2.0):
+            q2 = moved(qq, scale * np.median(delta), seed=20 + k)
+            keep = np.array([ann.moving_query_keeps(q2[t], qq[t], d1[t], s1[t])[0] for t in range(len(qq))])
+            i2, d2, s2 = search(q2, prev_idx=i1, motion=(qq, d1, s1, 1.0), with_second=True)
+            j, e, _, e2 = nn.nn_top2(ZZ, q2)
+            assert np.array_equal(i2, j)
+            assert np.all(s2 <= e2 * (1 + 1e-12))
+            kept += int(keep.sum())
+    assert kept > 0
+
+
+def line_case():
+    """Points on the first axis: cluster A = {0.1, 1.0}, cluster B =
+    {-0.3, -5.0}; query at 0.  The nearest point is 0.1 (A); the second
+    nearest is -0.3, in B, which Eq. (13) prunes at f_d = 1 (centroid -2.65,
+    radius 2.35: 2.65 - 2.35 = 0.3 >= d_c = 0.1)."""
+    x = np.array([0.1, 1.0, -0.3, -5.0])
+    Z = np.zeros((4, 12))
+    Z[:, 0] = x
+    cl = np.array([0, 0, 1, 1])
+    cent = np.zeros((2, 12))
+    cent[:, 0] = [0.55, -2.65]
+    rad = np.array([0.45, 2.35])
+    q = np.zeros((1, 12))
+    return Z, q, cent, rad, cl
+
+
+def test_second_nearest_in_a_pruned_cluster():
+    """The search reads only cluster A, so the second-best of the points read
+    is 1.0 (radius (1.0 - 0.1)/2 = 0.45); a move to -0.25 (0.25 < 0.45) would
+    keep 0.1 although -0.3 is then nearer (0.05 < 0.35).  The bound of the
+    pruned cluster gives the second bound 0.3 (radius 0.1): the move is not
+    kept and the search finds -0.3.  The same with B a leaf of one cell."""
+    Z, q, cent, rad, cl = line_case()
+    i, d, s = ann.ann_search(Z, q, cent, rad, cl, 1.0, with_second=True)
+    assert i[0] == 0 and np.isclose(d[0], 0.01) and np.isclose(s[0], 0.09)
+    q2 = q.copy()
+    q2[0, 0] = -0.25
+    # the rule on the points read would keep the stale answer
+    assert ann.moving_query_keeps(q2[0], q[0], d[0], 1.0)[0]
+    assert np.argmin(((Z - q2[0]) ** 2).sum(1)) == 2
+    keep, mv = ann.moving_query_keeps(q2[0], q[0], d[0], s[0])
+    assert not keep and np.isclose(mv, 0.25)
+    i2, d2 = ann.ann_search(Z, q2, cent, rad, cl, 1.0, prev_idx=i, motion=(q, d, s, 1.0))
+    assert i2[0] == 2 and np.isclose(d2[0], 0.05 ** 2)
+    # two levels: one cell holding A and B as leaves
+    cc = Z.mean(0, keepdims=True)
+    cr = np.array([np.sqrt(((Z - cc) ** 2).sum(1)).max()])
+    i, d, s = ann.tree2_search(Z, q, cc, cr, cent, rad, cl, 2, 1.0, with_second=True)
+    assert i[0] == 0 and np.isclose(s[0], 0.09)
+    i2, _ = ann.tree2_search(Z, q2, cc, cr, cent, rad, cl, 2, 1.0, prev_idx=i, motion=(q, d, s, 1.0))
+    assert i2[0] == 2
+
+
+def test_second_bound_scales_with_fd_and_records_are_not_used_above_their_fd():
+    """At f_d = 0.5 cluster B counts with half its radius: bound
+    2.65 - 1.175 = 1.475 > 1.0, so the second bound is the read 1.0.  That
+    record keeps the move to -0.25 at f_d = 0.5 (the search at 0.5 from the
+    warm start also prunes B and answers 0.1), but a search at f_d = 1 does
+    not use it and finds the exact -0.3."""
+    Z, q, cent, rad, cl = line_case()
+    i, d, s = ann.ann_search(Z, q, cent, rad, cl, 0.5, with_second=True)
+    assert i[0] == 0 and np.isclose(s[0], 1.0)
+    _, _, s0 = ann.ann_search(Z, q, cent, rad, cl, 0.0, with_second=True)
+    assert np.isclose(s0[0], 1.0)                           # B's bound 2.65
+    q2 = q.copy()
+    q2[0, 0] = -0.25
+    rec = (q, d, s, 0.5)
+    k5, d5, s5 = ann.ann_search(Z, q2, cent, rad, cl, 0.5, prev_idx=i, motion=rec, with_second=True)
+    assert k5[0] == 0 and np.isclose(d5[0], 0.35 ** 2) and np.isclose(s5[0], (1.0 - 0.25) ** 2)
+    assert ann.ann_search(Z, q2, cent, rad, cl, 0.5, prev_idx=i)[0][0] == 0
+    assert ann.ann_search(Z, q2, cent, rad, cl, 1.0, prev_idx=i, motion=rec)[0][0] == 2
+
+
+def test_one_leaf_per_cell_second_bound_is_the_flat_one():
+    Z, zq, cent, rad, cl = setup(seed=12)
+    prev = np.random.default_rng(2).integers(0, len(Z), len(zq))
+    for f_d in (0.0, 0.5, 1.0):
+        for pv in (None, prev):
+            a = ann.ann_search(Z, zq, cent, rad, cl, f_d, prev_idx=pv, n_cand=8, with_second=True)
+            b = ann.tree2_search(Z, zq, cent, rad, cent, rad, cl, 1, f_d, prev_idx=pv, n_cand=8, with_second=True)
+            assert all(np.array_equal(x, y) for x, y in zip(a, b))

@@ -94,3 +94,38 @@ def test_walk_ends_in_a_local_minimum_and_never_worse():
     g16 = knng.knn_graph(Z, 16)
     j16 = knng.walk_all(Z, g16, zq, starts)[0]
     assert 0.05 < np.mean(j == i1) < np.mean(j16 == i1) < 1.0
+
+
+def test_eq14_keep_reproduces_the_walk_from_the_warm_start():
+    """A walk that ended at a local minimum p1 evaluated every neighbour of
+    p1, so its second distance s bounds them from below.  A query that then
+    moves by less than (sqrt(s) - sqrt(d1)) / 2 (Eq. 14) is still strictly
+    nearer to p1 than to any neighbour of p1, so the walk from the warm start
+    p1 stays there: the skip returns what the walk would.  Moves just beyond
+    the radius do change some answers (the radius is not vacuous)."""
+    data = I.make_dataset(1200, I.NONLINEAR, seed=10)
+    Z = metric.to_z(data.astype(np.float64), I.isotropic_C())
+    g = knng.knn_graph(Z, 6)
+    y = I.make_states(150, I.NONLINEAR, seed=11, spread=0.1)
+    zq = metric.to_z(y, I.isotropic_C())
+    starts = np.random.default_rng(3).integers(0, len(Z), len(zq))
+    rng = np.random.default_rng(4)
+    kept = changed = 0
+    for i in range(len(zq)):
+        j, d, s, moves, _ = knng.greedy_walk(Z, g, zq[i], int(starts[i]))
+        delta = 0.5 * (np.sqrt(s) - np.sqrt(d))
+        if not delta > 0:
+            continue
+        for scale in (0.3, 0.999):
+            v = rng.standard_normal(12)
+            q2 = zq[i] + v / np.linalg.norm(v) * delta * scale
+            j2, _, _, m2, _ = knng.greedy_walk(Z, g, q2, j)
+            assert j2 == j and m2 == 0
+            kept += 1
+        # the nearest other point at 3 delta: moving towards it can flip the answer
+        nb = [int(t) for t in g[j]]
+        dn = ((Z[nb] - zq[i]) ** 2).sum(1)
+        far = nb[int(np.argmin(dn))]
+        u = (Z[far] - zq[i]) / np.linalg.norm(Z[far] - zq[i])
+        changed += int(knng.greedy_walk(Z, g, zq[i] + u * 3 * delta, j)[0] != j)
+    assert kept > 0 and changed > 0
