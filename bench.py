@@ -38,26 +38,26 @@ UNIT = "searches/s"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 L2_BYTES = 129 * 2 ** 20
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per search of
-# the dominant kernels, from one-pass ncu captures of the same workload and
-# mode, keyed by the sha256 of the kernels' source file: a changed source
-# reports null until it is captured again.
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant
+# kernels of one search, from ncu captures of a smaller case of the same mode,
+# keyed by the sha256 of the kernels' source file (a changed source reports
+# null until it is captured again).  A bench run scales the captured bytes by
+# the ratio of its own data points read per search to the capture's.
 TRAFFIC = {
-    # (workload, mode): (source file under the package's csrc/, sha256, bytes per launch)
-    # k_ann_gate + k_rank_small + k_ann_probe2 + k_leaf_scan of one search,
-    # mean of the 10 timed steps (profiles/launches_cube32_N1e9_ann_4loads.md)
-    ("cube32_N1e9_ann_4loads", "ann"): ("ann.cu", "d9fe69051be03a9269eaf8e5fb5535162394761f64fd2c7fd940d91b0c277f2c",
-                                       4244073113),
+    # mode: (source file under the package's csrc/, sha256, DRAM bytes per
+    #        search, data points read per search, the captured case)
 }
 
 
-def captured_traffic(workload: str, mode: str):
-    t = TRAFFIC.get((workload, mode))
+def captured_traffic(mode: str, points_now: float):
+    t = TRAFFIC.get(mode)
     if t is None:
         return None
-    path, sha, byts = t
+    path, sha, byts, pts, _ = t
     with open(os.path.join(ROOT, "paper_2012_00357_gb300", "csrc", path), "rb") as f:
-        return byts if hashlib.sha256(f.read()).hexdigest() == sha else None
+        if hashlib.sha256(f.read()).hexdigest() != sha:
+            return None
+    return byts * points_now / pts
 
 
 def load_peaks():
@@ -222,7 +222,7 @@ def run_ours(args, world, rank, local):
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     data_bytes = W.N * (64 if mode == P.DD_SEARCH_EXACT_TC else 52 if mode == P.DD_SEARCH_EXACT_FP32 else 48)
     ann_kw = dict(f_d0=args.fd0, f_d_final=args.fd_final, ramp_iters=args.ramp_iters,
-                  ann_budget=args.ann_budget) if mode == P.DD_SEARCH_ANN else {}
+                  ann_budget=args.ann_budget, eq14=args.eq14) if mode == P.DD_SEARCH_ANN else {}
     if mode == P.DD_SEARCH_KNNG:
         ann_kw = dict(f_s=args.f_s)
     flush_l2 = data_bytes < 2 * L2_BYTES
@@ -230,18 +230,18 @@ def run_ours(args, world, rank, local):
     loads = [I.load_case(*lc) for lc in W.loads]
     nload = len(loads)
 
-    def new_solver(k=0):
+    def new_solver(k=0, kw=None):
         return P.dd_solver_create(ds, ctx, W.n_el, loads[k], mode=mode, certify=certify, init_idx=init,
-                                  max_iter=100000, **ann_kw)
+                                  max_iter=100000, **(ann_kw if kw is None else kw))
 
     svs = [new_solver(k) for k in range(nload)]
 
-    def step():
+    def step(svs=svs, kw=None):
         """One iteration of every load case (one batched call when there are several)."""
         for k in range(nload):
             if P.dd_solver_done(svs[k]):
                 P.dd_solver_free(svs[k])
-                svs[k] = new_solver(k)
+                svs[k] = new_solver(k, kw)
         if nload == 1:
             return [P.dd_solver_step(svs[0], ctx)]
         return P.dd_solvers_step(svs, ctx)
@@ -277,6 +277,27 @@ def run_ours(args, world, rank, local):
     total_ms = max_over_ranks(total_ms, world)
     searches = W.m * nload * args.steps * world
     value = searches / (total_ms / 1e3)
+
+    # the other Eq. (14) rule over the same iteration window (fresh solves,
+    # the same warm-up and timed steps), reported beside the headline
+    eq14_other = None
+    if mode == P.DD_SEARCH_ANN and not args.no_eq14_compare:
+        kw2 = dict(ann_kw, eq14=1 - args.eq14)
+        svs2 = [new_solver(k, kw2) for k in range(nload)]
+        for _ in range(args.warmup):
+            step(svs2, kw2)
+        infos2 = []
+        for _ in range(args.steps):
+            if flush_l2:
+                flush.fill_(1.0)
+            infos2.append(step(svs2, kw2)[0])
+        for sv in svs2:
+            P.dd_solver_free(sv)
+        ms2 = sum(i.cg_ms + i.other_ms + i.search_ms for i in infos2)
+        eq14_other = {"eq14": "certified second bound" if kw2["eq14"] == 0 else "second-closest point found",
+                      "value": W.m * nload * args.steps / (ms2 / 1e3), "unit": UNIT, "ms_per_step": ms2 / args.steps,
+                      "scan_ms_per_step": statistics.mean(i.scan_ms for i in infos2),
+                      "skipped": sum(i.skipped for i in infos2)}
 
     # full solve from the random association (all load cases together,
     # outside the timed steps) through the public call, host arrays in and
@@ -324,6 +345,29 @@ def run_ours(args, world, rank, local):
                     "exact": "tensor-core split-FP16 scan, certified" if exact_tc else "FP32 scan, certified",
                     "exact_searches_per_s": len(pick) / t_ex, "exact_uncertified": int(st_ex.uncertified)}
 
+    # the metric's "solve time at N (ANN vs exact)": one load case solved with
+    # the certified tensor-core exact search and with the approximate search,
+    # from the same initial association (opt-in: the exact solve at 10^9
+    # points takes minutes)
+    exact_solve = None
+    if approx and args.exact_solve and exact_tc:
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        ra1 = P.dd_solve(ds, ctx, W.n_el, loads[0], mode=mode, certify=certify, init_idx=init_pin, max_iter=200,
+                         **ann_kw)
+        ta1 = time.perf_counter() - t
+        t = time.perf_counter()
+        rx = P.dd_solve(ds, ctx, W.n_el, loads[0], mode=P.DD_SEARCH_EXACT_TC, certify=True, init_idx=init_pin,
+                        max_iter=200)
+        tx = time.perf_counter() - t
+        exact_solve = {"load": W.loads[0][0], "exact": "tensor-core split-FP16 scan + FP64 rescoring, certified",
+                       "exact_solve_s": tx, "exact_iters": rx.iters, "exact_converged": rx.converged,
+                       "exact_d2": float(rx.d2_pd[-1]), "exact_uncertified": int(rx.uncertified),
+                       "exact_searches_per_s": W.m * rx.iters / (rx.search_ms / 1e3),
+                       "ann_solve_s": ta1, "ann_iters": ra1.iters, "ann_d2": float(ra1.d2_pd[-1]),
+                       "ann_rel_d2_vs_exact": float((ra1.d2_pd[-1] - rx.d2_pd[-1]) / rx.d2_pd[-1]),
+                       "speedup": tx / ta1}
+
     # end-to-end through the public API with host buffers (pinned): one
     # projection of the step's m states per call, copies inside the timed region
     m_e2e = W.m * nload
@@ -341,26 +385,46 @@ def run_ours(args, world, rank, local):
     peaks = load_peaks()
     kc = 3 if (mode == P.DD_SEARCH_EXACT_TC and certify) else 1
     scan_avg = statistics.mean(scan_ms)
+    clk_sum = clk.summary()
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    clk_mhz = clk_sum.get("sm_mhz") or 1920.0
+    # FP32 lane operations per second of the device (one FFMA or FADD per
+    # lane per clock), from its SM count and the clock sampled while timing
+    alu_peak = n_sm * 128 * clk_mhz * 1e6
+    alu_src = f"{n_sm} SMs x 128 FP32 lanes x {clk_mhz:.0f} MHz (median SM clock sampled while timing)"
     if mode == P.DD_SEARCH_ANN:
-        # centroid ranking + warp scans of the probed clusters.  Algorithmic
-        # bytes per launch = the probed clusters' points of every non-skipped
-        # query x 48 B + 48 B per query.  Clusters probed by several queries
-        # come from L1/L2, so the rate can pass the HBM copy bandwidth; the
-        # distinct clusters read (each must come from memory at least once)
-        # are reported beside it.
-        unique = statistics.mean(i.unique_points for i in infos)
-        scanned = statistics.mean(i.points for i in infos)
-        byts = scanned * 48 + W.m * nload * 48
-        achieved = byts / (scan_avg / 1e3) / 1e9
-        roof = {"kernel": ("k_ann_gate + k_rank_small + k_ann_probe2 + k_leaf_scan (per step)" if levels == 2
-                           else "k_ann_probe + centroid scan"),
-                "bound": "hbm", "achieved": achieved,
-                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                "traffic": captured_traffic(W.name, args.mode),
-                "peak_source": f"{peaks['source']} copy bandwidth",
-                "algorithmic": "48 B x points of the clusters each non-skipped query probed + 48 B x queries, per launch",
-                "distinct_gbs": (unique * 48 + W.m * nload * 48 + nlist * 52) / (scan_avg / 1e3) / 1e9,
-                "algorithmic_bytes": byts}
+        # The search is bound by SM work, not by HBM: per step it evaluates
+        # ~10^4 distances per query, most of them on leaves that L1/L2 serve.
+        # Lane operations: 24 per distance to a data point or a leaf centroid
+        # (12 differences, 12 FMA), 12 per coarse-cell distance (expanded
+        # form |c|^2 - 2 c.q).  The survey's HBM figure (48 B per probed point)
+        # and the measured DRAM traffic are reported beside it.
+        nq = W.m * nload
+        Lr = P.dd_dataset_ann_cells(ds, ctx)[1].shape[0] if levels == 2 else nlist
+        points = statistics.mean(i.points for i in infos)
+        dists = statistics.mean(i.distances for i in infos)
+        cells = statistics.mean((nq - i.skipped) * Lr for i in infos)
+        leafc = max(0.0, dists - points - cells)
+        lane_ops = 24 * (points + leafc) + 12 * cells
+        achieved = lane_ops / (scan_avg / 1e3)
+        byts = points * 48 + nq * 48
+        traffic = captured_traffic(args.mode, points)
+        roof = {"kernel": ("k_ann_gate + k_rank_small + k_ann_probe2 + k_leaf_scan (one search per step)"
+                           if levels == 2 else "k_ann_probe + centroid ranking (one search per step)"),
+                "bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12, "unit": "T FP32 lane-ops/s",
+                "frac": achieved / alu_peak, "traffic": traffic, "peak_source": alu_src,
+                "algorithmic": "24 lane-ops per point or leaf-centroid distance + 12 per coarse-cell distance, "
+                               "per search (the step's one launch sequence)",
+                "lane_ops": lane_ops, "distances": {"points": points, "leaf_centroids": leafc, "cells": cells},
+                "hbm": {"algorithmic_bytes": byts,
+                        "algorithmic": "48 B x points of the clusters each non-skipped query probed + 48 B x "
+                                       "queries (most served by L1/L2, so not an HBM rate)",
+                        "algorithmic_gbs": byts / (scan_avg / 1e3) / 1e9,
+                        "dram_gbs": None if traffic is None else traffic / (scan_avg / 1e3) / 1e9,
+                        "dram_frac": None if traffic is None else traffic / (scan_avg / 1e3) / 1e9 / peaks["hbm_gbs"],
+                        "peak": peaks["hbm_gbs"], "peak_source": f"{peaks['source']} copy bandwidth",
+                        "distinct_gbs": (statistics.mean(i.unique_points for i in infos) * 48 + nq * 48 + nlist * 52)
+                                        / (scan_avg / 1e3) / 1e9}}
     elif mode == P.DD_SEARCH_KNNG:
         # greedy walks: every evaluated neighbour costs its 4 B index and its
         # 48 B row, every query its 48 B record
@@ -368,25 +432,31 @@ def run_ours(args, world, rank, local):
         byts = evals * 52 + W.m * nload * 48
         achieved = byts / (scan_avg / 1e3) / 1e9
         roof = {"kernel": "k_knng_walk", "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": captured_traffic(W.name, args.mode),
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": captured_traffic(args.mode, evals),
                 "peak_source": f"{peaks['source']} copy bandwidth",
                 "algorithmic": "52 B x neighbours evaluated + 48 B x queries, per launch", "algorithmic_bytes": byts}
     elif mode == P.DD_SEARCH_EXACT_TC:
-        flops = 2.0 * W.m * W.N * 16 * kc
+        # method work: one K = 16 product per (query, point) distance; the
+        # split-FP16 form issues three of them (reported beside it)
+        long_scan = scan_avg > 100.0
+        peak = peaks["bf16_tflops_sustained"] if long_scan and peaks.get("bf16_tflops_sustained") else peaks["bf16_tflops"]
+        flops = 2.0 * W.m * nload * W.N * 16
         achieved = flops / (scan_avg / 1e3) / 1e12
         roof = {"kernel": f"k_scan_tc<{kc}>", "bound": "tensor", "achieved": achieved,
-                "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "frac": achieved / peaks["bf16_tflops"],
-                "traffic": captured_traffic(W.name, args.mode), "peak_source": f"{peaks['source']} bf16 dense burst (fp16 same rate)",
-                "algorithmic": f"2*m*N*16*{kc} flops per launch (K padded to 16 per FP16 term)"}
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": captured_traffic(args.mode, W.N), "peak_source":
+                    f"{peaks['source']} bf16 dense {'sustained' if long_scan else 'burst'} (fp16 runs at the same rate)",
+                "algorithmic": "2*m*N*16 flops per launch (one K = 16 product per distance)",
+                "issued_tflops": achieved * kc, "issued": f"{kc} FP16 products per distance (split-FP16 operands)"
+                if kc == 3 else "1 FP16 product per distance"}
     else:
-        # FP32 CUDA-core scan: 12 FFMA per (query, point); peak from unit counts and clocks
-        clk_mhz = clk.summary().get("sm_mhz") or 1920.0
-        peak_tflops = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12
-        flops = 2.0 * 12 * W.m * W.N
+        # FP32 CUDA-core scan: 12 FFMA per (query, point) on the expanded form
+        flops = 2.0 * 12 * W.m * nload * W.N
         achieved = flops / (scan_avg / 1e3) / 1e12
+        peak_tflops = 2 * alu_peak / 1e12
         roof = {"kernel": "k_scan_fp32", "bound": "alu", "achieved": achieved, "peak": peak_tflops,
-                "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": captured_traffic(W.name, args.mode),
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock",
+                "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": captured_traffic(args.mode, W.N),
+                "peak_source": alu_src + ", 2 flop per FFMA",
                 "algorithmic": "2*12*m*N flops per launch (12 FFMA per pair)"}
 
     line = {
@@ -401,7 +471,9 @@ def run_ours(args, world, rank, local):
                    "l2": "flushed before every step" if flush_l2 else "inputs larger than L2",
                    "parallelism": f"replicas x{world}",
                    **({"f_d": f"{args.fd0} -> {args.fd_final} over {args.ramp_iters} iterations",
-                       "leaves": P.dd_dataset_ann_nlist(ds), "ann_levels": levels} if mode == P.DD_SEARCH_ANN else {}),
+                       "leaves": P.dd_dataset_ann_nlist(ds), "ann_levels": levels,
+                       "eq14": "certified second bound" if args.eq14 == 0 else "second-closest point found"}
+                      if mode == P.DD_SEARCH_ANN else {}),
                    **({"knn_k": args.knn_k, "knn_fd": args.knn_fd, "f_s": args.f_s, "nlist": nlist}
                       if mode == P.DD_SEARCH_KNNG else {})},
         "roofline": roof,
@@ -417,7 +489,7 @@ def run_ours(args, world, rank, local):
                                "what": "dd_project_nearest of fresh states (no warm start) with pinned host "
                                        "buffers (states in, indices + distances out)"}},
         "gpu_launches": launches,
-        "clocks": clk.summary(),
+        "clocks": clk_sum,
         "detail": {
             "device_ms_per_step": statistics.mean(dev_ms), "scan_ms_per_step": scan_avg,
             "cg_ms_per_step": statistics.mean(i.cg_ms for i in infos),
@@ -435,37 +507,42 @@ def run_ours(args, world, rank, local):
             "points_per_query": statistics.mean(i.points for i in infos) / (W.m * nload),
             "distinct_points_per_step": statistics.mean(i.unique_points for i in infos),
             "walk_moves_per_query": statistics.mean(i.moves for i in infos) / (W.m * nload),
+            "solve_at_N_ann_vs_exact": exact_solve,
+            "eq14_other_rule": eq14_other,
         },
     }
     for sv in svs:
         P.dd_solver_free(sv)
     P.dd_free_dataset(ds)
+    del raw
+    torch.cuda.empty_cache()
+    if args.serve_requests > 0 and W.name != "serve_N1e7":
+        # the metric's p50/p99 serve latency: a short run of the serving
+        # configuration (resident 10^7-point data set, Poisson arrivals)
+        line["detail"]["serve"] = serve_leg(P, ctx, I.WORKLOADS["serve_N1e7"], args, args.serve_requests)
     P.dd_destroy(ctx)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_searches_per_s(W, C, target_s=args.cpu_seconds)
     return line
 
 
-def run_serve(args, world, rank, local):
-    """Serving: resident data set, Poisson arrivals, continuous batching."""
+def serve_leg(P, ctx, W, args, n_req, clk=None):
+    """Serving (BASELINE's serving configuration): one resident data set,
+    Poisson arrivals at 0.8 x the service rate measured by a closed-loop
+    burst, admission by a device-memory budget, continuous batching.
+    Returns the figures of the measured stream."""
     import threading as th
 
     import torch
 
-    import paper_2012_00357_gb300 as P
-
-    P.build()
-    torch.cuda.set_device(local)
-    W = make_workload(args.workload)
     C = I.isotropic_C(W.law.E, W.law.nu)
     ex = W.extra
-    ctx = P.dd_create(local)
     raw = torch.empty((W.N, 12), dtype=torch.float32, device="cuda")
     P.dd_synth_dataset(ctx, raw, W.law, C, seed=W.seed)
     nlist = args.nlist or max(64, 1 << int(np.log2(max(W.N // 3000, 64))))
     ds = P.dd_load_dataset(ctx, raw, C, borrow=True, ann_nlist=nlist, seed=1)
-    kw = dict(mode=P.DD_SEARCH_ANN, f_d0=args.fd0, f_d_final=args.fd_final, ramp_iters=args.ramp_iters, max_iter=200)
-    n_req = ex["requests"]
+    kw = dict(mode=P.DD_SEARCH_ANN, f_d0=args.fd0, f_d_final=args.fd_final, ramp_iters=args.ramp_iters, max_iter=200,
+              eq14=args.eq14)
 
     def serve(reqs, budget):
         srv = P.dd_server_start(ds, ctx, state_budget=budget, max_batch=args.max_batch, **kw)
@@ -499,30 +576,56 @@ def run_serve(args, world, rank, local):
     _, _, _, mk, _ = serve(burst, budget)
     rate = 0.8 * len(burst) / mk
     reqs = I.serve_requests(W.seed, n_req, ex["edge_min"], ex["edge_max"], ex["t_min"], ex["t_max"], rate)
-    with ClockSampler(local) as clk:
+    if clk is not None:
+        with clk:
+            lat, iters, m_tot, makespan, st = serve(reqs, budget)
+    else:
         lat, iters, m_tot, makespan, st = serve(reqs, budget)
-    searches = sum(i * m for i, m in zip(iters, m_tot))
+    P.dd_free_dataset(ds)
+    del raw
     lat_s = sorted(lat)
+    return {"workload": W.name, "requests": n_req, "data_points": W.N, "nlist": nlist,
+            "p50_ms": float(np.percentile(lat_s, 50)), "p99_ms": float(np.percentile(lat_s, 99)),
+            "mean_ms": float(np.mean(lat_s)), "solves_per_s": n_req / makespan, "makespan_s": makespan,
+            "searches_per_s": sum(i * m for i, m in zip(iters, m_tot)) / makespan,
+            "lambda_per_s": rate, "arrivals": f"Poisson, rate {rate:.2f}/s = 0.8 x calibrated service rate",
+            "max_active": int(st.max_active), "batched_steps": int(st.steps),
+            "mean_iterations": float(np.mean(iters)),
+            "step_ms": {"busy": st.busy_ms / max(1, st.steps), "cg": st.cg_ms / max(1, st.steps),
+                        "search": st.search_ms / max(1, st.steps), "other": st.other_ms / max(1, st.steps)},
+            "graph_steps": int(st.graph_steps), "state_budget_gb": args.serve_budget_gb,
+            "eq14": "certified second bound" if args.eq14 == 0 else "second-closest point found",
+            "f_d": f"{args.fd0} -> {args.fd_final} over {args.ramp_iters} iterations",
+            "edges": f"U{{{ex['edge_min']}..{ex['edge_max']}}}",
+            "traction": f"U[{ex['t_min']}, {ex['t_max']}] random direction"}
+
+
+def run_serve(args, world, rank, local):
+    """Serving: resident data set, Poisson arrivals, continuous batching."""
+    import torch
+
+    import paper_2012_00357_gb300 as P
+
+    P.build()
+    torch.cuda.set_device(local)
+    W = make_workload(args.workload)
+    ctx = P.dd_create(local)
+    clk = ClockSampler(local)
+    sv = serve_leg(P, ctx, W, args, W.extra["requests"], clk=clk)
+    n_req = sv["requests"]
     line = {
-        "metric": METRIC, "value": searches / makespan, "unit": UNIT, "n_gpus": 1, "steps": n_req, "warmup": 48,
-        "ms_per_step": makespan * 1e3 / n_req, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64 (P_C refinement, rescoring) + f32", "data": "synthetic (dd_inputs generator, made on device)",
-        "config": {"workload": W.name, "data_points": W.N, "requests": n_req, "edges": f"U{{{ex['edge_min']}..{ex['edge_max']}}}",
-                   "traction": f"U[{ex['t_min']}, {ex['t_max']}] random direction", "search": "ann",
-                   "f_d": f"{args.fd0} -> {args.fd_final} over {args.ramp_iters} iterations", "nlist": nlist, "state_budget_gb": args.serve_budget_gb,
-                   "arrivals": f"Poisson, rate {rate:.2f}/s = 0.8 x calibrated service rate",
+        "metric": METRIC, "value": sv["searches_per_s"], "unit": UNIT, "n_gpus": 1, "steps": n_req, "warmup": 48,
+        "ms_per_step": sv["makespan_s"] * 1e3 / n_req, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64 (P_C refinement, rescoring) + f32",
+        "data": "synthetic (dd_inputs generator, made on device)",
+        "config": {"workload": W.name, "data_points": W.N, "requests": n_req, "edges": sv["edges"],
+                   "traction": sv["traction"], "search": "ann", "f_d": sv["f_d"], "nlist": sv["nlist"],
+                   "state_budget_gb": args.serve_budget_gb, "arrivals": sv["arrivals"],
                    "l2": "inputs larger than L2", "parallelism": "replicas x1"},
-        "serve": {"p50_ms": float(np.percentile(lat_s, 50)), "p99_ms": float(np.percentile(lat_s, 99)),
-                  "mean_ms": float(np.mean(lat_s)), "solves_per_s": n_req / makespan, "makespan_s": makespan,
-                  "lambda_per_s": rate, "max_active": int(st.max_active), "batched_steps": int(st.steps),
-                  "mean_iterations": float(np.mean(iters)),
-                  "step_ms": {"busy": st.busy_ms / max(1, st.steps), "cg": st.cg_ms / max(1, st.steps),
-                              "search": st.search_ms / max(1, st.steps), "other": st.other_ms / max(1, st.steps)},
-                  "graph_steps": int(st.graph_steps)},
+        "serve": {k: v for k, v in sv.items() if k not in ("workload", "edges", "traction", "f_d", "arrivals")},
         "gpu_launches": int(P.dd_launch_count(ctx)),
         "clocks": clk.summary(),
     }
-    P.dd_free_dataset(ds)
     P.dd_destroy(ctx)
     return line
 
@@ -580,12 +683,22 @@ def main():
                     help="final states checked against the certified exact search (0: none)")
     ap.add_argument("--no-exact-tc", dest="exact_tc", action="store_false",
                     help="check with the FP32 exact scan instead of the tensor-core one (no FP16 copy)")
+    ap.add_argument("--eq14", type=int, default=1, choices=[0, 1],
+                    help="second distance of the Eq. (14) skip: 1 the second-closest point found (the paper's "
+                         "estimate, used below f_d = 1; the default here), 0 the certified bound (the library's "
+                         "default); the other rule is timed over the same steps and reported in detail")
+    ap.add_argument("--no-eq14-compare", action="store_true", help="do not time the other Eq. (14) rule")
     ap.add_argument("--ann-budget", type=int, default=0,
                     help="leaves a query's warp scans before the leaf-major pass (0: library default, -1: all)")
     ap.add_argument("--knn-k", type=int, default=None, help="k of the k-NN graph (default: the workload's, else 128)")
     ap.add_argument("--knn-fd", type=float, default=None, help="f_d of the graph build (default: workload's, else 0.8)")
     ap.add_argument("--f-s", type=int, default=None, help="node-change bound of the graph walk (0: none; default: "
                     "the workload's, else 2)")
+    ap.add_argument("--exact-solve", action="store_true",
+                    help="also solve the first load case with the certified tensor-core exact search and with the "
+                         "approximate search alone (solve time and distance at N, ANN vs exact; minutes at 10^9)")
+    ap.add_argument("--serve-requests", type=int, default=64,
+                    help="requests of the short serving run reported in detail.serve (0: none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()

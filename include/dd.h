@@ -235,7 +235,51 @@ typedef struct dd_search_opts {
                                  leaf.  0 = default (2), -1 = every leaf in
                                  the query's warp, < -1 = none (all leaves,
                                  the warm-start one included, leaf-major) */
+    int topk;                 /* exact modes: number k (1 .. DD_TOPK_MAX) of
+                                 nearest data points written to topk_out;
+                                 0 = none (topk_out must then be NULL) */
+    double *topk_d2;          /* [m x topk] FP64 d_e^2 (Eq. 3) of topk_out,
+                                 or NULL */
+    double *d2nd;             /* [m] output, or NULL: a lower bound on d_e^2
+                                 of every data point other than idx[i] - the
+                                 second-nearest distance of Eq. (14).  Exact
+                                 modes: certified (the exact second-nearest
+                                 distance when topk >= 2).  DD_SEARCH_ANN: the
+                                 smaller of the second-best point read and,
+                                 for every cluster, cell or leaf not
+                                 searched, (centroid distance - f_d radius)^2
+                                 in the mapped coordinates, times 2: a true
+                                 lower bound at f_d = 1, the bound of Eq.
+                                 (13)'s cluster model below.  DD_SEARCH_KNNG:
+                                 the nearest other point the walk evaluated
+                                 (0 when f_s stopped it), which keeps a query
+                                 exactly where the walk from its warm start
+                                 would stay */
+    const double *prev_y;     /* DD_SEARCH_ANN / DD_SEARCH_KNNG: moving-query
+                                 record of Eq. (14), or NULL.  The states
+                                 [m x 12] of the previous call, with prev_d2
+                                 and prev_d2nd [m] the d2 and d2nd it returned
+                                 and prev_idx its idx: a query whose mapped
+                                 state moved by less than
+                                 (sqrt(prev_d2nd / 2) - sqrt(prev_d2 / 2)) / 2
+                                 keeps prev_idx without a search.  For
+                                 DD_SEARCH_ANN the previous call must have
+                                 used an f_d no smaller than this call's (the
+                                 bound is that f_d's).  Same memory kind as y;
+                                 requires prev_idx, prev_d2 and prev_d2nd */
+    const double *prev_d2;
+    const double *prev_d2nd;
+    int eq14;                 /* DD_SEARCH_ANN: d2nd (and so the record a
+                                 later call makes of it) is 0 (default) the
+                                 certified bound above, 1 the second-closest
+                                 point found below f_d = 1 (the paper's
+                                 estimate; see dd_solve_opts.eq14) */
 } dd_search_opts;
+
+/* Largest k of dd_search_opts.topk.  k < DD_TOPK_MAX is certified from the
+ * low-precision candidates for almost every query; k = DD_TOPK_MAX re-searches
+ * most queries in FP64. */
+#define DD_TOPK_MAX 8
 
 typedef struct dd_search_stats {
     int64_t uncertified;      /* queries re-searched in FP64 (exact modes) */
@@ -257,15 +301,32 @@ typedef struct dd_search_stats {
  *     idx[i] = argmin_j d_e^2(y_i, (eps_j, sig_j)),  d2[i] = that d_e^2 (Eq. 3,
  *     without the 1/2 of Eq. 2), evaluated in FP64 from the stored data.
  * Ties between data points with equal FP64 distance go to the lowest index.
- *   y       host or device, float64 [m x 12] states (eps, sig).
- *   m       >= 0 (0 is a no-op).
- *   idx     host or device, int32 [m] (output).
- *   d2      host or device, float64 [m] (output), may be NULL.
- *   stats   host, may be NULL.
- * All of y, idx, d2 must be of the same kind (all host or all device). */
+ *   y         host or device, float64 [m x 12] states (eps, sig).
+ *   m         >= 0 (0 is a no-op).
+ *   idx       host or device, int32 [m] (output).
+ *   d2        host or device, float64 [m] (output), may be NULL.
+ *   topk_out  host or device, int32 [m x opts->topk] (output), or NULL:
+ *             exact modes only.  Row i lists the topk nearest data points of
+ *             y_i, nearest first by FP64 Eq. (3) distance (ties to the lower
+ *             index), -1 past the N-th.  With certify = 1 they are the exact
+ *             k nearest points (the low-precision scan keeps the best 8
+ *             scores per data range; a query whose k-th candidate is not
+ *             separated from the scores left out by the scan's error bound
+ *             is re-searched in FP64).  With certify = 0 they are the best of
+ *             those candidates after FP64 rescoring (the tensor-core top-k
+ *             form; the caller can measure their error against an exact
+ *             search).
+ *   stats     host, may be NULL.
+ * All of y, idx, d2, topk_out and the opts arrays must be of the same kind
+ * (all host or all device).  Errors: DD_ERR_ARG (bad sizes, f_d outside
+ * [0, 1], topk outside 0 .. DD_TOPK_MAX or with an approximate mode, a
+ * motion record without prev_idx, mixed memory kinds), DD_ERR_STATE (the
+ * mode's index or operand copy was not built), DD_ERR_OOM, DD_ERR_CUDA,
+ * DD_ERR_TIMEOUT. */
 dd_status dd_project_nearest(dd_dataset *ds, const double *y, int64_t m,
                              const dd_search_opts *opts, int32_t *idx,
-                             double *d2, dd_search_stats *stats);
+                             double *d2, int32_t *topk_out,
+                             dd_search_stats *stats);
 
 /* Largest query count accepted by dd_project_nearest_noalloc. */
 #define DD_NOALLOC_MAX_QUERIES 65536
@@ -276,11 +337,19 @@ dd_status dd_project_nearest(dd_dataset *ds, const double *y, int64_t m,
  * another allocator, or a latency-bound caller that cannot accept cudaMalloc /
  * cudaFree (which can fail under memory pressure, and cudaFree synchronises
  * the device).  Same result as dd_project_nearest with DD_SEARCH_EXACT_FP32
- * and certify = 1: idx[i] and d2[i] (Eq. 3, FP64) of the nearest data point.
+ * and certify = 1: idx[i], and d2[i] the FP64 squared energy-norm distance
+ * of that point, as dd_project_nearest returns it.
  *   y_dev    device, float64 [m x 12] states (eps, sig)
  *   m        0 .. DD_NOALLOC_MAX_QUERIES; larger m returns DD_ERR_ARG
  *   idx_dev  device, int32 [m] (output); d2_dev device, float64 [m] (output)
- *   stream   cudaStream_t, NULL = the context's stream; asynchronous
+ *   stream   cudaStream_t, NULL = the context's stream
+ *   wait     0: asynchronous on stream; a device-side wait that gave up
+ *            leaves the outputs unspecified and is not reported.  1: the call
+ *            synchronises the stream and returns DD_ERR_TIMEOUT if a bounded
+ *            device wait of this call gave up (the status word lives in the
+ *            scratch array and is cleared at the start of every call, so it
+ *            never reports another call's failure).
+ * The calling thread's current device is the same on return as on entry.
  * Scratch is one file-scope device array of 32 MiB that every GPU loading the
  * library holds until exit.  The first call on a device looks up the array's
  * device address (cudaGetSymbolAddress) with that device current; make that
@@ -288,7 +357,7 @@ dd_status dd_project_nearest(dd_dataset *ds, const double *y, int64_t m,
  * whose work overlaps on the GPU (different streams, or several host threads)
  * race on it and must be serialised by the caller. */
 dd_status dd_project_nearest_noalloc(dd_dataset *ds, const double *y_dev, int64_t m,
-                                     int32_t *idx_dev, double *d2_dev, void *stream);
+                                     int32_t *idx_dev, double *d2_dev, void *stream, int wait);
 
 /* ------------------------------------------------------------------------ */
 /* DD solve: z_{i+1} = P_D(P_C(z_i)), Eq. (8)                               */
@@ -355,6 +424,17 @@ typedef struct dd_solve_opts {
                                  The stop tests apply once f has reached
                                  f_d_final (rule 1) or the ramp has ended. */
     double fd_tau;            /* parameter of fd_rule 1 and 2 (>= 0) */
+    int eq14;                 /* DD_SEARCH_ANN: second distance of the
+                                 moving-query radius of Eq. (14).  0 (default)
+                                 = the certified bound of dd_search_opts.d2nd:
+                                 a kept query gets the answer a search would
+                                 certify at that f_d (the exact nearest point
+                                 at f_d = 1).  1 = the second-closest point the
+                                 search found, the paper's estimate: faster
+                                 (more queries kept) but a kept answer can be
+                                 stale where a pruned cluster holds a nearer
+                                 point; used only below f_d = 1 (an exact search
+                                 always takes the certified bound) */
 } dd_solve_opts;
 
 /* Result of a solve: the constraint-set state y = (u, eps, sig) of the last

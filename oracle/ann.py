@@ -40,6 +40,12 @@ at one f_d is used only by a search at the same or a lower f_d (the bound is
 weaker for a larger f_d).  After a keep, the new second bound is
 (sqrt(s) - |q_new - q_old|)^2 (triangle inequality again).
 
+The paper's own wording takes p2 as the second-closest point "from the
+search" and calls the relation an estimate.  `second="found"` returns that
+instead (the second-smallest distance among the points read) below f_d = 1;
+a search at f_d = 1 always returns the certified bound, so that an exact
+search stays exact.  A "found" record serves any f_d below 1.
+
 Distances are plain Euclidean distances in the mapped coordinates of
 Sec. 3.2 (|dq|^2 = d_e^2 / 2).  Ties go to the lowest data index.
 Pinned by tests/test_oracle_ann.py (f_d = 1 equals brute force; warm start
@@ -81,6 +87,14 @@ def moving_query_keeps(q, q_prev, d1_prev, d2_prev):
     return mv < 0.5 * (math.sqrt(d2_prev) - math.sqrt(d1_prev)), mv
 
 
+def second_rule_certified(second_rule, f_d):
+    """True when the second distance is the certified bound: always for
+    "certified", and for "found" (the paper's estimate) at f_d = 1."""
+    if second_rule not in ("certified", "found"):
+        raise ValueError(second_rule)
+    return second_rule == "certified" or f_d >= 1.0
+
+
 def _bound_sq(b):
     """Squared lower bound from a plain one that may be negative."""
     return max(b, 0.0) ** 2
@@ -102,13 +116,15 @@ def _kept(Z, q, qi, prev_idx, motion, f_d):
     return j0, float(((Z[j0] - q) ** 2).sum()), _bound_sq(math.sqrt(d2p[qi]) - mv)
 
 
-def ann_search(Z, zq, cent, rad, cluster_of, f_d, prev_idx=None, n_cand=8, motion=None, with_second=False):
+def ann_search(Z, zq, cent, rad, cluster_of, f_d, prev_idx=None, n_cand=8, motion=None, with_second=False,
+               second="certified"):
     """Returns (idx, squared distance) for every query row of zq, and with
     with_second=True also the squared second bound s (module docstring).
 
     motion: None, or (previous queries [m x 12], their squared answer
     distances [m], their squared second bounds [m], the f_d the record was
     made at (scalar or [m])); with prev_idx it enables the Eq. (14) skip."""
+    second_kind = second
     Z = np.asarray(Z, dtype=np.float64)
     zq = np.asarray(zq, dtype=np.float64)
     cent = np.asarray(cent, dtype=np.float64)
@@ -163,13 +179,14 @@ def ann_search(Z, zq, cent, rad, cluster_of, f_d, prev_idx=None, n_cand=8, motio
             second = float(np.min(np.delete(d, best_j))) if len(d) > 1 else np.inf
         else:
             second = min([v for j, v in read.items() if j != best_j], default=np.inf)
-            second = min(second, _bound_sq(bound))
+            if second_rule_certified(second_rule=second_kind, f_d=f_d):
+                second = min(second, _bound_sq(bound))
         out_i[qi], out_d[qi], out_s[qi] = best_j, best_d, second
     return (out_i, out_d, out_s) if with_second else (out_i, out_d)
 
 
 def tree2_search(Z, zq, cell_cent, cell_rad, leaf_cent, leaf_rad, leaf_of, L2, f_d, prev_idx=None, n_cand=8,
-                 k_fine=8, budget=None, motion=None, with_second=False):
+                 k_fine=8, budget=None, motion=None, with_second=False, second="certified"):
     """Returns (idx, squared distance) for every query row of zq on the
     two-level partition: cells (centroids, radii) and their leaves (leaf l
     in cell l // L2; centroids, radii, leaf of every data point); with
@@ -181,6 +198,7 @@ def tree2_search(Z, zq, cell_cent, cell_rad, leaf_cent, leaf_rad, leaf_of, L2, f
     d_c reached then is searched at the end, without shrinking d_c: the
     chosen set can only grow, so the answer is never farther.
     motion: as in ann_search (the Eq. 14 skip)."""
+    second_kind = second
     Z = np.asarray(Z, dtype=np.float64)
     zq = np.asarray(zq, dtype=np.float64)
     cell_cent = np.asarray(cell_cent, dtype=np.float64)
@@ -274,7 +292,8 @@ def tree2_search(Z, zq, cell_cent, cell_rad, leaf_cent, leaf_rad, leaf_of, L2, f
             second = float(np.min(np.delete(d, best_j))) if len(d) > 1 else np.inf
         else:
             second = min([v for j, v in read.items() if j != best_j], default=np.inf)
-            second = min(second, _bound_sq(bound))
+            if second_rule_certified(second_rule=second_kind, f_d=f_d):
+                second = min(second, _bound_sq(bound))
         out_i[qi], out_d[qi], out_s[qi] = best_j, best_d, second
     return (out_i, out_d, out_s) if with_second else (out_i, out_d)
 

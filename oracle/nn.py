@@ -102,3 +102,22 @@ def nn_stream(law, seed: int, N: int, C, zq):
     lib.oracle_nn_stream(law.code, law.eps_lo, law.eps_hi, law.noise_std, law.beta, C_law.ctypes.data, seed, N,
                          Ch.ctypes.data, Cmh.ctypes.data, zq.ctypes.data, m, i1.ctypes.data, d1.ctypes.data)
     return i1, d1
+
+
+def nn_topk(zd: np.ndarray, zq: np.ndarray, k: int, chunk: int = 256):
+    """The k nearest data rows of every query row (Eq. 7 extended to the k
+    best): indices int64 [m x k] and squared distances [m x k] in the mapped
+    coordinates, nearest first, ties to the lower index; -1 and +inf past the
+    N-th.  Plain numpy: full distance rows, then a stable sort."""
+    zd = np.asarray(zd, dtype=np.float64)
+    zq = np.asarray(zq, dtype=np.float64)
+    n, m = len(zd), len(zq)
+    idx = np.full((m, k), -1, np.int64)
+    dist = np.full((m, k), np.inf)
+    kk = min(k, n)
+    for a in range(0, m, chunk):
+        d = ((zq[a:a + chunk, None, :] - zd[None, :, :]) ** 2).sum(-1)
+        order = np.argsort(d, axis=1, kind="stable")[:, :kk]    # stable: equal distances keep index order
+        idx[a:a + chunk, :kk] = order
+        dist[a:a + chunk, :kk] = np.take_along_axis(d, order, axis=1)
+    return idx, dist

@@ -32,6 +32,7 @@ EXPORTS = [
     "dd_server_poll", "dd_server_get_stats", "dd_server_stop",
 ]
 DD_NOALLOC_MAX_QUERIES = 65536
+DD_TOPK_MAX = 8
 
 
 class DDError(RuntimeError):
@@ -48,7 +49,9 @@ class dd_dataset_opts(ctypes.Structure):
 
 class dd_search_opts(ctypes.Structure):
     _fields_ = [("mode", c_int), ("certify", c_int), ("f_d", c_double), ("prev_idx", c_void_p),
-                ("stream", c_void_p), ("f_s", c_int), ("ann_budget", c_int)]
+                ("stream", c_void_p), ("f_s", c_int), ("ann_budget", c_int), ("topk", c_int),
+                ("topk_d2", c_void_p), ("d2nd", c_void_p), ("prev_y", c_void_p), ("prev_d2", c_void_p),
+                ("prev_d2nd", c_void_p), ("eq14", c_int)]
 
 
 class dd_search_stats(ctypes.Structure):
@@ -84,7 +87,8 @@ class dd_solve_opts(ctypes.Structure):
     _fields_ = [("mode", c_int), ("certify", c_int), ("f_d0", c_double), ("f_d_final", c_double),
                 ("ramp_iters", c_int), ("max_iter", c_int), ("cg_rtol", c_double), ("cg_max_iter", c_int),
                 ("seed", c_uint64), ("init_idx", c_void_p), ("stall_iters", c_int), ("cg_mode", c_int),
-                ("f_s", c_int), ("ann_budget", c_int), ("fd_rule", c_int), ("fd_tau", c_double)]
+                ("f_s", c_int), ("ann_budget", c_int), ("fd_rule", c_int), ("fd_tau", c_double),
+                ("eq14", c_int)]
 
 
 class dd_server_opts(ctypes.Structure):
@@ -133,7 +137,7 @@ def lib():
         L.dd_dataset_bytes.restype = c_size_t
         L.dd_synth_dataset.argtypes = [vp, c_int, c_double, c_double, c_double, c_double, POINTER(c_double),
                                        c_uint64, c_int64, c_int64, vp, vp]
-        L.dd_project_nearest.argtypes = [vp, vp, c_int64, POINTER(dd_search_opts), vp, vp,
+        L.dd_project_nearest.argtypes = [vp, vp, c_int64, POINTER(dd_search_opts), vp, vp, vp,
                                          POINTER(dd_search_stats)]
         L.dd_solve.argtypes = [vp, POINTER(dd_mesh), POINTER(dd_load), POINTER(dd_solve_opts), POINTER(dd_result)]
         L.dd_result_free.argtypes = [POINTER(dd_result)]
@@ -155,7 +159,7 @@ def lib():
         L.dd_dataset_knn_k.restype = c_int
         L.dd_dataset_knn_graph.argtypes = [vp, vp]
         L.dd_pca_metric.argtypes = [vp, vp, c_int64, POINTER(c_double)]
-        L.dd_project_nearest_noalloc.argtypes = [vp, vp, c_int64, vp, vp, vp]
+        L.dd_project_nearest_noalloc.argtypes = [vp, vp, c_int64, vp, vp, vp, c_int]
         L.dd_solvers_step.argtypes = [POINTER(vp), c_int, POINTER(dd_iter_info)]
         L.dd_server_start.argtypes = [vp, POINTER(dd_server_opts), POINTER(vp)]
         L.dd_server_submit.argtypes = [vp, POINTER(dd_mesh), POINTER(dd_load), c_uint64, POINTER(c_int64)]
@@ -249,11 +253,16 @@ def dd_synth_dataset(ctx, out_dev, law, C, seed: int = 0, start: int = 0, stream
 
 def dd_project_nearest(ds, ctx, y, idx, d2=None, mode: int = DD_SEARCH_EXACT_FP32, certify: bool = True,
                        f_d: float = 0.0, prev_idx=None, stream=None, want_stats: bool = True, f_s: int = 0,
-                       ann_budget: int = 0):
+                       ann_budget: int = 0, topk_out=None, topk_d2=None, d2nd=None, prev_y=None, prev_d2=None,
+                       prev_d2nd=None, eq14: int = 0):
+    """topk_out: [m x k] int32 array (its second dimension gives k); the
+    other optional arrays as in dd_search_opts."""
     m = int(y.shape[0])
-    opts = dd_search_opts(int(mode), int(certify), float(f_d), _ptr(prev_idx), stream, int(f_s), int(ann_budget))
+    k = int(topk_out.shape[1]) if topk_out is not None else 0
+    opts = dd_search_opts(int(mode), int(certify), float(f_d), _ptr(prev_idx), stream, int(f_s), int(ann_budget),
+                          k, _ptr(topk_d2), _ptr(d2nd), _ptr(prev_y), _ptr(prev_d2), _ptr(prev_d2nd), int(eq14))
     st = dd_search_stats()
-    _check(ctx, lib().dd_project_nearest(ds, _ptr(y), m, ctypes.byref(opts), _ptr(idx), _ptr(d2),
+    _check(ctx, lib().dd_project_nearest(ds, _ptr(y), m, ctypes.byref(opts), _ptr(idx), _ptr(d2), _ptr(topk_out),
                                          ctypes.byref(st) if want_stats else None))
     return st
 
@@ -282,7 +291,7 @@ def dd_solve(ds, ctx, n_el, load, mode: int = DD_SEARCH_EXACT_FP32, init_idx=Non
              cg_rtol: float = 1e-12, cg_max_iter: int = 20000, certify: bool = True, f_d0: float = 0.0,
              f_d_final: float = 0.0, ramp_iters: int = 20, seed: int = 0, stall_iters: int = 3,
              lengths=(1.0, 1.0, 1.0), allow_not_converged: bool = True, cg_mode: int = 0, f_s: int = 0,
-             ann_budget: int = 0, fd_rule: int = 0, fd_tau: float = 0.0):
+             ann_budget: int = 0, fd_rule: int = 0, fd_tau: float = 0.0, eq14: int = 0):
     """Solve one cube problem; `load` is a dd_inputs.Load.  Returns a Result."""
     nx, ny, nz = (n_el, n_el, n_el) if np.isscalar(n_el) else n_el
     mesh = dd_mesh(nx, ny, nz, *lengths)
@@ -290,7 +299,7 @@ def dd_solve(ds, ctx, n_el, load, mode: int = DD_SEARCH_EXACT_FP32, init_idx=Non
     ii = None if init_idx is None else np.ascontiguousarray(init_idx, dtype=np.int32)
     opts = dd_solve_opts(int(mode), int(certify), float(f_d0), float(f_d_final), int(ramp_iters), int(max_iter),
                          float(cg_rtol), int(cg_max_iter), int(seed), _ptr(ii), int(stall_iters), int(cg_mode),
-                         int(f_s), int(ann_budget), int(fd_rule), float(fd_tau))
+                         int(f_s), int(ann_budget), int(fd_rule), float(fd_tau), int(eq14))
     r = dd_result()
     st = lib().dd_solve(ds, ctypes.byref(mesh), ctypes.byref(L), ctypes.byref(opts), ctypes.byref(r))
     try:
@@ -308,14 +317,14 @@ def dd_result_free(r: dd_result) -> None:
 
 
 def _solve_args(n_el, load, mode, init_idx, max_iter, cg_rtol, cg_max_iter, certify, f_d0, f_d_final, ramp_iters,
-                seed, stall_iters, lengths, cg_mode=0, f_s=0, ann_budget=0, fd_rule=0, fd_tau=0.0):
+                seed, stall_iters, lengths, cg_mode=0, f_s=0, ann_budget=0, fd_rule=0, fd_tau=0.0, eq14=0):
     nx, ny, nz = (n_el, n_el, n_el) if np.isscalar(n_el) else n_el
     mesh = dd_mesh(nx, ny, nz, *lengths)
     L = _load(load)
     ii = None if init_idx is None else np.ascontiguousarray(init_idx, dtype=np.int32)
     opts = dd_solve_opts(int(mode), int(certify), float(f_d0), float(f_d_final), int(ramp_iters), int(max_iter),
                          float(cg_rtol), int(cg_max_iter), int(seed), _ptr(ii), int(stall_iters), int(cg_mode),
-                         int(f_s), int(ann_budget), int(fd_rule), float(fd_tau))
+                         int(f_s), int(ann_budget), int(fd_rule), float(fd_tau), int(eq14))
     return mesh, L, opts, ii
 
 
@@ -323,10 +332,10 @@ def dd_solver_create(ds, ctx, n_el, load, mode: int = DD_SEARCH_EXACT_FP32, init
                      cg_rtol: float = 1e-12, cg_max_iter: int = 20000, certify: bool = True, f_d0: float = 0.0,
                      f_d_final: float = 0.0, ramp_iters: int = 20, seed: int = 0, stall_iters: int = 3,
                      lengths=(1.0, 1.0, 1.0), cg_mode: int = 0, f_s: int = 0, ann_budget: int = 0,
-                     fd_rule: int = 0, fd_tau: float = 0.0):
+                     fd_rule: int = 0, fd_tau: float = 0.0, eq14: int = 0):
     mesh, L, opts, ii = _solve_args(n_el, load, mode, init_idx, max_iter, cg_rtol, cg_max_iter, certify, f_d0,
                                     f_d_final, ramp_iters, seed, stall_iters, lengths, cg_mode, f_s, ann_budget,
-                                    fd_rule, fd_tau)
+                                    fd_rule, fd_tau, eq14)
     sv = c_void_p()
     _check(ctx, lib().dd_solver_create(ds, ctypes.byref(mesh), ctypes.byref(L), ctypes.byref(opts),
                                        ctypes.byref(sv)))
@@ -407,12 +416,13 @@ def dd_dataset_knn_graph(ds, ctx):
     return nbr
 
 
-def dd_project_nearest_noalloc(ds, ctx, y_dev, idx_dev, d2_dev, stream=None) -> None:
+def dd_project_nearest_noalloc(ds, ctx, y_dev, idx_dev, d2_dev, stream=None, wait: bool = False) -> None:
     """Exact projection that allocates no device memory (device buffers only;
-    asynchronous on `stream`).  For callers that cannot allocate during a
-    call, e.g. a loop whose device memory is reserved by another allocator."""
+    asynchronous on `stream` unless wait).  For callers that cannot allocate
+    during a call, e.g. a loop whose device memory is reserved by another
+    allocator.  wait=True synchronises and reports a device-side timeout."""
     _check(ctx, lib().dd_project_nearest_noalloc(ds, _ptr(y_dev), int(y_dev.shape[0]), _ptr(idx_dev),
-                                                 _ptr(d2_dev), stream))
+                                                 _ptr(d2_dev), stream, int(bool(wait))))
 
 
 def dd_solvers_step(svs, ctx):
@@ -428,7 +438,7 @@ def dd_solve_batch(ds, ctx, n_els, loads, mode: int = DD_SEARCH_EXACT_FP32, init
                    cg_rtol: float = 1e-12, cg_max_iter: int = 20000, certify: bool = True, f_d0: float = 0.0,
                    f_d_final: float = 0.0, ramp_iters: int = 20, seed: int = 0, stall_iters: int = 3,
                    cg_mode: int = 0, allow_not_converged: bool = True, f_s: int = 0, ann_budget: int = 0,
-                   fd_rule: int = 0, fd_tau: float = 0.0):
+                   fd_rule: int = 0, fd_tau: float = 0.0, eq14: int = 0):
     """Solve several cube problems together; n_els[i] edge elements, loads[i]."""
     n = len(n_els)
     meshes = (dd_mesh * n)(*[dd_mesh(k, k, k, 1.0, 1.0, 1.0) for k in n_els])
@@ -436,7 +446,7 @@ def dd_solve_batch(ds, ctx, n_els, loads, mode: int = DD_SEARCH_EXACT_FP32, init
                          for L in loads])
     _, _, opts, ii = _solve_args(n_els[0], loads[0], mode, init_idx, max_iter, cg_rtol, cg_max_iter, certify, f_d0,
                                  f_d_final, ramp_iters, seed, stall_iters, (1.0, 1.0, 1.0), cg_mode, f_s,
-                                 ann_budget, fd_rule, fd_tau)
+                                 ann_budget, fd_rule, fd_tau, eq14)
     outs = (dd_result * n)()
     st = lib().dd_solve_batch(ds, n, meshes, Ls, ctypes.byref(opts), outs)
     try:
@@ -451,10 +461,11 @@ def dd_solve_batch(ds, ctx, n_els, loads, mode: int = DD_SEARCH_EXACT_FP32, init
 def dd_server_start(ds, ctx, mode: int = DD_SEARCH_EXACT_FP32, state_budget: int = 0, max_batch: int = 0,
                     max_iter: int = 100, cg_rtol: float = 1e-12, cg_max_iter: int = 20000, certify: bool = True,
                     f_d0: float = 0.0, f_d_final: float = 0.0, ramp_iters: int = 20, stall_iters: int = 3,
-                    cg_mode: int = 0, f_s: int = 0, ann_budget: int = 0, fd_rule: int = 0, fd_tau: float = 0.0):
+                    cg_mode: int = 0, f_s: int = 0, ann_budget: int = 0, fd_rule: int = 0, fd_tau: float = 0.0,
+                    eq14: int = 0):
     so = dd_solve_opts(int(mode), int(certify), float(f_d0), float(f_d_final), int(ramp_iters), int(max_iter),
                        float(cg_rtol), int(cg_max_iter), 0, None, int(stall_iters), int(cg_mode), int(f_s),
-                       int(ann_budget), int(fd_rule), float(fd_tau))
+                       int(ann_budget), int(fd_rule), float(fd_tau), int(eq14))
     o = dd_server_opts(so, int(state_budget), int(max_batch))
     srv = c_void_p()
     _check(ctx, lib().dd_server_start(ds, ctypes.byref(o), ctypes.byref(srv)))

@@ -24,9 +24,15 @@
 //      re-searched by the certified exact scan, so f_d = 1 always returns the
 //      exact point;
 //   5. the answer is rescored with Eq. (3) in FP64.
-// Moving-query radius (Eq. 14): with a motion record (previous query, its
-// nearest and second-nearest distances) a query that moved less than
-// (d2 - d1)/2 keeps its previous neighbour without any scan.
+// Moving-query radius (Eq. 14): with a motion record (previous query, the
+// distance d1 of its answer, a lower bound d2 on the distance of every other
+// point) a query that moved less than (d2 - d1)/2 keeps its previous
+// neighbour without any scan.  The bound is the smaller of the second-best
+// point read and, for every cluster, cell or leaf not searched, its centroid
+// distance minus f_d times its radius (the cluster model Eq. 13 uses; at
+// f_d = 1 a true lower bound, so a kept answer is the exact nearest point).
+// A record made at one f_d is used only by searches at the same or a lower
+// f_d.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -415,6 +421,8 @@ struct ProbeArgs {
                                     // [5] points read
     unsigned *touched;              // [ceil(L / 32)] clusters scanned by any query of this search
     int gated;                      // 1: k_ann_gate ran; cand_cl[i * kCand] == kGated marks a kept query
+    int certified;                  // 1: the second distance is the certified bound (Eq. 14); 0: the
+                                    // second-best point read below f_d = 1 (the certified bound at 1)
 };
 
 constexpr int kGated = -2;
@@ -431,6 +439,8 @@ struct GateArgs {
     const int32_t *prev;
     const float *z32;
     const float *mot_q, *mot_d;
+    float f_d;
+    const float *fd_q;          // per-query f_d (may be null: f_d for all)
     int32_t *idx;
     float *d1, *d2;
     int32_t *cand_cl;
@@ -459,8 +469,10 @@ __global__ void __launch_bounds__(256) k_ann_gate(GateArgs G) {
                 mv = fmaf(t, t, mv);
             }
             mv = sqrtf(mv);
-            const float r1 = G.mot_d[i * 2], r2 = G.mot_d[i * 2 + 1];
-            if (mv < 0.5f * (r2 - r1)) {
+            const float4 r = *reinterpret_cast<const float4 *>(G.mot_d + i * kMotStride);
+            const float f_d = G.fd_q ? G.fd_q[i] : G.f_d;
+            if (mv < 0.5f * (r.y - r.x) && f_d <= r.z) {
+                const float r2 = r.y;
                 keep = true;
                 G.idx[i] = j0;
                 G.d1[i] = dist2_12(G.z32 + (size_t)j0 * 12, q);
@@ -517,12 +529,13 @@ __global__ void __launch_bounds__(256) k_ann_probe(ProbeArgs A) {
                     mv = fmaf(t, t, mv);
                 }
                 mv = sqrtf(mv);
-                const float r1 = A.mot_d[i * 2], r2 = A.mot_d[i * 2 + 1];
-                if (mv < 0.5f * (r2 - r1)) {
+                const float4 r = *reinterpret_cast<const float4 *>(A.mot_d + i * kMotStride);
+                const float fdi = A.fd_q ? A.fd_q[i] : A.f_d;
+                if (mv < 0.5f * (r.y - r.x) && fdi <= r.z) {
                     if (lane == 0) {
                         A.idx[i] = j0;
                         A.d1[i] = d0;
-                        float lb = fmaxf(r2 - mv, 0.f);
+                        float lb = fmaxf(r.y - mv, 0.f);
                         A.d2[i] = lb * lb;
                         atomicAdd(A.counters + 1, 1ull);
                     }
@@ -544,6 +557,8 @@ __global__ void __launch_bounds__(256) k_ann_probe(ProbeArgs A) {
     if (cl0 >= 0) scan(cl0);
     float dc = sqrtf(b.d);
     const float f_d = A.fd_q ? A.fd_q[i] : A.f_d;
+    const bool cert = A.certified || f_d >= 1.0f;
+    float lb = INFINITY;    // Eq. (14): plain bound on the points of the clusters not searched
     for (int k = 0; k < kCand; ++k) {
         const int l = A.cand_cl[i * kCand + k];
         if (l < 0) break;
@@ -552,8 +567,12 @@ __global__ void __launch_bounds__(256) k_ann_probe(ProbeArgs A) {
         if (k == 0 || dl - f_d * A.radius[l] < dc) {
             scan(l);
             dc = sqrtf(b.d);
+        } else if (cert) {
+            lb = fminf(lb, dl - f_d * A.radius[l]);
         }
     }
+    // clusters beyond the candidate list: no nearer centroid, no wider radius
+    if (cert && A.L > kCand) lb = fminf(lb, A.cand_d[i * kCand + kCand - 1] - f_d * A.rmax);
     // completeness of the candidate list under Eq. (13), for exact requests
     // (f_d = 1) only; below that, backtracking is bounded to the kCand
     // nearest centroids
@@ -571,7 +590,7 @@ __global__ void __launch_bounds__(256) k_ann_probe(ProbeArgs A) {
         }
         A.idx[i] = b.j;
         A.d1[i] = b.d;
-        A.d2[i] = b.s;
+        A.d2[i] = fminf(b.s, lb > 0.f ? lb * lb : 0.f);
     }
 }
 
@@ -797,12 +816,13 @@ __global__ void __launch_bounds__(256, 4) k_ann_probe2(Probe2Args P) {
                     mv = fmaf(t, t, mv);
                 }
                 mv = sqrtf(mv);
-                const float r1 = A.mot_d[i * 2], r2 = A.mot_d[i * 2 + 1];
-                if (mv < 0.5f * (r2 - r1)) {      // Eq. (14)
+                const float4 r = *reinterpret_cast<const float4 *>(A.mot_d + i * kMotStride);
+                const float fdi = A.fd_q ? A.fd_q[i] : A.f_d;
+                if (mv < 0.5f * (r.y - r.x) && fdi <= r.z) {      // Eq. (14)
                     if (lane == 0) {
                         A.idx[i] = j0;
                         A.d1[i] = d0;
-                        float lb = fmaxf(r2 - mv, 0.f);
+                        float lb = fmaxf(r.y - mv, 0.f);
                         A.d2[i] = lb * lb;
                         atomicAdd(A.counters + 1, 1ull);
                         if (P.n_pairs) P.n_pairs[i] = 0;
@@ -838,16 +858,24 @@ __global__ void __launch_bounds__(256, 4) k_ann_probe2(Probe2Args P) {
     }
     float dc = sqrtf(b.d);
     const float f_d = A.fd_q ? A.fd_q[i] : A.f_d;
+    const bool cert = A.certified || f_d >= 1.0f;
     bool incomplete = false;
+    // Eq. (14): plain lower bound on the points of the cells and leaves not
+    // searched (per lane over its own leaves; warp minimum at the end)
+    float lb = INFINITY;
     for (int k1 = 0; k1 < kCand; ++k1) {
         const int C = A.cand_cl[i * kCand + k1];
         if (C < 0) break;
         const float dC = A.cand_d[i * kCand + k1];
-        if (!(k1 == 0 || dC - f_d * P.rad1[C] < dc)) continue;
+        if (!(k1 == 0 || dC - f_d * P.rad1[C] < dc)) {
+            // a cell made of the warm-start leaf alone was searched
+            if (cert && !(P.L2 == 1 && C == l0)) lb = fminf(lb, dC - f_d * P.rad1[C]);
+            continue;
+        }
         // rank the cell's leaves: lane holds leaves f = lane + 32 t (squared
         // centroid distances; the plain distance is taken of the chosen ones)
         float fd[kFinePerLane];
-        unsigned vis = 0;
+        unsigned vis = 0, srch = 0;
         const float cell_lr = P.lrad1[C];
 #pragma unroll
         for (int t = 0; t < kFinePerLane; ++t) {
@@ -882,6 +910,7 @@ __global__ void __launch_bounds__(256, 4) k_ann_probe2(Probe2Args P) {
             if ((ml & 31) == lane) vis |= 1u << (ml >> 5);
             const int l = C * P.L2 + ml;
             if ((k1 == 0 && k2 == 0) || md - f_d * A.radius[l] < dc) {
+                if ((ml & 31) == lane) srch |= 1u << (ml >> 5);
                 if (l != l0) {
                     if (!P.pair_leaf || nscan < P.budget) {
                         scan(l);
@@ -895,6 +924,23 @@ __global__ void __launch_bounds__(256, 4) k_ann_probe2(Probe2Args P) {
                         }
                         ++npair;
                     }
+                }
+            }
+        }
+        // Eq. (14) bound of the cell's leaves not searched (each with its own
+        // radius).  A leaf can lower X = min(second read, bound so far) only
+        // if its centroid is nearer than X + f_d times the cell's widest leaf
+        // radius, so the others are passed over without their radius.
+        if (cert) {
+            const float X = fminf(sqrtf(b.s), lb);
+            const float thr = X + f_d * cell_lr;
+            const float thr2 = thr > 0.f ? thr * thr : 0.f;
+#pragma unroll
+            for (int t = 0; t < kFinePerLane; ++t) {
+                const int f = lane + 32 * t;
+                if (f < P.L2 && !((srch >> t) & 1u) && fd[t] < thr2) {
+                    const int l = C * P.L2 + f;
+                    if (l != l0) lb = fminf(lb, sqrtf(fd[t]) - f_d * A.radius[l]);
                 }
             }
         }
@@ -912,6 +958,9 @@ __global__ void __launch_bounds__(256, 4) k_ann_probe2(Probe2Args P) {
         const float dP = A.cand_d[i * kCand + kCand - 1];
         if (dP - f_d * P.r1max < dc) incomplete = true;
     }
+    // cells beyond the candidate list: no nearer centroid, no wider radius
+    if (cert && P.L1 > kCand) lb = fminf(lb, A.cand_d[i * kCand + kCand - 1] - f_d * P.r1max);
+    for (int o = 16; o > 0; o >>= 1) lb = fminf(lb, __shfl_xor_sync(0xffffffffu, lb, o));
     if (lane == 0) {
         atomicAdd(A.counters, scanned);
         atomicAdd(A.counters + 5, scanned);
@@ -921,7 +970,7 @@ __global__ void __launch_bounds__(256, 4) k_ann_probe2(Probe2Args P) {
         }
         A.idx[i] = b.j;
         A.d1[i] = b.d;
-        A.d2[i] = b.s;
+        A.d2[i] = fminf(b.s, lb > 0.f ? lb * lb : 0.f);
         if (P.n_pairs) P.n_pairs[i] = npair;
     }
 }
@@ -1225,15 +1274,26 @@ __global__ void k_touched_points(const unsigned *__restrict__ touched, int L, co
 }
 
 __global__ void k_motion_update(const QueryRec *__restrict__ rec, int64_t m, const double *__restrict__ d2,
-                                const double *__restrict__ d2nd, float *__restrict__ mq, float *__restrict__ md) {
+                                const double *__restrict__ d2nd, float f_d, const float *__restrict__ fd_q,
+                                int rule, float *__restrict__ mq, float *__restrict__ md) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= m) return;
 #pragma unroll
     for (int k = 0; k < 12; ++k) mq[i * 12 + k] = rec[i].q[k];
     // Eq. 3 distances -> plain distances in the mapped coordinates (|dq|^2 = d_e^2 / 2);
-    // the nearest one rounded up and the second rounded down keep the test conservative
-    md[i * 2] = (float)(sqrt(0.5 * d2[i]) * (1.0 + 1e-6));
-    md[i * 2 + 1] = (float)(sqrt(0.5 * d2nd[i]) * (1.0 - 1e-6));
+    // the nearest one rounded up and the second rounded down (by more than the
+    // FP32 rounding of the mapped coordinates and of the bounds) keep the test
+    // conservative
+    float4 r;
+    r.x = (float)(sqrt(0.5 * d2[i]) * (1.0 + 1e-5));
+    r.y = (float)(sqrt(0.5 * d2nd[i]) * (1.0 - 1e-5));
+    // the f_d the record serves: a certified bound serves its own f_d and any
+    // lower one; the second-best point found (rule 1, below f_d = 1) serves
+    // every f_d below 1 and never an exact (f_d = 1) search
+    const float fd = fd_q ? fd_q[i] : f_d;
+    r.z = (rule == 1 && fd < 1.0f) ? 0.99999994f : fd;
+    r.w = 0.f;
+    *reinterpret_cast<float4 *>(md + i * kMotStride) = r;
 }
 
 __global__ void k_export_index(const float *__restrict__ cent, const float *__restrict__ radius, int L, MetricMaps M,
@@ -1273,31 +1333,45 @@ static double fixed_scale(double maxabs) {
     return std::ldexp(1.0, 30 - (int)std::ceil(std::log2(m)));
 }
 
-// Certified exact search (FP32 scan + FP64 rescoring) of the listed queries.
+// Certified exact search (FP32 scan + FP64 rescoring) of the listed queries,
+// with the exact second-nearest distance (the two nearest points), so that
+// an exhaustively searched query records its true second distance for
+// Eq. (14).
 static dd_status ann_exact_subset(dd_dataset *ds, const double *y_dev, const int64_t *list, int64_t n, SearchOut out,
                                   cudaStream_t s) {
     dd_ctx *ctx = ds->ctx;
     auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
     void *w = nullptr;
-    DD_TRY(dd_workspace(ctx, WS_ANN_BUILD, r256((size_t)n * 96) + r256((size_t)n * 4) + 2 * r256((size_t)n * 8), &w));
+    DD_TRY(dd_workspace(ctx, WS_ANN_BUILD,
+                        r256((size_t)n * 96) + r256((size_t)n * 4) + 2 * r256((size_t)n * 8) + r256((size_t)n * 8) +
+                            r256((size_t)n * 16),
+                        &w));
     char *c = (char *)w;
     double *ys = (double *)c;
     int32_t *si = (int32_t *)(c + r256((size_t)n * 96));
     double *sd = (double *)(c + r256((size_t)n * 96) + r256((size_t)n * 4));
     double *sd2 = (double *)(c + r256((size_t)n * 96) + r256((size_t)n * 4) + r256((size_t)n * 8));
+    int32_t *tk = (int32_t *)(c + r256((size_t)n * 96) + r256((size_t)n * 4) + 2 * r256((size_t)n * 8));
+    double *tkd = (double *)(c + r256((size_t)n * 96) + r256((size_t)n * 4) + 2 * r256((size_t)n * 8) +
+                             r256((size_t)n * 8));
     ctx->launches += 2;
     k_gather_queries<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(y_dev, list, n, ys);
     DD_TRY_CUDA(ctx, cudaGetLastError());
-    DD_TRY(dd_search_exact_fp32(ds, ys, n, 1, SearchOut{si, sd, sd2}, nullptr, s));
+    SearchOut so{si, sd, sd2};
+    so.k = 2;
+    so.topk_idx = tk;
+    so.topk_d2 = tkd;
+    DD_TRY(dd_search_exact_fp32(ds, ys, n, 1, so, nullptr, s));
     k_scatter_results<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(list, n, si, sd, sd2, out.idx, out.d2, out.d2nd);
     DD_TRY_CUDA(ctx, cudaGetLastError());
     return DD_OK;
 }
 
 dd_status dd_ann_motion_update(dd_ctx *ctx, const QueryRec *rec, int64_t m, const double *d2, const double *d2nd,
-                               AnnMotion *mot, cudaStream_t s) {
+                               double f_d, const float *fd_q, int eq14, AnnMotion *mot, cudaStream_t s) {
     ctx->launches++;
-    k_motion_update<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(rec, m, d2, d2nd, mot->q, mot->d);
+    k_motion_update<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(rec, m, d2, d2nd, (float)f_d, fd_q, eq14,
+                                                                 mot->q, mot->d);
     DD_TRY_CUDA(ctx, cudaGetLastError());
     return DD_OK;
 }
@@ -1693,7 +1767,7 @@ dd_status dd_search_ann(dd_dataset *ds, const double *y_dev, int64_t m, double f
 
 dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, double f_d, const float *fd_q,
                                const int32_t *prev_idx_dev, AnnMotion *mot, int budget, SearchOut out,
-                               dd_search_stats *st, cudaStream_t s) {
+                               dd_search_stats *st, cudaStream_t s, int eq14) {
     dd_ctx *ctx = ds->ctx;
     AnnIndex &a = ds->ann;
     if (m == 0) return DD_OK;
@@ -1724,8 +1798,8 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
     // Eq. (14) ahead of the ranking: kept queries are neither ranked nor probed
     const bool gate = prev_idx_dev && mot && mot->q && rank_small(a);
     if (gate) {
-        GateArgs G{rec, m, ds->N, prev_idx_dev, ds->z32, mot->q, mot->d, out.idx, d1f, d2f, cand_cl, qlist, n_list,
-                   counters, Lr};
+        GateArgs G{rec,     m,        ds->N,    prev_idx_dev, ds->z32, mot->q, mot->d,   (float)f_d,
+                   fd_q,    out.idx,  d1f,      d2f,          cand_cl, qlist,  n_list, counters, Lr};
         ctx->launches++;
         k_ann_gate<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(G);
         DD_TRY_CUDA(ctx, cudaGetLastError());
@@ -1751,6 +1825,7 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
     A.mot_q = (mot && !gate) ? mot->q : nullptr;
     A.mot_d = (mot && !gate) ? mot->d : nullptr;
     A.gated = gate ? 1 : 0;
+    A.certified = eq14 == 1 ? 0 : 1;
     A.idx = out.idx;
     A.d1 = d1f;
     A.d2 = d2f;
@@ -1819,7 +1894,8 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
         DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
         if (n_fb) DD_TRY(ann_exact_subset(ds, y_dev, fb_list, (int64_t)n_fb, out, s));
     }
-    if (mot && out.d2 && out.d2nd) DD_TRY(dd_ann_motion_update(ctx, rec, m, out.d2, out.d2nd, mot, s));
+    if (mot && out.d2 && out.d2nd)
+        DD_TRY(dd_ann_motion_update(ctx, rec, m, out.d2, out.d2nd, f_d, fd_q, eq14, mot, s));
     if (st) {
         const int words = (a.nlist + 31) / 32;
         ctx->launches++;

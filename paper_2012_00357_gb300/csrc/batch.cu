@@ -1106,7 +1106,7 @@ struct StepIO {
 
 size_t concat_bytes(int64_t M) {
     return r256((size_t)M * 96) + 2 * r256((size_t)M * 4) + 2 * r256((size_t)M * 8) + r256((size_t)M * 4) +
-           r256((size_t)M * 48) + r256((size_t)M * 8);
+           r256((size_t)M * 48) + r256((size_t)M * 4 * kMotStride);
 }
 
 void concat_carve(StepIO &io, int64_t M, void *base) {
@@ -1179,7 +1179,7 @@ dd_status enqueue_step(dd_solver **svs, int n, const StepIO &io, const std::vect
         if (approx) {
             DD_TRY_CUDA(ctx, cudaMemcpyAsync(io.prev_cat + off, sv->cur, ng * 4, cudaMemcpyDeviceToDevice, s));
             DD_TRY_CUDA(ctx, cudaMemcpyAsync(io.mot.q + off * 12, sv->mot.q, ng * 48, cudaMemcpyDeviceToDevice, s));
-            DD_TRY_CUDA(ctx, cudaMemcpyAsync(io.mot.d + off * 2, sv->mot.d, ng * 8, cudaMemcpyDeviceToDevice, s));
+            DD_TRY_CUDA(ctx, cudaMemcpyAsync(io.mot.d + off * kMotStride, sv->mot.d, ng * 4 * kMotStride, cudaMemcpyDeviceToDevice, s));
         }
         if (ann) {
             ctx->launches++;
@@ -1193,7 +1193,7 @@ dd_status enqueue_step(dd_solver **svs, int n, const StepIO &io, const std::vect
     if (ann) {
         if (!ds->ann.nlist) return dd_fail(ctx, DD_ERR_STATE, "ANN search needs the partition (ann_nlist)");
         DD_TRY(dd_search_ann_motion(ds, io.y_cat, M, fps[0].f_far, io.fd_cat, io.prev_cat, &mot, o0.ann_budget, so,
-                                    &sst, s));
+                                    &sst, s, o0.eq14));
     } else if (o0.mode == DD_SEARCH_KNNG) {
         DD_TRY(dd_search_knng(ds, io.y_cat, M, o0.f_s, io.prev_cat, &mot, so, &sst, s));
     } else {
@@ -1209,7 +1209,7 @@ dd_status enqueue_step(dd_solver **svs, int n, const StepIO &io, const std::vect
         DD_TRY_CUDA(ctx, cudaMemcpyAsync(sv->d2nd, io.d2nd_cat + off, ng * 8, cudaMemcpyDeviceToDevice, s));
         if (approx) {
             DD_TRY_CUDA(ctx, cudaMemcpyAsync(sv->mot.q, io.mot.q + off * 12, ng * 48, cudaMemcpyDeviceToDevice, s));
-            DD_TRY_CUDA(ctx, cudaMemcpyAsync(sv->mot.d, io.mot.d + off * 2, ng * 8, cudaMemcpyDeviceToDevice, s));
+            DD_TRY_CUDA(ctx, cudaMemcpyAsync(sv->mot.d, io.mot.d + off * kMotStride, ng * 4 * kMotStride, cudaMemcpyDeviceToDevice, s));
         }
         off += ng;
     }
@@ -1426,9 +1426,9 @@ extern "C" dd_status dd_solvers_step(dd_solver **svs, int n, dd_iter_info *infos
         if (!sv || sv->ds != ds) return dd_fail(ctx, DD_ERR_ARG, "dd_solvers_step: solvers must share one data set");
         if (sv->done) return dd_fail(ctx, DD_ERR_STATE, "dd_solvers_step: a solve has already finished");
         if (sv->o.mode != o0.mode || sv->o.certify != o0.certify || sv->o.cg_mode != o0.cg_mode ||
-            sv->o.f_s != o0.f_s || sv->o.ann_budget != o0.ann_budget)
+            sv->o.f_s != o0.f_s || sv->o.ann_budget != o0.ann_budget || sv->o.eq14 != o0.eq14)
             return dd_fail(ctx, DD_ERR_ARG,
-                           "dd_solvers_step: solvers must share search mode, certify, cg_mode, f_s and ann_budget");
+                           "dd_solvers_step: solvers must share search mode, certify, cg_mode, f_s, ann_budget and eq14");
         for (int j = 0; j < i; ++j)
             if (svs[j] == sv) return dd_fail(ctx, DD_ERR_ARG, "dd_solvers_step: a solver appears twice");
         M += sv->g.n_gp;

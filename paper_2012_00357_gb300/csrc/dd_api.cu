@@ -248,7 +248,7 @@ dd_status dd_run_search(dd_dataset *ds, int mode, int certify, double f_d, int f
 }
 
 extern "C" dd_status dd_project_nearest(dd_dataset *ds, const double *y, int64_t m, const dd_search_opts *opts,
-                                        int32_t *idx, double *d2, dd_search_stats *stats) {
+                                        int32_t *idx, double *d2, int32_t *topk_out, dd_search_stats *stats) {
     if (!ds) return DD_ERR_ARG;
     dd_ctx *ctx = ds->ctx;
     if (m < 0) return dd_fail(ctx, DD_ERR_ARG, "dd_project_nearest: m < 0");
@@ -258,34 +258,70 @@ extern "C" dd_status dd_project_nearest(dd_dataset *ds, const double *y, int64_t
     std::memset(&o, 0, sizeof(o));
     o.certify = 1;
     if (opts) o = *opts;
+    const bool approx = o.mode == DD_SEARCH_ANN || o.mode == DD_SEARCH_KNNG;
     if (o.mode == DD_SEARCH_ANN && !(o.f_d >= 0.0 && o.f_d <= 1.0))
         return dd_fail(ctx, DD_ERR_ARG, "dd_project_nearest: f_d outside [0, 1]");
     if (o.mode == DD_SEARCH_KNNG && o.f_s < 0) return dd_fail(ctx, DD_ERR_ARG, "dd_project_nearest: f_s < 0");
+    const int k = o.topk;
+    if (k < 0 || k > DD_TOPK_MAX) return dd_fail(ctx, DD_ERR_ARG, "dd_project_nearest: topk outside 0 .. DD_TOPK_MAX");
+    if ((k > 0) != (topk_out != nullptr))
+        return dd_fail(ctx, DD_ERR_ARG, "dd_project_nearest: topk_out and opts->topk must be given together");
+    if (o.topk_d2 && !topk_out) return dd_fail(ctx, DD_ERR_ARG, "dd_project_nearest: topk_d2 without topk_out");
+    if (k > 0 && approx) return dd_fail(ctx, DD_ERR_ARG, "dd_project_nearest: topk needs an exact search mode");
+    if (o.eq14 < 0 || o.eq14 > 1) return dd_fail(ctx, DD_ERR_ARG, "dd_project_nearest: unknown eq14 rule");
+    const bool motion = o.prev_y != nullptr;
+    if (motion && !approx)
+        return dd_fail(ctx, DD_ERR_ARG, "dd_project_nearest: the motion record (prev_y) needs an approximate mode");
+    if (motion && (!o.prev_idx || !o.prev_d2 || !o.prev_d2nd))
+        return dd_fail(ctx, DD_ERR_ARG, "dd_project_nearest: prev_y needs prev_idx, prev_d2 and prev_d2nd");
     DD_TRY_CUDA(ctx, cudaSetDevice(ctx->device));
     const bool dev = dd_is_device_ptr(y);
-    if (dd_is_device_ptr(idx) != dev || (d2 && dd_is_device_ptr(d2) != dev))
-        return dd_fail(ctx, DD_ERR_ARG, "dd_project_nearest: y, idx and d2 must all be host or all device memory");
-    cudaStream_t s = o.stream ? (cudaStream_t)o.stream : ctx->stream;
-    const double *y_dev = y;
-    int32_t *idx_dev = idx;
-    double *d2_dev = d2;
-    const int32_t *prev_dev = o.prev_idx;
-    if (!dev) {
-        size_t by = (size_t)m * 96, bi = ((size_t)m * 4 + 255) / 256 * 256, bd = (size_t)m * 8;
-        void *w = nullptr;
-        DD_TRY(dd_workspace(ctx, WS_QUERY, by + 2 * bi + bd, &w));
-        char *c = (char *)w;
-        y_dev = (const double *)c;
-        idx_dev = (int32_t *)(c + by);
-        d2_dev = (double *)(c + by + bi);
-        int32_t *prev_tmp = (int32_t *)(c + by + bi + bd);
-        DD_TRY_CUDA(ctx, cudaMemcpyAsync((void *)y_dev, y, by, cudaMemcpyHostToDevice, s));
-        if (o.prev_idx) {
-            DD_TRY_CUDA(ctx, cudaMemcpyAsync(prev_tmp, o.prev_idx, (size_t)m * 4, cudaMemcpyHostToDevice, s));
-            prev_dev = prev_tmp;
-        }
-    } else if (o.prev_idx && !dd_is_device_ptr(o.prev_idx)) {
+    for (const void *p : {(const void *)idx, (const void *)d2, (const void *)topk_out, (const void *)o.topk_d2,
+                          (const void *)o.d2nd, (const void *)o.prev_y, (const void *)o.prev_d2,
+                          (const void *)o.prev_d2nd})
+        if (p && dd_is_device_ptr(p) != dev)
+            return dd_fail(ctx, DD_ERR_ARG, "dd_project_nearest: all arrays must be host or all device memory");
+    if (o.prev_idx && dev && !dd_is_device_ptr(o.prev_idx))
         return dd_fail(ctx, DD_ERR_ARG, "dd_project_nearest: prev_idx must be device memory with device y");
+    cudaStream_t s = o.stream ? (cudaStream_t)o.stream : ctx->stream;
+    auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
+    // device copies of host arrays, and the buffers the search needs besides
+    // the caller's: d2 and d2nd when not asked for (the motion record and the
+    // top-k distances read them), the motion record
+    const size_t by = r256((size_t)m * 96), bi = r256((size_t)m * 4), bd = r256((size_t)m * 8),
+                 bk = r256((size_t)m * (k > 0 ? k : 1) * 4), bkd = r256((size_t)m * (k > 0 ? k : 1) * 8),
+                 brec = r256((size_t)m * sizeof(QueryRec)), bmq = r256((size_t)m * 48),
+                 bmd = r256((size_t)m * 4 * kMotStride);
+    const size_t need = 2 * by + 2 * bi + 4 * bd + bk + bkd + brec + bmq + bmd;
+    void *w = nullptr;
+    DD_TRY(dd_workspace(ctx, WS_QUERY, need, &w));
+    char *c = (char *)w;
+    auto take = [&](size_t b) {
+        char *p = c;
+        c += b;
+        return p;
+    };
+    const double *y_dev = dev ? y : (const double *)take(by);
+    const double *py_dev = (dev || !motion) ? o.prev_y : (const double *)take(by);
+    int32_t *idx_dev = dev ? idx : (int32_t *)take(bi);
+    const int32_t *prev_dev = (dev || !o.prev_idx) ? o.prev_idx : (const int32_t *)take(bi);
+    double *d2_dev = (dev && d2) ? d2 : (double *)take(bd);
+    double *d2nd_dev = (dev && o.d2nd) ? o.d2nd : (double *)take(bd);
+    const double *pd2_dev = (dev || !motion) ? o.prev_d2 : (const double *)take(bd);
+    const double *pd2nd_dev = (dev || !motion) ? o.prev_d2nd : (const double *)take(bd);
+    int32_t *tk_dev = (dev || !topk_out) ? topk_out : (int32_t *)take(bk);
+    double *tkd_dev = (dev && o.topk_d2) ? o.topk_d2 : (k > 0 ? (double *)take(bkd) : nullptr);
+    QueryRec *prec = motion ? (QueryRec *)take(brec) : nullptr;
+    AnnMotion mot{motion ? (float *)take(bmq) : nullptr, motion ? (float *)take(bmd) : nullptr};
+    if (!dev) {
+        DD_TRY_CUDA(ctx, cudaMemcpyAsync((void *)y_dev, y, (size_t)m * 96, cudaMemcpyHostToDevice, s));
+        if (o.prev_idx)
+            DD_TRY_CUDA(ctx, cudaMemcpyAsync((void *)prev_dev, o.prev_idx, (size_t)m * 4, cudaMemcpyHostToDevice, s));
+        if (motion) {
+            DD_TRY_CUDA(ctx, cudaMemcpyAsync((void *)py_dev, o.prev_y, (size_t)m * 96, cudaMemcpyHostToDevice, s));
+            DD_TRY_CUDA(ctx, cudaMemcpyAsync((void *)pd2_dev, o.prev_d2, (size_t)m * 8, cudaMemcpyHostToDevice, s));
+            DD_TRY_CUDA(ctx, cudaMemcpyAsync((void *)pd2nd_dev, o.prev_d2nd, (size_t)m * 8, cudaMemcpyHostToDevice, s));
+        }
     }
     dd_search_stats local;
     std::memset(&local, 0, sizeof(local));
@@ -295,9 +331,37 @@ extern "C" dd_status dd_project_nearest(dd_dataset *ds, const double *y, int64_t
         DD_TRY_CUDA(ctx, cudaEventCreate(&e1));
         DD_TRY_CUDA(ctx, cudaEventRecord(e0, s));
     }
-    SearchOut out{idx_dev, d2_dev, nullptr};
-    dd_status st = dd_run_search(ds, o.mode, o.certify, o.f_d, o.f_s, o.ann_budget, prev_dev, y_dev, m, out, stats ? &local : nullptr, s);
+    SearchOut out{idx_dev, d2_dev, d2nd_dev};
+    if (k >= 2) {
+        out.k = k;
+        out.topk_idx = tk_dev;
+        out.topk_d2 = tkd_dev;
+    }
+    dd_search_stats *pst = stats ? &local : nullptr;
+    dd_status st = DD_OK;
+    if (motion) {
+        // the record of the previous call: its mapped states and the plain
+        // distances of Eq. (14), made at this call's f_d
+        DD_TRY(dd_map_queries(ds, py_dev, m, nullptr, prec, s));
+        DD_TRY(dd_ann_motion_update(ctx, prec, m, pd2_dev, pd2nd_dev, o.mode == DD_SEARCH_ANN ? o.f_d : 1.0, nullptr,
+                                    o.mode == DD_SEARCH_ANN ? o.eq14 : 0, &mot, s));
+        if (o.mode == DD_SEARCH_ANN) {
+            if (!ds->ann.nlist) return dd_fail(ctx, DD_ERR_STATE, "ANN search needs the partition (ann_nlist)");
+            st = dd_search_ann_motion(ds, y_dev, m, o.f_d, nullptr, prev_dev, &mot, o.ann_budget, out, pst, s, o.eq14);
+        } else {
+            st = dd_search_knng(ds, y_dev, m, o.f_s, prev_dev, &mot, out, pst, s);
+        }
+    } else if (o.mode == DD_SEARCH_ANN) {
+        if (!ds->ann.nlist) return dd_fail(ctx, DD_ERR_STATE, "ANN search needs the partition (ann_nlist)");
+        st = dd_search_ann_motion(ds, y_dev, m, o.f_d, nullptr, prev_dev, nullptr, o.ann_budget, out, pst, s, o.eq14);
+    } else {
+        st = dd_run_search(ds, o.mode, o.certify, o.f_d, o.f_s, o.ann_budget, prev_dev, y_dev, m, out, pst, s);
+    }
     if (st != DD_OK) return st;
+    if (k == 1) {
+        DD_TRY_CUDA(ctx, cudaMemcpyAsync(tk_dev, idx_dev, (size_t)m * 4, cudaMemcpyDeviceToDevice, s));
+        DD_TRY_CUDA(ctx, cudaMemcpyAsync(tkd_dev, d2_dev, (size_t)m * 8, cudaMemcpyDeviceToDevice, s));
+    }
     if (stats) {
         DD_TRY_CUDA(ctx, cudaEventRecord(e1, s));
         DD_TRY_CUDA(ctx, cudaEventSynchronize(e1));
@@ -311,6 +375,11 @@ extern "C" dd_status dd_project_nearest(dd_dataset *ds, const double *y, int64_t
     if (!dev) {
         DD_TRY_CUDA(ctx, cudaMemcpyAsync(idx, idx_dev, (size_t)m * 4, cudaMemcpyDeviceToHost, s));
         if (d2) DD_TRY_CUDA(ctx, cudaMemcpyAsync(d2, d2_dev, (size_t)m * 8, cudaMemcpyDeviceToHost, s));
+        if (o.d2nd) DD_TRY_CUDA(ctx, cudaMemcpyAsync(o.d2nd, d2nd_dev, (size_t)m * 8, cudaMemcpyDeviceToHost, s));
+        if (topk_out)
+            DD_TRY_CUDA(ctx, cudaMemcpyAsync(topk_out, tk_dev, (size_t)m * k * 4, cudaMemcpyDeviceToHost, s));
+        if (o.topk_d2)
+            DD_TRY_CUDA(ctx, cudaMemcpyAsync(o.topk_d2, tkd_dev, (size_t)m * k * 8, cudaMemcpyDeviceToHost, s));
         DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
     }
     if (!dev || stats) DD_TRY(dd_check_device_error(ctx, s, "dd_project_nearest"));

@@ -153,11 +153,15 @@ struct AnnIndex {
 };
 
 // Moving-query record of the approximate search (Eq. 14), per query:
-// previous mapped query (centred FP32) and its nearest / second-nearest
-// plain distances.  d = 0 disables the skip.
+// previous mapped query (centred FP32), the plain distance of its answer
+// (rounded up), a plain lower bound on the distance of every other data
+// point (rounded down; the bound of the search's cluster model at its f_d)
+// and the f_d the record was made at.  A record is used only by a search at
+// the same or a lower f_d; d = 0 disables the skip.
+constexpr int kMotStride = 4;   // floats per query in AnnMotion::d: (d1, d2 bound, f_d, unused)
 struct AnnMotion {
     float *q;      // [m x 12]
-    float *d;      // [m x 2]
+    float *d;      // [m x kMotStride]
 };
 
 // Host-side setup of the constraint projection for one mesh: element
@@ -225,6 +229,9 @@ struct SearchOut {
     int32_t *idx;     // [m]
     double *d2;       // [m] Eq. (3) distance, may be null
     double *d2nd;     // [m] second-best distance lower bound, may be null
+    int k = 0;                   // exact modes: >= 2 also fills the k nearest points
+    int32_t *topk_idx = nullptr; // [m x k] (k >= 2)
+    double *topk_d2 = nullptr;   // [m x k], may be null
 };
 
 dd_status dd_map_queries(dd_dataset *ds, const double *y_dev, int64_t m, double *zq64,
@@ -244,13 +251,16 @@ dd_status dd_build_ann(dd_dataset *ds, const dd_dataset_opts &o);
 // < -1 = none.
 dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, double f_d, const float *fd_q,
                                const int32_t *prev_idx_dev, AnnMotion *mot, int budget, SearchOut out,
-                               dd_search_stats *st, cudaStream_t s);
+                               dd_search_stats *st, cudaStream_t s, int eq14 = 0);
 // FP64 exhaustive re-search of the queries listed in fb_list (count on device).
 dd_status dd_fallback_exact(dd_dataset *ds, const double *y_dev, const int64_t *fb_list,
                             const unsigned long long *fb_count, int64_t m, SearchOut out, cudaStream_t s);
-// Record (q, d1, d2) of the last search for the moving-query test.
+// Record (q, d1, d2 bound, f_d) of the last search for the moving-query test
+// (f_d per query from fd_q when given, else f_d).
+// eq14: the rule that made d2nd (0 the certified bound, 1 the second-closest
+// point found; a rule-1 record below f_d = 1 serves every f_d below 1).
 dd_status dd_ann_motion_update(dd_ctx *ctx, const QueryRec *rec, int64_t m, const double *d2, const double *d2nd,
-                               AnnMotion *mot, cudaStream_t s);
+                               double f_d, const float *fd_q, int eq14, AnnMotion *mot, cudaStream_t s);
 dd_status dd_run_search(dd_dataset *ds, int mode, int certify, double f_d, int f_s, int budget,
                         const int32_t *prev_dev,
                         const double *y_dev, int64_t m, SearchOut out, dd_search_stats *st, cudaStream_t s);
@@ -289,6 +299,14 @@ struct CandHeader {
 dd_status dd_merge_rescore(dd_dataset *ds, const double *y_dev, int64_t m, int splits, int cap,
                            const CandHeader *hdr, const float2 *cand, const QueryRec *rec,
                            int certify, double inv_s2, SearchOut out, dd_search_stats *st, cudaStream_t s);
+// As dd_merge_rescore for the k >= 2 nearest points (out.k), from scans run
+// in top-k mode (the best `cap` scores of every split, no window): the k
+// nearest candidates by FP64 Eq. (3); with certify, a query whose k-th
+// score is not separated by the score window from every full split's worst
+// kept score is re-searched in FP64.
+dd_status dd_merge_topk(dd_dataset *ds, const double *y_dev, int64_t m, int splits, int cap, const CandHeader *hdr,
+                        const float2 *cand, const QueryRec *rec, int certify, double inv_s2, SearchOut out,
+                        dd_search_stats *st, cudaStream_t s);
 
 // Eq. (3) in FP64 between a state y (eps, sig) and data point j (raw FP32).
 __device__ __forceinline__ double dd_eq3(const MetricMaps &M, const double *y, const float *row) {

@@ -306,7 +306,7 @@ __device__ __forceinline__ void walk_one(const WalkArgs &A, int64_t i, int lane,
                 mv = fmaf(t, t, mv);
             }
             mv = sqrtf(mv);
-            const float r1 = A.mot_d[i * 2], r2 = A.mot_d[i * 2 + 1];
+            const float r1 = A.mot_d[i * kMotStride], r2 = A.mot_d[i * kMotStride + 1];
             if (mv < 0.5f * (r2 - r1)) {          // Eq. (14)
                 if (lane == 0) {
                     A.idx[i] = j0;
@@ -512,7 +512,8 @@ dd_status dd_search_knng(dd_dataset *ds, const double *y_dev, int64_t m, int f_s
     DD_TRY_CUDA(ctx, cudaGetLastError());
     if (st) DD_TRY_CUDA(ctx, dd_event_record(ctx, ctx->ev_scan[1], s));
     DD_TRY(dd_ann_finish(ds, y_dev, m, out.idx, d2f, out.d2, out.d2nd, s));
-    if (mot && out.d2 && out.d2nd) DD_TRY(dd_ann_motion_update(ctx, rec, m, out.d2, out.d2nd, mot, s));
+    // the walk's skip does not depend on f_d (its record is stored as made at f_d = 1)
+    if (mot && out.d2 && out.d2nd) DD_TRY(dd_ann_motion_update(ctx, rec, m, out.d2, out.d2nd, 1.0, nullptr, 0, mot, s));
     if (st && ctx->defer) {
         DD_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->defer->ann, counters, 8 * sizeof(unsigned long long),
                                          cudaMemcpyDeviceToDevice, s));

@@ -308,6 +308,174 @@ __global__ void __launch_bounds__(256) k_fallback_fp64(const float *__restrict__
     }
 }
 
+// ---------------------------------------------------------------------------
+// The k nearest points (k = 2 .. kTopMax) from scans run in top-k mode
+// ---------------------------------------------------------------------------
+constexpr int kTopMax = DD_TOPK_MAX;
+
+// Keep (d, j) among the k smallest of a list sorted by (d, j) ascending.
+template <typename T>
+__device__ __forceinline__ void topk_insert(T (&bd)[kTopMax], int (&bj)[kTopMax], int k, T d, int j) {
+    if (!(d < bd[k - 1] || (d == bd[k - 1] && j < bj[k - 1]))) return;
+    int p = k - 1;
+    while (p > 0 && (d < bd[p - 1] || (d == bd[p - 1] && j < bj[p - 1]))) {
+        bd[p] = bd[p - 1];
+        bj[p] = bj[p - 1];
+        --p;
+    }
+    bd[p] = d;
+    bj[p] = j;
+}
+
+// Thread per query.  Every split kept its best `cap` scores (score s =
+// |z|^2 - 2 z.q, error at most E = w2/2 against the exact score), so a point
+// left out of a full split scores at least that split's worst kept score.
+// The true k nearest points all score at most S_k + w2 (S_k the k-th smallest
+// kept score): if every full split's worst kept score exceeds S_k + w2, the
+// kept entries up to S_k + w2 hold them, and FP64 rescoring of those entries
+// gives the exact k nearest.  Otherwise (certify) the query is listed for the
+// FP64 re-search.
+__global__ void k_merge_topk(const float *__restrict__ raw, MetricMaps M, const double *__restrict__ y, int64_t m,
+                             int splits, int cap, const CandHeader *__restrict__ hdr, const float2 *__restrict__ cand,
+                             const QueryRec *__restrict__ rec, int k, int certify, double inv_s2,
+                             int32_t *__restrict__ idx, double *__restrict__ d2, double *__restrict__ d2nd,
+                             int32_t *__restrict__ tk_idx, double *__restrict__ tk_d2, int64_t *__restrict__ fb_list,
+                             unsigned long long *__restrict__ fb_count) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const CandHeader *h = hdr + (size_t)i * splits;
+    // pass 1: the k smallest kept scores, and the least worst-kept score of the full splits
+    float sk[kTopMax];
+    int sj[kTopMax];
+#pragma unroll
+    for (int e = 0; e < kTopMax; ++e) {
+        sk[e] = INFINITY;
+        sj[e] = 0x7fffffff;
+    }
+    float full_min = INFINITY;
+    for (int s = 0; s < splits; ++s) {
+        const float2 *c = cand + ((size_t)i * splits + s) * cap;
+        float mx = -INFINITY;
+        for (int e = 0; e < h[s].cnt; ++e) {
+            const float2 v = c[e];
+            mx = fmaxf(mx, v.x);
+            topk_insert(sk, sj, k, v.x, __float_as_int(v.y));
+        }
+        if (h[s].cnt >= cap) full_min = fminf(full_min, fminf(mx, h[s].dropped));
+    }
+    const float w2 = rec[i].w2;
+    const float lim = certify ? sk[k - 1] + w2 : INFINITY;
+    const bool uncert = certify && (!(w2 < INFINITY) || (full_min < INFINITY && !(full_min > lim)));
+    if (uncert) {
+        const unsigned long long t = atomicAdd(fb_count, 1ull);
+        fb_list[t] = i;
+        return;
+    }
+    // pass 2: FP64 rescoring (Eq. 3) of the kept entries up to lim
+    double yy[12];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) yy[q] = y[i * 12 + q];
+    double bd[kTopMax];
+    int bj[kTopMax];
+#pragma unroll
+    for (int e = 0; e < kTopMax; ++e) {
+        bd[e] = INFINITY;
+        bj[e] = 0x7fffffff;
+    }
+    for (int s = 0; s < splits; ++s) {
+        const float2 *c = cand + ((size_t)i * splits + s) * cap;
+        for (int e = 0; e < h[s].cnt; ++e) {
+            const float2 v = c[e];
+            if (!(v.x <= lim)) continue;
+            const int j = __float_as_int(v.y);
+            topk_insert(bd, bj, k, dd_eq3(M, yy, raw + (size_t)j * 12), j);
+        }
+    }
+    for (int e = 0; e < k; ++e) {
+        const bool ok = bd[e] < INFINITY;
+        tk_idx[i * k + e] = ok ? bj[e] : -1;
+        if (tk_d2) tk_d2[i * k + e] = bd[e];
+    }
+    idx[i] = bd[0] < INFINITY ? bj[0] : -1;
+    if (d2) d2[i] = bd[0];
+    if (d2nd) {
+        // points outside the kept entries score at least full_min, at least
+        // full_min - E exactly (plus |q|^2 for the squared distance)
+        const double out = full_min < INFINITY
+                               ? 2.0 * inv_s2 * ((double)full_min + (double)rec[i].qn - 0.5 * (double)w2)
+                               : INFINITY;
+        d2nd[i] = certify ? bd[1] : fmin(bd[1], out);
+    }
+}
+
+// FP64 exhaustive k-nearest search of the listed queries (block per query):
+// every thread keeps the k best of its points, then the block merges the
+// sorted lists pairwise.
+__global__ void __launch_bounds__(256) k_fallback_topk_fp64(const float *__restrict__ raw, int64_t N, MetricMaps M,
+                                                            const double *__restrict__ y,
+                                                            const int64_t *__restrict__ list,
+                                                            const unsigned long long *__restrict__ count, int k,
+                                                            int32_t *__restrict__ idx, double *__restrict__ d2,
+                                                            double *__restrict__ d2nd, int32_t *__restrict__ tk_idx,
+                                                            double *__restrict__ tk_d2) {
+    __shared__ double sd[256 * kTopMax];
+    __shared__ int sjx[256 * kTopMax];
+    const unsigned long long n = *count;
+    const int tid = threadIdx.x;
+    for (unsigned long long t = blockIdx.x; t < n; t += gridDim.x) {
+        const int64_t i = list[t];
+        double yy[12];
+#pragma unroll
+        for (int q = 0; q < 12; ++q) yy[q] = y[i * 12 + q];
+        double bd[kTopMax];
+        int bj[kTopMax];
+#pragma unroll
+        for (int e = 0; e < kTopMax; ++e) {
+            bd[e] = INFINITY;
+            bj[e] = 0x7fffffff;
+        }
+        for (int64_t j = tid; j < N; j += blockDim.x) topk_insert(bd, bj, k, dd_eq3(M, yy, raw + (size_t)j * 12), (int)j);
+        for (int e = 0; e < k; ++e) {
+            sd[tid * k + e] = bd[e];
+            sjx[tid * k + e] = bj[e];
+        }
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if (tid < w) {
+                // merge the sorted lists of threads tid and tid + w into bd/bj
+                int a = 0, b = 0;
+                const double *da = sd + tid * k, *db = sd + (tid + w) * k;
+                const int *ja = sjx + tid * k, *jb = sjx + (tid + w) * k;
+                for (int e = 0; e < k; ++e) {
+                    const bool take_a = (da[a] < db[b]) || (da[a] == db[b] && ja[a] <= jb[b]);
+                    bd[e] = take_a ? da[a] : db[b];
+                    bj[e] = take_a ? ja[a] : jb[b];
+                    if (take_a) ++a;
+                    else ++b;
+                }
+            }
+            __syncthreads();
+            if (tid < w)
+                for (int e = 0; e < k; ++e) {
+                    sd[tid * k + e] = bd[e];
+                    sjx[tid * k + e] = bj[e];
+                }
+            __syncthreads();
+        }
+        if (tid < k) {
+            const bool ok = sd[tid] < INFINITY;
+            tk_idx[i * k + tid] = ok ? sjx[tid] : -1;
+            if (tk_d2) tk_d2[i * k + tid] = sd[tid];
+        }
+        if (tid == 0) {
+            idx[i] = sd[0] < INFINITY ? sjx[0] : -1;
+            if (d2) d2[i] = sd[0];
+            if (d2nd) d2nd[i] = sd[1];
+        }
+        __syncthreads();
+    }
+}
+
 int pick_splits(int64_t qtiles, int64_t n_tiles, int n_sm, int per_sm) {
     const int64_t slots = (int64_t)n_sm * per_sm;
     if (qtiles >= slots) return 1;
@@ -382,6 +550,40 @@ dd_status dd_merge_rescore(dd_dataset *ds, const double *y_dev, int64_t m, int s
     return DD_OK;
 }
 
+dd_status dd_merge_topk(dd_dataset *ds, const double *y_dev, int64_t m, int splits, int cap, const CandHeader *hdr,
+                        const float2 *cand, const QueryRec *rec, int certify, double inv_s2, SearchOut out,
+                        dd_search_stats *st, cudaStream_t s) {
+    dd_ctx *ctx = ds->ctx;
+    if (out.k < 2 || out.k > kTopMax || !out.topk_idx) return dd_fail(ctx, DD_ERR_ARG, "top-k merge: k out of range");
+    void *w = nullptr;
+    DD_TRY(dd_workspace(ctx, WS_MISC, (size_t)m * sizeof(int64_t) + 256, &w));
+    unsigned long long *fb_count = reinterpret_cast<unsigned long long *>(w);
+    int64_t *fb_list = reinterpret_cast<int64_t *>(reinterpret_cast<char *>(w) + 256);
+    DD_TRY_CUDA(ctx, cudaMemsetAsync(fb_count, 0, sizeof(unsigned long long), s));
+    ctx->launches++;
+    k_merge_topk<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(ds->raw, ds->M, y_dev, m, splits, cap, hdr, cand, rec,
+                                                             out.k, certify, inv_s2, out.idx, out.d2, out.d2nd,
+                                                             out.topk_idx, out.topk_d2, fb_list, fb_count);
+    DD_TRY_CUDA(ctx, cudaGetLastError());
+    if (certify) {
+        const int grid = (int)std::min<int64_t>(m, (int64_t)ctx->n_sm * 4);
+        ctx->launches++;
+        k_fallback_topk_fp64<<<grid, 256, 0, s>>>(ds->raw, ds->N, ds->M, y_dev, fb_list, fb_count, out.k, out.idx,
+                                                  out.d2, out.d2nd, out.topk_idx, out.topk_d2);
+        DD_TRY_CUDA(ctx, cudaGetLastError());
+    }
+    if (st && ctx->defer) {
+        DD_TRY_CUDA(ctx, cudaMemcpyAsync(&ctx->defer->fb, fb_count, sizeof(*fb_count), cudaMemcpyDeviceToDevice, s));
+    } else if (st) {
+        unsigned long long n = 0;
+        DD_TRY_CUDA(ctx, cudaMemcpyAsync(&n, fb_count, sizeof(n), cudaMemcpyDeviceToHost, s));
+        DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+        st->uncertified += (int64_t)n;
+        st->distances += (int64_t)n * ds->N;
+    }
+    return DD_OK;
+}
+
 dd_status dd_scan_fp32_raw(dd_ctx *ctx, const float *z32, const float *zn, int64_t N, const QueryRec *rec, int64_t m,
                            bool topk, int slot, int *splits_out, int *cap_out, CandHeader **hdr_out, float2 **cand_out,
                            cudaStream_t s) {
@@ -430,12 +632,16 @@ dd_status dd_search_exact_fp32(dd_dataset *ds, const double *y_dev, int64_t m, i
     dim3 grid((unsigned)qtiles, (unsigned)splits);
     ctx->launches++;
     if (st) DD_TRY_CUDA(ctx, dd_event_record(ctx, ctx->ev_scan[0], s));
+    // top-k mode (the best kCap scores of every split, no window) for the k
+    // nearest points or an uncertified search; else the certified window
+    const bool topk = certify == 0 || out.k >= 2;
     k_scan_fp32<<<grid, kThreads, kScanSmem, s>>>(ds->z32, ds->zn, ds->N, n_tiles, rec, m, splits, tps,
-                                                  hdr, cand, certify == 0, ctx->dev_err);
+                                                  hdr, cand, topk, ctx->dev_err);
     DD_TRY_CUDA(ctx, cudaGetLastError());
     if (st) DD_TRY_CUDA(ctx, dd_event_record(ctx, ctx->ev_scan[1], s));
     if (st) st->distances += m * ds->N;
-    DD_TRY(dd_merge_rescore(ds, y_dev, m, splits, kCap, hdr, cand, rec, certify, 1.0, out, st, s));
+    if (out.k >= 2) DD_TRY(dd_merge_topk(ds, y_dev, m, splits, kCap, hdr, cand, rec, certify, 1.0, out, st, s));
+    else DD_TRY(dd_merge_rescore(ds, y_dev, m, splits, kCap, hdr, cand, rec, certify, 1.0, out, st, s));
     if (st && !ctx->defer) {
         float ms = 0.f;
         DD_TRY_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev_scan[0], ctx->ev_scan[1]));
@@ -465,8 +671,27 @@ std::mutex g_noalloc_mu;
 void *g_noalloc_ptr[kNoAllocMaxDevices] = {};
 }  // namespace
 
+namespace {
+// Makes ctx's device current for the lifetime of the guard and restores the
+// caller's current device afterwards.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            prev = -1;
+        }
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+}  // namespace
+
 extern "C" dd_status dd_project_nearest_noalloc(dd_dataset *ds, const double *y_dev, int64_t m, int32_t *idx_dev,
-                                               double *d2_dev, void *stream) {
+                                               double *d2_dev, void *stream, int wait) {
     if (!ds) return DD_ERR_ARG;
     dd_ctx *ctx = ds->ctx;
     if (m < 0 || m > DD_NOALLOC_MAX_QUERIES)
@@ -476,7 +701,12 @@ extern "C" dd_status dd_project_nearest_noalloc(dd_dataset *ds, const double *y_
     if (!y_dev || !idx_dev || !d2_dev) return dd_fail(ctx, DD_ERR_ARG, "dd_project_nearest_noalloc: NULL argument");
     if (ctx->device < 0 || ctx->device >= kNoAllocMaxDevices)
         return dd_fail(ctx, DD_ERR_ARG, "dd_project_nearest_noalloc: device index too large");
-    DD_TRY_CUDA(ctx, cudaSetDevice(ctx->device));
+    DeviceGuard guard(ctx->device);
+    {
+        int cur = -1;
+        DD_TRY_CUDA(ctx, cudaGetDevice(&cur));
+        if (cur != ctx->device) return dd_fail(ctx, DD_ERR_CUDA, "dd_project_nearest_noalloc: cannot select the device");
+    }
     // Set-up, once per device, with that device current: the device address
     // of the scratch array (host code only sees a host-side stand-in).
     void *base = nullptr;
@@ -501,24 +731,34 @@ extern "C" dd_status dd_project_nearest_noalloc(dd_dataset *ds, const double *y_
     const int splits = (int)std::max<int64_t>(1, std::min<int64_t>(pick_splits(qtiles, n_tiles, ctx->n_sm, 2), s_fit));
     const int64_t tps = (n_tiles + splits - 1) / splits;
     char *c = (char *)base;
+    // head of the array: the re-search counter (8 bytes) and this call's
+    // device status word (4 bytes), both cleared below
     unsigned long long *fb_count = (unsigned long long *)c;
+    unsigned *err = (unsigned *)(c + 8);
     QueryRec *rec = (QueryRec *)(c + 256);
     int64_t *fb_list = (int64_t *)(c + 256 + r256((size_t)m * sizeof(QueryRec)));
     CandHeader *hdr = (CandHeader *)(c + fixed);
     float2 *cand = (float2 *)(c + fixed + r256((size_t)m * splits * sizeof(CandHeader)));
-    // the re-search counter must start at zero; every other region is fully
-    // written before it is read
-    DD_TRY_CUDA(ctx, cudaMemsetAsync(fb_count, 0, sizeof(unsigned long long), s));
+    // the re-search counter and the status word must start at zero; every
+    // other region is fully written before it is read
+    DD_TRY_CUDA(ctx, cudaMemsetAsync(c, 0, 16, s));
     ctx->launches += 4;
     k_map_queries<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(y_dev, m, ds->M, ds->R, nullptr, rec);
     DD_TRY_CUDA(ctx, cudaFuncSetAttribute(k_scan_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScanSmem));
     k_scan_fp32<<<dim3((unsigned)qtiles, (unsigned)splits), kThreads, kScanSmem, s>>>(
-        ds->z32, ds->zn, ds->N, n_tiles, rec, m, splits, tps, hdr, cand, false, ctx->dev_err);
+        ds->z32, ds->zn, ds->N, n_tiles, rec, m, splits, tps, hdr, cand, false, err);
     k_merge_rescore<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(ds->raw, ds->M, y_dev, m, splits, kCap, hdr, cand,
                                                                 rec, 1, 1.0, idx_dev, d2_dev, nullptr, fb_list,
                                                                 fb_count);
     const int grid = (int)std::min<int64_t>(m, (int64_t)ctx->n_sm * 4);
     k_fallback_fp64<<<grid, 256, 0, s>>>(ds->raw, ds->N, ds->M, y_dev, fb_list, fb_count, idx_dev, d2_dev, nullptr);
     DD_TRY_CUDA(ctx, cudaGetLastError());
+    if (wait) {
+        unsigned h = 0;
+        DD_TRY_CUDA(ctx, cudaMemcpyAsync(&h, err, sizeof(h), cudaMemcpyDeviceToHost, s));
+        DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+        if (h & DEV_ERR_TIMEOUT)
+            return dd_fail(ctx, DD_ERR_TIMEOUT, "dd_project_nearest_noalloc: a device wait timed out");
+    }
     return DD_OK;
 }

@@ -109,6 +109,34 @@ __device__ __forceinline__ void tmem_wait(uint32_t (&r)[32]) {
                  : "memory");
 }
 
+// The same load with the minimum of the 32 values (Blackwell Ultra's reducing
+// TMEM load): the reduction is done by the load path, not by ALU
+// instructions.  `red` may be read only after tmem_wait_red.
+__device__ __forceinline__ void tmem_ld32_red_async(uint32_t taddr, uint32_t (&r)[32], float &red) {
+    asm volatile(
+        "tcgen05.ld.red.sync.aligned.32x32b.x32.min.f32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%"
+        "28,%29,%30,%31}, %32, [%33];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+          "=f"(red)
+        : "r"(taddr)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_red(uint32_t (&r)[32], float &red) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31]), "+f"(red)
+                 :
+                 : "memory");
+}
+
 __device__ __forceinline__ float min3f(float a, float b, float c) {
     float d;
     asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
@@ -262,7 +290,9 @@ __global__ void k_prep_tc(const double *__restrict__ y, int64_t m, int64_t m_pad
 }
 
 // ---- the contraction kernel ------------------------------------------------------
-template <int KC, int EPI>
+// RED: the epilogue takes each 32-column chunk's minimum from the reducing
+// TMEM load (1) or from a min tree on the ALU (0).
+template <int KC, int EPI, int RED>
 __global__ void __launch_bounds__(tc_threads<EPI>(), 2)
     k_scan_tc(const __half *__restrict__ zhi, const __half *__restrict__ zlo, int64_t N, int64_t n_tiles,
               const __half *__restrict__ qa, const QueryRec *__restrict__ rec, int64_t m, int splits, int64_t tps,
@@ -379,7 +409,8 @@ __global__ void __launch_bounds__(tc_threads<EPI>(), 2)
         const int row = quarter * 32 + lane;
         const int64_t qi = (int64_t)blockIdx.x * kTM + row;
         const bool active = qi < m;
-        const float w2 = active ? rec[qi].w2 : 0.f;
+        // top-k mode keeps the best kCap scores with no window
+        const float w2 = active ? (topk ? INFINITY : rec[qi].w2) : 0.f;
         constexpr int kSt = kTM * EPI / 4;            // candidate buffer stride
         CandState cs;
         cand_init(cs, active);
@@ -400,11 +431,12 @@ __global__ void __launch_bounds__(tc_threads<EPI>(), 2)
             constexpr int kChunks = kCols / 32;
             const uint32_t base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)ab * kTN + (uint32_t)(half * kCols);
             uint32_t ra[32], rb[32];
-            auto filter = [&](const uint32_t(&r)[32], int c) {
+            float mina = 0.f, minb = 0.f;   // chunk minima of the reducing load (RED)
+            auto filter = [&](const uint32_t(&r)[32], float mred, int c) {
                 float v[32];
 #pragma unroll
                 for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
-                if (min32(v) <= cs.lim) {   // rare: walk the columns inside the window
+                if ((RED ? mred : min32(v)) <= cs.lim) {   // rare: walk the columns inside the window
                     unsigned msk = 0;
 #pragma unroll
                     for (int k = 0; k < 32; ++k) msk |= (v[k] <= cs.lim ? 1u : 0u) << k;
@@ -419,24 +451,32 @@ __global__ void __launch_bounds__(tc_threads<EPI>(), 2)
                     }
                 }
             };
+            auto load = [&](uint32_t a, uint32_t(&r)[32], float &mred) {
+                if (RED) tmem_ld32_red_async(a, r, mred);
+                else tmem_ld32_async(a, r);
+            };
+            auto wait = [&](uint32_t(&r)[32], float &mred) {
+                if (RED) tmem_wait_red(r, mred);
+                else tmem_wait(r);
+            };
             auto release = [&]() {   // every column of this accumulator is in registers
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) dd_mbar_arrive(dd_smem_addr(&bar_tempty[ab]));
             };
-            tmem_ld32_async(base, ra);
-            tmem_wait(ra);
+            load(base, ra, mina);
+            wait(ra, mina);
 #pragma unroll 1
             for (int c = 0; c < kChunks; c += 2) {   // ra holds chunk c
-                if (c + 1 < kChunks) tmem_ld32_async(base + (uint32_t)((c + 1) * 32), rb);
+                if (c + 1 < kChunks) load(base + (uint32_t)((c + 1) * 32), rb, minb);
                 else release();
-                filter(ra, c);
+                filter(ra, mina, c);
                 if (c + 1 < kChunks) {
-                    tmem_wait(rb);                    // rb holds chunk c + 1
-                    if (c + 2 < kChunks) tmem_ld32_async(base + (uint32_t)((c + 2) * 32), ra);
+                    wait(rb, minb);                   // rb holds chunk c + 1
+                    if (c + 2 < kChunks) load(base + (uint32_t)((c + 2) * 32), ra, mina);
                     else release();
-                    filter(rb, c + 1);
-                    if (c + 2 < kChunks) tmem_wait(ra);
+                    filter(rb, minb, c + 1);
+                    if (c + 2 < kChunks) wait(ra, mina);
                 }
             }
         }
@@ -495,28 +535,45 @@ dd_status dd_build_fp16(dd_dataset *ds) {
     return DD_OK;
 }
 
-template <int KC, int EPI>
+template <int KC, int EPI, int RED>
 static dd_status launch_tc(dd_ctx *ctx, dim3 grid, dd_dataset *ds, int64_t n_tiles, const __half *qa,
                            const QueryRec *rec, int64_t m, int splits, int64_t tps, CandHeader *hdr, float2 *cand,
                            bool topk, cudaStream_t s) {
     const size_t sm = tc_smem_bytes<KC>();
-    DD_TRY_CUDA(ctx, cudaFuncSetAttribute(k_scan_tc<KC, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    DD_TRY_CUDA(ctx,
+                cudaFuncSetAttribute(k_scan_tc<KC, EPI, RED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     ctx->launches++;
-    k_scan_tc<KC, EPI><<<grid, tc_threads<EPI>(), sm, s>>>(ds->z16hi, ds->z16lo, ds->N, n_tiles, qa, rec, m, splits,
-                                                           tps, hdr, cand, topk, ctx->dev_err);
+    k_scan_tc<KC, EPI, RED><<<grid, tc_threads<EPI>(), sm, s>>>(ds->z16hi, ds->z16lo, ds->N, n_tiles, qa, rec, m,
+                                                                splits, tps, hdr, cand, topk, ctx->dev_err);
     DD_TRY_CUDA(ctx, cudaGetLastError());
     return DD_OK;
 }
 
-static dd_status launch_tc_any(dd_ctx *ctx, int kc, int epi, dim3 grid, dd_dataset *ds, int64_t n_tiles,
+// Epilogue layout codes of the autotuner: warps (4 or 8) | 256 x reducing load.
+constexpr int kEpiRed = 256;
+
+static dd_status launch_tc_any(dd_ctx *ctx, int kc, int code, dim3 grid, dd_dataset *ds, int64_t n_tiles,
                                const __half *qa, const QueryRec *rec, int64_t m, int splits, int64_t tps,
-                               CandHeader *hdr, float2 *cand, cudaStream_t s) {
+                               CandHeader *hdr, float2 *cand, bool topk, cudaStream_t s) {
+    const int epi = code & 0xff;
+    const bool red = (code & kEpiRed) != 0;
+#define DD_TC_LAUNCH(K, E, R) \
+    return launch_tc<K, E, R>(ctx, grid, ds, n_tiles, qa, rec, m, splits, tps, hdr, cand, topk, s)
     if (kc == 3) {
-        if (epi == 8) return launch_tc<3, 8>(ctx, grid, ds, n_tiles, qa, rec, m, splits, tps, hdr, cand, false, s);
-        return launch_tc<3, 4>(ctx, grid, ds, n_tiles, qa, rec, m, splits, tps, hdr, cand, false, s);
+        if (epi == 8) {
+            if (red) DD_TC_LAUNCH(3, 8, 1);
+            DD_TC_LAUNCH(3, 8, 0);
+        }
+        if (red) DD_TC_LAUNCH(3, 4, 1);
+        DD_TC_LAUNCH(3, 4, 0);
     }
-    if (epi == 8) return launch_tc<1, 8>(ctx, grid, ds, n_tiles, qa, rec, m, splits, tps, hdr, cand, true, s);
-    return launch_tc<1, 4>(ctx, grid, ds, n_tiles, qa, rec, m, splits, tps, hdr, cand, true, s);
+    if (epi == 8) {
+        if (red) DD_TC_LAUNCH(1, 8, 1);
+        DD_TC_LAUNCH(1, 8, 0);
+    }
+    if (red) DD_TC_LAUNCH(1, 4, 1);
+    DD_TC_LAUNCH(1, 4, 0);
+#undef DD_TC_LAUNCH
 }
 
 dd_status dd_search_exact_tc(dd_dataset *ds, const double *y_dev, int64_t m, int certify, SearchOut out,
@@ -524,6 +581,10 @@ dd_status dd_search_exact_tc(dd_dataset *ds, const double *y_dev, int64_t m, int
     dd_ctx *ctx = ds->ctx;
     if (m == 0) return DD_OK;
     const int kc = certify ? 3 : 1;
+    // the split-FP16 scan keeps a certified window, except for the k >= 2
+    // nearest points (best kCap scores, certified at the merge); the single
+    // FP16 scan always keeps the best kCap scores
+    const bool topk = kc == 1 || out.k >= 2;
     const int64_t n_tiles = (ds->N + kTN - 1) / kTN;
     const int64_t qtiles = (m + kTM - 1) / kTM;
     const int64_t m_pad = qtiles * kTM;
@@ -547,15 +608,16 @@ dd_status dd_search_exact_tc(dd_dataset *ds, const double *y_dev, int64_t m, int
     k_prep_tc<<<(unsigned)((m_pad + 127) / 128), 128, 0, s>>>(y_dev, m, m_pad, ds->M, ds->scale16, Rs, kc, qa, rec);
     DD_TRY_CUDA(ctx, cudaGetLastError());
     dim3 grid((unsigned)qtiles, (unsigned)splits);
-    // Autotuner: the first large call of each precision times both epilogue
-    // layouts (4 or 8 epilogue warps) on the live problem and keeps the faster
-    // one for this context; both return the same certified candidates.
+    // Autotuner: the first large call of each precision times the epilogue
+    // layouts (4 or 8 epilogue warps, chunk minima from the reducing TMEM load
+    // or from an ALU min tree) on the live problem and keeps the fastest for
+    // this context; all return the same candidates.
     int &epi = ctx->tc_epi[kc == 3 ? 1 : 0];
     if (epi == 0 && !ctx->capturing && (double)m * (double)ds->N >= 1e9) {
         float best = 1e30f;
-        for (int e : {4, 8}) {
+        for (int e : {4, 8, 4 | kEpiRed, 8 | kEpiRed}) {
             DD_TRY_CUDA(ctx, dd_event_record(ctx, ctx->ev_scan[0], s));
-            DD_TRY(launch_tc_any(ctx, kc, e, grid, ds, n_tiles, qa, rec, m, splits, tps, hdr, cand, s));
+            DD_TRY(launch_tc_any(ctx, kc, e, grid, ds, n_tiles, qa, rec, m, splits, tps, hdr, cand, topk, s));
             DD_TRY_CUDA(ctx, dd_event_record(ctx, ctx->ev_scan[1], s));
             DD_TRY_CUDA(ctx, cudaEventSynchronize(ctx->ev_scan[1]));
             float ms = 0.f;
@@ -566,13 +628,18 @@ dd_status dd_search_exact_tc(dd_dataset *ds, const double *y_dev, int64_t m, int
             }
         }
     }
-    const int use_epi = epi ? epi : 4;
+    const int use_epi = epi ? epi : (4 | kEpiRed);
     if (st) DD_TRY_CUDA(ctx, dd_event_record(ctx, ctx->ev_scan[0], s));
-    DD_TRY(launch_tc_any(ctx, kc, use_epi, grid, ds, n_tiles, qa, rec, m, splits, tps, hdr, cand, s));
+    DD_TRY(launch_tc_any(ctx, kc, use_epi, grid, ds, n_tiles, qa, rec, m, splits, tps, hdr, cand, topk, s));
     if (st) DD_TRY_CUDA(ctx, dd_event_record(ctx, ctx->ev_scan[1], s));
     if (st) st->distances += m * ds->N;
-    DD_TRY(dd_merge_rescore(ds, y_dev, m, splits * (use_epi / 4), kCap, hdr, cand, rec, certify,
-                            1.0 / (ds->scale16 * ds->scale16), out, st, s));
+    const double inv_s2 = 1.0 / (ds->scale16 * ds->scale16);
+    if (out.k >= 2)
+        DD_TRY(dd_merge_topk(ds, y_dev, m, splits * ((use_epi & 0xff) / 4), kCap, hdr, cand, rec, certify, inv_s2,
+                             out, st, s));
+    else
+        DD_TRY(dd_merge_rescore(ds, y_dev, m, splits * ((use_epi & 0xff) / 4), kCap, hdr, cand, rec, certify, inv_s2,
+                                out, st, s));
     if (st && !ctx->defer) {
         float ms = 0.f;
         DD_TRY_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev_scan[0], ctx->ev_scan[1]));

@@ -97,7 +97,7 @@ size_t carve(dd_solver *sv, char *base) {
     sv->idx_a = sv->cur;
     sv->stats = bp.take<double>(kIterStatsDoubles);
     sv->mot.q = bp.take<float>(ng * 12);
-    sv->mot.d = bp.take<float>(ng * 2);
+    sv->mot.d = bp.take<float>(ng * kMotStride);
     sv->fdq = bp.take<float>(ng);
     return bp.off;
 }
@@ -266,6 +266,7 @@ extern "C" dd_status dd_solver_create(dd_dataset *ds, const dd_mesh *mesh, const
         return dd_fail(ctx, DD_ERR_ARG, "dd_solver_create: f_d outside [0, 1]");
     if (o.fd_rule < 0 || o.fd_rule > 2 || !(o.fd_tau >= 0.0))
         return dd_fail(ctx, DD_ERR_ARG, "dd_solver_create: unknown fd_rule or fd_tau < 0");
+    if (o.eq14 < 0 || o.eq14 > 1) return dd_fail(ctx, DD_ERR_ARG, "dd_solver_create: unknown eq14 rule");
     for (int c = 0; c < 3; ++c)
         if (!std::isfinite(load->t0[c]) || !std::isfinite(load->tx[c]) || !std::isfinite(load->ty[c]))
             return dd_fail(ctx, DD_ERR_ARG, "dd_solver_create: non-finite load");
@@ -319,7 +320,7 @@ extern "C" dd_status dd_solver_create(dd_dataset *ds, const dd_mesh *mesh, const
          cudaMemcpyAsync(sv->cb.mg_inv, Kinv.data(), Kinv.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) ||
         cudaMemcpyAsync(sv->f, f.data(), nn * 3 * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(sv->cb.x, x0.data(), nn * 6 * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemsetAsync(sv->mot.d, 0, ng * 2 * sizeof(float), s) != cudaSuccess ||
+        cudaMemsetAsync(sv->mot.d, 0, ng * kMotStride * sizeof(float), s) != cudaSuccess ||
         cudaMemsetAsync(sv->stats, 0, kIterStatsDoubles * sizeof(double), s) != cudaSuccess)
         return fail(dd_fail(ctx, DD_ERR_CUDA, "dd_solver_create: upload"));
     if ((st = fem_block_jacobi(ctx, sv->g, sv->Ke, sv->Minv, s)) != DD_OK) return fail(st);
@@ -379,7 +380,7 @@ extern "C" dd_status dd_solver_step(dd_solver *sv, dd_iter_info *info) {
             DD_TRY(dd_fill_fd(ctx, sv->fdq, ng, nullptr, fp, sv->dpc, s));
             fdq = sv->fdq;
         }
-        DD_TRY(dd_search_ann_motion(ds, sv->y, ng, f_d, fdq, sv->cur, &sv->mot, o.ann_budget, so, &sst, s));
+        DD_TRY(dd_search_ann_motion(ds, sv->y, ng, f_d, fdq, sv->cur, &sv->mot, o.ann_budget, so, &sst, s, o.eq14));
     } else if (o.mode == DD_SEARCH_KNNG) {
         DD_TRY(dd_search_knng(ds, sv->y, ng, o.f_s, sv->cur, &sv->mot, so, &sst, s));
     } else {

@@ -74,8 +74,9 @@ def test_rules_match_oracle(ctx, annset, f_d, warm):
     # FP32 (GPU) and FP64 (oracle) may decide a near-tie differently
     dg = ((Z[idx] - metric.to_z(y, C)) ** 2).sum(1)
     close = np.abs(dg - od) <= 1e-4 * od
-    print(f"f_d={f_d} warm={warm}: agree {same.mean():.4f}")
-    assert same.mean() >= 0.98 and np.all(same | close | (dg <= od * (1 + 1e-6)) | (~same).cumsum() < 12)
+    print(f"f_d={f_d} warm={warm}: agree {same.mean():.4f}, {int((~same).sum())} near-ties")
+    # every disagreement is an FP32 (GPU) / FP64 (oracle) near-tie
+    assert same.mean() >= 0.98 and np.all(same | close)
     if warm:
         assert np.all(dg <= ((Z[prev] - metric.to_z(y, C)) ** 2).sum(1) * (1 + 1e-6))
     assert np.allclose(metric.local_d2(y, data[idx].astype(np.float64), C), d2, rtol=1e-10)
@@ -125,7 +126,9 @@ def test_ann_solve_ramp_close_to_exact(ctx):
     print(f"exact d2 {re.d2_pd[-1]:.6e} ({re.iters} it), ANN d2 {ra.d2_pd[-1]:.6e} ({ra.iters} it), rel {rel:.3e}")
     assert ra.converged
     assert rel < 0.05
-    assert np.all(np.diff(ra.d2_pd[5:]) <= 1e-12 * ra.d2_pd[0]) or True
+    # the warm start never returns a farther point than the previous one and
+    # P_C minimises over the constraint set, so the distance never grows
+    assert np.all(np.diff(ra.d2_pd) <= 1e-10 * ra.d2_pd[0])
 
 
 @pytest.fixture(scope="module")
@@ -164,8 +167,8 @@ def test_tree2_rules_match_oracle(ctx, treeset, f_d, warm):
     same = idx == oi
     dg = ((Z[idx] - zq) ** 2).sum(1)
     close = np.abs(dg - od) <= 1e-4 * od
-    print(f"tree2 f_d={f_d} warm={warm}: agree {same.mean():.4f}")
-    assert same.mean() >= 0.97 and np.all(same | close | (dg <= od * (1 + 1e-6)) | ((~same).cumsum() < 12))
+    print(f"tree2 f_d={f_d} warm={warm}: agree {same.mean():.4f}, {int((~same).sum())} near-ties")
+    assert same.mean() >= 0.97 and np.all(same | close)
     assert np.allclose(metric.local_d2(y, data[idx].astype(np.float64), C), d2, rtol=1e-10)
 
 
@@ -187,8 +190,9 @@ def test_tree2_handoff_matches_oracle(ctx, treeset, gpu_budget, budget, f_d, war
     same = idx == oi
     dg = ((Z[idx] - zq) ** 2).sum(1)
     close = np.abs(dg - od) <= 1e-4 * od
-    print(f"tree2 hand-off budget={budget} f_d={f_d} warm={warm}: agree {same.mean():.4f}")
-    assert same.mean() >= 0.97 and np.all(same | close | (dg <= od * (1 + 1e-6)) | ((~same).cumsum() < 12))
+    print(f"tree2 hand-off budget={budget} f_d={f_d} warm={warm}: agree {same.mean():.4f}, "
+          f"{int((~same).sum())} near-ties")
+    assert same.mean() >= 0.97 and np.all(same | close)
 
 
 def test_tree2_cells_export(ctx, treeset, annset):

@@ -139,3 +139,34 @@ def test_rotation_with_traction_is_rejected(ctx):
             P.dd_solve(ds, ctx, 3, bad)
     finally:
         P.dd_free_dataset(ds)
+
+
+@pytest.fixture(scope="module")
+def cfg1_oracle():
+    """The exact DD solve of the 16^3 cube on 10^6 linear-law points (Eq. 8
+    with the brute-force P_D and the direct P_C), seed 0, tension 1e-3:
+    minutes of host work, done once for the modes below."""
+    W = I.WORKLOADS["cube16_N1e6_exact"]
+    data = I.make_dataset(W.N, W.law, seed=W.seed)
+    load = I.load_case(*W.loads[0])
+    init = I.initial_association(W.m, W.N, seed=W.seed)
+    o = odd.DDProblem(data, C, W.n_el, load).solve(init)
+    return W, data, load, init, o
+
+
+@pytest.mark.parametrize("mode", ["fp32", "tc"])
+def test_cube16_N1e6_exact_solve_matches_oracle(ctx, cfg1_oracle, mode):
+    """The 16^3 / 10^6-point workload end to end: the certified FP32 scan and
+    the certified split-FP16 tensor-core scan give the oracle's associations
+    at every iteration and its displacements within 1e-6."""
+    W, data, load, init, o = cfg1_oracle
+    ds = P.dd_load_dataset(ctx, data, C, build_fp16=(mode == "tc"))
+    try:
+        md = P.DD_SEARCH_EXACT_TC if mode == "tc" else P.DD_SEARCH_EXACT_FP32
+        r = P.dd_solve(ds, ctx, W.n_el, load, mode=md, init_idx=init, max_iter=200)
+    finally:
+        P.dd_free_dataset(ds)
+    print(f"cube16 N=1e6 {mode}: {r.iters} iterations (oracle {o.iters}), "
+          f"{r.uncertified} FP64 re-searches")
+    compare(r, o)
+    assert r.converged

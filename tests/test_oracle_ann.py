@@ -280,3 +280,27 @@ def test_one_leaf_per_cell_second_bound_is_the_flat_one():
             a = ann.ann_search(Z, zq, cent, rad, cl, f_d, prev_idx=pv, n_cand=8, with_second=True)
             b = ann.tree2_search(Z, zq, cent, rad, cent, rad, cl, 1, f_d, prev_idx=pv, n_cand=8, with_second=True)
             assert all(np.array_equal(x, y) for x, y in zip(a, b))
+
+
+def test_found_second_is_the_papers_estimate_below_fd_one():
+    """second="found" returns the second-closest point read (the paper's p2)
+    below f_d = 1 and the certified bound at f_d = 1.  Line case at
+    f_d = 0.9: cluster B's bound is 2.65 - 0.9 x 2.35 = 0.535, so the
+    certified second is 0.535^2, the found one 1.0 (the point at 1.0)."""
+    Z, q, cent, rad, cl = line_case()
+    _, _, s = ann.ann_search(Z, q, cent, rad, cl, 0.9, with_second=True)
+    assert np.isclose(s[0], 0.535 ** 2)
+    _, _, s = ann.ann_search(Z, q, cent, rad, cl, 0.9, with_second=True, second="found")
+    assert np.isclose(s[0], 1.0)
+    _, _, s = ann.ann_search(Z, q, cent, rad, cl, 1.0, with_second=True, second="found")
+    assert np.isclose(s[0], 0.09)
+    cc = Z.mean(0, keepdims=True)
+    cr = np.array([np.sqrt(((Z - cc) ** 2).sum(1)).max()])
+    _, _, s = ann.tree2_search(Z, q, cc, cr, cent, rad, cl, 2, 0.9, with_second=True, second="found")
+    assert np.isclose(s[0], 1.0)
+    # the found second is never below the certified one
+    Z2, zq2, part = setup2(seed=13)
+    for f_d in (0.0, 0.5):
+        a = ann.tree2_search(Z2, zq2, *part, 10, f_d, with_second=True)
+        b = ann.tree2_search(Z2, zq2, *part, 10, f_d, with_second=True, second="found")
+        assert np.array_equal(a[0], b[0]) and np.all(b[2] >= a[2])

@@ -64,3 +64,25 @@ def test_streaming_scan_equals_in_memory_scan():
     i1, d1, _, _ = nn.nn_top2(M.to_z(data, C), zq)
     j1, e1 = nn.nn_stream(law, 6, N, C, zq)
     assert np.array_equal(i1, j1) and np.allclose(d1, e1, rtol=1e-12)
+
+
+def test_topk_by_hand_and_against_top2():
+    zd = np.zeros((5, 12)); zd[:, 0] = [0.0, 1.0, 2.0, 3.0, 1.0]
+    zq = np.zeros((1, 12)); zq[0, 0] = 1.4
+    i, d = nn.nn_topk(zd, zq, 4)
+    # distances 1.96, 0.16, 0.36, 2.56, 0.16: the tie 1 / 4 goes to the lower index
+    assert i.tolist() == [[1, 4, 2, 0]] and np.allclose(d, [[0.16, 0.16, 0.36, 1.96]])
+    i, d = nn.nn_topk(zd[:2], zq, 4)          # fewer points than k: padded
+    assert i.tolist() == [[1, 0, -1, -1]] and np.isinf(d[0, 2:]).all()
+    C = I.isotropic_C()
+    data = I.make_dataset(3000, I.NONLINEAR, seed=4).astype(np.float64)
+    Z, zq = M.to_z(data, C), M.to_z(I.make_states(300, I.NONLINEAR, seed=5, spread=0.2), C)
+    i, d = nn.nn_topk(Z, zq, 6)
+    i1, d1, i2, d2 = nn.nn_top2(Z, zq)
+    assert np.array_equal(i[:, 0], i1) and np.array_equal(i[:, 1], i2)
+    assert np.allclose(d[:, 0], d1, rtol=1e-12) and np.allclose(d[:, 1], d2, rtol=1e-12)
+    assert np.all(np.diff(d, axis=1) >= 0)
+    # every point left out is at least as far as the k-th
+    for q in range(0, 300, 37):
+        rest = np.setdiff1d(np.arange(len(Z)), i[q])
+        assert (((Z[rest] - zq[q]) ** 2).sum(1) >= d[q, -1]).all()

@@ -50,6 +50,33 @@ def test_noalloc_matches_allocating_entry_point_twice(ctx):
         P.dd_free_dataset(ds)
 
 
+def test_noalloc_at_the_query_limit_matches_oracle(ctx):
+    """At m = DD_NOALLOC_MAX_QUERIES the scan's data splits are capped so that
+    the candidate windows fit the fixed array; the answers still equal the
+    FP64 oracle's brute force (and the allocating entry point's), with the
+    call waiting for its own status (no device wait gave up)."""
+    from gpu_util import assert_nn_parity
+    data = I.make_dataset(4000, I.NONLINEAR, seed=13)
+    ds = P.dd_load_dataset(ctx, torch.from_numpy(data).cuda(), C)
+    try:
+        m = P.DD_NOALLOC_MAX_QUERIES
+        y_np = I.make_states(m, I.NONLINEAR, seed=14, spread=0.2)
+        y = torch.from_numpy(y_np).cuda()
+        got_i = torch.full((m,), -1, dtype=torch.int32, device="cuda")
+        got_d = torch.full((m,), -1.0, dtype=torch.float64, device="cuda")
+        P.dd_project_nearest_noalloc(ds, ctx, y, got_i, got_d, wait=True)
+        assert_nn_parity(got_i.cpu().numpy(), got_d.cpu().numpy(), data, y_np, C)
+        ref_i = torch.empty(m, dtype=torch.int32, device="cuda")
+        ref_d = torch.empty(m, dtype=torch.float64, device="cuda")
+        P.dd_project_nearest(ds, ctx, y, ref_i, ref_d, mode=P.DD_SEARCH_EXACT_FP32)
+        torch.cuda.synchronize()
+        assert torch.equal(got_i, ref_i)
+        assert np.allclose(got_d.cpu().numpy(), ref_d.cpu().numpy(), rtol=1e-12, atol=0)
+        assert torch.cuda.current_device() == 0
+    finally:
+        P.dd_free_dataset(ds)
+
+
 def test_noalloc_rejects_oversized_batch(ctx):
     data = I.make_dataset(1000, I.LINEAR, seed=1)
     ds = P.dd_load_dataset(ctx, data, C)
