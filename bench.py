@@ -38,26 +38,47 @@ UNIT = "searches/s"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 L2_BYTES = 129 * 2 ** 20
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant
-# kernels of one search, from ncu captures of a smaller case of the same mode,
-# keyed by the sha256 of the kernels' source file (a changed source reports
-# null until it is captured again).  A bench run scales the captured bytes by
-# the ratio of its own data points read per search to the capture's.
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the search's
+# kernels, from one-kernel ncu captures of a smaller case of the same mode
+# (profiles/dram_search_cube32_N3e7.md), keyed by the sha256 of the kernels'
+# source file (a changed source reports null until it is captured again).
+# The captured bytes split into the distinct data points the search read
+# (48 B each) and a per-query part; a bench run scales the per-query part by
+# its own query count and adds its own distinct points' bytes (a floor of the
+# data part).
 TRAFFIC = {
     # mode: (source file under the package's csrc/, sha256, DRAM bytes per
-    #        search, data points read per search, the captured case)
+    #        search, distinct data bytes per search, queries per search)
+    "ann": ("ann.cu", "c52d8efc985664fe0c1035ef5064c5de585d9e94956be673600df90ed8960a97",
+            192.7e6, 255238 * 48.0, 262144),
 }
 
 
-def captured_traffic(mode: str, points_now: float):
+# Captures of exactly the benched launch: (workload, mode): (source, sha256,
+# DRAM bytes per launch); profiles/k_scan_tc_cube16_N1e6.md.
+TRAFFIC_EXACT = {
+    ("cube16_N1e6_exact", "tc"): ("search_tc.cu", "b035cef58e7ebf9ffbc7210468cb7a40e2d65bc81f53ac18bfc462b487480928", 78.2e6),
+}
+
+
+def exact_traffic(workload: str, mode: str):
+    t = TRAFFIC_EXACT.get((workload, mode))
+    if t is None:
+        return None
+    path, sha, byts = t
+    with open(os.path.join(ROOT, "paper_2012_00357_gb300", "csrc", path), "rb") as f:
+        return byts if hashlib.sha256(f.read()).hexdigest() == sha else None
+
+
+def captured_traffic(mode: str, queries_now: float, distinct_bytes_now: float):
     t = TRAFFIC.get(mode)
     if t is None:
         return None
-    path, sha, byts, pts, _ = t
+    path, sha, byts, distinct, queries = t
     with open(os.path.join(ROOT, "paper_2012_00357_gb300", "csrc", path), "rb") as f:
         if hashlib.sha256(f.read()).hexdigest() != sha:
             return None
-    return byts * points_now / pts
+    return (byts - distinct) / queries * queries_now + distinct_bytes_now
 
 
 def load_peaks():
@@ -173,6 +194,36 @@ def oracle_searches_per_s(W: I.Workload, C, target_s: float = 12.0, max_queries:
             f"(extrapolated, brute force is linear in N)")
     return {"value": n / dt * scale, "unit": UNIT, "cores": nn.threads(), "kind": "oracle",
             "sample": f"{what}, brute-force FP64 scan (oracle/nn.c); data generation {gen_s:.1f}s not timed"}
+
+
+def oracle_dd_iterations(W: I.Workload, C, target_s: float = 12.0):
+    """The oracle's DD solve itself (Eq. 8: direct P_C, brute-force P_D over
+    all N points) from the workload's initial association, iterated until it
+    converges or target_s has passed: searches/s over whole DD iterations
+    (for data sets the oracle scans in seconds)."""
+    from oracle import dd as odd
+    from oracle import nn
+    data = I.make_dataset(W.N, W.law, seed=W.seed)
+    load = I.load_case(*W.loads[0])
+    t0 = time.perf_counter()
+    prob = odd.DDProblem(data, C, W.n_el, load)
+    setup_s = time.perf_counter() - t0
+    idx = I.initial_association(W.m, W.N, seed=W.seed)
+    t = time.perf_counter()
+    it, converged = 0, False
+    while True:
+        u, eta, eps, sig = prob.project_C(idx)
+        new, _, _ = prob.project_D(eps, sig)
+        it += 1
+        converged = bool(np.array_equal(new, idx))
+        idx = new
+        if converged or time.perf_counter() - t > target_s:
+            break
+    dt = time.perf_counter() - t
+    return {"value": W.m * it / dt, "unit": UNIT, "cores": nn.threads(), "kind": "oracle",
+            "sample": f"{it} full DD iterations of the oracle (direct P_C, brute-force FP64 P_D of all {W.m} "
+                      f"material points over all {W.N} data points) from the random association"
+                      f"{', converged' if converged else ''}; factorisation {setup_s:.1f}s not timed"}
 
 
 # ----------------------------------------------------------------------------
@@ -356,17 +407,34 @@ def run_ours(args, world, rank, local):
         ra1 = P.dd_solve(ds, ctx, W.n_el, loads[0], mode=mode, certify=certify, init_idx=init_pin, max_iter=200,
                          **ann_kw)
         ta1 = time.perf_counter() - t
+        # stepwise, so that every iteration is logged (stderr) and a wall-clock
+        # budget can end it: the exact iteration runs until its association
+        # stops changing, which can take many iterations at 10^9 points
+        sv = P.dd_solver_create(ds, ctx, W.n_el, loads[0], mode=P.DD_SEARCH_EXACT_TC, certify=True,
+                                init_idx=init, max_iter=200)
         t = time.perf_counter()
-        rx = P.dd_solve(ds, ctx, W.n_el, loads[0], mode=P.DD_SEARCH_EXACT_TC, certify=True, init_idx=init_pin,
-                        max_iter=200)
+        hist = []
+        while not P.dd_solver_done(sv):
+            info = P.dd_solver_step(sv, ctx)
+            hist.append({"iter": info.iter, "d2_pd": info.d2_pd, "changed": int(info.changed),
+                         "uncertified": int(info.uncertified), "search_ms": info.search_ms, "cg_ms": info.cg_ms,
+                         "t_s": time.perf_counter() - t})
+            print(json.dumps({"exact_solve_iteration": hist[-1]}), file=sys.stderr, flush=True)
+            if hist[-1]["t_s"] > args.exact_budget_s:
+                break
         tx = time.perf_counter() - t
+        done = bool(P.dd_solver_done(sv))
+        P.dd_solver_free(sv)
+        dx = hist[-1]["d2_pd"]
         exact_solve = {"load": W.loads[0][0], "exact": "tensor-core split-FP16 scan + FP64 rescoring, certified",
-                       "exact_solve_s": tx, "exact_iters": rx.iters, "exact_converged": rx.converged,
-                       "exact_d2": float(rx.d2_pd[-1]), "exact_uncertified": int(rx.uncertified),
-                       "exact_searches_per_s": W.m * rx.iters / (rx.search_ms / 1e3),
+                       "exact_solve_s": tx, "exact_iters": len(hist), "exact_converged": done,
+                       "exact_budget_s": args.exact_budget_s, "exact_d2": dx,
+                       "exact_changed_last": hist[-1]["changed"],
+                       "exact_uncertified": sum(h["uncertified"] for h in hist),
+                       "exact_searches_per_s": W.m * len(hist) / (sum(h["search_ms"] for h in hist) / 1e3),
+                       "exact_history": hist,
                        "ann_solve_s": ta1, "ann_iters": ra1.iters, "ann_d2": float(ra1.d2_pd[-1]),
-                       "ann_rel_d2_vs_exact": float((ra1.d2_pd[-1] - rx.d2_pd[-1]) / rx.d2_pd[-1]),
-                       "speedup": tx / ta1}
+                       "ann_rel_d2_vs_exact": float((ra1.d2_pd[-1] - dx) / dx), "speedup": tx / ta1}
 
     # end-to-end through the public API with host buffers (pinned): one
     # projection of the step's m states per call, copies inside the timed region
@@ -408,7 +476,7 @@ def run_ours(args, world, rank, local):
         lane_ops = 24 * (points + leafc) + 12 * cells
         achieved = lane_ops / (scan_avg / 1e3)
         byts = points * 48 + nq * 48
-        traffic = captured_traffic(args.mode, points)
+        traffic = captured_traffic(args.mode, nq, statistics.mean(i.unique_points for i in infos) * 48)
         roof = {"kernel": ("k_ann_gate + k_rank_small + k_ann_probe2 + k_leaf_scan (one search per step)"
                            if levels == 2 else "k_ann_probe + centroid ranking (one search per step)"),
                 "bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12, "unit": "T FP32 lane-ops/s",
@@ -432,7 +500,7 @@ def run_ours(args, world, rank, local):
         byts = evals * 52 + W.m * nload * 48
         achieved = byts / (scan_avg / 1e3) / 1e9
         roof = {"kernel": "k_knng_walk", "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": captured_traffic(args.mode, evals),
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
                 "peak_source": f"{peaks['source']} copy bandwidth",
                 "algorithmic": "52 B x neighbours evaluated + 48 B x queries, per launch", "algorithmic_bytes": byts}
     elif mode == P.DD_SEARCH_EXACT_TC:
@@ -444,7 +512,7 @@ def run_ours(args, world, rank, local):
         achieved = flops / (scan_avg / 1e3) / 1e12
         roof = {"kernel": f"k_scan_tc<{kc}>", "bound": "tensor", "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": captured_traffic(args.mode, W.N), "peak_source":
+                "traffic": exact_traffic(W.name, args.mode), "peak_source":
                     f"{peaks['source']} bf16 dense {'sustained' if long_scan else 'burst'} (fp16 runs at the same rate)",
                 "algorithmic": "2*m*N*16 flops per launch (one K = 16 product per distance)",
                 "issued_tflops": achieved * kc, "issued": f"{kc} FP16 products per distance (split-FP16 operands)"
@@ -455,7 +523,7 @@ def run_ours(args, world, rank, local):
         achieved = flops / (scan_avg / 1e3) / 1e12
         peak_tflops = 2 * alu_peak / 1e12
         roof = {"kernel": "k_scan_fp32", "bound": "alu", "achieved": achieved, "peak": peak_tflops,
-                "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": captured_traffic(args.mode, W.N),
+                "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
                 "peak_source": alu_src + ", 2 flop per FFMA",
                 "algorithmic": "2*12*m*N flops per launch (12 FFMA per pair)"}
 
@@ -522,7 +590,10 @@ def run_ours(args, world, rank, local):
         line["detail"]["serve"] = serve_leg(P, ctx, I.WORKLOADS["serve_N1e7"], args, args.serve_requests)
     P.dd_destroy(ctx)
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_searches_per_s(W, C, target_s=args.cpu_seconds)
+        # whole oracle DD iterations where it scans the data set in seconds,
+        # else its brute-force P_D on a bounded query sample
+        line["cpu_baseline"] = (oracle_dd_iterations(W, C, target_s=args.cpu_seconds) if W.N <= 2_000_000
+                                else oracle_searches_per_s(W, C, target_s=args.cpu_seconds))
     return line
 
 
@@ -640,7 +711,9 @@ def run_reference(args, world, rank):
     vals = []
     info = None
     for i in range(args.warmup + args.steps):
-        info = oracle_searches_per_s(W, C, target_s=per_step) if info is None or i == args.warmup else info
+        if info is None or i == args.warmup:
+            info = (oracle_dd_iterations(W, C, target_s=per_step) if W.N <= 2_000_000 and C is not None
+                    else oracle_searches_per_s(W, C, target_s=per_step))
         if i >= args.warmup:
             vals.append(info["value"])
     v = statistics.mean(vals)
@@ -697,6 +770,9 @@ def main():
     ap.add_argument("--exact-solve", action="store_true",
                     help="also solve the first load case with the certified tensor-core exact search and with the "
                          "approximate search alone (solve time and distance at N, ANN vs exact; minutes at 10^9)")
+    ap.add_argument("--exact-budget-s", type=float, default=900.0,
+                    help="wall-clock budget of the exact solve of --exact-solve (it stops after the iteration that "
+                         "passes it and reports whether it had converged)")
     ap.add_argument("--serve-requests", type=int, default=64,
                     help="requests of the short serving run reported in detail.serve (0: none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

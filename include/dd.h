@@ -274,6 +274,11 @@ typedef struct dd_search_opts {
                                  certified bound above, 1 the second-closest
                                  point found below f_d = 1 (the paper's
                                  estimate; see dd_solve_opts.eq14) */
+    int tc_terms;             /* DD_SEARCH_EXACT_TC, certify = 1, topk < 2:
+                                 FP16 products per distance, 3 (split query
+                                 and data) or 2 (split data, single FP16
+                                 query, wider window); both certified exact.
+                                 0 = the autotuner's choice */
 } dd_search_opts;
 
 /* Largest k of dd_search_opts.topk.  k < DD_TOPK_MAX is certified from the

@@ -51,7 +51,7 @@ class dd_search_opts(ctypes.Structure):
     _fields_ = [("mode", c_int), ("certify", c_int), ("f_d", c_double), ("prev_idx", c_void_p),
                 ("stream", c_void_p), ("f_s", c_int), ("ann_budget", c_int), ("topk", c_int),
                 ("topk_d2", c_void_p), ("d2nd", c_void_p), ("prev_y", c_void_p), ("prev_d2", c_void_p),
-                ("prev_d2nd", c_void_p), ("eq14", c_int)]
+                ("prev_d2nd", c_void_p), ("eq14", c_int), ("tc_terms", c_int)]
 
 
 class dd_search_stats(ctypes.Structure):
@@ -254,13 +254,13 @@ def dd_synth_dataset(ctx, out_dev, law, C, seed: int = 0, start: int = 0, stream
 def dd_project_nearest(ds, ctx, y, idx, d2=None, mode: int = DD_SEARCH_EXACT_FP32, certify: bool = True,
                        f_d: float = 0.0, prev_idx=None, stream=None, want_stats: bool = True, f_s: int = 0,
                        ann_budget: int = 0, topk_out=None, topk_d2=None, d2nd=None, prev_y=None, prev_d2=None,
-                       prev_d2nd=None, eq14: int = 0):
+                       prev_d2nd=None, eq14: int = 0, tc_terms: int = 0):
     """topk_out: [m x k] int32 array (its second dimension gives k); the
     other optional arrays as in dd_search_opts."""
     m = int(y.shape[0])
     k = int(topk_out.shape[1]) if topk_out is not None else 0
     opts = dd_search_opts(int(mode), int(certify), float(f_d), _ptr(prev_idx), stream, int(f_s), int(ann_budget),
-                          k, _ptr(topk_d2), _ptr(d2nd), _ptr(prev_y), _ptr(prev_d2), _ptr(prev_d2nd), int(eq14))
+                          k, _ptr(topk_d2), _ptr(d2nd), _ptr(prev_y), _ptr(prev_d2), _ptr(prev_d2nd), int(eq14), int(tc_terms))
     st = dd_search_stats()
     _check(ctx, lib().dd_project_nearest(ds, _ptr(y), m, ctypes.byref(opts), _ptr(idx), _ptr(d2), _ptr(topk_out),
                                          ctypes.byref(st) if want_stats else None))

@@ -269,6 +269,8 @@ extern "C" dd_status dd_project_nearest(dd_dataset *ds, const double *y, int64_t
     if (o.topk_d2 && !topk_out) return dd_fail(ctx, DD_ERR_ARG, "dd_project_nearest: topk_d2 without topk_out");
     if (k > 0 && approx) return dd_fail(ctx, DD_ERR_ARG, "dd_project_nearest: topk needs an exact search mode");
     if (o.eq14 < 0 || o.eq14 > 1) return dd_fail(ctx, DD_ERR_ARG, "dd_project_nearest: unknown eq14 rule");
+    if (o.tc_terms != 0 && o.tc_terms != 2 && o.tc_terms != 3)
+        return dd_fail(ctx, DD_ERR_ARG, "dd_project_nearest: tc_terms must be 0, 2 or 3");
     const bool motion = o.prev_y != nullptr;
     if (motion && !approx)
         return dd_fail(ctx, DD_ERR_ARG, "dd_project_nearest: the motion record (prev_y) needs an approximate mode");
@@ -354,6 +356,9 @@ extern "C" dd_status dd_project_nearest(dd_dataset *ds, const double *y, int64_t
     } else if (o.mode == DD_SEARCH_ANN) {
         if (!ds->ann.nlist) return dd_fail(ctx, DD_ERR_STATE, "ANN search needs the partition (ann_nlist)");
         st = dd_search_ann_motion(ds, y_dev, m, o.f_d, nullptr, prev_dev, nullptr, o.ann_budget, out, pst, s, o.eq14);
+    } else if (o.mode == DD_SEARCH_EXACT_TC) {
+        if (!ds->z16hi) return dd_fail(ctx, DD_ERR_STATE, "tensor-core search needs the FP16 copy (build_fp16)");
+        st = dd_search_exact_tc(ds, y_dev, m, o.certify, out, pst, s, o.tc_terms);
     } else {
         st = dd_run_search(ds, o.mode, o.certify, o.f_d, o.f_s, o.ann_budget, prev_dev, y_dev, m, out, pst, s);
     }

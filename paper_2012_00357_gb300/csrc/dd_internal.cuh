@@ -6,6 +6,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -94,7 +95,8 @@ struct dd_ctx {
     // grow-only scratch buffers keyed by purpose
     Workspace ws[12];
     int64_t launches = 0;               // kernels launched (instrumentation)
-    int tc_epi[2] = {0, 0};             // tuned epilogue warps of the tensor-core scan (top-k, certified)
+    int tc_epi[3] = {0, 0, 0};          // tuned tensor-core scan variants (uncertified, certified nearest, certified k nearest)
+    std::map<int64_t, int> fp32_splits; // tuned data splits of the FP32 scan, per query-tile count
     cudaEvent_t ev_scan[2] = {nullptr, nullptr};   // brackets the dominant scan kernel
     uint64_t ws_gen = 0;                // bumped whenever a workspace is reallocated
     bool capturing = false;             // a step is being captured: no host syncs, no allocation
@@ -238,8 +240,10 @@ dd_status dd_map_queries(dd_dataset *ds, const double *y_dev, int64_t m, double 
                          QueryRec *rec, cudaStream_t s);
 dd_status dd_search_exact_fp32(dd_dataset *ds, const double *y_dev, int64_t m, int certify,
                                SearchOut out, dd_search_stats *st, cudaStream_t s);
+// terms: FP16 products per distance of the certified nearest-point scan (2 or
+// 3; 0 = the autotuner's choice)
 dd_status dd_search_exact_tc(dd_dataset *ds, const double *y_dev, int64_t m, int certify,
-                             SearchOut out, dd_search_stats *st, cudaStream_t s);
+                             SearchOut out, dd_search_stats *st, cudaStream_t s, int terms = 0);
 dd_status dd_build_fp16(dd_dataset *ds);
 dd_status dd_search_ann(dd_dataset *ds, const double *y_dev, int64_t m, double f_d,
                         const int32_t *prev_idx_dev, int budget, SearchOut out, dd_search_stats *st,
@@ -407,12 +411,22 @@ __device__ __forceinline__ void cand_init(CandState &c, bool active) {
     c.cnt = 0;
 }
 
+// Window above the running minimum m: w2, plus, for a score taken against
+// a query rounded to q_hi (the two-product tensor-core scan), the q_lo term
+// qlo4 * D with qlo4 = 4 |q_lo| and D = sqrt(m + |q_hi|^2) + qlo4 / 2 bounding
+// the distance to q_hi of every point that can lie in the window.
+__device__ __forceinline__ float cand_window(float m, float w2, float qlo4, float qhn) {
+    if (!(qlo4 > 0.f)) return w2;
+    const float D = sqrtf(fmaxf(m + qhn + w2, 0.f)) + 0.5f * qlo4;
+    return w2 + qlo4 * D * 1.001f;
+}
+
 // buf: this query's entry 0; consecutive entries are `st` float2 apart.
 __device__ __forceinline__ void cand_insert(CandState &c, float s, int j, float w2, float2 *buf, int st, int cap,
-                                            bool topk) {
+                                            bool topk, float qlo4 = 0.f, float qhn = 0.f) {
     if (s < c.mrun) {
         c.mrun = s;
-        c.wl = s + w2;
+        c.wl = s + cand_window(s, w2, qlo4, qhn);
     }
     if (!(s <= c.wl)) return;
     if (c.cnt == cap) {

@@ -213,7 +213,8 @@ __global__ void k_merge_rescore(const float *__restrict__ raw, MetricMaps M,
     float gmin = INFINITY;
     for (int s = 0; s < splits; ++s) gmin = fminf(gmin, h[s].mrun);
     const float w2 = rec[i].w2;
-    const float lim = gmin + w2;
+    // the window (two-product tensor-core scan: with its q_lo term)
+    const float lim = gmin + cand_window(gmin, w2, rec[i].pad[0], rec[i].pad[1]);
     bool uncert = !(w2 < INFINITY);
     for (int s = 0; s < splits; ++s) uncert |= (h[s].dropped <= lim);
     double yy[12];
@@ -239,8 +240,16 @@ __global__ void k_merge_rescore(const float *__restrict__ raw, MetricMaps M,
     }
     if (bj < 0) uncert = true;
     // every point outside the window has |z - q|^2 >= gmin + qn + w2/2 (in
-    // score units; inv_s2 converts to the mapped coordinates)
-    double lb = 2.0 * inv_s2 * ((double)gmin + (double)rec[i].qn + 0.5 * (double)w2);
+    // score units; inv_s2 converts to the mapped coordinates); with the q_lo
+    // term (two-product scan) a score s outside it bounds the distance by
+    // s + |q_hi|^2 - (qlo4/2) sqrt(s + |q_hi|^2) - w2/2, increasing in s
+    double lb;
+    if (rec[i].pad[0] > 0.f) {
+        const double a = fmax((double)lim + (double)rec[i].pad[1], 0.0);
+        lb = 2.0 * inv_s2 * fmax(a - 0.5 * (double)rec[i].pad[0] * sqrt(a) - 0.5 * (double)w2, 0.0);
+    } else {
+        lb = 2.0 * inv_s2 * ((double)gmin + (double)rec[i].qn + 0.5 * (double)w2);
+    }
     if (uncert && certify) {
         unsigned long long k = atomicAdd(fb_count, 1ull);
         fb_list[k] = i;
@@ -615,12 +624,24 @@ dd_status dd_search_exact_fp32(dd_dataset *ds, const double *y_dev, int64_t m, i
     if (m == 0) return DD_OK;
     const int64_t n_tiles = (ds->N + kT - 1) / kT;
     const int64_t qtiles = (m + kQT - 1) / kQT;
-    const int splits = pick_splits(qtiles, n_tiles, ctx->n_sm, 2);
-    const int64_t tps = (n_tiles + splits - 1) / splits;
+    // Split count (data ranges per query tile, merged afterwards): the
+    // heuristic fills whole waves of CTAs; the autotuner times it, half and
+    // twice it on the first large call of every query-tile count and keeps
+    // the fastest for this context (all give the same answers).
+    const int s0 = pick_splits(qtiles, n_tiles, ctx->n_sm, 2);
+    int cands[3] = {s0, (int)std::max<int64_t>(1, s0 / 2), (int)std::min<int64_t>(n_tiles, (int64_t)s0 * 2)};
+    int splits = s0;
+    bool tune = false;
+    {
+        auto it = ctx->fp32_splits.find(qtiles);
+        if (it != ctx->fp32_splits.end()) splits = it->second;
+        else tune = !ctx->capturing && (double)m * (double)ds->N >= 1e9;
+    }
+    const int s_max = tune ? std::max(cands[0], std::max(cands[1], cands[2])) : splits;
 
     size_t rec_bytes = ((size_t)m * sizeof(QueryRec) + 255) / 256 * 256;
-    size_t hdr_bytes = ((size_t)m * splits * sizeof(CandHeader) + 255) / 256 * 256;
-    size_t cand_bytes = (size_t)m * splits * kCap * sizeof(float2);
+    size_t hdr_bytes = ((size_t)m * s_max * sizeof(CandHeader) + 255) / 256 * 256;
+    size_t cand_bytes = (size_t)m * s_max * kCap * sizeof(float2);
     void *w = nullptr;
     DD_TRY(dd_workspace(ctx, WS_SEARCH, rec_bytes + hdr_bytes + cand_bytes, &w));
     QueryRec *rec = reinterpret_cast<QueryRec *>(w);
@@ -629,12 +650,35 @@ dd_status dd_search_exact_fp32(dd_dataset *ds, const double *y_dev, int64_t m, i
 
     DD_TRY(dd_map_queries(ds, y_dev, m, nullptr, rec, s));
     DD_TRY_CUDA(ctx, cudaFuncSetAttribute(k_scan_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScanSmem));
-    dim3 grid((unsigned)qtiles, (unsigned)splits);
-    ctx->launches++;
-    if (st) DD_TRY_CUDA(ctx, dd_event_record(ctx, ctx->ev_scan[0], s));
     // top-k mode (the best kCap scores of every split, no window) for the k
     // nearest points or an uncertified search; else the certified window
     const bool topk = certify == 0 || out.k >= 2;
+    if (tune) {
+        float best = 1e30f;
+        for (int c = 0; c < 3; ++c) {
+            if (c > 0 && (cands[c] == cands[0] || (c == 2 && cands[2] == cands[1]))) continue;
+            const int sp = cands[c];
+            const int64_t tp = (n_tiles + sp - 1) / sp;
+            DD_TRY_CUDA(ctx, dd_event_record(ctx, ctx->ev_scan[0], s));
+            ctx->launches++;
+            k_scan_fp32<<<dim3((unsigned)qtiles, (unsigned)sp), kThreads, kScanSmem, s>>>(
+                ds->z32, ds->zn, ds->N, n_tiles, rec, m, sp, tp, hdr, cand, topk, ctx->dev_err);
+            DD_TRY_CUDA(ctx, cudaGetLastError());
+            DD_TRY_CUDA(ctx, dd_event_record(ctx, ctx->ev_scan[1], s));
+            DD_TRY_CUDA(ctx, cudaEventSynchronize(ctx->ev_scan[1]));
+            float ms = 0.f;
+            DD_TRY_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev_scan[0], ctx->ev_scan[1]));
+            if (ms < best) {
+                best = ms;
+                splits = sp;
+            }
+        }
+        ctx->fp32_splits[qtiles] = splits;
+    }
+    const int64_t tps = (n_tiles + splits - 1) / splits;
+    dim3 grid((unsigned)qtiles, (unsigned)splits);
+    ctx->launches++;
+    if (st) DD_TRY_CUDA(ctx, dd_event_record(ctx, ctx->ev_scan[0], s));
     k_scan_fp32<<<grid, kThreads, kScanSmem, s>>>(ds->z32, ds->zn, ds->N, n_tiles, rec, m, splits, tps,
                                                   hdr, cand, topk, ctx->dev_err);
     DD_TRY_CUDA(ctx, cudaGetLastError());

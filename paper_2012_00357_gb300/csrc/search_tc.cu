@@ -15,6 +15,13 @@
 //  * KC = 3: split FP16 (x = hi + lo for data and query): three MMAs
 //    (q_hi.x_hi + q_lo.x_hi + q_hi.x_lo) give ~22-bit operands, the window
 //    is narrow and the result is certified exact like the FP32 scan.
+//  * KC = 2: split data, single FP16 query: two MMAs (q_hi.x_hi + q_hi.x_lo)
+//    score |x - q_hi|^2 - |q_hi|^2 to ~22 bits.  Against the true query the
+//    score is off by a per-query constant plus 2 (x - q_hi).q_lo, at most
+//    4 |q_lo| D for the points of the window, D bounding their distance to
+//    q_hi (from the running minimum): the window widens by that term, which
+//    is small where it matters (near points, |q_lo| <= 2^-11 |q|), and the
+//    result is certified exact as for KC = 3 with two thirds of the MMAs.
 //
 // Pipeline per CTA (one 128-query tile x one range of 128-point data tiles):
 //   warp 0        TMA producer: 1-D bulk copies of the pre-laid-out FP16
@@ -216,7 +223,8 @@ __global__ void k_build_fp16(const float *__restrict__ z32, int64_t N, int64_t N
 
 // ---- query operands ----------------------------------------------------------
 // A chunks per 128-query tile (each 4 KB): A0 = (q_hi, 1, 1), A1 = (q_lo, 0, 0),
-// A2 = (q_hi, 1, 1).  KC = 1 uses A0 only.  rec: window and |q~|^2 (scaled).
+// A2 = (q_hi, 1, 1).  KC = 1 and KC = 2 use A0 only.  rec: window and |q~|^2
+// (scaled); KC = 2 also 4 |q_lo| (rounded up) and |q_hi|^2 in rec.pad.
 __global__ void k_prep_tc(const double *__restrict__ y, int64_t m, int64_t m_pad, MetricMaps M, double s, double Rs,
                           int kc, __half *__restrict__ qa, QueryRec *__restrict__ rec) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -241,7 +249,7 @@ __global__ void k_prep_tc(const double *__restrict__ y, int64_t m, int64_t m_pad
             z[6 + a] = (g * r2 - M.mu[6 + a]) * s;
         }
         bool in_range = true;
-        double qn = 0.0, qs = 0.0;
+        double qn = 0.0, qs = 0.0, qlo2 = 0.0;
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
             in_range &= fabs(z[k]) < 30000.0;
@@ -255,6 +263,8 @@ __global__ void k_prep_tc(const double *__restrict__ y, int64_t m, int64_t m_pad
                 lq[k] = __double2half(z[k] - h);
                 double t = (kc == 3) ? h + (double)__half2float(lq[k]) : h;
                 qn += t * t;
+                const double lo = z[k] - h;
+                qlo2 += lo * lo;
             }
             hq[12] = hq[13] = __float2half_rn(1.f);
         }
@@ -262,16 +272,20 @@ __global__ void k_prep_tc(const double *__restrict__ y, int64_t m, int64_t m_pad
 #pragma unroll
         for (int k = 0; k < 12; ++k) r.q[k] = 0.f;
         double B = Rs + sqrt(qs);
-        double E = (kc == 3) ? ldexp(B * B, -15) : 1.05 * ldexp(B * B, -10);
+        double E = (kc >= 2) ? ldexp(B * B, -15) : 1.05 * ldexp(B * B, -10);
         E += ldexp(1.0, -18);
         r.w2 = in_range ? (float)(2.0 * E) : INFINITY;
         r.qn = (float)qn;
         r.pad[0] = r.pad[1] = 0.f;
+        if (kc == 2) {   // the q_lo term of the window (see the header)
+            r.pad[0] = (float)(4.0 * sqrt(qlo2) * (1.0 + 1e-3));
+            r.pad[1] = (float)qn;
+        }
         rec[i] = r;
     }
     const int64_t tile = i / kTM;
     const int row = (int)(i % kTM);
-    char *base = reinterpret_cast<char *>(qa) + tile * (int64_t)kc * kTileBytes;
+    char *base = reinterpret_cast<char *>(qa) + tile * (int64_t)(kc == 3 ? 3 : 1) * kTileBytes;
 #pragma unroll
     for (int half8 = 0; half8 < 2; ++half8) {
         uint4 v0, v1;
@@ -298,9 +312,10 @@ __global__ void __launch_bounds__(tc_threads<EPI>(), 2)
               const __half *__restrict__ qa, const QueryRec *__restrict__ rec, int64_t m, int splits, int64_t tps,
               CandHeader *__restrict__ hdr, float2 *__restrict__ cand, bool topk, unsigned *__restrict__ err) {
     constexpr uint32_t kStageBytes = (KC == 1 ? 1 : 2) * kTileBytes;
+    constexpr int kATiles = KC == 3 ? 3 : 1;
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *sA = smem;                                   // KC * 4 KB
-    unsigned char *sB = smem + KC * kTileBytes;                 // kStages * stage
+    unsigned char *sA = smem;                                   // kATiles * 4 KB
+    unsigned char *sB = smem + kATiles * kTileBytes;            // kStages * stage
     float2 *sCand = reinterpret_cast<float2 *>(sB + kStages * kStageBytes);   // kCap x 256
     __shared__ __align__(8) uint64_t bar_full[kStages], bar_empty[kStages], bar_tfull[2], bar_tempty[2], bar_a,
         bar_done;
@@ -341,9 +356,9 @@ __global__ void __launch_bounds__(tc_threads<EPI>(), 2)
         if (lane == 0) {
             // ---------------- producer ----------------
             bool ok = true;
-            const char *ga = reinterpret_cast<const char *>(qa) + (int64_t)blockIdx.x * KC * kTileBytes;
-            dd_mbar_expect_tx(dd_smem_addr(&bar_a), KC * kTileBytes);
-            dd_bulk_g2s(dd_smem_addr(sA), ga, KC * kTileBytes, dd_smem_addr(&bar_a));
+            const char *ga = reinterpret_cast<const char *>(qa) + (int64_t)blockIdx.x * kATiles * kTileBytes;
+            dd_mbar_expect_tx(dd_smem_addr(&bar_a), kATiles * kTileBytes);
+            dd_bulk_g2s(dd_smem_addr(sA), ga, kATiles * kTileBytes, dd_smem_addr(&bar_a));
             int64_t issued = 0;
             for (int64_t t = 0; t < ntl; ++t) {
                 const int s = (int)(t % kStages);
@@ -356,7 +371,7 @@ __global__ void __launch_bounds__(tc_threads<EPI>(), 2)
                 dd_mbar_expect_tx(bf, kStageBytes);
                 dd_bulk_g2s(dd_smem_addr(sB + s * kStageBytes), reinterpret_cast<const char *>(zhi) + tile * kTileBytes,
                             kTileBytes, bf);
-                if (KC == 3)
+                if (KC != 1)
                     dd_bulk_g2s(dd_smem_addr(sB + s * kStageBytes + kTileBytes),
                                 reinterpret_cast<const char *>(zlo) + tile * kTileBytes, kTileBytes, bf);
                 issued = t + 1;
@@ -392,6 +407,8 @@ __global__ void __launch_bounds__(tc_threads<EPI>(), 2)
                 if (KC == 3) {
                     umma_f16(d, umma_desc(a0 + kTileBytes), umma_desc(bh), idesc, 1u);
                     umma_f16(d, umma_desc(a0 + 2 * kTileBytes), umma_desc(bh + kTileBytes), idesc, 1u);
+                } else if (KC == 2) {
+                    umma_f16(d, umma_desc(a0), umma_desc(bh + kTileBytes), idesc, 1u);
                 }
                 umma_commit(dd_smem_addr(&bar_empty[s]));
                 umma_commit(dd_smem_addr(&bar_tfull[ab]));
@@ -411,6 +428,7 @@ __global__ void __launch_bounds__(tc_threads<EPI>(), 2)
         const bool active = qi < m;
         // top-k mode keeps the best kCap scores with no window
         const float w2 = active ? (topk ? INFINITY : rec[qi].w2) : 0.f;
+        const float qlo4 = (KC == 2 && active) ? rec[qi].pad[0] : 0.f, qhn = (KC == 2 && active) ? rec[qi].pad[1] : 0.f;
         constexpr int kSt = kTM * EPI / 4;            // candidate buffer stride
         CandState cs;
         cand_init(cs, active);
@@ -447,7 +465,8 @@ __global__ void __launch_bounds__(tc_threads<EPI>(), 2)
                         float vk = v[0];
 #pragma unroll
                         for (int kk = 1; kk < 32; ++kk) vk = (k == kk) ? v[kk] : vk;
-                        if (vk <= cs.lim && j0 + k < N) cand_insert(cs, vk, (int)(j0 + k), w2, buf, kSt, kCap, topk);
+                        if (vk <= cs.lim && j0 + k < N)
+                            cand_insert(cs, vk, (int)(j0 + k), w2, buf, kSt, kCap, topk, qlo4, qhn);
                     }
                 }
             };
@@ -492,7 +511,8 @@ __global__ void __launch_bounds__(tc_threads<EPI>(), 2)
 
 template <int KC>
 size_t tc_smem_bytes() {
-    size_t s = KC * kTileBytes + kStages * (KC == 1 ? 1 : 2) * kTileBytes + kCap * 2 * kTM * 8 + 1024;   // EPI <= 8
+    size_t s = (KC == 3 ? 3 : 1) * kTileBytes + kStages * (KC == 1 ? 1 : 2) * kTileBytes + kCap * 2 * kTM * 8 +
+               1024;   // EPI <= 8
     return s < 100 * 1024 ? 100 * 1024 : s;   // at most two CTAs (2 x 256 TMEM columns) per SM
 }
 
@@ -549,8 +569,10 @@ static dd_status launch_tc(dd_ctx *ctx, dim3 grid, dd_dataset *ds, int64_t n_til
     return DD_OK;
 }
 
-// Epilogue layout codes of the autotuner: warps (4 or 8) | 256 x reducing load.
+// Variant codes of the autotuner: epilogue warps (4 or 8) | 256 x reducing
+// load | FP16 products per distance << kKcShift.
 constexpr int kEpiRed = 256;
+constexpr int kKcShift = 12;
 
 static dd_status launch_tc_any(dd_ctx *ctx, int kc, int code, dim3 grid, dd_dataset *ds, int64_t n_tiles,
                                const __half *qa, const QueryRec *rec, int64_t m, int splits, int64_t tps,
@@ -567,6 +589,14 @@ static dd_status launch_tc_any(dd_ctx *ctx, int kc, int code, dim3 grid, dd_data
         if (red) DD_TC_LAUNCH(3, 4, 1);
         DD_TC_LAUNCH(3, 4, 0);
     }
+    if (kc == 2) {
+        if (epi == 8) {
+            if (red) DD_TC_LAUNCH(2, 8, 1);
+            DD_TC_LAUNCH(2, 8, 0);
+        }
+        if (red) DD_TC_LAUNCH(2, 4, 1);
+        DD_TC_LAUNCH(2, 4, 0);
+    }
     if (epi == 8) {
         if (red) DD_TC_LAUNCH(1, 8, 1);
         DD_TC_LAUNCH(1, 8, 0);
@@ -577,21 +607,23 @@ static dd_status launch_tc_any(dd_ctx *ctx, int kc, int code, dim3 grid, dd_data
 }
 
 dd_status dd_search_exact_tc(dd_dataset *ds, const double *y_dev, int64_t m, int certify, SearchOut out,
-                             dd_search_stats *st, cudaStream_t s) {
+                             dd_search_stats *st, cudaStream_t s, int terms) {
     dd_ctx *ctx = ds->ctx;
     if (m == 0) return DD_OK;
-    const int kc = certify ? 3 : 1;
-    // the split-FP16 scan keeps a certified window, except for the k >= 2
-    // nearest points (best kCap scores, certified at the merge); the single
-    // FP16 scan always keeps the best kCap scores
-    const bool topk = kc == 1 || out.k >= 2;
+    // Variants: certified nearest point with two or three FP16 products per
+    // distance (tuned); certified k >= 2 nearest with three (its merge needs
+    // a uniform score error); uncertified top-k with one.  The split-FP16
+    // scans keep a certified window, except for the k >= 2 nearest points
+    // (best kCap scores, certified at the merge); the single FP16 scan keeps
+    // the best kCap scores.
+    const int slot = !certify ? 0 : out.k >= 2 ? 2 : 1;
     const int64_t n_tiles = (ds->N + kTN - 1) / kTN;
     const int64_t qtiles = (m + kTM - 1) / kTM;
     const int64_t m_pad = qtiles * kTM;
     const int splits = pick_splits_tc(qtiles, n_tiles, ctx->n_sm);
     const int64_t tps = (n_tiles + splits - 1) / splits;
     auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
-    size_t qa_bytes = r256((size_t)qtiles * kc * kTileBytes);
+    size_t qa_bytes = r256((size_t)qtiles * 3 * kTileBytes);
     size_t rec_bytes = r256((size_t)m * sizeof(QueryRec));
     size_t hdr_bytes = r256((size_t)m * splits * 2 * sizeof(CandHeader));
     size_t cand_bytes = (size_t)m * splits * 2 * kCap * sizeof(float2);
@@ -604,42 +636,61 @@ dd_status dd_search_exact_tc(dd_dataset *ds, const double *y_dev, int64_t m, int
     float2 *cand = (float2 *)(c + qa_bytes + rec_bytes + hdr_bytes);
 
     const double Rs = ds->R * ds->scale16 * (1.0 + 1e-6);
-    ctx->launches++;
-    k_prep_tc<<<(unsigned)((m_pad + 127) / 128), 128, 0, s>>>(y_dev, m, m_pad, ds->M, ds->scale16, Rs, kc, qa, rec);
-    DD_TRY_CUDA(ctx, cudaGetLastError());
+    int prepped = 0;
+    auto prep = [&](int kc) -> dd_status {
+        if (prepped == kc) return DD_OK;
+        ctx->launches++;
+        k_prep_tc<<<(unsigned)((m_pad + 127) / 128), 128, 0, s>>>(y_dev, m, m_pad, ds->M, ds->scale16, Rs, kc, qa,
+                                                                 rec);
+        DD_TRY_CUDA(ctx, cudaGetLastError());
+        prepped = kc;
+        return DD_OK;
+    };
     dim3 grid((unsigned)qtiles, (unsigned)splits);
-    // Autotuner: the first large call of each precision times the epilogue
+    // Autotuner: the first large call of each variant times the epilogue
     // layouts (4 or 8 epilogue warps, chunk minima from the reducing TMEM load
-    // or from an ALU min tree) on the live problem and keeps the fastest for
-    // this context; all return the same candidates.
-    int &epi = ctx->tc_epi[kc == 3 ? 1 : 0];
-    if (epi == 0 && !ctx->capturing && (double)m * (double)ds->N >= 1e9) {
+    // or from an ALU min tree) and, for the certified nearest point, the
+    // number of FP16 products (two or three), on the live problem, and keeps
+    // the fastest for this context; all return the same answers.
+    int &tuned = ctx->tc_epi[slot];
+    const int kc_fixed = slot == 0 ? 1 : 3;
+    if (tuned == 0 && !ctx->capturing && (double)m * (double)ds->N >= 1e9) {
         float best = 1e30f;
-        for (int e : {4, 8, 4 | kEpiRed, 8 | kEpiRed}) {
-            DD_TRY_CUDA(ctx, dd_event_record(ctx, ctx->ev_scan[0], s));
-            DD_TRY(launch_tc_any(ctx, kc, e, grid, ds, n_tiles, qa, rec, m, splits, tps, hdr, cand, topk, s));
-            DD_TRY_CUDA(ctx, dd_event_record(ctx, ctx->ev_scan[1], s));
-            DD_TRY_CUDA(ctx, cudaEventSynchronize(ctx->ev_scan[1]));
-            float ms = 0.f;
-            DD_TRY_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev_scan[0], ctx->ev_scan[1]));
-            if (ms < best) {
-                best = ms;
-                epi = e;
+        for (int kc : {3, 2}) {
+            if (kc == 2 && slot != 1) continue;
+            DD_TRY(prep(kc));
+            for (int e : {4, 8, 4 | kEpiRed, 8 | kEpiRed}) {
+                const bool topk = kc == 1 || out.k >= 2;
+                DD_TRY_CUDA(ctx, dd_event_record(ctx, ctx->ev_scan[0], s));
+                DD_TRY(launch_tc_any(ctx, slot == 0 ? 1 : kc, e, grid, ds, n_tiles, qa, rec, m, splits, tps, hdr,
+                                     cand, topk, s));
+                DD_TRY_CUDA(ctx, dd_event_record(ctx, ctx->ev_scan[1], s));
+                DD_TRY_CUDA(ctx, cudaEventSynchronize(ctx->ev_scan[1]));
+                float ms = 0.f;
+                DD_TRY_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev_scan[0], ctx->ev_scan[1]));
+                if (ms < best) {
+                    best = ms;
+                    tuned = e | ((slot == 0 ? 1 : kc) << kKcShift);
+                }
             }
         }
     }
-    const int use_epi = epi ? epi : (4 | kEpiRed);
+    int code = tuned ? tuned : (4 | kEpiRed | (kc_fixed << kKcShift));
+    if (slot == 1 && (terms == 2 || terms == 3)) code = (code & ((1 << kKcShift) - 1)) | (terms << kKcShift);
+    const int kc = code >> kKcShift;
+    const int epi_code = code & ((1 << kKcShift) - 1);
+    const bool topk = kc == 1 || out.k >= 2;
+    DD_TRY(prep(kc));
     if (st) DD_TRY_CUDA(ctx, dd_event_record(ctx, ctx->ev_scan[0], s));
-    DD_TRY(launch_tc_any(ctx, kc, use_epi, grid, ds, n_tiles, qa, rec, m, splits, tps, hdr, cand, topk, s));
+    DD_TRY(launch_tc_any(ctx, kc, epi_code, grid, ds, n_tiles, qa, rec, m, splits, tps, hdr, cand, topk, s));
     if (st) DD_TRY_CUDA(ctx, dd_event_record(ctx, ctx->ev_scan[1], s));
     if (st) st->distances += m * ds->N;
     const double inv_s2 = 1.0 / (ds->scale16 * ds->scale16);
+    const int nsplit = splits * ((epi_code & 0xff) / 4);
     if (out.k >= 2)
-        DD_TRY(dd_merge_topk(ds, y_dev, m, splits * ((use_epi & 0xff) / 4), kCap, hdr, cand, rec, certify, inv_s2,
-                             out, st, s));
+        DD_TRY(dd_merge_topk(ds, y_dev, m, nsplit, kCap, hdr, cand, rec, certify, inv_s2, out, st, s));
     else
-        DD_TRY(dd_merge_rescore(ds, y_dev, m, splits * ((use_epi & 0xff) / 4), kCap, hdr, cand, rec, certify, inv_s2,
-                                out, st, s));
+        DD_TRY(dd_merge_rescore(ds, y_dev, m, nsplit, kCap, hdr, cand, rec, certify, inv_s2, out, st, s));
     if (st && !ctx->defer) {
         float ms = 0.f;
         DD_TRY_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev_scan[0], ctx->ev_scan[1]));

@@ -91,8 +91,10 @@ def test_second_bound_matches_oracle(ctx, setup, f_d, eq14):
     assert np.all(d2nd >= 0)
     assert ok.mean() >= 0.99
     if f_d == 1.0:
+        # a lower bound up to the FP32 rounding of the search's distances (the
+        # library's motion record shrinks it by 1e-5 relative for that)
         _, _, _, e2 = nn.nn_top2(Z, zq)
-        assert np.all(d2nd <= 2 * e2 * (1 + 1e-6))
+        assert np.all(d2nd <= 2 * e2 * (1 + 1e-5))
 
 
 @pytest.mark.parametrize("f_d,budget,eq14", [(1.0, -1, 0), (1.0, 0, 0), (1.0, 0, 1), (0.6, 0, 0), (0.6, -1, 0),

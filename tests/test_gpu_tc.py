@@ -25,25 +25,35 @@ def ctx():
     P.dd_destroy(c)
 
 
-def project(ctx, ds, y, certify=True):
+def project(ctx, ds, y, certify=True, terms=0, d2nd=None):
     m = len(y)
     yd = torch.from_numpy(y).cuda()
     idx = torch.full((m,), -7, dtype=torch.int32, device="cuda")
     d2 = torch.full((m,), -1.0, dtype=torch.float64, device="cuda")
-    st = P.dd_project_nearest(ds, ctx, yd, idx, d2, mode=P.DD_SEARCH_EXACT_TC, certify=certify)
+    st = P.dd_project_nearest(ds, ctx, yd, idx, d2, mode=P.DD_SEARCH_EXACT_TC, certify=certify, tc_terms=terms,
+                              d2nd=d2nd)
     torch.cuda.synchronize()
     return idx.cpu().numpy(), d2.cpu().numpy(), st
 
 
+@pytest.mark.parametrize("terms", [3, 2])
 @pytest.mark.parametrize("N", [1, 100, 128, 129, 4097, 30000])
-def test_tc_certified_ragged(ctx, N):
+def test_tc_certified_ragged(ctx, N, terms):
+    """Three FP16 products per distance (split query and data) and two
+    (split data, single FP16 query, window widened by the query's rounding
+    term): both the exact nearest point, and the second-distance bound below
+    the true second distance."""
     data = I.make_dataset(N, I.NONLINEAR, seed=N + 1)
     ds = P.dd_load_dataset(ctx, data, C, build_fp16=True)
     try:
         for m, spread in ((1, 0.05), (127, 0.02), (129, 0.3), (3000, 2.0)):
             y = I.make_states(m, I.NONLINEAR, seed=7 * m + N, spread=spread)
-            idx, d2, st = project(ctx, ds, y)
+            d2nd = torch.full((m,), -1.0, dtype=torch.float64, device="cuda")
+            idx, d2, st = project(ctx, ds, y, terms=terms, d2nd=d2nd)
             assert_nn_parity(idx, d2, data, y, C)
+            if N > 1:
+                _, _, b2 = oracle_nn(data, y, C)
+                assert np.all(d2nd.cpu().numpy() <= b2 * (1 + 1e-9))
     finally:
         P.dd_free_dataset(ds)
 
@@ -82,18 +92,23 @@ def test_tc_topk_mode_reports_accuracy(ctx):
         P.dd_free_dataset(ds)
 
 
-def test_tc_full_size_sampled(ctx):
+@pytest.mark.parametrize("terms", [0, 3, 2])
+def test_tc_full_size_sampled(ctx, terms):
+    """32 768 queries x 10^6 points (the 16^3 workload's sizes): the tuned
+    variant (0), three and two FP16 products per distance, on sampled
+    queries against the oracle."""
     N, m = 1_000_000, 32768
     raw = torch.empty((N, 12), dtype=torch.float32, device="cuda")
     P.dd_synth_dataset(ctx, raw, I.LINEAR, C, seed=0)
     ds = P.dd_load_dataset(ctx, raw, C, borrow=True, build_fp16=True)
     try:
         y = I.make_states(m, I.LINEAR, seed=5, spread=0.05)
-        idx, d2, st = project(ctx, ds, y)
+        project(ctx, ds, y, terms=terms)                     # tunes / warms up
+        idx, d2, st = project(ctx, ds, y, terms=terms)
         sample = np.random.default_rng(1).choice(m, 192, replace=False)
         data = I.make_dataset(N, I.LINEAR, seed=0)
         assert_nn_parity(idx[sample], d2[sample], data, y[sample], C)
-        print(f"uncertified {st.uncertified} of {m}, scan {st.scan_ms:.3f} ms, call {st.ms:.3f} ms")
+        print(f"terms {terms}: uncertified {st.uncertified} of {m}, scan {st.scan_ms:.3f} ms, call {st.ms:.3f} ms")
         assert st.uncertified <= m // 50
     finally:
         P.dd_free_dataset(ds)
