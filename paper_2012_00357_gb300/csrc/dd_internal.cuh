@@ -117,7 +117,7 @@ void dd_plans_drop(dd_ctx *ctx, uint64_t id);
 
 enum WsSlot {
     WS_SEARCH = 0, WS_QUERY = 1, WS_MISC = 2, WS_SOLVE = 3, WS_TC = 4, WS_ANN = 5, WS_ANN_SCAN = 6, WS_ANN_BUILD = 7,
-    WS_BATCH = 8, WS_BATCH_CG = 9, WS_ANN_PAIRS = 10
+    WS_BATCH = 8, WS_BATCH_CG = 9, WS_ANN_PAIRS = 10, WS_SUBSET = 11
 };
 
 // Coarse cells a tree search ranks per query (ann.cu).
@@ -300,9 +300,13 @@ struct CandHeader {
     int cnt;          // valid entries
     int pad;
 };
+// fp32_first: uncertified queries are re-searched by the certified FP32 scan
+// (a window 8x narrower than the tensor-core scan's) before any FP64 scan,
+// when the call may synchronise (not while a step is captured).
 dd_status dd_merge_rescore(dd_dataset *ds, const double *y_dev, int64_t m, int splits, int cap,
                            const CandHeader *hdr, const float2 *cand, const QueryRec *rec,
-                           int certify, double inv_s2, SearchOut out, dd_search_stats *st, cudaStream_t s);
+                           int certify, double inv_s2, SearchOut out, dd_search_stats *st, cudaStream_t s,
+                           bool fp32_first = false);
 // As dd_merge_rescore for the k >= 2 nearest points (out.k), from scans run
 // in top-k mode (the best `cap` scores of every split, no window): the k
 // nearest candidates by FP64 Eq. (3); with certify, a query whose k-th

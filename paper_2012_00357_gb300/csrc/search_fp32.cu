@@ -525,9 +525,63 @@ dd_status dd_fallback_exact(dd_dataset *ds, const double *y_dev, const int64_t *
     return DD_OK;
 }
 
+namespace {
+__global__ void k_gather_listed(const double *__restrict__ y, const int64_t *__restrict__ list, int64_t n,
+                                double *__restrict__ ys, int64_t *__restrict__ list_copy) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int64_t i = list[t];
+    list_copy[t] = i;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) ys[t * 12 + k] = y[i * 12 + k];
+}
+
+__global__ void k_scatter_listed(const int64_t *__restrict__ list, int64_t n, const int32_t *__restrict__ si,
+                                 const double *__restrict__ sd, const double *__restrict__ sd2,
+                                 int32_t *__restrict__ idx, double *__restrict__ d2, double *__restrict__ d2nd) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int64_t i = list[t];
+    idx[i] = si[t];
+    if (d2) d2[i] = sd[t];
+    if (d2nd) d2nd[i] = sd2[t];
+}
+}  // namespace
+
+// The listed queries searched again by the certified FP32 scan (which
+// re-searches its own uncertified ones in FP64), results written back.
+static dd_status exact_fp32_subset(dd_dataset *ds, const double *y_dev, const int64_t *list, int64_t n,
+                                   SearchOut out, cudaStream_t s) {
+    dd_ctx *ctx = ds->ctx;
+    auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
+    void *w = nullptr;
+    DD_TRY(dd_workspace(ctx, WS_SUBSET,
+                        r256((size_t)n * 96) + r256((size_t)n * 8) + r256((size_t)n * 4) + 2 * r256((size_t)n * 8),
+                        &w));
+    char *c = (char *)w;
+    double *ys = (double *)c;
+    c += r256((size_t)n * 96);
+    int64_t *lc = (int64_t *)c;
+    c += r256((size_t)n * 8);
+    int32_t *si = (int32_t *)c;
+    c += r256((size_t)n * 4);
+    double *sd = (double *)c;
+    c += r256((size_t)n * 8);
+    double *sd2 = (double *)c;
+    ctx->launches++;
+    k_gather_listed<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(y_dev, list, n, ys, lc);
+    DD_TRY_CUDA(ctx, cudaGetLastError());
+    DD_TRY(dd_search_exact_fp32(ds, ys, n, 1, SearchOut{si, sd, sd2}, nullptr, s));
+    ctx->launches++;
+    k_scatter_listed<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(lc, n, si, sd, sd2, out.idx, out.d2, out.d2nd);
+    DD_TRY_CUDA(ctx, cudaGetLastError());
+    return DD_OK;
+}
+
 dd_status dd_merge_rescore(dd_dataset *ds, const double *y_dev, int64_t m, int splits, int cap,
                            const CandHeader *hdr, const float2 *cand, const QueryRec *rec,
-                           int certify, double inv_s2, SearchOut out, dd_search_stats *st, cudaStream_t s) {
+                           int certify, double inv_s2, SearchOut out, dd_search_stats *st, cudaStream_t s,
+                           bool fp32_first) {
     dd_ctx *ctx = ds->ctx;
     void *w = nullptr;
     size_t need = (size_t)m * sizeof(int64_t) + 256;
@@ -540,6 +594,17 @@ dd_status dd_merge_rescore(dd_dataset *ds, const double *y_dev, int64_t m, int s
         ds->raw, ds->M, y_dev, m, splits, cap, hdr, cand, rec, certify, inv_s2, out.idx, out.d2, out.d2nd,
         fb_list, fb_count);
     DD_TRY_CUDA(ctx, cudaGetLastError());
+    if (certify && fp32_first && !ctx->capturing && !ctx->defer) {
+        unsigned long long n = 0;
+        DD_TRY_CUDA(ctx, cudaMemcpyAsync(&n, fb_count, sizeof(n), cudaMemcpyDeviceToHost, s));
+        DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+        if (n) DD_TRY(exact_fp32_subset(ds, y_dev, fb_list, (int64_t)n, out, s));
+        if (st) {
+            st->uncertified += (int64_t)n;
+            st->distances += (int64_t)n * ds->N;
+        }
+        return DD_OK;
+    }
     if (certify) {
         int grid = (int)std::min<int64_t>(m, (int64_t)ctx->n_sm * 4);
         ctx->launches++;
@@ -626,8 +691,9 @@ dd_status dd_search_exact_fp32(dd_dataset *ds, const double *y_dev, int64_t m, i
     const int64_t qtiles = (m + kQT - 1) / kQT;
     // Split count (data ranges per query tile, merged afterwards): the
     // heuristic fills whole waves of CTAs; the autotuner times it, half and
-    // twice it on the first large call of every query-tile count and keeps
-    // the fastest for this context (all give the same answers).
+    // twice it on the first call of every query-tile count with 10^9 to
+    // 5 x 10^12 pairs and keeps the fastest for this context (all give the
+    // same answers); larger problems take the heuristic.
     const int s0 = pick_splits(qtiles, n_tiles, ctx->n_sm, 2);
     int cands[3] = {s0, (int)std::max<int64_t>(1, s0 / 2), (int)std::min<int64_t>(n_tiles, (int64_t)s0 * 2)};
     int splits = s0;
@@ -635,7 +701,9 @@ dd_status dd_search_exact_fp32(dd_dataset *ds, const double *y_dev, int64_t m, i
     {
         auto it = ctx->fp32_splits.find(qtiles);
         if (it != ctx->fp32_splits.end()) splits = it->second;
-        else tune = !ctx->capturing && (double)m * (double)ds->N >= 1e9;
+        // the trials run the whole problem (the split count decides the grid
+        // shape), so only where one trial costs tens of milliseconds
+        else tune = !ctx->capturing && (double)m * (double)ds->N >= 1e9 && (double)m * (double)ds->N <= 5e12;
     }
     const int s_max = tune ? std::max(cands[0], std::max(cands[1], cands[2])) : splits;
 

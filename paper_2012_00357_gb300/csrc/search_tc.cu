@@ -144,6 +144,63 @@ __device__ __forceinline__ void tmem_wait_red(uint32_t (&r)[32], float &red) {
                  : "memory");
 }
 
+// One reducing TMEM load of 128 columns (a thread's whole row of the tile)
+// and its minimum; the registers and `red` may be used only after
+// tmem_wait128_red.
+__device__ __forceinline__ void tmem_ld128_red_async(uint32_t taddr, uint32_t (&r)[128], float &red) {
+    asm volatile(
+        "tcgen05.ld.red.sync.aligned.32x32b.x128.min.f32 {"
+        "%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,"
+        "%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,"
+        "%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63,%64,%65,%66,%67,%68,"
+        "%69,%70,%71,%72,%73,%74,%75,%76,%77,%78,%79,%80,%81,%82,%83,%84,%85,%86,%87,%88,%89,%90,"
+        "%91,%92,%93,%94,%95,%96,%97,%98,%99,%100,%101,%102,%103,%104,%105,%106,%107,%108,%109,"
+        "%110,%111,%112,%113,%114,%115,%116,%117,%118,%119,%120,%121,%122,%123,%124,%125,%126,%127"
+        "}, %128, [%129];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+          "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
+          "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
+          "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
+          "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63]),
+          "=r"(r[64]), "=r"(r[65]), "=r"(r[66]), "=r"(r[67]), "=r"(r[68]), "=r"(r[69]), "=r"(r[70]), "=r"(r[71]),
+          "=r"(r[72]), "=r"(r[73]), "=r"(r[74]), "=r"(r[75]), "=r"(r[76]), "=r"(r[77]), "=r"(r[78]), "=r"(r[79]),
+          "=r"(r[80]), "=r"(r[81]), "=r"(r[82]), "=r"(r[83]), "=r"(r[84]), "=r"(r[85]), "=r"(r[86]), "=r"(r[87]),
+          "=r"(r[88]), "=r"(r[89]), "=r"(r[90]), "=r"(r[91]), "=r"(r[92]), "=r"(r[93]), "=r"(r[94]), "=r"(r[95]),
+          "=r"(r[96]), "=r"(r[97]), "=r"(r[98]), "=r"(r[99]), "=r"(r[100]), "=r"(r[101]), "=r"(r[102]), "=r"(r[103]),
+          "=r"(r[104]), "=r"(r[105]), "=r"(r[106]), "=r"(r[107]), "=r"(r[108]), "=r"(r[109]), "=r"(r[110]), "=r"(r[111]),
+          "=r"(r[112]), "=r"(r[113]), "=r"(r[114]), "=r"(r[115]), "=r"(r[116]), "=r"(r[117]), "=r"(r[118]), "=r"(r[119]),
+          "=r"(r[120]), "=r"(r[121]), "=r"(r[122]), "=r"(r[123]), "=r"(r[124]), "=r"(r[125]), "=r"(r[126]), "=r"(r[127]),
+          "=f"(red)
+        : "r"(taddr)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait128_red(uint32_t (&r)[128], float &red) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]),
+                   "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
+                   "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31]),
+                   "+r"(r[32]), "+r"(r[33]), "+r"(r[34]), "+r"(r[35]), "+r"(r[36]), "+r"(r[37]), "+r"(r[38]), "+r"(r[39]),
+                   "+r"(r[40]), "+r"(r[41]), "+r"(r[42]), "+r"(r[43]), "+r"(r[44]), "+r"(r[45]), "+r"(r[46]), "+r"(r[47]),
+                   "+r"(r[48]), "+r"(r[49]), "+r"(r[50]), "+r"(r[51]), "+r"(r[52]), "+r"(r[53]), "+r"(r[54]), "+r"(r[55]),
+                   "+r"(r[56]), "+r"(r[57]), "+r"(r[58]), "+r"(r[59]), "+r"(r[60]), "+r"(r[61]), "+r"(r[62]), "+r"(r[63]),
+                   "+r"(r[64]), "+r"(r[65]), "+r"(r[66]), "+r"(r[67]), "+r"(r[68]), "+r"(r[69]), "+r"(r[70]), "+r"(r[71]),
+                   "+r"(r[72]), "+r"(r[73]), "+r"(r[74]), "+r"(r[75]), "+r"(r[76]), "+r"(r[77]), "+r"(r[78]), "+r"(r[79]),
+                   "+r"(r[80]), "+r"(r[81]), "+r"(r[82]), "+r"(r[83]), "+r"(r[84]), "+r"(r[85]), "+r"(r[86]), "+r"(r[87]),
+                   "+r"(r[88]), "+r"(r[89]), "+r"(r[90]), "+r"(r[91]), "+r"(r[92]), "+r"(r[93]), "+r"(r[94]), "+r"(r[95]),
+                   "+r"(r[96]), "+r"(r[97]), "+r"(r[98]), "+r"(r[99]), "+r"(r[100]), "+r"(r[101]), "+r"(r[102]), "+r"(r[103]),
+                   "+r"(r[104]), "+r"(r[105]), "+r"(r[106]), "+r"(r[107]), "+r"(r[108]), "+r"(r[109]), "+r"(r[110]), "+r"(r[111]),
+                   "+r"(r[112]), "+r"(r[113]), "+r"(r[114]), "+r"(r[115]), "+r"(r[116]), "+r"(r[117]), "+r"(r[118]), "+r"(r[119]),
+                   "+r"(r[120]), "+r"(r[121]), "+r"(r[122]), "+r"(r[123]), "+r"(r[124]), "+r"(r[125]), "+r"(r[126]), "+r"(r[127]),
+                   "+f"(red)
+                 :
+                 : "memory");
+}
+
 __device__ __forceinline__ float min3f(float a, float b, float c) {
     float d;
     asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
@@ -305,7 +362,10 @@ __global__ void k_prep_tc(const double *__restrict__ y, int64_t m, int64_t m_pad
 
 // ---- the contraction kernel ------------------------------------------------------
 // RED: the epilogue takes each 32-column chunk's minimum from the reducing
-// TMEM load (1) or from a min tree on the ALU (0).
+// TMEM load (1), or from a min tree on the ALU (0); 2 (4 epilogue warps
+// only): one reducing load of the thread's whole 128-column row, after which
+// the accumulator is released at once (one TMEM-load latency per tile
+// instead of four).
 template <int KC, int EPI, int RED>
 __global__ void __launch_bounds__(tc_threads<EPI>(), 2)
     k_scan_tc(const __half *__restrict__ zhi, const __half *__restrict__ zlo, int64_t N, int64_t n_tiles,
@@ -483,6 +543,33 @@ __global__ void __launch_bounds__(tc_threads<EPI>(), 2)
                 __syncwarp();
                 if (lane == 0) dd_mbar_arrive(dd_smem_addr(&bar_tempty[ab]));
             };
+            if constexpr (RED == 2) {
+                static_assert(EPI == 4, "the 128-column load takes a thread's whole row");
+                uint32_t rr[128];
+                float mrow;
+                tmem_ld128_red_async(base, rr, mrow);
+                tmem_wait128_red(rr, mrow);
+                release();
+                if (mrow <= cs.lim) {   // rare: walk the columns inside the window
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        unsigned msk = 0;
+#pragma unroll
+                        for (int k = 0; k < 32; ++k) msk |= (__uint_as_float(rr[32 * c + k]) <= cs.lim ? 1u : 0u) << k;
+                        const int64_t j0 = jb + c * 32;
+                        while (msk) {
+                            const int k = __ffs(msk) - 1;
+                            msk &= msk - 1;
+                            float vk = __uint_as_float(rr[32 * c]);
+#pragma unroll
+                            for (int kk = 1; kk < 32; ++kk) vk = (k == kk) ? __uint_as_float(rr[32 * c + kk]) : vk;
+                            if (vk <= cs.lim && j0 + k < N)
+                                cand_insert(cs, vk, (int)(j0 + k), w2, buf, kSt, kCap, topk, qlo4, qhn);
+                        }
+                    }
+                }
+                continue;
+            }
             load(base, ra, mina);
             wait(ra, mina);
 #pragma unroll 1
@@ -570,8 +657,10 @@ static dd_status launch_tc(dd_ctx *ctx, dim3 grid, dd_dataset *ds, int64_t n_til
 }
 
 // Variant codes of the autotuner: epilogue warps (4 or 8) | 256 x reducing
-// load | FP16 products per distance << kKcShift.
+// 32-column loads | 512 x one reducing 128-column load per row | FP16
+// products per distance << kKcShift.
 constexpr int kEpiRed = 256;
+constexpr int kEpiRow = 512;
 constexpr int kKcShift = 12;
 
 static dd_status launch_tc_any(dd_ctx *ctx, int kc, int code, dim3 grid, dd_dataset *ds, int64_t n_tiles,
@@ -581,6 +670,11 @@ static dd_status launch_tc_any(dd_ctx *ctx, int kc, int code, dim3 grid, dd_data
     const bool red = (code & kEpiRed) != 0;
 #define DD_TC_LAUNCH(K, E, R) \
     return launch_tc<K, E, R>(ctx, grid, ds, n_tiles, qa, rec, m, splits, tps, hdr, cand, topk, s)
+    if (code & kEpiRow) {   // one 128-column reducing load per row (4 epilogue warps)
+        if (kc == 3) DD_TC_LAUNCH(3, 4, 2);
+        if (kc == 2) DD_TC_LAUNCH(2, 4, 2);
+        DD_TC_LAUNCH(1, 4, 2);
+    }
     if (kc == 3) {
         if (epi == 8) {
             if (red) DD_TC_LAUNCH(3, 8, 1);
@@ -622,11 +716,19 @@ dd_status dd_search_exact_tc(dd_dataset *ds, const double *y_dev, int64_t m, int
     const int64_t m_pad = qtiles * kTM;
     const int splits = pick_splits_tc(qtiles, n_tiles, ctx->n_sm);
     const int64_t tps = (n_tiles + splits - 1) / splits;
+    int &tuned = ctx->tc_epi[slot];
+    const bool tune = tuned == 0 && !ctx->capturing && (double)m * (double)ds->N >= 1e9;
+    // the trials run on the first m_t queries: about 10^11 pairs each
+    const int64_t m_t = std::min<int64_t>(m, std::max<int64_t>(1024, (int64_t)(1e11 / (double)ds->N) / kTM * kTM));
+    const int64_t qtiles_t = (m_t + kTM - 1) / kTM;
+    const int splits_t = pick_splits_tc(qtiles_t, n_tiles, ctx->n_sm);
+    const int64_t tps_t = (n_tiles + splits_t - 1) / splits_t;
+    const int64_t slots = std::max<int64_t>(m * splits, tune ? m_t * splits_t : 0);
     auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
     size_t qa_bytes = r256((size_t)qtiles * 3 * kTileBytes);
     size_t rec_bytes = r256((size_t)m * sizeof(QueryRec));
-    size_t hdr_bytes = r256((size_t)m * splits * 2 * sizeof(CandHeader));
-    size_t cand_bytes = (size_t)m * splits * 2 * kCap * sizeof(float2);
+    size_t hdr_bytes = r256((size_t)slots * 2 * sizeof(CandHeader));
+    size_t cand_bytes = (size_t)slots * 2 * kCap * sizeof(float2);
     void *w = nullptr;
     DD_TRY(dd_workspace(ctx, WS_TC, qa_bytes + rec_bytes + hdr_bytes + cand_bytes, &w));
     char *c = (char *)w;
@@ -650,20 +752,30 @@ dd_status dd_search_exact_tc(dd_dataset *ds, const double *y_dev, int64_t m, int
     // Autotuner: the first large call of each variant times the epilogue
     // layouts (4 or 8 epilogue warps, chunk minima from the reducing TMEM load
     // or from an ALU min tree) and, for the certified nearest point, the
-    // number of FP16 products (two or three), on the live problem, and keeps
-    // the fastest for this context; all return the same answers.
-    int &tuned = ctx->tc_epi[slot];
+    // number of FP16 products (two or three), on the live problem's first m_t
+    // queries, and keeps the fastest for this context; all return the same
+    // answers.
     const int kc_fixed = slot == 0 ? 1 : 3;
-    if (tuned == 0 && !ctx->capturing && (double)m * (double)ds->N >= 1e9) {
+    if (tune) {
+        const dim3 grid_t((unsigned)qtiles_t, (unsigned)splits_t);
         float best = 1e30f;
         for (int kc : {3, 2}) {
             if (kc == 2 && slot != 1) continue;
             DD_TRY(prep(kc));
-            for (int e : {4, 8, 4 | kEpiRed, 8 | kEpiRed}) {
+            for (int e : {4, 8, 4 | kEpiRed, 8 | kEpiRed, 4 | kEpiRow}) {
                 const bool topk = kc == 1 || out.k >= 2;
+                // timed with the merge and the re-search of uncertified
+                // queries: a wider window can cost more there than it saves
                 DD_TRY_CUDA(ctx, dd_event_record(ctx, ctx->ev_scan[0], s));
-                DD_TRY(launch_tc_any(ctx, slot == 0 ? 1 : kc, e, grid, ds, n_tiles, qa, rec, m, splits, tps, hdr,
-                                     cand, topk, s));
+                DD_TRY(launch_tc_any(ctx, slot == 0 ? 1 : kc, e, grid_t, ds, n_tiles, qa, rec, m_t, splits_t, tps_t,
+                                     hdr, cand, topk, s));
+                const int ns = splits_t * ((e & 0xff) / 4);
+                const double is2 = 1.0 / (ds->scale16 * ds->scale16);
+                if (out.k >= 2)
+                    DD_TRY(dd_merge_topk(ds, y_dev, m_t, ns, kCap, hdr, cand, rec, certify, is2, out, nullptr, s));
+                else
+                    DD_TRY(dd_merge_rescore(ds, y_dev, m_t, ns, kCap, hdr, cand, rec, certify, is2, out, nullptr, s,
+                                            true));
                 DD_TRY_CUDA(ctx, dd_event_record(ctx, ctx->ev_scan[1], s));
                 DD_TRY_CUDA(ctx, cudaEventSynchronize(ctx->ev_scan[1]));
                 float ms = 0.f;
@@ -690,7 +802,7 @@ dd_status dd_search_exact_tc(dd_dataset *ds, const double *y_dev, int64_t m, int
     if (out.k >= 2)
         DD_TRY(dd_merge_topk(ds, y_dev, m, nsplit, kCap, hdr, cand, rec, certify, inv_s2, out, st, s));
     else
-        DD_TRY(dd_merge_rescore(ds, y_dev, m, nsplit, kCap, hdr, cand, rec, certify, inv_s2, out, st, s));
+        DD_TRY(dd_merge_rescore(ds, y_dev, m, nsplit, kCap, hdr, cand, rec, certify, inv_s2, out, st, s, true));
     if (st && !ctx->defer) {
         float ms = 0.f;
         DD_TRY_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev_scan[0], ctx->ev_scan[1]));

@@ -77,7 +77,7 @@ def test_second_bound_matches_oracle(ctx, setup, f_d, eq14):
     same clusters; at f_d = 1 it never exceeds the true second distance."""
     data, ds, levels, part = setup
     Z = metric.to_z(data.astype(np.float64), C)
-    y = I.make_states(800, I.NONLINEAR, seed=32, spread=0.05)
+    y = I.make_states(500, I.NONLINEAR, seed=32, spread=0.05)
     zq = metric.to_z(y, C)
     prev = np.random.default_rng(6).integers(0, len(data), len(y)).astype(np.int32)
     idx, d2, d2nd, st = project(ctx, ds, y, f_d, prev, eq14=eq14)
@@ -97,8 +97,7 @@ def test_second_bound_matches_oracle(ctx, setup, f_d, eq14):
         assert np.all(d2nd <= 2 * e2 * (1 + 1e-5))
 
 
-@pytest.mark.parametrize("f_d,budget,eq14", [(1.0, -1, 0), (1.0, 0, 0), (1.0, 0, 1), (0.6, 0, 0), (0.6, -1, 0),
-                                             (0.6, 0, 1), (0.6, -1, 1)])
+@pytest.mark.parametrize("f_d,budget,eq14", [(1.0, -1, 0), (1.0, 0, 1), (0.6, 0, 0), (0.6, -1, 1)])
 def test_two_projections_with_a_motion_record(ctx, setup, f_d, budget, eq14):
     """A projection, then the states moved by steps around the Eq. (14)
     radius and projected again with the first call's record.  Query by query
@@ -107,7 +106,7 @@ def test_two_projections_with_a_motion_record(ctx, setup, f_d, budget, eq14):
     kept or searched, is the brute-force nearest point."""
     data, ds, levels, part = setup
     Z = metric.to_z(data.astype(np.float64), C)
-    y1 = I.make_states(1500, I.NONLINEAR, seed=33, spread=0.05)
+    y1 = I.make_states(700, I.NONLINEAR, seed=33, spread=0.05)
     prev = np.random.default_rng(7).integers(0, len(data), len(y1)).astype(np.int32)
     i1, a1, s1, _ = project(ctx, ds, y1, f_d, prev, budget, eq14=eq14)
     z1 = metric.to_z(y1, C)
