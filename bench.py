@@ -57,7 +57,7 @@ TRAFFIC = {
 # Captures of exactly the benched launch: (workload, mode): (source, sha256,
 # DRAM bytes per launch); profiles/k_scan_tc_cube16_N1e6.md.
 TRAFFIC_EXACT = {
-    ("cube16_N1e6_exact", "tc"): ("search_tc.cu", "b035cef58e7ebf9ffbc7210468cb7a40e2d65bc81f53ac18bfc462b487480928", 78.2e6),
+    ("cube16_N1e6_exact", "tc"): ("search_tc.cu", "014a9bc77e1ce7fa35332d7e18ed8bababb95804ccf158cecf784a9c6dba62b4", 78.5e6),
 }
 
 
