@@ -119,6 +119,14 @@ typedef struct dd_dataset_opts {
     double knn_fd;      /* f_d of the graph build (0 .. 1; 1 with at most 8
                            coarse cells of at most 8 leaves gives the exact
                            graph) */
+    int ann_alu;        /* 0 (default): the nearest-centroid passes of the
+                           partition build and the search's cell ranking run
+                           on the tensor cores, with answers equal to the ALU
+                           kernels' (rows the low-precision scores cannot
+                           settle are finished on the ALU), and the leaf sums
+                           of the build are gathered per run of points in
+                           shared memory first; 1: the plain ALU kernels
+                           throughout (same partition, same answers) */
 } dd_dataset_opts;
 
 /* Load a material data set D = {(eps_j, sig_j)}, j = 0..N-1 (Sec. 2) and
@@ -163,6 +171,11 @@ dd_status dd_dataset_ann_index(dd_dataset *ds, int32_t *cluster_of, double *cent
  * The cells order the descent and pass Eq. (13) with these radii (Sec. 4.2).
  * Errors: DD_ERR_STATE if no two-level partition was built.  Synchronous. */
 dd_status dd_dataset_ann_cells(dd_dataset *ds, int32_t *L1, int32_t *L2, double *centroids, double *radii);
+
+/* Rows of the partition build's nearest-centroid passes that the tensor-core
+ * scores could not settle and the ALU kernel finished (0 with ann_alu = 1 or
+ * no partition).  Not an error: the build's answers are the same either way. */
+int64_t dd_dataset_ann_build_fallback(const dd_dataset *ds);
 
 /* The k-nearest-neighbour graph of DD_SEARCH_KNNG (Sec. 4.4, built when
  * knn_k > 0): its k (0 if none), and a host copy.

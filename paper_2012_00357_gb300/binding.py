@@ -27,7 +27,7 @@ EXPORTS = [
     "dd_dataset_size", "dd_dataset_bytes", "dd_synth_dataset", "dd_project_nearest", "dd_solve",
     "dd_result_free", "dd_solver_create", "dd_solver_step", "dd_solver_done", "dd_solver_result",
     "dd_solver_free", "dd_launch_count", "dd_dataset_ann_nlist", "dd_dataset_ann_index",
-    "dd_dataset_ann_cells", "dd_dataset_knn_k", "dd_dataset_knn_graph", "dd_pca_metric",
+    "dd_dataset_ann_cells", "dd_dataset_ann_build_fallback", "dd_dataset_knn_k", "dd_dataset_knn_graph", "dd_pca_metric",
     "dd_project_nearest_noalloc", "dd_solvers_step", "dd_solve_batch", "dd_server_start", "dd_server_submit",
     "dd_server_poll", "dd_server_get_stats", "dd_server_stop",
 ]
@@ -44,7 +44,7 @@ class DDError(RuntimeError):
 class dd_dataset_opts(ctypes.Structure):
     _fields_ = [("build_fp16", c_int), ("ann_nlist", c_int), ("ann_train_iters", c_int),
                 ("ann_sample", c_int64), ("seed", c_uint64), ("borrow", c_int), ("ann_levels", c_int),
-                ("knn_k", c_int), ("knn_fd", c_double)]
+                ("knn_k", c_int), ("knn_fd", c_double), ("ann_alu", c_int)]
 
 
 class dd_search_opts(ctypes.Structure):
@@ -155,6 +155,8 @@ def lib():
         L.dd_dataset_ann_nlist.restype = c_int
         L.dd_dataset_ann_index.argtypes = [vp, vp, vp, vp]
         L.dd_dataset_ann_cells.argtypes = [vp, POINTER(c_int32), POINTER(c_int32), vp, vp]
+        L.dd_dataset_ann_build_fallback.argtypes = [vp]
+        L.dd_dataset_ann_build_fallback.restype = c_int64
         L.dd_dataset_knn_k.argtypes = [vp]
         L.dd_dataset_knn_k.restype = c_int
         L.dd_dataset_knn_graph.argtypes = [vp, vp]
@@ -222,11 +224,11 @@ def dd_bytes_in_use(ctx) -> int:
 
 def dd_load_dataset(ctx, eps_sig, C, build_fp16: bool = False, ann_nlist: int = 0, ann_train_iters: int = 0,
                     ann_sample: int = 0, seed: int = 0, borrow: bool = False, ann_levels: int = 1,
-                    knn_k: int = 0, knn_fd: float = 0.6):
+                    knn_k: int = 0, knn_fd: float = 0.6, ann_alu: bool = False):
     N = int(eps_sig.shape[0])
     assert tuple(eps_sig.shape[1:]) == (12,)
     opts = dd_dataset_opts(int(build_fp16), int(ann_nlist), int(ann_train_iters), int(ann_sample), int(seed),
-                           int(borrow), int(ann_levels), int(knn_k), float(knn_fd))
+                           int(borrow), int(ann_levels), int(knn_k), float(knn_fd), int(ann_alu))
     ds = c_void_p()
     _check(ctx, lib().dd_load_dataset(ctx, _ptr(eps_sig), N, _Cmat(C), ctypes.byref(opts), ctypes.byref(ds)))
     return ds
@@ -393,6 +395,11 @@ def dd_dataset_ann_cells(ds, ctx):
     rad = np.empty(L1.value, np.float64)
     _check(ctx, lib().dd_dataset_ann_cells(ds, None, None, _ptr(cent), _ptr(rad)))
     return L2.value, cent, rad
+
+
+def dd_dataset_ann_build_fallback(ds) -> int:
+    """Build rows the tensor-core nearest-centroid passes left to the ALU."""
+    return int(lib().dd_dataset_ann_build_fallback(ds))
 
 
 def dd_pca_metric(ctx, eps_sig) -> np.ndarray:

@@ -44,33 +44,22 @@ namespace {
 constexpr int kCand = kAnnCand;   // candidate clusters per query
 constexpr int kTileC = 256;       // centroids per shared-memory tile in k_assign
 
-__device__ __forceinline__ float dist2_12(const float *a, const float (&q)[12]) {
-    const float4 *p = reinterpret_cast<const float4 *>(a);
-    const float4 u = __ldg(p), v = __ldg(p + 1), w = __ldg(p + 2);
-    float d, s = 0.f;
-    d = u.x - q[0]; s = fmaf(d, d, s);
-    d = u.y - q[1]; s = fmaf(d, d, s);
-    d = u.z - q[2]; s = fmaf(d, d, s);
-    d = u.w - q[3]; s = fmaf(d, d, s);
-    d = v.x - q[4]; s = fmaf(d, d, s);
-    d = v.y - q[5]; s = fmaf(d, d, s);
-    d = v.z - q[6]; s = fmaf(d, d, s);
-    d = v.w - q[7]; s = fmaf(d, d, s);
-    d = w.x - q[8]; s = fmaf(d, d, s);
-    d = w.y - q[9]; s = fmaf(d, d, s);
-    d = w.z - q[10]; s = fmaf(d, d, s);
-    d = w.w - q[11]; s = fmaf(d, d, s);
-    return s;
-}
+__device__ __forceinline__ float dist2_12(const float *a, const float (&q)[12]) { return dd_dist2_12(a, q); }
 
 // Nearest centroid of every point (expanded FP32 score |c|^2 - 2 c.z, ties to
-// the lower centroid index).  Centroids stream through shared memory.
+// the lower centroid index).  Centroids stream through shared memory.  With
+// a list, only the rows list[0 .. *n_list - 1] (the rows the tensor-core
+// pass left open).
 __global__ void __launch_bounds__(256) k_assign(const float *__restrict__ z, int64_t n,
                                                 const float *__restrict__ cent, const float *__restrict__ cn,
-                                                int L, int32_t *__restrict__ out) {
+                                                int L, int32_t *__restrict__ out, const int32_t *__restrict__ list,
+                                                const unsigned *__restrict__ n_list) {
     __shared__ __align__(16) float sc[kTileC * 12];
     __shared__ float sn[kTileC];
-    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nq = list ? ((int64_t)*n_list < n ? (int64_t)*n_list : n) : n;
+    if (blockIdx.x * (int64_t)blockDim.x >= nq) return;   // the whole block, before any barrier
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t j = t < nq ? (list ? (int64_t)list[t] : t) : n;
     float q[12];
     if (j < n) {
 #pragma unroll
@@ -740,6 +729,37 @@ __global__ void __launch_bounds__(256) k_assign_fine(const float *__restrict__ z
     if (act) fasg[p] = bi;
 }
 
+// k_assign_fine for the sorted positions list[0 .. *n_list - 1] only: the
+// same score of each of the cell's leaves, in leaf order.
+__global__ void k_assign_fine_listed(const float *__restrict__ z, const int32_t *__restrict__ perm1,
+                                     const int32_t *__restrict__ c1s, const int32_t *__restrict__ list,
+                                     const unsigned *__restrict__ n_list, const float *__restrict__ centf,
+                                     const float *__restrict__ cnf, int L2, int32_t *__restrict__ fasg) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)*n_list) return;
+    const int64_t p = list[t];
+    const int c = c1s[p];
+    const float *zp = z + (size_t)perm1[p] * 12;
+    float q[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) q[k] = -2.f * zp[k];
+    float best = INFINITY;
+    int bi = 0;
+    for (int f = 0; f < L2; ++f) {
+        const float4 *pc = reinterpret_cast<const float4 *>(centf + ((size_t)c * L2 + f) * 12);
+        const float4 a = __ldg(pc), b = __ldg(pc + 1), d = __ldg(pc + 2);
+        float v = __ldg(cnf + (size_t)c * L2 + f);
+        v = fmaf(q[0], a.x, v); v = fmaf(q[1], a.y, v); v = fmaf(q[2], a.z, v); v = fmaf(q[3], a.w, v);
+        v = fmaf(q[4], b.x, v); v = fmaf(q[5], b.y, v); v = fmaf(q[6], b.z, v); v = fmaf(q[7], b.w, v);
+        v = fmaf(q[8], d.x, v); v = fmaf(q[9], d.y, v); v = fmaf(q[10], d.z, v); v = fmaf(q[11], d.w, v);
+        if (v < best) {
+            best = v;
+            bi = f;
+        }
+    }
+    fasg[p] = bi;
+}
+
 __global__ void k_accum_fine(const float *__restrict__ z, const int32_t *__restrict__ perm1,
                              const int32_t *__restrict__ c1s, const int32_t *__restrict__ fasg, int64_t n, int L2,
                              double fs, unsigned long long *__restrict__ sums, unsigned *__restrict__ cnt) {
@@ -750,6 +770,59 @@ __global__ void k_accum_fine(const float *__restrict__ z, const int32_t *__restr
 #pragma unroll
     for (int k = 0; k < 12; ++k) atomicAdd(sums + leaf * 12 + k, to_fixed(zp[k], fs));
     atomicAdd(cnt + leaf, 1u);
+}
+
+// k_accum_fine with the sums of a run of sorted positions gathered in shared
+// memory first: a block takes kAccumRun consecutive positions (the members
+// of one or two cells), adds every point to its leaf's shared-memory sum,
+// then adds the non-empty leaf sums to the global ones, so that the global
+// atomics fall from 13 per point to 13 per (block, leaf).  The sums are
+// 64-bit fixed point, so the result does not depend on the order.
+constexpr int kAccumRun = 8192;
+constexpr int kAccumThreads = 512;
+
+__global__ void __launch_bounds__(kAccumThreads) k_accum_fine_run(const float *__restrict__ z,
+                                                                  const int32_t *__restrict__ perm1,
+                                                                  const int32_t *__restrict__ c1s,
+                                                                  const int32_t *__restrict__ fasg, int64_t n, int L2,
+                                                                  double fs, unsigned long long *__restrict__ sums,
+                                                                  unsigned *__restrict__ cnt) {
+    extern __shared__ __align__(16) unsigned long long s_sum[];   // [L2 x 12], then L2 counts
+    unsigned *s_cnt = reinterpret_cast<unsigned *>(s_sum + (size_t)L2 * 12);
+    const int64_t p0 = (int64_t)blockIdx.x * kAccumRun;
+    const int64_t p1 = min(n, p0 + (int64_t)kAccumRun);
+    int64_t start = p0;
+    while (start < p1) {   // one cell's positions at a time (the cells are contiguous)
+        const int c = c1s[start];
+        int64_t lo = start, hi = p1;   // first position of [start, p1) outside cell c
+        while (lo + 1 < hi) {
+            const int64_t mid = (lo + hi) / 2;
+            if (c1s[mid] == c) lo = mid;
+            else hi = mid;
+        }
+        const int64_t end = hi;
+        for (int t = threadIdx.x; t < L2 * 12; t += blockDim.x) s_sum[t] = 0ull;
+        for (int t = threadIdx.x; t < L2; t += blockDim.x) s_cnt[t] = 0u;
+        __syncthreads();
+        for (int64_t p = start + threadIdx.x; p < end; p += blockDim.x) {
+            const int f = fasg[p];
+            const float *zp = z + (size_t)perm1[p] * 12;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) atomicAdd(s_sum + f * 12 + k, to_fixed(zp[k], fs));
+            atomicAdd(s_cnt + f, 1u);
+        }
+        __syncthreads();
+        const int64_t leaf0 = (int64_t)c * L2;
+        for (int t = threadIdx.x; t < L2; t += blockDim.x) {
+            const unsigned k = s_cnt[t];
+            if (!k) continue;
+            atomicAdd(cnt + leaf0 + t, k);
+#pragma unroll
+            for (int a = 0; a < 12; ++a) atomicAdd(sums + (leaf0 + t) * 12 + a, s_sum[t * 12 + a]);
+        }
+        __syncthreads();
+        start = end;
+    }
 }
 
 __global__ void k_leaf_of(const int32_t *__restrict__ perm1, const int32_t *__restrict__ c1s,
@@ -1402,6 +1475,8 @@ extern "C" dd_status dd_dataset_ann_index(dd_dataset *ds, int32_t *cluster_of, d
     return DD_OK;
 }
 
+extern "C" int64_t dd_dataset_ann_build_fallback(const dd_dataset *ds) { return ds ? ds->ann.build_fallback : 0; }
+
 extern "C" dd_status dd_dataset_ann_cells(dd_dataset *ds, int32_t *L1, int32_t *L2, double *centroids,
                                           double *radii) {
     if (!ds) return DD_ERR_ARG;
@@ -1446,10 +1521,117 @@ void dd_free_ann(dd_dataset *ds) {
         dd_free(ctx, a.rad1, L1p * 4);
         if (a.lrad1) dd_free(ctx, a.lrad1, L1p * 4);
     }
+    dd_near_tc_free(ctx, &a.rank_tc);
     a = AnnIndex();
 }
 
 static dd_status build_tree2(dd_dataset *ds, const dd_dataset_opts &o);
+
+// The nearest-centroid passes of a build: on the tensor cores (near_tc.cu,
+// the same answers) unless the options ask for the ALU, the centroid set is
+// too small, or the groups are not whole 128-leaf tiles; the rows that the
+// tensor-core scores leave open are finished by the ALU kernel.
+struct BuildNear {
+    dd_ctx *ctx = nullptr;
+    bool tc = false;
+    double s = 0.0;
+    float R = 0.f;
+    NearTcSet C;
+    int32_t *fb = nullptr;
+    unsigned *fb_n = nullptr;
+    int64_t cap = 0;
+    int64_t fallback = 0;
+
+    dd_status init(dd_dataset *ds, const dd_dataset_opts &o) {
+        ctx = ds->ctx;
+        tc = o.ann_alu == 0;
+        if (!tc) return DD_OK;
+        s = dd_tc_scale(ds->maxabs);
+        R = (float)(ds->R * (1.0 + 1e-6));
+        cap = std::min<int64_t>(ds->N, (int64_t)1 << 24);
+        void *p = nullptr;
+        DD_TRY(dd_alloc(ctx, &p, (size_t)cap * 4 + 256, "build fallback list"));
+        fb = (int32_t *)p;
+        fb_n = (unsigned *)((char *)p + (size_t)cap * 4);
+        return DD_OK;
+    }
+    void release() {
+        if (fb) dd_free(ctx, fb, (size_t)cap * 4 + 256);
+        fb = nullptr;
+        if (ctx) dd_near_tc_free(ctx, &C);
+    }
+    ~BuildNear() { release(); }
+    // rows the tensor-core pass left open (host count; synchronous)
+    dd_status open_rows(cudaStream_t st, int64_t *n) {
+        unsigned h = 0;
+        DD_TRY_CUDA(ctx, cudaMemcpyAsync(&h, fb_n, 4, cudaMemcpyDeviceToHost, st));
+        DD_TRY_CUDA(ctx, cudaStreamSynchronize(st));
+        *n = h;
+        fallback += h;
+        return DD_OK;
+    }
+    // out[j] = nearest of the L centroids to z[j], j < n
+    dd_status assign(const float *z, int64_t n, const float *cent, const float *cn, int L, int32_t *out,
+                     cudaStream_t st) {
+        if (n == 0) return DD_OK;
+        const unsigned g = (unsigned)((n + 255) / 256);
+        if (!tc || L < 16) {   // a handful of centroids: the ALU kernel
+            ctx->launches++;
+            k_assign<<<g, 256, 0, st>>>(z, n, cent, cn, L, out, nullptr, nullptr);
+            DD_TRY_CUDA(ctx, cudaGetLastError());
+            return DD_OK;
+        }
+        DD_TRY(dd_near_tc_operands(ctx, cent, cn, L, L, s, R, &C, st));
+        DD_TRY_CUDA(ctx, cudaMemsetAsync(fb_n, 0, 4, st));
+        DD_TRY(dd_near_tc_assign(ctx, C, z, n, out, fb, fb_n, cap, st));
+        int64_t nf = 0;
+        DD_TRY(open_rows(st, &nf));
+        if (nf == 0) return DD_OK;
+        ctx->launches++;
+        if (nf > cap) k_assign<<<g, 256, 0, st>>>(z, n, cent, cn, L, out, nullptr, nullptr);
+        else k_assign<<<(unsigned)((nf + 255) / 256), 256, 0, st>>>(z, n, cent, cn, L, out, fb, fb_n);
+        DD_TRY_CUDA(ctx, cudaGetLastError());
+        return DD_OK;
+    }
+    // fasg[p] = nearest of the L2 leaves of cell c1s[p] to z[perm1[p]]; the
+    // tensor-core operands of a cell's leaves are taken about the cell's
+    // centroid (cent1)
+    dd_status assign_fine(const float *z, const int32_t *perm1, const int32_t *c1s, int64_t n, const float *cent,
+                          const float *cn, const float *cent1, int L1, int L2, int32_t *fasg, cudaStream_t st) {
+        const unsigned g = (unsigned)((n + 255) / 256);
+        if (!tc || L2 % 128 != 0) {
+            ctx->launches++;
+            k_assign_fine<<<g, 256, 0, st>>>(z, perm1, c1s, n, cent, cn, L2, fasg);
+            DD_TRY_CUDA(ctx, cudaGetLastError());
+            return DD_OK;
+        }
+        DD_TRY(dd_near_tc_operands_grouped(ctx, cent, cn, L1, L2, cent1, R, &C, st));
+        DD_TRY_CUDA(ctx, cudaMemsetAsync(fb_n, 0, 4, st));
+        DD_TRY(dd_near_tc_assign_grouped(ctx, C, z, perm1, c1s, n, fasg, fb, fb_n, cap, st));
+        int64_t nf = 0;
+        DD_TRY(open_rows(st, &nf));
+        if (nf == 0) return DD_OK;
+        ctx->launches++;
+        if (nf > cap) k_assign_fine<<<g, 256, 0, st>>>(z, perm1, c1s, n, cent, cn, L2, fasg);
+        else k_assign_fine_listed<<<(unsigned)((nf + 255) / 256), 256, 0, st>>>(z, perm1, c1s, fb, fb_n, cent, cn,
+                                                                                 L2, fasg);
+        DD_TRY_CUDA(ctx, cudaGetLastError());
+        return DD_OK;
+    }
+};
+
+// Tensor-core operands of the centroid set the search ranks (kept with the
+// index; the ranking falls back to the ALU kernel without them).
+static dd_status build_rank_operands(dd_dataset *ds, const dd_dataset_opts &o) {
+    AnnIndex &a = ds->ann;
+    const bool two = a.levels == 2;
+    const int Lr = two ? a.L1 : a.nlist;
+    if (o.ann_alu || Lr < 16 || Lr > kRankMax) return DD_OK;
+    DD_TRY(dd_near_tc_operands(ds->ctx, two ? a.cent1 : a.cent, two ? a.cn1 : a.cn, Lr, Lr, dd_tc_scale(ds->maxabs),
+                               (float)(ds->R * (1.0 + 1e-6)), &a.rank_tc, ds->ctx->stream));
+    ds->bytes += (size_t)a.rank_tc.rows_pad * 64;
+    return DD_OK;
+}
 
 dd_status dd_build_ann(dd_dataset *ds, const dd_dataset_opts &o) {
     if (o.ann_levels == 2) return build_tree2(ds, o);
@@ -1503,9 +1685,11 @@ dd_status dd_build_ann(dd_dataset *ds, const dd_dataset_opts &o) {
     DD_TRY_CUDA(ctx, cudaMemsetAsync(cnt, 0, (size_t)Lp * 4, s));
     ctx->launches++;
     k_update<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(sums, cnt, fs, a.cent, a.cn, L);   // norms only
+    BuildNear near;
+    DD_TRY(near.init(ds, o));
     for (int it = 0; it < iters; ++it) {
-        ctx->launches += 3;
-        k_assign<<<(unsigned)((S + 255) / 256), 256, 0, s>>>(sample, S, a.cent, a.cn, L, asg);
+        DD_TRY(near.assign(sample, S, a.cent, a.cn, L, asg, s));
+        ctx->launches += 2;
         k_accum<<<(unsigned)((S + 255) / 256), 256, 0, s>>>(sample, S, asg, fs, sums, cnt);
         k_update<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(sums, cnt, fs, a.cent, a.cn, L);
     }
@@ -1517,8 +1701,10 @@ dd_status dd_build_ann(dd_dataset *ds, const dd_dataset_opts &o) {
         DD_TRY_CUDA(ctx, cudaStreamSynchronize(s));
     }
     // assignment of every point, counting sort
-    ctx->launches += 2;
-    k_assign<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(ds->z32, N, a.cent, a.cn, L, asg);
+    DD_TRY(near.assign(ds->z32, N, a.cent, a.cn, L, asg, s));
+    a.build_fallback = near.fallback;
+    near.release();
+    ctx->launches++;
     DD_TRY_CUDA(ctx, cudaMemsetAsync(cnt, 0, (size_t)Lp * 4, s));
     k_hist<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(asg, N, cnt);
     DD_TRY_CUDA(ctx, cudaGetLastError());
@@ -1546,7 +1732,7 @@ dd_status dd_build_ann(dd_dataset *ds, const dd_dataset_opts &o) {
         nonempty += hc[l] > 0;
     }
     a.nonempty = nonempty;
-    return DD_OK;
+    return build_rank_operands(ds, o);
 }
 
 // Two-level tree: coarse k-means cells (Lloyd on a sample), every cell split
@@ -1618,9 +1804,11 @@ static dd_status build_tree2(dd_dataset *ds, const dd_dataset_opts &o) {
     DD_TRY_CUDA(ctx, cudaMemsetAsync(cnt, 0, b_cnt, s));
     ctx->launches++;
     k_update<<<(unsigned)((L1 + 255) / 256), 256, 0, s>>>(sums, cnt, fs, a.cent1, a.cn1, L1);
+    BuildNear near;
+    DD_TRY(near.init(ds, o));
     for (int it = 0; it < iters; ++it) {
-        ctx->launches += 3;
-        k_assign<<<(unsigned)((S1 + 255) / 256), 256, 0, s>>>(sample, S1, a.cent1, a.cn1, L1, asg1);
+        DD_TRY(near.assign(sample, S1, a.cent1, a.cn1, L1, asg1, s));
+        ctx->launches += 2;
         k_accum<<<(unsigned)((S1 + 255) / 256), 256, 0, s>>>(sample, S1, asg1, fs, sums, cnt);
         k_update<<<(unsigned)((L1 + 255) / 256), 256, 0, s>>>(sums, cnt, fs, a.cent1, a.cn1, L1);
     }
@@ -1628,8 +1816,8 @@ static dd_status build_tree2(dd_dataset *ds, const dd_dataset_opts &o) {
         std::vector<float> big((size_t)(L1p - L1), 1e30f);
         DD_TRY_CUDA(ctx, cudaMemcpyAsync(a.cn1 + L1, big.data(), (L1p - L1) * 4, cudaMemcpyHostToDevice, s));
     }
-    ctx->launches += 2;
-    k_assign<<<gN, 256, 0, s>>>(ds->z32, N, a.cent1, a.cn1, L1, asg1);
+    DD_TRY(near.assign(ds->z32, N, a.cent1, a.cn1, L1, asg1, s));
+    ctx->launches++;
     DD_TRY_CUDA(ctx, cudaMemsetAsync(cnt, 0, b_cnt, s));
     k_hist<<<gN, 256, 0, s>>>(asg1, N, cnt);
     DD_TRY_CUDA(ctx, cudaGetLastError());
@@ -1660,14 +1848,24 @@ static dd_status build_tree2(dd_dataset *ds, const dd_dataset_opts &o) {
     DD_TRY_CUDA(ctx, cudaMemsetAsync(cnt, 0, b_cnt, s));
     ctx->launches++;
     k_update<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(sums, cnt, fs, a.cent, a.cn, L);
+    const size_t accum_smem = (size_t)L2 * (12 * 8 + 4);
+    if (near.tc && accum_smem <= 160 * 1024 && accum_smem > 48 * 1024)
+        DD_TRY_CUDA(ctx, cudaFuncSetAttribute(k_accum_fine_run, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)accum_smem));
     for (int it = 0; it < iters; ++it) {
-        ctx->launches += 3;
-        k_assign_fine<<<gN, 256, 0, s>>>(ds->z32, perm1, c1s, N, a.cent, a.cn, L2, fasg);
-        k_accum_fine<<<gN, 256, 0, s>>>(ds->z32, perm1, c1s, fasg, N, L2, fs, sums, cnt);
+        DD_TRY(near.assign_fine(ds->z32, perm1, c1s, N, a.cent, a.cn, a.cent1, L1, L2, fasg, s));
+        ctx->launches += 2;
+        if (near.tc && accum_smem <= 160 * 1024)
+            k_accum_fine_run<<<(unsigned)((N + kAccumRun - 1) / kAccumRun), kAccumThreads, accum_smem, s>>>(
+                ds->z32, perm1, c1s, fasg, N, L2, fs, sums, cnt);
+        else
+            k_accum_fine<<<gN, 256, 0, s>>>(ds->z32, perm1, c1s, fasg, N, L2, fs, sums, cnt);
         k_update<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(sums, cnt, fs, a.cent, a.cn, L);
     }
-    ctx->launches += 2;
-    k_assign_fine<<<gN, 256, 0, s>>>(ds->z32, perm1, c1s, N, a.cent, a.cn, L2, fasg);
+    DD_TRY(near.assign_fine(ds->z32, perm1, c1s, N, a.cent, a.cn, a.cent1, L1, L2, fasg, s));
+    a.build_fallback = near.fallback;
+    near.release();
+    ctx->launches++;
     k_leaf_of<<<gN, 256, 0, s>>>(perm1, c1s, fasg, N, L2, a.cluster_of);
     // ---- leaf order, radii ----
     DD_TRY_CUDA(ctx, cudaMemsetAsync(cnt, 0, b_cnt, s));
@@ -1711,7 +1909,7 @@ static dd_status build_tree2(dd_dataset *ds, const dd_dataset_opts &o) {
         a.lrad1 = (float *)p;
         DD_TRY_CUDA(ctx, cudaMemcpy(a.lrad1, lr.data(), L1p * 4, cudaMemcpyHostToDevice));
     }
-    return DD_OK;
+    return build_rank_operands(ds, o);
 }
 
 static bool rank_small(const AnnIndex &a) { return (a.levels == 2 ? a.L1 : a.nlist) <= kRankMax; }
@@ -1727,7 +1925,19 @@ static dd_status ann_rank_listed(dd_dataset *ds, const QueryRec *rec, int64_t m,
     const float *rank_cent = two ? a.cent1 : a.cent;
     const float *rank_cn = two ? a.cn1 : a.cn;
     const int Lr = two ? a.L1 : a.nlist;
-    if (Lr <= kRankMax) {
+    if (Lr <= kRankMax && a.rank_tc.hi) {
+        // tensor cores; the queries their scores leave open go to the ALU kernel
+        const size_t b_fb = ((size_t)m * 4 + 255) / 256 * 256;
+        void *w = nullptr;
+        DD_TRY(dd_workspace(ctx, WS_NEAR, b_fb + 256, &w));
+        int32_t *fb = (int32_t *)w;
+        unsigned *fb_n = (unsigned *)((char *)w + b_fb);
+        DD_TRY_CUDA(ctx, cudaMemsetAsync(fb_n, 0, 4, s));
+        DD_TRY(dd_near_tc_rank(ctx, a.rank_tc, rec, m, list, n_list, cand_cl, cand_d, fb, fb_n, s));
+        ctx->launches++;
+        k_rank_small<<<(unsigned)((m + 256 * kRankQ - 1) / (256 * kRankQ)), 256, 0, s>>>(
+            rec, m, fb, fb_n, rank_cent, rank_cn, Lr, cand_cl, cand_d);
+    } else if (Lr <= kRankMax) {
         ctx->launches++;
         k_rank_small<<<(unsigned)((m + 256 * kRankQ - 1) / (256 * kRankQ)), 256, 0, s>>>(
             rec, m, list, n_list, rank_cent, rank_cn, Lr, cand_cl, cand_d);

@@ -93,7 +93,7 @@ struct dd_ctx {
     std::string err;
     unsigned *dev_err = nullptr;        // device error word
     // grow-only scratch buffers keyed by purpose
-    Workspace ws[12];
+    Workspace ws[13];
     int64_t launches = 0;               // kernels launched (instrumentation)
     int tc_epi[3] = {0, 0, 0};          // tuned tensor-core scan variants (uncertified, certified nearest, certified k nearest)
     std::map<int64_t, int> fp32_splits; // tuned data splits of the FP32 scan, per query-tile count
@@ -117,7 +117,7 @@ void dd_plans_drop(dd_ctx *ctx, uint64_t id);
 
 enum WsSlot {
     WS_SEARCH = 0, WS_QUERY = 1, WS_MISC = 2, WS_SOLVE = 3, WS_TC = 4, WS_ANN = 5, WS_ANN_SCAN = 6, WS_ANN_BUILD = 7,
-    WS_BATCH = 8, WS_BATCH_CG = 9, WS_ANN_PAIRS = 10, WS_SUBSET = 11
+    WS_BATCH = 8, WS_BATCH_CG = 9, WS_ANN_PAIRS = 10, WS_SUBSET = 11, WS_NEAR = 12
 };
 
 // Coarse cells a tree search ranks per query (ann.cu).
@@ -130,6 +130,23 @@ struct KnnGraph {
     float fd = 0.f;
     int32_t *nbr = nullptr;     // [N x k] neighbour positions, nearest first (-1: none)
     int32_t *pos_of = nullptr;  // [N] sorted position of every original point
+};
+
+// Tensor-core operands of a centroid set (near_tc.cu).
+struct NearTcSet {
+    __half *hi = nullptr, *lo = nullptr;   // split FP16 operand tiles [rows_pad x 16] each
+    int64_t rows_pad = 0;
+    const float *cent = nullptr;           // FP32 centroids [L x 12] and |c|^2 [L]
+    const float *cn = nullptr;
+    int64_t L = 0;
+    int per_group = 0;                     // centroids per group (the whole set, or the leaves of a cell)
+    double s = 0.0;                        // operand scale
+    float R = 0.f;                         // bound on |c|
+    // groups with their own origin (the leaves of a cell about the cell's
+    // centroid): per group 12 origin coordinates, the operand scale and the
+    // bound on |c - origin| ([G x 16] floats); null: one origin and scale
+    float *gmeta = nullptr;
+    int64_t groups = 0;
 };
 
 struct AnnIndex {
@@ -152,6 +169,10 @@ struct AnnIndex {
     float *rad1 = nullptr;      // [L1p]
     float r1max = 0.f;
     float *lrad1 = nullptr;     // [L1p] largest leaf radius of every cell
+    // tensor-core operands of the ranked centroid set (cells, or the clusters
+    // of one level); hi null: the ranking runs on the ALU only
+    NearTcSet rank_tc;
+    int64_t build_fallback = 0; // build rows the tensor-core passes left to the ALU
 };
 
 // Moving-query record of the approximate search (Eq. 14), per query:
@@ -245,6 +266,42 @@ dd_status dd_search_exact_fp32(dd_dataset *ds, const double *y_dev, int64_t m, i
 dd_status dd_search_exact_tc(dd_dataset *ds, const double *y_dev, int64_t m, int certify,
                              SearchOut out, dd_search_stats *st, cudaStream_t s, int terms = 0);
 dd_status dd_build_fp16(dd_dataset *ds);
+// Power-of-two operand scale of the tensor-core kernels (max |s z| <= 32 for
+// coordinates bounded by maxabs).
+double dd_tc_scale(double maxabs);
+// Split FP16 operand tiles (UMMA canonical layout, 128 rows per 4 KB tile) of
+// the n rows z [n x 12]: hi row (-2 x_hi, |x_hi|^2 in two terms, 0, 0), lo row
+// (-2 x_lo, |x_hi + x_lo|^2 - |x_hi|^2 in two terms, 0, 0), x = s z; rows n ..
+// n_pad - 1 are padding.  hi and lo hold n_pad x 16 halves each.
+dd_status dd_tc_split_rows(dd_ctx *ctx, const float *z, int64_t n, int64_t n_pad, double s, __half *hi, __half *lo,
+                           cudaStream_t st);
+
+// Nearest centroids on the tensor cores (near_tc.cu), answers equal to the ALU
+// kernels of ann.cu; rows that the tensor-core scores cannot settle are
+// appended to fb (count fb_n, zeroed by the caller; at most fb_cap entries
+// are written, the count keeps counting) for the ALU kernel.
+dd_status dd_near_tc_operands(dd_ctx *ctx, const float *cent, const float *cn, int64_t L, int per_group, double s,
+                              float R, NearTcSet *C, cudaStream_t st);
+void dd_near_tc_free(dd_ctx *ctx, NearTcSet *C);
+// kAnnCand nearest cells of the listed queries (list/n_list on the device;
+// both null: queries 0..m-1), as k_rank_small writes them; fb holds m entries.
+dd_status dd_near_tc_rank(dd_ctx *ctx, const NearTcSet &C, const QueryRec *rec, int64_t m, const int32_t *list,
+                          const unsigned *n_list, int32_t *out_cl, float *out_d, int32_t *fb, unsigned *fb_n,
+                          cudaStream_t s);
+// Nearest centroid of every row of z [n x 12] (ties to the lower index).
+dd_status dd_near_tc_assign(dd_ctx *ctx, const NearTcSet &C, const float *z, int64_t n, int32_t *out, int32_t *fb,
+                            unsigned *fb_n, int64_t fb_cap, cudaStream_t s);
+// Operands of G groups of per_group centroids each (centroid g * per_group + f
+// in group g), every group about its own origin origins[g] with its own
+// power-of-two scale, so that the tensor-core error follows the group's
+// extent, not the data set's.
+dd_status dd_near_tc_operands_grouped(dd_ctx *ctx, const float *cent, const float *cn, int64_t G, int per_group,
+                                      const float *origins, float R, NearTcSet *C, cudaStream_t st);
+// Nearest of the per_group centroids of group grp[p] for the rows z[perm[p]],
+// p = 0..n-1 in group order (the leaf within its cell).
+dd_status dd_near_tc_assign_grouped(dd_ctx *ctx, const NearTcSet &C, const float *z, const int32_t *perm,
+                                    const int32_t *grp, int64_t n, int32_t *out, int32_t *fb, unsigned *fb_n,
+                                    int64_t fb_cap, cudaStream_t s);
 dd_status dd_search_ann(dd_dataset *ds, const double *y_dev, int64_t m, double f_d,
                         const int32_t *prev_idx_dev, int budget, SearchOut out, dd_search_stats *st,
                         cudaStream_t s);
@@ -357,6 +414,28 @@ __device__ __forceinline__ bool dd_mbar_wait(uint32_t bar, uint32_t parity) {
             else if (t - t0 > kWaitLimitNs) return false;
         }
     }
+}
+
+// Plain FP32 squared distance of a 12-float row (16-byte aligned) to q, in
+// coordinate order: the arithmetic every FP32 distance of the tree search
+// uses, so that kernels sharing it agree bit for bit.
+__device__ __forceinline__ float dd_dist2_12(const float *a, const float (&q)[12]) {
+    const float4 *p = reinterpret_cast<const float4 *>(a);
+    const float4 u = __ldg(p), v = __ldg(p + 1), w = __ldg(p + 2);
+    float d, s = 0.f;
+    d = u.x - q[0]; s = fmaf(d, d, s);
+    d = u.y - q[1]; s = fmaf(d, d, s);
+    d = u.z - q[2]; s = fmaf(d, d, s);
+    d = u.w - q[3]; s = fmaf(d, d, s);
+    d = v.x - q[4]; s = fmaf(d, d, s);
+    d = v.y - q[5]; s = fmaf(d, d, s);
+    d = v.z - q[6]; s = fmaf(d, d, s);
+    d = v.w - q[7]; s = fmaf(d, d, s);
+    d = w.x - q[8]; s = fmaf(d, d, s);
+    d = w.y - q[9]; s = fmaf(d, d, s);
+    d = w.z - q[10]; s = fmaf(d, d, s);
+    d = w.w - q[11]; s = fmaf(d, d, s);
+    return s;
 }
 
 __device__ __forceinline__ uint32_t dd_smem_addr(const void *p) {

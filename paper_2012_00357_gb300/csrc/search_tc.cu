@@ -43,8 +43,11 @@
 #include <cmath>
 
 #include "dd_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace {
+
+using namespace dd_tc;
 
 constexpr int kTN = 128;            // data points per tile (MMA N)
 constexpr int kTM = 128;            // queries per CTA (MMA M)
@@ -54,95 +57,9 @@ constexpr int kCap = 8;
 // warps share a TMEM lane quarter and take half of the tile's columns each
 template <int EPI>
 constexpr int tc_threads() { return 64 + 32 * EPI; }
-constexpr uint32_t kTileBytes = 4096;   // 128 rows x 16 fp16
 constexpr uint32_t kTmemCols = 256;
 
-// ---- PTX wrappers --------------------------------------------------------
-__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);          // start address
-    d |= (uint64_t)(128u >> 4) << 16;                  // LBO: next core matrix along K
-    d |= (uint64_t)(256u >> 4) << 32;                  // SBO: next 8-row group
-    d |= (uint64_t)1 << 46;                            // descriptor version
-    return d;                                          // base offset 0, no swizzle
-}
-
-__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
-    return (1u << 4)                       // D format F32
-           | (0u << 7) | (0u << 10)        // A, B format F16
-           | ((uint32_t)(N >> 3) << 17)    // N
-           | ((uint32_t)(M >> 4) << 24);   // M
-}
-
-__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-}
-
-__device__ __forceinline__ void umma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// Issue a 32-column TMEM load without waiting for it.  Its registers may be
-// used only after tmem_wait on the same array, which names them as read-write
-// operands so that no use is moved above the wait.
-__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%"
-        "28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr)
-        : "memory");
-}
-
-__device__ __forceinline__ void tmem_wait(uint32_t (&r)[32]) {
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
-                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
-                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
-                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
-                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
-                 :
-                 : "memory");
-}
-
-// The same load with the minimum of the 32 values (Blackwell Ultra's reducing
-// TMEM load): the reduction is done by the load path, not by ALU
-// instructions.  `red` may be read only after tmem_wait_red.
-__device__ __forceinline__ void tmem_ld32_red_async(uint32_t taddr, uint32_t (&r)[32], float &red) {
-    asm volatile(
-        "tcgen05.ld.red.sync.aligned.32x32b.x32.min.f32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%"
-        "28,%29,%30,%31}, %32, [%33];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
-          "=f"(red)
-        : "r"(taddr)
-        : "memory");
-}
-
-__device__ __forceinline__ void tmem_wait_red(uint32_t (&r)[32], float &red) {
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
-                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
-                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
-                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
-                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31]), "+f"(red)
-                 :
-                 : "memory");
-}
+// ---- PTX wrappers (the shared ones are in tc_ptx.cuh) ----------------------
 
 // One reducing TMEM load of 128 columns (a thread's whole row of the tile)
 // and its minimum; the registers and `red` may be used only after
@@ -215,11 +132,6 @@ __device__ __forceinline__ float min32(const float (&v)[32]) {
     float b0 = min3f(a[0], a[1], a[2]), b1 = min3f(a[3], a[4], a[5]), b2 = min3f(a[6], a[7], a[8]);
     float b3 = fminf(a[9], a[10]);
     return fminf(min3f(b0, b1, b2), b3);
-}
-
-// Offset of (row, k) inside a tile in the canonical layout (bytes).
-__host__ __device__ __forceinline__ uint32_t canon_off(int row, int k) {
-    return (uint32_t)((row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 
 // ---- data operands ---------------------------------------------------------
@@ -623,12 +535,25 @@ int pick_splits_tc(int64_t qtiles, int64_t n_tiles, int n_sm) {
 
 }  // namespace
 
+double dd_tc_scale(double maxabs) {
+    // power-of-two scale with max |s z| <= 32
+    const double mx = maxabs > 0 ? maxabs : 1.0;
+    return std::ldexp(1.0, (int)std::floor(std::log2(32.0 / mx)));
+}
+
+dd_status dd_tc_split_rows(dd_ctx *ctx, const float *z, int64_t n, int64_t n_pad, double s, __half *hi, __half *lo,
+                           cudaStream_t st) {
+    if (n_pad % kTN != 0 || n_pad < n) return dd_fail(ctx, DD_ERR_STATE, "split operands: padding is not whole tiles");
+    ctx->launches++;
+    k_build_fp16<<<(unsigned)((n_pad + 255) / 256), 256, 0, st>>>(z, n, n_pad, (float)s, hi, lo);
+    DD_TRY_CUDA(ctx, cudaGetLastError());
+    return DD_OK;
+}
+
 dd_status dd_build_fp16(dd_dataset *ds) {
     dd_ctx *ctx = ds->ctx;
     if (ds->z16hi) return DD_OK;
-    // power-of-two scale with max |s z| <= 32
-    double mx = ds->maxabs > 0 ? ds->maxabs : 1.0;
-    ds->scale16 = std::ldexp(1.0, (int)std::floor(std::log2(32.0 / mx)));
+    ds->scale16 = dd_tc_scale(ds->maxabs);
     void *p = nullptr;
     DD_TRY(dd_alloc(ctx, &p, (size_t)ds->N_pad * 32, "fp16 operands"));
     ds->z16hi = (__half *)p;

@@ -73,14 +73,14 @@ def exact_solve(big):
 
 def test_ann_solve_within_1e3_of_exact_full_size(big, exact_solve):
     """The DD solution driven by the approximate search (tree, f_d from 0.3
-    to 0.7 over 5 iterations, the benchmark schedule) ends at most 1e-3 relative above, in global
+    to 0.8 over 5 iterations, the benchmark schedule) ends at most 1e-3 relative above, in global
     distance (Eq. 2) of the solution driven by the certified exact search, on
     the 32^3 cube with the 10^8-point data set, from the same initial
     association."""
     ctx, ds, y, sample, oi, od = big
     L = I.load_case("tension", 1e-3)
     exact = exact_solve
-    ann = P.dd_solve(ds, ctx, W.n_el, L, mode=P.DD_SEARCH_ANN, f_d0=0.3, f_d_final=0.7, ramp_iters=5,
+    ann = P.dd_solve(ds, ctx, W.n_el, L, mode=P.DD_SEARCH_ANN, f_d0=0.3, f_d_final=0.8, ramp_iters=5,
                      seed=W.seed, max_iter=60)
     de, da = float(exact.d2_pd[-1]), float(ann.d2_pd[-1])
     print(f"exact: {exact.iters} iterations, d2 {de:.6e}; approximate: {ann.iters} iterations, d2 {da:.6e}, "
