@@ -729,37 +729,6 @@ __global__ void __launch_bounds__(256) k_assign_fine(const float *__restrict__ z
     if (act) fasg[p] = bi;
 }
 
-// k_assign_fine for the sorted positions list[0 .. *n_list - 1] only: the
-// same score of each of the cell's leaves, in leaf order.
-__global__ void k_assign_fine_listed(const float *__restrict__ z, const int32_t *__restrict__ perm1,
-                                     const int32_t *__restrict__ c1s, const int32_t *__restrict__ list,
-                                     const unsigned *__restrict__ n_list, const float *__restrict__ centf,
-                                     const float *__restrict__ cnf, int L2, int32_t *__restrict__ fasg) {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= (int64_t)*n_list) return;
-    const int64_t p = list[t];
-    const int c = c1s[p];
-    const float *zp = z + (size_t)perm1[p] * 12;
-    float q[12];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) q[k] = -2.f * zp[k];
-    float best = INFINITY;
-    int bi = 0;
-    for (int f = 0; f < L2; ++f) {
-        const float4 *pc = reinterpret_cast<const float4 *>(centf + ((size_t)c * L2 + f) * 12);
-        const float4 a = __ldg(pc), b = __ldg(pc + 1), d = __ldg(pc + 2);
-        float v = __ldg(cnf + (size_t)c * L2 + f);
-        v = fmaf(q[0], a.x, v); v = fmaf(q[1], a.y, v); v = fmaf(q[2], a.z, v); v = fmaf(q[3], a.w, v);
-        v = fmaf(q[4], b.x, v); v = fmaf(q[5], b.y, v); v = fmaf(q[6], b.z, v); v = fmaf(q[7], b.w, v);
-        v = fmaf(q[8], d.x, v); v = fmaf(q[9], d.y, v); v = fmaf(q[10], d.z, v); v = fmaf(q[11], d.w, v);
-        if (v < best) {
-            best = v;
-            bi = f;
-        }
-    }
-    fasg[p] = bi;
-}
-
 __global__ void k_accum_fine(const float *__restrict__ z, const int32_t *__restrict__ perm1,
                              const int32_t *__restrict__ c1s, const int32_t *__restrict__ fasg, int64_t n, int L2,
                              double fs, unsigned long long *__restrict__ sums, unsigned *__restrict__ cnt) {
@@ -1527,10 +1496,10 @@ void dd_free_ann(dd_dataset *ds) {
 
 static dd_status build_tree2(dd_dataset *ds, const dd_dataset_opts &o);
 
-// The nearest-centroid passes of a build: on the tensor cores (near_tc.cu,
-// the same answers) unless the options ask for the ALU, the centroid set is
-// too small, or the groups are not whole 128-leaf tiles; the rows that the
-// tensor-core scores leave open are finished by the ALU kernel.
+// The nearest-centroid passes of a build.  The assignment to the cells runs
+// on the tensor cores (near_tc.cu, the same answers) unless the options ask
+// for the ALU or the cells are a handful; the rows that the tensor-core
+// scores leave open are finished by the ALU kernel.
 struct BuildNear {
     dd_ctx *ctx = nullptr;
     bool tc = false;
@@ -1581,7 +1550,7 @@ struct BuildNear {
             DD_TRY_CUDA(ctx, cudaGetLastError());
             return DD_OK;
         }
-        DD_TRY(dd_near_tc_operands(ctx, cent, cn, L, L, s, R, &C, st));
+        DD_TRY(dd_near_tc_operands(ctx, cent, cn, L, s, R, &C, st));
         DD_TRY_CUDA(ctx, cudaMemsetAsync(fb_n, 0, 4, st));
         DD_TRY(dd_near_tc_assign(ctx, C, z, n, out, fb, fb_n, cap, st));
         int64_t nf = 0;
@@ -1593,28 +1562,13 @@ struct BuildNear {
         DD_TRY_CUDA(ctx, cudaGetLastError());
         return DD_OK;
     }
-    // fasg[p] = nearest of the L2 leaves of cell c1s[p] to z[perm1[p]]; the
-    // tensor-core operands of a cell's leaves are taken about the cell's
-    // centroid (cent1)
+    // fasg[p] = nearest of the L2 leaves of cell c1s[p] to z[perm1[p]] (on
+    // the ALU: with four centroid tiles per 128 points the tensor-core
+    // kernel was slower, 0.6 s per pass at 10^9 points against 0.38 s)
     dd_status assign_fine(const float *z, const int32_t *perm1, const int32_t *c1s, int64_t n, const float *cent,
-                          const float *cn, const float *cent1, int L1, int L2, int32_t *fasg, cudaStream_t st) {
-        const unsigned g = (unsigned)((n + 255) / 256);
-        if (!tc || L2 % 128 != 0) {
-            ctx->launches++;
-            k_assign_fine<<<g, 256, 0, st>>>(z, perm1, c1s, n, cent, cn, L2, fasg);
-            DD_TRY_CUDA(ctx, cudaGetLastError());
-            return DD_OK;
-        }
-        DD_TRY(dd_near_tc_operands_grouped(ctx, cent, cn, L1, L2, cent1, R, &C, st));
-        DD_TRY_CUDA(ctx, cudaMemsetAsync(fb_n, 0, 4, st));
-        DD_TRY(dd_near_tc_assign_grouped(ctx, C, z, perm1, c1s, n, fasg, fb, fb_n, cap, st));
-        int64_t nf = 0;
-        DD_TRY(open_rows(st, &nf));
-        if (nf == 0) return DD_OK;
+                          const float *cn, int L2, int32_t *fasg, cudaStream_t st) {
         ctx->launches++;
-        if (nf > cap) k_assign_fine<<<g, 256, 0, st>>>(z, perm1, c1s, n, cent, cn, L2, fasg);
-        else k_assign_fine_listed<<<(unsigned)((nf + 255) / 256), 256, 0, st>>>(z, perm1, c1s, fb, fb_n, cent, cn,
-                                                                                 L2, fasg);
+        k_assign_fine<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(z, perm1, c1s, n, cent, cn, L2, fasg);
         DD_TRY_CUDA(ctx, cudaGetLastError());
         return DD_OK;
     }
@@ -1627,7 +1581,7 @@ static dd_status build_rank_operands(dd_dataset *ds, const dd_dataset_opts &o) {
     const bool two = a.levels == 2;
     const int Lr = two ? a.L1 : a.nlist;
     if (o.ann_alu || Lr < 16 || Lr > kRankMax) return DD_OK;
-    DD_TRY(dd_near_tc_operands(ds->ctx, two ? a.cent1 : a.cent, two ? a.cn1 : a.cn, Lr, Lr, dd_tc_scale(ds->maxabs),
+    DD_TRY(dd_near_tc_operands(ds->ctx, two ? a.cent1 : a.cent, two ? a.cn1 : a.cn, Lr, dd_tc_scale(ds->maxabs),
                                (float)(ds->R * (1.0 + 1e-6)), &a.rank_tc, ds->ctx->stream));
     ds->bytes += (size_t)a.rank_tc.rows_pad * 64;
     return DD_OK;
@@ -1853,7 +1807,7 @@ static dd_status build_tree2(dd_dataset *ds, const dd_dataset_opts &o) {
         DD_TRY_CUDA(ctx, cudaFuncSetAttribute(k_accum_fine_run, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)accum_smem));
     for (int it = 0; it < iters; ++it) {
-        DD_TRY(near.assign_fine(ds->z32, perm1, c1s, N, a.cent, a.cn, a.cent1, L1, L2, fasg, s));
+        DD_TRY(near.assign_fine(ds->z32, perm1, c1s, N, a.cent, a.cn, L2, fasg, s));
         ctx->launches += 2;
         if (near.tc && accum_smem <= 160 * 1024)
             k_accum_fine_run<<<(unsigned)((N + kAccumRun - 1) / kAccumRun), kAccumThreads, accum_smem, s>>>(
@@ -1862,7 +1816,7 @@ static dd_status build_tree2(dd_dataset *ds, const dd_dataset_opts &o) {
             k_accum_fine<<<gN, 256, 0, s>>>(ds->z32, perm1, c1s, fasg, N, L2, fs, sums, cnt);
         k_update<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(sums, cnt, fs, a.cent, a.cn, L);
     }
-    DD_TRY(near.assign_fine(ds->z32, perm1, c1s, N, a.cent, a.cn, a.cent1, L1, L2, fasg, s));
+    DD_TRY(near.assign_fine(ds->z32, perm1, c1s, N, a.cent, a.cn, L2, fasg, s));
     a.build_fallback = near.fallback;
     near.release();
     ctx->launches++;

@@ -139,14 +139,8 @@ struct NearTcSet {
     const float *cent = nullptr;           // FP32 centroids [L x 12] and |c|^2 [L]
     const float *cn = nullptr;
     int64_t L = 0;
-    int per_group = 0;                     // centroids per group (the whole set, or the leaves of a cell)
     double s = 0.0;                        // operand scale
     float R = 0.f;                         // bound on |c|
-    // groups with their own origin (the leaves of a cell about the cell's
-    // centroid): per group 12 origin coordinates, the operand scale and the
-    // bound on |c - origin| ([G x 16] floats); null: one origin and scale
-    float *gmeta = nullptr;
-    int64_t groups = 0;
 };
 
 struct AnnIndex {
@@ -280,8 +274,8 @@ dd_status dd_tc_split_rows(dd_ctx *ctx, const float *z, int64_t n, int64_t n_pad
 // kernels of ann.cu; rows that the tensor-core scores cannot settle are
 // appended to fb (count fb_n, zeroed by the caller; at most fb_cap entries
 // are written, the count keeps counting) for the ALU kernel.
-dd_status dd_near_tc_operands(dd_ctx *ctx, const float *cent, const float *cn, int64_t L, int per_group, double s,
-                              float R, NearTcSet *C, cudaStream_t st);
+dd_status dd_near_tc_operands(dd_ctx *ctx, const float *cent, const float *cn, int64_t L, double s, float R,
+                              NearTcSet *C, cudaStream_t st);
 void dd_near_tc_free(dd_ctx *ctx, NearTcSet *C);
 // kAnnCand nearest cells of the listed queries (list/n_list on the device;
 // both null: queries 0..m-1), as k_rank_small writes them; fb holds m entries.
@@ -291,17 +285,6 @@ dd_status dd_near_tc_rank(dd_ctx *ctx, const NearTcSet &C, const QueryRec *rec, 
 // Nearest centroid of every row of z [n x 12] (ties to the lower index).
 dd_status dd_near_tc_assign(dd_ctx *ctx, const NearTcSet &C, const float *z, int64_t n, int32_t *out, int32_t *fb,
                             unsigned *fb_n, int64_t fb_cap, cudaStream_t s);
-// Operands of G groups of per_group centroids each (centroid g * per_group + f
-// in group g), every group about its own origin origins[g] with its own
-// power-of-two scale, so that the tensor-core error follows the group's
-// extent, not the data set's.
-dd_status dd_near_tc_operands_grouped(dd_ctx *ctx, const float *cent, const float *cn, int64_t G, int per_group,
-                                      const float *origins, float R, NearTcSet *C, cudaStream_t st);
-// Nearest of the per_group centroids of group grp[p] for the rows z[perm[p]],
-// p = 0..n-1 in group order (the leaf within its cell).
-dd_status dd_near_tc_assign_grouped(dd_ctx *ctx, const NearTcSet &C, const float *z, const int32_t *perm,
-                                    const int32_t *grp, int64_t n, int32_t *out, int32_t *fb, unsigned *fb_n,
-                                    int64_t fb_cap, cudaStream_t s);
 dd_status dd_search_ann(dd_dataset *ds, const double *y_dev, int64_t m, double f_d,
                         const int32_t *prev_idx_dev, int budget, SearchOut out, dd_search_stats *st,
                         cudaStream_t s);
@@ -408,7 +391,9 @@ __device__ __forceinline__ bool dd_mbar_wait(uint32_t bar, uint32_t parity) {
             : "r"(bar), "r"(parity)
             : "memory");
         if (done) return true;
-        if ((spin & 63) == 0) {
+        // the clock is read only once a wait has lasted (the fast path of a
+        // pipeline wait does not pay for it), then every 64 tries
+        if (spin >= 256 && (spin & 63) == 0) {
             unsigned long long t = dd_globaltimer();
             if (t0 == 0) t0 = t;
             else if (t - t0 > kWaitLimitNs) return false;

@@ -1,14 +1,12 @@
 // Nearest centroids on the tensor cores, with exactly the answers of the ALU
 // kernels they replace.
 //
-// Three places of the approximate search rank centroids by the expanded FP32
+// Two places of the approximate search rank centroids by the expanded FP32
 // score v(c) = |c|^2 - 2 c.q (the nearest centroid is the one of least v):
 //  * the cell ranking of every listed query (Sec. 4.2: the kCand = 8 nearest
-//    cells, then ordered by distance; ann.cu k_rank_small),
+//    cells, then ordered by distance; ann.cu k_rank_small), and
 //  * the k-means assignment of the tree build to the nearest cell
-//    (ann.cu k_assign), and
-//  * the assignment of every point to the nearest leaf of its own cell
-//    (ann.cu k_assign_fine).
+//    (ann.cu k_assign).
 // Each is a (rows x centroids) contraction of width 12.  Here it runs as split
 // FP16 MMAs (tcgen05, FP32 accumulators in TMEM; three products per score as
 // in the certified exact scan of search_tc.cu), an epilogue keeps, per row,
@@ -34,15 +32,22 @@
 // scan: 2^-15 B^2 + 2^-18 with B = s (R + |q|), R bounding |c|) plus the FP32
 // score's own rounding, at most 2^-19 (R^2 + 2 R |q|) s^2.
 //
-// Pipeline per CTA (128 rows): all threads build the row operands in shared
-// memory (A0 = (q_hi, 1, 1), A1 = (q_lo), A2 = A0); warp 0 streams the
-// centroid operand tiles (hi and lo, 4 KB each) into a ring of stages with
-// 1-D bulk copies; warp 1 allocates TMEM and issues the three MMAs of every
-// 128-centroid tile into one of two accumulators; warps 2..5 take one row
-// each per thread: a min-reducing 32-column TMEM load per chunk, and only
-// chunks whose minimum is within the window are walked.  Every mbarrier wait
-// is bounded; on a timeout the kernel flags the error, stops issuing work,
-// drains what is in flight and frees TMEM.
+// The assignment of points to the leaves of their own cell (ann.cu
+// k_assign_fine: 512 leaves per cell) stays on the ALU: with its four
+// centroid tiles per 128 points this kernel measured 0.6 s per pass at 10^9
+// points against 0.38 s for the ALU kernel (tensor pipe 3 % busy; the time
+// goes to the per-tile hand-offs).
+//
+// Persistent CTAs (two per SM), each taking every grid-th tile of 128 rows.
+// Warp 0 streams the centroid operand tiles (hi and lo, 4 KB each) into a
+// ring of stages with 1-D bulk copies; warp 1 allocates TMEM and issues the
+// three MMAs of every 128-centroid tile into one of two accumulators; warps
+// 2..5 take one row each per thread: they write the rows' operands into one
+// of two A buffers (A0 = (q_hi, 1, 1), A1 = (q_lo), A2 = A0; the next row
+// tile's while the current one runs), and per accumulator a min-reducing
+// 32-column TMEM load per chunk, walking only chunks whose minimum is within
+// the window.  Every mbarrier wait is bounded; on a timeout the kernel flags
+// the error, stops issuing work, drains what is in flight and frees TMEM.
 #include <algorithm>
 #include <cmath>
 
@@ -61,8 +66,7 @@ constexpr uint32_t kStageBytes = 2 * kTileBytes;
 constexpr uint32_t kTmemCols = 256;
 
 // MODE 0: cell ranking of listed queries (K = kAnnCand nearest by v, then
-// ordered by distance); MODE 1: nearest centroid of every row; MODE 2:
-// nearest leaf of the row's own cell (rows in cell order).
+// ordered by distance); MODE 1: nearest centroid of every row.
 template <int MODE>
 struct NearCfg {
     static constexpr int K = MODE == 0 ? kAnnCand : 1;
@@ -70,21 +74,18 @@ struct NearCfg {
 };
 
 struct NearArgs {
-    const float *z;            // MODE 1, 2: point coordinates [.. x 12]
+    const float *z;            // MODE 1: point coordinates [.. x 12]
     const QueryRec *rec;       // MODE 0: query records
     const int32_t *list;       // MODE 0: listed queries (null: 0..n-1)
     const unsigned *n_list;    // MODE 0: device count of `list` (null: n)
-    const int32_t *perm;       // MODE 2: point of every sorted position
-    const int32_t *grp;        // MODE 2: cell of every sorted position
     int64_t n;                 // rows (MODE 0: the capacity of the list)
     const __half *chi, *clo;   // split FP16 centroid operand tiles
     const float *cent, *cn;    // FP32 centroids [.. x 12] and |c|^2: the ALU kernels' operands
-    int Lc;                    // centroids per group (MODE 2: leaves per cell)
-    int tpg;                   // operand tiles per group
+    int Lc;                    // centroids
+    int tpg;                   // their operand tiles
     float s;                   // operand scale (a power of two)
     float R;                   // bound on |c|
-    const float *gmeta;        // MODE 2: per group origin[12], scale, bound on |c - origin| (null: global)
-    int32_t *out;              // MODE 1: nearest centroid; MODE 2: nearest leaf of the row's cell
+    int32_t *out;              // MODE 1: nearest centroid
     int32_t *out_cl;           // MODE 0: [m x K] cells, nearest first
     float *out_d;              // MODE 0: [m x K] their FP32 distances
     int32_t *fb;               // rows (MODE 0: queries) left to the ALU kernel
@@ -110,75 +111,57 @@ __device__ __forceinline__ float alu_score(const float *__restrict__ cent, const
     return v;
 }
 
-// Row tile `rt` of the kernel: its first row, rows, and (MODE 2) the groups
-// of its rows, whose operand tiles it streams: g0 * tpg .. (g1 + 1) * tpg - 1.
-struct RowTile {
-    int64_t r0;
-    int g0, ntl;
+// Operands of one row (this thread's row of a row tile), fetched in two
+// steps so that the loads of the next row tile overlap the current one's
+// epilogue: the row's index, then its coordinates.
+struct RowSrc {
+    int64_t idx;     // MODE 0: query; MODE 1: row (-1: no row)
+    float q[12];
 };
 
 template <int MODE>
-__device__ __forceinline__ RowTile row_tile(const NearArgs &P, int64_t nrows, int64_t rt) {
-    RowTile T;
-    T.r0 = rt * kRows;
-    T.g0 = MODE == 2 ? P.grp[T.r0] : 0;
-    const int g1 = MODE == 2 ? P.grp[min(nrows, T.r0 + kRows) - 1] : 0;
-    T.ntl = (g1 - T.g0 + 1) * P.tpg;
-    return T;
+__device__ __forceinline__ void fetch_index(const NearArgs &P, int64_t nrows, int64_t r, RowSrc &S) {
+    S.idx = r < nrows ? (MODE == 0 && P.list ? (int64_t)P.list[r] : r) : -1;
 }
 
-// Operands of one row (this thread's row of row tile T) into A buffer sA
-// (A0 = (q_hi, 1, 1), A1 = (q_lo), A2 = A0 at `row`), its FP32 coordinates
-// into sQ and its window into sW.
 template <int MODE>
-__device__ __forceinline__ void build_row(const NearArgs &P, int64_t nrows, int64_t r0, int row, unsigned char *sA,
-                                          float *sQ, float *sW) {
-    const int64_t r = r0 + row;
-    float q[12];
-    float sg = P.s, Rg = P.R;       // operand scale and centroid bound of this row's group
-    const float *og = nullptr;      // the group's origin (null: the data set's)
-    if (r < nrows) {
-        const float *src;
-        if (MODE == 0) src = P.rec[P.list ? (int64_t)P.list[r] : r].q;
-        else if (MODE == 1) src = P.z + r * 12;
-        else src = P.z + (int64_t)P.perm[r] * 12;
+__device__ __forceinline__ void fetch_coords(const NearArgs &P, RowSrc &S) {
+    if (S.idx < 0) {
 #pragma unroll
-        for (int k = 0; k < 12; ++k) q[k] = src[k];
-        if (MODE == 2 && P.gmeta) {
-            og = P.gmeta + (size_t)P.grp[r] * 16;
-            sg = og[12];
-            Rg = og[13];
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < 12; ++k) q[k] = 0.f;
+        for (int k = 0; k < 12; ++k) S.q[k] = 0.f;
+        return;
     }
+    const float *src = MODE == 0 ? P.rec[S.idx].q : P.z + S.idx * 12;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) S.q[k] = src[k];
+}
+
+// The row's operands into A buffer sA (A0 = (q_hi, 1, 1), A1 = (q_lo),
+// A2 = A0 at `row`), its FP32 coordinates into sQ and its window into sW.
+__device__ __forceinline__ void build_row(const RowSrc &S, float sc, float R, int row, unsigned char *sA, float *sQ,
+                                          float *sW) {
     __half h[16], l[16];
-    float qn = 0.f, qg = 0.f;      // |q|^2, |q - origin|^2
+    float qn = 0.f;      // |q|^2
     bool in_range = true;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-        const float u = og ? q[k] - og[k] : q[k];
-        const float x = u * sg;   // exact: the scale is a power of two
+        const float x = S.q[k] * sc;   // exact: the scale is a power of two
         in_range &= fabsf(x) < 30000.f;
-        qn = fmaf(q[k], q[k], qn);
-        qg = fmaf(u, u, qg);
+        qn = fmaf(S.q[k], S.q[k], qn);
         h[k] = __float2half_rn(x);
         l[k] = __float2half_rn(x - __half2float(h[k]));   // the difference is exact in FP32
-        sQ[row * 12 + k] = q[k];
+        sQ[row * 12 + k] = S.q[k];
     }
     h[12] = h[13] = __float2half_rn(in_range ? 1.f : 0.f);
     h[14] = h[15] = l[12] = l[13] = l[14] = l[15] = __float2half_rn(0.f);
     if (!in_range)
 #pragma unroll
         for (int k = 0; k < 12; ++k) h[k] = l[k] = __float2half_rn(0.f);
-    // tensor-core error with the group's origin and scale; the FP32 score's
-    // own rounding is that of the global coordinates (norms rounded up by a
-    // relative 1e-5 for their FP32 evaluation)
-    const float qa = sqrtf(qn) * 1.00001f, qb = sqrtf(qg) * 1.00001f;
-    const float B = sg * (Rg + qb);
+    // the norm is rounded up by a relative 1e-5 for its FP32 evaluation
+    const float qa = sqrtf(qn) * 1.00001f;
+    const float B = sc * (R + qa);
     const float Et = ldexpf(B * B, -15) + ldexpf(1.f, -18);
-    const float Ef = ldexpf(P.R * P.R + 2.f * P.R * qa, -19) * sg * sg;
+    const float Ef = ldexpf(R * R + 2.f * R * qa, -19) * sc * sc;
     sW[row] = in_range ? 2.f * (Et + Ef) * 1.0001f : INFINITY;
 #pragma unroll
     for (int half8 = 0; half8 < 2; ++half8) {
@@ -252,8 +235,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_near_tc(NearArgs P) {
             bool ok = true;
             int64_t gt = 0;   // operand tiles issued over all row tiles
             for (int64_t rt = blockIdx.x; ok && rt < n_rt; rt += stride) {
-                const RowTile T = row_tile<MODE>(P, nrows, rt);
-                for (int t = 0; t < T.ntl; ++t, ++gt) {
+                for (int t = 0; t < P.tpg; ++t, ++gt) {
                     const int s = (int)(gt % kStages);
                     if (gt >= kStages &&
                         !dd_mbar_wait(dd_smem_addr(&bar_empty[s]), (uint32_t)(((gt / kStages) - 1) & 1))) {
@@ -261,7 +243,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_near_tc(NearArgs P) {
                         break;
                     }
                     const uint32_t bf = dd_smem_addr(&bar_full[s]);
-                    const int64_t tile = (int64_t)T.g0 * P.tpg + t;
+                    const int64_t tile = t;
                     dd_mbar_expect_tx(bf, kStageBytes);
                     dd_bulk_g2s(dd_smem_addr(sB + s * kStageBytes),
                                 reinterpret_cast<const char *>(P.chi) + tile * kTileBytes, kTileBytes, bf);
@@ -284,14 +266,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_near_tc(NearArgs P) {
             int64_t gt = 0;
             int64_t i = 0;   // row tiles of this CTA
             for (int64_t rt = blockIdx.x; ok && rt < n_rt; rt += stride, ++i) {
-                const RowTile T = row_tile<MODE>(P, nrows, rt);
                 const int b = (int)(i & 1);
                 if (!dd_mbar_wait(dd_smem_addr(&bar_afull[b]), (uint32_t)((i >> 1) & 1))) {
                     ok = false;
                     break;
                 }
                 const uint32_t a0 = dd_smem_addr(sA + b * 3 * kTileBytes);
-                for (int t = 0; t < T.ntl; ++t, ++gt) {
+                for (int t = 0; t < P.tpg; ++t, ++gt) {
                     const int s = (int)(gt % kStages);
                     const int ab = (int)(gt & 1);
                     if (!dd_mbar_wait(dd_smem_addr(&bar_full[s]), (uint32_t)((gt / kStages) & 1))) {
@@ -326,30 +307,39 @@ __global__ void __launch_bounds__(kThreads, 2) k_near_tc(NearArgs P) {
             __syncwarp();
             if (lane == 0) dd_mbar_arrive(dd_smem_addr(&bar_afull[b]));
         };
-        build_row<MODE>(P, nrows, (int64_t)blockIdx.x * kRows, row, sA, sQ, sW);
+        RowSrc src;
+        fetch_index<MODE>(P, nrows, (int64_t)blockIdx.x * kRows + row, src);
+        fetch_coords<MODE>(P, src);
+        build_row(src, P.s, P.R, row, sA, sQ, sW);
         publish(0);
         bool ok = true;
         int64_t gt = 0;
         int64_t i = 0;
         for (int64_t rt = blockIdx.x; ok && rt < n_rt; rt += stride, ++i) {
             const int b = (int)(i & 1);
-            // the next row tile's operands, into the other buffer (free once the
-            // MMAs of the row tile before this one are complete)
-            if (rt + stride < n_rt) {
+            // the next row tile's operands go into the other buffer (free once
+            // the MMAs of the row tile before this one are complete): its
+            // index now, its coordinates after the first tile, the operands
+            // after the second (or the last) one, so that the loads overlap
+            // this row tile's epilogue
+            const bool next = rt + stride < n_rt;
+            if (next) fetch_index<MODE>(P, nrows, (rt + stride) * kRows + row, src);
+            auto stage_next = [&](int t, int ntl) {
+                if (!next) return true;
+                if (t == 0) fetch_coords<MODE>(P, src);
+                if (t != (ntl > 1 ? 1 : 0)) return true;
                 const int nb = b ^ 1;
                 if (i >= 1 &&
                     !__all_sync(0xffffffffu, dd_mbar_wait(dd_smem_addr(&bar_adone[nb]), (uint32_t)(((i - 1) >> 1) & 1)))) {
                     if (lane == 0) atomicOr(P.err, DEV_ERR_TIMEOUT);
-                    break;
+                    return false;
                 }
-                build_row<MODE>(P, nrows, (rt + stride) * kRows, row, sA + nb * 3 * kTileBytes,
-                                sQ + nb * kRows * 12, sW + nb * kRows);
+                build_row(src, P.s, P.R, row, sA + nb * 3 * kTileBytes, sQ + nb * kRows * 12, sW + nb * kRows);
                 publish(nb);
-            }
-            const RowTile T = row_tile<MODE>(P, nrows, rt);
-            const int64_t r = T.r0 + row;
+                return true;
+            };
+            const int64_t r = rt * kRows + row;
             const bool active = r < nrows;
-            const int mygrp = (MODE == 2 && active) ? P.grp[r] : T.g0;
             // the row's kept list: the best tensor-core scores within the
             // window W of its K-th best so far (sorted; +inf: empty);
             // `dropped` is the least score that was within that window when
@@ -388,7 +378,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_near_tc(NearArgs P) {
                     dropped = fminf(dropped, v);
                 }
             };
-            for (int t = 0; t < T.ntl; ++t, ++gt) {
+            for (int t = 0; t < P.tpg; ++t, ++gt) {
                 const int ab = (int)(gt & 1);
                 // warp-uniform outcome: tcgen05.ld below is .sync.aligned
                 if (!__all_sync(0xffffffffu, dd_mbar_wait(dd_smem_addr(&bar_tfull[ab]), (uint32_t)((gt >> 1) & 1)))) {
@@ -397,8 +387,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_near_tc(NearArgs P) {
                     break;
                 }
                 tc_fence_after();
-                const bool use = rowok && (MODE != 2 || mygrp == T.g0 + t / P.tpg);
-                const int colbase = (t % P.tpg) * kCols;
+                const bool use = rowok;
+                const int colbase = t * kCols;
                 const uint32_t base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)ab * kCols;
                 uint32_t ra[32], rb[32];
                 float mina = 0.f, minb = 0.f;
@@ -435,6 +425,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_near_tc(NearArgs P) {
                     filter(rb, minb, c + 1);
                     if (c + 2 < 4) tmem_wait_red(ra, mina);
                 }
+                if (!stage_next(t, P.tpg)) {
+                    ok = false;
+                    break;
+                }
             }
             if (!ok || !active) continue;
             // every score not kept exceeds thr, unless `dropped` says otherwise
@@ -451,7 +445,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_near_tc(NearArgs P) {
                 q[k] = sQ[(b * kRows + row) * 12 + k];
                 qm2[k] = -2.f * q[k];
             }
-            const int64_t cb = MODE == 2 ? (int64_t)mygrp * P.Lc : 0;
             float bv[K];
             int bc[K];
 #pragma unroll
@@ -463,7 +456,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_near_tc(NearArgs P) {
             for (int e = 0; e < CAP; ++e) {
                 if (!(sv[e] <= thr)) continue;
                 const int col = sc[e];
-                const float v = alu_score(P.cent, P.cn, cb + col, qm2);
+                const float v = alu_score(P.cent, P.cn, col, qm2);
                 if (!better(v, col, bv[K - 1], bc[K - 1] < 0 ? 0x7fffffff : bc[K - 1])) continue;
                 bv[K - 1] = v;
                 bc[K - 1] = col;
@@ -514,80 +507,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_near_tc(NearArgs P) {
     }
 }
 
-// Operands of the groups (one block per group): origin = the group's own
-// origin, scale = the power of two with max |scale (c - origin)| <= 32 over
-// the group's centroids, bound = max |c - origin| (rounded up); rows in the
-// canonical layout of dd_tc_split_rows.
-__global__ void k_split_groups(const float *__restrict__ cent, int per_group, const float *__restrict__ origins,
-                               float *__restrict__ gmeta, __half *__restrict__ hi, __half *__restrict__ lo) {
-    __shared__ float s_ma, s_r2;
-    const int64_t g = blockIdx.x;
-    const float *o = origins + g * 12;
-    if (threadIdx.x == 0) {
-        s_ma = 0.f;
-        s_r2 = 0.f;
-    }
-    __syncthreads();
-    float ma = 0.f, r2 = 0.f;
-    for (int f = threadIdx.x; f < per_group; f += blockDim.x) {
-        const float *c = cent + (g * per_group + f) * 12;
-        float n2 = 0.f;
-#pragma unroll
-        for (int k = 0; k < 12; ++k) {
-            const float u = c[k] - o[k];
-            ma = fmaxf(ma, fabsf(u));
-            n2 = fmaf(u, u, n2);
-        }
-        r2 = fmaxf(r2, n2);
-    }
-    atomicMax(reinterpret_cast<unsigned *>(&s_ma), __float_as_uint(ma));   // non-negative floats order as integers
-    atomicMax(reinterpret_cast<unsigned *>(&s_r2), __float_as_uint(r2));
-    __syncthreads();
-    const float sc = s_ma > 0.f ? exp2f(floorf(log2f(32.f / s_ma))) : 1.f;
-    if (threadIdx.x < 12) gmeta[g * 16 + threadIdx.x] = o[threadIdx.x];
-    if (threadIdx.x == 12) gmeta[g * 16 + 12] = sc;
-    if (threadIdx.x == 13) gmeta[g * 16 + 13] = sqrtf(s_r2) * 1.0001f + 1e-30f;
-    for (int f = threadIdx.x; f < per_group; f += blockDim.x) {
-        const int64_t j = g * per_group + f;
-        const float *c = cent + j * 12;
-        __half h[16], l[16];
-        double nh = 0.0, nt = 0.0;
-#pragma unroll
-        for (int k = 0; k < 12; ++k) {
-            const float x = (c[k] - o[k]) * sc;
-            const __half xh = __float2half_rn(x);
-            const __half xl = __float2half_rn(x - __half2float(xh));
-            const double a = (double)__half2float(xh), b = (double)__half2float(xl);
-            nh += a * a;
-            nt += (a + b) * (a + b);
-            h[k] = __float2half_rn(-2.0f * __half2float(xh));
-            l[k] = __float2half_rn(-2.0f * __half2float(xl));
-        }
-        const double cc = nt - nh;
-        const __half nh0 = __double2half(nh), c0 = __double2half(cc);
-        h[12] = nh0;
-        h[13] = __double2half(nh - (double)__half2float(nh0));
-        l[12] = c0;
-        l[13] = __double2half(cc - (double)__half2float(c0));
-        h[14] = h[15] = l[14] = l[15] = __float2half_rn(0.f);
-        char *ph = reinterpret_cast<char *>(hi) + (j / kCols) * kTileBytes;
-        char *pl = reinterpret_cast<char *>(lo) + (j / kCols) * kTileBytes;
-        const int row = (int)(j % kCols);
-#pragma unroll
-        for (int half8 = 0; half8 < 2; ++half8) {
-            uint4 vh, vl;
-            __half *th = reinterpret_cast<__half *>(&vh), *tl = reinterpret_cast<__half *>(&vl);
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                th[k] = h[8 * half8 + k];
-                tl[k] = l[8 * half8 + k];
-            }
-            *reinterpret_cast<uint4 *>(ph + canon_off(row, 8 * half8)) = vh;
-            *reinterpret_cast<uint4 *>(pl + canon_off(row, 8 * half8)) = vl;
-        }
-    }
-}
-
 constexpr size_t kNearSmem = 100 * 1024;   // at most two CTAs (2 x 256 TMEM columns) per SM
 
 template <int MODE>
@@ -611,11 +530,10 @@ NearArgs base_args(dd_ctx *ctx, const NearTcSet &C, int32_t *fb, unsigned *fb_n,
     P.clo = C.lo;
     P.cent = C.cent;
     P.cn = C.cn;
-    P.Lc = C.per_group;
-    P.tpg = (int)((C.per_group + kCols - 1) / kCols);
+    P.Lc = (int)C.L;
+    P.tpg = (int)((C.L + kCols - 1) / kCols);
     P.s = (float)C.s;
     P.R = C.R;
-    P.gmeta = C.gmeta;
     P.fb = fb;
     P.fb_n = fb_n;
     P.fb_cap = fb_cap;
@@ -625,11 +543,9 @@ NearArgs base_args(dd_ctx *ctx, const NearTcSet &C, int32_t *fb, unsigned *fb_n,
 
 }  // namespace
 
-dd_status dd_near_tc_operands(dd_ctx *ctx, const float *cent, const float *cn, int64_t L, int per_group, double s,
+dd_status dd_near_tc_operands(dd_ctx *ctx, const float *cent, const float *cn, int64_t L, double s,
                               float R, NearTcSet *C, cudaStream_t st) {
     const int64_t L_pad = (L + kCols - 1) / kCols * kCols;
-    if (per_group % kCols != 0 && per_group != L)
-        return dd_fail(ctx, DD_ERR_STATE, "tensor-core centroid groups must be whole 128-centroid tiles");
     if (!C->hi || C->rows_pad < L_pad) {
         if (C->hi) dd_free(ctx, C->hi, (size_t)C->rows_pad * 64);
         C->hi = C->lo = nullptr;
@@ -639,53 +555,16 @@ dd_status dd_near_tc_operands(dd_ctx *ctx, const float *cent, const float *cn, i
         C->lo = C->hi + (size_t)L_pad * 16;
         C->rows_pad = L_pad;
     }
-    if (C->gmeta) dd_free(ctx, C->gmeta, (size_t)C->groups * 64);
-    C->gmeta = nullptr;
-    C->groups = 0;
     C->cent = cent;
     C->cn = cn;
     C->L = L;
-    C->per_group = per_group;
     C->s = s;
     C->R = R;
     return dd_tc_split_rows(ctx, cent, L, L_pad, s, C->hi, C->lo, st);
 }
 
-dd_status dd_near_tc_operands_grouped(dd_ctx *ctx, const float *cent, const float *cn, int64_t G, int per_group,
-                                      const float *origins, float R, NearTcSet *C, cudaStream_t st) {
-    if (per_group % kCols != 0) return dd_fail(ctx, DD_ERR_STATE, "groups must be whole 128-centroid tiles");
-    const int64_t L = G * per_group;
-    if (!C->hi || C->rows_pad < L) {
-        if (C->hi) dd_free(ctx, C->hi, (size_t)C->rows_pad * 64);
-        C->hi = C->lo = nullptr;
-        void *p = nullptr;
-        DD_TRY(dd_alloc(ctx, &p, (size_t)L * 64, "tensor-core centroid operands"));
-        C->hi = (__half *)p;
-        C->lo = C->hi + (size_t)L * 16;
-        C->rows_pad = L;
-    }
-    if (!C->gmeta || C->groups < G) {
-        if (C->gmeta) dd_free(ctx, C->gmeta, (size_t)C->groups * 64);
-        void *p = nullptr;
-        DD_TRY(dd_alloc(ctx, &p, (size_t)G * 64, "tensor-core group origins"));
-        C->gmeta = (float *)p;
-        C->groups = G;
-    }
-    C->cent = cent;
-    C->cn = cn;
-    C->L = L;
-    C->per_group = per_group;
-    C->s = 0.0;   // per group
-    C->R = R;
-    ctx->launches++;
-    k_split_groups<<<(unsigned)G, 128, 0, st>>>(cent, per_group, origins, C->gmeta, C->hi, C->lo);
-    DD_TRY_CUDA(ctx, cudaGetLastError());
-    return DD_OK;
-}
-
 void dd_near_tc_free(dd_ctx *ctx, NearTcSet *C) {
     if (C->hi) dd_free(ctx, C->hi, (size_t)C->rows_pad * 64);
-    if (C->gmeta) dd_free(ctx, C->gmeta, (size_t)C->groups * 64);
     *C = NearTcSet{};
 }
 
@@ -711,17 +590,4 @@ dd_status dd_near_tc_assign(dd_ctx *ctx, const NearTcSet &C, const float *z, int
     P.n = n;
     P.out = out;
     return launch_near<1>(ctx, P, n, s);
-}
-
-dd_status dd_near_tc_assign_grouped(dd_ctx *ctx, const NearTcSet &C, const float *z, const int32_t *perm,
-                                    const int32_t *grp, int64_t n, int32_t *out, int32_t *fb, unsigned *fb_n,
-                                    int64_t fb_cap, cudaStream_t s) {
-    if (C.per_group % kCols != 0) return dd_fail(ctx, DD_ERR_STATE, "leaves per cell must be a multiple of 128");
-    NearArgs P = base_args(ctx, C, fb, fb_n, fb_cap);
-    P.z = z;
-    P.perm = perm;
-    P.grp = grp;
-    P.n = n;
-    P.out = out;
-    return launch_near<2>(ctx, P, n, s);
 }

@@ -1,10 +1,11 @@
 """The tensor-core nearest-centroid passes (cell ranking of the search, the
-k-means assignments of the tree build) give exactly the answers of the ALU
-kernels they replace: a partition built with them equals, centroid for
-centroid and point for point, the one built on the ALU from the same data
-and seed, and searches on the two give the same indices and distances,
-including queries so far out that the tensor-core scores cannot settle them
-(those rows are finished by the ALU kernel)."""
+k-means assignment of the tree build to the cells) and the shared-memory
+leaf sums give exactly the answers of the ALU kernels they replace: a
+partition built with them equals, centroid for centroid and point for point,
+the one built on the ALU from the same data and seed, and searches on the
+two give the same indices and distances, including queries so far out that
+the tensor-core scores cannot settle them (those rows are finished by the
+ALU kernel)."""
 import numpy as np
 import pytest
 
@@ -62,9 +63,9 @@ def states(n, seed, far=0):
     return np.ascontiguousarray(y)
 
 
-# (levels, N, nlist): 128 cells of 128 leaves (every pass on the tensor
-# cores, leaf groups of one 128-centroid tile); 256 cells of 256 leaves
-# (groups of two tiles); one level of 1000 clusters (a partial last tile)
+# (levels, N, nlist): 128 cells of 128 leaves (one centroid tile); 256
+# cells of 256 leaves (two tiles); one level of 1000 clusters (a partial
+# last tile)
 CASES = [(2, 200_000, 128 * 128), (2, 300_000, 256 * 256), (1, 60_000, 1000)]
 
 
