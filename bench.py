@@ -47,17 +47,18 @@ L2_BYTES = 129 * 2 ** 20
 # its own query count and adds its own distinct points' bytes (a floor of the
 # data part).
 TRAFFIC = {
-    # mode: (source file under the package's csrc/, sha256, DRAM bytes per
-    #        search, distinct data bytes per search, queries per search)
-    "ann": ("ann.cu", "c52d8efc985664fe0c1035ef5064c5de585d9e94956be673600df90ed8960a97",
-            192.7e6, 255238 * 48.0, 262144),
+    # mode: ((source file under the package's csrc/, sha256), ...), DRAM bytes
+    #        per search, distinct data bytes per search, queries per search
+    "ann": ((("ann.cu", "f9d663d4c8381e14888e8cace9fd59a71adbfebebe45c7e486faddefb5e59579"),
+             ("near_tc.cu", "7f925e5f2a22e2a025fadf2e822dc2bd4ed3b94324d0de05e0876f0e7fc0d7f4")),
+            239.2e6, 307232 * 48.0, 262144),
 }
 
 
 # Captures of exactly the benched launch: (workload, mode): (source, sha256,
 # DRAM bytes per launch); profiles/k_scan_tc_cube16_N1e6.md.
 TRAFFIC_EXACT = {
-    ("cube16_N1e6_exact", "tc"): ("search_tc.cu", "014a9bc77e1ce7fa35332d7e18ed8bababb95804ccf158cecf784a9c6dba62b4", 78.5e6),
+    ("cube16_N1e6_exact", "tc"): ("search_tc.cu", "88f6e8471c848cf2a664b288412b49176e7e9d072215266d4cd5fdf669e3d7a7", 78.45e6),
 }
 
 
@@ -74,10 +75,11 @@ def captured_traffic(mode: str, queries_now: float, distinct_bytes_now: float):
     t = TRAFFIC.get(mode)
     if t is None:
         return None
-    path, sha, byts, distinct, queries = t
-    with open(os.path.join(ROOT, "paper_2012_00357_gb300", "csrc", path), "rb") as f:
-        if hashlib.sha256(f.read()).hexdigest() != sha:
-            return None
+    sources, byts, distinct, queries = t
+    for path, sha in sources:
+        with open(os.path.join(ROOT, "paper_2012_00357_gb300", "csrc", path), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != sha:
+                return None
     return (byts - distinct) / queries * queries_now + distinct_bytes_now
 
 
