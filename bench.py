@@ -476,12 +476,14 @@ def run_ours(args, world, rank, local):
     if mode == P.DD_SEARCH_ANN:
         # The search is bound by SM work, not by HBM: per step it evaluates
         # ~10^4 distances per query, most of them on leaves that L1/L2 serve.
-        # Lane operations: 24 per distance to a data point or a leaf centroid
-        # (12 differences, 12 FMA), and, when the cells are ranked on the ALU,
-        # 12 per coarse-cell distance (expanded form |c|^2 - 2 c.q); ranked
-        # on the tensor cores (the default) the cell distances are MMA work
-        # and are not counted.  The survey's HBM figure (48 B per probed
-        # point) and the measured DRAM traffic are reported beside it.
+        # FP32 lane operations: 12 per distance to a data point (the 12 FMA
+        # of the leaf-frame expanded form of the leaf-major scan; the in-warp
+        # probe's direct form takes 24, so this undercounts its share), 24 per
+        # leaf-centroid distance (12 differences, 12 FMA), and, when the cells
+        # are ranked on the ALU, 12 per coarse-cell distance; ranked on the
+        # tensor cores (the default) those are MMA work and are not counted.
+        # The survey's HBM figure (48 B per probed point) and the measured
+        # DRAM traffic are reported beside it.
         nq = W.m * nload
         Lr = P.dd_dataset_ann_cells(ds, ctx)[1].shape[0] if levels == 2 else nlist
         points = statistics.mean(i.points for i in infos)
@@ -489,7 +491,7 @@ def run_ours(args, world, rank, local):
         cells = statistics.mean((nq - i.skipped) * Lr for i in infos)
         leafc = max(0.0, dists - points - cells)
         tc_rank = not args.ann_alu and 16 <= Lr <= 4096
-        lane_ops = 24 * (points + leafc) + (0 if tc_rank else 12 * cells)
+        lane_ops = 12 * points + 24 * leafc + (0 if tc_rank else 12 * cells)
         achieved = lane_ops / (scan_avg / 1e3)
         byts = points * 48 + nq * 48
         traffic = captured_traffic(args.mode, nq, statistics.mean(i.unique_points for i in infos) * 48)
@@ -498,10 +500,12 @@ def run_ours(args, world, rank, local):
                            if levels == 2 else "k_ann_probe + centroid ranking (one search per step)"),
                 "bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12, "unit": "T FP32 lane-ops/s",
                 "frac": achieved / alu_peak, "traffic": traffic, "peak_source": alu_src,
-                "algorithmic": ("24 lane-ops per point or leaf-centroid distance, per search (the step's one launch "
-                                "sequence); the coarse-cell distances run on the tensor cores" if tc_rank else
-                                "24 lane-ops per point or leaf-centroid distance + 12 per coarse-cell distance, "
-                                "per search (the step's one launch sequence)"),
+                "algorithmic": ("12 lane-ops per point distance + 24 per leaf-centroid distance, per search (the "
+                                "step's one launch sequence); the coarse-cell distances run on the tensor cores"
+                                if tc_rank else
+                                "12 lane-ops per point distance + 24 per leaf-centroid distance + 12 per coarse-cell "
+                                "distance, per search (the step's one launch sequence)"),
+                "lane_ops_direct_form": 24 * (points + leafc),
                 "lane_ops": lane_ops, "distances": {"points": points, "leaf_centroids": leafc, "cells": cells},
                 "hbm": {"algorithmic_bytes": byts,
                         "algorithmic": "48 B x points of the clusters each non-skipped query probed + 48 B x "

@@ -1145,6 +1145,7 @@ struct PairRes {
 
 struct LeafScanArgs {
     const float *zs;
+    const float *cent;          // [L x 12] leaf centroids
     const int64_t *offs;
     const QueryRec *rec;
     const unsigned *bucket, *pair_off, *item_off;
@@ -1170,15 +1171,27 @@ struct LeafBest {
 };
 
 // One warp per chunk of up to 64 queries of a leaf: lane l takes queries l
-// and l + 32, so every point read serves two distances (the scan is bound by
-// the L1 reads of the points, one broadcast read per point and warp).  A
-// chunk of at most 16 queries (a leaf few queries reach, typical of the first
-// DD iterations) gives each query several lanes, which split the points.
-__global__ void __launch_bounds__(256) k_leaf_scan(LeafScanArgs A) {
+// and l + 32, so every point read serves two distances.  A chunk of at most
+// 16 queries (a leaf few queries reach, typical of the first DD iterations)
+// gives each query several lanes, which split the points.
+//
+// Distances in the leaf's own frame: the warp stages 32 points at a time in
+// shared memory as x' = x - c (c the leaf's centroid) with |x'|^2, and a
+// query q' = q - c scores |x'|^2 - 2 x'.q' (12 FMA against the direct form's
+// 12 differences and 12 FMA); |q'|^2 is added to the best two at the end.
+// In the leaf's frame the magnitudes are those of the leaf and of the query's
+// distance to it, so the expanded form keeps the direct form's precision.
+constexpr int kStagePts = 32;   // points a warp stages at a time
+
+__global__ void __launch_bounds__(256, 3) k_leaf_scan(LeafScanArgs A) {
     __shared__ unsigned long long sc;
+    __shared__ __align__(16) float4 sx[8][kStagePts][4];   // per warp: x' (3 float4) and |x'|^2
+    __shared__ __align__(16) float4 scen[8][3];            // per warp: the leaf's centroid
     if (threadIdx.x == 0) sc = 0ull;
     __syncthreads();
     const int lane = threadIdx.x & 31;
+    float4(*const px)[4] = sx[threadIdx.x >> 5];
+    float4 *const pc = scen[threadIdx.x >> 5];
     const unsigned nw = (gridDim.x * blockDim.x) >> 5;
     const unsigned total = A.item_off[A.L];
     for (unsigned it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < total; it += nw) {
@@ -1199,42 +1212,69 @@ __global__ void __launch_bounds__(256) k_leaf_scan(LeafScanArgs A) {
         const unsigned slot = (unsigned)(lane / G), sub = (unsigned)(lane & (G - 1));
         const bool act0 = slot < qn, act1 = (unsigned)lane + 32u < qn;
         const unsigned s0 = act0 ? A.bucket[q0 + slot] : 0u, s1 = act1 ? A.bucket[q0 + 32 + lane] : 0u;
-        float qa[12], qb[12];
         const QueryRec *ra = A.rec + (act0 ? s0 / kPairMax : 0), *rb = A.rec + (act1 ? s1 / kPairMax : 0);
+        __syncwarp();   // the previous chunk's reads of the centroid are done
+        if (lane < 3) pc[lane] = __ldg(reinterpret_cast<const float4 *>(A.cent + (size_t)l * 12) + lane);
+        __syncwarp();
+        float ma[12], mb[12];   // -2 q' of the lane's queries
+        float qna = 0.f, qnb = 0.f;
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
-            qa[k] = ra->q[k];
-            qb[k] = rb->q[k];
+            const float ck = reinterpret_cast<const float *>(pc)[k];
+            const float ua = ra->q[k] - ck, ub = rb->q[k] - ck;
+            ma[k] = -2.f * ua;
+            mb[k] = -2.f * ub;
+            qna = fmaf(ua, ua, qna);
+            qnb = fmaf(ub, ub, qnb);
         }
         const int64_t p0 = A.offs[l], p1 = A.offs[l + 1];
-        const float *zp = A.zs + p0 * 12;
         const int n = (int)(p1 - p0);
-        LeafBest ba, bb;
-        if (two) {
-            for (int t = 0; t < n; ++t) {
-                const float4 *v = reinterpret_cast<const float4 *>(zp + (size_t)t * 12);
+        LeafBest ba, bb;   // scores |x'|^2 - 2 x'.q' until |q'|^2 is added
+        for (int t0 = 0; t0 < n; t0 += kStagePts) {
+            const int nc = min(kStagePts, n - t0);
+            __syncwarp();
+            if (lane < nc) {
+                const float4 *v = reinterpret_cast<const float4 *>(A.zs + (size_t)(p0 + t0 + lane) * 12);
                 const float4 u0 = __ldg(v), u1 = __ldg(v + 1), u2 = __ldg(v + 2);
-                const float x[12] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w, u2.x, u2.y, u2.z, u2.w};
-                float da = 0.f, db = 0.f;
-#pragma unroll
-                for (int k = 0; k < 12; ++k) {
-                    const float ta = x[k] - qa[k], tb = x[k] - qb[k];
-                    da = fmaf(ta, ta, da);
-                    db = fmaf(tb, tb, db);
+                const float4 e0 = pc[0], e1 = pc[1], e2 = pc[2];
+                const float4 w0 = make_float4(u0.x - e0.x, u0.y - e0.y, u0.z - e0.z, u0.w - e0.w);
+                const float4 w1 = make_float4(u1.x - e1.x, u1.y - e1.y, u1.z - e1.z, u1.w - e1.w);
+                const float4 w2 = make_float4(u2.x - e2.x, u2.y - e2.y, u2.z - e2.z, u2.w - e2.w);
+                float nx = 0.f;
+                nx = fmaf(w0.x, w0.x, nx); nx = fmaf(w0.y, w0.y, nx); nx = fmaf(w0.z, w0.z, nx); nx = fmaf(w0.w, w0.w, nx);
+                nx = fmaf(w1.x, w1.x, nx); nx = fmaf(w1.y, w1.y, nx); nx = fmaf(w1.z, w1.z, nx); nx = fmaf(w1.w, w1.w, nx);
+                nx = fmaf(w2.x, w2.x, nx); nx = fmaf(w2.y, w2.y, nx); nx = fmaf(w2.z, w2.z, nx); nx = fmaf(w2.w, w2.w, nx);
+                px[lane][0] = w0;
+                px[lane][1] = w1;
+                px[lane][2] = w2;
+                px[lane][3] = make_float4(nx, 0.f, 0.f, 0.f);
+            }
+            __syncwarp();
+            auto score = [&](const float (&m)[12], const float4 &w0, const float4 &w1, const float4 &w2, float nx) {
+                float s = nx;
+                s = fmaf(m[0], w0.x, s); s = fmaf(m[1], w0.y, s); s = fmaf(m[2], w0.z, s); s = fmaf(m[3], w0.w, s);
+                s = fmaf(m[4], w1.x, s); s = fmaf(m[5], w1.y, s); s = fmaf(m[6], w1.z, s); s = fmaf(m[7], w1.w, s);
+                s = fmaf(m[8], w2.x, s); s = fmaf(m[9], w2.y, s); s = fmaf(m[10], w2.z, s); s = fmaf(m[11], w2.w, s);
+                return s;
+            };
+            if (two) {
+                for (int t = 0; t < nc; ++t) {
+                    const float4 w0 = px[t][0], w1 = px[t][1], w2 = px[t][2];
+                    const float nx = px[t][3].x;
+                    ba.offer(score(ma, w0, w1, w2, nx), (int)p0 + t0 + t);
+                    bb.offer(score(mb, w0, w1, w2, nx), (int)p0 + t0 + t);
                 }
-                ba.offer(da, (int)p0 + t);
-                bb.offer(db, (int)p0 + t);
+            } else {
+                for (int t = (int)sub; t < nc; t += G)
+                    ba.offer(score(ma, px[t][0], px[t][1], px[t][2], px[t][3].x), (int)p0 + t0 + t);
             }
-        } else {
-            int t = (int)sub;
-            for (; t + 3 * G < n; t += 4 * G) {
-                float d[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) d[u] = dist2_12(zp + (size_t)(t + u * G) * 12, qa);
-#pragma unroll
-                for (int u = 0; u < 4; ++u) ba.offer(d[u], (int)p0 + t + u * G);
-            }
-            for (; t < n; t += G) ba.offer(dist2_12(zp + (size_t)t * 12, qa), (int)p0 + t);
+        }
+        // back to squared distances (rounding can take a score below -|q'|^2)
+        ba.b1 = fmaxf(ba.b1 + qna, 0.f);
+        ba.b2 = fmaxf(ba.b2 + qna, 0.f);
+        bb.b1 = fmaxf(bb.b1 + qnb, 0.f);
+        bb.b2 = fmaxf(bb.b2 + qnb, 0.f);
+        if (!two) {
             // merge the G partial results of a query (ties to the lower point;
             // the second distance is the second smallest of all points read)
             for (int o = 1; o < G; o <<= 1) {
@@ -2038,7 +2078,7 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
         k_leaf_sums_top<<<1, 1024, 0, s>>>(bsum, bitem, nb);
         k_leaf_offsets<<<nb, 256, 0, s>>>(leaf_cnt, L, bsum, bitem, pair_off, item_off);
         k_pair_scatter<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(pair_leaf, n_pairs, m, pair_off, cursor, bucket);
-        LeafScanArgs LS{a.zs, a.offs, rec, bucket, pair_off, item_off, L, res, counters, touched};
+        LeafScanArgs LS{a.zs, a.cent, a.offs, rec, bucket, pair_off, item_off, L, res, counters, touched};
         k_leaf_scan<<<(unsigned)(ctx->n_sm * 8), 256, 0, s>>>(LS);
         k_pair_merge<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(n_pairs, res, a.perm, m, out.idx, d1f, d2f);
     } else if (two) {
