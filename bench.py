@@ -49,9 +49,9 @@ L2_BYTES = 129 * 2 ** 20
 TRAFFIC = {
     # mode: ((source file under the package's csrc/, sha256), ...), DRAM bytes
     #        per search, distinct data bytes per search, queries per search
-    "ann": ((("ann.cu", "f9d663d4c8381e14888e8cace9fd59a71adbfebebe45c7e486faddefb5e59579"),
+    "ann": ((("ann.cu", "5b2f6957a4c2794718292bb185b28d16b28b282505443acd7bbbf0abaada8162"),
              ("near_tc.cu", "7f925e5f2a22e2a025fadf2e822dc2bd4ed3b94324d0de05e0876f0e7fc0d7f4")),
-            239.2e6, 307232 * 48.0, 262144),
+            239.86e6, 307232 * 48.0, 262144),
 }
 
 
