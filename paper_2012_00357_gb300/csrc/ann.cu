@@ -570,6 +570,14 @@ __global__ void __launch_bounds__(256) k_ann_probe(ProbeArgs A) {
         const float dP = A.cand_d[i * kCand + kCand - 1];
         incomplete = (dP - f_d * A.rmax < dc);
     }
+    // every candidate cluster was empty (degenerate data, e.g. many copies of
+    // a few points leave most clusters without members): the whole data set,
+    // so that the answer is always a data point (b is warp-uniform here)
+    if (b.j == 0x7fffffff) {
+        scan_range(A.zs, A.perm, 0, A.N, lane, q, b);
+        scanned += (unsigned long long)A.N;
+        best_warp(b);
+    }
     if (lane == 0) {
         atomicAdd(A.counters, scanned);
         atomicAdd(A.counters + 5, scanned);
@@ -583,12 +591,33 @@ __global__ void __launch_bounds__(256) k_ann_probe(ProbeArgs A) {
     }
 }
 
-// FP64 rescoring of the answer (Eq. 3) and the second distance in Eq. 3 units
+// FP64 rescoring of the answer (Eq. 3) and the second distance in Eq. 3 units.
+// A query whose candidate leaves were all empty and none handed off
+// (degenerate data: many copies of a few points leave most leaves without
+// members) has no answer yet: this thread scans the whole data set for it
+// (the two-level probe leaves that rare case here to keep its registers).
 __global__ void k_ann_finish(const float *__restrict__ raw, MetricMaps M, const double *__restrict__ y, int64_t m,
-                             const int32_t *__restrict__ idx, const float *__restrict__ d2f,
-                             double *__restrict__ d2, double *__restrict__ d2nd) {
+                             int32_t *__restrict__ idx, float *__restrict__ d2f, double *__restrict__ d2,
+                             double *__restrict__ d2nd, const float *__restrict__ z32, int64_t N,
+                             const QueryRec *__restrict__ rec) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= m) return;
+    if (idx[i] < 0 || idx[i] >= N) {
+        float q[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) q[k] = rec[i].q[k];
+        float b1 = INFINITY;
+        int j1 = 0;
+        for (int64_t j = 0; j < N; ++j) {
+            const float d = dist2_12(z32 + j * 12, q);
+            if (d < b1) {
+                b1 = d;
+                j1 = (int)j;
+            }
+        }
+        idx[i] = j1;
+        d2f[i] = 0.f;   // no second-distance bound: the query is searched again next time
+    }
     double yy[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) yy[k] = y[i * 12 + k];
@@ -1955,11 +1984,12 @@ dd_status dd_ann_rank_cells(dd_dataset *ds, const QueryRec *rec, int64_t m, int3
     return ann_rank_listed(ds, rec, m, nullptr, nullptr, cand_cl, cand_d, s);
 }
 
-dd_status dd_ann_finish(dd_dataset *ds, const double *y_dev, int64_t m, const int32_t *idx, const float *d2f,
-                        double *d2, double *d2nd, cudaStream_t s) {
+dd_status dd_ann_finish(dd_dataset *ds, const double *y_dev, int64_t m, const QueryRec *rec, int32_t *idx,
+                        float *d2f, double *d2, double *d2nd, cudaStream_t s) {
     dd_ctx *ctx = ds->ctx;
     ctx->launches++;
-    k_ann_finish<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(ds->raw, ds->M, y_dev, m, idx, d2f, d2, d2nd);
+    k_ann_finish<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(ds->raw, ds->M, y_dev, m, idx, d2f, d2, d2nd, ds->z32,
+                                                             ds->N, rec);
     DD_TRY_CUDA(ctx, cudaGetLastError());
     return DD_OK;
 }
@@ -2089,7 +2119,7 @@ dd_status dd_search_ann_motion(dd_dataset *ds, const double *y_dev, int64_t m, d
     }
     DD_TRY_CUDA(ctx, cudaGetLastError());
     if (st) DD_TRY_CUDA(ctx, dd_event_record(ctx, ctx->ev_scan[1], s));
-    DD_TRY(dd_ann_finish(ds, y_dev, m, out.idx, d2f, out.d2, out.d2nd, s));
+    DD_TRY(dd_ann_finish(ds, y_dev, m, rec, out.idx, d2f, out.d2, out.d2nd, s));
     // exact re-search where the candidate list may be incomplete (f_d = 1)
     unsigned long long n_fb = 0;
     // (a captured step never holds f_d = 1: its caller checks)

@@ -314,9 +314,11 @@ void dd_free_ann(dd_dataset *ds);
 dd_status dd_ann_rank_cells(dd_dataset *ds, const QueryRec *rec, int64_t m, int32_t *cand_cl, float *cand_d,
                             cudaStream_t s);
 // FP64 Eq. (3) distance of every answer, and the second distance (FP32 plain
-// squared, mapped coordinates) in Eq. (3) units.
-dd_status dd_ann_finish(dd_dataset *ds, const double *y_dev, int64_t m, const int32_t *idx, const float *d2f,
-                        double *d2, double *d2nd, cudaStream_t s);
+// squared, mapped coordinates) in Eq. (3) units; a query left without an
+// answer (every candidate leaf empty) is searched over the whole data set
+// here.
+dd_status dd_ann_finish(dd_dataset *ds, const double *y_dev, int64_t m, const QueryRec *rec, int32_t *idx,
+                        float *d2f, double *d2, double *d2nd, cudaStream_t s);
 
 // k-nearest-neighbour graph (knng.cu)
 dd_status dd_build_knng(dd_dataset *ds, const dd_dataset_opts &o);

@@ -511,7 +511,7 @@ dd_status dd_search_knng(dd_dataset *ds, const double *y_dev, int64_t m, int f_s
     else k_knng_walk<4><<<grid, 256, 0, s>>>(A);
     DD_TRY_CUDA(ctx, cudaGetLastError());
     if (st) DD_TRY_CUDA(ctx, dd_event_record(ctx, ctx->ev_scan[1], s));
-    DD_TRY(dd_ann_finish(ds, y_dev, m, out.idx, d2f, out.d2, out.d2nd, s));
+    DD_TRY(dd_ann_finish(ds, y_dev, m, rec, out.idx, d2f, out.d2, out.d2nd, s));
     // the walk's skip does not depend on f_d (its record is stored as made at f_d = 1)
     if (mot && out.d2 && out.d2nd) DD_TRY(dd_ann_motion_update(ctx, rec, m, out.d2, out.d2nd, 1.0, nullptr, 0, mot, s));
     if (st && ctx->defer) {

@@ -109,3 +109,27 @@ def test_assignment_is_nearest_centroid(ctx):
         assert np.all(got - best <= 1e-5 * scale)
     finally:
         P.dd_free_dataset(ds)
+
+
+def test_tied_centroids_are_finished_on_the_alu(ctx):
+    """Forty distinct points, each repeated 500 times: the k-means build
+    starts from many identical centroids, so most points have more tied
+    nearest cells than the tensor-core list holds; those rows go to the ALU
+    kernel, and the partition and the searches still equal the ALU-only
+    build's (ties to the lower index)."""
+    base = I.make_dataset(40, I.NONLINEAR, seed=35)
+    data = np.ascontiguousarray(np.repeat(base, 500, axis=0))
+    a, b = pair(ctx, data, ann_nlist=1000, seed=3)
+    try:
+        print(f"tied centroids: build rows left to the ALU {P.dd_dataset_ann_build_fallback(a)}")
+        assert P.dd_dataset_ann_build_fallback(a) > 0
+        for x, z in zip(export(ctx, a, False), export(ctx, b, False)):
+            assert np.array_equal(x, z)
+        y = states(500, seed=36)
+        for f_d in (0.0, 0.8):
+            ia, da = search(ctx, a, y, f_d, None)
+            ib, db = search(ctx, b, y, f_d, None)
+            assert np.array_equal(ia, ib) and np.array_equal(da, db)
+    finally:
+        P.dd_free_dataset(a)
+        P.dd_free_dataset(b)
