@@ -49,7 +49,7 @@ L2_BYTES = 129 * 2 ** 20
 TRAFFIC = {
     # mode: ((source file under the package's csrc/, sha256), ...), DRAM bytes
     #        per search, distinct data bytes per search, queries per search
-    "ann": ((("ann.cu", "5b2f6957a4c2794718292bb185b28d16b28b282505443acd7bbbf0abaada8162"),
+    "ann": ((("ann.cu", "b215ecd4527cb4aa091bd5db4d12157189d5e0570ca1156428f73788cf452cd5"),
              ("near_tc.cu", "7f925e5f2a22e2a025fadf2e822dc2bd4ed3b94324d0de05e0876f0e7fc0d7f4")),
             239.86e6, 307232 * 48.0, 262144),
 }
